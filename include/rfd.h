@@ -1,0 +1,177 @@
+/*
+ * rfd.h -- C ABI of the GB300 RFDiffusion (RFD) graph-field integrator.
+ *
+ * RFD (Sec. 2.4, "RFDiffusion") approximates graph-field integration
+ *     i(v) = sum_w K(w, v) F(w)                  (Sec. 1, Eq. base_integ)
+ * with the graph diffusion kernel K = exp(lambda W) (Sec. 2, Eq. diffusion)
+ * on the eps-nearest-neighbour graph of a point cloud, W(i,j) = f(n_i - n_j)
+ * (Sec. 2.4, Eq. w), by a random-feature factorisation W ~ A B^T and
+ *     out = F + A ([exp(lambda B^T A) - I] (B^T A)^{-1} (B^T F))   (Sec. 2.4)
+ * evaluated here as out = F + A (G (B^T F)), G = lambda phi1(lambda B^T A),
+ * phi1(X) = sum_k X^k / (k+1)!  (the same matrix whenever B^T A is
+ * invertible; no inverse is ever formed).
+ *
+ * Conventions used by every entry point
+ *   - Kernel f: indicator of the L-infinity cube ||z||_inf <= eps; its Fourier
+ *     transform is tau(w) = prod_d sin(2 pi eps w_d)/(pi w_d) (Sec. 2.4).
+ *   - m = number of REAL columns of A and B (even): m/2 frequencies w_j in R^3,
+ *     each giving a cos and a sin column (the real-part estimator of App. A.4).
+ *   - Frequencies: per-coordinate N(0, sigma^2) truncated to [-R, R], drawn by
+ *     rejection from a SplitMix64 stream seeded with `seed` (rfd_sample_frequencies
+ *     documents the exact order); r_j = tau(w_j)/p(w_j).
+ *   - A = Phi diag(s sgn r), B = Phi diag(s), s_j = sqrt(2 |r_j| / m), where
+ *     Phi = [cos 2 pi X w^T | sin 2 pi X w^T] (N x m).
+ *   - Points: N x 3 float32, row-major (x, y, z), DEVICE memory unless stated.
+ *   - Fields F and outputs: N x c float32, row-major with leading dimension
+ *     ld >= c (elements), DEVICE memory unless stated.
+ *   - Every call returns an rfd_status; nothing aborts or throws across the
+ *     ABI.  On failure rfd_last_error() returns a thread-local message and the
+ *     plan stays usable (unless the CUDA context itself is lost).
+ *   - Device work is asynchronous on the plan's stream unless stated; the caller
+ *     keeps device buffers alive until rfd_sync() (or rfd_poll()) reports
+ *     completion.
+ */
+#ifndef RFD_H_
+#define RFD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RFD_API __attribute__((visibility("default")))
+#else
+#define RFD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RFD_OK = 0,
+  RFD_EINVAL = 1,      /* invalid argument (sizes, null pointers, parameters)      */
+  RFD_ENOMEM = 2,      /* device or host allocation failed                          */
+  RFD_ECUDA = 3,       /* a CUDA runtime/driver call failed                         */
+  RFD_ENOTREADY = 4,   /* rfd_poll: the request has not finished yet                */
+  RFD_ETIMEDOUT = 5,   /* a bounded wait ran out (host poll or device-side wait)    */
+  RFD_ENUMERIC = 6,    /* G or the output is not finite (overflow of exp(lambda W)) */
+  RFD_EBUSY = 7,       /* serving: admission refused (memory budget / queue full)   */
+  RFD_ENOTSUP = 8      /* feature not available in this build / on this device      */
+} rfd_status;
+
+typedef enum {
+  RFD_FP32_PLAIN = 0,  /* FP32 features, SIMT FP32 reductions (compensated), FP64 G */
+  RFD_BF16_TC = 1      /* BF16 features, tcgen05 BF16 x BF16 -> FP32 GEMMs, FP64 G  */
+} rfd_precision;
+
+/* Parameters of one point cloud's integrator (Sec. 2.4: points, eps, lambda,
+ * m random features, seed).  Zero for freq_sigma / freq_radius selects the
+ * defaults sigma = 1/(2 eps), R = 1/eps. */
+typedef struct {
+  int64_t n;             /* number of points N >= 1                               */
+  int32_t m;             /* real feature columns, even, 2 <= m <= 4096            */
+  int32_t max_channels;  /* largest c passed to rfd_integrate / rfd_gfi, 1..256   */
+  double eps;            /* L-infinity radius of the eps-NN graph, > 0            */
+  double lambda;         /* diffusion parameter, any finite real; 0 => out == F   */
+  uint64_t seed;         /* seed of the frequency stream                          */
+  int32_t precision;     /* rfd_precision                                         */
+  int32_t flags;         /* reserved, must be 0                                   */
+  double freq_sigma;     /* sigma of the truncated Gaussian (0 => 1/(2 eps))      */
+  double freq_radius;    /* truncation half-width R (0 => 1/eps)                  */
+} rfd_params;
+
+typedef struct rfd_plan_s* rfd_plan_t;
+
+/* Step statistics of the last rfd_features / rfd_gfi call on a plan. */
+typedef struct {
+  double norm1;          /* ||lambda M||_1                                         */
+  int32_t pade_degree;   /* diagonal Pade degree q used for exp of the augmented matrix */
+  int32_t squarings;     /* scaling-and-squaring steps s                          */
+  int32_t nonfinite;     /* 1 if G was not finite                                 */
+  int32_t splits;        /* split-K factor used by the reductions over N          */
+} rfd_stats;
+
+/* ---------------------------------------------------------------------------
+ * Step a1 (host only, no device work): the random frequencies and weights.
+ * Sec. 2.4: w_1..w_{m/2} iid ~ P, nu_j^2 = tau(w_j)/p(w_j).
+ *
+ * Draw order: a SplitMix64 stream (state += 0x9E3779B97F4A7C15, finaliser
+ * shifts 30/27/31) seeded with `seed` yields uniforms u = ((x >> 11) + 0.5)
+ * 2^-53.  For j = 0..m/2-1, d = 0..2: repeat { u1, u2 from the stream;
+ * w = R (2 u1 - 1); accept if u2 < exp(-(w/sigma)^2 / 2) } (at most 2^20
+ * tries per coordinate, else RFD_EINVAL).
+ *   omega_out: host, (m/2) x 3 doubles, row-major, caller-owned (may be NULL)
+ *   r_out:     host, m/2 doubles r_j = tau(w_j)/p(w_j), caller-owned (may be NULL)
+ * --------------------------------------------------------------------------- */
+RFD_API rfd_status rfd_sample_frequencies(int32_t m, double eps, uint64_t seed, double freq_sigma,
+                                  double freq_radius, double* omega_out, double* r_out);
+
+/* Create a plan: validate params, run step a1 on the host, upload the
+ * frequencies and column scales, and allocate every device buffer the plan
+ * will use (the feature matrix, split-K partials, M, G and the FP64 phi1
+ * workspace).  `cuda_stream` is a cudaStream_t (NULL = legacy default
+ * stream); all of the plan's device work runs on it.  *out receives the plan
+ * (owned by the caller, released with rfd_plan_destroy).  RFD_ENOMEM if a
+ * device allocation fails (nothing is leaked). */
+RFD_API rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out);
+
+/* Release a plan and its device memory (synchronises the plan's stream). */
+RFD_API rfd_status rfd_plan_destroy(rfd_plan_t plan);
+
+/* Pre-processing (Sec. 2.4: "linear in N, cubic in m"), steps a2-a4:
+ * features Phi of d_points (N x 3 float32, device), M = B^T A by split-K
+ * reduction over N, and G = lambda phi1(lambda M) in FP64 (scaling-and-
+ * squaring diagonal Pade on the block-triangular augmented matrix
+ * [[lambda M, I], [0, 0]]).  Phi and G stay resident in the plan for later
+ * rfd_integrate calls.  Synchronises the stream once (the Pade degree and the
+ * number of squarings are chosen on the host from ||lambda M||_1).
+ * RFD_ENUMERIC if G is not finite. */
+RFD_API rfd_status rfd_features(rfd_plan_t plan, const float* d_points);
+
+/* Inference (Sec. 2.4: "linear in N, quadratic in m"), steps a3(Y)-a6, on
+ * the resident Phi and G: Y = B^T F, Z = diag(s sgn r) G Y, out = F + Phi Z.
+ * d_F: N x c float32 device, leading dimension ldF >= c; d_out: N x c float32
+ * device, leading dimension ldOut >= c.  d_out == d_F (same ld) is allowed.
+ * 1 <= c <= params.max_channels.  Asynchronous on the plan's stream. */
+RFD_API rfd_status rfd_integrate(rfd_plan_t plan, const float* d_F, int32_t c, int64_t ldF,
+                         float* d_out, int64_t ldOut);
+
+/* One cold pass of the whole path (a2-a6) when F is known up front: the
+ * reductions B^T A and B^T F share one pass over the feature matrix.
+ * Arguments as rfd_features + rfd_integrate; leaves Phi and G resident. */
+RFD_API rfd_status rfd_gfi(rfd_plan_t plan, const float* d_points, const float* d_F, int32_t c,
+                   int64_t ldF, float* d_out, int64_t ldOut);
+
+/* Step a4 alone: G = lambda phi1(lambda M) for an m x m FP64 matrix M
+ * (Sec. 2.4: [exp(lambda M) - I] M^{-1}, evaluated without the inverse),
+ * by the same scaling-and-squaring Pade evaluation rfd_features uses.
+ * d_M, d_G: m x m row-major float64 DEVICE buffers (may not alias);
+ * 1 <= m <= 4096.  Allocates (and frees) its own FP64 workspace, about
+ * 24 m^2 doubles; synchronises `cuda_stream`.  stats_out (host, may be NULL)
+ * receives ||lambda M||_1, the Pade degree and the squaring count.
+ * RFD_ENUMERIC if G is not finite. */
+RFD_API rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double* d_G, void* cuda_stream,
+                            rfd_stats* stats_out);
+
+/* Wait for all of the plan's queued device work. */
+RFD_API rfd_status rfd_sync(rfd_plan_t plan);
+
+/* Copy the plan's random features and (if computed) G to HOST buffers:
+ * omega (m/2 x 3), r (m/2), G (m x m, row-major FP64; pass NULL to skip, or
+ * if rfd_features has not run).  Synchronises the stream. */
+RFD_API rfd_status rfd_plan_export(rfd_plan_t plan, double* omega, double* r, double* G);
+
+/* Statistics of the last rfd_features / rfd_gfi (host struct). */
+RFD_API rfd_status rfd_plan_stats(rfd_plan_t plan, rfd_stats* out);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+RFD_API const char* rfd_last_error(void);
+
+/* Library version string. */
+RFD_API const char* rfd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RFD_H_ */

@@ -1,0 +1,255 @@
+"""CPU FP64 oracle of the RFDiffusion (RFD) graph-field integrator.
+
+TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and bench.py's
+CPU-baseline / reference leg may import this module.  The library
+(paper_2302_00942_gb300) never imports, links or runs anything here, and this
+module imports nothing from the library: the two share no code.
+
+What it computes (Sec. 2.4 "RFDiffusion", App. A.4):
+
+  graph field integration   i = exp(lambda W) F            (Eq. base_integ, Eq. diffusion)
+  eps-NN graph              W(i,j) = f(n_i - n_j)          (Eq. w)
+  random features           f(z) = int exp(2 pi i w^T z) tau(w) dw, importance-sampled with p
+  real-part estimator       W_hat = (1/h) sum_k cos(2 pi w_k^T z) tau(w_k)/p(w_k)   (App. A.4)
+  low-rank identity         exp(lambda A B^T) = I + A [exp(lambda B^T A) - I](B^T A)^{-1} B^T
+  evaluation order          x + A([exp(lambda B^T A) - I]((B^T A)^{-1}(B^T x)))
+
+with the readings of the paper used throughout this project:
+
+  * f is the indicator of the L-infinity cube ||z||_inf <= eps: the product of
+    per-coordinate sincs printed for tau in Sec. 2.4 is the Fourier transform of
+    that cube (an L1 ball's transform does not factor).  With the 2 pi
+    convention of Sec. 2.4, tau(w) = prod_d sin(2 pi eps w_d) / (pi w_d)
+    (value 2 eps at w_d = 0).
+  * P is a per-coordinate Gaussian N(0, sigma^2) truncated to [-R, R]
+    ("(truncated) Gaussian", Sec. 2.4; App. A.4), default sigma = 1/(2 eps),
+    R = 1/eps.
+  * m counts REAL columns of A and B: h = m/2 frequencies, each giving a cos
+    and a sin column, so that A B^T is the real part of phi(n_i)^T psi(n_j).
+  * tau/p may be negative, so sqrt(tau/p) is split as A = Phi diag(s sgn r),
+    B = Phi diag(s), s = sqrt(2|r|/m): then A B^T = Phi diag(2r/m) Phi^T = W_hat.
+  * (B^T A)^{-1} need not exist (N < m); [exp(lambda M) - I] M^{-1} is the
+    entire function lambda * phi1(lambda M), phi1(X) = sum_k X^k/(k+1)!,
+    which is what is evaluated (never an inverse).
+
+Random numbers (the frequencies w) follow a counter-free published generator,
+SplitMix64 (Steele, Lea, Flood, OOPSLA 2014), written out here from its
+definition; the library implements the same definition independently.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg
+import scipy.special
+
+MASK64 = (1 << 64) - 1
+MAX_TRIES = 1 << 20  # rejection-sampling attempts allowed per coordinate
+
+
+# ---------------------------------------------------------------------------
+# Random numbers: SplitMix64 -> 53-bit uniforms in (0, 1)
+# ---------------------------------------------------------------------------
+class SplitMix64:
+    """SplitMix64: a Weyl sequence (increment 0x9E3779B97F4A7C15) passed
+    through the variant-13 64-bit finaliser (shifts 30/27/31)."""
+
+    GAMMA = 0x9E3779B97F4A7C15
+
+    def __init__(self, seed: int):
+        self.state = int(seed) & MASK64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + self.GAMMA) & MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        return z ^ (z >> 31)
+
+    def next_uniform(self) -> float:
+        """(top 53 bits + 1/2) * 2^-53: never 0, never 1."""
+        return ((self.next_u64() >> 11) + 0.5) * (1.0 / 9007199254740992.0)
+
+
+def default_sigma(eps: float) -> float:
+    return 1.0 / (2.0 * eps)
+
+
+def default_radius(eps: float) -> float:
+    return 1.0 / eps
+
+
+# ---------------------------------------------------------------------------
+# Step a1: frequencies w_j ~ P and weights r_j = tau(w_j)/p(w_j)   (Sec. 2.4)
+# ---------------------------------------------------------------------------
+def sample_frequencies(m: int, eps: float, seed: int, sigma: float = 0.0,
+                       radius: float = 0.0) -> np.ndarray:
+    """h = m/2 frequencies in R^3 from the truncated Gaussian P (Sec. 2.4 "Note").
+
+    Per coordinate, independently, in the order j = 0..h-1, d = 0..2: draw
+    u1, u2 from the stream; w = R (2 u1 - 1) is uniform on [-R, R]; accept when
+    u2 < exp(-(w/sigma)^2 / 2).  Accepted w are exactly N(0, sigma^2)
+    conditioned on |w| <= R.
+    """
+    if m < 2 or m % 2:
+        raise ValueError("m must be even and >= 2")
+    sigma = sigma or default_sigma(eps)
+    radius = radius or default_radius(eps)
+    rng = SplitMix64(seed)
+    h = m // 2
+    omega = np.empty((h, 3), dtype=np.float64)
+    for j in range(h):
+        for d in range(3):
+            for _ in range(MAX_TRIES):
+                u1 = rng.next_uniform()
+                u2 = rng.next_uniform()
+                w = radius * (2.0 * u1 - 1.0)
+                a = w / sigma
+                if u2 < math.exp(-0.5 * a * a):
+                    omega[j, d] = w
+                    break
+            else:
+                raise RuntimeError("rejection sampler did not accept within MAX_TRIES")
+    return omega
+
+
+def tau(omega: np.ndarray, eps: float) -> np.ndarray:
+    """Fourier transform of 1[||z||_inf <= eps] (Sec. 2.4, the product of
+    per-coordinate sincs), 2 pi convention: prod_d sin(2 pi eps w_d)/(pi w_d)."""
+    w = np.asarray(omega, dtype=np.float64)
+    safe = np.where(w == 0.0, 1.0, w)
+    per = np.where(w == 0.0, 2.0 * eps, np.sin(2.0 * np.pi * eps * w) / (np.pi * safe))
+    return np.prod(per, axis=-1)
+
+
+def density(omega: np.ndarray, sigma: float, radius: float) -> np.ndarray:
+    """pdf of P: per coordinate exp(-w^2/(2 sigma^2)) / (sigma sqrt(2 pi) erf(R/(sigma sqrt 2)))
+    on [-R, R] (zero outside)."""
+    w = np.asarray(omega, dtype=np.float64)
+    norm = sigma * math.sqrt(2.0 * math.pi) * math.erf(radius / (sigma * math.sqrt(2.0)))
+    per = np.exp(-0.5 * (w / sigma) ** 2) / norm
+    per = np.where(np.abs(w) <= radius, per, 0.0)
+    return np.prod(per, axis=-1)
+
+
+def weights(omega: np.ndarray, eps: float, sigma: float = 0.0, radius: float = 0.0) -> np.ndarray:
+    """r_j = tau(w_j) / p(w_j)  (Sec. 2.4: nu_j^2)."""
+    sigma = sigma or default_sigma(eps)
+    radius = radius or default_radius(eps)
+    return tau(omega, eps) / density(omega, sigma, radius)
+
+
+# ---------------------------------------------------------------------------
+# Step a2: feature map and low-rank factors A, B   (Sec. 2.4, App. A.4)
+# ---------------------------------------------------------------------------
+def features(points: np.ndarray, omega: np.ndarray) -> np.ndarray:
+    """Phi = [cos(2 pi X w^T) | sin(2 pi X w^T)], N x m (real part, App. A.4)."""
+    X = np.asarray(points, dtype=np.float64)
+    ang = 2.0 * np.pi * (X @ np.asarray(omega, dtype=np.float64).T)
+    return np.concatenate([np.cos(ang), np.sin(ang)], axis=1)
+
+
+def column_scales(r: np.ndarray, m: int) -> tuple[np.ndarray, np.ndarray]:
+    """(Omega_a, Omega_b) diagonals: s sgn(r) and s with s = sqrt(2|r|/m),
+    each r_j used for its cos and its sin column."""
+    s = np.sqrt(2.0 * np.abs(r) / m)
+    sa = s * np.sign(r)
+    return np.concatenate([sa, sa]), np.concatenate([s, s])
+
+
+def factors(points: np.ndarray, omega: np.ndarray, r: np.ndarray):
+    """A = Phi Omega_a, B = Phi Omega_b with A B^T = W_hat (Sec. 2.4)."""
+    m = 2 * omega.shape[0]
+    Phi = features(points, omega)
+    oa, ob = column_scales(r, m)
+    return Phi * oa[None, :], Phi * ob[None, :]
+
+
+# ---------------------------------------------------------------------------
+# Step a4: G = lambda phi1(lambda M) = [exp(lambda M) - I] M^{-1}
+# ---------------------------------------------------------------------------
+def phi1(X: np.ndarray) -> np.ndarray:
+    """phi1(X) = sum_k X^k/(k+1)!, read off the top-right block of
+    exp([[X, I], [0, 0]]) = [[e^X, phi1(X)], [0, I]].  SciPy's expm is the
+    Al-Mohy--Higham scaling-and-squaring Pade method."""
+    X = np.asarray(X, dtype=np.float64)
+    k = X.shape[0]
+    aug = np.zeros((2 * k, 2 * k))
+    aug[:k, :k] = X
+    aug[:k, k:] = np.eye(k)
+    return scipy.linalg.expm(aug)[:k, k:]
+
+
+# ---------------------------------------------------------------------------
+# The whole estimator, steps a1..a6, in the paper's order
+# ---------------------------------------------------------------------------
+def rfd_gfi(points, F, eps, lam, m, seed, sigma=0.0, radius=0.0, *, return_parts=False):
+    """out = F + A (G (B^T F)),  G = lambda phi1(lambda B^T A)  (Sec. 2.4)."""
+    F64 = np.asarray(F, dtype=np.float64)
+    omega = sample_frequencies(m, eps, seed, sigma, radius)
+    r = weights(omega, eps, sigma, radius)
+    A, B = factors(points, omega, r)
+    M = B.T @ A                 # m x m   (pre-processing, Sec. 2.4)
+    Y = B.T @ F64               # m x c   (inference)
+    G = lam * phi1(lam * M)     # m x m   no inverse formed
+    out = F64 + A @ (G @ Y)
+    if return_parts:
+        return out, dict(omega=omega, r=r, A=A, B=B, M=M, Y=Y, G=G)
+    return out
+
+
+def rfd_gfi_from_plan(points, F, lam, omega, r):
+    """Same as rfd_gfi for frequencies/weights already drawn (resident plan)."""
+    A, B = factors(points, omega, r)
+    G = lam * phi1(lam * (B.T @ A))
+    F64 = np.asarray(F, dtype=np.float64)
+    return F64 + A @ (G @ (B.T @ F64))
+
+
+# ---------------------------------------------------------------------------
+# Brute-force references (small N only)
+# ---------------------------------------------------------------------------
+def dense_lowrank_gfi(A: np.ndarray, B: np.ndarray, F: np.ndarray, lam: float) -> np.ndarray:
+    """exp(lambda A B^T) F with A B^T formed densely (N x N) and exponentiated by
+    its symmetric eigendecomposition (LAPACK), no low-rank identity used."""
+    W = A @ B.T
+    W = 0.5 * (W + W.T)
+    e, V = np.linalg.eigh(W)
+    return V @ (np.exp(lam * e)[:, None] * (V.T @ np.asarray(F, dtype=np.float64)))
+
+
+def exact_adjacency(points: np.ndarray, eps: float) -> np.ndarray:
+    """W(i,j) = 1[||n_i - n_j||_inf <= eps] (Eq. w; diagonal f(0) = 1)."""
+    X = np.asarray(points, dtype=np.float64)
+    d = np.abs(X[:, None, :] - X[None, :, :]).max(axis=2)
+    return (d <= eps).astype(np.float64)
+
+
+def dense_exact_gfi(points, F, eps, lam) -> np.ndarray:
+    """exp(lambda W) F on the explicit eps-NN graph (the brute-force GFI of
+    Sec. 1: materialise the kernel matrix, then multiply)."""
+    W = exact_adjacency(points, eps)
+    e, V = np.linalg.eigh(W)
+    return V @ (np.exp(lam * e)[:, None] * (V.T @ np.asarray(F, dtype=np.float64)))
+
+
+def smoothed_kernel(z: np.ndarray, eps: float, radius: float) -> np.ndarray:
+    """E[W_hat(z)] = int_{[-R,R]^3} exp(2 pi i w^T z) tau(w) dw (App. A.4's f~)
+    in closed form: prod_d (1/pi)[Si(2 pi R (eps + z_d)) + Si(2 pi R (eps - z_d))]."""
+    z = np.asarray(z, dtype=np.float64)
+    si_p = scipy.special.sici(2.0 * np.pi * radius * (eps + z))[0]
+    si_m = scipy.special.sici(2.0 * np.pi * radius * (eps - z))[0]
+    return np.prod((si_p + si_m) / np.pi, axis=-1)
+
+
+def smoothed_adjacency(points: np.ndarray, eps: float, radius: float) -> np.ndarray:
+    """W~_R(i,j) = f~_R(n_i - n_j), the expectation of W_hat (dense, small N)."""
+    X = np.asarray(points, dtype=np.float64)
+    return smoothed_kernel(X[:, None, :] - X[None, :, :], eps, radius)
+
+
+def rel_frobenius(x: np.ndarray, ref: np.ndarray) -> float:
+    """||x - ref||_F / ||ref||_F, the error measure used for every comparison."""
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.linalg.norm(np.asarray(x, dtype=np.float64) - ref) / np.linalg.norm(ref))

@@ -1,0 +1,236 @@
+"""GB300-native RFDiffusion (RFD) graph-field integrator (arXiv 2302.00942, Sec. 2.4).
+
+Thin Python binding of the C ABI in include/rfd.h: argument marshalling only.
+Every step of the integrator runs in the CUDA kernels of librfd_gb300.so; this
+module never computes any of it.  Importing it loads the library and raises
+if it is missing (build it with ``python -m paper_2302_00942_gb300.build``):
+there is no CPU fallback.
+
+Device buffers are passed as torch CUDA tensors (PyTorch is used for device
+memory and streams only) or as raw integer device pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "RFD_OK", "RFD_EINVAL", "RFD_ENOMEM", "RFD_ECUDA", "RFD_ENOTREADY", "RFD_ETIMEDOUT", "RFD_ENUMERIC",
+    "RFD_EBUSY", "RFD_ENOTSUP", "RFD_FP32_PLAIN", "RFD_BF16_TC", "RfdError", "rfd_params", "rfd_stats",
+    "lib", "lib_path", "rfd_sample_frequencies", "rfd_plan", "rfd_plan_destroy", "rfd_features",
+    "rfd_integrate", "rfd_gfi", "rfd_phi1", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_last_error",
+    "rfd_version", "rfd_debug_fail_alloc_after", "Plan", "HEADER_SYMBOLS",
+]
+
+RFD_OK, RFD_EINVAL, RFD_ENOMEM, RFD_ECUDA, RFD_ENOTREADY, RFD_ETIMEDOUT, RFD_ENUMERIC, RFD_EBUSY, RFD_ENOTSUP = range(9)
+RFD_FP32_PLAIN, RFD_BF16_TC = 0, 1
+_STATUS = {0: "RFD_OK", 1: "RFD_EINVAL", 2: "RFD_ENOMEM", 3: "RFD_ECUDA", 4: "RFD_ENOTREADY",
+           5: "RFD_ETIMEDOUT", 6: "RFD_ENUMERIC", 7: "RFD_EBUSY", 8: "RFD_ENOTSUP"}
+
+lib_path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "librfd_gb300.so")
+
+
+class rfd_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int32), ("max_channels", ctypes.c_int32),
+                ("eps", ctypes.c_double), ("lambda_", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("precision", ctypes.c_int32), ("flags", ctypes.c_int32), ("freq_sigma", ctypes.c_double),
+                ("freq_radius", ctypes.c_double)]
+
+
+class rfd_stats(ctypes.Structure):
+    _fields_ = [("norm1", ctypes.c_double), ("pade_degree", ctypes.c_int32), ("squarings", ctypes.c_int32),
+                ("nonfinite", ctypes.c_int32), ("splits", ctypes.c_int32)]
+
+
+class RfdError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(lib_path):
+        raise ImportError(f"{lib_path} is missing: build it with `python -m paper_2302_00942_gb300.build` "
+                          "(this package has no CPU fallback)")
+    L = ctypes.CDLL(lib_path)
+    P, D, I32, I64, U64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    DP = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "rfd_sample_frequencies": (I32, [I32, D, U64, D, D, DP, DP]),
+        "rfd_plan": (I32, [ctypes.POINTER(rfd_params), P, ctypes.POINTER(P)]),
+        "rfd_plan_destroy": (I32, [P]),
+        "rfd_features": (I32, [P, P]),
+        "rfd_integrate": (I32, [P, P, I32, I64, P, I64]),
+        "rfd_gfi": (I32, [P, P, P, I32, I64, P, I64]),
+        "rfd_sync": (I32, [P]),
+        "rfd_phi1": (I32, [I32, D, P, P, P, ctypes.POINTER(rfd_stats)]),
+        "rfd_plan_export": (I32, [P, DP, DP, DP]),
+        "rfd_plan_stats": (I32, [P, ctypes.POINTER(rfd_stats)]),
+        "rfd_last_error": (ctypes.c_char_p, []),
+        "rfd_version": (ctypes.c_char_p, []),
+        "rfd_debug_fail_alloc_after": (None, [I32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype, fn.argtypes = res, args
+    return L
+
+
+lib = _load()
+
+# Every function include/rfd.h and include/rfd_testing.h declare (checked against the headers by a test).
+HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
+                  "rfd_gfi", "rfd_phi1", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_last_error", "rfd_version",
+                  "rfd_debug_fail_alloc_after")
+
+
+def rfd_last_error() -> str:
+    return lib.rfd_last_error().decode()
+
+
+def rfd_version() -> str:
+    return lib.rfd_version().decode()
+
+
+def _check(st: int, where: str) -> None:
+    if st != RFD_OK:
+        raise RfdError(st, where, rfd_last_error())
+
+
+def _dptr(x) -> int:
+    """Device pointer of a CUDA tensor (or an int pointer)."""
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return x.data_ptr()
+
+
+def rfd_sample_frequencies(m: int, eps: float, seed: int, freq_sigma: float = 0.0, freq_radius: float = 0.0):
+    """Step a1 on the host: (omega (m/2, 3) float64, r (m/2,) float64)."""
+    om = np.zeros((m // 2, 3), dtype=np.float64)
+    r = np.zeros(m // 2, dtype=np.float64)
+    _check(lib.rfd_sample_frequencies(m, eps, seed, freq_sigma, freq_radius,
+                                      om.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      r.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "rfd_sample_frequencies")
+    return om, r
+
+
+def rfd_plan(n, m, eps, lam, seed=0, max_channels=3, precision=RFD_BF16_TC, stream=None, freq_sigma=0.0,
+             freq_radius=0.0) -> int:
+    p = rfd_params(n=n, m=m, max_channels=max_channels, eps=eps, lambda_=lam, seed=seed, precision=precision,
+                   flags=0, freq_sigma=freq_sigma, freq_radius=freq_radius)
+    h = ctypes.c_void_p()
+    _check(lib.rfd_plan(ctypes.byref(p), stream, ctypes.byref(h)), "rfd_plan")
+    return h.value
+
+
+def rfd_plan_destroy(plan: int) -> None:
+    _check(lib.rfd_plan_destroy(plan), "rfd_plan_destroy")
+
+
+def rfd_features(plan: int, points) -> None:
+    _check(lib.rfd_features(plan, _dptr(points)), "rfd_features")
+
+
+def rfd_integrate(plan: int, F, c: int, ldF: int, out, ldOut: int) -> None:
+    _check(lib.rfd_integrate(plan, _dptr(F), c, ldF, _dptr(out), ldOut), "rfd_integrate")
+
+
+def rfd_gfi(plan: int, points, F, c: int, ldF: int, out, ldOut: int) -> None:
+    _check(lib.rfd_gfi(plan, _dptr(points), _dptr(F), c, ldF, _dptr(out), ldOut), "rfd_gfi")
+
+
+def rfd_sync(plan: int) -> None:
+    _check(lib.rfd_sync(plan), "rfd_sync")
+
+
+def rfd_phi1(m: int, lam: float, M, G, stream=None) -> dict:
+    """G = lam * phi1(lam * M) for float64 CUDA tensors M, G (m x m)."""
+    s = rfd_stats()
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(lib.rfd_phi1(m, lam, _dptr(M), _dptr(G), st, ctypes.byref(s)), "rfd_phi1")
+    return {k: getattr(s, k) for k, _ in rfd_stats._fields_}
+
+
+def rfd_plan_export(plan: int, m: int, with_G: bool = True):
+    om = np.zeros((m // 2, 3)), np.zeros(m // 2)
+    G = np.zeros((m, m)) if with_G else None
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib.rfd_plan_export(plan, om[0].ctypes.data_as(dp), om[1].ctypes.data_as(dp),
+                               G.ctypes.data_as(dp) if G is not None else None), "rfd_plan_export")
+    return om[0], om[1], G
+
+
+def rfd_plan_stats(plan: int) -> dict:
+    s = rfd_stats()
+    _check(lib.rfd_plan_stats(plan, ctypes.byref(s)), "rfd_plan_stats")
+    return {k: getattr(s, k) for k, _ in rfd_stats._fields_}
+
+
+def rfd_debug_fail_alloc_after(k: int) -> None:
+    lib.rfd_debug_fail_alloc_after(k)
+
+
+class Plan:
+    """Owning wrapper of an rfd_plan_t (one point cloud's integrator).
+
+    All tensors are torch CUDA float32, contiguous: points (N, 3), F and out (N, c).
+    """
+
+    def __init__(self, n, m, eps, lam, seed=0, max_channels=3, precision=RFD_BF16_TC, stream=None,
+                 freq_sigma=0.0, freq_radius=0.0):
+        self.n, self.m, self.max_channels = int(n), int(m), int(max_channels)
+        self.handle = None
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        self.handle = rfd_plan(n, m, eps, lam, seed, max_channels, precision, s, freq_sigma, freq_radius)
+
+    @staticmethod
+    def _chk(t, shape_last=None):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32):
+            raise TypeError("expected a float32 CUDA tensor")
+        if t.dim() != 2 or t.stride(1) != 1:
+            raise ValueError("expected a 2-D row-major tensor")
+        return t
+
+    def features(self, points):
+        self._chk(points)
+        rfd_features(self.handle, points)
+
+    def integrate(self, F, out=None):
+        import torch
+        self._chk(F)
+        out = torch.empty_like(F) if out is None else self._chk(out)
+        rfd_integrate(self.handle, F, F.shape[1], F.stride(0), out, out.stride(0))
+        return out
+
+    def gfi(self, points, F, out=None):
+        import torch
+        self._chk(points)
+        self._chk(F)
+        out = torch.empty_like(F) if out is None else self._chk(out)
+        rfd_gfi(self.handle, points, F, F.shape[1], F.stride(0), out, out.stride(0))
+        return out
+
+    def sync(self):
+        rfd_sync(self.handle)
+
+    def export(self, with_G=True):
+        return rfd_plan_export(self.handle, self.m, with_G)
+
+    def stats(self):
+        return rfd_plan_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            rfd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,114 @@
+// Step a3, FP32 "plain" form: the reductions over N, K = Phi^T Phi (upper
+// tiles) and Y' = Phi^T F, on SIMT FP32 FMA (Sec. 2.4: M = B^T A, Y = B^T F;
+// the diagonal column scales are applied by the reduce kernel).
+//
+// Each CTA computes one split-K piece (GramUnit) of a 128 x 128 tile:
+//   C[f, g] = sum_{n in [k0, k1)} Psi[i0 + f][n] * Psi[j0 + g][n].
+// Psi is feature-major (n contiguous), so every row of a tile is a contiguous
+// run of points: 16-point slabs are read with float4 loads and transposed
+// into shared memory.
+//
+// Accuracy: per-thread FP32 accumulators are folded every 256 points into a
+// Kahan-compensated (sum, carry) pair, so the rounding error of a partial is
+// ~sqrt(16) ulps of the partial instead of growing with N; the split-K
+// partials are summed in a fixed order, compensated, by the reduce kernel.
+#include <cuda_runtime.h>
+#include "kernels.h"
+
+namespace rfd {
+
+namespace {
+
+constexpr int kT = kSimtTile;   // 128
+constexpr int kK = kSimtK;      // 16 points per slab
+constexpr int kThreads = 256;   // 16 x 16 threads, 8 x 8 outputs each
+constexpr int kFold = 16;       // slabs per Kahan fold (256 points)
+
+__global__ void __launch_bounds__(kThreads, 1)
+gram_simt_kernel(const float* __restrict__ psi, int64_t n_pad, const GramUnit* __restrict__ units,
+                 float* __restrict__ partials) {
+  const GramUnit u = units[blockIdx.x];
+  __shared__ __align__(16) float As[kK][kT + 4];
+  __shared__ __align__(16) float Bs[kK][kT + 4];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+
+  float acc[8][8], sum[8][8], carry[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { acc[i][j] = 0.f; sum[i][j] = 0.f; carry[i][j] = 0.f; }
+
+  // loader mapping: 128 rows x 4 float4 per slab and operand -> 2 float4 per thread
+  const int lrow = threadIdx.x >> 2;       // 0..63
+  const int lq = threadIdx.x & 3;          // which float4 of the 16-point slab
+  const float* arow0 = psi + (size_t)(u.i0 + lrow) * n_pad;
+  const float* arow1 = psi + (size_t)(u.i0 + lrow + 64) * n_pad;
+  const float* brow0 = psi + (size_t)(u.j0 + lrow) * n_pad;
+  const float* brow1 = psi + (size_t)(u.j0 + lrow + 64) * n_pad;
+  // The plan allocates Psi with whole 128-row blocks past every tile start, so
+  // these rows always exist; rows beyond a tile's valid range only feed
+  // output rows/columns that the reduce ignores.
+
+  int slab = 0;
+  for (int64_t k = u.k0; k < u.k1; k += kK, ++slab) {
+    const float4 va0 = *reinterpret_cast<const float4*>(arow0 + k + lq * 4);
+    const float4 va1 = *reinterpret_cast<const float4*>(arow1 + k + lq * 4);
+    const float4 vb0 = *reinterpret_cast<const float4*>(brow0 + k + lq * 4);
+    const float4 vb1 = *reinterpret_cast<const float4*>(brow1 + k + lq * 4);
+    __syncthreads();
+    As[lq * 4 + 0][lrow] = va0.x; As[lq * 4 + 1][lrow] = va0.y; As[lq * 4 + 2][lrow] = va0.z; As[lq * 4 + 3][lrow] = va0.w;
+    As[lq * 4 + 0][lrow + 64] = va1.x; As[lq * 4 + 1][lrow + 64] = va1.y; As[lq * 4 + 2][lrow + 64] = va1.z; As[lq * 4 + 3][lrow + 64] = va1.w;
+    Bs[lq * 4 + 0][lrow] = vb0.x; Bs[lq * 4 + 1][lrow] = vb0.y; Bs[lq * 4 + 2][lrow] = vb0.z; Bs[lq * 4 + 3][lrow] = vb0.w;
+    Bs[lq * 4 + 0][lrow + 64] = vb1.x; Bs[lq * 4 + 1][lrow + 64] = vb1.y; Bs[lq * 4 + 2][lrow + 64] = vb1.z; Bs[lq * 4 + 3][lrow + 64] = vb1.w;
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kK; ++kk) {
+      const float4 a_lo = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 a_hi = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
+      const float4 b_lo = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float4 b_hi = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+      const float a[8] = {a_lo.x, a_lo.y, a_lo.z, a_lo.w, a_hi.x, a_hi.y, a_hi.z, a_hi.w};
+      const float b[8] = {b_lo.x, b_lo.y, b_lo.z, b_lo.w, b_hi.x, b_hi.y, b_hi.z, b_hi.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if ((slab + 1) % kFold == 0) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float y = acc[i][j] - carry[i][j];
+          const float t = sum[i][j] + y;
+          carry[i][j] = (t - sum[i][j]) - y;
+          sum[i][j] = t;
+          acc[i][j] = 0.f;
+        }
+    }
+  }
+  float* out = partials + u.out;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = (i < 4) ? (ty * 4 + i) : (64 + ty * 4 + i - 4);
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float y = acc[i][j] - carry[i][j];
+      v[j] = sum[i][j] + y;
+    }
+    *reinterpret_cast<float4*>(out + (size_t)r * kT + tx * 4) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4*>(out + (size_t)r * kT + 64 + tx * 4) = make_float4(v[4], v[5], v[6], v[7]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gram_simt(const float* psi, int64_t n_pad, const GramUnit* units, int num_units,
+                             float* partials, cudaStream_t st) {
+  if (num_units <= 0) return cudaSuccess;
+  gram_simt_kernel<<<num_units, kThreads, 0, st>>>(psi, n_pad, units, partials);
+  return cudaGetLastError();
+}
+
+}  // namespace rfd

@@ -1,0 +1,112 @@
+// Step a1 of the RFD path on the host, in FP64 (Sec. 2.4): the random
+// frequencies w_j ~ P and the importance weights r_j = tau(w_j)/p(w_j).
+//
+// P is a per-coordinate Gaussian N(0, sigma^2) truncated to [-R, R] (the
+// "(truncated) Gaussian" of Sec. 2.4), sampled by rejection from the uniform
+// distribution on [-R, R] with acceptance probability exp(-(w/sigma)^2/2):
+// only +, *, / and one exp comparison per try, so two IEEE-754 implementations
+// of this stream agree bit for bit except when u2 falls within an ulp of the
+// acceptance threshold.
+//
+// tau is the Fourier transform of the L-infinity cube indicator
+// 1[||z||_inf <= eps] with the 2 pi convention of Sec. 2.4:
+// tau(w) = prod_d sin(2 pi eps w_d) / (pi w_d), 2 eps at w_d = 0.
+//
+// This file must be compiled without floating-point contraction
+// (-ffp-contract=off) so that R (2 u1 - 1) is two rounded operations.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include "rfd_internal.h"
+
+namespace rfd {
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// SplitMix64 (Steele, Lea, Flood 2014): a Weyl sequence with increment
+// 0x9E3779B97F4A7C15 followed by a 64-bit mixing finaliser.
+struct SplitMix64 {
+  uint64_t s;
+  explicit SplitMix64(uint64_t seed) : s(seed) {}
+  uint64_t next() {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  // 53 random bits centred in their cell: a double strictly inside (0, 1)
+  double uniform() { return (static_cast<double>(next() >> 11) + 0.5) * 0x1.0p-53; }
+};
+
+constexpr int kMaxTries = 1 << 20;
+constexpr double kPi = 3.14159265358979323846;
+
+double sinc_cube(double w, double eps) {  // one coordinate of tau
+  if (w == 0.0) return 2.0 * eps;
+  return std::sin(2.0 * kPi * eps * w) / (kPi * w);
+}
+
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+rfd_status fail(rfd_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+const char* last_error_cstr() { return g_last_error.c_str(); }
+
+double default_sigma(double eps) { return 1.0 / (2.0 * eps); }
+double default_radius(double eps) { return 1.0 / eps; }
+
+rfd_status sample_frequencies_host(int m, double eps, uint64_t seed, double sigma,
+                                   double radius, double* omega, double* r) {
+  if (m < 2 || (m & 1)) return fail(RFD_EINVAL, "m must be even and >= 2");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(RFD_EINVAL, "eps must be finite and > 0");
+  if (sigma == 0.0) sigma = default_sigma(eps);
+  if (radius == 0.0) radius = default_radius(eps);
+  if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(RFD_EINVAL, "freq_sigma must be > 0");
+  if (!(radius > 0.0) || !std::isfinite(radius)) return fail(RFD_EINVAL, "freq_radius must be > 0");
+  const int h = m / 2;
+  SplitMix64 rng(seed);
+  // density normaliser per coordinate: sigma sqrt(2 pi) erf(R / (sigma sqrt 2))
+  const double norm = sigma * std::sqrt(2.0 * kPi) * std::erf(radius / (sigma * std::sqrt(2.0)));
+  for (int j = 0; j < h; ++j) {
+    double w3[3];
+    for (int d = 0; d < 3; ++d) {
+      int t = 0;
+      for (; t < kMaxTries; ++t) {
+        const double u1 = rng.uniform();
+        const double u2 = rng.uniform();
+        const double w = radius * (2.0 * u1 - 1.0);
+        const double a = w / sigma;
+        if (u2 < std::exp(-0.5 * a * a)) {
+          w3[d] = w;
+          break;
+        }
+      }
+      if (t == kMaxTries)
+        return fail(RFD_EINVAL, "frequency sampler: acceptance rate too low (freq_radius >> freq_sigma)");
+    }
+    if (omega) std::memcpy(omega + 3 * j, w3, sizeof(w3));
+    if (r) {
+      double tau = 1.0, p = 1.0;
+      for (int d = 0; d < 3; ++d) {
+        tau *= sinc_cube(w3[d], eps);
+        const double a = w3[d] / sigma;
+        p *= std::exp(-0.5 * a * a) / norm;
+      }
+      r[j] = tau / p;
+    }
+  }
+  return RFD_OK;
+}
+
+}  // namespace rfd
+
+extern "C" rfd_status rfd_sample_frequencies(int32_t m, double eps, uint64_t seed, double freq_sigma,
+                                             double freq_radius, double* omega_out, double* r_out) {
+  return rfd::sample_frequencies_host(m, eps, seed, freq_sigma, freq_radius, omega_out, r_out);
+}

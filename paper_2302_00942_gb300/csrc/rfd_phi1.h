@@ -1,0 +1,25 @@
+// Step a4 entry point: G = lambda phi1(lambda M), FP64, on the device.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include "../../include/rfd.h"
+
+namespace rfd {
+
+struct Phi1Info {
+  double norm1;   // ||lambda M||_1
+  int degree;     // Pade degree q
+  int squarings;  // s
+  int nonfinite;
+};
+
+// FP64 doubles of workspace needed for an m x m problem.
+size_t phi1_workspace_doubles(int m);
+
+// d_M, d_G: m x m row-major FP64 device buffers.  work: phi1_workspace_doubles(m)
+// doubles; d_ipiv: m ints; d_info, d_flag: one int; d_scalar: one double.
+// Synchronises `st` (norm -> host; finiteness flag -> host).
+rfd_status phi1_fp64(int m, double lambda, const double* d_M, double* d_G, double* work, int* d_ipiv, int* d_info,
+                     double* d_scalar, int* d_flag, cudaStream_t st, Phi1Info* info);
+
+}  // namespace rfd

@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle.
+
+Tolerances (relative Frobenius error over the whole N x c output):
+  FP32 plain form   <= 1e-5
+  BF16 tensor-core  <= 1e-3
+Step a4 alone (FP64 on both sides): <= 1e-12.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2302_00942_gb300 as rfd  # noqa: E402
+
+TOL = {rfd.RFD_FP32_PLAIN: 1e-5, rfd.RFD_BF16_TC: 1e-3}
+PRECS = [rfd.RFD_FP32_PLAIN, rfd.RFD_BF16_TC]
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+def gpu_gfi(pts, F, eps, lam, m, seed, precision, *, api="gfi", max_channels=None, ld=None, inplace=False):
+    n, c = F.shape
+    ld = ld or c
+    Fp = np.zeros((n, ld), np.float32)
+    Fp[:, :c] = F
+    P, Ft = _cuda(pts), _cuda(Fp)
+    out = Ft if inplace else torch.full((n, ld), float("nan"), device=DEV)
+    plan = rfd.Plan(n, m, eps, lam, seed, max_channels=max_channels or c, precision=precision,
+                    stream=torch.cuda.current_stream(DEV))
+    try:
+        if api == "gfi":
+            rfd.rfd_gfi(plan.handle, P, Ft, c, ld, out, ld)
+        else:
+            plan.features(P)
+            rfd.rfd_integrate(plan.handle, Ft, c, ld, out, ld)
+        plan.sync()
+        stats = plan.stats()
+        om, r, G = plan.export()
+    finally:
+        plan.close()
+    res = out.cpu().numpy()
+    if ld > c and not inplace:
+        assert np.isnan(res[:, c:]).all(), "columns beyond c were written"
+    return res[:, :c], stats, (om, r, G)
+
+
+def small_case(name="small", c=None):
+    spec = synth.config_single(name, c)
+    pts, F = synth.make_cloud(spec)
+    lam = spec.lam * spec.m / spec.n
+    return spec, pts, F, lam
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_small_config_matches_oracle(prec):
+    spec, pts, F, lam = small_case()
+    ref, parts = oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, return_parts=True)
+    out, stats, (om, r, G) = gpu_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, prec)
+    err = oracle.rel_frobenius(out, ref)
+    print(f"precision {prec}: rel err {err:.3e}, inc {oracle.rel_frobenius(F, ref):.3e}, stats {stats}")
+    assert err <= TOL[prec]
+    np.testing.assert_array_equal(om, parts["omega"])
+    np.testing.assert_allclose(r, parts["r"], rtol=1e-13)
+    # G from the device-side M against the oracle's G: limited by the reductions' precision
+    gerr = oracle.rel_frobenius(G, parts["G"])
+    assert gerr <= (1e-5 if prec == rfd.RFD_FP32_PLAIN else 2e-2), gerr
+
+
+@pytest.mark.parametrize("m,norm,lam", [(1, 0.5, 1.0), (7, 0.01, 1.0), (64, 0.2, -1.0), (64, 0.9, 1.0),
+                                        (96, 2.0, 0.5), (200, 5.0, 1.0), (130, 40.0, -1.0), (64, 300.0, 1.0)])
+def test_phi1_matches_oracle(m, norm, lam):
+    rng = np.random.default_rng(m * 1000 + int(norm * 10))
+    M = rng.standard_normal((m, m))
+    M *= norm / (np.abs(lam) * np.abs(M).sum(0).max())
+    G = torch.zeros((m, m), dtype=torch.float64, device=DEV)
+    stats = rfd.rfd_phi1(m, lam, _cuda(M), G)
+    ref = lam * oracle.phi1(lam * M)
+    err = oracle.rel_frobenius(G.cpu().numpy(), ref)
+    print(m, norm, stats, err)
+    assert abs(stats["norm1"] - norm) <= 1e-9 * norm
+    assert err <= 1e-12 * max(1.0, norm)
+
+
+def test_phi1_singular_and_zero():
+    m = 48
+    rng = np.random.default_rng(5)
+    Bm = rng.standard_normal((m, 10))
+    M = Bm @ Bm.T * 0.05                      # rank 10
+    G = torch.zeros((m, m), dtype=torch.float64, device=DEV)
+    rfd.rfd_phi1(m, 0.7, _cuda(M), G)
+    assert oracle.rel_frobenius(G.cpu().numpy(), 0.7 * oracle.phi1(0.7 * M)) <= 1e-12
+    rfd.rfd_phi1(m, 0.0, _cuda(M), G)
+    assert not G.cpu().numpy().any()
+    rfd.rfd_phi1(m, 2.0, _cuda(np.zeros((m, m))), G)
+    np.testing.assert_array_equal(G.cpu().numpy(), 2.0 * np.eye(m))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,m,c,ld", [(1000, 66, 5, 7), (40, 64, 3, 3), (1, 8, 2, 2), (3001, 130, 1, 1),
+                                      (700, 2, 4, 4), (5000, 256, 64, 64)])
+def test_ragged_and_degenerate_shapes(prec, n, m, c, ld):
+    rng = synth.rng_for(11, 1, n)
+    pts = synth.unit_sphere(n, rng)
+    F = synth.gaussian_field(n, c, 11, n)
+    eps, seed = 0.1, 3
+    lam = 0.1 * m / max(n, m)
+    ref = oracle.rfd_gfi(pts, F, eps, lam, m, seed)
+    out, stats, _ = gpu_gfi(pts, F, eps, lam, m, seed, prec, ld=ld)
+    err = oracle.rel_frobenius(out, ref)
+    print(n, m, c, prec, err, stats)
+    assert err <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_lambda_zero_is_identity_bitwise(prec):
+    spec, pts, F, _ = small_case()
+    out, _, _ = gpu_gfi(pts, F, spec.eps, 0.0, spec.m, spec.seed, prec)
+    np.testing.assert_array_equal(out, F)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_negative_lambda(prec):
+    # W_hat is indefinite (r_j of both signs), so lambda < 0 amplifies through its
+    # negative eigenvalues exactly as lambda > 0 does through the positive ones.
+    spec, pts, F, lam = small_case()
+    ref = oracle.rfd_gfi(pts, F, spec.eps, -lam, spec.m, spec.seed)
+    out, _, _ = gpu_gfi(pts, F, spec.eps, -lam, spec.m, spec.seed, prec)
+    assert oracle.rel_frobenius(out, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_warm_path_equals_cold_and_inplace(prec):
+    spec, pts, F, lam = small_case()
+    cold, _, _ = gpu_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, prec)
+    warm, _, _ = gpu_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, prec, api="split", max_channels=8)
+    inpl, _, _ = gpu_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, prec, inplace=True)
+    ref = oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed)
+    assert oracle.rel_frobenius(warm, ref) <= TOL[prec]
+    np.testing.assert_array_equal(inpl, cold)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_resident_plan_reuse_new_fields(prec):
+    """One plan, resident Phi and G, several fields of different widths (Sec. 2.4 inference)."""
+    spec, pts, F, lam = small_case()
+    plan = rfd.Plan(spec.n, spec.m, spec.eps, lam, spec.seed, max_channels=32, precision=prec,
+                    stream=torch.cuda.current_stream(DEV))
+    try:
+        plan.features(_cuda(pts))
+        for k, c in enumerate((1, 32, 7)):
+            Fk = synth.gaussian_field(spec.n, c, 99, k)
+            out = plan.integrate(_cuda(Fk))
+            plan.sync()
+            ref = oracle.rfd_gfi(pts, Fk, spec.eps, lam, spec.m, spec.seed)
+            assert oracle.rel_frobenius(out.cpu().numpy(), ref) <= TOL[prec]
+    finally:
+        plan.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_torus_config(prec):
+    spec, pts, F, lam = small_case("torus")
+    ref = oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed)
+    out, stats, _ = gpu_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, prec)
+    err = oracle.rel_frobenius(out, ref)
+    print(f"torus N={spec.n} m={spec.m} c={spec.c} prec={prec} err={err:.3e} stats={stats}")
+    assert err <= TOL[prec]
+
+
+def test_invalid_arguments_and_alloc_failure():
+    spec, pts, F, lam = small_case()
+    plan = rfd.Plan(spec.n, spec.m, spec.eps, lam, spec.seed, max_channels=3, precision=rfd.RFD_BF16_TC)
+    try:
+        Ft = _cuda(F)
+        out = torch.empty_like(Ft)
+        with pytest.raises(rfd.RfdError) as e:
+            rfd.rfd_integrate(plan.handle, Ft, 3, 3, out, 3)   # before rfd_features
+        assert e.value.status == rfd.RFD_EINVAL
+        F4 = _cuda(np.zeros((spec.n, 4), np.float32))
+        with pytest.raises(rfd.RfdError) as e:
+            rfd.rfd_gfi(plan.handle, _cuda(pts), F4, 4, 4, F4, 4)  # c > max_channels
+        assert e.value.status == rfd.RFD_EINVAL
+        # the plan stays usable after failed calls
+        out = plan.gfi(_cuda(pts), Ft)
+        plan.sync()
+        assert oracle.rel_frobenius(out.cpu().numpy(), oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed)) <= 1e-3
+    finally:
+        plan.close()
+    for k in (0, 3, 9):
+        rfd.rfd_debug_fail_alloc_after(k)
+        with pytest.raises(rfd.RfdError) as e:
+            rfd.Plan(spec.n, spec.m, spec.eps, lam, spec.seed, max_channels=3)
+        assert e.value.status == rfd.RFD_ENOMEM
+    rfd.rfd_debug_fail_alloc_after(-1)
+    free0 = torch.cuda.mem_get_info()[0]
+    p = rfd.Plan(spec.n, spec.m, spec.eps, lam, spec.seed, max_channels=3)
+    p.close()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
