@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the RFD graph-field integration hot path on GB300.
+
+One step = one pass of the whole path (Sec. 2.4): features (a2), the
+reductions B^T A and B^T F over N (a3), G = lambda phi1(lambda M) in FP64 (a4),
+Z = diag(s sgn r) G Y (a5) and out = F + Phi Z (a6), through rfd_gfi on inputs
+already resident in HBM.  Default workload: N = 1,000,000 points on 8 random
+ellipsoid surfaces, eps = 0.02, m = 1024, c = 3 (BF16 tensor-core form).
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU FP64 oracle
+(the reference arm of this project) on a bounded sample of the same workload.
+
+Multi-GPU: the clouds are independent problems, so N ranks each integrate
+their own cloud (weak scaling, no collective on the data path); the timed
+region is bracketed by barriers and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (profiling recipe's table); a DFMA probe measured ~1.0
+MUFU_PER_SM_CLK = 16            # sin or cos results per SM per clock (SFU)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["large", "torus", "small"], default="large")
+    ap.add_argument("--channels", type=int, default=None, help="field channels (default: the workload's)")
+    ap.add_argument("--precision", choices=["bf16", "fp32"], default="bf16")
+    ap.add_argument("--fp32-steps", type=int, default=2, help="timed steps of the FP32 plain form (0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-sample", type=int, default=65536, help="points in the CPU-oracle sample")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="override the workload's point count (profiling runs)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (torchrun: one rank per GPU)
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Dist:
+    def __init__(self, backend):
+        import torch
+        import torch.distributed as dist
+        self.ws, self.rank, self.local = dist_env()
+        self.dist = dist if self.ws > 1 else None
+        if self.dist:
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend)
+        self.torch = torch
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.dist:
+            return x
+        t = self.torch.tensor([x], dtype=self.torch.float64,
+                              device="cuda" if self.dist.get_backend() == "nccl" else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"rfd_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.remove(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per step ("Roofline")
+# ---------------------------------------------------------------------------
+def work_model(n, m, c):
+    gram_flops = n * m * (m + 1) + 2 * n * m * c          # symmetric Phi^T Phi + Phi^T F
+    apply_flops = 2 * n * m * c
+    hbm_bytes = 12 * n * (1 + c)                           # points, F read twice, out
+    sincos = n * m                                         # feature values (cos + sin)
+    return dict(gram_flops=gram_flops, apply_flops=apply_flops, hbm_bytes=hbm_bytes, sincos=sincos)
+
+
+def phi1_flops(m, q, s):
+    """FP64 flops of the block-triangular Pade evaluation: its m x m x m GEMMs
+    (2 m^3 each: the even powers, X Sp, Higham's two grouped products for q = 13,
+    two per squaring but the last), the LU (2/3 m^3) and the two triangular
+    solves with m (s = 0) or 2m right-hand sides (2 m^2 per right-hand side)."""
+    if not q:
+        return 0.0
+    gemms = (3 if q == 13 else (q - 1) // 2) + (2 if q == 13 else 0) + 1 + (2 * s - 1 if s > 0 else 0)
+    nrhs = 2 * m if s > 0 else m
+    return gemms * 2.0 * m ** 3 + (2.0 / 3.0) * m ** 3 + 2.0 * m * m * nrhs
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def time_oracle(pts, F, eps, lam, m, seed, steps=1):
+    import oracle
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.rfd_gfi(pts, F, eps, lam, m, seed)
+    return (time.perf_counter() - t0) / steps
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def reference_arm(args, spec, pts, F, lam):
+    ns = min(args.cpu_sample, spec.n)
+    c = F.shape[1]
+    for _ in range(args.warmup if args.warmup < 2 else 1):
+        time_oracle(pts[:ns], F[:ns], spec.eps, lam, spec.m, spec.seed)
+    t = time_oracle(pts[:ns], F[:ns], spec.eps, lam, spec.m, spec.seed, steps=args.steps)
+    val = ns * c / t
+    unit = "points*ch/s"
+    cb = {"value": val, "unit": unit, "cores": cpu_cores(), "kind": "oracle",
+          "sample": f"first {ns} of {spec.n} points, m={spec.m}, c={c}, FP64 NumPy/SciPy, whole path per step"}
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: N={ns} (sample of {spec.n}) m={spec.m} c={c}"},
+            "cpu_baseline": cb, "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+METRIC = "RFD GFI points*ch/s at N=1M, m=1024 (BF16 tensor-core form; FP32 plain form alongside)"
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    spec = synth.config_single(args.workload, args.channels)
+    if args.n:
+        import dataclasses
+        spec = dataclasses.replace(spec, n=args.n)
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        pts, F = synth.make_cloud(spec)
+        lam = spec.lam * spec.m / spec.n
+        print(json.dumps(reference_arm(args, spec, pts, F, lam)))
+        return 0
+
+    import torch
+    import paper_2302_00942_gb300 as rfd
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    D = Dist("nccl")
+    # each rank integrates its own cloud (independent problems)
+    if ws > 1:
+        import dataclasses
+        spec = dataclasses.replace(spec, sub=rank)
+    pts, F = synth.make_cloud(spec)
+    n, c, m = spec.n, F.shape[1], spec.m
+    lam = spec.lam * m / n   # diffusion time in units of the estimator's mean eigenvalue N/m
+    stream = torch.cuda.current_stream(dev)
+    P = torch.from_numpy(pts).to(dev)
+    Ft = torch.from_numpy(F).to(dev)
+    out = torch.empty_like(Ft)
+    prec = rfd.RFD_BF16_TC if args.precision == "bf16" else rfd.RFD_FP32_PLAIN
+    plan = rfd.Plan(n, m, spec.eps, lam, spec.seed, max_channels=c, precision=prec, stream=stream, timing=True)
+
+    for _ in range(args.warmup):
+        plan.gfi(P, Ft, out)
+    plan.sync()
+    plan.stats_reset()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    D.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.gfi(P, Ft, out)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    D.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = D.max(ms)
+    st = plan.stats()
+    out_bf = out.clone()
+
+    # end to end: host buffers, H2D of the step's inputs and D2H of its result inside the timed region
+    Ph = torch.from_numpy(pts).pin_memory()
+    Fh = torch.from_numpy(F).pin_memory()
+    Oh = torch.empty_like(Fh).pin_memory()
+    Pd, Fd, Od = torch.empty_like(P), torch.empty_like(Ft), torch.empty_like(Ft)
+    D.barrier()
+    torch.cuda.synchronize(dev)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(args.e2e_steps):
+        Pd.copy_(Ph, non_blocking=True)
+        Fd.copy_(Fh, non_blocking=True)
+        rfd.rfd_gfi(plan.handle, Pd, Fd, c, c, Od, c)
+        Oh.copy_(Od, non_blocking=True)
+    a1.record(stream)
+    torch.cuda.synchronize(dev)
+    D.barrier()
+    e2e_ms = D.max(a0.elapsed_time(a1) / args.e2e_steps)
+    plan.close()
+
+    # FP32 plain form on the same inputs (the form the BF16 path must beat), and the BF16 form's
+    # deviation from it (the FP32 form matches the FP64 oracle to <= 1e-5 in the parity tests)
+    fp32 = None
+    if args.fp32_steps > 0 and prec == rfd.RFD_BF16_TC:
+        p32 = rfd.Plan(n, m, spec.eps, lam, spec.seed, max_channels=c, precision=rfd.RFD_FP32_PLAIN, stream=stream,
+                       timing=True)
+        o32 = torch.empty_like(Ft)
+        p32.gfi(P, Ft, o32)
+        p32.sync()
+        p32.stats_reset()
+        torch.cuda.synchronize(dev)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(args.fp32_steps):
+            p32.gfi(P, Ft, o32)
+        b1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms32 = D.max(b0.elapsed_time(b1) / args.fp32_steps)
+        st32 = p32.stats()
+        p32.close()
+        diff = float(torch.linalg.norm((out_bf - o32).double()) / torch.linalg.norm(o32.double()))
+        inc = float(torch.linalg.norm((o32 - Ft).double()) / torch.linalg.norm(Ft.double()))
+        fp32 = {"value": ws * n * c / (ms32 * 1e-3), "ms_per_step": ms32,
+                "step_ms": {k: round(v, 4) for k, v in st32["step_ms"].items()},
+                "bf16_rel_err_vs_fp32": diff, "relative_increment": inc}
+
+    peaks, peak_src = load_peaks()
+    wm = work_model(n, m, c)
+    steps = st["step_ms"]
+    dom = max(steps, key=steps.get)
+    pf = phi1_flops(m, st["pade_degree"], st["squarings"])
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mufu_peak = sms * MUFU_PER_SM_CLK * (clk["sm_mhz"] or 1900.0) * 1e6
+    step_roof = {
+        "gram": {"bound": "tensor", "achieved": wm["gram_flops"] / (steps["gram"] * 1e-3) / 1e12,
+                 "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s"},
+        "phi1": {"bound": "alu", "achieved": pf / (steps["phi1"] * 1e-3) / 1e12, "peak": FP64_NOMINAL_TFLOPS,
+                 "unit": "TFLOP/s"},
+        "features": {"bound": "alu", "achieved": wm["sincos"] / (steps["features"] * 1e-3) / 1e9,
+                     "peak": mufu_peak / 1e9, "unit": "Gsincos/s"},
+        "apply": {"bound": "hbm", "achieved": (4 * n * 2 * c + m * c * 4) / (steps["apply"] * 1e-3) / 1e9,
+                  "peak": peaks["hbm_gbs"], "unit": "GB/s"},
+    }
+    for v in step_roof.values():
+        v["frac"] = v["achieved"] / v["peak"]
+    roof = dict(step_roof.get(dom, step_roof["gram"]))
+    roof["kernel"] = dom
+    roof["traffic"] = None
+    roof["peak_source"] = peak_src if roof["bound"] in ("tensor", "hbm") else "recipe nominal"
+    # whole-path roofline: slower of HBM bytes at peak bandwidth and tensor flops at peak
+    t_roof = max(wm["hbm_bytes"] / (peaks["hbm_gbs"] * 1e9),
+                 (wm["gram_flops"] + wm["apply_flops"]) / (peaks["bf16_tflops_sustained"] * 1e12))
+
+    res = {
+        "metric": METRIC, "value": ws * n * c / (ms_max * 1e-3), "unit": "points*ch/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": f"{args.workload}: N={n} points ({spec.kind}), eps={spec.eps}, m={m}, c={c}, "
+                               f"lambda={spec.lam} x m/N = {lam:.4g}, seed={spec.seed}",
+                   "l2": "inputs > L2: the step rewrites and rereads the feature matrix "
+                         f"({(m + 16) * n * (2 if prec else 4) / 1e9:.2f} GB)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roof,
+        "path_roofline": {"t_roofline_ms": t_roof * 1e3, "frac_of_step": t_roof * 1e3 / ms_max,
+                          "bound": "tensor" if wm["gram_flops"] / peaks["bf16_tflops_sustained"] / 1e12 >
+                          wm["hbm_bytes"] / peaks["hbm_gbs"] / 1e9 else "hbm"},
+        "step_ms": {k: round(v, 4) for k, v in steps.items()},
+        "step_roofline": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                          for k, v in step_roof.items()},
+        "phi1": {"pade_degree": st["pade_degree"], "squarings": st["squarings"], "norm1": st["norm1"]},
+        "clocks": clk,
+        "e2e": {"value": ws * n * c / (e2e_ms * 1e-3), "unit": "points*ch/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(Ph.numel() * 4 + Fh.numel() * 4), "d2h_bytes_per_step": int(Oh.numel() * 4)},
+        "gpu_launches": int(st["kernel_launches"]),
+        "fp32_plain": fp32,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        ns = min(args.cpu_sample, n)
+        t = time_oracle(pts[:ns], F[:ns], spec.eps, lam, m, spec.seed)
+        res["cpu_baseline"] = {"value": ns * c / t, "unit": "points*ch/s", "cores": cpu_cores(), "kind": "oracle",
+                               "sample": f"first {ns} of {n} points, same m, c, eps, lambda; whole path, FP64"}
+    if rank == 0:
+        print(json.dumps(res))
+    D.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -75,20 +75,42 @@ typedef struct {
   double lambda;         /* diffusion parameter, any finite real; 0 => out == F   */
   uint64_t seed;         /* seed of the frequency stream                          */
   int32_t precision;     /* rfd_precision                                         */
-  int32_t flags;         /* reserved, must be 0                                   */
+  int32_t flags;         /* RFD_FLAG_* bits (0 = none)                            */
   double freq_sigma;     /* sigma of the truncated Gaussian (0 => 1/(2 eps))      */
   double freq_radius;    /* truncation half-width R (0 => 1/eps)                  */
 } rfd_params;
 
 typedef struct rfd_plan_s* rfd_plan_t;
 
-/* Step statistics of the last rfd_features / rfd_gfi call on a plan. */
+/* rfd_params.flags bits */
+#define RFD_FLAG_TIMING 1  /* record CUDA events around every step (see rfd_stats.step_ms) */
+
+/* Indices of rfd_stats.step_ms */
+enum {
+  RFD_STEP_FEATURES = 0,  /* a2: feature map                      */
+  RFD_STEP_FIELD = 1,     /* F^T rows of the feature matrix        */
+  RFD_STEP_GRAM = 2,      /* a3: reductions over N (GEMMs)         */
+  RFD_STEP_REDUCE = 3,    /* a3: split-K reduction and scaling     */
+  RFD_STEP_PHI1 = 4,      /* a4: G = lambda phi1(lambda M), FP64   */
+  RFD_STEP_SMALL = 5,     /* a5: Z = diag(s sgn r) G Y             */
+  RFD_STEP_APPLY = 6,     /* a6: out = F + Phi Z                   */
+  RFD_NUM_STEPS = 7
+};
+
+/* Statistics of a plan.  norm1 .. splits describe the last rfd_features /
+ * rfd_gfi call.  With RFD_FLAG_TIMING, step_ms holds the mean device time of
+ * each step (CUDA events on the plan's stream) over the `timed_calls` calls
+ * since the last rfd_plan_stats_reset; kernel_launches counts every kernel
+ * the plan launched since then.  rfd_plan_stats synchronises the stream. */
 typedef struct {
   double norm1;          /* ||lambda M||_1                                         */
   int32_t pade_degree;   /* diagonal Pade degree q used for exp of the augmented matrix */
   int32_t squarings;     /* scaling-and-squaring steps s                          */
   int32_t nonfinite;     /* 1 if G was not finite                                 */
-  int32_t splits;        /* split-K factor used by the reductions over N          */
+  int32_t splits;        /* split-K pieces per tile (mean) of the reductions over N */
+  double step_ms[RFD_NUM_STEPS];
+  int64_t timed_calls;
+  int64_t kernel_launches;
 } rfd_stats;
 
 /* ---------------------------------------------------------------------------
@@ -161,8 +183,11 @@ RFD_API rfd_status rfd_sync(rfd_plan_t plan);
  * if rfd_features has not run).  Synchronises the stream. */
 RFD_API rfd_status rfd_plan_export(rfd_plan_t plan, double* omega, double* r, double* G);
 
-/* Statistics of the last rfd_features / rfd_gfi (host struct). */
+/* Statistics of the plan (host struct; synchronises the plan's stream). */
 RFD_API rfd_status rfd_plan_stats(rfd_plan_t plan, rfd_stats* out);
+
+/* Zero the accumulated step timings and launch count of a plan. */
+RFD_API rfd_status rfd_plan_stats_reset(rfd_plan_t plan);
 
 /* Thread-local description of the last error on this thread ("" if none). */
 RFD_API const char* rfd_last_error(void);

@@ -20,8 +20,8 @@ __all__ = [
     "RFD_OK", "RFD_EINVAL", "RFD_ENOMEM", "RFD_ECUDA", "RFD_ENOTREADY", "RFD_ETIMEDOUT", "RFD_ENUMERIC",
     "RFD_EBUSY", "RFD_ENOTSUP", "RFD_FP32_PLAIN", "RFD_BF16_TC", "RfdError", "rfd_params", "rfd_stats",
     "lib", "lib_path", "rfd_sample_frequencies", "rfd_plan", "rfd_plan_destroy", "rfd_features",
-    "rfd_integrate", "rfd_gfi", "rfd_phi1", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_last_error",
-    "rfd_version", "rfd_debug_fail_alloc_after", "Plan", "HEADER_SYMBOLS",
+    "rfd_integrate", "rfd_gfi", "rfd_phi1", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
+    "rfd_version", "RFD_FLAG_TIMING", "STEP_NAMES", "rfd_debug_fail_alloc_after", "Plan", "HEADER_SYMBOLS",
 ]
 
 RFD_OK, RFD_EINVAL, RFD_ENOMEM, RFD_ECUDA, RFD_ENOTREADY, RFD_ETIMEDOUT, RFD_ENUMERIC, RFD_EBUSY, RFD_ENOTSUP = range(9)
@@ -39,9 +39,21 @@ class rfd_params(ctypes.Structure):
                 ("freq_radius", ctypes.c_double)]
 
 
+RFD_FLAG_TIMING = 1
+STEP_NAMES = ("features", "field", "gram", "reduce", "phi1", "small", "apply")
+
+
 class rfd_stats(ctypes.Structure):
     _fields_ = [("norm1", ctypes.c_double), ("pade_degree", ctypes.c_int32), ("squarings", ctypes.c_int32),
-                ("nonfinite", ctypes.c_int32), ("splits", ctypes.c_int32)]
+                ("nonfinite", ctypes.c_int32), ("splits", ctypes.c_int32),
+                ("step_ms", ctypes.c_double * len(STEP_NAMES)), ("timed_calls", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+def _stats_dict(s: "rfd_stats") -> dict:
+    d = {k: getattr(s, k) for k, _ in rfd_stats._fields_ if k != "step_ms"}
+    d["step_ms"] = dict(zip(STEP_NAMES, list(s.step_ms)))
+    return d
 
 
 class RfdError(RuntimeError):
@@ -68,6 +80,7 @@ def _load():
         "rfd_phi1": (I32, [I32, D, P, P, P, ctypes.POINTER(rfd_stats)]),
         "rfd_plan_export": (I32, [P, DP, DP, DP]),
         "rfd_plan_stats": (I32, [P, ctypes.POINTER(rfd_stats)]),
+        "rfd_plan_stats_reset": (I32, [P]),
         "rfd_last_error": (ctypes.c_char_p, []),
         "rfd_version": (ctypes.c_char_p, []),
         "rfd_debug_fail_alloc_after": (None, [I32]),
@@ -82,8 +95,8 @@ lib = _load()
 
 # Every function include/rfd.h and include/rfd_testing.h declare (checked against the headers by a test).
 HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
-                  "rfd_gfi", "rfd_phi1", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_last_error", "rfd_version",
-                  "rfd_debug_fail_alloc_after")
+                  "rfd_gfi", "rfd_phi1", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
+                  "rfd_version", "rfd_debug_fail_alloc_after")
 
 
 def rfd_last_error() -> str:
@@ -119,9 +132,9 @@ def rfd_sample_frequencies(m: int, eps: float, seed: int, freq_sigma: float = 0.
 
 
 def rfd_plan(n, m, eps, lam, seed=0, max_channels=3, precision=RFD_BF16_TC, stream=None, freq_sigma=0.0,
-             freq_radius=0.0) -> int:
+             freq_radius=0.0, flags=0) -> int:
     p = rfd_params(n=n, m=m, max_channels=max_channels, eps=eps, lambda_=lam, seed=seed, precision=precision,
-                   flags=0, freq_sigma=freq_sigma, freq_radius=freq_radius)
+                   flags=flags, freq_sigma=freq_sigma, freq_radius=freq_radius)
     h = ctypes.c_void_p()
     _check(lib.rfd_plan(ctypes.byref(p), stream, ctypes.byref(h)), "rfd_plan")
     return h.value
@@ -152,7 +165,7 @@ def rfd_phi1(m: int, lam: float, M, G, stream=None) -> dict:
     s = rfd_stats()
     st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
     _check(lib.rfd_phi1(m, lam, _dptr(M), _dptr(G), st, ctypes.byref(s)), "rfd_phi1")
-    return {k: getattr(s, k) for k, _ in rfd_stats._fields_}
+    return _stats_dict(s)
 
 
 def rfd_plan_export(plan: int, m: int, with_G: bool = True):
@@ -167,7 +180,11 @@ def rfd_plan_export(plan: int, m: int, with_G: bool = True):
 def rfd_plan_stats(plan: int) -> dict:
     s = rfd_stats()
     _check(lib.rfd_plan_stats(plan, ctypes.byref(s)), "rfd_plan_stats")
-    return {k: getattr(s, k) for k, _ in rfd_stats._fields_}
+    return _stats_dict(s)
+
+
+def rfd_plan_stats_reset(plan: int) -> None:
+    _check(lib.rfd_plan_stats_reset(plan), "rfd_plan_stats_reset")
 
 
 def rfd_debug_fail_alloc_after(k: int) -> None:
@@ -181,11 +198,12 @@ class Plan:
     """
 
     def __init__(self, n, m, eps, lam, seed=0, max_channels=3, precision=RFD_BF16_TC, stream=None,
-                 freq_sigma=0.0, freq_radius=0.0):
+                 freq_sigma=0.0, freq_radius=0.0, timing=False):
         self.n, self.m, self.max_channels = int(n), int(m), int(max_channels)
         self.handle = None
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
-        self.handle = rfd_plan(n, m, eps, lam, seed, max_channels, precision, s, freq_sigma, freq_radius)
+        self.handle = rfd_plan(n, m, eps, lam, seed, max_channels, precision, s, freq_sigma, freq_radius,
+                               RFD_FLAG_TIMING if timing else 0)
 
     @staticmethod
     def _chk(t, shape_last=None):
@@ -223,6 +241,9 @@ class Plan:
 
     def stats(self):
         return rfd_plan_stats(self.handle)
+
+    def stats_reset(self):
+        rfd_plan_stats_reset(self.handle)
 
     def close(self):
         if self.handle:

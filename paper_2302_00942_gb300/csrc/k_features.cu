@@ -175,7 +175,7 @@ cudaError_t launch_features(const float* pts, int64_t n, int64_t n_pad, const fl
   else
     features_f32_kernel<<<grid, kFeatThreads, 0, st>>>(pts, n, n_pad, omega_hi, omega_lo, h,
                                                        static_cast<float*>(psi));
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_fill_field_rows(const float* F, int64_t ldF, int c, int64_t n, int64_t n_pad, int cpad,
@@ -187,7 +187,7 @@ cudaError_t launch_fill_field_rows(const float* F, int64_t ldF, int c, int64_t n
                                                                   static_cast<__nv_bfloat16*>(rows));
   else
     fill_field_rows_kernel<float><<<grid, block, 0, st>>>(F, ldF, c, n, n_pad, cpad, static_cast<float*>(rows));
-  return cudaGetLastError();
+  return launched();
 }
 
 }  // namespace rfd

@@ -228,7 +228,7 @@ cudaError_t dgemm(int M, int N, int K, double alpha, const double* A, int lda, c
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid(blocks_for(N, kGT), blocks_for(M, kGT));
   dgemm_kernel<<<grid, kGThreads, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t dcombine(int m, int n, double* D, int ldd, double a0, const double* X0, double a1, const double* X1,
@@ -236,19 +236,19 @@ cudaError_t dcombine(int m, int n, double* D, int ldd, double a0, const double* 
                      cudaStream_t st) {
   dcombine_kernel<<<blocks_for((int64_t)m * n, 256), 256, 0, st>>>(m, n, D, ldd, a0, X0, a1, X1, a2, X2, a3, X3,
                                                                     diag, ldx);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t dnorm1(int m, const double* X, int ldx, double* out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
   dnorm1_kernel<<<blocks_for(m, 128), 128, 0, st>>>(m, X, ldx, reinterpret_cast<unsigned long long*>(out));
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t dfinite_check(int m, int n, const double* X, int ldx, int* flag, cudaStream_t st) {
   dfinite_kernel<<<blocks_for((int64_t)m * n, 256), 256, 0, st>>>(m, n, X, ldx, flag);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t dgetrf(int m, double* A, int lda, int* ipiv, double* /*work*/, int* info, cudaStream_t st) {
@@ -258,8 +258,10 @@ cudaError_t dgetrf(int m, double* A, int lda, int* ipiv, double* /*work*/, int* 
     const int nb = (m - k0 < kNB) ? (m - k0) : kNB;
     panel_kernel<<<1, kPanelThreads, 0, st>>>(m, A, lda, k0, nb, ipiv, info);
     swap_outside_kernel<<<blocks_for(m, 128), 128, 0, st>>>(m, A, lda, ipiv, k0, nb);
+    count_launch(2);
     const int rest = m - k0 - nb;
     if (rest > 0) {
+      count_launch(1);
       trsm_lower_unit_kernel<<<blocks_for(rest, 128), 128, 0, st>>>(A, lda, k0, nb, A, lda, k0 + nb, rest);
       e = dgemm(rest, rest, nb, -1.0, A + (size_t)(k0 + nb) * lda + k0, lda, A + (size_t)k0 * lda + k0 + nb, lda,
                 1.0, A + (size_t)(k0 + nb) * lda + k0 + nb, lda, st);
@@ -272,10 +274,12 @@ cudaError_t dgetrf(int m, double* A, int lda, int* ipiv, double* /*work*/, int* 
 cudaError_t dgetrs(int m, int nrhs, const double* LU, int lda, const int* ipiv, double* B, int ldb,
                    cudaStream_t st) {
   apply_pivots_kernel<<<blocks_for(nrhs, 128), 128, 0, st>>>(m, ipiv, B, ldb, nrhs);
+  count_launch(1);
   // forward: L y = P b  (unit lower), block by block
   for (int k0 = 0; k0 < m; k0 += kNB) {
     const int nb = (m - k0 < kNB) ? (m - k0) : kNB;
     trsm_lower_unit_kernel<<<blocks_for(nrhs, 128), 128, 0, st>>>(LU, lda, k0, nb, B, ldb, 0, nrhs);
+    count_launch(1);
     const int rest = m - k0 - nb;
     if (rest > 0) {
       cudaError_t e = dgemm(rest, nrhs, nb, -1.0, LU + (size_t)(k0 + nb) * lda + k0, lda, B + (size_t)k0 * ldb, ldb,
@@ -288,6 +292,7 @@ cudaError_t dgetrs(int m, int nrhs, const double* LU, int lda, const int* ipiv, 
   for (int k0 = last; k0 >= 0; k0 -= kNB) {
     const int nb = (m - k0 < kNB) ? (m - k0) : kNB;
     trsm_upper_kernel<<<blocks_for(nrhs, 128), 128, 0, st>>>(LU, lda, k0, nb, B, ldb, nrhs);
+    count_launch(1);
     if (k0 > 0) {
       cudaError_t e = dgemm(k0, nrhs, nb, -1.0, LU + k0, lda, B + (size_t)k0 * ldb, ldb, 1.0, B, ldb, st);
       if (e != cudaSuccess) return e;

@@ -108,7 +108,7 @@ cudaError_t launch_gram_simt(const float* psi, int64_t n_pad, const GramUnit* un
                              float* partials, cudaStream_t st) {
   if (num_units <= 0) return cudaSuccess;
   gram_simt_kernel<<<num_units, kThreads, 0, st>>>(psi, n_pad, units, partials);
-  return cudaGetLastError();
+  return launched();
 }
 
 }  // namespace rfd

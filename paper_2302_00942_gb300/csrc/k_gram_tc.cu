@@ -323,7 +323,7 @@ cudaError_t launch_gram_tc(const TcGramArgs& a, int grid, cudaStream_t st) {
   if (grid > a.num_units) grid = a.num_units;
   gram_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(ma, mb, mf, a.units, a.num_units, a.cpad, (int)a_rows,
                                                      (int)b_rows, a.partials, a.err);
-  return cudaGetLastError();
+  return launched();
 }
 
 }  // namespace rfd

@@ -109,7 +109,7 @@ cudaError_t apply_cg(const void* psi, bool bf16, int64_t n, int64_t n_pad, int m
   else
     apply_simt_kernel<CG, float><<<grid, 256, 0, st>>>(static_cast<const float*>(psi), n, n_pad, m, Z, c, F, ldF,
                                                        out, ldOut);
-  return cudaGetLastError();
+  return launched();
 }
 
 }  // namespace
@@ -120,13 +120,13 @@ cudaError_t launch_reduce(const GramTile* tiles, int num_tiles, const float* par
   if (num_tiles <= 0) return cudaSuccess;
   dim3 grid((unsigned)((tile_rows * tile_cols + 255) / 256), (unsigned)num_tiles);
   reduce_kernel<<<grid, 256, 0, st>>>(tiles, partials, slot_elems, oa, ob, m, c, M, Y, tile_cols);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_small_product(const double* G, const double* Y, const double* oa, int m, int c, float* Z,
                                  cudaStream_t st) {
   small_product_kernel<<<m, dim3(32, 8), 0, st>>>(G, Y, oa, m, c, Z);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_apply_simt(const void* psi, bool bf16, int64_t n, int64_t n_pad, int m, const float* Z, int c,

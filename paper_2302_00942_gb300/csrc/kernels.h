@@ -5,6 +5,15 @@
 
 namespace rfd {
 
+// Kernels launched by this thread (every launcher adds its count); the plan
+// reports the difference around its calls.
+extern thread_local long long t_kernel_launches;
+inline void count_launch(long long k = 1) { t_kernel_launches += k; }
+inline cudaError_t launched(long long k = 1) {
+  t_kernel_launches += k;
+  return cudaGetLastError();
+}
+
 // One output tile of the reductions over N (step a3).  Rows i0.. of the
 // feature matrix Psi form the M side (features f), rows j0.. the N side
 // (features g, or field channels when kind == kTileField).

@@ -14,6 +14,7 @@
 
 namespace rfd {
 const char* last_error_cstr();
+thread_local long long t_kernel_launches = 0;
 }
 
 using namespace rfd;
@@ -77,9 +78,74 @@ struct rfd_plan_s {
   bool have_G = false;
   rfd_stats stats{};
   std::vector<void*> allocs;
+  // step timing (RFD_FLAG_TIMING): a ring of per-call event sets, folded into
+  // the sums when the stream is synchronised by rfd_plan_stats
+  struct Slot {
+    cudaEvent_t ev[2 * RFD_NUM_STEPS];
+    bool used[RFD_NUM_STEPS];
+  };
+  bool timing = false;
+  std::vector<Slot> ring;
+  int ring_head = 0, ring_pending = 0;
+  Slot* cur = nullptr;
+  double step_sum[RFD_NUM_STEPS] = {};
+  long long timed_calls = 0;
+  long long launches = 0;
+  long long launch_mark = 0;
 };
 
 namespace {
+
+constexpr int kRing = 64;
+
+void fold_timings(rfd_plan_s* pl) {
+  if (!pl->timing || pl->ring_pending == 0) return;
+  cudaStreamSynchronize(pl->stream);
+  for (int k = pl->ring_pending; k > 0; --k) {
+    auto& s = pl->ring[(pl->ring_head - k + kRing) % kRing];
+    for (int i = 0; i < RFD_NUM_STEPS; ++i) {
+      if (!s.used[i]) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, s.ev[2 * i], s.ev[2 * i + 1]) == cudaSuccess) pl->step_sum[i] += ms;
+    }
+    ++pl->timed_calls;
+  }
+  pl->ring_pending = 0;
+}
+
+// Brackets one entry-point call: picks a timing slot and snapshots the launch counter.
+struct CallScope {
+  rfd_plan_s* pl;
+  explicit CallScope(rfd_plan_s* p) : pl(p) {
+    pl->launch_mark = t_kernel_launches;
+    if (!pl->timing) return;
+    if (pl->ring_pending == kRing) fold_timings(pl);
+    pl->cur = &pl->ring[pl->ring_head];
+    for (bool& u : pl->cur->used) u = false;
+  }
+  ~CallScope() {
+    pl->launches += t_kernel_launches - pl->launch_mark;
+    if (!pl->timing) return;
+    pl->cur = nullptr;
+    pl->ring_head = (pl->ring_head + 1) % kRing;
+    ++pl->ring_pending;
+  }
+};
+
+// Records CUDA events around one step of the path on the plan's stream.
+struct StepScope {
+  rfd_plan_s* pl;
+  int step;
+  StepScope(rfd_plan_s* p, int s) : pl(p), step(s) {
+    if (pl->cur) cudaEventRecord(pl->cur->ev[2 * step], pl->stream);
+  }
+  ~StepScope() {
+    if (pl->cur) {
+      cudaEventRecord(pl->cur->ev[2 * step + 1], pl->stream);
+      pl->cur->used[step] = true;
+    }
+  }
+};
 
 rfd_status cuda_fail(const char* what, cudaError_t e) {
   return fail(RFD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -208,12 +274,20 @@ rfd_status run_reductions(rfd_plan_s* pl, const TileSet& ts, int c) {
     a.num_units = (int)ts.units.size();
     a.partials = pl->d_part;
     a.err = pl->d_ints;
-    RFD_CUDA(launch_gram_tc(a, pl->sms, st));
+    {
+      StepScope t(pl, RFD_STEP_GRAM);
+      RFD_CUDA(launch_gram_tc(a, pl->sms, st));
+    }
+    StepScope t(pl, RFD_STEP_REDUCE);
     RFD_CUDA(launch_reduce(ts.d_tiles, (int)ts.tiles.size(), pl->d_part, pl->slot_elems, pl->d_oa, pl->d_ob, pl->m, c,
                            pl->d_M, pl->d_Y, kTcBM, kTcBNMax, st));
   } else {
-    RFD_CUDA(launch_gram_simt(static_cast<const float*>(pl->d_psi), pl->n_pad, ts.d_units, (int)ts.units.size(),
-                              pl->d_part, st));
+    {
+      StepScope t(pl, RFD_STEP_GRAM);
+      RFD_CUDA(launch_gram_simt(static_cast<const float*>(pl->d_psi), pl->n_pad, ts.d_units, (int)ts.units.size(),
+                                pl->d_part, st));
+    }
+    StepScope t(pl, RFD_STEP_REDUCE);
     RFD_CUDA(launch_reduce(ts.d_tiles, (int)ts.tiles.size(), pl->d_part, pl->slot_elems, pl->d_oa, pl->d_ob, pl->m, c,
                            pl->d_M, pl->d_Y, kSimtTile, kSimtTile, st));
   }
@@ -233,7 +307,9 @@ rfd_status check_device_error(rfd_plan_s* pl) {
 
 rfd_status run_phi1(rfd_plan_s* pl) {
   Phi1Info info{};
-  rfd_status s = phi1_fp64(pl->m, pl->p.lambda, pl->d_M, pl->d_G, pl->d_work, pl->d_ipiv, pl->d_ints + 1,
+  rfd_status s;
+  StepScope t(pl, RFD_STEP_PHI1);
+  s = phi1_fp64(pl->m, pl->p.lambda, pl->d_M, pl->d_G, pl->d_work, pl->d_ipiv, pl->d_ints + 1,
                            pl->d_scalar, pl->d_ints + 2, pl->stream, &info);
   pl->stats.norm1 = info.norm1;
   pl->stats.pade_degree = info.degree;
@@ -258,7 +334,11 @@ rfd_status check_field_args(rfd_plan_s* pl, const float* F, int c, int64_t ldF, 
 }
 
 rfd_status apply_step(rfd_plan_s* pl, const float* F, int c, int64_t ldF, float* out, int64_t ldOut) {
-  RFD_CUDA(launch_small_product(pl->d_G, pl->d_Y, pl->d_oa, pl->m, c, pl->d_Z, pl->stream));
+  {
+    StepScope t(pl, RFD_STEP_SMALL);
+    RFD_CUDA(launch_small_product(pl->d_G, pl->d_Y, pl->d_oa, pl->m, c, pl->d_Z, pl->stream));
+  }
+  StepScope t(pl, RFD_STEP_APPLY);
   RFD_CUDA(launch_apply_simt(pl->d_psi, pl->bf16, pl->n, pl->n_pad, pl->m, pl->d_Z, c, F, ldF, out, ldOut,
                              pl->stream));
   return RFD_OK;
@@ -280,7 +360,7 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
   if (p.max_channels < 1 || p.max_channels > kMaxChannels) return fail(RFD_EINVAL, "max_channels must be in [1, 256]");
   if (!std::isfinite(p.lambda)) return fail(RFD_EINVAL, "lambda must be finite");
   if (p.precision != RFD_FP32_PLAIN && p.precision != RFD_BF16_TC) return fail(RFD_EINVAL, "unknown precision");
-  if (p.flags != 0) return fail(RFD_EINVAL, "flags must be 0");
+  if (p.flags & ~RFD_FLAG_TIMING) return fail(RFD_EINVAL, "unknown bits in flags");
   if (p.n > (int64_t)1 << 31) return fail(RFD_EINVAL, "n must be < 2^31");
   auto* pl = new (std::nothrow) rfd_plan_s();
   if (!pl) return fail(RFD_ENOMEM, "host allocation failed");
@@ -292,6 +372,7 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
   pl->n_pad = round_up(p.n, 128);
   pl->cpad = (int)round_up(p.max_channels, 16);
   pl->bf16 = (p.precision == RFD_BF16_TC);
+  pl->timing = (p.flags & RFD_FLAG_TIMING) != 0;
   pl->omega.resize((size_t)pl->h * 3);
   pl->r.resize(pl->h);
   rfd_status st = rfd::sample_frequencies_host(p.m, p.eps, p.seed, p.freq_sigma, p.freq_radius, pl->omega.data(),
@@ -370,6 +451,20 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
     return bail(RFD_ECUDA);
   }
   pl->stats.splits = pl->both.units.empty() ? 0 : (int)(pl->both.units.size() / pl->both.tiles.size());
+  if (pl->timing) {
+    pl->ring.resize(kRing);
+    for (auto& s : pl->ring)
+      for (cudaEvent_t& e : s.ev) e = nullptr;
+    for (auto& s : pl->ring)
+      for (cudaEvent_t& e : s.ev)
+        if ((ce = cudaEventCreate(&e)) != cudaSuccess) {
+          for (auto& s2 : pl->ring)
+            for (cudaEvent_t e2 : s2.ev)
+              if (e2) cudaEventDestroy(e2);
+          cuda_fail("event creation", ce);
+          return bail(RFD_ECUDA);
+        }
+  }
   *out = pl;
   return RFD_OK;
 }
@@ -377,19 +472,35 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
 rfd_status rfd_plan_destroy(rfd_plan_t plan) {
   if (!plan) return RFD_OK;
   cudaStreamSynchronize(plan->stream);
+  for (auto& s : plan->ring)
+    for (cudaEvent_t e : s.ev) cudaEventDestroy(e);
   plan_free(plan);
   delete plan;
   return RFD_OK;
 }
 
-rfd_status rfd_features(rfd_plan_t pl, const float* d_points) {
-  if (!pl || !d_points) return fail(RFD_EINVAL, "null plan or points");
-  pl->have_G = false;
+static rfd_status features_step(rfd_plan_t pl, const float* d_points) {
+  StepScope t(pl, RFD_STEP_FEATURES);
   RFD_CUDA(launch_features(d_points, pl->n, pl->n_pad, pl->d_omega_hi, pl->d_omega_lo, pl->h, pl->bf16, pl->d_psi,
                            pl->stream));
-  rfd_status s = run_reductions(pl, pl->gram_only, 1);
-  if (s != RFD_OK) return s;
-  return run_phi1(pl);
+  return RFD_OK;
+}
+
+static rfd_status field_step(rfd_plan_t pl, const float* d_F, int c, int64_t ldF) {
+  StepScope t(pl, RFD_STEP_FIELD);
+  void* rows = static_cast<uint8_t*>(pl->d_psi) + (size_t)pl->m * pl->n_pad * (pl->bf16 ? 2 : 4);
+  RFD_CUDA(launch_fill_field_rows(d_F, ldF, c, pl->n, pl->n_pad, pl->cpad, pl->bf16, rows, pl->stream));
+  return RFD_OK;
+}
+
+rfd_status rfd_features(rfd_plan_t pl, const float* d_points) {
+  if (!pl || !d_points) return fail(RFD_EINVAL, "null plan or points");
+  CallScope call(pl);
+  pl->have_G = false;
+  rfd_status s = features_step(pl, d_points);
+  if (s == RFD_OK) s = run_reductions(pl, pl->gram_only, 1);
+  if (s == RFD_OK) s = run_phi1(pl);
+  return s;
 }
 
 rfd_status rfd_integrate(rfd_plan_t pl, const float* d_F, int32_t c, int64_t ldF, float* d_out, int64_t ldOut) {
@@ -397,11 +508,11 @@ rfd_status rfd_integrate(rfd_plan_t pl, const float* d_F, int32_t c, int64_t ldF
   rfd_status s = check_field_args(pl, d_F, c, ldF, d_out, ldOut);
   if (s != RFD_OK) return s;
   if (!pl->have_G) return fail(RFD_EINVAL, "rfd_features (or rfd_gfi) must run before rfd_integrate");
-  void* rows = static_cast<uint8_t*>(pl->d_psi) + (size_t)pl->m * pl->n_pad * (pl->bf16 ? 2 : 4);
-  RFD_CUDA(launch_fill_field_rows(d_F, ldF, c, pl->n, pl->n_pad, pl->cpad, pl->bf16, rows, pl->stream));
-  s = run_reductions(pl, pl->field_only, c);
-  if (s != RFD_OK) return s;
-  return apply_step(pl, d_F, c, ldF, d_out, ldOut);
+  CallScope call(pl);
+  s = field_step(pl, d_F, c, ldF);
+  if (s == RFD_OK) s = run_reductions(pl, pl->field_only, c);
+  if (s == RFD_OK) s = apply_step(pl, d_F, c, ldF, d_out, ldOut);
+  return s;
 }
 
 rfd_status rfd_gfi(rfd_plan_t pl, const float* d_points, const float* d_F, int32_t c, int64_t ldF, float* d_out,
@@ -409,16 +520,14 @@ rfd_status rfd_gfi(rfd_plan_t pl, const float* d_points, const float* d_F, int32
   if (!pl || !d_points) return fail(RFD_EINVAL, "null plan or points");
   rfd_status s = check_field_args(pl, d_F, c, ldF, d_out, ldOut);
   if (s != RFD_OK) return s;
+  CallScope call(pl);
   pl->have_G = false;
-  RFD_CUDA(launch_features(d_points, pl->n, pl->n_pad, pl->d_omega_hi, pl->d_omega_lo, pl->h, pl->bf16, pl->d_psi,
-                           pl->stream));
-  void* rows = static_cast<uint8_t*>(pl->d_psi) + (size_t)pl->m * pl->n_pad * (pl->bf16 ? 2 : 4);
-  RFD_CUDA(launch_fill_field_rows(d_F, ldF, c, pl->n, pl->n_pad, pl->cpad, pl->bf16, rows, pl->stream));
-  s = run_reductions(pl, pl->both, c);
-  if (s != RFD_OK) return s;
-  s = run_phi1(pl);
-  if (s != RFD_OK) return s;
-  return apply_step(pl, d_F, c, ldF, d_out, ldOut);
+  s = features_step(pl, d_points);
+  if (s == RFD_OK) s = field_step(pl, d_F, c, ldF);
+  if (s == RFD_OK) s = run_reductions(pl, pl->both, c);
+  if (s == RFD_OK) s = run_phi1(pl);
+  if (s == RFD_OK) s = apply_step(pl, d_F, c, ldF, d_out, ldOut);
+  return s;
 }
 
 rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double* d_G, void* cuda_stream,
@@ -475,7 +584,23 @@ rfd_status rfd_plan_export(rfd_plan_t pl, double* omega, double* r, double* G) {
 
 rfd_status rfd_plan_stats(rfd_plan_t pl, rfd_stats* out) {
   if (!pl || !out) return fail(RFD_EINVAL, "null plan or output");
+  RFD_CUDA(cudaStreamSynchronize(pl->stream));
+  fold_timings(pl);
   *out = pl->stats;
+  for (int i = 0; i < RFD_NUM_STEPS; ++i)
+    out->step_ms[i] = pl->timed_calls ? pl->step_sum[i] / (double)pl->timed_calls : 0.0;
+  out->timed_calls = pl->timed_calls;
+  out->kernel_launches = pl->launches;
+  return RFD_OK;
+}
+
+rfd_status rfd_plan_stats_reset(rfd_plan_t pl) {
+  if (!pl) return fail(RFD_EINVAL, "null plan");
+  RFD_CUDA(cudaStreamSynchronize(pl->stream));
+  fold_timings(pl);
+  for (double& v : pl->step_sum) v = 0.0;
+  pl->timed_calls = 0;
+  pl->launches = 0;
   return RFD_OK;
 }
 

@@ -16,6 +16,11 @@ struct Phi1Info {
 // FP64 doubles of workspace needed for an m x m problem.
 size_t phi1_workspace_doubles(int m);
 
+// Number of m x m x m GEMMs of the evaluation for degree q and s squarings
+// (besides them: one LU factorisation and a solve with m, or 2m when s > 0,
+// right-hand sides).
+int phi1_gemm_count(int q, int s);
+
 // d_M, d_G: m x m row-major FP64 device buffers.  work: phi1_workspace_doubles(m)
 // doubles; d_ipiv: m ints; d_info, d_flag: one int; d_scalar: one double.
 // Synchronises `st` (norm -> host; finiteness flag -> host).

