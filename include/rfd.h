@@ -83,7 +83,9 @@ typedef struct {
 typedef struct rfd_plan_s* rfd_plan_t;
 
 /* rfd_params.flags bits */
-#define RFD_FLAG_TIMING 1  /* record CUDA events around every step (see rfd_stats.step_ms) */
+#define RFD_FLAG_TIMING 1       /* record CUDA events around every step (see rfd_stats.step_ms) */
+#define RFD_FLAG_NATIVE_FP64 2  /* step a4 products in native FP64 instead of the FP64-accurate
+                                   Ozaki-split emulation on the BF16 tensor cores (the default) */
 
 /* Indices of rfd_stats.step_ms */
 enum {
@@ -108,6 +110,8 @@ typedef struct {
   int32_t squarings;     /* scaling-and-squaring steps s                          */
   int32_t nonfinite;     /* 1 if G was not finite                                 */
   int32_t splits;        /* split-K pieces per tile (mean) of the reductions over N */
+  int32_t phi1_emulated; /* 1: the m x m x m products of step a4 used the FP64-accurate tensor-core emulation */
+  int32_t phi1_gemms;    /* m x m x m products evaluated by step a4 (LU solve not included) */
   double step_ms[RFD_NUM_STEPS];
   int64_t timed_calls;
   int64_t kernel_launches;
@@ -167,12 +171,13 @@ RFD_API rfd_status rfd_gfi(rfd_plan_t plan, const float* d_points, const float* 
 /* Step a4 alone: G = lambda phi1(lambda M) for an m x m FP64 matrix M
  * (Sec. 2.4: [exp(lambda M) - I] M^{-1}, evaluated without the inverse),
  * by the same scaling-and-squaring Pade evaluation rfd_features uses.
- * d_M, d_G: m x m row-major float64 DEVICE buffers (may not alias);
+ * d_M, d_G: m x m row-major float64 DEVICE buffers (may not alias); flags:
+ * RFD_FLAG_NATIVE_FP64 or 0;
  * 1 <= m <= 4096.  Allocates (and frees) its own FP64 workspace, about
  * 24 m^2 doubles; synchronises `cuda_stream`.  stats_out (host, may be NULL)
  * receives ||lambda M||_1, the Pade degree and the squaring count.
  * RFD_ENUMERIC if G is not finite. */
-RFD_API rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double* d_G, void* cuda_stream,
+RFD_API rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double* d_G, int32_t flags, void* cuda_stream,
                             rfd_stats* stats_out);
 
 /* Wait for all of the plan's queued device work. */

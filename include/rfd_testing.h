@@ -19,6 +19,16 @@ extern "C" {
  * k < 0 disables the hook.  Process-wide, not thread-safe; tests only. */
 RFD_API void rfd_debug_fail_alloc_after(int32_t k);
 
+/* The FP64 GEMM building block of step a4 on its own:
+ * C = alpha A B + beta C for row-major float64 DEVICE buffers (A: M x K, lda;
+ * B: K x N, ldb; C: M x N, ldc).  method 0: native FP64 kernel; method 1: the
+ * FP64-accurate Ozaki-split emulation on the BF16 tensor cores (K <= 1024,
+ * sm_103 only, else RFD_ENOTSUP).  Allocates its workspace, synchronises
+ * `cuda_stream`, and returns RFD_ETIMEDOUT if a bounded device wait ran out. */
+RFD_API rfd_status rfd_debug_dgemm(int32_t method, int32_t M, int32_t N, int32_t K, double alpha, const double* A,
+                                   int32_t lda, const double* B, int32_t ldb, double beta, double* C, int32_t ldc,
+                                   void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,8 @@ __all__ = [
     "RFD_EBUSY", "RFD_ENOTSUP", "RFD_FP32_PLAIN", "RFD_BF16_TC", "RfdError", "rfd_params", "rfd_stats",
     "lib", "lib_path", "rfd_sample_frequencies", "rfd_plan", "rfd_plan_destroy", "rfd_features",
     "rfd_integrate", "rfd_gfi", "rfd_phi1", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
-    "rfd_version", "RFD_FLAG_TIMING", "STEP_NAMES", "rfd_debug_fail_alloc_after", "Plan", "HEADER_SYMBOLS",
+    "rfd_version", "RFD_FLAG_TIMING", "STEP_NAMES", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "Plan", "HEADER_SYMBOLS",
+    "RFD_FLAG_NATIVE_FP64",
 ]
 
 RFD_OK, RFD_EINVAL, RFD_ENOMEM, RFD_ECUDA, RFD_ENOTREADY, RFD_ETIMEDOUT, RFD_ENUMERIC, RFD_EBUSY, RFD_ENOTSUP = range(9)
@@ -40,13 +41,14 @@ class rfd_params(ctypes.Structure):
 
 
 RFD_FLAG_TIMING = 1
+RFD_FLAG_NATIVE_FP64 = 2
 STEP_NAMES = ("features", "field", "gram", "reduce", "phi1", "small", "apply")
 
 
 class rfd_stats(ctypes.Structure):
     _fields_ = [("norm1", ctypes.c_double), ("pade_degree", ctypes.c_int32), ("squarings", ctypes.c_int32),
-                ("nonfinite", ctypes.c_int32), ("splits", ctypes.c_int32),
-                ("step_ms", ctypes.c_double * len(STEP_NAMES)), ("timed_calls", ctypes.c_int64),
+                ("nonfinite", ctypes.c_int32), ("splits", ctypes.c_int32), ("phi1_emulated", ctypes.c_int32),
+                ("phi1_gemms", ctypes.c_int32), ("step_ms", ctypes.c_double * len(STEP_NAMES)), ("timed_calls", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64)]
 
 
@@ -77,13 +79,14 @@ def _load():
         "rfd_integrate": (I32, [P, P, I32, I64, P, I64]),
         "rfd_gfi": (I32, [P, P, P, I32, I64, P, I64]),
         "rfd_sync": (I32, [P]),
-        "rfd_phi1": (I32, [I32, D, P, P, P, ctypes.POINTER(rfd_stats)]),
+        "rfd_phi1": (I32, [I32, D, P, P, I32, P, ctypes.POINTER(rfd_stats)]),
         "rfd_plan_export": (I32, [P, DP, DP, DP]),
         "rfd_plan_stats": (I32, [P, ctypes.POINTER(rfd_stats)]),
         "rfd_plan_stats_reset": (I32, [P]),
         "rfd_last_error": (ctypes.c_char_p, []),
         "rfd_version": (ctypes.c_char_p, []),
         "rfd_debug_fail_alloc_after": (None, [I32]),
+        "rfd_debug_dgemm": (I32, [I32, I32, I32, I32, D, P, I32, P, I32, D, P, I32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -96,7 +99,7 @@ lib = _load()
 # Every function include/rfd.h and include/rfd_testing.h declare (checked against the headers by a test).
 HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
                   "rfd_gfi", "rfd_phi1", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
-                  "rfd_version", "rfd_debug_fail_alloc_after")
+                  "rfd_version", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm")
 
 
 def rfd_last_error() -> str:
@@ -160,11 +163,12 @@ def rfd_sync(plan: int) -> None:
     _check(lib.rfd_sync(plan), "rfd_sync")
 
 
-def rfd_phi1(m: int, lam: float, M, G, stream=None) -> dict:
+def rfd_phi1(m: int, lam: float, M, G, stream=None, native_fp64: bool = False) -> dict:
     """G = lam * phi1(lam * M) for float64 CUDA tensors M, G (m x m)."""
     s = rfd_stats()
     st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
-    _check(lib.rfd_phi1(m, lam, _dptr(M), _dptr(G), st, ctypes.byref(s)), "rfd_phi1")
+    flags = RFD_FLAG_NATIVE_FP64 if native_fp64 else 0
+    _check(lib.rfd_phi1(m, lam, _dptr(M), _dptr(G), flags, st, ctypes.byref(s)), "rfd_phi1")
     return _stats_dict(s)
 
 
@@ -191,6 +195,15 @@ def rfd_debug_fail_alloc_after(k: int) -> None:
     lib.rfd_debug_fail_alloc_after(k)
 
 
+def rfd_debug_dgemm(method: int, A, B, C, alpha=1.0, beta=0.0, stream=None) -> None:
+    """C = alpha A B + beta C on float64 CUDA tensors (method 0 native FP64, 1 emulated)."""
+    M, K = A.shape
+    N = B.shape[1]
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(lib.rfd_debug_dgemm(method, M, N, K, alpha, _dptr(A), A.stride(0), _dptr(B), B.stride(0), beta,
+                               _dptr(C), C.stride(0), st), "rfd_debug_dgemm")
+
+
 class Plan:
     """Owning wrapper of an rfd_plan_t (one point cloud's integrator).
 
@@ -198,12 +211,12 @@ class Plan:
     """
 
     def __init__(self, n, m, eps, lam, seed=0, max_channels=3, precision=RFD_BF16_TC, stream=None,
-                 freq_sigma=0.0, freq_radius=0.0, timing=False):
+                 freq_sigma=0.0, freq_radius=0.0, timing=False, native_fp64=False):
         self.n, self.m, self.max_channels = int(n), int(m), int(max_channels)
         self.handle = None
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
         self.handle = rfd_plan(n, m, eps, lam, seed, max_channels, precision, s, freq_sigma, freq_radius,
-                               RFD_FLAG_TIMING if timing else 0)
+                               (RFD_FLAG_TIMING if timing else 0) | (RFD_FLAG_NATIVE_FP64 if native_fp64 else 0))
 
     @staticmethod
     def _chk(t, shape_last=None):

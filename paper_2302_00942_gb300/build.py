@@ -23,7 +23,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librfd_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["k_features.cu", "k_gram_simt.cu", "k_gram_tc.cu", "k_reduce_apply.cu", "k_fp64.cu",
+CU_SOURCES = ["tc_common.cu", "k_features.cu", "k_gram_simt.cu", "k_gram_tc.cu", "k_reduce_apply.cu", "k_fp64.cu", "k_ozaki.cu",
               "rfd_phi1.cu", "rfd_api.cu"]
 CPP_SOURCES = ["rfd_host.cpp"]
 
@@ -56,7 +56,7 @@ def build(verbose: bool = False, jobs: int | None = None, extra_nvcc: list[str] 
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(HERE, "..", "include", "rfd.h"))
     cmds, objs = [], []
     for src in CU_SOURCES:

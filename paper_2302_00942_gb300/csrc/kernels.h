@@ -92,6 +92,12 @@ cudaError_t dcombine(int m, int n, double* D, int ldd, double a0, const double* 
                      double diag, int ldx, cudaStream_t st);
 cudaError_t dnorm1(int m, const double* X, int ldx, double* out, cudaStream_t st);  // max column abs-sum
 cudaError_t dfinite_check(int m, int n, const double* X, int ldx, int* flag, cudaStream_t st);
+// FP64-accurate C = alpha A B + beta C on the BF16 tensor cores (Ozaki
+// splitting, k_ozaki.cu); K <= 1024.  `work` holds ozaki_workspace_bytes(M, N, K).
+size_t ozaki_workspace_bytes(int M, int N, int K);
+bool ozaki_supported(int K);
+cudaError_t dgemm_ozaki(int M, int N, int K, double alpha, const double* A, int lda, const double* B, int ldb,
+                        double beta, double* C, int ldc, void* work, int* err, cudaStream_t st);
 // LU with partial pivoting (in place), then solve for nrhs right-hand sides
 cudaError_t dgetrf(int m, double* A, int lda, int* ipiv, double* work, int* info, cudaStream_t st);
 cudaError_t dgetrs(int m, int nrhs, const double* LU, int lda, const int* ipiv, double* B, int ldb,

@@ -309,8 +309,10 @@ rfd_status run_phi1(rfd_plan_s* pl) {
   Phi1Info info{};
   rfd_status s;
   StepScope t(pl, RFD_STEP_PHI1);
-  s = phi1_fp64(pl->m, pl->p.lambda, pl->d_M, pl->d_G, pl->d_work, pl->d_ipiv, pl->d_ints + 1,
-                           pl->d_scalar, pl->d_ints + 2, pl->stream, &info);
+  s = phi1_fp64(pl->m, pl->p.lambda, pl->d_M, pl->d_G, pl->d_work, pl->d_ipiv, pl->d_ints + 1, pl->d_scalar,
+                pl->d_ints + 2, pl->d_ints, (pl->p.flags & RFD_FLAG_NATIVE_FP64) == 0, pl->stream, &info);
+  pl->stats.phi1_emulated = info.emulated;
+  pl->stats.phi1_gemms = info.gemms;
   pl->stats.norm1 = info.norm1;
   pl->stats.pade_degree = info.degree;
   pl->stats.squarings = info.squarings;
@@ -360,7 +362,7 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
   if (p.max_channels < 1 || p.max_channels > kMaxChannels) return fail(RFD_EINVAL, "max_channels must be in [1, 256]");
   if (!std::isfinite(p.lambda)) return fail(RFD_EINVAL, "lambda must be finite");
   if (p.precision != RFD_FP32_PLAIN && p.precision != RFD_BF16_TC) return fail(RFD_EINVAL, "unknown precision");
-  if (p.flags & ~RFD_FLAG_TIMING) return fail(RFD_EINVAL, "unknown bits in flags");
+  if (p.flags & ~(RFD_FLAG_TIMING | RFD_FLAG_NATIVE_FP64)) return fail(RFD_EINVAL, "unknown bits in flags");
   if (p.n > (int64_t)1 << 31) return fail(RFD_EINVAL, "n must be < 2^31");
   auto* pl = new (std::nothrow) rfd_plan_s();
   if (!pl) return fail(RFD_ENOMEM, "host allocation failed");
@@ -530,7 +532,7 @@ rfd_status rfd_gfi(rfd_plan_t pl, const float* d_points, const float* d_F, int32
   return s;
 }
 
-rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double* d_G, void* cuda_stream,
+rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double* d_G, int32_t flags, void* cuda_stream,
                     rfd_stats* stats_out) {
   if (m < 1 || m > kMaxM) return fail(RFD_EINVAL, "m must be in [1, 4096]");
   if (!d_M || !d_G || d_M == d_G) return fail(RFD_EINVAL, "null or aliased M / G");
@@ -549,8 +551,12 @@ rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double* d_G, vo
     return s;
   }
   Phi1Info info{};
-  s = phi1_fp64(m, lambda, d_M, d_G, work, ipiv, ints + 1, scalar, ints + 2, st, &info);
+  s = phi1_fp64(m, lambda, d_M, d_G, work, ipiv, ints + 1, scalar, ints + 2, ints, (flags & RFD_FLAG_NATIVE_FP64) == 0,
+                st, &info);
   cudaStreamSynchronize(st);
+  int err = 0;
+  cudaMemcpy(&err, ints, sizeof(int), cudaMemcpyDeviceToHost);
+  if (s == RFD_OK && err) s = fail(RFD_ETIMEDOUT, "a device-side wait ran out in phi1 (code " + std::to_string(err) + ")");
   plan_free(&tmp);
   if (stats_out) {
     *stats_out = rfd_stats{};
@@ -558,6 +564,8 @@ rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double* d_G, vo
     stats_out->pade_degree = info.degree;
     stats_out->squarings = info.squarings;
     stats_out->nonfinite = info.nonfinite;
+    stats_out->phi1_emulated = info.emulated;
+    stats_out->phi1_gemms = info.gemms;
   }
   if (s == RFD_ECUDA) return fail(s, std::string("phi1: ") + cudaGetErrorString(cudaGetLastError()));
   if (s == RFD_ENUMERIC) return fail(s, "G is not finite");
@@ -607,5 +615,37 @@ rfd_status rfd_plan_stats_reset(rfd_plan_t pl) {
 // Test hook (host-side fault injection): the k-th device allocation from now
 // on fails with RFD_ENOMEM (k = 0: the next one); k < 0 disables.
 void rfd_debug_fail_alloc_after(int32_t k) { g_fail_alloc_after = k; }
+
+rfd_status rfd_debug_dgemm(int32_t method, int32_t M, int32_t N, int32_t K, double alpha, const double* A, int32_t lda,
+                           const double* B, int32_t ldb, double beta, double* C, int32_t ldc, void* cuda_stream) {
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C || lda < K || ldb < N || ldc < N)
+    return fail(RFD_EINVAL, "invalid GEMM arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (method == 0) {
+    RFD_CUDA(dgemm(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st));
+    RFD_CUDA(cudaStreamSynchronize(st));
+    return RFD_OK;
+  }
+  if (method != 1) return fail(RFD_EINVAL, "method must be 0 or 1");
+  if (!ozaki_supported(K)) return fail(RFD_ENOTSUP, "emulated FP64 GEMM needs K <= 1024 on sm_103");
+  rfd_plan_s tmp;
+  uint8_t* work = nullptr;
+  int* err = nullptr;
+  rfd_status s;
+  if ((s = plan_alloc(&tmp, &work, ozaki_workspace_bytes(M, N, K))) != RFD_OK ||
+      (s = plan_alloc(&tmp, &err, 1)) != RFD_OK) {
+    plan_free(&tmp);
+    return s;
+  }
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = dgemm_ozaki(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, work, err, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  int h_err = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost);
+  plan_free(&tmp);
+  if (e != cudaSuccess) return cuda_fail("emulated dgemm", e);
+  if (h_err) return fail(RFD_ETIMEDOUT, "a device-side wait ran out (code " + std::to_string(h_err) + ")");
+  return RFD_OK;
+}
 
 }  // extern "C"

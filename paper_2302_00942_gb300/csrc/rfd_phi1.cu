@@ -53,7 +53,7 @@ std::vector<double> pade_coeffs(int q) {
 
 }  // namespace
 
-size_t phi1_workspace_doubles(int m) { return (size_t)m * m * 18; }
+size_t phi1_workspace_doubles(int m) { return (size_t)m * m * 18 + (ozaki_workspace_bytes(m, m, m) + 7) / 8; }
 
 int phi1_gemm_count(int q, int s) {
   const int powers = (q == 13) ? 3 : (q - 1) / 2;  // X^2, X^4, ... up to X^{q-1} (X^6 for q = 13)
@@ -61,8 +61,19 @@ int phi1_gemm_count(int q, int s) {
 }
 
 rfd_status phi1_fp64(int m, double lambda, const double* d_M, double* d_G, double* work, int* d_ipiv, int* d_info,
-                     double* d_scalar, int* d_flag, cudaStream_t st, Phi1Info* info) {
+                     double* d_scalar, int* d_flag, int* d_err, bool emulated, cudaStream_t st, Phi1Info* info) {
   const size_t mm = (size_t)m * m;
+  void* oz_work = work + mm * 18;
+  const bool use_oz = emulated && ozaki_supported(m);
+  // the m x m x m products: FP64-accurate emulation on the tensor cores, or native FP64
+  auto mm3 = [&](double alpha, const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+                 cudaStream_t s_) {
+    ++info->gemms;
+    return use_oz ? dgemm_ozaki(m, m, m, alpha, A, lda, B, ldb, beta, C, ldc, oz_work, d_err, s_)
+                  : dgemm(m, m, m, alpha, A, lda, B, ldb, beta, C, ldc, s_);
+  };
+  *info = Phi1Info{};
+  info->emulated = use_oz ? 1 : 0;
   info->degree = 0;
   info->squarings = 0;
   info->norm1 = 0.0;
@@ -84,10 +95,9 @@ rfd_status phi1_fp64(int m, double lambda, const double* d_M, double* d_G, doubl
   double* Vp = work + 8 * mm;        // sum_{k even} b_k X^k
   double* LU = work + 9 * mm;
   double* RHS = work + 10 * mm;      // m x 2m: [E | F] (s > 0) or m x m: F (s = 0)
-  double* Ea = work + 12 * mm;
-  double* Fa = work + 13 * mm;
+  double* Ea = work + 12 * mm;       // squaring phase
+  double* Fsq = work + 13 * mm;
   double* Eb = work + 14 * mm;
-  double* Fb = work + 15 * mm;
 
   CK(dcombine(m, m, X, m, lambda, d_M, 0, nullptr, 0, nullptr, 0, nullptr, 0.0, m, st));
   CK(dnorm1(m, X, m, d_scalar, st));
@@ -103,16 +113,22 @@ rfd_status phi1_fp64(int m, double lambda, const double* d_M, double* d_G, doubl
     CK(dcombine(m, m, d_G, m, 0, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, lambda, m, st));
     return RFD_OK;
   }
-  int q = 13, s = 0;
+  // Degree and scaling.  Native path: Higham's cheapest degree (up to 13), LU
+  // solve.  Emulated path: degree <= 5, so that the denominator residual
+  // R = I - q_q(X) obeys ||R||_1 <= p_q(||X||_1) - 1 <= p_5(theta_5) - 1 < 0.14
+  // and q_q(X)^{-1} = prod_j (I + R^(2^j)) converges in five factors: the whole
+  // evaluation is then GEMMs, which the tensor-core emulation makes cheap.
+  const int top = use_oz ? 1 : 4;  // index of the largest admissible degree
+  int q = kDegrees[top], s = 0;
   bool chosen = false;
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < top; ++i)
     if (nrm <= kTheta[i]) {
       q = kDegrees[i];
       chosen = true;
       break;
     }
   if (!chosen) {
-    s = std::max(0, (int)std::ceil(std::log2(nrm / kTheta[4])));
+    s = std::max(0, (int)std::ceil(std::log2(nrm / kTheta[top])));
     if (s > 1000) {
       info->nonfinite = 1;
       return RFD_ENUMERIC;
@@ -125,20 +141,20 @@ rfd_status phi1_fp64(int m, double lambda, const double* d_M, double* d_G, doubl
 
   // even powers X^2, X^4, ... (X^6 at most for q = 13)
   const int kmax = (q == 13) ? 3 : (q - 1) / 2;
-  CK(dgemm(m, m, m, 1.0, X, m, X, m, 0.0, Xp[1], m, st));
-  if (kmax >= 2) CK(dgemm(m, m, m, 1.0, Xp[1], m, Xp[1], m, 0.0, Xp[2], m, st));
-  if (kmax >= 3) CK(dgemm(m, m, m, 1.0, Xp[2], m, Xp[1], m, 0.0, Xp[3], m, st));
-  if (kmax >= 4) CK(dgemm(m, m, m, 1.0, Xp[2], m, Xp[2], m, 0.0, Xp[4], m, st));
+  CK(mm3(1.0, X, m, X, m, 0.0, Xp[1], m, st));
+  if (kmax >= 2) CK(mm3(1.0, Xp[1], m, Xp[1], m, 0.0, Xp[2], m, st));
+  if (kmax >= 3) CK(mm3(1.0, Xp[2], m, Xp[1], m, 0.0, Xp[3], m, st));
+  if (kmax >= 4) CK(mm3(1.0, Xp[2], m, Xp[2], m, 0.0, Xp[4], m, st));
 
   if (q == 13) {
     // Sp = X^6 (b13 X^6 + b11 X^4 + b9 X^2) + b7 X^6 + b5 X^4 + b3 X^2 + b1 I
     CK(dcombine(m, m, T, m, b[13], Xp[3], b[11], Xp[2], b[9], Xp[1], 0, nullptr, 0.0, m, st));
     CK(dcombine(m, m, Sp, m, b[7], Xp[3], b[5], Xp[2], b[3], Xp[1], 0, nullptr, b[1], m, st));
-    CK(dgemm(m, m, m, 1.0, Xp[3], m, T, m, 1.0, Sp, m, st));
+    CK(mm3(1.0, Xp[3], m, T, m, 1.0, Sp, m, st));
     // Vp = X^6 (b12 X^6 + b10 X^4 + b8 X^2) + b6 X^6 + b4 X^4 + b2 X^2 + b0 I
     CK(dcombine(m, m, T, m, b[12], Xp[3], b[10], Xp[2], b[8], Xp[1], 0, nullptr, 0.0, m, st));
     CK(dcombine(m, m, Vp, m, b[6], Xp[3], b[4], Xp[2], b[2], Xp[1], 0, nullptr, b[0], m, st));
-    CK(dgemm(m, m, m, 1.0, Xp[3], m, T, m, 1.0, Vp, m, st));
+    CK(mm3(1.0, Xp[3], m, T, m, 1.0, Vp, m, st));
   } else {
     double so[4] = {0, 0, 0, 0}, se[4] = {0, 0, 0, 0};
     for (int k = 1; k <= kmax; ++k) {
@@ -149,34 +165,55 @@ rfd_status phi1_fp64(int m, double lambda, const double* d_M, double* d_G, doubl
     CK(dcombine(m, m, Sp, m, so[0], P(0), so[1], P(1), so[2], P(2), so[3], P(3), b[1], m, st));
     CK(dcombine(m, m, Vp, m, se[0], P(0), se[1], P(1), se[2], P(2), se[3], P(3), b[0], m, st));
   }
-  CK(dgemm(m, m, m, 1.0, X, m, Sp, m, 0.0, Up, m, st));
-  // (Vp - Up) [E | F] = [Vp + Up | 2 Sp]   (only F when there is no squaring)
-  CK(dcombine(m, m, LU, m, 1.0, Vp, -1.0, Up, 0, nullptr, 0, nullptr, 0.0, m, st));
-  const int nrhs = (s > 0) ? 2 * m : m;
-  double* Frhs = (s > 0) ? RHS + m : RHS;
-  if (s > 0) CK(dcombine(m, m, RHS, nrhs, 1.0, Vp, 1.0, Up, 0, nullptr, 0, nullptr, 0.0, m, st));
-  CK(dcombine(m, m, Frhs, nrhs, 2.0, Sp, 0, nullptr, 0, nullptr, 0, nullptr, 0.0, m, st));
-  CK(dgetrf(m, LU, m, d_ipiv, nullptr, d_info, st));
-  CK(dgetrs(m, nrhs, LU, m, d_ipiv, RHS, nrhs, st));
-  const double* F = Frhs;
-  int ldf = nrhs;
+  CK(mm3(1.0, X, m, Sp, m, 0.0, Up, m, st));
+  // F ~ phi1(X) from (Vp - Up) F = 2 Sp
+  double* F = RHS;
+  if (!use_oz) {
+    CK(dcombine(m, m, LU, m, 1.0, Vp, -1.0, Up, 0, nullptr, 0, nullptr, 0.0, m, st));
+    CK(dcombine(m, m, F, m, 2.0, Sp, 0, nullptr, 0, nullptr, 0, nullptr, 0.0, m, st));
+    CK(dgetrf(m, LU, m, d_ipiv, nullptr, d_info, st));
+    CK(dgetrs(m, m, LU, m, d_ipiv, F, m, st));
+    info->lu = 1;
+  } else {
+    // R = I - (Vp - Up);  F = (I + R^(2^(k-1))) ... (I + R^2)(I + R) 2 Sp
+    double rho = 0.0, xs = std::ldexp(nrm, -s), pw = 1.0;
+    for (int k = 1; k <= q; ++k) rho += b[k] * (pw *= xs);
+    int nfac = 1;
+    for (double r2 = rho; r2 / (1.0 - rho) > 0x1p-56 && nfac < 8; r2 *= r2) ++nfac;
+    double* Pa = T;
+    double* Pb = LU;
+    double* Fb = RHS + mm;
+    CK(dcombine(m, m, Pa, m, -1.0, Vp, 1.0, Up, 0, nullptr, 0, nullptr, 1.0, m, st));
+    CK(dcombine(m, m, F, m, 2.0, Sp, 0, nullptr, 0, nullptr, 0, nullptr, 0.0, m, st));
+    for (int j = 0; j < nfac; ++j) {
+      CK(cudaMemcpyAsync(Fb, F, mm * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      CK(mm3(1.0, Pa, m, F, m, 1.0, Fb, m, st));  // F <- F + R^(2^j) F
+      std::swap(F, Fb);
+      if (j + 1 < nfac) {
+        CK(mm3(1.0, Pa, m, Pa, m, 0.0, Pb, m, st));  // R^(2^(j+1))
+        std::swap(Pa, Pb);
+      }
+    }
+    info->solve_factors = nfac;
+  }
   if (s > 0) {
-    // squaring phase, ping-pong between (Ea, Fa) and (Eb, Fb)
-    CK(dcombine(m, m, Ea, m, 1.0, RHS, 0, nullptr, 0, nullptr, 0, nullptr, 0.0, nrhs, st));
-    CK(dcombine(m, m, Fa, m, 1.0, Frhs, 0, nullptr, 0, nullptr, 0, nullptr, 0.0, nrhs, st));
+    // squaring phase: E = I + X F (the Pade quantities satisfy it exactly:
+    // E - I = (Vp - Up)^{-1} 2 X Sp = X F), then F' = (E F + F)/2, E' = E E
+    double* Fa = F;
+    double* Fb = (F == RHS) ? Fsq : RHS;
+    CK(dcombine(m, m, Ea, m, 0, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, 1.0, m, st));
+    CK(mm3(1.0, X, m, Fa, m, 1.0, Ea, m, st));
     for (int i = 0; i < s; ++i) {
-      // F' = (E F + F)/2 ; E' = E E
       CK(dcombine(m, m, Fb, m, 0.5, Fa, 0, nullptr, 0, nullptr, 0, nullptr, 0.0, m, st));
-      CK(dgemm(m, m, m, 0.5, Ea, m, Fa, m, 1.0, Fb, m, st));
-      if (i + 1 < s) CK(dgemm(m, m, m, 1.0, Ea, m, Ea, m, 0.0, Eb, m, st));  // the last E is not needed
+      CK(mm3(0.5, Ea, m, Fa, m, 1.0, Fb, m, st));
+      if (i + 1 < s) CK(mm3(1.0, Ea, m, Ea, m, 0.0, Eb, m, st));  // the last E is not needed
       std::swap(Ea, Eb);
       std::swap(Fa, Fb);
     }
     F = Fa;
-    ldf = m;
   }
   // G = lambda phi1(X)
-  CK(dcombine(m, m, d_G, m, lambda, F, 0, nullptr, 0, nullptr, 0, nullptr, 0.0, ldf, st));
+  CK(dcombine(m, m, d_G, m, lambda, F, 0, nullptr, 0, nullptr, 0, nullptr, 0.0, m, st));
   CK(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
   CK(dfinite_check(m, m, d_G, m, d_flag, st));
   int flag = 0;

@@ -93,8 +93,9 @@ def test_null_handles_rejected():
     assert rfd.lib.rfd_plan_stats(None, None) == rfd.RFD_EINVAL
     assert rfd.lib.rfd_plan_stats_reset(None) == rfd.RFD_EINVAL
     assert rfd.lib.rfd_plan_destroy(None) == rfd.RFD_OK
-    assert rfd.lib.rfd_phi1(0, 1.0, None, None, None, None) == rfd.RFD_EINVAL
-    assert rfd.lib.rfd_phi1(4, 1.0, None, None, None, None) == rfd.RFD_EINVAL
+    assert rfd.lib.rfd_phi1(0, 1.0, None, None, 0, None, None) == rfd.RFD_EINVAL
+    assert rfd.lib.rfd_phi1(4, 1.0, None, None, 0, None, None) == rfd.RFD_EINVAL
+    assert rfd.lib.rfd_debug_dgemm(1, 0, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, None) == rfd.RFD_EINVAL
 
 
 def test_phi1_gemm_count_matches_bench_model():
