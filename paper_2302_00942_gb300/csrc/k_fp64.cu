@@ -82,13 +82,22 @@ __global__ void dcombine_kernel(int m, int n, double* D, int ldd, double a0, con
 
 // max over columns of the column abs-sum; non-negative doubles order like
 // their bit patterns, so an integer atomicMax on the bits is exact.
+// Block (32 columns x 32 row lanes): each thread sums every 32nd row of one
+// column (coalesced across x), the 32 partial sums are reduced in shared memory.
 __global__ void dnorm1_kernel(int m, const double* __restrict__ X, int ldx, unsigned long long* out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m) return;
+  __shared__ double part[32][33];
+  const int j = blockIdx.x * 32 + threadIdx.x;
   double s = 0.0;
-  for (int i = 0; i < m; ++i) s += fabs(X[(size_t)i * ldx + j]);
-  if (!(s == s)) s = __longlong_as_double(0x7FF0000000000000ll);  // NaN -> +inf
-  atomicMax(out, (unsigned long long)__double_as_longlong(s));
+  if (j < m)
+    for (int i = threadIdx.y; i < m; i += 32) s += fabs(X[(size_t)i * ldx + j]);
+  part[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && j < m) {
+    double t = 0.0;
+    for (int y = 0; y < 32; ++y) t += part[y][threadIdx.x];
+    if (!(t == t)) t = __longlong_as_double(0x7FF0000000000000ll);  // NaN -> +inf
+    atomicMax(out, (unsigned long long)__double_as_longlong(t));
+  }
 }
 
 __global__ void dfinite_kernel(int m, int n, const double* __restrict__ X, int ldx, int* flag) {
@@ -242,7 +251,7 @@ cudaError_t dcombine(int m, int n, double* D, int ldd, double a0, const double* 
 cudaError_t dnorm1(int m, const double* X, int ldx, double* out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
-  dnorm1_kernel<<<blocks_for(m, 128), 128, 0, st>>>(m, X, ldx, reinterpret_cast<unsigned long long*>(out));
+  dnorm1_kernel<<<blocks_for(m, 32), dim3(32, 32), 0, st>>>(m, X, ldx, reinterpret_cast<unsigned long long*>(out));
   return launched();
 }
 

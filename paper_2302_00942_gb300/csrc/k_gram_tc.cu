@@ -6,20 +6,20 @@
 //   Y'[f, c] = sum_n Psi[i0 + f][n] * Psi[m + c][n]      (Phi^T F)
 //
 // Psi (bf16, feature-major: n contiguous) makes both operands K-major.  Each
-// work unit is a 128 x N tile (N <= 256) over a point range; TMA brings
-// 128 x 64 (A) and N x 64 (B) slabs into shared memory with the 128-byte
-// swizzle, one elected thread issues tcgen05.mma (M = 128, K = 16 per
-// instruction, FP32 accumulators in TMEM), and four epilogue warps drain TMEM
-// with tcgen05.ld into the unit's FP32 partial tile.
+// CTA owns one tile -- 128 feature rows against up to 256 Gram rows and,
+// for one tile per row block, the cpad field rows -- and one "lane" of the
+// point axis: the 64-point blocks kb = lane, lane + L, lane + 2L, ...  All
+// lanes of all tiles run in one wave and walk the point axis together, so
+// every 64-point slab of Psi is fetched from HBM once and served from L2 to
+// every tile that needs it.  The field columns ride on the same A slab: a
+// second MMA (N = cpad) per k-step into TMEM columns 256.., so B^T F costs
+// no extra pass over Psi.
 //
-// Persistent CTAs (one per SM) walk the unit list round-robin.  Warp roles:
-//   warp 0      TMA producer (one lane)
-//   warp 1      TMEM allocator + MMA issuer (one lane)
-//   warps 2..5  epilogue (TMEM lane quarter = warp % 4)
-// Two 256-column TMEM accumulators let the epilogue of unit u overlap the
-// MMAs of unit u + 1.  Every mbarrier wait is bounded by a %globaltimer
-// limit; a wait that runs out records a code in *err and the CTA unwinds
-// (waiting, again bounded, for its own TMA copies) instead of hanging.
+// Warp roles: warp 0 TMA producer (one lane), warp 1 TMEM allocator + MMA
+// issuer (one lane), warps 2..5 epilogue (TMEM lane quarter = warp % 4).
+// Every mbarrier wait is bounded by a %globaltimer limit; a wait that runs
+// out records a code in *err and the CTA unwinds (waiting, again bounded, for
+// its own TMA copies) instead of hanging.
 #include <cuda_runtime.h>
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -31,20 +31,20 @@ namespace rfd {
 
 namespace {
 
-constexpr int kStages = 4;
-constexpr int kABytes = kTcBM * kTcBK * 2;          // 16 KB
-constexpr int kBBytesMax = kTcBNMax * kTcBK * 2;    // 32 KB
-constexpr int kStageBytes = kABytes + kBBytesMax;   // 48 KB
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int kThreads = 192;
-constexpr uint32_t kTmemCols = 512;                 // 2 accumulators x 256 columns
 using namespace tc;
 
+constexpr int kMaxStages = 8;
+constexpr int kABytes = kTcBM * kTcBK * 2;          // 16 KB
+constexpr int kBBytes = kTcBNMax * kTcBK * 2;       // 32 KB
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 512;                 // Gram part [0, 256), field part [256, 256 + cpad)
+constexpr int kSmemLimit = 232448;                  // opt-in shared memory per CTA on sm_103
+constexpr int kSmemExtra = 1024 + 256;              // alignment slack + barriers
+
 struct Smem {
-  uint64_t full[kStages];
-  uint64_t empty[kStages];
-  uint64_t acc_full[2];
-  uint64_t acc_empty[2];
+  uint64_t full[kMaxStages];
+  uint64_t empty[kMaxStages];
+  uint64_t acc_full;
   uint32_t tmem_base;
 };
 
@@ -52,25 +52,23 @@ __global__ void __launch_bounds__(kThreads, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap map_a,   // Phi rows, box 64 x 128
                const __grid_constant__ CUtensorMap map_b,   // Phi rows, box 64 x 256
                const __grid_constant__ CUtensorMap map_f,   // F rows,   box 64 x cpad
-               const GramUnit* __restrict__ units, int num_units, int cpad, int a_rows_box,
-               int b_rows_box, float* __restrict__ partials, int* err) {
+               const GramUnit* __restrict__ units, int kb_total, int cpad, int a_rows_box, int b_rows_box,
+               int stages, int stage_bytes, float* __restrict__ partials, int* err) {
   extern __shared__ uint8_t smem_raw[];
-  // stage buffers 1024-aligned (the 128-byte swizzle atom); bookkeeping after them
   const uint32_t raw_addr = smem_u32(smem_raw);
   const uint32_t base = (raw_addr + 1023u) & ~1023u;
-  uint8_t* base_ptr = smem_raw + (base - raw_addr);
-  Smem* sm = reinterpret_cast<Smem*>(base_ptr + kStages * kStageBytes);
+  Smem* sm = reinterpret_cast<Smem*>(smem_raw + (base - raw_addr) + stages * stage_bytes);
+  const GramUnit u = units[blockIdx.x];
+  const bool has_g = u.nj_mma > 0, has_f = u.has_f != 0;
+  const int count = (u.lane < kb_total) ? (kb_total - u.lane + u.nlanes - 1) / u.nlanes : 0;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(smem_u32(&sm->full[s]), 1);
       mbar_init(smem_u32(&sm->empty[s]), 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(smem_u32(&sm->acc_full[b]), 1);
-      mbar_init(smem_u32(&sm->acc_empty[b]), 4);  // one arrive per epilogue warp
-    }
+    mbar_init(smem_u32(&sm->acc_full), 1);
     fence_mbar_init();
   }
   if (warp == 1) tmem_alloc(smem_u32(&sm->tmem_base), kTmemCols);
@@ -78,95 +76,82 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_a,   // Phi rows, box 64 
   __syncthreads();
   fence_after();
   const uint32_t tmem = sm->tmem_base;
-  const int a_bytes = a_rows_box * kTcBK * 2;
+  const uint32_t tx_bytes =
+      a_rows_box * kTcBK * 2 + (has_g ? b_rows_box * kTcBK * 2 : 0) + (has_f ? cpad * kTcBK * 2 : 0);
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
-      uint32_t kb = 0;  // global k-block counter (stage ring position)
-      bool ok = true;
-      for (int ui = blockIdx.x; ui < num_units && ok; ui += gridDim.x) {
-        const GramUnit u = units[ui];
-        const bool field = (u.kind == kTileField);
-        const int b_bytes = (field ? cpad : b_rows_box) * kTcBK * 2;
-        for (int64_t k = u.k0; k < u.k1; k += kTcBK, ++kb) {
-          const int s = kb % kStages;
-          const uint32_t ph = (kb / kStages) & 1u;
-          if (!mbar_wait(smem_u32(&sm->empty[s]), ph ^ 1u, err, 1)) { ok = false; break; }
-          const uint32_t full = smem_u32(&sm->full[s]);
-          mbar_arrive_expect_tx(full, a_bytes + b_bytes);
-          const uint32_t sa = base + s * kStageBytes;
-          tma_load_2d(sa, &map_a, (int32_t)k, u.i0, full);
-          if (field)
-            tma_load_2d(sa + kABytes, &map_f, (int32_t)k, 0, full);  // the F map starts at Psi row m
-          else
-            tma_load_2d(sa + kABytes, &map_b, (int32_t)k, u.j0, full);
-        }
+      int i = 0;
+      for (; i < count; ++i) {
+        const int s = i % stages;
+        const uint32_t ph = (uint32_t)(i / stages) & 1u;
+        if (!mbar_wait(smem_u32(&sm->empty[s]), ph ^ 1u, err, 1)) break;
+        const uint32_t full = smem_u32(&sm->full[s]);
+        mbar_arrive_expect_tx(full, tx_bytes);
+        const uint32_t sa = base + s * stage_bytes;
+        const int32_t x = (u.lane + i * u.nlanes) * kTcBK;
+        tma_load_2d(sa, &map_a, x, u.i0, full);
+        if (has_g) tma_load_2d(sa + kABytes, &map_b, x, u.j0, full);
+        if (has_f) tma_load_2d(sa + kABytes + kBBytes, &map_f, x, 0, full);  // the F map starts at Psi row m
       }
       // drain: our copies into the last stages must land before the CTA exits
-      const uint32_t issued = kb;
-      for (uint32_t t = (issued > (uint32_t)kStages ? issued - kStages : 0); t < issued; ++t)
-        mbar_wait(smem_u32(&sm->full[t % kStages]), (t / kStages) & 1u, err, 2);
+      for (int t = (i > stages ? i - stages : 0); t < i; ++t)
+        mbar_wait(smem_u32(&sm->full[t % stages]), (uint32_t)(t / stages) & 1u, err, 2);
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && count > 0) {
       // ---------------- MMA issuer ----------------
-      uint32_t kb = 0;
-      int local = 0;
+      const uint32_t idesc_g = idesc_bf16(kTcBM, has_g ? u.nj_mma : 16);
+      const uint32_t idesc_f = idesc_bf16(kTcBM, cpad);
       bool ok = true;
-      for (int ui = blockIdx.x; ui < num_units && ok; ui += gridDim.x, ++local) {
-        const GramUnit u = units[ui];
-        const int buf = local & 1;
-        const uint32_t use = (uint32_t)(local >> 1);
-        if (!mbar_wait(smem_u32(&sm->acc_empty[buf]), (use & 1u) ^ 1u, err, 3)) { ok = false; break; }
-        fence_after();
-        const uint32_t d_tmem = tmem + (uint32_t)(buf * kTcBNMax);
-        const uint32_t idesc = idesc_bf16(kTcBM, u.nj_mma);
-        uint32_t accumulate = 0;
-        for (int64_t k = u.k0; k < u.k1; k += kTcBK, ++kb) {
-          const int s = kb % kStages;
-          const uint32_t ph = (kb / kStages) & 1u;
-          if (!mbar_wait(smem_u32(&sm->full[s]), ph, err, 4)) { ok = false; break; }
-          fence_after();
-          const uint32_t sa = base + s * kStageBytes;
-#pragma unroll
-          for (int kk = 0; kk < kTcBK / 16; ++kk) {
-            const uint64_t da = sdesc_sw128(sa + kk * 32);
-            const uint64_t db = sdesc_sw128(sa + kABytes + kk * 32);
-            mma_bf16(d_tmem, da, db, idesc, accumulate);
-            accumulate = 1;
-          }
-          mma_commit(smem_u32(&sm->empty[s]));  // frees the stage when these MMAs finish
+      for (int i = 0; i < count; ++i) {
+        const int s = i % stages;
+        const uint32_t ph = (uint32_t)(i / stages) & 1u;
+        if (!mbar_wait(smem_u32(&sm->full[s]), ph, err, 4)) {
+          ok = false;
+          break;
         }
-        if (!ok) break;
-        mma_commit(smem_u32(&sm->acc_full[buf]));  // accumulator ready for the epilogue
+        fence_after();
+        const uint32_t sa = base + s * stage_bytes;
+#pragma unroll
+        for (int kk = 0; kk < kTcBK / 16; ++kk) {
+          const uint64_t da = sdesc_sw128(sa + kk * 32);
+          const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+          if (has_g) mma_bf16(tmem, da, sdesc_sw128(sa + kABytes + kk * 32), idesc_g, acc);
+          if (has_f)
+            mma_bf16(tmem + (uint32_t)kTcBNMax, da, sdesc_sw128(sa + kABytes + kBBytes + kk * 32), idesc_f, acc);
+        }
+        mma_commit(smem_u32(&sm->empty[s]));  // frees the stage when these MMAs finish
       }
+      if (ok) mma_commit(smem_u32(&sm->acc_full));
     }
     __syncwarp();
   } else {
     // ---------------- epilogue (warps 2..5) ----------------
-    const int quarter = warp & 3;           // TMEM lanes 32*quarter .. +31
-    const int row = quarter * 32 + lane;    // tile row (feature f - i0)
-    int local = 0;
-    for (int ui = blockIdx.x; ui < num_units; ui += gridDim.x, ++local) {
-      const GramUnit u = units[ui];
-      const int buf = local & 1;
-      const uint32_t use = (uint32_t)(local >> 1);
-      if (!mbar_wait(smem_u32(&sm->acc_full[buf]), use & 1u, err, 5)) break;
-      fence_after();
-      float* out = partials + u.out + (size_t)row * kTcBNMax;
-      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * kTcBNMax);
-      for (int c0 = 0; c0 < u.nj_mma; c0 += 32) {
+    const int quarter = warp & 3;         // TMEM lanes 32*quarter .. +31
+    const int row = quarter * 32 + lane;  // tile row (feature f - i0)
+    float* out = partials + u.out + (size_t)row * kTcLd;
+    const bool ready = (count > 0) && mbar_wait(smem_u32(&sm->acc_full), 0u, err, 5);
+    if (ready) fence_after();
+    const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
+    auto drain = [&](int col0, int ncols) {
+      for (int c0 = 0; c0 < ncols; c0 += 32) {
         float v[32];
-        tmem_ld32(taddr + (uint32_t)c0, v);
+        if (ready) {
+          tmem_ld32(taddr + (uint32_t)(col0 + c0), v);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] = 0.f;  // no point blocks in this lane: a zero partial
+        }
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-          *reinterpret_cast<float4*>(out + c0 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          *reinterpret_cast<float4*>(out + col0 + c0 + 4 * q) =
+              make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&sm->acc_empty[buf]));
-    }
+    };
+    if (has_g) drain(0, u.nj_mma);
+    if (has_f) drain(kTcBNMax, cpad);
   }
   fence_before();
   __syncthreads();
@@ -174,34 +159,41 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_a,   // Phi rows, box 64 
   if (warp == 1) tmem_dealloc(tmem, kTmemCols);
 }
 
-bool make_map(CUtensorMap* map, const void* base, uint64_t n_pad, uint64_t rows, uint32_t box_rows) {
-  return make_map_bf16(map, base, n_pad, rows, n_pad, box_rows);
-}
-
 }  // namespace
 
 bool tc_gram_supported() { return tc::sm103_available(); }
 
+int tc_gram_stage_bytes(int cpad) { return (kABytes + kBBytes + cpad * kTcBK * 2 + 1023) / 1024 * 1024; }
+
 cudaError_t launch_gram_tc(const TcGramArgs& a, int grid, cudaStream_t st) {
+  (void)grid;
   if (a.num_units <= 0) return cudaSuccess;
   if (a.cpad < 16 || a.cpad > 256 || (a.cpad % 16) || (a.n_pad % kTcBK)) return cudaErrorInvalidValue;
   CUtensorMap ma, mb, mf;
   const uint32_t a_rows = (uint32_t)(a.m < kTcBM ? a.m : kTcBM);
   const uint32_t b_rows = (uint32_t)(a.m < kTcBNMax ? a.m : kTcBNMax);
   const auto* psi = static_cast<const uint16_t*>(a.psi);
-  if (!make_map(&ma, psi, (uint64_t)a.n_pad, (uint64_t)a.m, a_rows)) return cudaErrorInvalidValue;
-  if (!make_map(&mb, psi, (uint64_t)a.n_pad, (uint64_t)a.m, b_rows)) return cudaErrorInvalidValue;
-  if (!make_map(&mf, psi + (size_t)a.m * a.n_pad, (uint64_t)a.n_pad, (uint64_t)a.cpad, (uint32_t)a.cpad))
+  if (!make_map_bf16(&ma, psi, (uint64_t)a.n_pad, (uint64_t)a.m, (uint64_t)a.n_pad, a_rows))
     return cudaErrorInvalidValue;
+  if (!make_map_bf16(&mb, psi, (uint64_t)a.n_pad, (uint64_t)a.m, (uint64_t)a.n_pad, b_rows))
+    return cudaErrorInvalidValue;
+  if (!make_map_bf16(&mf, psi + (size_t)a.m * a.n_pad, (uint64_t)a.n_pad, (uint64_t)a.cpad, (uint64_t)a.n_pad,
+                     (uint32_t)a.cpad))
+    return cudaErrorInvalidValue;
+  const int stage_bytes = tc_gram_stage_bytes(a.cpad);
+  int stages = (kSmemLimit - kSmemExtra) / stage_bytes;
+  if (stages > kMaxStages) stages = kMaxStages;
+  if (stages < 2) return cudaErrorInvalidValue;
+  const int smem = stages * stage_bytes + kSmemExtra;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  if (grid > a.num_units) grid = a.num_units;
-  gram_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(ma, mb, mf, a.units, a.num_units, a.cpad, (int)a_rows,
-                                                     (int)b_rows, a.partials, a.err);
+  const int kb_total = (int)(a.n_pad / kTcBK);
+  gram_tc_kernel<<<a.num_units, kThreads, smem, st>>>(ma, mb, mf, a.units, kb_total, a.cpad, (int)a_rows,
+                                                      (int)b_rows, stages, stage_bytes, a.partials, a.err);
   return launched();
 }
 

@@ -53,27 +53,42 @@ constexpr int kMaxK = 1024;              // exactness bound of one FP32 accumula
 
 // Row-wise split of a row-major FP64 matrix X (rows x cols, ld) into kS BF16
 // slices [kS][rows_pad][cols_pad] (zero padded) and per-row exponents.
+//
+// Done on the bit pattern with integer operations (FP64 arithmetic is the
+// slow pipe on this GPU): with E the biased exponent of an entry, Emax the
+// largest in its row and mant its 53-bit significand, |a| = |x| 2^-e equals
+// mant 2^(E - Emax - 53) (e = Emax - 1022), so F = floor(|a| 2^56) =
+// mant << (E - Emax + 3) (or >> when negative) and the digits are the 7-bit
+// fields d_p = (F >> (56 - 7p)) & 127 with the entry's sign: exactly the
+// digits trunc(2^7 a), a <- 2^7 a - d_p produce.
 __global__ void split_rows_kernel(const double* __restrict__ X, int ld, int rows, int cols, int rows_pad,
                                   int cols_pad, __nv_bfloat16* __restrict__ slices, int* __restrict__ exps) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= rows_pad) return;
   const int i = warp;
-  double mx = 0.0;
+  int emax = 0;  // largest biased exponent in the row (0: all entries zero or subnormal)
   if (i < rows)
-    for (int k = lane; k < cols; k += 32) mx = fmax(mx, fabs(X[(size_t)i * ld + k]));
-  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): |X[i, :]| < 2^e
-  if (lane == 0) exps[i] = e;
+    for (int k = lane; k < cols; k += 32)
+      emax = max(emax, (int)((__double_as_longlong(X[(size_t)i * ld + k]) >> 52) & 0x7FF));
+  for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+  if (emax == 0) emax = 1;  // subnormal-only rows: scale as the smallest normal binade
+  if (lane == 0) exps[i] = emax - 1022;  // |X[i, :]| < 2^(emax - 1022)
   const size_t plane = (size_t)rows_pad * cols_pad;
   for (int k = lane; k < cols_pad; k += 32) {
-    double a = (i < rows && k < cols) ? ldexp(X[(size_t)i * ld + k], -e) : 0.0;
+    unsigned long long F = 0;
+    bool neg = false;
+    if (i < rows && k < cols) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(X[(size_t)i * ld + k]);
+      const int E = (int)((b >> 52) & 0x7FF);
+      const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
+      const int sh = (E ? E : 1) - emax + 3;
+      F = (sh >= 0) ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0ull);
+      neg = (b >> 63) != 0;
+    }
 #pragma unroll
-    for (int p = 0; p < kS; ++p) {
-      const double t = a * 128.0;
-      const double d = trunc(t);
-      a = t - d;
-      slices[p * plane + (size_t)i * cols_pad + k] = __float2bfloat16_rn((float)d);
+    for (int p = 1; p <= kS; ++p) {
+      const int d = (int)((F >> (56 - kBeta * p)) & 127ull);
+      slices[(p - 1) * plane + (size_t)i * cols_pad + k] = __int2bfloat16_rn(neg ? -d : d);
     }
   }
 }

@@ -21,7 +21,7 @@ __global__ void reduce_kernel(const GramTile* __restrict__ tiles, const float* _
   if (r >= t.ni || col >= t.nj) return;
   double s = 0.0;
   for (int u = 0; u < t.unit_count; ++u)
-    s += (double)partials[(int64_t)(t.unit_first + u) * slot_elems + (int64_t)r * t.ld + col];
+    s += (double)partials[(int64_t)(t.unit_first + u) * slot_elems + (int64_t)r * t.ld + t.col_off + col];
   const int f = t.i0 + r;
   if (t.kind == kTileGram) {
     const int g = t.j0 + col;

@@ -26,16 +26,23 @@ struct GramTile {
   int32_t unit_first;  // first partial slot of this tile (its split-K pieces use consecutive slots)
   int32_t unit_count;  // number of split-K pieces
   int32_t ld;          // row stride (floats) of this tile's partials
+  int32_t col_off;     // column of this tile's first entry within a partial row
+  int32_t pad_;
 };
 
-// One split-K piece: a tile over the point range [k0, k1).
+// One split-K piece of the reductions over N.
+//  SIMT form: a tile over the point range [k0, k1).
+//  Tensor-core form: one persistent CTA; a Gram part (rows i0.. x rows j0.., N = nj_mma,
+//  absent when nj_mma == 0) and/or a field part (rows i0.. x the cpad field rows,
+//  when has_f), accumulated over the 64-point blocks kb = lane, lane + nlanes, ...
 struct GramUnit {
   int32_t tile;
   int32_t kind;
-  int32_t i0, j0, nj_mma;  // nj_mma: N of the MMA (multiple of 16) for tensor-core units
-  int32_t pad_;
+  int32_t i0, j0, nj_mma;
+  int32_t has_f;
   int64_t k0, k1;
   int64_t out;             // float offset of this unit's partial tile
+  int32_t lane, nlanes;
 };
 
 // ---- step a2: features ---------------------------------------------------
@@ -51,10 +58,13 @@ constexpr int kSimtK = 16;
 cudaError_t launch_gram_simt(const float* psi, int64_t n_pad, const GramUnit* units, int num_units,
                              float* partials, cudaStream_t st);
 
-// BF16 tensor-core form (tcgen05 + TMA): 128 x (<=256) tiles, persistent CTAs.
+// BF16 tensor-core form (tcgen05 + TMA): one CTA per (tile, lane); a tile is
+// 128 rows x (<= 256 Gram columns + cpad field columns).  Partial rows have
+// kTcLd floats: Gram part at column 0, field part at column kTcBNMax.
 constexpr int kTcBM = 128;
 constexpr int kTcBNMax = 256;
 constexpr int kTcBK = 64;
+constexpr int kTcLd = 512;
 struct TcGramArgs {
   const void* psi;       // bf16 [rows][n_pad]
   int64_t n_pad;

@@ -222,29 +222,59 @@ void build_tiles(rfd_plan_s* pl, bool with_gram, bool with_field, TileSet& ts) {
   const int m = pl->m;
   std::vector<double> cost;
   if (pl->bf16) {
-    // 128 x 256 tiles on the upper triangle of Phi^T Phi, 128 x cpad field tiles
-    for (int i0 = 0; i0 < m && with_gram; i0 += kTcBM)
+    // Compute tiles: 128 feature rows x up to 256 Gram rows on the upper
+    // triangle of Phi^T Phi; the row block's field part (Phi^T F, cpad columns)
+    // rides on the tile whose Gram block holds the row block's diagonal (or on
+    // a field-only tile when there is no Gram work).  Each tile gets L lanes of
+    // the point axis, L = SMs / tiles, all CTAs in one wave (lockstep in kb).
+    struct CT { int i0, j0, ni, nj; bool f; };
+    std::vector<CT> ct;
+    for (int i0 = 0; i0 < m; i0 += kTcBM) {
+      const int ni = std::min(kTcBM, m - i0);
+      if (!with_gram) {
+        ct.push_back(CT{i0, -1, ni, 0, true});
+        continue;
+      }
       for (int j0 = 0; j0 < m; j0 += kTcBNMax) {
         const int nj = std::min(kTcBNMax, m - j0);
         if (j0 + nj - 1 < i0) continue;  // entirely below the diagonal
-        ts.tiles.push_back(GramTile{i0, j0, std::min(kTcBM, m - i0), nj, kTileGram, 0, 0, 0});
-        cost.push_back((double)std::max<int64_t>(round_up(nj, 16), 64));
+        ct.push_back(CT{i0, j0, ni, nj, with_field && j0 == (i0 / kTcBNMax) * kTcBNMax});
       }
-    for (int i0 = 0; i0 < m && with_field; i0 += kTcBM) {
-      ts.tiles.push_back(GramTile{i0, m, std::min(kTcBM, m - i0), pl->cpad, kTileField, 0, 0, 0});
-      cost.push_back((double)std::max(pl->cpad, 64));
     }
-    schedule(ts, pl->n_pad, kTcBK, 4 * pl->sms, cost, kTcBM, kTcBNMax);
+    const int64_t kb_total = pl->n_pad / kTcBK;
+    const int T = (int)ct.size();
+    const int L = (int)std::max<int64_t>(1, std::min<int64_t>(kb_total, pl->sms / std::max(T, 1)));
+    for (int t = 0; t < T; ++t) {
+      const CT& c = ct[t];
+      if (c.nj > 0)
+        ts.tiles.push_back(GramTile{c.i0, c.j0, c.ni, c.nj, kTileGram, t * L, L, kTcLd, 0, 0});
+      if (c.f) ts.tiles.push_back(GramTile{c.i0, m, c.ni, pl->cpad, kTileField, t * L, L, kTcLd, kTcBNMax, 0});
+      for (int l = 0; l < L; ++l) {
+        GramUnit u{};
+        u.tile = t;
+        u.kind = c.nj > 0 ? kTileGram : kTileField;
+        u.i0 = c.i0;
+        u.j0 = c.j0;
+        u.nj_mma = c.nj > 0 ? (int)round_up(c.nj, 16) : 0;
+        u.has_f = c.f ? 1 : 0;
+        u.lane = l;
+        u.nlanes = L;
+        u.out = (int64_t)(t * L + l) * kTcBM * kTcLd;
+        ts.units.push_back(u);
+      }
+    }
+    ts.slots = T * L;
   } else {
     for (int i0 = 0; i0 < m && with_gram; i0 += kSimtTile)
       for (int j0 = i0; j0 < m; j0 += kSimtTile) {
-        ts.tiles.push_back(GramTile{i0, j0, std::min(kSimtTile, m - i0), std::min(kSimtTile, m - j0), kTileGram, 0, 0, 0});
+        ts.tiles.push_back(
+            GramTile{i0, j0, std::min(kSimtTile, m - i0), std::min(kSimtTile, m - j0), kTileGram, 0, 0, 0, 0, 0});
         cost.push_back(1.0);
       }
     for (int i0 = 0; i0 < m && with_field; i0 += kSimtTile)
       for (int c0 = 0; c0 < pl->cpad; c0 += kSimtTile) {
-        ts.tiles.push_back(
-            GramTile{i0, m + c0, std::min(kSimtTile, m - i0), std::min(kSimtTile, pl->cpad - c0), kTileField, 0, 0, 0});
+        ts.tiles.push_back(GramTile{i0, m + c0, std::min(kSimtTile, m - i0), std::min(kSimtTile, pl->cpad - c0),
+                                    kTileField, 0, 0, 0, 0, 0});
         cost.push_back(1.0);
       }
     schedule(ts, pl->n_pad, kSimtK, 2 * pl->sms, cost, kSimtTile, kSimtTile);
@@ -281,7 +311,7 @@ rfd_status run_reductions(rfd_plan_s* pl, const TileSet& ts, int c) {
     StepScope t(pl, RFD_STEP_REDUCE);
     RFD_CUDA(launch_reduce(ts.d_tiles, (int)ts.tiles.size(), pl->d_part, pl->slot_elems, pl->d_oa, pl->d_ob, pl->m, c,
                            pl->d_M, pl->d_Y, kTcBM, kTcBNMax, st));
-  } else {
+  } else {  // (the tile columns above bound both parts: Gram nj <= 256, field cpad <= 256)
     {
       StepScope t(pl, RFD_STEP_GRAM);
       RFD_CUDA(launch_gram_simt(static_cast<const float*>(pl->d_psi), pl->n_pad, ts.d_units, (int)ts.units.size(),
@@ -413,7 +443,7 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
   build_tiles(pl, false, true, pl->field_only);
   build_tiles(pl, true, true, pl->both);
   const int slots = std::max({pl->gram_only.slots, pl->field_only.slots, pl->both.slots});
-  pl->slot_elems = pl->bf16 ? (int64_t)kTcBM * kTcBNMax : (int64_t)kSimtTile * kSimtTile;
+  pl->slot_elems = pl->bf16 ? (int64_t)kTcBM * kTcLd : (int64_t)kSimtTile * kSimtTile;
   pl->rows_alloc = (int)std::max<int64_t>(round_up(p.m, 128), p.m + round_up(pl->cpad, 128));
   const size_t esz = pl->bf16 ? 2 : 4;
   // device buffers

@@ -178,8 +178,9 @@ rfd_status phi1_fp64(int m, double lambda, const double* d_M, double* d_G, doubl
     // R = I - (Vp - Up);  F = (I + R^(2^(k-1))) ... (I + R^2)(I + R) 2 Sp
     double rho = 0.0, xs = std::ldexp(nrm, -s), pw = 1.0;
     for (int k = 1; k <= q; ++k) rho += b[k] * (pw *= xs);
+    // after nfac factors the error is R^(2^nfac) (I - R)^{-1}: stop once rho^(2^nfac)/(1 - rho) <= 2^-56
     int nfac = 1;
-    for (double r2 = rho; r2 / (1.0 - rho) > 0x1p-56 && nfac < 8; r2 *= r2) ++nfac;
+    for (double r2 = rho * rho; r2 / (1.0 - rho) > 0x1p-56 && nfac < 8; r2 *= r2) ++nfac;
     double* Pa = T;
     double* Pb = LU;
     double* Fb = RHS + mm;
