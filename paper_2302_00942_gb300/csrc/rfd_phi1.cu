@@ -64,7 +64,7 @@ rfd_status phi1_fp64(int m, double lambda, const double* d_M, double* d_G, doubl
                      double* d_scalar, int* d_flag, int* d_err, bool emulated, cudaStream_t st, Phi1Info* info) {
   const size_t mm = (size_t)m * m;
   void* oz_work = work + mm * 18;
-  const bool use_oz = emulated && ozaki_supported(m);
+  const bool use_oz = emulated && m >= 256 && ozaki_supported(m);  // below m = 256 native FP64 is as fast
   // the m x m x m products: FP64-accurate emulation on the tensor cores, or native FP64
   auto mm3 = [&](double alpha, const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
                  cudaStream_t s_) {
