@@ -180,6 +180,22 @@ RFD_API rfd_status rfd_gfi(rfd_plan_t plan, const float* d_points, const float* 
 RFD_API rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double* d_G, int32_t flags, void* cuda_stream,
                             rfd_stats* stats_out);
 
+/* Step a4 for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of rfd_phi1 (same arguments, same
+ * result) for code in which cudaMalloc/cudaFree are not allowed -- a
+ * latency-critical loop where an allocation could synchronise the device, or a
+ * process whose device memory is owned by another allocator.  It calls no
+ * allocating routine: its workspace is a fixed 3.25 MiB __device__ array that
+ * every GPU loading the library holds until the process exits, so it only
+ * serves 1 <= m <= 128 (RFD_EINVAL with a message beyond that).  The first call
+ * on each device looks up that array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the previous call's contents: calls whose device work overlaps
+ * (other streams or threads) race and must be serialised by the caller.
+ * Synchronises `cuda_stream`. */
+RFD_API rfd_status rfd_phi1_noalloc(int32_t m, double lambda, const double* d_M, double* d_G, int32_t flags,
+                                    void* cuda_stream, rfd_stats* stats_out);
+
 /* Wait for all of the plan's queued device work. */
 RFD_API rfd_status rfd_sync(rfd_plan_t plan);
 

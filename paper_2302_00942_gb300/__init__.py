@@ -80,6 +80,7 @@ def _load():
         "rfd_gfi": (I32, [P, P, P, I32, I64, P, I64]),
         "rfd_sync": (I32, [P]),
         "rfd_phi1": (I32, [I32, D, P, P, I32, P, ctypes.POINTER(rfd_stats)]),
+        "rfd_phi1_noalloc": (I32, [I32, D, P, P, I32, P, ctypes.POINTER(rfd_stats)]),
         "rfd_plan_export": (I32, [P, DP, DP, DP]),
         "rfd_plan_stats": (I32, [P, ctypes.POINTER(rfd_stats)]),
         "rfd_plan_stats_reset": (I32, [P]),
@@ -98,7 +99,7 @@ lib = _load()
 
 # Every function include/rfd.h and include/rfd_testing.h declare (checked against the headers by a test).
 HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
-                  "rfd_gfi", "rfd_phi1", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
+                  "rfd_gfi", "rfd_phi1", "rfd_phi1_noalloc", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
                   "rfd_version", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm")
 
 
@@ -169,6 +170,16 @@ def rfd_phi1(m: int, lam: float, M, G, stream=None, native_fp64: bool = False) -
     st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
     flags = RFD_FLAG_NATIVE_FP64 if native_fp64 else 0
     _check(lib.rfd_phi1(m, lam, _dptr(M), _dptr(G), flags, st, ctypes.byref(s)), "rfd_phi1")
+    return _stats_dict(s)
+
+
+def rfd_phi1_noalloc(m: int, lam: float, M, G, stream=None, native_fp64: bool = False) -> dict:
+    """rfd_phi1 for callers that cannot allocate device memory (m <= 128; the
+    workspace is a fixed device array shared by all calls -- serialise them)."""
+    s = rfd_stats()
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    flags = RFD_FLAG_NATIVE_FP64 if native_fp64 else 0
+    _check(lib.rfd_phi1_noalloc(m, lam, _dptr(M), _dptr(G), flags, st, ctypes.byref(s)), "rfd_phi1_noalloc")
     return _stats_dict(s)
 
 
