@@ -210,6 +210,44 @@ RFD_API rfd_status rfd_plan_stats(rfd_plan_t plan, rfd_stats* out);
 /* Zero the accumulated step timings and launch count of a plan. */
 RFD_API rfd_status rfd_plan_stats_reset(rfd_plan_t plan);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many point clouds of uneven N and m integrated by shared launches
+ * (one launch per step for all clouds; step a4 of every cloud on the
+ * FP64-accurate tensor-core emulation with per-cloud scaling).  A batch is a
+ * fixed list of BF16 plans (RFD_BF16_TC, each listed once) and uses their
+ * device buffers; it runs on its own stream, and a plan in a batch must not
+ * be used on its own while a batch call on it may be in flight.
+ * --------------------------------------------------------------------------- */
+typedef struct rfd_batch_s* rfd_batch_t;
+
+/* Per-cloud arguments of a batched call (device pointers; see rfd_gfi). */
+typedef struct {
+  const float* d_points;  /* N x 3 (features / gfi)                       */
+  const float* d_F;       /* N x c, leading dimension ldF (integrate / gfi) */
+  float* d_out;           /* N x c, leading dimension ldOut; may equal d_F */
+  int32_t c;
+  int32_t reserved_;
+  int64_t ldF, ldOut;
+} rfd_batch_item;
+
+/* Build a batch over `count` plans (caller-owned array, copied).  flags:
+ * RFD_FLAG_TIMING or 0.  Allocates the batch's device tables; RFD_EINVAL for
+ * FP32 plans or a repeated plan. */
+RFD_API rfd_status rfd_batch_create(const rfd_plan_t* plans, int32_t count, int32_t flags, void* cuda_stream,
+                                    rfd_batch_t* out);
+RFD_API rfd_status rfd_batch_destroy(rfd_batch_t batch);
+/* Batched rfd_features / rfd_integrate / rfd_gfi: items[k] belongs to plans[k].
+ * features and gfi synchronise the batch stream once (the per-cloud scaling
+ * of step a4 is chosen on the host) and return RFD_ENUMERIC naming the clouds
+ * whose G is not finite. */
+RFD_API rfd_status rfd_batch_features(rfd_batch_t batch, const rfd_batch_item* items);
+RFD_API rfd_status rfd_batch_integrate(rfd_batch_t batch, const rfd_batch_item* items);
+RFD_API rfd_status rfd_batch_gfi(rfd_batch_t batch, const rfd_batch_item* items);
+RFD_API rfd_status rfd_batch_sync(rfd_batch_t batch);
+/* Step timings / launch count of the batch (RFD_FLAG_TIMING), as rfd_plan_stats. */
+RFD_API rfd_status rfd_batch_stats(rfd_batch_t batch, rfd_stats* out);
+RFD_API rfd_status rfd_batch_stats_reset(rfd_batch_t batch);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 RFD_API const char* rfd_last_error(void);
 

@@ -21,7 +21,7 @@ __all__ = [
     "RFD_EBUSY", "RFD_ENOTSUP", "RFD_FP32_PLAIN", "RFD_BF16_TC", "RfdError", "rfd_params", "rfd_stats",
     "lib", "lib_path", "rfd_sample_frequencies", "rfd_plan", "rfd_plan_destroy", "rfd_features",
     "rfd_integrate", "rfd_gfi", "rfd_phi1", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
-    "rfd_version", "RFD_FLAG_TIMING", "STEP_NAMES", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "Plan", "HEADER_SYMBOLS",
+    "rfd_version", "RFD_FLAG_TIMING", "STEP_NAMES", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "Plan", "Batch", "rfd_batch_item", "HEADER_SYMBOLS",
     "RFD_FLAG_NATIVE_FP64",
 ]
 
@@ -50,6 +50,12 @@ class rfd_stats(ctypes.Structure):
                 ("nonfinite", ctypes.c_int32), ("splits", ctypes.c_int32), ("phi1_emulated", ctypes.c_int32),
                 ("phi1_gemms", ctypes.c_int32), ("step_ms", ctypes.c_double * len(STEP_NAMES)), ("timed_calls", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64)]
+
+
+class rfd_batch_item(ctypes.Structure):
+    _fields_ = [("d_points", ctypes.c_void_p), ("d_F", ctypes.c_void_p), ("d_out", ctypes.c_void_p),
+                ("c", ctypes.c_int32), ("reserved_", ctypes.c_int32), ("ldF", ctypes.c_int64),
+                ("ldOut", ctypes.c_int64)]
 
 
 def _stats_dict(s: "rfd_stats") -> dict:
@@ -88,6 +94,14 @@ def _load():
         "rfd_version": (ctypes.c_char_p, []),
         "rfd_debug_fail_alloc_after": (None, [I32]),
         "rfd_debug_dgemm": (I32, [I32, I32, I32, I32, D, P, I32, P, I32, D, P, I32, P]),
+        "rfd_batch_create": (I32, [ctypes.POINTER(P), I32, I32, P, ctypes.POINTER(P)]),
+        "rfd_batch_destroy": (I32, [P]),
+        "rfd_batch_features": (I32, [P, ctypes.POINTER(rfd_batch_item)]),
+        "rfd_batch_integrate": (I32, [P, ctypes.POINTER(rfd_batch_item)]),
+        "rfd_batch_gfi": (I32, [P, ctypes.POINTER(rfd_batch_item)]),
+        "rfd_batch_sync": (I32, [P]),
+        "rfd_batch_stats": (I32, [P, ctypes.POINTER(rfd_stats)]),
+        "rfd_batch_stats_reset": (I32, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -100,7 +114,9 @@ lib = _load()
 # Every function include/rfd.h and include/rfd_testing.h declare (checked against the headers by a test).
 HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
                   "rfd_gfi", "rfd_phi1", "rfd_phi1_noalloc", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
-                  "rfd_version", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm")
+                  "rfd_version", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "rfd_batch_create",
+                  "rfd_batch_destroy", "rfd_batch_features", "rfd_batch_integrate", "rfd_batch_gfi",
+                  "rfd_batch_sync", "rfd_batch_stats", "rfd_batch_stats_reset")
 
 
 def rfd_last_error() -> str:
@@ -272,6 +288,79 @@ class Plan:
     def close(self):
         if self.handle:
             rfd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many BF16 plans integrated by shared launches (include/rfd.h, batches).
+
+    items: a list with one dict per plan: {"points": (N, 3) tensor, "F": (N, c)
+    tensor, "out": (N, c) tensor or None}; all float32 CUDA, row-major.
+    """
+
+    def __init__(self, plans, stream=None, timing=False):
+        self.plans = list(plans)
+        self.handle = None
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle for p in self.plans])
+        h = ctypes.c_void_p()
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        _check(lib.rfd_batch_create(arr, len(self.plans), RFD_FLAG_TIMING if timing else 0, s, ctypes.byref(h)),
+               "rfd_batch_create")
+        self.handle = h.value
+
+    def _items(self, items, need_f):
+        arr = (rfd_batch_item * len(self.plans))()
+        outs = []
+        for k, it in enumerate(items):
+            P = it.get("points")
+            F = it.get("F")
+            arr[k].d_points = _dptr(P) if P is not None else None
+            if need_f:
+                import torch
+                out = it.get("out")
+                if out is None:
+                    out = torch.empty_like(F)
+                arr[k].d_F, arr[k].d_out = _dptr(F), _dptr(out)
+                arr[k].c, arr[k].ldF, arr[k].ldOut = F.shape[1], F.stride(0), out.stride(0)
+                outs.append(out)
+            else:
+                arr[k].c, arr[k].ldF, arr[k].ldOut = 1, 1, 1
+        return arr, outs
+
+    def gfi(self, items):
+        arr, outs = self._items(items, True)
+        _check(lib.rfd_batch_gfi(self.handle, arr), "rfd_batch_gfi")
+        return outs
+
+    def features(self, items):
+        arr, _ = self._items(items, False)
+        _check(lib.rfd_batch_features(self.handle, arr), "rfd_batch_features")
+
+    def integrate(self, items):
+        arr, outs = self._items(items, True)
+        _check(lib.rfd_batch_integrate(self.handle, arr), "rfd_batch_integrate")
+        return outs
+
+    def sync(self):
+        _check(lib.rfd_batch_sync(self.handle), "rfd_batch_sync")
+
+    def stats(self):
+        st = rfd_stats()
+        _check(lib.rfd_batch_stats(self.handle, ctypes.byref(st)), "rfd_batch_stats")
+        return _stats_dict(st)
+
+    def stats_reset(self):
+        _check(lib.rfd_batch_stats_reset(self.handle), "rfd_batch_stats_reset")
+
+    def close(self):
+        if self.handle:
+            _check(lib.rfd_batch_destroy(self.handle), "rfd_batch_destroy")
             self.handle = None
 
     def __del__(self):

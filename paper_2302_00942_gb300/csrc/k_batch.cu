@@ -1,0 +1,312 @@
+// Batched forms of the RFD steps (Sec. 2.4) around the tensor-core kernels:
+// one launch serves every cloud of a batch (a single cloud is a batch of one).
+// Jobs with a per-cloud number of blocks find their cloud by binary search over
+// a prefix array of block counts (prefix[count] = total blocks).
+//   a2  features_batched:  Phi[n, j] = cos 2 pi w_j^T x_n, Phi[n, h+j] = sin ..., bf16, feature-major
+//       fill_batched:      F^T into rows m.. of the same buffer (bf16)
+//   a3  reduce_batched:    fixed-order sum of the split-K partials, column scales applied
+//   a5  small_batched:     Z = diag(s sgn r) G Y
+//   a6  apply_batched:     out = F + Phi Z (F read before out is written: in place is fine)
+//   a4  bcombine / bnorm1 / bfinite: element-wise pieces of the phi1 evaluation
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include "kernels.h"
+
+namespace rfd {
+
+namespace {
+
+__device__ __forceinline__ int find_job(const int* __restrict__ prefix, int count, int b) {
+  int lo = 0, hi = count;  // prefix[lo] <= b < prefix[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(prefix + mid) <= b)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kFeatThreads = 256;
+constexpr int kFeatPts = 512;   // 2 points per thread
+constexpr int kFeatFreq = 32;
+
+__global__ void __launch_bounds__(kFeatThreads)
+features_batched_kernel(const FeatJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
+                        const CloudCall* __restrict__ calls) {
+  const int j = find_job(prefix, count, blockIdx.x);
+  const FeatJob jb = jobs[j];
+  const int local = blockIdx.x - prefix[j];
+  const int bxi = local % jb.bx, byi = local / jb.bx;
+  const float* __restrict__ pts = calls[jb.cloud].pts;
+  auto* psi = reinterpret_cast<__nv_bfloat16*>(jb.psi);
+  __shared__ float w_s[kFeatFreq][3];
+  const int j0 = byi * kFeatFreq;
+  const int jn = min(kFeatFreq, jb.h - j0);
+  if (threadIdx.x < jn * 3) w_s[threadIdx.x / 3][threadIdx.x % 3] = jb.omega[(size_t)j0 * 3 + threadIdx.x];
+  __syncthreads();
+  const int64_t p0 = (int64_t)bxi * kFeatPts + (int64_t)threadIdx.x * 2;
+  if (p0 >= jb.n_pad) return;
+  float x[2][3];
+  bool valid[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    valid[q] = (p0 + q) < jb.n;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) x[q][d] = valid[q] ? pts[(p0 + q) * 3 + d] : 0.f;
+  }
+  const float two_pi = 6.283185307179586f;
+  for (int jj = 0; jj < jn; ++jj) {
+    const float w0 = w_s[jj][0], w1 = w_s[jj][1], w2 = w_s[jj][2];
+    float c[2], s[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float t = fmaf(w0, x[q][0], fmaf(w1, x[q][1], w2 * x[q][2]));
+      const float a = two_pi * (t - rintf(t));   // |a| <= pi: MUFU sin/cos accurate to ~1e-6
+      c[q] = valid[q] ? __cosf(a) : 0.f;
+      s[q] = valid[q] ? __sinf(a) : 0.f;
+    }
+    const int jg = j0 + jj;
+    *reinterpret_cast<__nv_bfloat162*>(psi + (size_t)jg * jb.n_pad + p0) = __floats2bfloat162_rn(c[0], c[1]);
+    *reinterpret_cast<__nv_bfloat162*>(psi + (size_t)(jb.h + jg) * jb.n_pad + p0) = __floats2bfloat162_rn(s[0], s[1]);
+  }
+}
+
+__global__ void fill_batched_kernel(const FillJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
+                                    const CloudCall* __restrict__ calls) {
+  const int j = find_job(prefix, count, blockIdx.x);
+  const FillJob jb = jobs[j];
+  const int local = blockIdx.x - prefix[j];
+  const int bxi = local % jb.bx, cyi = local / jb.bx;
+  const CloudCall cc = calls[jb.cloud];
+  auto* rows = reinterpret_cast<__nv_bfloat16*>(jb.rows);
+  __shared__ float tile[32][33];
+  const int64_t n0 = (int64_t)bxi * 32;
+  const int c0 = cyi * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t pn = n0 + i;
+    const int ch = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (pn < jb.n && ch < cc.c) ? cc.F[pn * cc.ldF + ch] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int ch = c0 + i;
+    const int64_t pn = n0 + threadIdx.x;
+    if (ch < jb.cpad && pn < jb.n_pad) rows[(size_t)ch * jb.n_pad + pn] = __float2bfloat16_rn(tile[threadIdx.x][i]);
+  }
+}
+
+// One thread per tile element; lanes summed in order (deterministic) in FP64.
+__global__ void reduce_batched_kernel(const RedTile* __restrict__ tiles, const CloudCall* __restrict__ calls) {
+  const RedTile t = tiles[blockIdx.y];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = e / kTcBNMax, col = e % kTcBNMax;
+  if (r >= t.ni || col >= t.nj) return;
+  const float* p = t.part + (int64_t)r * t.ld + t.col_off + col;
+  double s = 0.0;
+  for (int u = 0; u < t.count; ++u) s += (double)p[(int64_t)u * t.slot_elems];
+  const int f = t.i0 + r;
+  if (t.kind == kTileGram) {
+    const int g = t.j0 + col;
+    if (f > g) return;  // the mirrored entry (g, f) is covered as (row g, column f)
+    t.M[(size_t)f * t.m + g] = t.ob[f] * s * t.oa[g];
+    if (f != g) t.M[(size_t)g * t.m + f] = t.ob[g] * s * t.oa[f];
+  } else {
+    const int c = calls[t.cloud].c;
+    if (col < c) t.Y[(size_t)f * c + col] = t.ob[f] * s;
+  }
+}
+
+// Z[f, ch] = oa[f] sum_g G[f, g] Y[g, ch]: block (32 channels x 8 g-slices) per row.
+__global__ void small_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
+                                     const CloudCall* __restrict__ calls) {
+  const int j = find_job(prefix, count, blockIdx.x);
+  const ApplyJob jb = jobs[j];
+  const int f = blockIdx.x - prefix[j];
+  const int c = calls[jb.cloud].c, m = jb.m;
+  __shared__ double red[8][32];
+  for (int ch0 = 0; ch0 < c; ch0 += 32) {
+    const int ch = ch0 + threadIdx.x;
+    double acc = 0.0;
+    if (ch < c)
+      for (int g = threadIdx.y; g < m; g += 8) acc = fma(jb.G[(size_t)f * m + g], jb.Y[(size_t)g * c + ch], acc);
+    red[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && ch < c) {
+      double s = 0.0;
+      for (int y = 0; y < 8; ++y) s += red[y][threadIdx.x];
+      jb.Z[(size_t)f * c + ch] = (float)(jb.oa[f] * s);
+    }
+    __syncthreads();
+  }
+}
+
+// out[n, ch] = F[n, ch] + sum_f Psi[f][n] Z[f, ch]: one point per thread
+// (coalesced Psi reads along n), CG channels per thread, Z through shared memory.
+template <int CG>
+__global__ void __launch_bounds__(256)
+apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
+                     const CloudCall* __restrict__ calls) {
+  constexpr int kChunk = 64;
+  __shared__ float zs[kChunk][CG];
+  const int j = find_job(prefix, count, blockIdx.x);
+  const ApplyJob jb = jobs[j];
+  const CloudCall cc = calls[jb.cloud];
+  const int local = blockIdx.x - prefix[j];
+  const int bxi = local % jb.bx, cgi = local / jb.bx;
+  const auto* psi = reinterpret_cast<const __nv_bfloat16*>(jb.psi);
+  const int64_t p = (int64_t)bxi * 256 + threadIdx.x;
+  const int ch0 = cgi * CG;
+  const int cg = min(CG, cc.c - ch0);
+  float acc[CG];
+#pragma unroll
+  for (int q = 0; q < CG; ++q) acc[q] = 0.f;
+  for (int f0 = 0; f0 < jb.m; f0 += kChunk) {
+    const int fn = min(kChunk, jb.m - f0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kChunk * CG; i += blockDim.x) {
+      const int fr = i / CG, q = i % CG;
+      zs[fr][q] = (fr < fn && q < cg) ? jb.Z[(size_t)(f0 + fr) * cc.c + ch0 + q] : 0.f;
+    }
+    __syncthreads();
+    if (p < jb.n) {
+      for (int fr = 0; fr < fn; ++fr) {
+        const float v = __bfloat162float(psi[(size_t)(f0 + fr) * jb.n_pad + p]);
+#pragma unroll
+        for (int q = 0; q < CG; ++q) acc[q] = fmaf(v, zs[fr][q], acc[q]);
+      }
+    }
+  }
+  if (p < jb.n)
+    for (int q = 0; q < cg; ++q) {
+      const float fv = cc.F[p * cc.ldF + ch0 + q];
+      cc.out[p * cc.ldOut + ch0 + q] = fv + acc[q];
+    }
+}
+
+__device__ __forceinline__ const double* slot_ptr(const PhiCloud& pc, int slot) {
+  return slot == kSlotM ? pc.M : (slot == kSlotG ? pc.G : pc.work + (size_t)slot * pc.m * pc.m);
+}
+
+struct Comb {
+  int src[4];
+  double a[4];
+};
+
+__global__ void bcombine_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count, int dst,
+                                Comb cb, double diag, int kmode, int mask_k) {
+  const int j = find_job(prefix, count, blockIdx.x);
+  const PhiCloud pc = pcs[j];
+  if (mask_k >= 0 && pc.s <= mask_k) return;
+  const int64_t e = (int64_t)(blockIdx.x - prefix[j]) * blockDim.x + threadIdx.x;
+  const int m = pc.m;
+  if (e >= (int64_t)m * m) return;
+  const int r = (int)(e / m), c = (int)(e % m);
+  const double k = (kmode == 1) ? pc.lambda : (kmode == 2 ? pc.scale : 1.0);
+  double v = (r == c) ? diag : 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (cb.src[i] != 0x7fffffff) v += cb.a[i] * slot_ptr(pc, cb.src[i])[e];
+  const_cast<double*>(slot_ptr(pc, dst))[e] = k * v;
+}
+
+// Max column abs-sum per cloud: block (32 columns x 32 row lanes), atomicMax on the bits.
+__global__ void bnorm1_kernel(const PhiCloud* __restrict__ pcs, int slot, unsigned long long* norms) {
+  const PhiCloud pc = pcs[blockIdx.y];
+  const int m = pc.m;
+  const int col = blockIdx.x * 32 + threadIdx.x;
+  if (blockIdx.x * 32 >= m) return;
+  const double* X = slot_ptr(pc, slot);
+  __shared__ double part[32][33];
+  double s = 0.0;
+  if (col < m)
+    for (int i = threadIdx.y; i < m; i += 32) s += fabs(X[(size_t)i * m + col]);
+  part[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && col < m) {
+    double t = 0.0;
+    for (int y = 0; y < 32; ++y) t += part[y][threadIdx.x];
+    if (!(t == t)) t = __longlong_as_double(0x7FF0000000000000ll);
+    atomicMax(norms + blockIdx.y, (unsigned long long)__double_as_longlong(t));
+  }
+}
+
+__global__ void bfinite_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count, int slot) {
+  const int j = find_job(prefix, count, blockIdx.x);
+  const PhiCloud pc = pcs[j];
+  const int64_t e = (int64_t)(blockIdx.x - prefix[j]) * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)pc.m * pc.m) return;
+  if (!isfinite(slot_ptr(pc, slot)[e])) atomicExch(pc.flag, 1);
+}
+
+}  // namespace
+
+cudaError_t launch_features_batched(const FeatJob* jobs, const int* prefix, int count, int total_blocks,
+                                    const CloudCall* calls, cudaStream_t st) {
+  if (total_blocks <= 0) return cudaSuccess;
+  features_batched_kernel<<<total_blocks, kFeatThreads, 0, st>>>(jobs, prefix, count, calls);
+  return launched();
+}
+
+cudaError_t launch_fill_batched(const FillJob* jobs, const int* prefix, int count, int total_blocks,
+                                const CloudCall* calls, cudaStream_t st) {
+  if (total_blocks <= 0) return cudaSuccess;
+  fill_batched_kernel<<<total_blocks, dim3(32, 8), 0, st>>>(jobs, prefix, count, calls);
+  return launched();
+}
+
+cudaError_t launch_reduce_batched(const RedTile* tiles, int num_tiles, const CloudCall* calls, cudaStream_t st) {
+  if (num_tiles <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((kTcBM * kTcBNMax + 255) / 256), (unsigned)num_tiles);
+  reduce_batched_kernel<<<grid, 256, 0, st>>>(tiles, calls);
+  return launched();
+}
+
+cudaError_t launch_small_batched(const ApplyJob* jobs, const int* prefix, int count, int total_rows,
+                                 const CloudCall* calls, cudaStream_t st) {
+  if (total_rows <= 0) return cudaSuccess;
+  small_batched_kernel<<<total_rows, dim3(32, 8), 0, st>>>(jobs, prefix, count, calls);
+  return launched();
+}
+
+cudaError_t launch_apply_batched(const ApplyJob* jobs, const int* prefix, int count, int total_blocks, int cg,
+                                 const CloudCall* calls, cudaStream_t st) {
+  if (total_blocks <= 0) return cudaSuccess;
+  switch (cg) {
+    case 4: apply_batched_kernel<4><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
+    case 8: apply_batched_kernel<8><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
+    case 16: apply_batched_kernel<16><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
+    case 32: apply_batched_kernel<32><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return launched();
+}
+
+cudaError_t launch_bcombine(const PhiCloud* pc, const int* prefix, int count, int total_blocks, int dst,
+                            const int* src4, const double* a4, double diag, int kmode, int mask_k, cudaStream_t st) {
+  Comb cb;
+  for (int i = 0; i < 4; ++i) {
+    cb.src[i] = src4 ? src4[i] : 0x7fffffff;
+    cb.a[i] = a4 ? a4[i] : 0.0;
+  }
+  bcombine_kernel<<<total_blocks, 256, 0, st>>>(pc, prefix, count, dst, cb, diag, kmode, mask_k);
+  return launched();
+}
+
+cudaError_t launch_bnorm1(const PhiCloud* pc, int count, int max_m, int slot, double* norms, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(norms, 0, (size_t)count * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((max_m + 31) / 32), (unsigned)count);
+  bnorm1_kernel<<<grid, dim3(32, 32), 0, st>>>(pc, slot, reinterpret_cast<unsigned long long*>(norms));
+  return launched();
+}
+
+cudaError_t launch_bfinite(const PhiCloud* pc, const int* prefix, int count, int total_blocks, int slot,
+                           cudaStream_t st) {
+  bfinite_kernel<<<total_blocks, 256, 0, st>>>(pc, prefix, count, slot);
+  return launched();
+}
+
+}  // namespace rfd

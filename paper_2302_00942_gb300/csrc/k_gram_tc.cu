@@ -6,14 +6,15 @@
 //   Y'[f, c] = sum_n Psi[i0 + f][n] * Psi[m + c][n]      (Phi^T F)
 //
 // Psi (bf16, feature-major: n contiguous) makes both operands K-major.  Each
-// CTA owns one tile -- 128 feature rows against up to 256 Gram rows and,
-// for one tile per row block, the cpad field rows -- and one "lane" of the
-// point axis: the 64-point blocks kb = lane, lane + L, lane + 2L, ...  All
-// lanes of all tiles run in one wave and walk the point axis together, so
-// every 64-point slab of Psi is fetched from HBM once and served from L2 to
-// every tile that needs it.  The field columns ride on the same A slab: a
-// second MMA (N = cpad) per k-step into TMEM columns 256.., so B^T F costs
-// no extra pass over Psi.
+// CTA (a TcUnit) owns one tile of one cloud -- 128 feature rows against up to
+// 256 Gram rows and, for one tile per row block, the cpad field rows -- and
+// one "lane" of that cloud's point axis: the 64-point blocks kb = lane,
+// lane + L, lane + 2L, ...  The lanes of a cloud run in the same wave and walk
+// its point axis together, so each 64-point slab of Psi is fetched from HBM
+// once and served from L2 to every tile that needs it.  The field columns ride
+// on the same A slab: a second MMA (N = cpad) per k-step into TMEM columns
+// 256.., so B^T F costs no extra pass over Psi.  Tensor maps live in global
+// memory (three per cloud), so one launch can serve many clouds.
 //
 // Warp roles: warp 0 TMA producer (one lane), warp 1 TMEM allocator + MMA
 // issuer (one lane), warps 2..5 epilogue (TMEM lane quarter = warp % 4).
@@ -49,18 +50,18 @@ struct Smem {
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
-gram_tc_kernel(const __grid_constant__ CUtensorMap map_a,   // Phi rows, box 64 x 128
-               const __grid_constant__ CUtensorMap map_b,   // Phi rows, box 64 x 256
-               const __grid_constant__ CUtensorMap map_f,   // F rows,   box 64 x cpad
-               const GramUnit* __restrict__ units, int kb_total, int cpad, int a_rows_box, int b_rows_box,
-               int stages, int stage_bytes, float* __restrict__ partials, int* err) {
+gram_tc_kernel(const CUtensorMap* __restrict__ maps, const TcUnit* __restrict__ units, int stages, int stage_bytes,
+               int* err) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
   const uint32_t base = (raw_addr + 1023u) & ~1023u;
   Smem* sm = reinterpret_cast<Smem*>(smem_raw + (base - raw_addr) + stages * stage_bytes);
-  const GramUnit u = units[blockIdx.x];
+  const TcUnit u = units[blockIdx.x];
+  const CUtensorMap* map_a = maps + u.map;
+  const CUtensorMap* map_b = maps + u.map + 1;
+  const CUtensorMap* map_f = maps + u.map + 2;
   const bool has_g = u.nj_mma > 0, has_f = u.has_f != 0;
-  const int count = (u.lane < kb_total) ? (kb_total - u.lane + u.nlanes - 1) / u.nlanes : 0;
+  const int count = (u.lane < u.kb_total) ? (u.kb_total - u.lane + u.nlanes - 1) / u.nlanes : 0;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -76,8 +77,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_a,   // Phi rows, box 64 
   __syncthreads();
   fence_after();
   const uint32_t tmem = sm->tmem_base;
-  const uint32_t tx_bytes =
-      a_rows_box * kTcBK * 2 + (has_g ? b_rows_box * kTcBK * 2 : 0) + (has_f ? cpad * kTcBK * 2 : 0);
+  const uint32_t tx_bytes = u.a_rows * kTcBK * 2 + (has_g ? u.b_rows * kTcBK * 2 : 0) + (has_f ? u.cpad * kTcBK * 2 : 0);
 
   if (warp == 0) {
     if (lane == 0) {
@@ -91,9 +91,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_a,   // Phi rows, box 64 
         mbar_arrive_expect_tx(full, tx_bytes);
         const uint32_t sa = base + s * stage_bytes;
         const int32_t x = (u.lane + i * u.nlanes) * kTcBK;
-        tma_load_2d(sa, &map_a, x, u.i0, full);
-        if (has_g) tma_load_2d(sa + kABytes, &map_b, x, u.j0, full);
-        if (has_f) tma_load_2d(sa + kABytes + kBBytes, &map_f, x, 0, full);  // the F map starts at Psi row m
+        tma_load_2d(sa, map_a, x, u.i0, full);
+        if (has_g) tma_load_2d(sa + kABytes, map_b, x, u.j0, full);
+        if (has_f) tma_load_2d(sa + kABytes + kBBytes, map_f, x, 0, full);  // the F map starts at Psi row m
       }
       // drain: our copies into the last stages must land before the CTA exits
       for (int t = (i > stages ? i - stages : 0); t < i; ++t)
@@ -103,7 +103,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_a,   // Phi rows, box 64 
     if (lane == 0 && count > 0) {
       // ---------------- MMA issuer ----------------
       const uint32_t idesc_g = idesc_bf16(kTcBM, has_g ? u.nj_mma : 16);
-      const uint32_t idesc_f = idesc_bf16(kTcBM, cpad);
+      const uint32_t idesc_f = idesc_bf16(kTcBM, has_f ? u.cpad : 16);
       bool ok = true;
       for (int i = 0; i < count; ++i) {
         const int s = i % stages;
@@ -131,7 +131,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_a,   // Phi rows, box 64 
     // ---------------- epilogue (warps 2..5) ----------------
     const int quarter = warp & 3;         // TMEM lanes 32*quarter .. +31
     const int row = quarter * 32 + lane;  // tile row (feature f - i0)
-    float* out = partials + u.out + (size_t)row * kTcLd;
+    float* out = u.out + (size_t)row * kTcLd;
     const bool ready = (count > 0) && mbar_wait(smem_u32(&sm->acc_full), 0u, err, 5);
     if (ready) fence_after();
     const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
@@ -151,7 +151,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_a,   // Phi rows, box 64 
       }
     };
     if (has_g) drain(0, u.nj_mma);
-    if (has_f) drain(kTcBNMax, cpad);
+    if (has_f) drain(kTcBNMax, u.cpad);
   }
   fence_before();
   __syncthreads();
@@ -159,28 +159,28 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_a,   // Phi rows, box 64 
   if (warp == 1) tmem_dealloc(tmem, kTmemCols);
 }
 
+int stage_bytes_for(int cpad) { return (kABytes + kBBytes + cpad * kTcBK * 2 + 1023) / 1024 * 1024; }
+
 }  // namespace
 
 bool tc_gram_supported() { return tc::sm103_available(); }
 
-int tc_gram_stage_bytes(int cpad) { return (kABytes + kBBytes + cpad * kTcBK * 2 + 1023) / 1024 * 1024; }
+bool make_gram_maps(void* maps_host3, const void* psi, int64_t n_pad, int m, int cpad) {
+  auto* maps = static_cast<CUtensorMap*>(maps_host3);
+  const uint32_t a_rows = (uint32_t)(m < kTcBM ? m : kTcBM);
+  const uint32_t b_rows = (uint32_t)(m < kTcBNMax ? m : kTcBNMax);
+  const auto* p = static_cast<const uint16_t*>(psi);
+  return make_map_bf16(&maps[0], p, (uint64_t)n_pad, (uint64_t)m, (uint64_t)n_pad, a_rows) &&
+         make_map_bf16(&maps[1], p, (uint64_t)n_pad, (uint64_t)m, (uint64_t)n_pad, b_rows) &&
+         make_map_bf16(&maps[2], p + (size_t)m * n_pad, (uint64_t)n_pad, (uint64_t)cpad, (uint64_t)n_pad,
+                       (uint32_t)cpad);
+}
 
-cudaError_t launch_gram_tc(const TcGramArgs& a, int grid, cudaStream_t st) {
-  (void)grid;
-  if (a.num_units <= 0) return cudaSuccess;
-  if (a.cpad < 16 || a.cpad > 256 || (a.cpad % 16) || (a.n_pad % kTcBK)) return cudaErrorInvalidValue;
-  CUtensorMap ma, mb, mf;
-  const uint32_t a_rows = (uint32_t)(a.m < kTcBM ? a.m : kTcBM);
-  const uint32_t b_rows = (uint32_t)(a.m < kTcBNMax ? a.m : kTcBNMax);
-  const auto* psi = static_cast<const uint16_t*>(a.psi);
-  if (!make_map_bf16(&ma, psi, (uint64_t)a.n_pad, (uint64_t)a.m, (uint64_t)a.n_pad, a_rows))
-    return cudaErrorInvalidValue;
-  if (!make_map_bf16(&mb, psi, (uint64_t)a.n_pad, (uint64_t)a.m, (uint64_t)a.n_pad, b_rows))
-    return cudaErrorInvalidValue;
-  if (!make_map_bf16(&mf, psi + (size_t)a.m * a.n_pad, (uint64_t)a.n_pad, (uint64_t)a.cpad, (uint64_t)a.n_pad,
-                     (uint32_t)a.cpad))
-    return cudaErrorInvalidValue;
-  const int stage_bytes = tc_gram_stage_bytes(a.cpad);
+cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_units, int max_cpad, int* err,
+                           cudaStream_t st) {
+  if (num_units <= 0) return cudaSuccess;
+  if (max_cpad < 16 || max_cpad > 256) return cudaErrorInvalidValue;
+  const int stage_bytes = stage_bytes_for(max_cpad);
   int stages = (kSmemLimit - kSmemExtra) / stage_bytes;
   if (stages > kMaxStages) stages = kMaxStages;
   if (stages < 2) return cudaErrorInvalidValue;
@@ -191,9 +191,8 @@ cudaError_t launch_gram_tc(const TcGramArgs& a, int grid, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const int kb_total = (int)(a.n_pad / kTcBK);
-  gram_tc_kernel<<<a.num_units, kThreads, smem, st>>>(ma, mb, mf, a.units, kb_total, a.cpad, (int)a_rows,
-                                                      (int)b_rows, stages, stage_bytes, a.partials, a.err);
+  gram_tc_kernel<<<num_units, kThreads, smem, st>>>(static_cast<const CUtensorMap*>(maps_dev), units, stages,
+                                                    stage_bytes, err);
   return launched();
 }
 

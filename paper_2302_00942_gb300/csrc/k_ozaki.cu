@@ -61,11 +61,9 @@ constexpr int kMaxK = 1024;              // exactness bound of one FP32 accumula
 // mant << (E - Emax + 3) (or >> when negative) and the digits are the 7-bit
 // fields d_p = (F >> (56 - 7p)) & 127 with the entry's sign: exactly the
 // digits trunc(2^7 a), a <- 2^7 a - d_p produce.
-__global__ void split_rows_kernel(const double* __restrict__ X, int ld, int rows, int cols, int rows_pad,
-                                  int cols_pad, __nv_bfloat16* __restrict__ slices, int* __restrict__ exps) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= rows_pad) return;
-  const int i = warp;
+__device__ __forceinline__ void split_row(const double* __restrict__ X, int ld, int rows, int cols, int rows_pad,
+                                          int cols_pad, __nv_bfloat16* __restrict__ slices, int* __restrict__ exps,
+                                          int i, int lane) {
   int emax = 0;  // largest biased exponent in the row (0: all entries zero or subnormal)
   if (i < rows)
     for (int k = lane; k < cols; k += 32)
@@ -93,6 +91,69 @@ __global__ void split_rows_kernel(const double* __restrict__ X, int ld, int rows
   }
 }
 
+__global__ void split_rows_kernel(const double* __restrict__ X, int ld, int rows, int cols, int rows_pad,
+                                  int cols_pad, __nv_bfloat16* __restrict__ slices, int* __restrict__ exps) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= rows_pad) return;
+  split_row(X, ld, rows, cols, rows_pad, cols_pad, slices, exps, warp, lane);
+}
+
+__device__ __forceinline__ int find_job(const int* __restrict__ prefix, int count, int b) {
+  int lo = 0, hi = count;  // prefix[lo] <= b < prefix[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(prefix + mid) <= b)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ double* pc_slot(const PhiCloud& pc, int slot) {
+  return slot == kSlotM ? const_cast<double*>(pc.M) : (slot == kSlotG ? pc.G : pc.work + (size_t)slot * pc.m * pc.m);
+}
+
+// Batched row split: one warp per padded row of every cloud (prefix over rows).
+// operand 0: A = slot (rows/cols m, padded to mpa x kp) -> sa, ea;
+// operand 1: B^T = bt (padded to mpb x kp) -> sb, eb.
+__global__ void bsplit_rows_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
+                                   int operand, int slot, int mask_k) {
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (wg >= __ldg(prefix + count)) return;
+  const int j = find_job(prefix, count, wg);
+  const PhiCloud pc = pcs[j];
+  if (mask_k >= 0 && pc.s <= mask_k) return;
+  const int i = wg - prefix[j];
+  if (operand == 0)
+    split_row(pc_slot(pc, slot), pc.m, pc.m, pc.m, pc.mpa, pc.kp, reinterpret_cast<__nv_bfloat16*>(pc.sa), pc.ea, i,
+              lane);
+  else
+    split_row(pc.bt, pc.m, pc.m, pc.m, pc.mpb, pc.kp, reinterpret_cast<__nv_bfloat16*>(pc.sb), pc.eb, i, lane);
+}
+
+// Batched transpose of slot -> bt (32 x 32 tiles; prefix over tiles per cloud).
+__global__ void btranspose_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count, int slot,
+                                  int mask_k) {
+  const int j = find_job(prefix, count, blockIdx.x);
+  const PhiCloud pc = pcs[j];
+  if (mask_k >= 0 && pc.s <= mask_k) return;
+  const int m = pc.m, nb = (m + 31) / 32;
+  const int local = blockIdx.x - prefix[j];
+  const int c0 = (local % nb) * 32, r0 = (local / nb) * 32;
+  const double* B = pc_slot(pc, slot);
+  __shared__ double tile[32][33];
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int r = r0 + y, c = c0 + threadIdx.x;
+    tile[y][threadIdx.x] = (r < m && c < m) ? B[(size_t)r * m + c] : 0.0;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int c = c0 + y, r = r0 + threadIdx.x;
+    if (c < m && r < m) pc.bt[(size_t)c * m + r] = tile[threadIdx.x][y];
+  }
+}
+
 __global__ void transpose_kernel(const double* __restrict__ B, int ldb, int rows, int cols, double* __restrict__ Bt) {
   __shared__ double tile[32][33];
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
@@ -115,16 +176,19 @@ struct Smem {
   uint32_t tmem_base;
 };
 
-__global__ void __launch_bounds__(kThreads, 1)
-ozaki_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int M,
-                  int N, int M_pad, int N_pad, int K_pad, const int* __restrict__ ea, const int* __restrict__ eb,
-                  double alpha, double beta, double* C, int ldc, int* err) {
+// One 128 x 64 output tile (m0, n0) of C = alpha A B + beta C from the slice
+// tensor maps (A: rows p M_pad + i, B^T: rows q N_pad + j; K_pad columns).
+__device__ __forceinline__ void ozaki_tile(const CUtensorMap* map_a_p, const CUtensorMap* map_b_p, int M, int N,
+                                           int M_pad, int N_pad, int K_pad, const int* __restrict__ ea,
+                                           const int* __restrict__ eb, double alpha, double beta, double* C, int ldc,
+                                           int m0, int n0, int* err) {
   extern __shared__ uint8_t smem_raw[];
+  const CUtensorMap& map_a = *map_a_p;
+  const CUtensorMap& map_b = *map_b_p;
   const uint32_t raw_addr = smem_u32(smem_raw);
   const uint32_t base = (raw_addr + 1023u) & ~1023u;
   Smem* sm = reinterpret_cast<Smem*>(smem_raw + (base - raw_addr) + kStages * kStageBytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
   const int nkc = K_pad / kBK;
 
   if (threadIdx.x == 0) {
@@ -257,7 +321,54 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_consta
   if (warp == 1) tmem_dealloc(tmem, 512);
 }
 
+__global__ void __launch_bounds__(kThreads, 1)
+ozaki_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int M,
+                  int N, int M_pad, int N_pad, int K_pad, const int* __restrict__ ea, const int* __restrict__ eb,
+                  double alpha, double beta, double* C, int ldc, int* err) {
+  ozaki_tile(&map_a, &map_b, M, N, M_pad, N_pad, K_pad, ea, eb, alpha, beta, C, ldc, blockIdx.y * kBM,
+             blockIdx.x * kBN, err);
+}
+
+// Batched: one CTA per OzTile of any cloud; C = slot c_slot of the cloud.
+__global__ void __launch_bounds__(kThreads, 1)
+ozaki_gemm_batched_kernel(const CUtensorMap* __restrict__ maps, const OzTile* __restrict__ tiles,
+                          const PhiCloud* __restrict__ pcs, int c_slot, double alpha, double beta, int mask_k,
+                          int* err) {
+  const OzTile t = tiles[blockIdx.x];
+  const PhiCloud pc = pcs[t.cloud];
+  if (mask_k >= 0 && pc.s <= mask_k) return;
+  ozaki_tile(maps + pc.map_a, maps + pc.map_b, pc.m, pc.m, pc.mpa, pc.mpb, pc.kp, pc.ea, pc.eb, alpha, beta,
+             pc_slot(pc, c_slot), pc.m, t.m0, t.n0, err);
+}
+
 }  // namespace
+
+bool make_ozaki_maps(void* map_a_host, void* map_b_host, const void* sa, const void* sb, int mpa, int mpb, int kp) {
+  return tc::make_map_bf16(static_cast<CUtensorMap*>(map_a_host), sa, (uint64_t)kp, (uint64_t)kS * mpa, (uint64_t)kp,
+                           kBM) &&
+         tc::make_map_bf16(static_cast<CUtensorMap*>(map_b_host), sb, (uint64_t)kp, (uint64_t)kS * mpb, (uint64_t)kp,
+                           kBN);
+}
+
+cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* row_prefix_b,
+                         int rows_b, const int* t_prefix, int t_blocks, const OzTile* tiles, int num_tiles,
+                         const void* maps_dev, int a_slot, int b_slot, int c_slot, double alpha, double beta,
+                         int mask_k, int* err, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(ozaki_gemm_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  bsplit_rows_kernel<<<(rows_a * 32 + 255) / 256, 256, 0, st>>>(pc, row_prefix_a, count, 0, a_slot, mask_k);
+  btranspose_kernel<<<t_blocks, dim3(32, 8), 0, st>>>(pc, t_prefix, count, b_slot, mask_k);
+  bsplit_rows_kernel<<<(rows_b * 32 + 255) / 256, 256, 0, st>>>(pc, row_prefix_b, count, 1, 0, mask_k);
+  count_launch(3);
+  ozaki_gemm_batched_kernel<<<num_tiles, kThreads, kSmemBytes, st>>>(static_cast<const CUtensorMap*>(maps_dev), tiles,
+                                                                     pc, c_slot, alpha, beta, mask_k, err);
+  return launched();
+}
 
 size_t ozaki_workspace_bytes(int M, int N, int K) {
   const size_t mp = (size_t)((M + kBM - 1) / kBM) * kBM, np = (size_t)((N + kBN - 1) / kBN) * kBN;

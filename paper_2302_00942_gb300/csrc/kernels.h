@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <cuda_bf16.h>
 
 namespace rfd {
 
@@ -65,16 +66,22 @@ constexpr int kTcBM = 128;
 constexpr int kTcBNMax = 256;
 constexpr int kTcBK = 64;
 constexpr int kTcLd = 512;
-struct TcGramArgs {
-  const void* psi;       // bf16 [rows][n_pad]
-  int64_t n_pad;
-  int32_t m, cpad;
-  const GramUnit* units;
-  int32_t num_units;
-  float* partials;
-  int* err;              // device error word (bounded waits record here)
+// One CTA of the tensor-core reductions: tile rows i0.. of one cloud's Psi
+// against a Gram block j0.. (nj_mma > 0) and/or the cloud's cpad field rows
+// (has_f), over the 64-point blocks kb = lane, lane + nlanes, ... < kb_total.
+// maps[map + 0/1/2]: the cloud's A (box 64 x 128), B (64 x 256), F (64 x cpad) maps.
+struct TcUnit {
+  float* out;          // this CTA's partial tile: 128 rows x kTcLd floats
+  int32_t map;
+  int32_t i0, j0, nj_mma, has_f, cpad;
+  int32_t lane, nlanes, kb_total, a_rows, b_rows;
+  int32_t pad_;
 };
-cudaError_t launch_gram_tc(const TcGramArgs& a, int grid, cudaStream_t st);
+// Encodes the three tensor maps of a cloud's bf16 feature matrix Psi
+// ([rows_alloc][n_pad], rows 0..m-1 features, m..m+cpad-1 field) into maps[0..2].
+bool make_gram_maps(void* maps_host3, const void* psi, int64_t n_pad, int m, int cpad);
+cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_units, int max_cpad, int* err,
+                           cudaStream_t st);
 bool tc_gram_supported();
 
 // Sum the split-K partials of every tile in a fixed order (Kahan) and apply
@@ -112,5 +119,104 @@ cudaError_t dgemm_ozaki(int M, int N, int K, double alpha, const double* A, int 
 cudaError_t dgetrf(int m, double* A, int lda, int* ipiv, double* work, int* info, cudaStream_t st);
 cudaError_t dgetrs(int m, int nrhs, const double* LU, int lda, const int* ipiv, double* B, int ldb,
                    cudaStream_t st);
+
+// ===========================================================================
+// Batched path: many clouds per launch (and a single cloud as a batch of one).
+// Each launcher takes device tables; kernels with a per-cloud block count find
+// their cloud by binary search over a prefix array of block counts.
+// ===========================================================================
+
+// Per call and cloud: the caller's buffers and channel count.
+struct CloudCall {
+  const float* pts;
+  const float* F;
+  float* out;
+  int64_t ldF, ldOut;
+  int32_t c, pad_;
+};
+
+// Step a2 (features) for one cloud, BF16 form.
+struct FeatJob {
+  int64_t n, n_pad;
+  const float* omega;   // h x 3 FP32 frequencies
+  __nv_bfloat16_raw* psi;
+  int32_t h, bx, cloud, pad_;  // bx: 512-point blocks; the job has bx * ceil(h / 32) blocks
+};
+// F^T rows of a cloud's Psi (rows m .. m + cpad - 1), BF16.
+struct FillJob {
+  int64_t n, n_pad;
+  __nv_bfloat16_raw* rows;
+  int32_t cpad, bx, cloud, pad_;  // bx: 32-point blocks; the job has bx * ceil(cpad / 32) blocks
+};
+// One output tile of the split-K reduction (absolute pointers).
+struct RedTile {
+  const float* part;    // partial of lane 0; lane l at part + l * slot_elems
+  double* M;
+  double* Y;
+  const double* oa;
+  const double* ob;
+  int64_t slot_elems;
+  int32_t i0, j0, ni, nj, kind, count, ld, col_off, m, cloud;
+};
+// Steps a5 / a6 for one cloud.
+struct ApplyJob {
+  const __nv_bfloat16_raw* psi;
+  const double* G;
+  const double* Y;
+  const double* oa;
+  float* Z;
+  int64_t n, n_pad;
+  int32_t m, cloud, bx, pad_;  // bx: 256-point blocks
+};
+// Step a4 (phi1) for one cloud on the emulated-FP64 path.  Matrix "slots":
+// slot k >= 0 is work + k m^2; kSlotM is M, kSlotG is G.
+constexpr int kSlotM = -1, kSlotG = -2;
+struct PhiCloud {
+  double* work;
+  const double* M;
+  double* G;
+  __nv_bfloat16_raw* sa;  // A-operand slices [8][mpa][kp]
+  __nv_bfloat16_raw* sb;  // B-operand slices [8][mpb][kp]
+  int* ea;                // row exponents of A (mpa)
+  int* eb;                // column exponents of B (mpb)
+  double* bt;             // B^T scratch (m x m)
+  int* flag;              // finiteness flag
+  double lambda, scale;   // scale = 2^-s (set per call)
+  int32_t m, mpa, mpb, kp;
+  int32_t map_a, map_b;   // tensor maps of sa / sb
+  int32_t s, pad_;        // squarings (set per call)
+};
+struct OzTile {
+  int32_t cloud, m0, n0, pad_;
+};
+
+cudaError_t launch_features_batched(const FeatJob* jobs, const int* prefix, int count, int total_blocks,
+                                    const CloudCall* calls, cudaStream_t st);
+cudaError_t launch_fill_batched(const FillJob* jobs, const int* prefix, int count, int total_blocks,
+                                const CloudCall* calls, cudaStream_t st);
+cudaError_t launch_reduce_batched(const RedTile* tiles, int num_tiles, const CloudCall* calls, cudaStream_t st);
+// Z = diag(oa) G Y per cloud (one block per matrix row: prefix over m)
+cudaError_t launch_small_batched(const ApplyJob* jobs, const int* prefix, int count, int total_rows,
+                                 const CloudCall* calls, cudaStream_t st);
+// out = F + Phi Z per cloud; cg: channels per thread (4, 8, 16 or 32);
+// prefix over bx * ceil(c / cg) blocks per cloud
+cudaError_t launch_apply_batched(const ApplyJob* jobs, const int* prefix, int count, int total_blocks, int cg,
+                                 const CloudCall* calls, cudaStream_t st);
+// phi1 building blocks over all clouds (elements: prefix over ceil(m^2 / 256) blocks)
+// D = k (a0 X0 + a1 X1 + a2 X2 + a3 X3 + diag I), k = 1, lambda or scale (kmode 0/1/2);
+// clouds with s <= mask_k are skipped (mask_k < 0: none).
+cudaError_t launch_bcombine(const PhiCloud* pc, const int* prefix, int count, int total_blocks, int dst,
+                            const int* src4, const double* a4, double diag, int kmode, int mask_k, cudaStream_t st);
+cudaError_t launch_bnorm1(const PhiCloud* pc, int count, int max_m, int slot, double* norms, cudaStream_t st);
+cudaError_t launch_bfinite(const PhiCloud* pc, const int* prefix, int count, int total_blocks, int slot,
+                           cudaStream_t st);
+// C = alpha A B + beta C on every cloud (emulated FP64): splits + tensor-core products.
+// row_prefix_a / row_prefix_b: warp-row prefixes over mpa / mpb rows; t_prefix: transpose blocks.
+cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* row_prefix_b,
+                         int rows_b, const int* t_prefix, int t_blocks, const OzTile* tiles, int num_tiles,
+                         const void* maps_dev, int a_slot, int b_slot, int c_slot, double alpha, double beta,
+                         int mask_k, int* err, cudaStream_t st);
+// tensor maps of a cloud's Ozaki slice buffers (A: box 64 x 128 rows, B: box 64 x 64 rows)
+bool make_ozaki_maps(void* map_a_host, void* map_b_host, const void* sa, const void* sb, int mpa, int mpb, int kp);
 
 }  // namespace rfd

@@ -1,6 +1,10 @@
 // C ABI of the RFD integrator: plan management and the entry points that run
 // steps a2..a6 (Sec. 2.4) on the plan's CUDA stream.  See include/rfd.h for
 // the contract of every function.
+//
+// BF16 tensor-core plans run through the batched path (rfd_batch.cu) as a
+// batch of one; rfd_batch_* run many plans with shared launches.  FP32 plain
+// plans run the SIMT reductions and the native-FP64 step a4.
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <cmath>
@@ -11,13 +15,21 @@
 #include "kernels.h"
 #include "rfd_internal.h"
 #include "rfd_phi1.h"
+#include "rfd_plan.h"
 
 namespace rfd {
 const char* last_error_cstr();
 thread_local long long t_kernel_launches = 0;
-}
+}  // namespace rfd
 
 using namespace rfd;
+
+struct rfd_batch_s {
+  BatchImpl* impl = nullptr;
+  std::vector<rfd_plan_t> plans;
+  Timing timing;
+  cudaStream_t stream = nullptr;
+};
 
 namespace {
 
@@ -28,7 +40,7 @@ int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 // Allocation hook: every device allocation of a plan goes through here, so a
 // test can make the n-th allocation fail (RFD_ENOMEM path) without a GPU fault.
-int g_fail_alloc_after = -1;  // -1: never; k >= 0: the allocation after k more succeeds fails
+int g_fail_alloc_after = -1;
 
 cudaError_t dev_alloc(void** p, size_t bytes) {
   if (g_fail_alloc_after == 0) {
@@ -40,120 +52,13 @@ cudaError_t dev_alloc(void** p, size_t bytes) {
   return cudaMalloc(p, bytes);
 }
 
-struct TileSet {
-  std::vector<GramTile> tiles;
-  std::vector<GramUnit> units;
-  GramTile* d_tiles = nullptr;
-  GramUnit* d_units = nullptr;
-  int slots = 0;  // partial slots used
-};
-
-}  // namespace
-
-struct rfd_plan_s {
-  rfd_params p{};
-  cudaStream_t stream = nullptr;
-  int m = 0, h = 0, cpad = 0, sms = 0;
-  int64_t n = 0, n_pad = 0;
-  int rows_alloc = 0;
-  bool bf16 = false;
-  std::vector<double> omega, r, oa, ob;
-  // device
-  float* d_omega_hi = nullptr;
-  float* d_omega_lo = nullptr;
-  double* d_oa = nullptr;
-  double* d_ob = nullptr;
-  void* d_psi = nullptr;
-  float* d_part = nullptr;
-  int64_t slot_elems = 0;
-  double* d_M = nullptr;
-  double* d_Y = nullptr;
-  double* d_G = nullptr;
-  float* d_Z = nullptr;
-  double* d_work = nullptr;
-  int* d_ipiv = nullptr;
-  int* d_ints = nullptr;      // [0] error word, [1] LU info, [2] finite flag
-  double* d_scalar = nullptr;
-  TileSet gram_only, field_only, both;
-  bool have_G = false;
-  rfd_stats stats{};
-  std::vector<void*> allocs;
-  // step timing (RFD_FLAG_TIMING): a ring of per-call event sets, folded into
-  // the sums when the stream is synchronised by rfd_plan_stats
-  struct Slot {
-    cudaEvent_t ev[2 * RFD_NUM_STEPS];
-    bool used[RFD_NUM_STEPS];
-  };
-  bool timing = false;
-  std::vector<Slot> ring;
-  int ring_head = 0, ring_pending = 0;
-  Slot* cur = nullptr;
-  double step_sum[RFD_NUM_STEPS] = {};
-  long long timed_calls = 0;
-  long long launches = 0;
-  long long launch_mark = 0;
-};
-
-namespace {
-
-constexpr int kRing = 64;
-
-void fold_timings(rfd_plan_s* pl) {
-  if (!pl->timing || pl->ring_pending == 0) return;
-  cudaStreamSynchronize(pl->stream);
-  for (int k = pl->ring_pending; k > 0; --k) {
-    auto& s = pl->ring[(pl->ring_head - k + kRing) % kRing];
-    for (int i = 0; i < RFD_NUM_STEPS; ++i) {
-      if (!s.used[i]) continue;
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, s.ev[2 * i], s.ev[2 * i + 1]) == cudaSuccess) pl->step_sum[i] += ms;
-    }
-    ++pl->timed_calls;
-  }
-  pl->ring_pending = 0;
-}
-
-// Brackets one entry-point call: picks a timing slot and snapshots the launch counter.
-struct CallScope {
-  rfd_plan_s* pl;
-  explicit CallScope(rfd_plan_s* p) : pl(p) {
-    pl->launch_mark = t_kernel_launches;
-    if (!pl->timing) return;
-    if (pl->ring_pending == kRing) fold_timings(pl);
-    pl->cur = &pl->ring[pl->ring_head];
-    for (bool& u : pl->cur->used) u = false;
-  }
-  ~CallScope() {
-    pl->launches += t_kernel_launches - pl->launch_mark;
-    if (!pl->timing) return;
-    pl->cur = nullptr;
-    pl->ring_head = (pl->ring_head + 1) % kRing;
-    ++pl->ring_pending;
-  }
-};
-
-// Records CUDA events around one step of the path on the plan's stream.
-struct StepScope {
-  rfd_plan_s* pl;
-  int step;
-  StepScope(rfd_plan_s* p, int s) : pl(p), step(s) {
-    if (pl->cur) cudaEventRecord(pl->cur->ev[2 * step], pl->stream);
-  }
-  ~StepScope() {
-    if (pl->cur) {
-      cudaEventRecord(pl->cur->ev[2 * step + 1], pl->stream);
-      pl->cur->used[step] = true;
-    }
-  }
-};
-
 rfd_status cuda_fail(const char* what, cudaError_t e) {
   return fail(RFD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define RFD_CUDA(call)                                 \
-  do {                                                 \
-    cudaError_t e_ = (call);                           \
+#define RFD_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
     if (e_ != cudaSuccess) return cuda_fail(#call, e_); \
   } while (0)
 
@@ -162,7 +67,7 @@ rfd_status plan_alloc(rfd_plan_s* pl, T** p, size_t count) {
   void* raw = nullptr;
   cudaError_t e = dev_alloc(&raw, std::max<size_t>(count, 1) * sizeof(T));
   if (e != cudaSuccess) {
-    cudaGetLastError();  // clear the sticky-free allocation error
+    cudaGetLastError();
     return fail(RFD_ENOMEM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
   }
   pl->allocs.push_back(raw);
@@ -175,15 +80,12 @@ void plan_free(rfd_plan_s* pl) {
   pl->allocs.clear();
 }
 
-// Split-K schedule.  Each tile gets a number of point-range pieces in
-// proportion to its cost so that all pieces cost about the same; pieces are
-// ordered split-major (all tiles' first pieces, then the second ones, ...) so
-// that CTAs running at the same time read the same point range of Psi and the
-// L2 serves it to all of them.  Depends only on (N, m, channel capacity, SM
-// count): the result of a cloud never depends on other work.
-void schedule(TileSet& ts, int64_t n_pad, int kstep, int target_units, const std::vector<double>& cost,
-              int tile_rows, int ld) {
-  const int64_t ksteps = n_pad / kstep;
+// ---- FP32 plain form: SIMT split-K schedule --------------------------------
+// Each tile gets point-range pieces in proportion to its cost; pieces are
+// ordered split-major so concurrently running CTAs read the same point range.
+// Depends only on (N, m, channel capacity, SM count).
+void schedule_simt(TileSet& ts, int64_t n_pad, int target_units, const std::vector<double>& cost) {
+  const int64_t ksteps = n_pad / kSimtK;
   double total = 0;
   for (double c : cost) total += c;
   int slot = 0;
@@ -194,11 +96,11 @@ void schedule(TileSet& ts, int64_t n_pad, int kstep, int target_units, const std
     splits[t] = (int)s;
     ts.tiles[t].unit_first = slot;
     ts.tiles[t].unit_count = (int)s;
-    ts.tiles[t].ld = ld;
+    ts.tiles[t].ld = kSimtTile;
     slot += (int)s;
   }
   ts.slots = slot;
-  const int smax = *std::max_element(splits.begin(), splits.end());
+  const int smax = ts.tiles.empty() ? 0 : *std::max_element(splits.begin(), splits.end());
   for (int s = 0; s < smax; ++s)
     for (size_t t = 0; t < ts.tiles.size(); ++t) {
       if (s >= splits[t]) continue;
@@ -208,26 +110,59 @@ void schedule(TileSet& ts, int64_t n_pad, int kstep, int target_units, const std
       u.kind = T.kind;
       u.i0 = T.i0;
       u.j0 = T.j0;
-      u.nj_mma = (int)round_up(T.nj, 16);
       const int64_t a = ksteps * s / splits[t], b = ksteps * (s + 1) / splits[t];
-      u.k0 = a * kstep;
-      u.k1 = b * kstep;
-      u.out = (int64_t)(T.unit_first + s) * tile_rows * ld;
+      u.k0 = a * kSimtK;
+      u.k1 = b * kSimtK;
+      u.out = (int64_t)(T.unit_first + s) * kSimtTile * kSimtTile;
       ts.units.push_back(u);
     }
-  (void)tile_rows;
 }
 
-void build_tiles(rfd_plan_s* pl, bool with_gram, bool with_field, TileSet& ts) {
+void build_tiles_simt(rfd_plan_s* pl, bool with_gram, bool with_field, TileSet& ts) {
   const int m = pl->m;
   std::vector<double> cost;
-  if (pl->bf16) {
-    // Compute tiles: 128 feature rows x up to 256 Gram rows on the upper
-    // triangle of Phi^T Phi; the row block's field part (Phi^T F, cpad columns)
-    // rides on the tile whose Gram block holds the row block's diagonal (or on
-    // a field-only tile when there is no Gram work).  Each tile gets L lanes of
-    // the point axis, L = SMs / tiles, all CTAs in one wave (lockstep in kb).
-    struct CT { int i0, j0, ni, nj; bool f; };
+  for (int i0 = 0; i0 < m && with_gram; i0 += kSimtTile)
+    for (int j0 = i0; j0 < m; j0 += kSimtTile) {
+      ts.tiles.push_back(
+          GramTile{i0, j0, std::min(kSimtTile, m - i0), std::min(kSimtTile, m - j0), kTileGram, 0, 0, 0, 0, 0});
+      cost.push_back(1.0);
+    }
+  for (int i0 = 0; i0 < m && with_field; i0 += kSimtTile)
+    for (int c0 = 0; c0 < pl->cpad; c0 += kSimtTile) {
+      ts.tiles.push_back(GramTile{i0, m + c0, std::min(kSimtTile, m - i0), std::min(kSimtTile, pl->cpad - c0),
+                                  kTileField, 0, 0, 0, 0, 0});
+      cost.push_back(1.0);
+    }
+  schedule_simt(ts, pl->n_pad, 2 * pl->sms, cost);
+}
+
+rfd_status upload_tiles(rfd_plan_s* pl, TileSet& ts) {
+  rfd_status s = plan_alloc(pl, &ts.d_tiles, ts.tiles.size());
+  if (s != RFD_OK) return s;
+  s = plan_alloc(pl, &ts.d_units, ts.units.size());
+  if (s != RFD_OK) return s;
+  RFD_CUDA(cudaMemcpy(ts.d_tiles, ts.tiles.data(), ts.tiles.size() * sizeof(GramTile), cudaMemcpyHostToDevice));
+  RFD_CUDA(cudaMemcpy(ts.d_units, ts.units.data(), ts.units.size() * sizeof(GramUnit), cudaMemcpyHostToDevice));
+  return RFD_OK;
+}
+
+// ---- BF16 tensor-core form: the plan's batched-path descriptors -------------
+// Compute tiles: 128 feature rows x up to 256 Gram rows on the upper triangle
+// of Phi^T Phi; a row block's field part (Phi^T F, cpad columns) rides on the
+// tile whose Gram block holds the row block's diagonal (or on a field-only
+// tile when there is no Gram work).  Each tile gets L lanes of the point axis,
+// L = SMs / tiles, so a lone cloud fills the GPU in one wave.
+rfd_status build_desc(rfd_plan_s* pl) {
+  PlanDesc& d = pl->desc;
+  const int m = pl->m;
+  const int64_t kb_total = pl->n_pad / kTcBK;
+  const int a_rows = std::min(kTcBM, m), b_rows = std::min(kTcBNMax, m);
+  for (int mode = 0; mode < 3; ++mode) {
+    const bool with_gram = mode != kModeIntegrate, with_field = mode != kModeFeatures;
+    struct CT {
+      int i0, j0, ni, nj;
+      bool f;
+    };
     std::vector<CT> ct;
     for (int i0 = 0; i0 < m; i0 += kTcBM) {
       const int ni = std::min(kTcBM, m - i0);
@@ -241,90 +176,108 @@ void build_tiles(rfd_plan_s* pl, bool with_gram, bool with_field, TileSet& ts) {
         ct.push_back(CT{i0, j0, ni, nj, with_field && j0 == (i0 / kTcBNMax) * kTcBNMax});
       }
     }
-    const int64_t kb_total = pl->n_pad / kTcBK;
     const int T = (int)ct.size();
     const int L = (int)std::max<int64_t>(1, std::min<int64_t>(kb_total, pl->sms / std::max(T, 1)));
     for (int t = 0; t < T; ++t) {
       const CT& c = ct[t];
-      if (c.nj > 0)
-        ts.tiles.push_back(GramTile{c.i0, c.j0, c.ni, c.nj, kTileGram, t * L, L, kTcLd, 0, 0});
-      if (c.f) ts.tiles.push_back(GramTile{c.i0, m, c.ni, pl->cpad, kTileField, t * L, L, kTcLd, kTcBNMax, 0});
       for (int l = 0; l < L; ++l) {
-        GramUnit u{};
-        u.tile = t;
-        u.kind = c.nj > 0 ? kTileGram : kTileField;
+        TcUnit u{};
+        u.out = pl->d_part + (int64_t)(t * L + l) * pl->slot_elems;
+        u.map = 0;
         u.i0 = c.i0;
         u.j0 = c.j0;
         u.nj_mma = c.nj > 0 ? (int)round_up(c.nj, 16) : 0;
         u.has_f = c.f ? 1 : 0;
+        u.cpad = pl->cpad;
         u.lane = l;
         u.nlanes = L;
-        u.out = (int64_t)(t * L + l) * kTcBM * kTcLd;
-        ts.units.push_back(u);
+        u.kb_total = (int)kb_total;
+        u.a_rows = a_rows;
+        u.b_rows = b_rows;
+        d.units[mode].push_back(u);
+      }
+      // reduce tiles: .count holds the compute tile index until a batch assigns lanes
+      RedTile r{};
+      r.M = pl->d_M;
+      r.Y = pl->d_Y;
+      r.oa = pl->d_oa;
+      r.ob = pl->d_ob;
+      r.slot_elems = pl->slot_elems;
+      r.i0 = c.i0;
+      r.ni = c.ni;
+      r.count = t;
+      r.ld = kTcLd;
+      r.m = m;
+      if (c.nj > 0) {
+        r.j0 = c.j0;
+        r.nj = c.nj;
+        r.kind = kTileGram;
+        r.col_off = 0;
+        d.red[mode].push_back(r);
+      }
+      if (c.f) {
+        r.j0 = m;
+        r.nj = pl->cpad;
+        r.kind = kTileField;
+        r.col_off = kTcBNMax;
+        d.red[mode].push_back(r);
       }
     }
-    ts.slots = T * L;
-  } else {
-    for (int i0 = 0; i0 < m && with_gram; i0 += kSimtTile)
-      for (int j0 = i0; j0 < m; j0 += kSimtTile) {
-        ts.tiles.push_back(
-            GramTile{i0, j0, std::min(kSimtTile, m - i0), std::min(kSimtTile, m - j0), kTileGram, 0, 0, 0, 0, 0});
-        cost.push_back(1.0);
-      }
-    for (int i0 = 0; i0 < m && with_field; i0 += kSimtTile)
-      for (int c0 = 0; c0 < pl->cpad; c0 += kSimtTile) {
-        ts.tiles.push_back(GramTile{i0, m + c0, std::min(kSimtTile, m - i0), std::min(kSimtTile, pl->cpad - c0),
-                                    kTileField, 0, 0, 0, 0, 0});
-        cost.push_back(1.0);
-      }
-    schedule(ts, pl->n_pad, kSimtK, 2 * pl->sms, cost, kSimtTile, kSimtTile);
   }
-}
-
-rfd_status upload_tiles(rfd_plan_s* pl, TileSet& ts) {
-  rfd_status s = plan_alloc(pl, &ts.d_tiles, ts.tiles.size());
-  if (s != RFD_OK) return s;
-  s = plan_alloc(pl, &ts.d_units, ts.units.size());
-  if (s != RFD_OK) return s;
-  RFD_CUDA(cudaMemcpy(ts.d_tiles, ts.tiles.data(), ts.tiles.size() * sizeof(GramTile), cudaMemcpyHostToDevice));
-  RFD_CUDA(cudaMemcpy(ts.d_units, ts.units.data(), ts.units.size() * sizeof(GramUnit), cudaMemcpyHostToDevice));
+  auto* psi = static_cast<__nv_bfloat16_raw*>(pl->d_psi);
+  d.feat = FeatJob{pl->n, pl->n_pad, pl->d_omega_hi, psi, pl->h, (int)((pl->n_pad + 511) / 512), 0, 0};
+  d.fill = FillJob{pl->n, pl->n_pad, psi + (size_t)m * pl->n_pad, pl->cpad, (int)((pl->n_pad + 31) / 32), 0, 0};
+  d.apply = ApplyJob{psi, pl->d_G, pl->d_Y, pl->d_oa, pl->d_Z, pl->n, pl->n_pad, m, 0, (int)((pl->n + 255) / 256), 0};
+  // step a4 on the emulated path: slots in the FP64 workspace, Ozaki slices after them
+  PhiCloud& pc = d.phi;
+  pc = PhiCloud{};
+  pc.work = pl->d_work;
+  pc.M = pl->d_M;
+  pc.G = pl->d_G;
+  pc.m = m;
+  pc.mpa = (int)round_up(m, 128);
+  pc.mpb = (int)round_up(m, 64);
+  pc.kp = (int)round_up(m, 64);
+  auto* oz = reinterpret_cast<unsigned char*>(pl->d_work + (size_t)m * m * 18);
+  pc.sa = reinterpret_cast<__nv_bfloat16_raw*>(oz);
+  oz += (size_t)8 * pc.mpa * pc.kp * 2;
+  pc.sb = reinterpret_cast<__nv_bfloat16_raw*>(oz);
+  oz += (size_t)8 * pc.mpb * pc.kp * 2;
+  pc.ea = reinterpret_cast<int*>(oz);
+  oz += (size_t)pc.mpa * 4;
+  pc.eb = reinterpret_cast<int*>(oz);
+  oz += (size_t)pc.mpb * 4;
+  oz = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(oz) + 255) & ~uintptr_t(255));
+  pc.bt = reinterpret_cast<double*>(oz);
+  pc.lambda = pl->p.lambda;
+  pc.scale = 1.0;
+  pc.map_a = 3;
+  pc.map_b = 4;
+  for (int m0 = 0; m0 < pc.mpa; m0 += 128)
+    for (int n0 = 0; n0 < pc.mpb; n0 += 64) d.oz.push_back(OzTile{0, m0, n0, 0});
+  if (!make_gram_maps(d.maps[0], pl->d_psi, pl->n_pad, m, pl->cpad))
+    return fail(RFD_ECUDA, "tensor-map encoding of the feature matrix failed");
+  if (!make_ozaki_maps(d.maps[3], d.maps[4], pc.sa, pc.sb, pc.mpa, pc.mpb, pc.kp))
+    return fail(RFD_ECUDA, "tensor-map encoding of the FP64-emulation slices failed");
   return RFD_OK;
 }
 
-// Step a3 for one tile set: reductions over N, then the fixed-order reduce.
-rfd_status run_reductions(rfd_plan_s* pl, const TileSet& ts, int c) {
+// ---- FP32 plain form steps ---------------------------------------------------
+rfd_status run_reductions_simt(rfd_plan_s* pl, const TileSet& ts, int c) {
   cudaStream_t st = pl->stream;
-  if (pl->bf16) {
-    TcGramArgs a{};
-    a.psi = pl->d_psi;
-    a.n_pad = pl->n_pad;
-    a.m = pl->m;
-    a.cpad = pl->cpad;
-    a.units = ts.d_units;
-    a.num_units = (int)ts.units.size();
-    a.partials = pl->d_part;
-    a.err = pl->d_ints;
-    {
-      StepScope t(pl, RFD_STEP_GRAM);
-      RFD_CUDA(launch_gram_tc(a, pl->sms, st));
-    }
-    StepScope t(pl, RFD_STEP_REDUCE);
-    RFD_CUDA(launch_reduce(ts.d_tiles, (int)ts.tiles.size(), pl->d_part, pl->slot_elems, pl->d_oa, pl->d_ob, pl->m, c,
-                           pl->d_M, pl->d_Y, kTcBM, kTcBNMax, st));
-  } else {  // (the tile columns above bound both parts: Gram nj <= 256, field cpad <= 256)
-    {
-      StepScope t(pl, RFD_STEP_GRAM);
-      RFD_CUDA(launch_gram_simt(static_cast<const float*>(pl->d_psi), pl->n_pad, ts.d_units, (int)ts.units.size(),
-                                pl->d_part, st));
-    }
-    StepScope t(pl, RFD_STEP_REDUCE);
-    RFD_CUDA(launch_reduce(ts.d_tiles, (int)ts.tiles.size(), pl->d_part, pl->slot_elems, pl->d_oa, pl->d_ob, pl->m, c,
-                           pl->d_M, pl->d_Y, kSimtTile, kSimtTile, st));
+  {
+    StepScope t(&pl->timing, st, RFD_STEP_GRAM);
+    RFD_CUDA(launch_gram_simt(static_cast<const float*>(pl->d_psi), pl->n_pad, ts.d_units, (int)ts.units.size(),
+                              pl->d_part, st));
   }
+  StepScope t(&pl->timing, st, RFD_STEP_REDUCE);
+  RFD_CUDA(launch_reduce(ts.d_tiles, (int)ts.tiles.size(), pl->d_part, pl->slot_elems, pl->d_oa, pl->d_ob, pl->m, c,
+                         pl->d_M, pl->d_Y, kSimtTile, kSimtTile, st));
   return RFD_OK;
 }
 
 rfd_status check_device_error(rfd_plan_s* pl) {
+  if (pl->bf16) return batch_check_error(pl->self);
   int err = 0;
   RFD_CUDA(cudaMemcpyAsync(&err, pl->d_ints, sizeof(int), cudaMemcpyDeviceToHost, pl->stream));
   RFD_CUDA(cudaStreamSynchronize(pl->stream));
@@ -335,12 +288,14 @@ rfd_status check_device_error(rfd_plan_s* pl) {
   return RFD_OK;
 }
 
-rfd_status run_phi1(rfd_plan_s* pl) {
+rfd_status run_phi1_simt(rfd_plan_s* pl) {
   Phi1Info info{};
   rfd_status s;
-  StepScope t(pl, RFD_STEP_PHI1);
-  s = phi1_fp64(pl->m, pl->p.lambda, pl->d_M, pl->d_G, pl->d_work, pl->d_ipiv, pl->d_ints + 1, pl->d_scalar,
-                pl->d_ints + 2, pl->d_ints, (pl->p.flags & RFD_FLAG_NATIVE_FP64) == 0, pl->stream, &info);
+  {
+    StepScope t(&pl->timing, pl->stream, RFD_STEP_PHI1);
+    s = phi1_fp64(pl->m, pl->p.lambda, pl->d_M, pl->d_G, pl->d_work, pl->d_ipiv, pl->d_ints + 1, pl->d_scalar,
+                  pl->d_ints + 2, pl->d_ints, (pl->p.flags & RFD_FLAG_NATIVE_FP64) == 0, pl->stream, &info);
+  }
   pl->stats.phi1_emulated = info.emulated;
   pl->stats.phi1_gemms = info.gemms;
   pl->stats.norm1 = info.norm1;
@@ -348,12 +303,22 @@ rfd_status run_phi1(rfd_plan_s* pl) {
   pl->stats.squarings = info.squarings;
   pl->stats.nonfinite = info.nonfinite;
   if (s == RFD_ECUDA) return fail(s, std::string("phi1: ") + cudaGetErrorString(cudaGetLastError()));
-  if (s == RFD_ENUMERIC) return fail(s, "G = lambda phi1(lambda M) is not finite (||lambda M||_1 = " +
-                                            std::to_string(info.norm1) + ")");
+  if (s == RFD_ENUMERIC)
+    return fail(s, "G = lambda phi1(lambda M) is not finite (||lambda M||_1 = " + std::to_string(info.norm1) + ")");
   if (s != RFD_OK) return s;
   rfd_status e = check_device_error(pl);
   if (e != RFD_OK) return e;
   pl->have_G = true;
+  return RFD_OK;
+}
+
+rfd_status apply_simt(rfd_plan_s* pl, const float* F, int c, int64_t ldF, float* out, int64_t ldOut) {
+  {
+    StepScope t(&pl->timing, pl->stream, RFD_STEP_SMALL);
+    RFD_CUDA(launch_small_product(pl->d_G, pl->d_Y, pl->d_oa, pl->m, c, pl->d_Z, pl->stream));
+  }
+  StepScope t(&pl->timing, pl->stream, RFD_STEP_APPLY);
+  RFD_CUDA(launch_apply_simt(pl->d_psi, false, pl->n, pl->n_pad, pl->m, pl->d_Z, c, F, ldF, out, ldOut, pl->stream));
   return RFD_OK;
 }
 
@@ -365,15 +330,43 @@ rfd_status check_field_args(rfd_plan_s* pl, const float* F, int c, int64_t ldF, 
   return RFD_OK;
 }
 
-rfd_status apply_step(rfd_plan_s* pl, const float* F, int c, int64_t ldF, float* out, int64_t ldOut) {
-  {
-    StepScope t(pl, RFD_STEP_SMALL);
-    RFD_CUDA(launch_small_product(pl->d_G, pl->d_Y, pl->d_oa, pl->m, c, pl->d_Z, pl->stream));
+// Brackets one entry-point call for the timing ring and the launch count.
+struct CallScope {
+  Timing* t;
+  cudaStream_t st;
+  CallScope(Timing* tt, cudaStream_t s) : t(tt), st(s) { t->begin_call(st); }
+  ~CallScope() { t->end_call(); }
+};
+
+rfd_status run_plan(rfd_plan_s* pl, int mode, const float* pts, const float* F, int c, int64_t ldF, float* out,
+                    int64_t ldOut) {
+  CallScope call(&pl->timing, pl->stream);
+  if (pl->bf16) {
+    CloudCall cc{pts, F, out, ldF, ldOut, c, 0};
+    return batch_run(pl->self, mode, &cc, &pl->timing);
   }
-  StepScope t(pl, RFD_STEP_APPLY);
-  RFD_CUDA(launch_apply_simt(pl->d_psi, pl->bf16, pl->n, pl->n_pad, pl->m, pl->d_Z, c, F, ldF, out, ldOut,
-                             pl->stream));
-  return RFD_OK;
+  cudaStream_t st = pl->stream;
+  void* rows = static_cast<uint8_t*>(pl->d_psi) + (size_t)pl->m * pl->n_pad * 4;
+  if (mode != kModeIntegrate) {
+    pl->have_G = false;
+    StepScope t(&pl->timing, st, RFD_STEP_FEATURES);
+    RFD_CUDA(launch_features(pts, pl->n, pl->n_pad, pl->d_omega_hi, pl->d_omega_lo, pl->h, false, pl->d_psi, st));
+  }
+  if (mode != kModeFeatures) {
+    StepScope t(&pl->timing, st, RFD_STEP_FIELD);
+    RFD_CUDA(launch_fill_field_rows(F, ldF, c, pl->n, pl->n_pad, pl->cpad, false, rows, st));
+  }
+  const TileSet& ts = mode == kModeFeatures ? pl->gram_only : (mode == kModeIntegrate ? pl->field_only : pl->both);
+  rfd_status s = run_reductions_simt(pl, ts, mode == kModeFeatures ? 1 : c);
+  if (s == RFD_OK && mode != kModeIntegrate) s = run_phi1_simt(pl);
+  if (s == RFD_OK && mode != kModeFeatures) s = apply_simt(pl, F, c, ldF, out, ldOut);
+  return s;
+}
+
+void fill_stats(const Timing& tm, rfd_stats* out) {
+  for (int i = 0; i < RFD_NUM_STEPS; ++i) out->step_ms[i] = tm.calls ? tm.sum[i] / (double)tm.calls : 0.0;
+  out->timed_calls = tm.calls;
+  out->kernel_launches = tm.launches;
 }
 
 }  // namespace
@@ -381,7 +374,7 @@ rfd_status apply_step(rfd_plan_s* pl, const float* F, int c, int64_t ldF, float*
 extern "C" {
 
 const char* rfd_last_error(void) { return rfd::last_error_cstr(); }
-const char* rfd_version(void) { return "rfd-gb300 0.1 (sm_103a)"; }
+const char* rfd_version(void) { return "rfd-gb300 0.2 (sm_103a)"; }
 
 rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out) {
   if (!params || !out) return fail(RFD_EINVAL, "null params or output pointer");
@@ -404,7 +397,6 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
   pl->n_pad = round_up(p.n, 128);
   pl->cpad = (int)round_up(p.max_channels, 16);
   pl->bf16 = (p.precision == RFD_BF16_TC);
-  pl->timing = (p.flags & RFD_FLAG_TIMING) != 0;
   pl->omega.resize((size_t)pl->h * 3);
   pl->r.resize(pl->h);
   rfd_status st = rfd::sample_frequencies_host(p.m, p.eps, p.seed, p.freq_sigma, p.freq_radius, pl->omega.data(),
@@ -434,19 +426,23 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
     return fail(RFD_ENOTSUP, "the BF16 tensor-core form needs an sm_103 GPU (tcgen05) and cuTensorMapEncodeTiled");
   }
   auto bail = [&](rfd_status s) {
+    if (pl->self) batch_free(pl->self);
+    pl->timing.destroy();
     plan_free(pl);
     delete pl;
     return s;
   };
-  // host tables
-  build_tiles(pl, true, false, pl->gram_only);
-  build_tiles(pl, false, true, pl->field_only);
-  build_tiles(pl, true, true, pl->both);
-  const int slots = std::max({pl->gram_only.slots, pl->field_only.slots, pl->both.slots});
+  // partial slots: SIMT tiles, or up to one per SM for the tensor-core lanes
+  if (!pl->bf16) {
+    build_tiles_simt(pl, true, false, pl->gram_only);
+    build_tiles_simt(pl, false, true, pl->field_only);
+    build_tiles_simt(pl, true, true, pl->both);
+  }
+  const int slots = pl->bf16 ? std::max(pl->sms, 1) + 64
+                             : std::max({pl->gram_only.slots, pl->field_only.slots, pl->both.slots});
   pl->slot_elems = pl->bf16 ? (int64_t)kTcBM * kTcLd : (int64_t)kSimtTile * kSimtTile;
   pl->rows_alloc = (int)std::max<int64_t>(round_up(p.m, 128), p.m + round_up(pl->cpad, 128));
   const size_t esz = pl->bf16 ? 2 : 4;
-  // device buffers
   std::vector<float> whi(pl->omega.size()), wlo(pl->omega.size());
   for (size_t i = 0; i < pl->omega.size(); ++i) {
     whi[i] = (float)pl->omega[i];
@@ -469,9 +465,11 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
   if ((st = plan_alloc(pl, &pl->d_ipiv, (size_t)p.m)) != RFD_OK) return bail(st);
   if ((st = plan_alloc(pl, &pl->d_ints, 4)) != RFD_OK) return bail(st);
   if ((st = plan_alloc(pl, &pl->d_scalar, 2)) != RFD_OK) return bail(st);
-  if ((st = upload_tiles(pl, pl->gram_only)) != RFD_OK) return bail(st);
-  if ((st = upload_tiles(pl, pl->field_only)) != RFD_OK) return bail(st);
-  if ((st = upload_tiles(pl, pl->both)) != RFD_OK) return bail(st);
+  if (!pl->bf16) {
+    if ((st = upload_tiles(pl, pl->gram_only)) != RFD_OK) return bail(st);
+    if ((st = upload_tiles(pl, pl->field_only)) != RFD_OK) return bail(st);
+    if ((st = upload_tiles(pl, pl->both)) != RFD_OK) return bail(st);
+  }
   auto up = [&](void* dst, const void* src, size_t bytes) { return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice); };
   if ((ce = up(pl->d_omega_hi, whi.data(), whi.size() * 4)) != cudaSuccess ||
       (ce = up(pl->d_omega_lo, wlo.data(), wlo.size() * 4)) != cudaSuccess ||
@@ -482,20 +480,19 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
     cuda_fail("plan upload", ce);
     return bail(RFD_ECUDA);
   }
-  pl->stats.splits = pl->both.units.empty() ? 0 : (int)(pl->both.units.size() / pl->both.tiles.size());
-  if (pl->timing) {
-    pl->ring.resize(kRing);
-    for (auto& s : pl->ring)
-      for (cudaEvent_t& e : s.ev) e = nullptr;
-    for (auto& s : pl->ring)
-      for (cudaEvent_t& e : s.ev)
-        if ((ce = cudaEventCreate(&e)) != cudaSuccess) {
-          for (auto& s2 : pl->ring)
-            for (cudaEvent_t e2 : s2.ev)
-              if (e2) cudaEventDestroy(e2);
-          cuda_fail("event creation", ce);
-          return bail(RFD_ECUDA);
-        }
+  if (pl->bf16) {
+    if ((st = build_desc(pl)) != RFD_OK) return bail(st);
+    rfd_plan_s* self = pl;
+    if ((st = batch_build(&self, 1, pl->stream, &pl->self)) != RFD_OK) return bail(st);
+    pl->stats.splits = pl->desc.units[kModeGfi].empty() ? 0 : pl->desc.units[kModeGfi][0].nlanes;
+  } else {
+    pl->stats.splits = pl->both.units.empty() ? 0 : (int)(pl->both.units.size() / pl->both.tiles.size());
+  }
+  if (p.flags & RFD_FLAG_TIMING) {
+    if ((ce = pl->timing.init()) != cudaSuccess) {
+      cuda_fail("event creation", ce);
+      return bail(RFD_ECUDA);
+    }
   }
   *out = pl;
   return RFD_OK;
@@ -504,35 +501,16 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
 rfd_status rfd_plan_destroy(rfd_plan_t plan) {
   if (!plan) return RFD_OK;
   cudaStreamSynchronize(plan->stream);
-  for (auto& s : plan->ring)
-    for (cudaEvent_t e : s.ev) cudaEventDestroy(e);
+  if (plan->self) batch_free(plan->self);
+  plan->timing.destroy();
   plan_free(plan);
   delete plan;
   return RFD_OK;
 }
 
-static rfd_status features_step(rfd_plan_t pl, const float* d_points) {
-  StepScope t(pl, RFD_STEP_FEATURES);
-  RFD_CUDA(launch_features(d_points, pl->n, pl->n_pad, pl->d_omega_hi, pl->d_omega_lo, pl->h, pl->bf16, pl->d_psi,
-                           pl->stream));
-  return RFD_OK;
-}
-
-static rfd_status field_step(rfd_plan_t pl, const float* d_F, int c, int64_t ldF) {
-  StepScope t(pl, RFD_STEP_FIELD);
-  void* rows = static_cast<uint8_t*>(pl->d_psi) + (size_t)pl->m * pl->n_pad * (pl->bf16 ? 2 : 4);
-  RFD_CUDA(launch_fill_field_rows(d_F, ldF, c, pl->n, pl->n_pad, pl->cpad, pl->bf16, rows, pl->stream));
-  return RFD_OK;
-}
-
 rfd_status rfd_features(rfd_plan_t pl, const float* d_points) {
   if (!pl || !d_points) return fail(RFD_EINVAL, "null plan or points");
-  CallScope call(pl);
-  pl->have_G = false;
-  rfd_status s = features_step(pl, d_points);
-  if (s == RFD_OK) s = run_reductions(pl, pl->gram_only, 1);
-  if (s == RFD_OK) s = run_phi1(pl);
-  return s;
+  return run_plan(pl, kModeFeatures, d_points, nullptr, 1, 1, nullptr, 1);
 }
 
 rfd_status rfd_integrate(rfd_plan_t pl, const float* d_F, int32_t c, int64_t ldF, float* d_out, int64_t ldOut) {
@@ -540,11 +518,7 @@ rfd_status rfd_integrate(rfd_plan_t pl, const float* d_F, int32_t c, int64_t ldF
   rfd_status s = check_field_args(pl, d_F, c, ldF, d_out, ldOut);
   if (s != RFD_OK) return s;
   if (!pl->have_G) return fail(RFD_EINVAL, "rfd_features (or rfd_gfi) must run before rfd_integrate");
-  CallScope call(pl);
-  s = field_step(pl, d_F, c, ldF);
-  if (s == RFD_OK) s = run_reductions(pl, pl->field_only, c);
-  if (s == RFD_OK) s = apply_step(pl, d_F, c, ldF, d_out, ldOut);
-  return s;
+  return run_plan(pl, kModeIntegrate, nullptr, d_F, c, ldF, d_out, ldOut);
 }
 
 rfd_status rfd_gfi(rfd_plan_t pl, const float* d_points, const float* d_F, int32_t c, int64_t ldF, float* d_out,
@@ -552,14 +526,7 @@ rfd_status rfd_gfi(rfd_plan_t pl, const float* d_points, const float* d_F, int32
   if (!pl || !d_points) return fail(RFD_EINVAL, "null plan or points");
   rfd_status s = check_field_args(pl, d_F, c, ldF, d_out, ldOut);
   if (s != RFD_OK) return s;
-  CallScope call(pl);
-  pl->have_G = false;
-  s = features_step(pl, d_points);
-  if (s == RFD_OK) s = field_step(pl, d_F, c, ldF);
-  if (s == RFD_OK) s = run_reductions(pl, pl->both, c);
-  if (s == RFD_OK) s = run_phi1(pl);
-  if (s == RFD_OK) s = apply_step(pl, d_F, c, ldF, d_out, ldOut);
-  return s;
+  return run_plan(pl, kModeGfi, d_points, d_F, c, ldF, d_out, ldOut);
 }
 
 rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double* d_G, int32_t flags, void* cuda_stream,
@@ -567,6 +534,7 @@ rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double* d_G, in
   if (m < 1 || m > kMaxM) return fail(RFD_EINVAL, "m must be in [1, 4096]");
   if (!d_M || !d_G || d_M == d_G) return fail(RFD_EINVAL, "null or aliased M / G");
   if (!std::isfinite(lambda)) return fail(RFD_EINVAL, "lambda must be finite");
+  if (flags & ~RFD_FLAG_NATIVE_FP64) return fail(RFD_EINVAL, "unknown bits in flags");
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   rfd_plan_s tmp;  // only used as an allocation owner
   double* work = nullptr;
@@ -580,6 +548,7 @@ rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double* d_G, in
     plan_free(&tmp);
     return s;
   }
+  cudaMemsetAsync(ints, 0, 4 * sizeof(int), st);
   Phi1Info info{};
   s = phi1_fp64(m, lambda, d_M, d_G, work, ipiv, ints + 1, scalar, ints + 2, ints, (flags & RFD_FLAG_NATIVE_FP64) == 0,
                 st, &info);
@@ -623,22 +592,105 @@ rfd_status rfd_plan_export(rfd_plan_t pl, double* omega, double* r, double* G) {
 rfd_status rfd_plan_stats(rfd_plan_t pl, rfd_stats* out) {
   if (!pl || !out) return fail(RFD_EINVAL, "null plan or output");
   RFD_CUDA(cudaStreamSynchronize(pl->stream));
-  fold_timings(pl);
+  pl->timing.fold(pl->stream);
   *out = pl->stats;
-  for (int i = 0; i < RFD_NUM_STEPS; ++i)
-    out->step_ms[i] = pl->timed_calls ? pl->step_sum[i] / (double)pl->timed_calls : 0.0;
-  out->timed_calls = pl->timed_calls;
-  out->kernel_launches = pl->launches;
+  fill_stats(pl->timing, out);
   return RFD_OK;
 }
 
 rfd_status rfd_plan_stats_reset(rfd_plan_t pl) {
   if (!pl) return fail(RFD_EINVAL, "null plan");
   RFD_CUDA(cudaStreamSynchronize(pl->stream));
-  fold_timings(pl);
-  for (double& v : pl->step_sum) v = 0.0;
-  pl->timed_calls = 0;
-  pl->launches = 0;
+  pl->timing.reset(pl->stream);
+  return RFD_OK;
+}
+
+// ---- batches -------------------------------------------------------------------
+rfd_status rfd_batch_create(const rfd_plan_t* plans, int32_t count, int32_t flags, void* cuda_stream,
+                            rfd_batch_t* out) {
+  if (!plans || !out || count < 1) return fail(RFD_EINVAL, "null plans / output or count < 1");
+  if (flags & ~RFD_FLAG_TIMING) return fail(RFD_EINVAL, "unknown bits in flags");
+  *out = nullptr;
+  std::vector<rfd_plan_s*> v(plans, plans + count);
+  for (int i = 0; i < count; ++i) {
+    if (!v[i]) return fail(RFD_EINVAL, "null plan in batch");
+    if (!v[i]->bf16) return fail(RFD_EINVAL, "batches run the BF16 tensor-core form: plan " + std::to_string(i));
+    for (int j = 0; j < i; ++j)
+      if (v[j] == v[i]) return fail(RFD_EINVAL, "a plan appears twice in the batch");
+  }
+  auto* b = new (std::nothrow) rfd_batch_s();
+  if (!b) return fail(RFD_ENOMEM, "host allocation failed");
+  b->plans = v;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  rfd_status s = batch_build(v.data(), count, b->stream, &b->impl);
+  if (s == RFD_OK && (flags & RFD_FLAG_TIMING)) {
+    cudaError_t ce = b->timing.init();
+    if (ce != cudaSuccess) s = cuda_fail("event creation", ce);
+  }
+  if (s != RFD_OK) {
+    if (b->impl) batch_free(b->impl);
+    b->timing.destroy();
+    delete b;
+    return s;
+  }
+  *out = b;
+  return RFD_OK;
+}
+
+rfd_status rfd_batch_destroy(rfd_batch_t b) {
+  if (!b) return RFD_OK;
+  batch_free(b->impl);
+  b->timing.destroy();
+  delete b;
+  return RFD_OK;
+}
+
+static rfd_status batch_call(rfd_batch_t b, int mode, const rfd_batch_item* items) {
+  if (!b || !items) return fail(RFD_EINVAL, "null batch or items");
+  std::vector<CloudCall> calls(b->plans.size());
+  for (size_t k = 0; k < b->plans.size(); ++k) {
+    rfd_plan_s* pl = b->plans[k];
+    const rfd_batch_item& it = items[k];
+    if (mode != kModeIntegrate && !it.d_points) return fail(RFD_EINVAL, "null points for item " + std::to_string(k));
+    int c = 1;
+    if (mode != kModeFeatures) {
+      rfd_status s = check_field_args(pl, it.d_F, it.c, it.ldF, it.d_out, it.ldOut);
+      if (s != RFD_OK) return fail(s, "item " + std::to_string(k) + ": " + rfd_last_error());
+      if (mode == kModeIntegrate && !pl->have_G)
+        return fail(RFD_EINVAL, "item " + std::to_string(k) + ": features not computed");
+      c = it.c;
+    }
+    calls[k] = CloudCall{it.d_points, it.d_F, it.d_out, it.ldF, it.ldOut, c, 0};
+  }
+  CallScope call(&b->timing, b->stream);
+  return batch_run(b->impl, mode, calls.data(), &b->timing);
+}
+
+rfd_status rfd_batch_features(rfd_batch_t b, const rfd_batch_item* items) { return batch_call(b, kModeFeatures, items); }
+rfd_status rfd_batch_integrate(rfd_batch_t b, const rfd_batch_item* items) {
+  return batch_call(b, kModeIntegrate, items);
+}
+rfd_status rfd_batch_gfi(rfd_batch_t b, const rfd_batch_item* items) { return batch_call(b, kModeGfi, items); }
+
+rfd_status rfd_batch_sync(rfd_batch_t b) {
+  if (!b) return fail(RFD_EINVAL, "null batch");
+  RFD_CUDA(cudaStreamSynchronize(b->stream));
+  return batch_check_error(b->impl);
+}
+
+rfd_status rfd_batch_stats(rfd_batch_t b, rfd_stats* out) {
+  if (!b || !out) return fail(RFD_EINVAL, "null batch or output");
+  RFD_CUDA(cudaStreamSynchronize(b->stream));
+  b->timing.fold(b->stream);
+  *out = rfd_stats{};
+  fill_stats(b->timing, out);
+  return RFD_OK;
+}
+
+rfd_status rfd_batch_stats_reset(rfd_batch_t b) {
+  if (!b) return fail(RFD_EINVAL, "null batch");
+  RFD_CUDA(cudaStreamSynchronize(b->stream));
+  b->timing.reset(b->stream);
   return RFD_OK;
 }
 

@@ -1,0 +1,91 @@
+"""Batched integration (many clouds of uneven N and m in shared launches)
+against the CPU FP64 oracle and against each cloud integrated alone."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+import paper_2302_00942_gb300 as rfd  # noqa: E402
+
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+TOL = 1e-3
+
+
+def _specs(count=9, seed=4):
+    specs = synth.batched_specs(count=count, seed=seed, n_lo=500, n_hi=12000, ms=(64, 128, 256), c=8)
+    # uneven channel counts too
+    for k, s in enumerate(specs):
+        s.c = (1, 3, 8)[k % 3]
+    return specs
+
+
+def _lam(s):
+    return s.lam * s.m / s.n   # diffusion time in units of the estimator's mean eigenvalue
+
+
+def _plans(specs, stream):
+    return [rfd.Plan(s.n, s.m, s.eps, _lam(s), s.seed, max_channels=8, precision=rfd.RFD_BF16_TC, stream=stream)
+            for s in specs]
+
+
+def test_batch_gfi_matches_oracle_and_single_cloud_runs():
+    specs = _specs()
+    clouds = [synth.make_cloud(s) for s in specs]
+    stream = torch.cuda.current_stream(DEV)
+    plans = _plans(specs, stream)
+    batch = rfd.Batch(plans, stream=stream, timing=True)
+    items = [{"points": torch.from_numpy(p).to(DEV), "F": torch.from_numpy(F).to(DEV)} for p, F in clouds]
+    outs = batch.gfi(items)
+    batch.sync()
+    st = batch.stats()
+    assert st["timed_calls"] == 1 and st["kernel_launches"] > 0
+    for k, (s, (pts, F)) in enumerate(zip(specs, clouds)):
+        ref = oracle.rfd_gfi(pts, F, s.eps, _lam(s), s.m, s.seed)
+        got = outs[k].cpu().numpy()
+        err = oracle.rel_frobenius(got, ref)
+        inc = np.linalg.norm(ref - F) / np.linalg.norm(F)
+        print(f"cloud {k}: N={s.n} m={s.m} c={s.c} err={err:.2e} increment={inc:.2e}")
+        assert err <= TOL
+        # the same cloud alone (its own plan, a batch of one)
+        alone = plans[k].gfi(items[k]["points"], items[k]["F"])
+        plans[k].sync()
+        assert oracle.rel_frobenius(got, alone.cpu().numpy()) <= TOL
+    batch.close()
+    for p in plans:
+        p.close()
+
+
+def test_batch_warm_integrate_reuses_resident_G():
+    specs = _specs(count=5, seed=7)
+    clouds = [synth.make_cloud(s) for s in specs]
+    stream = torch.cuda.current_stream(DEV)
+    plans = _plans(specs, stream)
+    batch = rfd.Batch(plans, stream=stream)
+    batch.features([{"points": torch.from_numpy(p).to(DEV)} for p, _ in clouds])
+    for rep in range(2):
+        fields = [synth.gaussian_field(s.n, s.c, 1000 + rep, k) for k, s in enumerate(specs)]
+        outs = batch.integrate([{"F": torch.from_numpy(F).to(DEV)} for F in fields])
+        batch.sync()
+        for k, s in enumerate(specs):
+            ref = oracle.rfd_gfi(clouds[k][0], fields[k], s.eps, _lam(s), s.m, s.seed)
+            assert oracle.rel_frobenius(outs[k].cpu().numpy(), ref) <= TOL
+    batch.close()
+    for p in plans:
+        p.close()
+
+
+def test_batch_rejects_fp32_and_repeated_plans():
+    s = _specs(count=2)
+    p16 = rfd.Plan(s[0].n, s[0].m, s[0].eps, _lam(s[0]), 0, precision=rfd.RFD_BF16_TC)
+    p32 = rfd.Plan(s[1].n, s[1].m, s[1].eps, _lam(s[1]), 0, precision=rfd.RFD_FP32_PLAIN)
+    with pytest.raises(rfd.RfdError) as e:
+        rfd.Batch([p16, p32])
+    assert e.value.status == rfd.RFD_EINVAL
+    with pytest.raises(rfd.RfdError) as e:
+        rfd.Batch([p16, p16])
+    assert e.value.status == rfd.RFD_EINVAL
+    p16.close()
+    p32.close()
