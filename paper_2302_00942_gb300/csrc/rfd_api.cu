@@ -147,6 +147,27 @@ rfd_status upload_tiles(rfd_plan_s* pl, TileSet& ts) {
 }
 
 // ---- BF16 tensor-core form: the plan's batched-path descriptors -------------
+// Number of compute tiles of a mode (see build_desc) and the partial slots the
+// plan needs: max over modes of tiles x lanes (lanes = SMs / tiles, >= 1).
+int tc_tiles(int m, int mode) {
+  if (mode == kModeIntegrate) return (m + kTcBM - 1) / kTcBM;
+  int t = 0;
+  for (int i0 = 0; i0 < m; i0 += kTcBM)
+    for (int j0 = 0; j0 < m; j0 += kTcBNMax)
+      if (j0 + std::min(kTcBNMax, m - j0) - 1 >= i0) ++t;
+  return t;
+}
+
+int tc_partial_slots(int m, int64_t n_pad, int sms) {
+  int slots = 1;
+  for (int mode = 0; mode < 3; ++mode) {
+    const int T = tc_tiles(m, mode);
+    const int L = (int)std::max<int64_t>(1, std::min<int64_t>(n_pad / kTcBK, sms / std::max(T, 1)));
+    slots = std::max(slots, T * L);
+  }
+  return slots;
+}
+
 // Compute tiles: 128 feature rows x up to 256 Gram rows on the upper triangle
 // of Phi^T Phi; a row block's field part (Phi^T F, cpad columns) rides on the
 // tile whose Gram block holds the row block's diagonal (or on a field-only
@@ -438,7 +459,7 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
     build_tiles_simt(pl, false, true, pl->field_only);
     build_tiles_simt(pl, true, true, pl->both);
   }
-  const int slots = pl->bf16 ? std::max(pl->sms, 1) + 64
+  const int slots = pl->bf16 ? tc_partial_slots(pl->m, pl->n_pad, pl->sms)
                              : std::max({pl->gram_only.slots, pl->field_only.slots, pl->both.slots});
   pl->slot_elems = pl->bf16 ? (int64_t)kTcBM * kTcLd : (int64_t)kSimtTile * kSimtTile;
   pl->rows_alloc = (int)std::max<int64_t>(round_up(p.m, 128), p.m + round_up(pl->cpad, 128));
