@@ -86,6 +86,9 @@ typedef struct rfd_plan_s* rfd_plan_t;
 #define RFD_FLAG_TIMING 1       /* record CUDA events around every step (see rfd_stats.step_ms) */
 #define RFD_FLAG_NATIVE_FP64 2  /* step a4 products in native FP64 instead of the FP64-accurate
                                    Ozaki-split emulation on the BF16 tensor cores (the default) */
+#define RFD_FLAG_GRAPH 4        /* batches only: replay each call's launches from CUDA graphs,
+                                   captured on first use per call shape (per-step timings are
+                                   then not recorded) */
 
 /* Indices of rfd_stats.step_ms */
 enum {
@@ -149,9 +152,10 @@ RFD_API rfd_status rfd_plan_destroy(rfd_plan_t plan);
  * reduction over N, and G = lambda phi1(lambda M) in FP64 (scaling-and-
  * squaring diagonal Pade on the block-triangular augmented matrix
  * [[lambda M, I], [0, 0]]).  Phi and G stay resident in the plan for later
- * rfd_integrate calls.  Synchronises the stream once (the Pade degree and the
- * number of squarings are chosen on the host from ||lambda M||_1).
- * RFD_ENUMERIC if G is not finite. */
+ * rfd_integrate calls.  The host waits once on the stream, for the number of
+ * squarings (chosen from ||lambda M||_1).  A G that is not finite is reported
+ * as RFD_ENUMERIC: by this call in the FP32 plain form or with
+ * RFD_FLAG_NATIVE_FP64, by the next rfd_sync in the BF16 tensor-core form. */
 RFD_API rfd_status rfd_features(rfd_plan_t plan, const float* d_points);
 
 /* Inference (Sec. 2.4: "linear in N, quadratic in m"), steps a3(Y)-a6, on
@@ -196,7 +200,9 @@ RFD_API rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double*
 RFD_API rfd_status rfd_phi1_noalloc(int32_t m, double lambda, const double* d_M, double* d_G, int32_t flags,
                                     void* cuda_stream, rfd_stats* stats_out);
 
-/* Wait for all of the plan's queued device work. */
+/* Wait for all of the plan's queued device work.  Reports (and clears) what
+ * the device recorded since the last rfd_sync: RFD_ETIMEDOUT if a bounded
+ * device-side wait ran out, RFD_ENUMERIC if G was not finite (BF16 form). */
 RFD_API rfd_status rfd_sync(rfd_plan_t plan);
 
 /* Copy the plan's random features and (if computed) G to HOST buffers:
@@ -231,15 +237,18 @@ typedef struct {
 } rfd_batch_item;
 
 /* Build a batch over `count` plans (caller-owned array, copied).  flags:
- * RFD_FLAG_TIMING or 0.  Allocates the batch's device tables; RFD_EINVAL for
- * FP32 plans or a repeated plan. */
+ * RFD_FLAG_TIMING, RFD_FLAG_GRAPH or 0.  Allocates the batch's device tables
+ * (one block) and pinned staging (one block); RFD_EINVAL for FP32 plans or a
+ * repeated plan. */
 RFD_API rfd_status rfd_batch_create(const rfd_plan_t* plans, int32_t count, int32_t flags, void* cuda_stream,
                                     rfd_batch_t* out);
 RFD_API rfd_status rfd_batch_destroy(rfd_batch_t batch);
 /* Batched rfd_features / rfd_integrate / rfd_gfi: items[k] belongs to plans[k].
- * features and gfi synchronise the batch stream once (the per-cloud scaling
- * of step a4 is chosen on the host) and return RFD_ENUMERIC naming the clouds
- * whose G is not finite. */
+ * features and gfi wait once on the batch stream for the largest per-cloud
+ * squaring count of step a4 (each cloud's count is chosen on the device).
+ * rfd_batch_sync returns RFD_ENUMERIC naming the clouds whose G was not
+ * finite since the last rfd_batch_sync (the other clouds' results stand),
+ * or RFD_ETIMEDOUT if a bounded device-side wait ran out. */
 RFD_API rfd_status rfd_batch_features(rfd_batch_t batch, const rfd_batch_item* items);
 RFD_API rfd_status rfd_batch_integrate(rfd_batch_t batch, const rfd_batch_item* items);
 RFD_API rfd_status rfd_batch_gfi(rfd_batch_t batch, const rfd_batch_item* items);
@@ -247,6 +256,86 @@ RFD_API rfd_status rfd_batch_sync(rfd_batch_t batch);
 /* Step timings / launch count of the batch (RFD_FLAG_TIMING), as rfd_plan_stats. */
 RFD_API rfd_status rfd_batch_stats(rfd_batch_t batch, rfd_stats* out);
 RFD_API rfd_status rfd_batch_stats_reset(rfd_batch_t batch);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop for GFI requests (the paper's graph field
+ * integration, Sec. 2.4, one request = one point cloud and one field F).
+ * rfd_submit only queues; executor threads admit queued requests in arrival
+ * order as device memory allows (a fixed budget, allocated once, from which
+ * plans and batch tables are carved), batch the admitted requests of all sizes
+ * that are waiting when an executor is free, and run them on the BF16
+ * tensor-core batched path.  Several batches are in flight at once on
+ * separate streams, so requests that arrive while others run are started as
+ * soon as an executor and memory free up.  A request that names a resident
+ * cloud reuses its features Phi and its G (only steps a3(Y)-a6 run); clouds
+ * submitted with keep = 1 stay resident until memory is needed (least
+ * recently used first) or the server is destroyed.
+ * --------------------------------------------------------------------------- */
+typedef struct rfd_server_s* rfd_server_t;
+
+typedef struct {
+  size_t mem_budget;   /* device bytes for plans, resident clouds and batch tables   */
+  int32_t max_queue;   /* queued + running requests before RFD_EBUSY (0: 4096)       */
+  int32_t max_batch;   /* requests per batch (0: 256)                                */
+  int32_t executors;   /* batches in flight at once, one stream each (0: 2, max 8)   */
+  int32_t reserved_;
+} rfd_server_config;
+
+typedef struct {
+  const float* d_points; /* N x 3 float32 device; may be NULL when `cloud` is resident   */
+  const float* d_F;      /* N x c float32 device, leading dimension ldF                 */
+  float* d_out;          /* N x c float32 device, leading dimension ldOut; may equal d_F */
+  int64_t n;
+  int64_t ldF, ldOut;
+  int32_t m;             /* random features (even); ignored for a resident cloud       */
+  int32_t c;             /* 1 <= c <= 256                                               */
+  double eps, lambda;    /* as rfd_params                                               */
+  uint64_t seed;
+  uint64_t cloud;        /* 0, or an id returned by an earlier request: reuse that cloud */
+  int32_t keep;          /* 1: keep this request's cloud resident, its id in rfd_result */
+  int32_t max_channels;  /* channel capacity of a kept cloud for later requests (0: c)  */
+} rfd_request;
+
+typedef struct {
+  int32_t status;        /* the request's own outcome (an rfd_status)                   */
+  int32_t reused;        /* 1 if a resident cloud's Phi and G were reused              */
+  uint64_t cloud;        /* id of the resident cloud (keep = 1 or reuse), else 0       */
+  double queue_ms;       /* rfd_submit -> its batch's launch                            */
+  double latency_ms;     /* rfd_submit -> the server saw its batch complete            */
+  int32_t batch_size;    /* requests in the batch that ran it                          */
+  int32_t reserved_;
+} rfd_result;
+
+typedef struct {
+  int64_t submitted, completed, rejected, batches, reused, evicted, resident;
+  int64_t mem_used, mem_peak, mem_budget;  /* device bytes */
+  int64_t kernel_launches;
+} rfd_server_stats;
+
+/* Create a server on the current device.  cfg: host, may be NULL (then a
+ * budget of mem_budget bytes and the defaults above).  Allocates the whole
+ * budget up front (RFD_ENOMEM if it cannot) and starts the executor threads. */
+RFD_API rfd_status rfd_server_create(size_t mem_budget, const rfd_server_config* cfg, rfd_server_t* out);
+
+/* Stop the server: queued requests that have not started complete with
+ * status RFD_EBUSY; running batches finish first.  Frees all of its memory. */
+RFD_API rfd_status rfd_server_destroy(rfd_server_t server);
+
+/* Queue one request (host struct, copied).  Never blocks on the device.
+ * *ticket receives the id to poll.  RFD_EINVAL for invalid arguments or an
+ * unknown cloud id with no points; RFD_EBUSY when admission is refused: the
+ * queue is full, or the request alone needs more than the memory budget.
+ * The request's device buffers must stay valid until rfd_poll reports it. */
+RFD_API rfd_status rfd_submit(rfd_server_t server, const rfd_request* request, uint64_t* ticket);
+
+/* Wait up to timeout_us microseconds (0: do not wait) for a ticket.
+ * RFD_OK: done, *out holds its result and the ticket is retired;
+ * RFD_ENOTREADY: not done and timeout_us == 0; RFD_ETIMEDOUT: not done when
+ * the wait ran out; RFD_EINVAL: unknown or retired ticket. */
+RFD_API rfd_status rfd_poll(rfd_server_t server, uint64_t ticket, int32_t timeout_us, rfd_result* out);
+
+/* Counters of the server (host struct). */
+RFD_API rfd_status rfd_server_stats_get(rfd_server_t server, rfd_server_stats* out);
 
 /* Thread-local description of the last error on this thread ("" if none). */
 RFD_API const char* rfd_last_error(void);

@@ -13,8 +13,8 @@
 extern "C" {
 #endif
 
-/* Make the k-th device allocation performed by the library from now on fail
- * (k = 0: the next one), as if cudaMalloc had returned out-of-memory; the
+/* Make the k-th device or pinned allocation performed by the library from
+ * now on fail (k = 0: the next one), as if cudaMalloc had returned out-of-memory; the
  * failing entry point returns RFD_ENOMEM and releases what it had allocated.
  * k < 0 disables the hook.  Process-wide, not thread-safe; tests only. */
 RFD_API void rfd_debug_fail_alloc_after(int32_t k);
@@ -22,12 +22,17 @@ RFD_API void rfd_debug_fail_alloc_after(int32_t k);
 /* The FP64 GEMM building block of step a4 on its own:
  * C = alpha A B + beta C for row-major float64 DEVICE buffers (A: M x K, lda;
  * B: K x N, ldb; C: M x N, ldc).  method 0: native FP64 kernel; method 1: the
- * FP64-accurate Ozaki-split emulation on the BF16 tensor cores (K <= 1024,
+ * FP64-accurate Ozaki-split emulation on the BF16 tensor cores (K <= 4096,
  * sm_103 only, else RFD_ENOTSUP).  Allocates its workspace, synchronises
  * `cuda_stream`, and returns RFD_ETIMEDOUT if a bounded device wait ran out. */
 RFD_API rfd_status rfd_debug_dgemm(int32_t method, int32_t M, int32_t N, int32_t K, double alpha, const double* A,
                                    int32_t lda, const double* B, int32_t ldb, double beta, double* C, int32_t ldc,
                                    void* cuda_stream);
+
+/* Hold (paused = 1) or release (0) a server's executors: while held they
+ * start no new batch (batches already running finish), so a test can make a
+ * poll wait run out deterministically. */
+RFD_API void rfd_debug_server_pause(rfd_server_t server, int32_t paused);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,8 @@ __all__ = [
     "lib", "lib_path", "rfd_sample_frequencies", "rfd_plan", "rfd_plan_destroy", "rfd_features",
     "rfd_integrate", "rfd_gfi", "rfd_phi1", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
     "rfd_version", "RFD_FLAG_TIMING", "STEP_NAMES", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "Plan", "Batch", "rfd_batch_item", "HEADER_SYMBOLS",
-    "RFD_FLAG_NATIVE_FP64",
+    "RFD_FLAG_NATIVE_FP64", "RFD_FLAG_GRAPH", "Server", "rfd_request", "rfd_result", "rfd_server_config",
+    "rfd_server_stats",
 ]
 
 RFD_OK, RFD_EINVAL, RFD_ENOMEM, RFD_ECUDA, RFD_ENOTREADY, RFD_ETIMEDOUT, RFD_ENUMERIC, RFD_EBUSY, RFD_ENOTSUP = range(9)
@@ -42,6 +43,7 @@ class rfd_params(ctypes.Structure):
 
 RFD_FLAG_TIMING = 1
 RFD_FLAG_NATIVE_FP64 = 2
+RFD_FLAG_GRAPH = 4
 STEP_NAMES = ("features", "field", "gram", "reduce", "phi1", "small", "apply")
 
 
@@ -56,6 +58,30 @@ class rfd_batch_item(ctypes.Structure):
     _fields_ = [("d_points", ctypes.c_void_p), ("d_F", ctypes.c_void_p), ("d_out", ctypes.c_void_p),
                 ("c", ctypes.c_int32), ("reserved_", ctypes.c_int32), ("ldF", ctypes.c_int64),
                 ("ldOut", ctypes.c_int64)]
+
+
+class rfd_server_config(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_size_t), ("max_queue", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("executors", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+
+
+class rfd_request(ctypes.Structure):
+    _fields_ = [("d_points", ctypes.c_void_p), ("d_F", ctypes.c_void_p), ("d_out", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("ldF", ctypes.c_int64), ("ldOut", ctypes.c_int64), ("m", ctypes.c_int32),
+                ("c", ctypes.c_int32), ("eps", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("cloud", ctypes.c_uint64), ("keep", ctypes.c_int32),
+                ("max_channels", ctypes.c_int32)]
+
+
+class rfd_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reused", ctypes.c_int32), ("cloud", ctypes.c_uint64),
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("batch_size", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
+
+
+class rfd_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "rejected", "batches", "reused", "evicted",
+                                               "resident", "mem_used", "mem_peak", "mem_budget", "kernel_launches")]
 
 
 def _stats_dict(s: "rfd_stats") -> dict:
@@ -102,6 +128,12 @@ def _load():
         "rfd_batch_sync": (I32, [P]),
         "rfd_batch_stats": (I32, [P, ctypes.POINTER(rfd_stats)]),
         "rfd_batch_stats_reset": (I32, [P]),
+        "rfd_server_create": (I32, [ctypes.c_size_t, ctypes.POINTER(rfd_server_config), ctypes.POINTER(P)]),
+        "rfd_server_destroy": (I32, [P]),
+        "rfd_submit": (I32, [P, ctypes.POINTER(rfd_request), ctypes.POINTER(U64)]),
+        "rfd_poll": (I32, [P, U64, I32, ctypes.POINTER(rfd_result)]),
+        "rfd_server_stats_get": (I32, [P, ctypes.POINTER(rfd_server_stats)]),
+        "rfd_debug_server_pause": (None, [P, I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -116,7 +148,8 @@ HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_plan", "rfd_plan_destroy", "rfd
                   "rfd_gfi", "rfd_phi1", "rfd_phi1_noalloc", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
                   "rfd_version", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "rfd_batch_create",
                   "rfd_batch_destroy", "rfd_batch_features", "rfd_batch_integrate", "rfd_batch_gfi",
-                  "rfd_batch_sync", "rfd_batch_stats", "rfd_batch_stats_reset")
+                  "rfd_batch_sync", "rfd_batch_stats", "rfd_batch_stats_reset", "rfd_server_create",
+                  "rfd_server_destroy", "rfd_submit", "rfd_poll", "rfd_server_stats_get", "rfd_debug_server_pause")
 
 
 def rfd_last_error() -> str:
@@ -304,14 +337,14 @@ class Batch:
     tensor, "out": (N, c) tensor or None}; all float32 CUDA, row-major.
     """
 
-    def __init__(self, plans, stream=None, timing=False):
+    def __init__(self, plans, stream=None, timing=False, graph=False):
         self.plans = list(plans)
         self.handle = None
         arr = (ctypes.c_void_p * len(self.plans))(*[p.handle for p in self.plans])
         h = ctypes.c_void_p()
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
-        _check(lib.rfd_batch_create(arr, len(self.plans), RFD_FLAG_TIMING if timing else 0, s, ctypes.byref(h)),
-               "rfd_batch_create")
+        flags = (RFD_FLAG_TIMING if timing else 0) | (RFD_FLAG_GRAPH if graph else 0)
+        _check(lib.rfd_batch_create(arr, len(self.plans), flags, s, ctypes.byref(h)), "rfd_batch_create")
         self.handle = h.value
 
     def _items(self, items, need_f):
@@ -361,6 +394,66 @@ class Batch:
     def close(self):
         if self.handle:
             _check(lib.rfd_batch_destroy(self.handle), "rfd_batch_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owning wrapper of an rfd_server_t (the GFI request loop, include/rfd.h).
+
+    submit() takes float32 CUDA tensors (points (N, 3), F and out (N, c)) that
+    must stay alive until poll() reports the ticket; it returns the ticket.
+    poll() returns (status, result dict or None).
+    """
+
+    def __init__(self, mem_budget, max_queue=0, max_batch=0, executors=0):
+        self.handle = None
+        cfg = rfd_server_config(mem_budget=int(mem_budget), max_queue=max_queue, max_batch=max_batch,
+                                executors=executors)
+        h = ctypes.c_void_p()
+        _check(lib.rfd_server_create(int(mem_budget), ctypes.byref(cfg), ctypes.byref(h)), "rfd_server_create")
+        self.handle = h.value
+
+    def submit(self, F, out, points=None, m=0, eps=0.0, lam=0.0, seed=0, cloud=0, keep=False, max_channels=0,
+               n=None):
+        r = rfd_request(d_points=_dptr(points) if points is not None else None, d_F=_dptr(F), d_out=_dptr(out),
+                        n=int(F.shape[0] if n is None else n), ldF=F.stride(0), ldOut=out.stride(0), m=m,
+                        c=F.shape[1], eps=eps, lambda_=lam, seed=seed, cloud=cloud, keep=1 if keep else 0,
+                        max_channels=max_channels)
+        t = ctypes.c_uint64()
+        _check(lib.rfd_submit(self.handle, ctypes.byref(r), ctypes.byref(t)), "rfd_submit")
+        return t.value
+
+    def try_submit(self, *args, **kw):
+        """submit(), but returns (status, ticket or None) instead of raising."""
+        try:
+            return RFD_OK, self.submit(*args, **kw)
+        except RfdError as e:
+            return e.status, None
+
+    def poll(self, ticket, timeout_us=0):
+        res = rfd_result()
+        st = lib.rfd_poll(self.handle, ticket, int(timeout_us), ctypes.byref(res))
+        if st != RFD_OK:
+            return st, None
+        return st, {k: getattr(res, k) for k, _ in rfd_result._fields_ if k != "reserved_"}
+
+    def stats(self):
+        s = rfd_server_stats()
+        _check(lib.rfd_server_stats_get(self.handle, ctypes.byref(s)), "rfd_server_stats_get")
+        return {k: getattr(s, k) for k, _ in rfd_server_stats._fields_}
+
+    def pause(self, paused=True):
+        lib.rfd_debug_server_pause(self.handle, 1 if paused else 0)
+
+    def close(self):
+        if self.handle:
+            _check(lib.rfd_server_destroy(self.handle), "rfd_server_destroy")
             self.handle = None
 
     def __del__(self):

@@ -56,6 +56,9 @@ features_batched_kernel(const FeatJob* __restrict__ jobs, const int* __restrict_
     valid[q] = (p0 + q) < jb.n;
 #pragma unroll
     for (int d = 0; d < 3; ++d) x[q][d] = valid[q] ? pts[(p0 + q) * 3 + d] : 0.f;
+    if (byi == 0 && valid[q])  // the cloud's own copy of its points, for the apply
+#pragma unroll
+      for (int d = 0; d < 3; ++d) jb.xyz[(p0 + q) * 3 + d] = x[q][d];
   }
   const float two_pi = 6.283185307179586f;
   for (int jj = 0; jj < jn; ++jj) {
@@ -74,28 +77,30 @@ features_batched_kernel(const FeatJob* __restrict__ jobs, const int* __restrict_
   }
 }
 
-__global__ void fill_batched_kernel(const FillJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
-                                    const CloudCall* __restrict__ calls) {
+// F^T rows of the feature buffer: one point per thread, every row of the
+// point written by it (coalesced along the points); points >= N and rows
+// beyond the channels get zeros.
+__global__ void __launch_bounds__(256)
+fill_batched_kernel(const FillJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
+                    const CloudCall* __restrict__ calls) {
   const int j = find_job(prefix, count, blockIdx.x);
   const FillJob jb = jobs[j];
-  const int local = blockIdx.x - prefix[j];
-  const int bxi = local % jb.bx, cyi = local / jb.bx;
   const CloudCall cc = calls[jb.cloud];
+  const int64_t p = (int64_t)(blockIdx.x - prefix[j]) * 256 + threadIdx.x;
+  if (p >= jb.n_pad) return;
   auto* rows = reinterpret_cast<__nv_bfloat16*>(jb.rows);
-  __shared__ float tile[32][33];
-  const int64_t n0 = (int64_t)bxi * 32;
-  const int c0 = cyi * 32;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int64_t pn = n0 + i;
-    const int ch = c0 + threadIdx.x;
-    tile[i][threadIdx.x] = (pn < jb.n && ch < cc.c) ? cc.F[pn * cc.ldF + ch] : 0.f;
+  const int c = cc.c;
+  const bool valid = p < jb.n;
+  const float* f = cc.F + (valid ? p * cc.ldF : 0);
+  for (int ch = 0; ch < c; ++ch) {
+    const float v = valid ? f[ch] : 0.f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    rows[(size_t)ch * jb.n_pad + p] = hi;
+    // row c + ch: the lo part of channel ch (fsplit)
+    if (jb.fsplit) rows[(size_t)(c + ch) * jb.n_pad + p] = __float2bfloat16_rn(v - __bfloat162float(hi));
   }
-  __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int ch = c0 + i;
-    const int64_t pn = n0 + threadIdx.x;
-    if (ch < jb.cpad && pn < jb.n_pad) rows[(size_t)ch * jb.n_pad + pn] = __float2bfloat16_rn(tile[threadIdx.x][i]);
-  }
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  for (int row = jb.fsplit ? 2 * c : c; row < jb.cpad; ++row) rows[(size_t)row * jb.n_pad + p] = zero;
 }
 
 // One thread per tile element; lanes summed in order (deterministic) in FP64.
@@ -115,7 +120,13 @@ __global__ void reduce_batched_kernel(const RedTile* __restrict__ tiles, const C
     if (f != g) t.M[(size_t)g * t.m + f] = t.ob[g] * s * t.oa[f];
   } else {
     const int c = calls[t.cloud].c;
-    if (col < c) t.Y[(size_t)f * c + col] = t.ob[f] * s;
+    if (col < c) {
+      if (t.fsplit) {  // add the lo column of the same channel
+        const float* q = t.part + (int64_t)r * t.ld + t.col_off + c + col;
+        for (int u = 0; u < t.count; ++u) s += (double)q[(int64_t)u * t.slot_elems];
+      }
+      t.Y[(size_t)f * c + col] = t.ob[f] * s;
+    }
   }
 }
 
@@ -143,43 +154,70 @@ __global__ void small_batched_kernel(const ApplyJob* __restrict__ jobs, const in
   }
 }
 
-// out[n, ch] = F[n, ch] + sum_f Psi[f][n] Z[f, ch]: one point per thread
-// (coalesced Psi reads along n), CG channels per thread, Z through shared memory.
+// out[n, ch] = F[n, ch] + sum_j (cos(2 pi w_j^T x_n) Z[j, ch] + sin(2 pi w_j^T x_n) Z[h + j, ch]):
+// the features are recomputed in FP32 from the cloud's copy of its points
+// instead of read back from the BF16 Psi, so the apply carries no BF16
+// rounding and reads only points, F and out.  The angle in cycles: each
+// product w_d x_d is split exactly (FMA) and its integer part removed before
+// the sum, so r = frac(w^T x) has an absolute error ~2^-23 whatever |w^T x|;
+// MUFU sin/cos of 2 pi r (|2 pi r| <= pi) add ~4e-7.  One point per thread, CG
+// channels per thread; frequencies and Z rows of a 64-frequency chunk in
+// shared memory.  F[n] is read before out[n] is written by the same thread.
 template <int CG>
 __global__ void __launch_bounds__(256)
 apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
                      const CloudCall* __restrict__ calls) {
   constexpr int kChunk = 64;
-  __shared__ float zs[kChunk][CG];
+  __shared__ float wh[kChunk][3], wl[kChunk][3];
+  __shared__ float zc[kChunk][CG], zsn[kChunk][CG];
   const int j = find_job(prefix, count, blockIdx.x);
   const ApplyJob jb = jobs[j];
   const CloudCall cc = calls[jb.cloud];
   const int local = blockIdx.x - prefix[j];
   const int bxi = local % jb.bx, cgi = local / jb.bx;
-  const auto* psi = reinterpret_cast<const __nv_bfloat16*>(jb.psi);
+  const int h = jb.m / 2;
   const int64_t p = (int64_t)bxi * 256 + threadIdx.x;
+  const bool valid = p < jb.n;
+  const float x0 = valid ? jb.xyz[p * 3 + 0] : 0.f;
+  const float x1 = valid ? jb.xyz[p * 3 + 1] : 0.f;
+  const float x2 = valid ? jb.xyz[p * 3 + 2] : 0.f;
   const int ch0 = cgi * CG;
   const int cg = min(CG, cc.c - ch0);
   float acc[CG];
 #pragma unroll
   for (int q = 0; q < CG; ++q) acc[q] = 0.f;
-  for (int f0 = 0; f0 < jb.m; f0 += kChunk) {
-    const int fn = min(kChunk, jb.m - f0);
+  const float two_pi = 6.283185307179586f;
+  for (int f0 = 0; f0 < h; f0 += kChunk) {
+    const int fn = min(kChunk, h - f0);
     __syncthreads();
+    for (int i = threadIdx.x; i < kChunk * 3; i += blockDim.x) {
+      const int fr = i / 3, d = i % 3;
+      wh[fr][d] = fr < fn ? jb.omega_hi[(size_t)(f0 + fr) * 3 + d] : 0.f;
+      wl[fr][d] = fr < fn ? jb.omega_lo[(size_t)(f0 + fr) * 3 + d] : 0.f;
+    }
     for (int i = threadIdx.x; i < kChunk * CG; i += blockDim.x) {
       const int fr = i / CG, q = i % CG;
-      zs[fr][q] = (fr < fn && q < cg) ? jb.Z[(size_t)(f0 + fr) * cc.c + ch0 + q] : 0.f;
+      const bool ok = fr < fn && q < cg;
+      zc[fr][q] = ok ? jb.Z[(size_t)(f0 + fr) * cc.c + ch0 + q] : 0.f;
+      zsn[fr][q] = ok ? jb.Z[(size_t)(h + f0 + fr) * cc.c + ch0 + q] : 0.f;
     }
     __syncthreads();
-    if (p < jb.n) {
+    if (valid) {
       for (int fr = 0; fr < fn; ++fr) {
-        const float v = __bfloat162float(psi[(size_t)(f0 + fr) * jb.n_pad + p]);
+        const float a0 = wh[fr][0] * x0, a1 = wh[fr][1] * x1, a2 = wh[fr][2] * x2;
+        const float e0 = fmaf(wl[fr][0], x0, fmaf(wh[fr][0], x0, -a0));
+        const float e1 = fmaf(wl[fr][1], x1, fmaf(wh[fr][1], x1, -a1));
+        const float e2 = fmaf(wl[fr][2], x2, fmaf(wh[fr][2], x2, -a2));
+        float r = ((a0 - rintf(a0)) + (a1 - rintf(a1))) + ((a2 - rintf(a2)) + ((e0 + e1) + e2));
+        r -= rintf(r);
+        const float ang = two_pi * r;
+        const float cs = __cosf(ang), sn = __sinf(ang);
 #pragma unroll
-        for (int q = 0; q < CG; ++q) acc[q] = fmaf(v, zs[fr][q], acc[q]);
+        for (int q = 0; q < CG; ++q) acc[q] = fmaf(cs, zc[fr][q], fmaf(sn, zsn[fr][q], acc[q]));
       }
     }
   }
-  if (p < jb.n)
+  if (valid)
     for (int q = 0; q < cg; ++q) {
       const float fv = cc.F[p * cc.ldF + ch0 + q];
       cc.out[p * cc.ldOut + ch0 + q] = fv + acc[q];
@@ -233,6 +271,41 @@ __global__ void bnorm1_kernel(const PhiCloud* __restrict__ pcs, int slot, unsign
   }
 }
 
+// Squarings of each cloud (degree-5 rule): s = 0 when ||X||_1 <= theta, else the
+// least s with 2^-s ||X||_1 <= theta, found exactly from the binary exponent of
+// ||X||_1 / theta.  Writes s and 2^-s into the cloud table, s into sv[k] and
+// the largest s into sv[count].  A cloud whose norm is not finite or needs more
+// than max_s squarings is flagged (and runs with s = 0: its G is not used).
+__global__ void bselect_kernel(PhiCloud* __restrict__ pcs, int count, const double* __restrict__ norms,
+                               double theta, int max_s, int* __restrict__ sv) {
+  __shared__ int smax;
+  if (threadIdx.x == 0) smax = 0;
+  __syncthreads();
+  int mx = 0;
+  for (int k = threadIdx.x; k < count; k += blockDim.x) {
+    const double nrm = norms[k];
+    bool bad = !isfinite(nrm);
+    int s = 0;
+    if (!bad && nrm > theta) {
+      int e = 0;
+      const double f = frexp(nrm / theta, &e);  // nrm / theta = f 2^e, f in [1/2, 1)
+      s = (f == 0.5) ? e - 1 : e;
+      bad = s > max_s;
+    }
+    if (bad) {
+      s = 0;
+      atomicExch(pcs[k].flag, 1);
+    }
+    pcs[k].s = s;
+    pcs[k].scale = ldexp(1.0, -s);
+    sv[k] = s;
+    mx = max(mx, s);
+  }
+  atomicMax(&smax, mx);
+  __syncthreads();
+  if (threadIdx.x == 0) sv[count] = smax;
+}
+
 __global__ void bfinite_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count, int slot) {
   const int j = find_job(prefix, count, blockIdx.x);
   const PhiCloud pc = pcs[j];
@@ -253,7 +326,7 @@ cudaError_t launch_features_batched(const FeatJob* jobs, const int* prefix, int 
 cudaError_t launch_fill_batched(const FillJob* jobs, const int* prefix, int count, int total_blocks,
                                 const CloudCall* calls, cudaStream_t st) {
   if (total_blocks <= 0) return cudaSuccess;
-  fill_batched_kernel<<<total_blocks, dim3(32, 8), 0, st>>>(jobs, prefix, count, calls);
+  fill_batched_kernel<<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls);
   return launched();
 }
 
@@ -300,6 +373,12 @@ cudaError_t launch_bnorm1(const PhiCloud* pc, int count, int max_m, int slot, do
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((max_m + 31) / 32), (unsigned)count);
   bnorm1_kernel<<<grid, dim3(32, 32), 0, st>>>(pc, slot, reinterpret_cast<unsigned long long*>(norms));
+  return launched();
+}
+
+cudaError_t launch_bselect(PhiCloud* pc, int count, const double* norms, double theta, int max_s, int* sv,
+                           cudaStream_t st) {
+  bselect_kernel<<<1, 256, 0, st>>>(pc, count, norms, theta, max_s, sv);
   return launched();
 }
 

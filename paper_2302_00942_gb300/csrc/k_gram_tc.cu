@@ -51,7 +51,7 @@ struct Smem {
 
 __global__ void __launch_bounds__(kThreads, 1)
 gram_tc_kernel(const CUtensorMap* __restrict__ maps, const TcUnit* __restrict__ units, int stages, int stage_bytes,
-               int* err) {
+               int kb0, int kb_len, int* err) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
   const uint32_t base = (raw_addr + 1023u) & ~1023u;
@@ -61,7 +61,11 @@ gram_tc_kernel(const CUtensorMap* __restrict__ maps, const TcUnit* __restrict__ 
   const CUtensorMap* map_b = maps + u.map + 1;
   const CUtensorMap* map_f = maps + u.map + 2;
   const bool has_g = u.nj_mma > 0, has_f = u.has_f != 0;
-  const int count = (u.lane < u.kb_total) ? (u.kb_total - u.lane + u.nlanes - 1) / u.nlanes : 0;
+  // this launch's phase of the point axis: blocks kb in [kb0, kb1) with kb = lane (mod nlanes)
+  const int kb1 = min(kb0 + kb_len, u.kb_total);
+  const int kb_first = kb0 + ((u.lane - kb0 % u.nlanes) + u.nlanes) % u.nlanes;
+  const int count = (kb_first < kb1) ? (kb1 - kb_first + u.nlanes - 1) / u.nlanes : 0;
+  const bool accumulate = kb0 > 0;  // later phases add to the lane's partial
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -90,7 +94,7 @@ gram_tc_kernel(const CUtensorMap* __restrict__ maps, const TcUnit* __restrict__ 
         const uint32_t full = smem_u32(&sm->full[s]);
         mbar_arrive_expect_tx(full, tx_bytes);
         const uint32_t sa = base + s * stage_bytes;
-        const int32_t x = (u.lane + i * u.nlanes) * kTcBK;
+        const int32_t x = (kb_first + i * u.nlanes) * kTcBK;
         tma_load_2d(sa, map_a, x, u.i0, full);
         if (has_g) tma_load_2d(sa + kABytes, map_b, x, u.j0, full);
         if (has_f) tma_load_2d(sa + kABytes + kBBytes, map_f, x, 0, full);  // the F map starts at Psi row m
@@ -136,6 +140,7 @@ gram_tc_kernel(const CUtensorMap* __restrict__ maps, const TcUnit* __restrict__ 
     if (ready) fence_after();
     const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
     auto drain = [&](int col0, int ncols) {
+      if (!ready && accumulate) return;  // nothing in this phase: the partial stands
       for (int c0 = 0; c0 < ncols; c0 += 32) {
         float v[32];
         if (ready) {
@@ -145,9 +150,18 @@ gram_tc_kernel(const CUtensorMap* __restrict__ maps, const TcUnit* __restrict__ 
           for (int q = 0; q < 32; ++q) v[q] = 0.f;  // no point blocks in this lane: a zero partial
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          *reinterpret_cast<float4*>(out + col0 + c0 + 4 * q) =
-              make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        for (int q = 0; q < 8; ++q) {
+          float4* o = reinterpret_cast<float4*>(out + col0 + c0 + 4 * q);
+          float4 w = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          if (accumulate) {
+            const float4 old = *o;
+            w.x += old.x;
+            w.y += old.y;
+            w.z += old.z;
+            w.w += old.w;
+          }
+          *o = w;
+        }
       }
     };
     if (has_g) drain(0, u.nj_mma);
@@ -176,8 +190,14 @@ bool make_gram_maps(void* maps_host3, const void* psi, int64_t n_pad, int m, int
                        (uint32_t)cpad);
 }
 
-cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_units, int max_cpad, int* err,
-                           cudaStream_t st) {
+cudaError_t gram_tc_prepare() {
+  static const cudaError_t attr =  // once per process (thread-safe initialisation)
+      cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+  return attr;
+}
+
+cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_units, int max_cpad, int max_kb,
+                           int* err, cudaStream_t st) {
   if (num_units <= 0) return cudaSuccess;
   if (max_cpad < 16 || max_cpad > 256) return cudaErrorInvalidValue;
   const int stage_bytes = stage_bytes_for(max_cpad);
@@ -185,15 +205,18 @@ cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_un
   if (stages > kMaxStages) stages = kMaxStages;
   if (stages < 2) return cudaErrorInvalidValue;
   const int smem = stages * stage_bytes + kSmemExtra;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+  const cudaError_t attr = gram_tc_prepare();
+  if (attr != cudaSuccess) return attr;
+  // the point axis in phases of kGramPhaseBlocks 64-point blocks, one launch each, so that the
+  // lanes of a tile restart in step (and the slab they share stays in L2) every phase
+  const int phases = max_kb > 0 ? (max_kb + kGramPhaseBlocks - 1) / kGramPhaseBlocks : 1;
+  for (int ph = 0; ph < phases; ++ph) {
+    gram_tc_kernel<<<num_units, kThreads, smem, st>>>(static_cast<const CUtensorMap*>(maps_dev), units, stages,
+                                                      stage_bytes, ph * kGramPhaseBlocks, kGramPhaseBlocks, err);
+    const cudaError_t e = launched();
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
-  gram_tc_kernel<<<num_units, kThreads, smem, st>>>(static_cast<const CUtensorMap*>(maps_dev), units, stages,
-                                                    stage_bytes, err);
-  return launched();
+  return cudaSuccess;
 }
 
 }  // namespace rfd

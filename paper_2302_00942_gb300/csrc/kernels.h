@@ -80,8 +80,11 @@ struct TcUnit {
 // Encodes the three tensor maps of a cloud's bf16 feature matrix Psi
 // ([rows_alloc][n_pad], rows 0..m-1 features, m..m+cpad-1 field) into maps[0..2].
 bool make_gram_maps(void* maps_host3, const void* psi, int64_t n_pad, int m, int cpad);
-cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_units, int max_cpad, int* err,
-                           cudaStream_t st);
+// One launch per phase of kGramPhaseBlocks 64-point blocks (max_kb: the largest
+// point-block count of the units' clouds); later phases add to the partials.
+constexpr int kGramPhaseBlocks = 4096;
+cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_units, int max_cpad, int max_kb,
+                           int* err, cudaStream_t st);
 bool tc_gram_supported();
 
 // Sum the split-K partials of every tile in a fixed order (Kahan) and apply
@@ -111,7 +114,16 @@ cudaError_t dnorm1(int m, const double* X, int ldx, double* out, cudaStream_t st
 cudaError_t dfinite_check(int m, int n, const double* X, int ldx, int* flag, cudaStream_t st);
 // FP64-accurate C = alpha A B + beta C on the BF16 tensor cores (Ozaki
 // splitting, k_ozaki.cu); K <= 1024.  `work` holds ozaki_workspace_bytes(M, N, K).
-size_t ozaki_workspace_bytes(int M, int N, int K);
+// Workspace layout of the emulated FP64 GEMM (byte offsets from a 256-byte
+// aligned base): A slices [8][mp][kp] and B^T slices [8][np][kp] (BF16),
+// exponents, B^T scratch.  The single source of the padded sizes.
+struct OzLayout {
+  int mp, np, kp;
+  size_t sa, sb, ea, eb, bt, bytes;
+};
+OzLayout ozaki_layout(int M, int N, int K);
+size_t ozaki_workspace_bytes(int M, int N, int K);  // layout bytes + alignment slack
+int ozaki_col_split_blocks(int m);  // blocks of the batched column split of an m x m operand
 bool ozaki_supported(int K);
 cudaError_t dgemm_ozaki(int M, int N, int K, double alpha, const double* A, int lda, const double* B, int ldb,
                         double beta, double* C, int ldc, void* work, int* err, cudaStream_t st);
@@ -140,13 +152,17 @@ struct FeatJob {
   int64_t n, n_pad;
   const float* omega;   // h x 3 FP32 frequencies
   __nv_bfloat16_raw* psi;
+  float* xyz;           // the plan's copy of the points (N x 3), read by the apply
   int32_t h, bx, cloud, pad_;  // bx: 512-point blocks; the job has bx * ceil(h / 32) blocks
 };
 // F^T rows of a cloud's Psi (rows m .. m + cpad - 1), BF16.
+// With fsplit, channel ch of F is written as two BF16 rows, hi = bf16(F) at
+// row ch and lo = bf16(F - hi) at row c + ch, so Phi^T F carries no BF16
+// rounding of F (the reduction adds the two columns).
 struct FillJob {
   int64_t n, n_pad;
   __nv_bfloat16_raw* rows;
-  int32_t cpad, bx, cloud, pad_;  // bx: 32-point blocks; the job has bx * ceil(cpad / 32) blocks
+  int32_t cpad, bx, cloud, fsplit;  // bx: 256-point blocks
 };
 // One output tile of the split-K reduction (absolute pointers).
 struct RedTile {
@@ -157,10 +173,13 @@ struct RedTile {
   const double* ob;
   int64_t slot_elems;
   int32_t i0, j0, ni, nj, kind, count, ld, col_off, m, cloud;
+  int32_t fsplit, pad_;  // field tiles: columns c..2c-1 hold the lo parts of F (see FillJob)
 };
 // Steps a5 / a6 for one cloud.
 struct ApplyJob {
-  const __nv_bfloat16_raw* psi;
+  const float* xyz;       // the plan's copy of the points (N x 3)
+  const float* omega_hi;  // h x 3 frequencies, FP32 hi + lo parts
+  const float* omega_lo;
   const double* G;
   const double* Y;
   const double* oa;
@@ -170,7 +189,7 @@ struct ApplyJob {
 };
 // Step a4 (phi1) for one cloud on the emulated-FP64 path.  Matrix "slots":
 // slot k >= 0 is work + k m^2; kSlotM is M, kSlotG is G.
-constexpr int kSlotM = -1, kSlotG = -2;
+constexpr int kSlotM = -1, kSlotG = -2, kNoSlot = -3;
 struct PhiCloud {
   double* work;
   const double* M;
@@ -179,7 +198,6 @@ struct PhiCloud {
   __nv_bfloat16_raw* sb;  // B-operand slices [8][mpb][kp]
   int* ea;                // row exponents of A (mpa)
   int* eb;                // column exponents of B (mpb)
-  double* bt;             // B^T scratch (m x m)
   int* flag;              // finiteness flag
   double lambda, scale;   // scale = 2^-s (set per call)
   int32_t m, mpa, mpb, kp;
@@ -208,14 +226,23 @@ cudaError_t launch_apply_batched(const ApplyJob* jobs, const int* prefix, int co
 cudaError_t launch_bcombine(const PhiCloud* pc, const int* prefix, int count, int total_blocks, int dst,
                             const int* src4, const double* a4, double diag, int kmode, int mask_k, cudaStream_t st);
 cudaError_t launch_bnorm1(const PhiCloud* pc, int count, int max_m, int slot, double* norms, cudaStream_t st);
+// squarings per cloud from the norms (see bselect_kernel); sv: count + 1 ints
+cudaError_t launch_bselect(PhiCloud* pc, int count, const double* norms, double theta, int max_s, int* sv,
+                           cudaStream_t st);
+// sets a cloud's flag when an entry of the slot is not finite (flags are sticky)
 cudaError_t launch_bfinite(const PhiCloud* pc, const int* prefix, int count, int total_blocks, int slot,
                            cudaStream_t st);
-// C = alpha A B + beta C on every cloud (emulated FP64): splits + tensor-core products.
-// row_prefix_a / row_prefix_b: warp-row prefixes over mpa / mpb rows; t_prefix: transpose blocks.
-cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* row_prefix_b,
-                         int rows_b, const int* t_prefix, int t_blocks, const OzTile* tiles, int num_tiles,
-                         const void* maps_dev, int a_slot, int b_slot, int c_slot, double alpha, double beta,
-                         int mask_k, int* err, cudaStream_t st);
+// D = alpha A B + beta C + diag I on every cloud (emulated FP64): row split of
+// A (warp-row prefix over mpa rows), column split of B (prefix over
+// ozaki_col_split_blocks(m) per cloud) and the tensor-core products.  c_slot kNoSlot: no C.  Clouds with
+// s <= mask_k (mask_k >= 0) skip the product and copy C to D.
+cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* strip_prefix,
+                         int col_strips, const OzTile* tiles, int num_tiles, const void* maps_dev, int a_slot,
+                         int b_slot, int c_slot, int d_slot, double alpha, double beta, double diag, int mask_k,
+                         int* err, cudaStream_t st);
+// one-time kernel attribute set-up of launch_gram_tc / launch_bgemm (call before a stream capture)
+cudaError_t gram_tc_prepare();
+cudaError_t bgemm_prepare();
 // tensor maps of a cloud's Ozaki slice buffers (A: box 64 x 128 rows, B: box 64 x 64 rows)
 bool make_ozaki_maps(void* map_a_host, void* map_b_host, const void* sa, const void* sb, int mpa, int mpb, int kp);
 

@@ -52,6 +52,32 @@ cudaError_t dev_alloc(void** p, size_t bytes) {
   return cudaMalloc(p, bytes);
 }
 
+struct CudaMem final : MemSource {
+  void* dev(size_t bytes) override {
+    void* p = nullptr;
+    if (dev_alloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void dev_free(void* p) override { cudaFree(p); }
+  void* pinned(size_t bytes) override {
+    void* p = nullptr;
+    if (g_fail_alloc_after == 0) {
+      g_fail_alloc_after = -1;
+      return nullptr;
+    }
+    if (g_fail_alloc_after > 0) --g_fail_alloc_after;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void pinned_free(void* p) override { cudaFreeHost(p); }
+};
+
 rfd_status cuda_fail(const char* what, cudaError_t e) {
   return fail(RFD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
@@ -134,16 +160,6 @@ void build_tiles_simt(rfd_plan_s* pl, bool with_gram, bool with_field, TileSet& 
       cost.push_back(1.0);
     }
   schedule_simt(ts, pl->n_pad, 2 * pl->sms, cost);
-}
-
-rfd_status upload_tiles(rfd_plan_s* pl, TileSet& ts) {
-  rfd_status s = plan_alloc(pl, &ts.d_tiles, ts.tiles.size());
-  if (s != RFD_OK) return s;
-  s = plan_alloc(pl, &ts.d_units, ts.units.size());
-  if (s != RFD_OK) return s;
-  RFD_CUDA(cudaMemcpy(ts.d_tiles, ts.tiles.data(), ts.tiles.size() * sizeof(GramTile), cudaMemcpyHostToDevice));
-  RFD_CUDA(cudaMemcpy(ts.d_units, ts.units.data(), ts.units.size() * sizeof(GramUnit), cudaMemcpyHostToDevice));
-  return RFD_OK;
 }
 
 // ---- BF16 tensor-core form: the plan's batched-path descriptors -------------
@@ -239,6 +255,7 @@ rfd_status build_desc(rfd_plan_s* pl) {
       if (c.f) {
         r.j0 = m;
         r.nj = pl->cpad;
+        r.fsplit = pl->fsplit ? 1 : 0;
         r.kind = kTileField;
         r.col_off = kTcBNMax;
         d.red[mode].push_back(r);
@@ -246,9 +263,11 @@ rfd_status build_desc(rfd_plan_s* pl) {
     }
   }
   auto* psi = static_cast<__nv_bfloat16_raw*>(pl->d_psi);
-  d.feat = FeatJob{pl->n, pl->n_pad, pl->d_omega_hi, psi, pl->h, (int)((pl->n_pad + 511) / 512), 0, 0};
-  d.fill = FillJob{pl->n, pl->n_pad, psi + (size_t)m * pl->n_pad, pl->cpad, (int)((pl->n_pad + 31) / 32), 0, 0};
-  d.apply = ApplyJob{psi, pl->d_G, pl->d_Y, pl->d_oa, pl->d_Z, pl->n, pl->n_pad, m, 0, (int)((pl->n + 255) / 256), 0};
+  d.feat = FeatJob{pl->n, pl->n_pad, pl->d_omega_hi, psi, pl->d_xyz, pl->h, (int)((pl->n_pad + 511) / 512), 0, 0};
+  d.fill = FillJob{pl->n, pl->n_pad, psi + (size_t)m * pl->n_pad, pl->cpad, (int)((pl->n_pad + 255) / 256), 0,
+                   pl->fsplit ? 1 : 0};
+  d.apply = ApplyJob{pl->d_xyz,  pl->d_omega_hi, pl->d_omega_lo, pl->d_G, pl->d_Y, pl->d_oa, pl->d_Z,
+                     pl->n,      pl->n_pad,      m, 0, (int)((pl->n + 255) / 256), 0};
   // step a4 on the emulated path: slots in the FP64 workspace, Ozaki slices after them
   PhiCloud& pc = d.phi;
   pc = PhiCloud{};
@@ -256,20 +275,18 @@ rfd_status build_desc(rfd_plan_s* pl) {
   pc.M = pl->d_M;
   pc.G = pl->d_G;
   pc.m = m;
-  pc.mpa = (int)round_up(m, 128);
-  pc.mpb = (int)round_up(m, 64);
-  pc.kp = (int)round_up(m, 64);
-  auto* oz = reinterpret_cast<unsigned char*>(pl->d_work + (size_t)m * m * 18);
-  pc.sa = reinterpret_cast<__nv_bfloat16_raw*>(oz);
-  oz += (size_t)8 * pc.mpa * pc.kp * 2;
-  pc.sb = reinterpret_cast<__nv_bfloat16_raw*>(oz);
-  oz += (size_t)8 * pc.mpb * pc.kp * 2;
-  pc.ea = reinterpret_cast<int*>(oz);
-  oz += (size_t)pc.mpa * 4;
-  pc.eb = reinterpret_cast<int*>(oz);
-  oz += (size_t)pc.mpb * 4;
-  oz = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(oz) + 255) & ~uintptr_t(255));
-  pc.bt = reinterpret_cast<double*>(oz);
+  const OzLayout L = ozaki_layout(m, m, m);
+  pc.mpa = L.mp;
+  pc.mpb = L.np;
+  pc.kp = L.kp;
+  auto* oz0 = reinterpret_cast<unsigned char*>(pl->d_work + (size_t)m * m * 18);
+  auto* oz = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(oz0) + 255) & ~uintptr_t(255));
+  if ((size_t)(oz - oz0) + L.bytes > ozaki_workspace_bytes(m, m, m))
+    return fail(RFD_ECUDA, "internal: phi1 workspace layout exceeds its allocation");
+  pc.sa = reinterpret_cast<__nv_bfloat16_raw*>(oz + L.sa);
+  pc.sb = reinterpret_cast<__nv_bfloat16_raw*>(oz + L.sb);
+  pc.ea = reinterpret_cast<int*>(oz + L.ea);
+  pc.eb = reinterpret_cast<int*>(oz + L.eb);
   pc.lambda = pl->p.lambda;
   pc.scale = 1.0;
   pc.map_a = 3;
@@ -392,15 +409,67 @@ void fill_stats(const Timing& tm, rfd_stats* out) {
 
 }  // namespace
 
-extern "C" {
+// ---- plan construction (shared by rfd_plan and the server) ------------------
+namespace rfd {
 
-const char* rfd_last_error(void) { return rfd::last_error_cstr(); }
-const char* rfd_version(void) { return "rfd-gb300 0.2 (sm_103a)"; }
+namespace {
 
-rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out) {
-  if (!params || !out) return fail(RFD_EINVAL, "null params or output pointer");
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// The plan's device buffers, carved from one chunk in a fixed order.
+struct PlanCarve {
+  size_t total = 0;
+  std::vector<std::pair<void**, size_t>> items;
+  void bytes(void** p, size_t n) {
+    items.push_back({p, align256(std::max<size_t>(n, 1))});
+    total += items.back().second;
+  }
+  template <typename T>
+  void add(T** p, size_t count) {
+    bytes(reinterpret_cast<void**>(p), count * sizeof(T));
+  }
+  void assign(void* base) {
+    size_t off = 0;
+    for (auto& it : items) {
+      *it.first = static_cast<unsigned char*>(base) + off;
+      off += it.second;
+    }
+  }
+};
+
+void plan_carve(rfd_plan_s* pl, PlanCarve& c) {
+  const int m = pl->m;
+  c.add(&pl->d_omega_hi, (size_t)pl->h * 3);
+  c.add(&pl->d_omega_lo, (size_t)pl->h * 3);
+  c.add(&pl->d_oa, (size_t)m);
+  c.add(&pl->d_ob, (size_t)m);
+  if (pl->bf16) c.add(&pl->d_xyz, (size_t)pl->n * 3);
+  c.bytes(&pl->d_psi, (size_t)pl->rows_alloc * pl->n_pad * (pl->bf16 ? 2 : 4));
+  c.add(&pl->d_part, (size_t)pl->part_slots * pl->slot_elems);
+  c.add(&pl->d_M, (size_t)m * m);
+  c.add(&pl->d_Y, (size_t)m * pl->p.max_channels);
+  c.add(&pl->d_G, (size_t)m * m);
+  c.add(&pl->d_Z, (size_t)m * pl->p.max_channels);
+  c.add(&pl->d_work, phi1_workspace_doubles(m));
+  c.add(&pl->d_ipiv, (size_t)m);
+  c.add(&pl->d_ints, 4);
+  c.add(&pl->d_scalar, 2);
+  if (!pl->bf16)
+    for (TileSet* ts : {&pl->gram_only, &pl->field_only, &pl->both}) {
+      c.add(&ts->d_tiles, ts->tiles.size());
+      c.add(&ts->d_units, ts->units.size());
+    }
+}
+
+}  // namespace
+
+MemSource* cuda_mem() {
+  static CudaMem m;
+  return &m;
+}
+
+rfd_status plan_prepare(const rfd_params& p, cudaStream_t stream, rfd_plan_s** out) {
   *out = nullptr;
-  const rfd_params& p = *params;
   if (p.n < 1) return fail(RFD_EINVAL, "n must be >= 1");
   if (p.m < 2 || p.m > kMaxM || (p.m & 1)) return fail(RFD_EINVAL, "m must be even, 2 <= m <= 4096");
   if (p.max_channels < 1 || p.max_channels > kMaxChannels) return fail(RFD_EINVAL, "max_channels must be in [1, 256]");
@@ -411,17 +480,19 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
   auto* pl = new (std::nothrow) rfd_plan_s();
   if (!pl) return fail(RFD_ENOMEM, "host allocation failed");
   pl->p = p;
-  pl->stream = static_cast<cudaStream_t>(cuda_stream);
+  pl->stream = stream;
   pl->m = p.m;
   pl->h = p.m / 2;
   pl->n = p.n;
   pl->n_pad = round_up(p.n, 128);
-  pl->cpad = (int)round_up(p.max_channels, 16);
   pl->bf16 = (p.precision == RFD_BF16_TC);
+  // BF16 form: F enters as hi + lo rows (2c) while that fits the field part of the Gram tiles
+  pl->fsplit = pl->bf16 && 2 * p.max_channels <= 256;
+  pl->cpad = (int)round_up(pl->fsplit ? 2 * p.max_channels : p.max_channels, 16);
   pl->omega.resize((size_t)pl->h * 3);
   pl->r.resize(pl->h);
-  rfd_status st = rfd::sample_frequencies_host(p.m, p.eps, p.seed, p.freq_sigma, p.freq_radius, pl->omega.data(),
-                                               pl->r.data());
+  rfd_status st = sample_frequencies_host(p.m, p.eps, p.seed, p.freq_sigma, p.freq_radius, pl->omega.data(),
+                                          pl->r.data());
   if (st != RFD_OK) {
     delete pl;
     return st;
@@ -435,6 +506,12 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
     pl->oa[j] = pl->oa[pl->h + j] = sa;
     pl->ob[j] = pl->ob[pl->h + j] = s;
   }
+  pl->omega_hi_h.resize(pl->omega.size());
+  pl->omega_lo_h.resize(pl->omega.size());
+  for (size_t i = 0; i < pl->omega.size(); ++i) {
+    pl->omega_hi_h[i] = (float)pl->omega[i];
+    pl->omega_lo_h[i] = (float)(pl->omega[i] - (double)pl->omega_hi_h[i]);
+  }
   int dev = 0;
   cudaError_t ce = cudaGetDevice(&dev);
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -446,75 +523,109 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
     delete pl;
     return fail(RFD_ENOTSUP, "the BF16 tensor-core form needs an sm_103 GPU (tcgen05) and cuTensorMapEncodeTiled");
   }
-  auto bail = [&](rfd_status s) {
-    if (pl->self) batch_free(pl->self);
-    pl->timing.destroy();
-    plan_free(pl);
-    delete pl;
-    return s;
-  };
-  // partial slots: SIMT tiles, or up to one per SM for the tensor-core lanes
+  // partial slots: SIMT tiles, or the tensor-core tiles x lanes
   if (!pl->bf16) {
     build_tiles_simt(pl, true, false, pl->gram_only);
     build_tiles_simt(pl, false, true, pl->field_only);
     build_tiles_simt(pl, true, true, pl->both);
   }
-  const int slots = pl->bf16 ? tc_partial_slots(pl->m, pl->n_pad, pl->sms)
-                             : std::max({pl->gram_only.slots, pl->field_only.slots, pl->both.slots});
+  pl->part_slots = pl->bf16 ? tc_partial_slots(pl->m, pl->n_pad, pl->sms)
+                            : std::max({pl->gram_only.slots, pl->field_only.slots, pl->both.slots});
   pl->slot_elems = pl->bf16 ? (int64_t)kTcBM * kTcLd : (int64_t)kSimtTile * kSimtTile;
   pl->rows_alloc = (int)std::max<int64_t>(round_up(p.m, 128), p.m + round_up(pl->cpad, 128));
-  const size_t esz = pl->bf16 ? 2 : 4;
-  std::vector<float> whi(pl->omega.size()), wlo(pl->omega.size());
-  for (size_t i = 0; i < pl->omega.size(); ++i) {
-    whi[i] = (float)pl->omega[i];
-    wlo[i] = (float)(pl->omega[i] - (double)whi[i]);
+  *out = pl;
+  return RFD_OK;
+}
+
+size_t plan_device_bytes(rfd_plan_s* pl) {
+  PlanCarve c;
+  plan_carve(pl, c);
+  return c.total;
+}
+
+void plan_destroy(rfd_plan_s* pl) {
+  if (!pl) return;
+  if (pl->self) batch_free(pl->self);
+  pl->timing.destroy();
+  if (pl->chunk) pl->mem->dev_free(pl->chunk);
+  plan_free(pl);
+  delete pl;
+}
+
+rfd_status plan_materialize(rfd_plan_s* pl, MemSource* mem, bool self_batch, bool sync_init) {
+  auto bail = [&](rfd_status s) {
+    if (sync_init || pl->self) cudaStreamSynchronize(pl->stream);
+    plan_destroy(pl);
+    return s;
+  };
+  pl->mem = mem;
+  PlanCarve c;
+  plan_carve(pl, c);
+  if (!pl->chunk) pl->chunk = mem->dev(c.total);  // a caller may have reserved it
+  if (!pl->chunk) {
+    fail(RFD_ENOMEM, "device allocation of " + std::to_string(c.total) + " bytes failed");
+    return bail(RFD_ENOMEM);
   }
-  if ((st = plan_alloc(pl, &pl->d_omega_hi, whi.size())) != RFD_OK) return bail(st);
-  if ((st = plan_alloc(pl, &pl->d_omega_lo, wlo.size())) != RFD_OK) return bail(st);
-  if ((st = plan_alloc(pl, &pl->d_oa, (size_t)p.m)) != RFD_OK) return bail(st);
-  if ((st = plan_alloc(pl, &pl->d_ob, (size_t)p.m)) != RFD_OK) return bail(st);
-  void* psi = nullptr;
-  if ((st = plan_alloc(pl, reinterpret_cast<uint8_t**>(&psi), (size_t)pl->rows_alloc * pl->n_pad * esz)) != RFD_OK)
-    return bail(st);
-  pl->d_psi = psi;
-  if ((st = plan_alloc(pl, &pl->d_part, (size_t)slots * pl->slot_elems)) != RFD_OK) return bail(st);
-  if ((st = plan_alloc(pl, &pl->d_M, (size_t)p.m * p.m)) != RFD_OK) return bail(st);
-  if ((st = plan_alloc(pl, &pl->d_Y, (size_t)p.m * p.max_channels)) != RFD_OK) return bail(st);
-  if ((st = plan_alloc(pl, &pl->d_G, (size_t)p.m * p.m)) != RFD_OK) return bail(st);
-  if ((st = plan_alloc(pl, &pl->d_Z, (size_t)p.m * p.max_channels)) != RFD_OK) return bail(st);
-  if ((st = plan_alloc(pl, &pl->d_work, phi1_workspace_doubles(p.m))) != RFD_OK) return bail(st);
-  if ((st = plan_alloc(pl, &pl->d_ipiv, (size_t)p.m)) != RFD_OK) return bail(st);
-  if ((st = plan_alloc(pl, &pl->d_ints, 4)) != RFD_OK) return bail(st);
-  if ((st = plan_alloc(pl, &pl->d_scalar, 2)) != RFD_OK) return bail(st);
-  if (!pl->bf16) {
-    if ((st = upload_tiles(pl, pl->gram_only)) != RFD_OK) return bail(st);
-    if ((st = upload_tiles(pl, pl->field_only)) != RFD_OK) return bail(st);
-    if ((st = upload_tiles(pl, pl->both)) != RFD_OK) return bail(st);
-  }
-  auto up = [&](void* dst, const void* src, size_t bytes) { return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice); };
-  if ((ce = up(pl->d_omega_hi, whi.data(), whi.size() * 4)) != cudaSuccess ||
-      (ce = up(pl->d_omega_lo, wlo.data(), wlo.size() * 4)) != cudaSuccess ||
-      (ce = up(pl->d_oa, pl->oa.data(), pl->oa.size() * 8)) != cudaSuccess ||
-      (ce = up(pl->d_ob, pl->ob.data(), pl->ob.size() * 8)) != cudaSuccess ||
-      (ce = cudaMemset(pl->d_psi, 0, (size_t)pl->rows_alloc * pl->n_pad * esz)) != cudaSuccess ||
-      (ce = cudaMemset(pl->d_ints, 0, 4 * sizeof(int))) != cudaSuccess) {
+  pl->chunk_bytes = c.total;
+  c.assign(pl->chunk);
+  cudaStream_t st = pl->stream;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  cudaError_t ce = up(pl->d_omega_hi, pl->omega_hi_h.data(), pl->omega_hi_h.size() * 4);
+  if (ce == cudaSuccess) ce = up(pl->d_omega_lo, pl->omega_lo_h.data(), pl->omega_lo_h.size() * 4);
+  if (ce == cudaSuccess) ce = up(pl->d_oa, pl->oa.data(), pl->oa.size() * 8);
+  if (ce == cudaSuccess) ce = up(pl->d_ob, pl->ob.data(), pl->ob.size() * 8);
+  if (ce == cudaSuccess)
+    ce = cudaMemsetAsync(pl->d_psi, 0, (size_t)pl->rows_alloc * pl->n_pad * (pl->bf16 ? 2 : 4), st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(pl->d_ints, 0, 4 * sizeof(int), st);
+  if (!pl->bf16)
+    for (TileSet* ts : {&pl->gram_only, &pl->field_only, &pl->both}) {
+      if (ce == cudaSuccess) ce = up(ts->d_tiles, ts->tiles.data(), ts->tiles.size() * sizeof(GramTile));
+      if (ce == cudaSuccess) ce = up(ts->d_units, ts->units.data(), ts->units.size() * sizeof(GramUnit));
+    }
+  if (ce != cudaSuccess) {
     cuda_fail("plan upload", ce);
     return bail(RFD_ECUDA);
   }
+  rfd_status st2;
   if (pl->bf16) {
-    if ((st = build_desc(pl)) != RFD_OK) return bail(st);
-    rfd_plan_s* self = pl;
-    if ((st = batch_build(&self, 1, pl->stream, &pl->self)) != RFD_OK) return bail(st);
+    if ((st2 = build_desc(pl)) != RFD_OK) return bail(st2);
+    if (self_batch) {
+      rfd_plan_s* self = pl;
+      if ((st2 = batch_build(&self, 1, st, mem, 0, &pl->self)) != RFD_OK) return bail(st2);
+    }
     pl->stats.splits = pl->desc.units[kModeGfi].empty() ? 0 : pl->desc.units[kModeGfi][0].nlanes;
   } else {
     pl->stats.splits = pl->both.units.empty() ? 0 : (int)(pl->both.units.size() / pl->both.tiles.size());
   }
-  if (p.flags & RFD_FLAG_TIMING) {
+  if (pl->p.flags & RFD_FLAG_TIMING) {
     if ((ce = pl->timing.init()) != cudaSuccess) {
       cuda_fail("event creation", ce);
       return bail(RFD_ECUDA);
     }
   }
+  if (sync_init && (ce = cudaStreamSynchronize(st)) != cudaSuccess) {
+    cuda_fail("plan upload", ce);
+    return bail(RFD_ECUDA);
+  }
+  return RFD_OK;
+}
+
+}  // namespace rfd
+
+extern "C" {
+
+const char* rfd_last_error(void) { return rfd::last_error_cstr(); }
+const char* rfd_version(void) { return "rfd-gb300 0.3 (sm_103a)"; }
+
+rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out) {
+  if (!params || !out) return fail(RFD_EINVAL, "null params or output pointer");
+  *out = nullptr;
+  rfd_plan_s* pl = nullptr;
+  rfd_status st = plan_prepare(*params, static_cast<cudaStream_t>(cuda_stream), &pl);
+  if (st != RFD_OK) return st;
+  if ((st = plan_materialize(pl, cuda_mem(), true, true)) != RFD_OK) return st;
   *out = pl;
   return RFD_OK;
 }
@@ -522,10 +633,7 @@ rfd_status rfd_plan(const rfd_params* params, void* cuda_stream, rfd_plan_t* out
 rfd_status rfd_plan_destroy(rfd_plan_t plan) {
   if (!plan) return RFD_OK;
   cudaStreamSynchronize(plan->stream);
-  if (plan->self) batch_free(plan->self);
-  plan->timing.destroy();
-  plan_free(plan);
-  delete plan;
+  plan_destroy(plan);
   return RFD_OK;
 }
 
@@ -630,7 +738,7 @@ rfd_status rfd_plan_stats_reset(rfd_plan_t pl) {
 rfd_status rfd_batch_create(const rfd_plan_t* plans, int32_t count, int32_t flags, void* cuda_stream,
                             rfd_batch_t* out) {
   if (!plans || !out || count < 1) return fail(RFD_EINVAL, "null plans / output or count < 1");
-  if (flags & ~RFD_FLAG_TIMING) return fail(RFD_EINVAL, "unknown bits in flags");
+  if (flags & ~(RFD_FLAG_TIMING | RFD_FLAG_GRAPH)) return fail(RFD_EINVAL, "unknown bits in flags");
   *out = nullptr;
   std::vector<rfd_plan_s*> v(plans, plans + count);
   for (int i = 0; i < count; ++i) {
@@ -643,12 +751,14 @@ rfd_status rfd_batch_create(const rfd_plan_t* plans, int32_t count, int32_t flag
   if (!b) return fail(RFD_ENOMEM, "host allocation failed");
   b->plans = v;
   b->stream = static_cast<cudaStream_t>(cuda_stream);
-  rfd_status s = batch_build(v.data(), count, b->stream, &b->impl);
+  rfd_status s = batch_build(v.data(), count, b->stream, cuda_mem(), (flags & RFD_FLAG_GRAPH) ? kBatchGraphs : 0,
+                             &b->impl);
   if (s == RFD_OK && (flags & RFD_FLAG_TIMING)) {
     cudaError_t ce = b->timing.init();
     if (ce != cudaSuccess) s = cuda_fail("event creation", ce);
   }
   if (s != RFD_OK) {
+    cudaStreamSynchronize(b->stream);
     if (b->impl) batch_free(b->impl);
     b->timing.destroy();
     delete b;
@@ -660,6 +770,7 @@ rfd_status rfd_batch_create(const rfd_plan_t* plans, int32_t count, int32_t flag
 
 rfd_status rfd_batch_destroy(rfd_batch_t b) {
   if (!b) return RFD_OK;
+  cudaStreamSynchronize(b->stream);
   batch_free(b->impl);
   b->timing.destroy();
   delete b;
@@ -730,7 +841,7 @@ rfd_status rfd_debug_dgemm(int32_t method, int32_t M, int32_t N, int32_t K, doub
     return RFD_OK;
   }
   if (method != 1) return fail(RFD_EINVAL, "method must be 0 or 1");
-  if (!ozaki_supported(K)) return fail(RFD_ENOTSUP, "emulated FP64 GEMM needs K <= 1024 on sm_103");
+  if (!ozaki_supported(K)) return fail(RFD_ENOTSUP, "emulated FP64 GEMM needs K <= 4096 on sm_103");
   rfd_plan_s tmp;
   uint8_t* work = nullptr;
   int* err = nullptr;

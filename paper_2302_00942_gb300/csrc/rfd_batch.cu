@@ -6,9 +6,14 @@
 // diagonal Pade of degree 5 on the block-triangular augmented matrix, the
 // denominator solved by the product (I + R)(I + R^2)...(I + R^16) (||R|| <
 // 0.14 for ||X||_1 <= theta_5, see rfd_phi1.cu), and per-cloud squarings s_c
-// (clouds with s_c <= k skip squaring step k).  The only host synchronisation
-// of a batched call is the one that brings the clouds' ||lambda M||_1 to the
-// host to choose s_c (and one for the finiteness flags).
+// chosen on the device from ||lambda M||_1 (clouds with s_c <= k skip squaring
+// step k).  The host waits once per call, for the largest s_c, which sets the
+// number of squaring launches.  Non-finite results and device-side timeouts
+// are recorded in sticky device words that batch_check_error reads.
+//
+// A batch's tables live in one device block and one pinned host block from its
+// memory source.  With kBatchGraphs the launches of a call are captured once per
+// shape (mode, largest s_c, apply grid) into CUDA graphs and replayed.
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <cmath>
@@ -26,20 +31,9 @@ namespace {
 
 constexpr double kTheta5 = 2.539398330063230e-1;  // Higham (2005), Table 2.3, degree 5
 constexpr int kSolveFactors = 5;                  // (0.135)^(2^5) / (1 - 0.135) < 2^-56
+constexpr int kMaxSquarings = 60;                 // beyond this exp(lambda M) overflows anyway
 // matrix slots of the phi1 evaluation (see kernels.h: slot k = work + k m^2)
 enum : int { sX = 0, sX2, sX4, sSp, sVp, sUp, sR, sR2, sF, sFb, sE, sT1, sT2 };
-
-template <typename T>
-cudaError_t upload(T** dst, const std::vector<T>& v, std::vector<void*>& owned) {
-  *dst = nullptr;
-  if (v.empty()) return cudaSuccess;
-  void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, v.size() * sizeof(T));
-  if (e != cudaSuccess) return e;
-  owned.push_back(p);
-  *dst = static_cast<T*>(p);
-  return cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
-}
 
 std::vector<int> prefix_of(const std::vector<int>& counts) {
   std::vector<int> p(counts.size() + 1, 0);
@@ -47,13 +41,30 @@ std::vector<int> prefix_of(const std::vector<int>& counts) {
   return p;
 }
 
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Lays out sections in one block: add() returns each section's offset.
+struct Layout {
+  size_t total = 0;
+  size_t add(size_t bytes) {
+    const size_t off = total;
+    total += align256(std::max<size_t>(bytes, 1));
+    return off;
+  }
+};
+
 }  // namespace
 
 struct BatchImpl {
   std::vector<rfd_plan_s*> plans;
   int count = 0;
   cudaStream_t st = nullptr;
-  std::vector<void*> owned;  // device allocations
+  MemSource* mem = nullptr;
+  int options = 0;
+  unsigned char* dblob = nullptr;  // device tables + per-call device words
+  size_t dbytes = 0;
+  unsigned char* hblob = nullptr;  // pinned: table image, call staging ring, read-back words
+  // device tables
   void* d_maps = nullptr;
   TcUnit* d_units[3] = {};
   int n_units[3] = {};
@@ -66,66 +77,76 @@ struct BatchImpl {
   int* d_fill_prefix = nullptr;
   int fill_blocks = 0;
   ApplyJob* d_apply = nullptr;
-  std::vector<ApplyJob> h_apply;
+  std::vector<int> apply_bx;
   int* d_small_prefix = nullptr;
   int small_rows = 0;
   PhiCloud* d_phi = nullptr;
-  std::vector<PhiCloud> h_phi;
   int* d_elem_prefix = nullptr;
   int elem_blocks = 0;
   int* d_rowa_prefix = nullptr;
   int rows_a = 0;
-  int* d_rowb_prefix = nullptr;
-  int rows_b = 0;
-  int* d_t_prefix = nullptr;
-  int t_blocks = 0;
+  int* d_strip_prefix = nullptr;  // blocks of the B operand's column split
+  int col_strips = 0;
   OzTile* d_oz = nullptr;
   int n_oz = 0;
-  int max_m = 0, max_cpad = 16;
-  bool phi_batched = true;  // all clouds on the emulated path (m <= 1024, no native flag)
-  // per call
-  CloudCall* d_calls = nullptr;
-  int* d_apply_prefix = nullptr;
-  static constexpr int kStageRing = 4;  // pinned per-call staging buffers, reused round-robin
-  unsigned char* h_stage_ring[kStageRing] = {};
+  int max_m = 0, max_cpad = 16, max_kb = 0;
+  bool phi_batched = true;  // all clouds on the emulated path (no native-FP64 flag)
+  // per-call device words
+  CloudCall* d_calls = nullptr;  // followed by the apply-block prefix (count + 1 ints)
+  double* d_norms = nullptr;
+  int* d_sv = nullptr;     // squarings per cloud, then their maximum
+  int* d_flags = nullptr;  // sticky: G of cloud k not finite
+  int* d_err = nullptr;    // sticky: a bounded device-side wait ran out
+  // pinned
+  static constexpr int kStageRing = 4;  // per-call staging buffers, reused round-robin
+  unsigned char* h_stage[kStageRing] = {};
   cudaEvent_t stage_done[kStageRing] = {};
   int stage_next = 0;
-  PhiCloud* h_phi_stage = nullptr;   // pinned copy of h_phi for the async upload
-  double* d_norms = nullptr;
-  double* h_norms = nullptr;         // pinned
-  int* d_flags = nullptr;
-  int* h_flags = nullptr;            // pinned
-  int* d_err = nullptr;
+  size_t stage_bytes = 0;
+  double* h_norms = nullptr;
+  int* h_sv = nullptr;
+  int* h_flags = nullptr;  // followed by the error word
+  cudaEvent_t ev_mid = nullptr;
+  // CUDA graphs (kBatchGraphs)
+  cudaStream_t cap = nullptr;  // capture-only stream (the caller's stream may be the legacy one)
+  struct Graph {
+    int key[4];
+    cudaGraphExec_t exec;
+    long long launches;
+  };
+  std::vector<Graph> graphs;
 };
 
 cudaStream_t batch_stream(BatchImpl* b) { return b->st; }
+size_t batch_device_bytes(BatchImpl* b) { return b ? b->dbytes : 0; }
 
 void batch_free(BatchImpl* b) {
   if (!b) return;
-  if (b->st) cudaStreamSynchronize(b->st);
-  for (void* p : b->owned) cudaFree(p);
-  for (int i = 0; i < BatchImpl::kStageRing; ++i) {
-    if (b->h_stage_ring[i]) cudaFreeHost(b->h_stage_ring[i]);
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (int i = 0; i < BatchImpl::kStageRing; ++i)
     if (b->stage_done[i]) cudaEventDestroy(b->stage_done[i]);
-  }
-  if (b->h_phi_stage) cudaFreeHost(b->h_phi_stage);
-  if (b->h_norms) cudaFreeHost(b->h_norms);
-  if (b->h_flags) cudaFreeHost(b->h_flags);
+  if (b->ev_mid) cudaEventDestroy(b->ev_mid);
+  if (b->dblob) b->mem->dev_free(b->dblob);
+  if (b->hblob) b->mem->pinned_free(b->hblob);
   delete b;
 }
 
-rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, BatchImpl** out) {
+rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, MemSource* mem, int options,
+                       BatchImpl** out) {
   *out = nullptr;
   auto* b = new (std::nothrow) BatchImpl();
   if (!b) return fail(RFD_ENOMEM, "host allocation failed");
   b->plans.assign(plans, plans + count);
   b->count = count;
   b->st = st;
+  b->mem = mem;
+  b->options = options;
   auto bail = [&](rfd_status s, const std::string& msg) {
     batch_free(b);
     return fail(s, msg);
   };
-  int sms = plans[0]->sms;
+  const int sms = plans[0]->sms;
   // --- Gram lanes: each cloud's lanes share the batch's CTAs in proportion to its work
   double work = 0.0;
   for (int k = 0; k < count; ++k)
@@ -136,14 +157,17 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Bat
   std::vector<unsigned char> maps((size_t)count * kMapsPerCloud * kTensorMapBytes);
   std::vector<FeatJob> feat;
   std::vector<FillJob> fill;
-  std::vector<int> feat_n, fill_n, small_n, elem_n, rowa_n, rowb_n, t_n;
+  std::vector<ApplyJob> apply;
+  std::vector<PhiCloud> phi;
+  std::vector<int> feat_n, fill_n, small_n, elem_n, rowa_n, strip_n;
   std::vector<OzTile> oz;
   for (int k = 0; k < count; ++k) {
     rfd_plan_s* pl = plans[k];
     const PlanDesc& d = pl->desc;
     b->max_m = std::max(b->max_m, pl->m);
     b->max_cpad = std::max(b->max_cpad, pl->cpad);
-    if (pl->m > 1024 || (pl->p.flags & RFD_FLAG_NATIVE_FP64)) b->phi_batched = false;
+    b->max_kb = std::max<int>(b->max_kb, (int)(pl->n_pad / kTcBK));
+    if (!ozaki_supported(pl->m) || (pl->p.flags & RFD_FLAG_NATIVE_FP64)) b->phi_batched = false;
     std::memcpy(maps.data() + (size_t)k * kMapsPerCloud * kTensorMapBytes, d.maps, sizeof(d.maps));
     const int64_t kb = pl->n_pad / kTcBK;
     for (int mode = 0; mode < 3; ++mode) {
@@ -179,87 +203,120 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Bat
     FillJob fl = d.fill;
     fl.cloud = k;
     fill.push_back(fl);
-    fill_n.push_back(fl.bx * ((fl.cpad + 31) / 32));
+    fill_n.push_back(fl.bx);
     ApplyJob aj = d.apply;
     aj.cloud = k;
-    b->h_apply.push_back(aj);
+    apply.push_back(aj);
+    b->apply_bx.push_back(aj.bx);
     small_n.push_back(pl->m);
     PhiCloud pc = d.phi;
     pc.map_a += k * kMapsPerCloud;
     pc.map_b += k * kMapsPerCloud;
-    b->h_phi.push_back(pc);
+    pc.s = 0;
+    pc.scale = 1.0;
+    phi.push_back(pc);
     elem_n.push_back((int)(((int64_t)pl->m * pl->m + 255) / 256));
     rowa_n.push_back(pc.mpa);
-    rowb_n.push_back(pc.mpb);
-    t_n.push_back(((pl->m + 31) / 32) * ((pl->m + 31) / 32));
+    strip_n.push_back(ozaki_col_split_blocks(pl->m));
     for (OzTile o : d.oz) {
       o.cloud = k;
       oz.push_back(o);
     }
   }
-  cudaError_t e = cudaSuccess;
-  {
-    void* p = nullptr;
-    if ((e = cudaMalloc(&p, maps.size())) != cudaSuccess) return bail(RFD_ENOMEM, "batch tables");
-    b->owned.push_back(p);
-    b->d_maps = p;
-    if ((e = cudaMemcpy(p, maps.data(), maps.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
-      return bail(RFD_ECUDA, "batch tables");
-  }
-  auto up_prefix = [&](int** d, const std::vector<int>& n, int* total) {
-    std::vector<int> pre = prefix_of(n);
-    *total = pre.back();
-    return upload(d, pre, b->owned);
+  const std::vector<int> pre_feat = prefix_of(feat_n), pre_fill = prefix_of(fill_n), pre_small = prefix_of(small_n),
+                         pre_elem = prefix_of(elem_n), pre_rowa = prefix_of(rowa_n), pre_strip = prefix_of(strip_n);
+  b->feat_blocks = pre_feat.back();
+  b->fill_blocks = pre_fill.back();
+  b->small_rows = pre_small.back();
+  b->elem_blocks = pre_elem.back();
+  b->rows_a = pre_rowa.back();
+  b->col_strips = pre_strip.back();
+  b->n_oz = (int)oz.size();
+  // --- one device block: the tables, then the per-call words
+  struct Sec {
+    size_t off;
+    const void* src;
+    size_t bytes;
   };
-  for (int mode = 0; mode < 3 && e == cudaSuccess; ++mode) {
+  std::vector<Sec> secs;
+  Layout L;
+  auto table = [&](const void* src, size_t bytes) {
+    secs.push_back(Sec{L.add(bytes), src, bytes});
+    return secs.back().off;
+  };
+  auto vtable = [&](const auto& v) { return table(v.data(), v.size() * sizeof(v[0])); };
+  const size_t o_maps = vtable(maps);
+  size_t o_units[3], o_red[3];
+  for (int mode = 0; mode < 3; ++mode) {
+    o_units[mode] = vtable(units[mode]);
+    o_red[mode] = vtable(red[mode]);
     b->n_units[mode] = (int)units[mode].size();
     b->n_red[mode] = (int)red[mode].size();
-    if ((e = upload(&b->d_units[mode], units[mode], b->owned)) != cudaSuccess) break;
-    e = upload(&b->d_red[mode], red[mode], b->owned);
   }
-  if (e == cudaSuccess) e = upload(&b->d_feat, feat, b->owned);
-  if (e == cudaSuccess) e = up_prefix(&b->d_feat_prefix, feat_n, &b->feat_blocks);
-  if (e == cudaSuccess) e = upload(&b->d_fill, fill, b->owned);
-  if (e == cudaSuccess) e = up_prefix(&b->d_fill_prefix, fill_n, &b->fill_blocks);
-  if (e == cudaSuccess) e = upload(&b->d_apply, b->h_apply, b->owned);
-  if (e == cudaSuccess) e = up_prefix(&b->d_small_prefix, small_n, &b->small_rows);
-  if (e == cudaSuccess) e = up_prefix(&b->d_elem_prefix, elem_n, &b->elem_blocks);
-  if (e == cudaSuccess) e = up_prefix(&b->d_rowa_prefix, rowa_n, &b->rows_a);
-  if (e == cudaSuccess) e = up_prefix(&b->d_rowb_prefix, rowb_n, &b->rows_b);
-  if (e == cudaSuccess) e = up_prefix(&b->d_t_prefix, t_n, &b->t_blocks);
-  if (e == cudaSuccess) e = upload(&b->d_oz, oz, b->owned);
-  b->n_oz = (int)oz.size();
-  // per-call buffers
-  auto dev = [&](void** p, size_t bytes) {
-    cudaError_t r = cudaMalloc(p, bytes);
-    if (r == cudaSuccess) b->owned.push_back(*p);
-    return r;
-  };
-  void* p = nullptr;
-  if (e == cudaSuccess && (e = dev(&p, (size_t)count * sizeof(CloudCall) + (size_t)(count + 1) * sizeof(int))) == cudaSuccess) {
-    b->d_calls = static_cast<CloudCall*>(p);
-    b->d_apply_prefix = reinterpret_cast<int*>(static_cast<unsigned char*>(p) + (size_t)count * sizeof(CloudCall));
+  const size_t o_feat = vtable(feat), o_feat_pre = vtable(pre_feat), o_fill = vtable(fill),
+               o_fill_pre = vtable(pre_fill), o_apply = vtable(apply), o_small_pre = vtable(pre_small),
+               o_phi = vtable(phi), o_elem_pre = vtable(pre_elem), o_rowa_pre = vtable(pre_rowa),
+               o_strip_pre = vtable(pre_strip), o_oz = vtable(oz);
+  const size_t table_bytes = L.total;
+  b->stage_bytes = (size_t)count * sizeof(CloudCall) + (size_t)(count + 1) * sizeof(int);
+  const size_t o_calls = L.add(b->stage_bytes);
+  const size_t o_norms = L.add((size_t)count * sizeof(double));
+  const size_t o_sv = L.add((size_t)(count + 1) * sizeof(int));
+  const size_t o_flags = L.add((size_t)(count + 1) * sizeof(int));  // flags, then the error word
+  b->dbytes = L.total;
+  // --- one pinned block: the table image (same offsets), the staging ring, read-back words
+  Layout H;
+  H.add(table_bytes);
+  size_t o_stage[BatchImpl::kStageRing];
+  for (size_t& o : o_stage) o = H.add(b->stage_bytes);
+  const size_t o_hn = H.add((size_t)count * sizeof(double));
+  const size_t o_hsv = H.add((size_t)(count + 1) * sizeof(int));
+  const size_t o_hf = H.add((size_t)(count + 1) * sizeof(int));
+  b->dblob = static_cast<unsigned char*>(mem->dev(b->dbytes));
+  if (!b->dblob) return bail(RFD_ENOMEM, "device allocation of " + std::to_string(b->dbytes) + " bytes (batch tables) failed");
+  b->hblob = static_cast<unsigned char*>(mem->pinned(H.total));
+  if (!b->hblob) return bail(RFD_ENOMEM, "pinned allocation of " + std::to_string(H.total) + " bytes failed");
+  unsigned char* D = b->dblob;
+  b->d_maps = D + o_maps;
+  for (int mode = 0; mode < 3; ++mode) {
+    b->d_units[mode] = reinterpret_cast<TcUnit*>(D + o_units[mode]);
+    b->d_red[mode] = reinterpret_cast<RedTile*>(D + o_red[mode]);
   }
-  if (e == cudaSuccess && (e = dev(&p, (size_t)count * sizeof(PhiCloud))) == cudaSuccess) b->d_phi = static_cast<PhiCloud*>(p);
-  if (e == cudaSuccess && (e = dev(&p, (size_t)count * sizeof(double))) == cudaSuccess) b->d_norms = static_cast<double*>(p);
-  if (e == cudaSuccess && (e = dev(&p, (size_t)count * sizeof(int) + 256)) == cudaSuccess) {
-    b->d_flags = static_cast<int*>(p);
-    b->d_err = reinterpret_cast<int*>(static_cast<unsigned char*>(p) + (((size_t)count * sizeof(int) + 127) & ~size_t(127)));
-  }
-  for (int i = 0; i < BatchImpl::kStageRing && e == cudaSuccess; ++i) {
-    e = cudaMallocHost(&b->h_stage_ring[i], (size_t)count * sizeof(CloudCall) + (size_t)(count + 1) * sizeof(int));
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->stage_done[i], cudaEventDisableTiming);
-  }
-  if (e == cudaSuccess) e = cudaMallocHost(&b->h_phi_stage, (size_t)count * sizeof(PhiCloud));
-  if (e == cudaSuccess) e = cudaMallocHost(&b->h_norms, (size_t)count * sizeof(double));
-  if (e == cudaSuccess) e = cudaMallocHost(&b->h_flags, (size_t)count * sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+  b->d_feat = reinterpret_cast<FeatJob*>(D + o_feat);
+  b->d_feat_prefix = reinterpret_cast<int*>(D + o_feat_pre);
+  b->d_fill = reinterpret_cast<FillJob*>(D + o_fill);
+  b->d_fill_prefix = reinterpret_cast<int*>(D + o_fill_pre);
+  b->d_apply = reinterpret_cast<ApplyJob*>(D + o_apply);
+  b->d_small_prefix = reinterpret_cast<int*>(D + o_small_pre);
+  b->d_phi = reinterpret_cast<PhiCloud*>(D + o_phi);
+  b->d_elem_prefix = reinterpret_cast<int*>(D + o_elem_pre);
+  b->d_rowa_prefix = reinterpret_cast<int*>(D + o_rowa_pre);
+  b->d_strip_prefix = reinterpret_cast<int*>(D + o_strip_pre);
+  b->d_oz = reinterpret_cast<OzTile*>(D + o_oz);
+  b->d_calls = reinterpret_cast<CloudCall*>(D + o_calls);
+  b->d_norms = reinterpret_cast<double*>(D + o_norms);
+  b->d_sv = reinterpret_cast<int*>(D + o_sv);
+  b->d_flags = reinterpret_cast<int*>(D + o_flags);
+  b->d_err = b->d_flags + count;
+  for (int k = 0; k < count; ++k) phi[k].flag = b->d_flags + k;
+  for (const Sec& s : secs)
+    if (s.bytes) std::memcpy(b->hblob + s.off, s.src, s.bytes);
+  for (int i = 0; i < BatchImpl::kStageRing; ++i) b->h_stage[i] = b->hblob + o_stage[i];
+  b->h_norms = reinterpret_cast<double*>(b->hblob + o_hn);
+  b->h_sv = reinterpret_cast<int*>(b->hblob + o_hsv);
+  b->h_flags = reinterpret_cast<int*>(b->hblob + o_hf);
+  cudaError_t e = cudaMemcpyAsync(b->dblob, b->hblob, table_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->dblob + table_bytes, 0, b->dbytes - table_bytes, st);
+  for (int i = 0; i < BatchImpl::kStageRing && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&b->stage_done[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_mid, cudaEventDisableTiming);
+  if (e == cudaSuccess && (options & kBatchGraphs)) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = gram_tc_prepare();
+  if (e == cudaSuccess) e = bgemm_prepare();
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return bail(e == cudaErrorMemoryAllocation ? RFD_ENOMEM : RFD_ECUDA,
-                std::string("batch set-up: ") + cudaGetErrorString(e));
+    return bail(RFD_ECUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
   }
-  for (int k = 0; k < count; ++k) b->h_phi[k].flag = b->d_flags + k;
   *out = b;
   return RFD_OK;
 }
@@ -276,9 +333,26 @@ rfd_status cuda_fail2(const char* what, cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail2(#call, e_); \
   } while (0)
 
-// Step a4 for every cloud of the batch (emulated FP64 on the tensor cores).
-rfd_status phi1_batched(BatchImpl* b) {
-  cudaStream_t st = b->st;
+// Step a4, first part, for every cloud: X = lambda M, ||X||_1, and the
+// squarings s_c (device); the s_c and norms are copied to pinned memory.
+rfd_status phi1_select(BatchImpl* b, cudaStream_t st) {
+  const int n = b->count;
+  const int src[4] = {kSlotM, 0x7fffffff, 0x7fffffff, 0x7fffffff};
+  const double a[4] = {1.0, 0.0, 0.0, 0.0};
+  BCK(launch_bcombine(b->d_phi, b->d_elem_prefix, n, b->elem_blocks, sX, src, a, 0.0, 1, -1, st));  // X = lambda M
+  BCK(launch_bnorm1(b->d_phi, n, b->max_m, sX, b->d_norms, st));
+  BCK(launch_bselect(b->d_phi, n, b->d_norms, kTheta5, kMaxSquarings, b->d_sv, st));
+  BCK(cudaMemcpyAsync(b->h_sv, b->d_sv, (size_t)(n + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+  BCK(cudaMemcpyAsync(b->h_norms, b->d_norms, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return RFD_OK;
+}
+
+// Step a4, second part: diagonal Pade of degree 5 at 2^-s_c X, the product-form
+// solve, max_s masked squaring steps, G = lambda F, and the finiteness flags.
+// The combinations ride in the product epilogues (D = alpha A B + beta C +
+// diag I): R = I - Vp + X Sp, F_0 = (I + R) 2 Sp, F_j+1 = F_j + R^(2^j) F_j,
+// E = I + X F, F <- (E F + F) / 2; slots are swapped instead of copied.
+rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s) {
   const int n = b->count;
   auto comb = [&](int dst, std::initializer_list<int> src, std::initializer_list<double> a, double diag, int kmode,
                   int mask) {
@@ -290,112 +364,46 @@ rfd_status phi1_batched(BatchImpl* b) {
     for (double v : a) a4[i++] = v;
     return launch_bcombine(b->d_phi, b->d_elem_prefix, n, b->elem_blocks, dst, s4, a4, diag, kmode, mask, st);
   };
-  int gemms = 0;
-  auto gemm = [&](int a, int bb, int c, double alpha, double beta, int mask) {
-    ++gemms;
-    return launch_bgemm(b->d_phi, n, b->d_rowa_prefix, b->rows_a, b->d_rowb_prefix, b->rows_b, b->d_t_prefix,
-                        b->t_blocks, b->d_oz, b->n_oz, b->d_maps, a, bb, c, alpha, beta, mask, b->d_err, st);
+  auto gemm = [&](int a, int bb, int c, int d, double alpha, double beta, double diag, int mask) {
+    return launch_bgemm(b->d_phi, n, b->d_rowa_prefix, b->rows_a, b->d_strip_prefix, b->col_strips, b->d_oz,
+                        b->n_oz, b->d_maps, a, bb, c, d, alpha, beta, diag, mask, b->d_err, st);
   };
-  // the per-call fields of the cloud descriptors are not known yet: upload with s = 0
-  for (int k = 0; k < n; ++k) {
-    b->h_phi[k].s = 0;
-    b->h_phi[k].scale = 1.0;
-  }
-  std::memcpy(b->h_phi_stage, b->h_phi.data(), (size_t)n * sizeof(PhiCloud));
-  BCK(cudaMemcpyAsync(b->d_phi, b->h_phi_stage, (size_t)n * sizeof(PhiCloud), cudaMemcpyHostToDevice, st));
-  BCK(comb(sX, {kSlotM}, {1.0}, 0.0, 1, -1));  // X = lambda M
-  BCK(launch_bnorm1(b->d_phi, n, b->max_m, sX, b->d_norms, st));
-  BCK(cudaMemcpyAsync(b->h_norms, b->d_norms, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
-  BCK(cudaStreamSynchronize(st));
-  int max_s = 0;
-  std::string bad;
-  for (int k = 0; k < n; ++k) {
-    const double nrm = b->h_norms[k];
-    rfd_plan_s* pl = b->plans[k];
-    pl->stats.norm1 = nrm;
-    pl->stats.nonfinite = 0;
-    if (!std::isfinite(nrm)) {
-      pl->stats.nonfinite = 1;
-      bad += (bad.empty() ? "" : ",") + std::to_string(k);
-      continue;
-    }
-    int s = 0;
-    if (nrm > kTheta5) s = (int)std::ceil(std::log2(nrm / kTheta5));
-    if (s > 1000) {
-      pl->stats.nonfinite = 1;
-      bad += (bad.empty() ? "" : ",") + std::to_string(k);
-      continue;
-    }
-    b->h_phi[k].s = s;
-    b->h_phi[k].scale = std::ldexp(1.0, -s);
-    max_s = std::max(max_s, s);
-    pl->stats.pade_degree = 5;
-    pl->stats.squarings = s;
-    pl->stats.phi1_emulated = 1;
-  }
-  if (!bad.empty()) return fail(RFD_ENUMERIC, "||lambda M||_1 is not finite for cloud(s) " + bad);
-  std::memcpy(b->h_phi_stage, b->h_phi.data(), (size_t)n * sizeof(PhiCloud));
-  BCK(cudaMemcpyAsync(b->d_phi, b->h_phi_stage, (size_t)n * sizeof(PhiCloud), cudaMemcpyHostToDevice, st));
   // diagonal Pade, degree 5: b_k = (10-k)! 5! / (10! k! (5-k)!) with b_0 = 1
   double pb[6];
   pb[0] = 1.0;
   for (int k = 0; k < 5; ++k) pb[k + 1] = pb[k] * double(5 - k) / (double(10 - k) * double(k + 1));
   if (max_s > 0) BCK(comb(sX, {sX}, {1.0}, 0.0, 2, -1));  // X = 2^-s X
-  BCK(gemm(sX, sX, sX2, 1.0, 0.0, -1));
-  BCK(gemm(sX2, sX2, sX4, 1.0, 0.0, -1));
+  BCK(gemm(sX, sX, kNoSlot, sX2, 1.0, 0.0, 0.0, -1));
+  BCK(gemm(sX2, sX2, kNoSlot, sX4, 1.0, 0.0, 0.0, -1));
   BCK(comb(sSp, {sX4, sX2}, {pb[5], pb[3]}, pb[1], 0, -1));
   BCK(comb(sVp, {sX4, sX2}, {pb[4], pb[2]}, pb[0], 0, -1));
-  BCK(gemm(sX, sSp, sUp, 1.0, 0.0, -1));
-  BCK(comb(sR, {sVp, sUp}, {-1.0, 1.0}, 1.0, 0, -1));  // R = I - (Vp - Up)
-  BCK(comb(sF, {sSp}, {2.0}, 0.0, 0, -1));             // F = 2 Sp
+  BCK(gemm(sX, sSp, sVp, sR, 1.0, -1.0, 1.0, -1));  // R = I - (Vp - Up), Up = X Sp
+  BCK(gemm(sR, sSp, sSp, sF, 2.0, 2.0, 0.0, -1));   // F = (I + R) 2 Sp
   int F = sF, Fb = sFb, R = sR, R2 = sR2;
-  for (int j = 0; j < kSolveFactors; ++j) {
-    BCK(comb(Fb, {F}, {1.0}, 0.0, 0, -1));
-    BCK(gemm(R, F, Fb, 1.0, 1.0, -1));  // F <- F + R^(2^j) F
+  for (int j = 1; j < kSolveFactors; ++j) {
+    BCK(gemm(R, R, kNoSlot, R2, 1.0, 0.0, 0.0, -1));  // R^(2^j)
+    std::swap(R, R2);
+    BCK(gemm(R, F, F, Fb, 1.0, 1.0, 0.0, -1));  // F <- F + R^(2^j) F
     std::swap(F, Fb);
-    if (j + 1 < kSolveFactors) {
-      BCK(gemm(R, R, R2, 1.0, 0.0, -1));
-      std::swap(R, R2);
-    }
   }
   if (max_s > 0) {
-    BCK(comb(sE, {}, {}, 1.0, 0, -1));
-    BCK(gemm(sX, F, sE, 1.0, 1.0, -1));  // E = I + X F
+    int E = sE, E2 = sT1;
+    BCK(gemm(sX, F, kNoSlot, E, 1.0, 0.0, 1.0, -1));  // E = I + X F
     for (int k = 0; k < max_s; ++k) {
-      BCK(gemm(sE, F, sT1, 1.0, 0.0, k));
-      BCK(comb(F, {F, sT1}, {0.5, 0.5}, 0.0, 0, k));  // F <- (F + E F) / 2
+      BCK(gemm(E, F, F, Fb, 0.5, 0.5, 0.0, k));  // F <- (E F + F) / 2 (clouds with s <= k copy F)
+      std::swap(F, Fb);
       if (k + 1 < max_s) {
-        BCK(gemm(sE, sE, sT2, 1.0, 0.0, k + 1));
-        BCK(comb(sE, {sT2}, {1.0}, 0.0, 0, k + 1));
+        BCK(gemm(E, E, kNoSlot, E2, 1.0, 0.0, 0.0, k + 1));  // E <- E^2 (clouds with s <= k + 1 skip)
+        std::swap(E, E2);
       }
     }
   }
   BCK(comb(kSlotG, {F}, {1.0}, 0.0, 1, -1));  // G = lambda F
-  BCK(cudaMemsetAsync(b->d_flags, 0, (size_t)n * sizeof(int), st));
   BCK(launch_bfinite(b->d_phi, b->d_elem_prefix, n, b->elem_blocks, kSlotG, st));
-  BCK(cudaMemcpyAsync(b->h_flags, b->d_flags, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, st));
-  int err = 0;
-  BCK(cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  BCK(cudaStreamSynchronize(st));
-  if (err) {
-    cudaMemsetAsync(b->d_err, 0, sizeof(int), st);
-    return fail(RFD_ETIMEDOUT, "a device-side wait ran out in the batched phi1 (code " + std::to_string(err) + ")");
-  }
-  for (int k = 0; k < n; ++k) {
-    rfd_plan_s* pl = b->plans[k];
-    const int s = b->h_phi[k].s;
-    pl->stats.phi1_gemms = 3 + 2 * kSolveFactors - 1 + (s > 0 ? 2 * s : 0);
-    if (b->h_flags[k]) {
-      pl->stats.nonfinite = 1;
-      bad += (bad.empty() ? "" : ",") + std::to_string(k);
-    }
-  }
-  (void)gemms;
-  if (!bad.empty()) return fail(RFD_ENUMERIC, "G = lambda phi1(lambda M) is not finite for cloud(s) " + bad);
   return RFD_OK;
 }
 
-// Step a4 one cloud at a time (native FP64, or clouds beyond the emulated path's m <= 1024).
+// Step a4 one cloud at a time (native FP64 requested).
 rfd_status phi1_per_plan(BatchImpl* b) {
   for (rfd_plan_s* pl : b->plans) {
     Phi1Info info{};
@@ -414,6 +422,35 @@ rfd_status phi1_per_plan(BatchImpl* b) {
   return RFD_OK;
 }
 
+// Runs enqueue(stream, timing) on the batch's stream, or (kBatchGraphs) replays
+// the graph captured for `key`, capturing it on first use.
+template <typename Fn>
+rfd_status run_segment(BatchImpl* b, const int (&key)[4], bool graph, Timing* tm, Fn enqueue) {
+  if (!graph) return enqueue(b->st, tm);
+  BatchImpl::Graph* g = nullptr;
+  for (auto& x : b->graphs)
+    if (std::equal(key, key + 4, x.key)) g = &x;
+  if (!g) {
+    BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    const long long l0 = t_kernel_launches;
+    rfd_status s = enqueue(b->cap, nullptr);
+    const long long nl = t_kernel_launches - l0;
+    t_kernel_launches = l0;
+    cudaGraph_t graph_obj = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap, &graph_obj);
+    cudaGraphExec_t exec = nullptr;
+    if (s == RFD_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph_obj, 0);
+    if (graph_obj) cudaGraphDestroy(graph_obj);
+    if (s != RFD_OK) return s;
+    if (e != cudaSuccess) return cuda_fail2("CUDA graph capture", e);
+    b->graphs.push_back(BatchImpl::Graph{{key[0], key[1], key[2], key[3]}, exec, nl});
+    g = &b->graphs.back();
+  }
+  BCK(cudaGraphLaunch(g->exec, b->st));
+  count_launch(g->launches);
+  return RFD_OK;
+}
+
 }  // namespace
 
 rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm) {
@@ -427,53 +464,101 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   const int slot = b->stage_next;
   b->stage_next = (slot + 1) % BatchImpl::kStageRing;
   BCK(cudaEventSynchronize(b->stage_done[slot]));
-  unsigned char* stage = b->h_stage_ring[slot];
+  unsigned char* stage = b->h_stage[slot];
   auto* hc = reinterpret_cast<CloudCall*>(stage);
   auto* hp = reinterpret_cast<int*>(stage + (size_t)n * sizeof(CloudCall));
   hp[0] = 0;
   for (int k = 0; k < n; ++k) {
     hc[k] = calls[k];
-    const int nb = (mode == kModeFeatures) ? 0 : b->h_apply[k].bx * ((calls[k].c + cg - 1) / cg);
+    const int nb = (mode == kModeFeatures) ? 0 : b->apply_bx[k] * ((calls[k].c + cg - 1) / cg);
     hp[k + 1] = hp[k] + nb;
   }
   const int apply_blocks = hp[n];
-  BCK(cudaMemcpyAsync(b->d_calls, stage, (size_t)n * sizeof(CloudCall) + (size_t)(n + 1) * sizeof(int),
-                      cudaMemcpyHostToDevice, st));
+  const int* d_apply_prefix = reinterpret_cast<const int*>(reinterpret_cast<unsigned char*>(b->d_calls) +
+                                                           (size_t)n * sizeof(CloudCall));
+  BCK(cudaMemcpyAsync(b->d_calls, stage, b->stage_bytes, cudaMemcpyHostToDevice, st));
   BCK(cudaEventRecord(b->stage_done[slot], st));
-  if (mode != kModeIntegrate) {
-    StepScope t(tm, st, RFD_STEP_FEATURES);
-    BCK(launch_features_batched(b->d_feat, b->d_feat_prefix, n, b->feat_blocks, b->d_calls, st));
-  }
-  if (mode != kModeFeatures) {
-    StepScope t(tm, st, RFD_STEP_FIELD);
-    BCK(launch_fill_batched(b->d_fill, b->d_fill_prefix, n, b->fill_blocks, b->d_calls, st));
-  }
-  {
-    StepScope t(tm, st, RFD_STEP_GRAM);
-    BCK(launch_gram_tc(b->d_maps, b->d_units[mode], b->n_units[mode], b->max_cpad, b->d_err, st));
-  }
-  {
-    StepScope t(tm, st, RFD_STEP_REDUCE);
-    BCK(launch_reduce_batched(b->d_red[mode], b->n_red[mode], b->d_calls, st));
-  }
-  if (mode != kModeIntegrate) {
-    for (rfd_plan_s* pl : b->plans) pl->have_G = false;
-    rfd_status s;
-    {
-      StepScope t(tm, st, RFD_STEP_PHI1);
-      s = b->phi_batched ? phi1_batched(b) : phi1_per_plan(b);
+  const bool with_phi = mode != kModeIntegrate, with_apply = mode != kModeFeatures;
+  const bool graph = (b->options & kBatchGraphs) && (!with_phi || b->phi_batched);
+
+  auto reductions = [&](cudaStream_t s, Timing* t) -> rfd_status {
+    if (with_phi) {
+      StepScope sc(t, s, RFD_STEP_FEATURES);
+      BCK(launch_features_batched(b->d_feat, b->d_feat_prefix, n, b->feat_blocks, b->d_calls, s));
     }
-    if (s != RFD_OK) return s;
+    if (with_apply) {
+      StepScope sc(t, s, RFD_STEP_FIELD);
+      BCK(launch_fill_batched(b->d_fill, b->d_fill_prefix, n, b->fill_blocks, b->d_calls, s));
+    }
+    {
+      StepScope sc(t, s, RFD_STEP_GRAM);
+      BCK(launch_gram_tc(b->d_maps, b->d_units[mode], b->n_units[mode], b->max_cpad, b->max_kb, b->d_err, s));
+    }
+    StepScope sc(t, s, RFD_STEP_REDUCE);
+    BCK(launch_reduce_batched(b->d_red[mode], b->n_red[mode], b->d_calls, s));
+    return RFD_OK;
+  };
+  auto small_apply = [&](cudaStream_t s, Timing* t) -> rfd_status {
+    {
+      StepScope sc(t, s, RFD_STEP_SMALL);
+      BCK(launch_small_batched(b->d_apply, b->d_small_prefix, n, b->small_rows, b->d_calls, s));
+    }
+    StepScope sc(t, s, RFD_STEP_APPLY);
+    BCK(launch_apply_batched(b->d_apply, d_apply_prefix, n, apply_blocks, cg, b->d_calls, s));
+    return RFD_OK;
+  };
+
+  if (!with_phi) {
+    const int key[4] = {mode, -1, cg, apply_blocks};
+    return run_segment(b, key, graph, tm, [&](cudaStream_t s, Timing* t) -> rfd_status {
+      rfd_status r = reductions(s, t);
+      return r == RFD_OK ? small_apply(s, t) : r;
+    });
+  }
+  for (rfd_plan_s* pl : b->plans) pl->have_G = false;
+  if (!b->phi_batched) {
+    rfd_status r = reductions(st, tm);
+    if (r != RFD_OK) return r;
+    {
+      StepScope sc(tm, st, RFD_STEP_PHI1);
+      r = phi1_per_plan(b);
+    }
+    if (r != RFD_OK) return r;
     for (rfd_plan_s* pl : b->plans) pl->have_G = true;
+    return with_apply ? small_apply(st, tm) : RFD_OK;
   }
-  if (mode != kModeFeatures) {
+  // reductions, then the first part of a4; the host learns the largest s_c
+  const int key_pre[4] = {mode, -2, 0, 0};
+  rfd_status r = run_segment(b, key_pre, graph, tm, [&](cudaStream_t s, Timing* t) -> rfd_status {
+    rfd_status q = reductions(s, t);
+    if (q != RFD_OK) return q;
+    StepScope sc(t, s, RFD_STEP_PHI1);
+    return phi1_select(b, s);
+  });
+  if (r != RFD_OK) return r;
+  BCK(cudaEventRecord(b->ev_mid, st));
+  BCK(cudaEventSynchronize(b->ev_mid));
+  const int max_s = std::min(std::max(b->h_sv[n], 0), kMaxSquarings);
+  for (int k = 0; k < n; ++k) {
+    rfd_plan_s* pl = b->plans[k];
+    const int s = b->h_sv[k];
+    pl->stats.norm1 = b->h_norms[k];
+    pl->stats.pade_degree = 5;
+    pl->stats.squarings = s;
+    pl->stats.phi1_emulated = 1;
+    pl->stats.phi1_gemms = 3 + 2 * kSolveFactors - 1 + (s > 0 ? 2 * s : 0);
+  }
+  const int key_post[4] = {mode, max_s, with_apply ? cg : 0, with_apply ? apply_blocks : 0};
+  r = run_segment(b, key_post, graph, tm, [&](cudaStream_t s, Timing* t) -> rfd_status {
     {
-      StepScope t(tm, st, RFD_STEP_SMALL);
-      BCK(launch_small_batched(b->d_apply, b->d_small_prefix, n, b->small_rows, b->d_calls, st));
+      StepScope sc(t, s, RFD_STEP_PHI1);
+      rfd_status q = phi1_core(b, s, max_s);
+      if (q != RFD_OK) return q;
     }
-    StepScope t(tm, st, RFD_STEP_APPLY);
-    BCK(launch_apply_batched(b->d_apply, b->d_apply_prefix, n, apply_blocks, cg, b->d_calls, st));
-  }
+    return with_apply ? small_apply(s, t) : RFD_OK;
+  });
+  if (r != RFD_OK) return r;
+  for (rfd_plan_s* pl : b->plans) pl->have_G = true;
   return RFD_OK;
 }
 
@@ -531,14 +616,24 @@ void Timing::reset(cudaStream_t st) {
   launches = 0;
 }
 
-rfd_status batch_check_error(BatchImpl* b) {
-  int err = 0;
-  BCK(cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+rfd_status batch_check_error(BatchImpl* b, int* bad) {
+  const int n = b->count;
+  BCK(cudaMemcpyAsync(b->h_flags, b->d_flags, (size_t)(n + 1) * sizeof(int), cudaMemcpyDeviceToHost, b->st));
   BCK(cudaStreamSynchronize(b->st));
-  if (err) {
-    cudaMemsetAsync(b->d_err, 0, sizeof(int), b->st);
-    return fail(RFD_ETIMEDOUT, "a device-side wait ran out (code " + std::to_string(err) + ")");
+  const int err = b->h_flags[n];
+  std::string clouds;
+  for (int k = 0; k < n; ++k) {
+    if (bad) bad[k] = b->h_flags[k] ? 1 : 0;
+    if (!b->h_flags[k]) continue;
+    b->plans[k]->stats.nonfinite = 1;
+    b->plans[k]->have_G = false;
+    clouds += (clouds.empty() ? "" : ",") + std::to_string(k);
   }
+  if (err || !clouds.empty()) BCK(cudaMemsetAsync(b->d_flags, 0, (size_t)(n + 1) * sizeof(int), b->st));
+  if (err) return fail(RFD_ETIMEDOUT, "a device-side wait ran out (code " + std::to_string(err) + ")");
+  if (!clouds.empty())
+    return fail(RFD_ENUMERIC, "G = lambda phi1(lambda M) is not finite for cloud(s) " + clouds +
+                                  (n == 1 ? "" : " of the batch"));
   return RFD_OK;
 }
 

@@ -39,12 +39,13 @@ struct Timing {
 };
 
 // Records CUDA events around one step on a stream (no-op when timing is off).
+// A second scope of the same step in one call extends the first.
 struct StepScope {
   Timing* t;
   cudaStream_t st;
   int step;
   StepScope(Timing* tt, cudaStream_t s, int k) : t(tt), st(s), step(k) {
-    if (t && t->cur) cudaEventRecord(t->cur->ev[2 * step], st);
+    if (t && t->cur && !t->cur->used[step]) cudaEventRecord(t->cur->ev[2 * step], st);
   }
   ~StepScope() {
     if (t && t->cur) {
@@ -81,6 +82,21 @@ struct PlanDesc {
 
 struct BatchImpl;  // rfd_batch.cu
 
+// Where the device and pinned host memory of plans and batches comes from: the
+// CUDA allocator (the default), or a server's pools, which hand out memory
+// without cudaMalloc / cudaFree (both can synchronise the device).
+struct MemSource {
+  virtual ~MemSource() = default;
+  virtual void* dev(size_t bytes) = 0;  // nullptr when out of memory
+  virtual void dev_free(void* p) = 0;
+  virtual void* pinned(size_t bytes) = 0;
+  virtual void pinned_free(void* p) = 0;
+};
+MemSource* cuda_mem();  // cudaMalloc / cudaMallocHost, with the allocation-failure test hook
+
+// Batch options
+enum : int { kBatchGraphs = 1 };  // replay the batch's launches from CUDA graphs
+
 }  // namespace rfd
 
 struct rfd_plan_s {
@@ -90,14 +106,18 @@ struct rfd_plan_s {
   int64_t n = 0, n_pad = 0;
   int rows_alloc = 0;
   bool bf16 = false;
+  bool fsplit = false;  // F as hi + lo BF16 rows (BF16 form, 2 max_channels <= 256)
   std::vector<double> omega, r, oa, ob;
   float* d_omega_hi = nullptr;
   float* d_omega_lo = nullptr;
   double* d_oa = nullptr;
   double* d_ob = nullptr;
+  float* d_xyz = nullptr;  // BF16 form: copy of the points, written by the features step
   void* d_psi = nullptr;
   float* d_part = nullptr;
+  int part_slots = 0;
   int64_t slot_elems = 0;
+  std::vector<float> omega_hi_h, omega_lo_h;  // FP32 split of omega (hi + lo)
   double* d_M = nullptr;
   double* d_Y = nullptr;
   double* d_G = nullptr;
@@ -111,20 +131,38 @@ struct rfd_plan_s {
   rfd::BatchImpl* self = nullptr;             // the plan as a batch of one (BF16 form)
   bool have_G = false;
   rfd_stats stats{};
-  std::vector<void*> allocs;
+  std::vector<void*> allocs;       // temporary owners only (rfd_phi1, debug GEMM)
+  rfd::MemSource* mem = nullptr;   // source of the plan's single device chunk
+  void* chunk = nullptr;
+  size_t chunk_bytes = 0;
   rfd::Timing timing;
 };
 
 namespace rfd {
 
-// Builds / frees the device tables of a batch over the given BF16 plans.
-rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, BatchImpl** out);
-void batch_free(BatchImpl* b);
+// Plans: validation and host set-up (no device memory), the size of the plan's
+// device chunk, and the device half (chunk from `mem`, descriptors, uploads on
+// the plan's stream; `self_batch` also builds the plan's batch of one).
+rfd_status plan_prepare(const rfd_params& p, cudaStream_t st, rfd_plan_s** out);
+size_t plan_device_bytes(rfd_plan_s* pl);
+rfd_status plan_materialize(rfd_plan_s* pl, MemSource* mem, bool self_batch, bool sync_init);
+void plan_destroy(rfd_plan_s* pl);  // frees without synchronising (the caller has)
+
+// Builds / frees the device tables of a batch over the given BF16 plans (one
+// device and one pinned block from `mem`; uploads are asynchronous on `st`).
+rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, MemSource* mem, int options,
+                       BatchImpl** out);
+void batch_free(BatchImpl* b);  // the caller has synchronised the batch's stream
+size_t batch_device_bytes(BatchImpl* b);
 // Runs one batched call.  calls: one CloudCall per plan (pts / F / out as the
-// mode needs).  Updates each plan's stats and have_G.
+// mode needs).  Updates each plan's stats and have_G.  Non-finite G and
+// device-side timeouts are reported by batch_check_error.
 rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* timing);
 cudaStream_t batch_stream(BatchImpl* b);
-// Reads (and clears) the batch's device error word: RFD_ETIMEDOUT if a bounded wait ran out.
-rfd_status batch_check_error(BatchImpl* b);
+// Synchronises the batch's stream and reads (and clears) its device error word
+// and per-cloud finiteness flags: RFD_ETIMEDOUT if a bounded wait ran out,
+// RFD_ENUMERIC if some cloud's G is not finite (bad[k] = 1 for those clouds when
+// bad is given).
+rfd_status batch_check_error(BatchImpl* b, int* bad = nullptr);
 
 }  // namespace rfd

@@ -89,3 +89,49 @@ def test_batch_rejects_fp32_and_repeated_plans():
     assert e.value.status == rfd.RFD_EINVAL
     p16.close()
     p32.close()
+
+
+def test_batch_graph_replay_matches_direct_launches():
+    specs = _specs(count=6, seed=12)
+    clouds = [synth.make_cloud(s) for s in specs]
+    stream = torch.cuda.current_stream(DEV)
+    plans = _plans(specs, stream)
+    direct = rfd.Batch(plans, stream=stream)
+    items = [{"points": torch.from_numpy(p).to(DEV), "F": torch.from_numpy(F).to(DEV)} for p, F in clouds]
+    ref = [o.cpu().numpy() for o in direct.gfi(items)]
+    direct.sync()
+    direct.close()
+    graph = rfd.Batch(plans, stream=stream, graph=True)
+    for rep in range(3):   # first call captures, the others replay
+        outs = graph.gfi(items)
+        graph.sync()
+        for k in range(len(specs)):
+            np.testing.assert_array_equal(outs[k].cpu().numpy(), ref[k])   # same launches, same bits
+    # warm integrate under a graph as well
+    fields = [synth.gaussian_field(s.n, s.c, 500, k) for k, s in enumerate(specs)]
+    outs = graph.integrate([{"F": torch.from_numpy(F).to(DEV)} for F in fields])
+    graph.sync()
+    for k, s in enumerate(specs):
+        want = oracle.rfd_gfi(clouds[k][0], fields[k], s.eps, _lam(s), s.m, s.seed)
+        assert oracle.rel_frobenius(outs[k].cpu().numpy(), want) <= TOL
+    assert graph.stats()["kernel_launches"] > 0
+    graph.close()
+    for p in plans:
+        p.close()
+
+
+def test_nonfinite_G_is_reported_at_sync():
+    s = _specs(count=1, seed=2)[0]
+    pts, F = synth.make_cloud(s)
+    p = rfd.Plan(s.n, s.m, s.eps, 1e30, s.seed, max_channels=8, precision=rfd.RFD_BF16_TC)
+    P, Fd = torch.from_numpy(pts).to(DEV), torch.from_numpy(F).to(DEV)
+    p.gfi(P, Fd)   # enqueues; ||lambda M||_1 needs more than 60 squarings: flagged on the device
+    with pytest.raises(rfd.RfdError) as e:
+        p.sync()
+    assert e.value.status == rfd.RFD_ENUMERIC
+    assert p.stats()["nonfinite"] == 1
+    with pytest.raises(rfd.RfdError) as e:   # G is not resident after a failed features pass
+        p.integrate(Fd)
+    assert e.value.status == rfd.RFD_EINVAL
+    p.sync()   # the flags were cleared by the first sync
+    p.close()

@@ -23,7 +23,8 @@ def _run(method, A, B, C0=None, alpha=1.0, beta=0.0):
     return Ct.cpu().numpy()
 
 
-@pytest.mark.parametrize("M,N,K", [(1024, 1024, 1024), (1000, 777, 999), (1, 1, 1), (130, 65, 64), (257, 300, 33)])
+@pytest.mark.parametrize("M,N,K", [(1024, 1024, 1024), (1000, 777, 999), (1, 1, 1), (130, 65, 64), (257, 300, 33),
+                                   (256, 192, 2048), (100, 70, 4096)])
 def test_integer_matrices_exact(M, N, K):
     """Integer entries below 2^20: every FP64 product and partial sum is exact, so the
     emulated result must equal the exact integer result bit for bit."""
@@ -35,7 +36,7 @@ def test_integer_matrices_exact(M, N, K):
     np.testing.assert_array_equal(_run(1, A, B), ref)
 
 
-@pytest.mark.parametrize("M,N,K", [(512, 512, 512), (1024, 1024, 1024), (200, 130, 1000)])
+@pytest.mark.parametrize("M,N,K", [(512, 512, 512), (1024, 1024, 1024), (200, 130, 1000), (300, 200, 3000)])
 def test_real_matrices_against_exact_dot_products(M, N, K):
     rng = np.random.default_rng(K)
     A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-20, 20, (M, 1)))   # rows over ~17 decades
