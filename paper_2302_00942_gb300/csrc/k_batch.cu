@@ -2,7 +2,8 @@
 // one launch serves every cloud of a batch (a single cloud is a batch of one).
 // Jobs with a per-cloud number of blocks find their cloud by binary search over
 // a prefix array of block counts (prefix[count] = total blocks).
-//   a2  features_batched:  Phi[n, j] = cos 2 pi w_j^T x_n, Phi[n, h+j] = sin ..., bf16, feature-major
+//   a2  features_batched:  Phi[n, j] = cos 2 pi w_j^T x_n, Phi[n, h+j] = sin ..., bf16, blocked layout
+//                          (64-point blocks of all rows, psi_index)
 //       fill_batched:      F^T into rows m.. of the same buffer (bf16)
 //   a3  reduce_batched:    fixed-order sum of the split-K partials, column scales applied
 //   a5  small_batched:     Z = diag(s sgn r) G Y
@@ -27,6 +28,14 @@ __device__ __forceinline__ int find_job(const int* __restrict__ prefix, int coun
       hi = mid;
   }
   return lo;
+}
+
+// Nearest integer of |t| < 2^22 with two FP32 additions (round to nearest
+// even): adding 1.5 2^23 leaves no fraction bits.  Keeps the rounding on the
+// FMA pipe instead of the slower conversion unit.
+__device__ __forceinline__ float round_int(float t) {
+  constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+  return __fsub_rn(__fadd_rn(t, kMagic), kMagic);
 }
 
 constexpr int kFeatThreads = 256;
@@ -67,13 +76,14 @@ features_batched_kernel(const FeatJob* __restrict__ jobs, const int* __restrict_
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const float t = fmaf(w0, x[q][0], fmaf(w1, x[q][1], w2 * x[q][2]));
-      const float a = two_pi * (t - rintf(t));   // |a| <= pi: MUFU sin/cos accurate to ~1e-6
+      const float a = two_pi * (t - round_int(t));   // |a| <= pi: MUFU sin/cos accurate to ~1e-6
       c[q] = valid[q] ? __cosf(a) : 0.f;
       s[q] = valid[q] ? __sinf(a) : 0.f;
     }
     const int jg = j0 + jj;
-    *reinterpret_cast<__nv_bfloat162*>(psi + (size_t)jg * jb.n_pad + p0) = __floats2bfloat162_rn(c[0], c[1]);
-    *reinterpret_cast<__nv_bfloat162*>(psi + (size_t)(jb.h + jg) * jb.n_pad + p0) = __floats2bfloat162_rn(s[0], s[1]);
+    *reinterpret_cast<__nv_bfloat162*>(psi + psi_index(p0, jg, jb.rows_alloc)) = __floats2bfloat162_rn(c[0], c[1]);
+    *reinterpret_cast<__nv_bfloat162*>(psi + psi_index(p0, jb.h + jg, jb.rows_alloc)) =
+        __floats2bfloat162_rn(s[0], s[1]);
   }
 }
 
@@ -88,19 +98,19 @@ fill_batched_kernel(const FillJob* __restrict__ jobs, const int* __restrict__ pr
   const CloudCall cc = calls[jb.cloud];
   const int64_t p = (int64_t)(blockIdx.x - prefix[j]) * 256 + threadIdx.x;
   if (p >= jb.n_pad) return;
-  auto* rows = reinterpret_cast<__nv_bfloat16*>(jb.rows);
-  const int c = cc.c;
+  auto* psi = reinterpret_cast<__nv_bfloat16*>(jb.psi);
+  const int c = cc.c, r0 = jb.row0, ra = jb.rows_alloc;
   const bool valid = p < jb.n;
   const float* f = cc.F + (valid ? p * cc.ldF : 0);
   for (int ch = 0; ch < c; ++ch) {
     const float v = valid ? f[ch] : 0.f;
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    rows[(size_t)ch * jb.n_pad + p] = hi;
+    psi[psi_index(p, r0 + ch, ra)] = hi;
     // row c + ch: the lo part of channel ch (fsplit)
-    if (jb.fsplit) rows[(size_t)(c + ch) * jb.n_pad + p] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    if (jb.fsplit) psi[psi_index(p, r0 + c + ch, ra)] = __float2bfloat16_rn(v - __bfloat162float(hi));
   }
   const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
-  for (int row = jb.fsplit ? 2 * c : c; row < jb.cpad; ++row) rows[(size_t)row * jb.n_pad + p] = zero;
+  for (int row = jb.fsplit ? 2 * c : c; row < jb.cpad; ++row) psi[psi_index(p, r0 + row, ra)] = zero;
 }
 
 // One thread per tile element; lanes summed in order (deterministic) in FP64.
@@ -208,8 +218,8 @@ apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ 
         const float e0 = fmaf(wl[fr][0], x0, fmaf(wh[fr][0], x0, -a0));
         const float e1 = fmaf(wl[fr][1], x1, fmaf(wh[fr][1], x1, -a1));
         const float e2 = fmaf(wl[fr][2], x2, fmaf(wh[fr][2], x2, -a2));
-        float r = ((a0 - rintf(a0)) + (a1 - rintf(a1))) + ((a2 - rintf(a2)) + ((e0 + e1) + e2));
-        r -= rintf(r);
+        float r = ((a0 - round_int(a0)) + (a1 - round_int(a1))) + ((a2 - round_int(a2)) + ((e0 + e1) + e2));
+        r -= round_int(r);
         const float ang = two_pi * r;
         const float cs = __cosf(ang), sn = __sinf(ang);
 #pragma unroll

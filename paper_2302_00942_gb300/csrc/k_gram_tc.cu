@@ -5,7 +5,9 @@
 //   K[f, g]  = sum_n Psi[i0 + f][n] * Psi[j0 + g][n]     (Phi^T Phi, upper tiles)
 //   Y'[f, c] = sum_n Psi[i0 + f][n] * Psi[m + c][n]      (Phi^T F)
 //
-// Psi (bf16, feature-major: n contiguous) makes both operands K-major.  Each
+// Psi (bf16, blocked: 64-point blocks holding all rows, 128 B per row per
+// block, see psi_index) makes both operands K-major, and a 64-point slab of
+// any rows is one contiguous span (a 3-D TMA box), whatever N.  Each
 // CTA (a TcUnit) owns one tile of one cloud -- 128 feature rows against up to
 // 256 Gram rows and, for one tile per row block, the cpad field rows -- and
 // one "lane" of that cloud's point axis: the 64-point blocks kb = lane,
@@ -94,10 +96,10 @@ gram_tc_kernel(const CUtensorMap* __restrict__ maps, const TcUnit* __restrict__ 
         const uint32_t full = smem_u32(&sm->full[s]);
         mbar_arrive_expect_tx(full, tx_bytes);
         const uint32_t sa = base + s * stage_bytes;
-        const int32_t x = (kb_first + i * u.nlanes) * kTcBK;
-        tma_load_2d(sa, map_a, x, u.i0, full);
-        if (has_g) tma_load_2d(sa + kABytes, map_b, x, u.j0, full);
-        if (has_f) tma_load_2d(sa + kABytes + kBBytes, map_f, x, 0, full);  // the F map starts at Psi row m
+        const int32_t kb = kb_first + i * u.nlanes;  // 64-point block of the blocked Psi
+        tma_load_3d(sa, map_a, 0, u.i0, kb, full);
+        if (has_g) tma_load_3d(sa + kABytes, map_b, 0, u.j0, kb, full);
+        if (has_f) tma_load_3d(sa + kABytes + kBBytes, map_f, 0, 0, kb, full);  // the F map starts at Psi row m
       }
       // drain: our copies into the last stages must land before the CTA exits
       for (int t = (i > stages ? i - stages : 0); t < i; ++t)
@@ -179,15 +181,15 @@ int stage_bytes_for(int cpad) { return (kABytes + kBBytes + cpad * kTcBK * 2 + 1
 
 bool tc_gram_supported() { return tc::sm103_available(); }
 
-bool make_gram_maps(void* maps_host3, const void* psi, int64_t n_pad, int m, int cpad) {
+bool make_gram_maps(void* maps_host3, const void* psi, int64_t n_pad, int m, int cpad, int rows_alloc) {
   auto* maps = static_cast<CUtensorMap*>(maps_host3);
   const uint32_t a_rows = (uint32_t)(m < kTcBM ? m : kTcBM);
   const uint32_t b_rows = (uint32_t)(m < kTcBNMax ? m : kTcBNMax);
   const auto* p = static_cast<const uint16_t*>(psi);
-  return make_map_bf16(&maps[0], p, (uint64_t)n_pad, (uint64_t)m, (uint64_t)n_pad, a_rows) &&
-         make_map_bf16(&maps[1], p, (uint64_t)n_pad, (uint64_t)m, (uint64_t)n_pad, b_rows) &&
-         make_map_bf16(&maps[2], p + (size_t)m * n_pad, (uint64_t)n_pad, (uint64_t)cpad, (uint64_t)n_pad,
-                       (uint32_t)cpad);
+  const uint64_t nb = (uint64_t)(n_pad / 64), ra = (uint64_t)rows_alloc;
+  return make_map_bf16_blocked(&maps[0], p, (uint64_t)m, ra, nb, a_rows) &&
+         make_map_bf16_blocked(&maps[1], p, (uint64_t)m, ra, nb, b_rows) &&
+         make_map_bf16_blocked(&maps[2], p + (size_t)m * 64, (uint64_t)cpad, ra, nb, (uint32_t)cpad);
 }
 
 cudaError_t gram_tc_prepare() {

@@ -232,6 +232,52 @@ __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
   return d;
 }
 
+// Correctly rounded (to nearest, ties to even) double of S 2^E for the exact
+// integer S = TA 2^28 + TB, in integer arithmetic (the FP64 pipe is the slow
+// one on this GPU).  S 2^(e-63) = T_A 2^(e-35) + T_B 2^(e-63), so this is the
+// same single rounding as summing the two exact FP64 terms.  Returns false
+// when the result is not a normal double (the caller takes the FP64 route).
+__device__ __forceinline__ bool exact_sum_to_double(long long TA, long long TB, int E, bool flip, double* out) {
+  const __int128 S = ((__int128)TA << 28) + (__int128)TB;
+  if (S == 0) {
+    *out = 0.0;
+    return true;
+  }
+  const bool neg = (S < 0) != flip;
+  const unsigned __int128 mag = (S < 0) ? (unsigned __int128)(-S) : (unsigned __int128)S;
+  const unsigned long long hi = (unsigned long long)(mag >> 64), lo = (unsigned long long)mag;
+  int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  unsigned long long q;
+  if (msb > 52) {
+    const int sh = msb - 52;
+    q = (unsigned long long)(mag >> sh);
+    const unsigned __int128 rem = mag & ((((unsigned __int128)1) << sh) - 1);
+    const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+    if (q >> 53) {
+      q >>= 1;
+      ++msb;
+    }
+  } else {
+    q = lo << (52 - msb);
+  }
+  const int be = msb + E + 1023;
+  if (be < 1 || be > 2046) return false;
+  *out = __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) |
+                                          (q & 0xFFFFFFFFFFFFFull)));
+  return true;
+}
+
+// alpha = +-2^k (k small): returns true with k and the sign, so the scaling is exact in the exponent.
+__device__ __forceinline__ bool pow2_of(double alpha, int* k, bool* neg) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(alpha);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if ((b & 0xFFFFFFFFFFFFFull) != 0 || E == 0 || E == 0x7FF) return false;
+  *k = E - 1023;
+  *neg = (b >> 63) != 0;
+  return true;
+}
+
 // One 128 x 64 output tile (m0, n0) of C = alpha A B + beta C from the slice
 // tensor maps (A: rows p M_pad + i, B^T: rows q N_pad + j; K_pad columns).
 // D = alpha A B + beta C + diag I (C may be null when beta == 0; D may equal C).
@@ -345,19 +391,36 @@ __device__ __forceinline__ void ozaki_tile(const CUtensorMap* map_a_p, const CUt
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&sm->acc_empty));
     }
-    if (ok && gi < M) {
-      const int eri = ea[gi];
-      const double* crow = C ? C + (size_t)gi * ldc : nullptr;
-      double* drow = D + (size_t)gi * ldc;
+    // the tile of alpha A B, correctly rounded, into shared memory (the stages are idle now) ...
+    double* tile = reinterpret_cast<double*>(smem_raw + (base - raw_addr));  // kBM rows x (kBN + 1)
+    if (ok) {
+      int ak = 0;
+      bool aneg = false;
+      const bool ap2 = pow2_of(alpha, &ak, &aneg);
+      const int eri = ea[gi < M_pad ? gi : 0];
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
-        const int gj = n0 + col0 + c;
-        if (gj < N) {
-          const int e = eri + eb[gj];
-          double v = alpha * (ldexp((double)TA[c], e - 35) + ldexp((double)TB[c], e - 63));
-          if (beta != 0.0) v = fma(beta, crow[gj], v);
-          if (gi == gj) v += diag;
-          drow[gj] = v;
+        const int e = eri + eb[n0 + col0 + c];
+        double v;
+        if (!(ap2 && exact_sum_to_double(TA[c], TB[c], e - 63 + ak, aneg, &v)))
+          v = alpha * (ldexp((double)TA[c], e - 35) + ldexp((double)TB[c], e - 63));
+        tile[row * (kBN + 1) + col0 + c] = v;
+      }
+    }
+    asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 epilogue warps
+    // ... then out with coalesced rows: D = tile + beta C (+ diag on the diagonal)
+    if (ok) {
+      const int ew = warp - 2;
+      for (int r = ew; r < kBM; r += 8) {
+        const int i = m0 + r;
+        if (i >= M) break;
+        for (int jj = lane; jj < kBN; jj += 32) {
+          const int j = n0 + jj;
+          if (j >= N) continue;
+          double v = tile[r * (kBN + 1) + jj];
+          if (beta != 0.0) v = fma(beta, C[(size_t)i * ldc + j], v);
+          if (i == j) v += diag;
+          D[(size_t)i * ldc + j] = v;
         }
       }
     }

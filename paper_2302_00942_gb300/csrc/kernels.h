@@ -79,7 +79,7 @@ struct TcUnit {
 };
 // Encodes the three tensor maps of a cloud's bf16 feature matrix Psi
 // ([rows_alloc][n_pad], rows 0..m-1 features, m..m+cpad-1 field) into maps[0..2].
-bool make_gram_maps(void* maps_host3, const void* psi, int64_t n_pad, int m, int cpad);
+bool make_gram_maps(void* maps_host3, const void* psi, int64_t n_pad, int m, int cpad, int rows_alloc);
 // One launch per phase of kGramPhaseBlocks 64-point blocks (max_kb: the largest
 // point-block count of the units' clouds); later phases add to the partials.
 constexpr int kGramPhaseBlocks = 4096;
@@ -148,12 +148,18 @@ struct CloudCall {
 };
 
 // Step a2 (features) for one cloud, BF16 form.
+// BF16 feature buffer layout (blocked): 64-point blocks, each holding all of
+// its rows contiguously, so that a 64-point slab of every row is one
+// contiguous span: element (row, point p) at ((p / 64) rows_alloc + row) 64 + p % 64.
+__host__ __device__ inline size_t psi_index(int64_t p, int row, int rows_alloc) {
+  return ((size_t)(p >> 6) * (size_t)rows_alloc + (size_t)row) * 64 + (size_t)(p & 63);
+}
 struct FeatJob {
   int64_t n, n_pad;
   const float* omega;   // h x 3 FP32 frequencies
   __nv_bfloat16_raw* psi;
   float* xyz;           // the plan's copy of the points (N x 3), read by the apply
-  int32_t h, bx, cloud, pad_;  // bx: 512-point blocks; the job has bx * ceil(h / 32) blocks
+  int32_t h, bx, cloud, rows_alloc;  // bx: 512-point blocks; the job has bx * ceil(h / 32) blocks
 };
 // F^T rows of a cloud's Psi (rows m .. m + cpad - 1), BF16.
 // With fsplit, channel ch of F is written as two BF16 rows, hi = bf16(F) at
@@ -161,8 +167,9 @@ struct FeatJob {
 // rounding of F (the reduction adds the two columns).
 struct FillJob {
   int64_t n, n_pad;
-  __nv_bfloat16_raw* rows;
+  __nv_bfloat16_raw* psi;
   int32_t cpad, bx, cloud, fsplit;  // bx: 256-point blocks
+  int32_t row0, rows_alloc;         // F rows start at row0 (= m) of the blocked buffer
 };
 // One output tile of the split-K reduction (absolute pointers).
 struct RedTile {

@@ -263,9 +263,10 @@ rfd_status build_desc(rfd_plan_s* pl) {
     }
   }
   auto* psi = static_cast<__nv_bfloat16_raw*>(pl->d_psi);
-  d.feat = FeatJob{pl->n, pl->n_pad, pl->d_omega_hi, psi, pl->d_xyz, pl->h, (int)((pl->n_pad + 511) / 512), 0, 0};
-  d.fill = FillJob{pl->n, pl->n_pad, psi + (size_t)m * pl->n_pad, pl->cpad, (int)((pl->n_pad + 255) / 256), 0,
-                   pl->fsplit ? 1 : 0};
+  d.feat = FeatJob{pl->n, pl->n_pad, pl->d_omega_hi, psi, pl->d_xyz, pl->h, (int)((pl->n_pad + 511) / 512), 0,
+                   pl->rows_alloc};
+  d.fill = FillJob{pl->n, pl->n_pad, psi, pl->cpad, (int)((pl->n_pad + 255) / 256), 0, pl->fsplit ? 1 : 0, m,
+                   pl->rows_alloc};
   d.apply = ApplyJob{pl->d_xyz,  pl->d_omega_hi, pl->d_omega_lo, pl->d_G, pl->d_Y, pl->d_oa, pl->d_Z,
                      pl->n,      pl->n_pad,      m, 0, (int)((pl->n + 255) / 256), 0};
   // step a4 on the emulated path: slots in the FP64 workspace, Ozaki slices after them
@@ -293,7 +294,7 @@ rfd_status build_desc(rfd_plan_s* pl) {
   pc.map_b = 4;
   for (int m0 = 0; m0 < pc.mpa; m0 += 128)
     for (int n0 = 0; n0 < pc.mpb; n0 += 64) d.oz.push_back(OzTile{0, m0, n0, 0});
-  if (!make_gram_maps(d.maps[0], pl->d_psi, pl->n_pad, m, pl->cpad))
+  if (!make_gram_maps(d.maps[0], pl->d_psi, pl->n_pad, m, pl->cpad, pl->rows_alloc))
     return fail(RFD_ECUDA, "tensor-map encoding of the feature matrix failed");
   if (!make_ozaki_maps(d.maps[3], d.maps[4], pc.sa, pc.sb, pc.mpa, pc.mpb, pc.kp))
     return fail(RFD_ECUDA, "tensor-map encoding of the FP64-emulation slices failed");

@@ -62,6 +62,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, int32_t z,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
 // Shared-memory matrix descriptor, K-major operand with the 128-byte swizzle:
 // rows of 128 B, 8-row core groups 1024 B apart (stride byte offset), the
 // leading byte offset unused for this layout, descriptor version 1.
@@ -123,6 +131,12 @@ bool make_map_bf16(CUtensorMap* map, const void* base, uint64_t cols, uint64_t r
 // The same with a box of 32 columns (64 B) x box_rows and the 64-byte swizzle.
 bool make_map_bf16_sw64(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t row_stride,
                         uint32_t box_rows);
+// 3-D bf16 tensor map over a blocked buffer: blocks of 64 columns (points),
+// each holding `rows_alloc` rows of 64 elements; the map covers rows
+// [0, rows) of every block (base may point at a later row) and nblocks
+// blocks; box = 64 x box_rows x 1, 128-byte swizzle.
+bool make_map_bf16_blocked(CUtensorMap* map, const void* base, uint64_t rows, uint64_t rows_alloc, uint64_t nblocks,
+                           uint32_t box_rows);
 bool sm103_available();
 
 }  // namespace tc
