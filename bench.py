@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the serving trace (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--sections", default="main,batched,serving",
+                    help="comma list of main, batched, serving (profiling runs select one; the JSON line then "
+                         "carries only what ran)")
     return ap.parse_args()
 
 
@@ -388,6 +391,18 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     D = Dist("nccl")
+    sections = set(args.sections.split(","))
+    if "main" not in sections:   # a profiling run of one section
+        stream = torch.cuda.current_stream(dev)
+        res = {"metric": METRIC, "sections": sorted(sections)}
+        if "batched" in sections and args.batched_clouds > 0:
+            res["batched"] = bench_batched(args, dev, stream, D)
+        if "serving" in sections and args.serve_seconds > 0:
+            res["serving"] = bench_serving(args, dev)
+        if rank == 0:
+            print(json.dumps(res))
+        D.close()
+        return 0
     # each rank integrates its own cloud (independent problems)
     if ws > 1:
         import dataclasses
@@ -533,9 +548,9 @@ def main():
         "gpu_launches": int(st["kernel_launches"]),
         "fp32_plain": fp32,
     }
-    if args.batched_clouds > 0 and prec == rfd.RFD_BF16_TC:
+    if "batched" in sections and args.batched_clouds > 0 and prec == rfd.RFD_BF16_TC:
         res["batched"] = bench_batched(args, dev, stream, D)
-    if args.serve_seconds > 0 and prec == rfd.RFD_BF16_TC:
+    if "serving" in sections and args.serve_seconds > 0 and prec == rfd.RFD_BF16_TC:
         res["serving"] = bench_serving(args, dev)
         res["p99_ms"] = res["serving"]["p99_ms"]
     if rank == 0 and ws == 1 and not args.no_cpu:
