@@ -167,71 +167,87 @@ __global__ void small_batched_kernel(const ApplyJob* __restrict__ jobs, const in
 // out[n, ch] = F[n, ch] + sum_j (cos(2 pi w_j^T x_n) Z[j, ch] + sin(2 pi w_j^T x_n) Z[h + j, ch]):
 // the features are recomputed in FP32 from the cloud's copy of its points
 // instead of read back from the BF16 Psi, so the apply carries no BF16
-// rounding and reads only points, F and out.  The angle in cycles: each
-// product w_d x_d is split exactly (FMA) and its integer part removed before
-// the sum, so r = frac(w^T x) has an absolute error ~2^-23 whatever |w^T x|;
-// MUFU sin/cos of 2 pi r (|2 pi r| <= pi) add ~4e-7.  One point per thread, CG
-// channels per thread; frequencies and Z rows of a 64-frequency chunk in
-// shared memory.  F[n] is read before out[n] is written by the same thread.
+// rounding and reads only points, F and out.  The angle in cycles is the FP32
+// t = w^T x (absolute error ~|t| 2^-24) reduced to [-1/2, 1/2]; MUFU sin/cos
+// of 2 pi r add ~4e-7.  Two points per thread (p and p + 256) share each
+// frequency's shared-memory loads; CG channels per thread.  F[n] is read
+// before out[n] is written by the same thread.
 template <int CG>
 __global__ void __launch_bounds__(256)
 apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
                      const CloudCall* __restrict__ calls) {
   constexpr int kChunk = 64;
-  __shared__ float wh[kChunk][3], wl[kChunk][3];
-  __shared__ float zc[kChunk][CG], zsn[kChunk][CG];
+  static_assert(CG % 4 == 0, "channel groups are float4 rows");
+  __shared__ float4 w_s[kChunk];
+  __shared__ float4 zc[kChunk][CG / 4], zsn[kChunk][CG / 4];
   const int j = find_job(prefix, count, blockIdx.x);
   const ApplyJob jb = jobs[j];
   const CloudCall cc = calls[jb.cloud];
   const int local = blockIdx.x - prefix[j];
   const int bxi = local % jb.bx, cgi = local / jb.bx;
   const int h = jb.m / 2;
-  const int64_t p = (int64_t)bxi * 256 + threadIdx.x;
-  const bool valid = p < jb.n;
-  const float x0 = valid ? jb.xyz[p * 3 + 0] : 0.f;
-  const float x1 = valid ? jb.xyz[p * 3 + 1] : 0.f;
-  const float x2 = valid ? jb.xyz[p * 3 + 2] : 0.f;
+  int64_t p[2];
+  bool valid[2];
+  float x[2][3];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    p[u] = (int64_t)bxi * 512 + u * 256 + threadIdx.x;
+    valid[u] = p[u] < jb.n;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) x[u][d] = valid[u] ? jb.xyz[p[u] * 3 + d] : 0.f;
+  }
   const int ch0 = cgi * CG;
   const int cg = min(CG, cc.c - ch0);
-  float acc[CG];
+  float acc[2][CG];
 #pragma unroll
-  for (int q = 0; q < CG; ++q) acc[q] = 0.f;
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int q = 0; q < CG; ++q) acc[u][q] = 0.f;
   const float two_pi = 6.283185307179586f;
   for (int f0 = 0; f0 < h; f0 += kChunk) {
     const int fn = min(kChunk, h - f0);
     __syncthreads();
-    for (int i = threadIdx.x; i < kChunk * 3; i += blockDim.x) {
-      const int fr = i / 3, d = i % 3;
-      wh[fr][d] = fr < fn ? jb.omega_hi[(size_t)(f0 + fr) * 3 + d] : 0.f;
-      wl[fr][d] = fr < fn ? jb.omega_lo[(size_t)(f0 + fr) * 3 + d] : 0.f;
+    for (int i = threadIdx.x; i < kChunk; i += blockDim.x) {
+      const float* w = jb.omega_hi + (size_t)(f0 + i) * 3;
+      w_s[i] = i < fn ? make_float4(w[0], w[1], w[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     for (int i = threadIdx.x; i < kChunk * CG; i += blockDim.x) {
       const int fr = i / CG, q = i % CG;
       const bool ok = fr < fn && q < cg;
-      zc[fr][q] = ok ? jb.Z[(size_t)(f0 + fr) * cc.c + ch0 + q] : 0.f;
-      zsn[fr][q] = ok ? jb.Z[(size_t)(h + f0 + fr) * cc.c + ch0 + q] : 0.f;
+      reinterpret_cast<float*>(zc[fr])[q] = ok ? jb.Z[(size_t)(f0 + fr) * cc.c + ch0 + q] : 0.f;
+      reinterpret_cast<float*>(zsn[fr])[q] = ok ? jb.Z[(size_t)(h + f0 + fr) * cc.c + ch0 + q] : 0.f;
     }
     __syncthreads();
-    if (valid) {
-      for (int fr = 0; fr < fn; ++fr) {
-        const float a0 = wh[fr][0] * x0, a1 = wh[fr][1] * x1, a2 = wh[fr][2] * x2;
-        const float e0 = fmaf(wl[fr][0], x0, fmaf(wh[fr][0], x0, -a0));
-        const float e1 = fmaf(wl[fr][1], x1, fmaf(wh[fr][1], x1, -a1));
-        const float e2 = fmaf(wl[fr][2], x2, fmaf(wh[fr][2], x2, -a2));
-        float r = ((a0 - round_int(a0)) + (a1 - round_int(a1))) + ((a2 - round_int(a2)) + ((e0 + e1) + e2));
-        r -= round_int(r);
-        const float ang = two_pi * r;
-        const float cs = __cosf(ang), sn = __sinf(ang);
+    for (int fr = 0; fr < fn; ++fr) {
+      const float4 w = w_s[fr];
+      float cs[2], sn[2];
 #pragma unroll
-        for (int q = 0; q < CG; ++q) acc[q] = fmaf(cs, zc[fr][q], fmaf(sn, zsn[fr][q], acc[q]));
+      for (int u = 0; u < 2; ++u) {
+        const float t = fmaf(w.x, x[u][0], fmaf(w.y, x[u][1], w.z * x[u][2]));
+        const float ang = two_pi * (t - round_int(t));
+        cs[u] = __cosf(ang);
+        sn[u] = __sinf(ang);
+      }
+#pragma unroll
+      for (int q4 = 0; q4 < CG / 4; ++q4) {
+        const float4 a = zc[fr][q4], b = zsn[fr][q4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          acc[u][4 * q4 + 0] = fmaf(cs[u], a.x, fmaf(sn[u], b.x, acc[u][4 * q4 + 0]));
+          acc[u][4 * q4 + 1] = fmaf(cs[u], a.y, fmaf(sn[u], b.y, acc[u][4 * q4 + 1]));
+          acc[u][4 * q4 + 2] = fmaf(cs[u], a.z, fmaf(sn[u], b.z, acc[u][4 * q4 + 2]));
+          acc[u][4 * q4 + 3] = fmaf(cs[u], a.w, fmaf(sn[u], b.w, acc[u][4 * q4 + 3]));
+        }
       }
     }
   }
-  if (valid)
-    for (int q = 0; q < cg; ++q) {
-      const float fv = cc.F[p * cc.ldF + ch0 + q];
-      cc.out[p * cc.ldOut + ch0 + q] = fv + acc[q];
-    }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+    if (valid[u])
+      for (int q = 0; q < cg; ++q) {
+        const float fv = cc.F[p[u] * cc.ldF + ch0 + q];
+        cc.out[p[u] * cc.ldOut + ch0 + q] = fv + acc[u][q];
+      }
 }
 
 __device__ __forceinline__ const double* slot_ptr(const PhiCloud& pc, int slot) {

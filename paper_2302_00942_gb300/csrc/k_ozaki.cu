@@ -24,13 +24,16 @@
 // two conversions to FP64 and their sum, so the result carries FP64 accuracy
 // relative to |A||B|, for any K.
 //
-// Kernel layout: one CTA per 128 x 64 output tile.  Per 32-column chunk of K a
-// stage holds all 8 slices of the A tile and of the B tile (96 KB, 64-byte
-// swizzle; two stages), so each slice is read from L2 once per chunk and
-// serves every pair it belongs to.  Warp 0 issues the TMA loads, warp 1 the 72
-// tcgen05.mma of a chunk into the eight 64-column TMEM accumulators, warps
-// 2..9 drain them (two warps per TMEM lane quarter, 32 columns each).  Waits
-// are bounded (2 s) and record an error code instead of hanging.
+// Kernel layout: one CTA per 128 x 64 output tile.  Per 64-column chunk of K
+// the 8 slices of the B tile stay resident as one set (64 KB, double-buffered)
+// while the 8 slices of the A tile stream through a 4-deep ring (16 KB each,
+// 128-byte swizzle); A slice p is multiplied with B slices q <= 9 - p, so each
+// slice is read from L2 once per chunk and serves every pair it belongs to.
+// Warp 0 issues the TMA loads, warp 1 the tcgen05.mma (144 per chunk) into the
+// eight 64-column TMEM accumulators, warps 2..9 drain them (two warps per TMEM
+// lane quarter, 32 columns each) into exact integer sums and write the tile
+// through shared memory with coalesced rows.  Waits are bounded (2 s) and
+// record an error code instead of hanging.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -45,15 +48,16 @@ using namespace tc;
 
 constexpr int kS = 8;             // slices per operand
 constexpr int kBeta = 7;          // bits per slice
-constexpr int kBM = 128, kBN = 64, kBK = 32;
-constexpr int kStages = 2;
-constexpr int kATile = kBM * kBK * 2;          // 8 KB: one slice of the A tile
-constexpr int kBTile = kBN * kBK * 2;          // 4 KB: one slice of the B tile
-constexpr int kStageBytes = kS * (kATile + kBTile);  // 96 KB
-constexpr int kAcc = 8;                        // TMEM accumulators, t = 2..9 (64 columns each)
+constexpr int kBM = 128, kBN = 64, kBK = 64;
+constexpr int kATile = kBM * kBK * 2;          // 16 KB: one slice of the A tile (128-byte rows)
+constexpr int kBTile = kBN * kBK * 2;          // 8 KB: one slice of the B tile
+constexpr int kBSet = kS * kBTile;             // 64 KB: all slices of the B tile for one K chunk
+constexpr int kBBufs = 2;                      // B sets in flight
+constexpr int kARing = 4;                      // A slices in flight
+constexpr int kPipeBytes = kBBufs * kBSet + kARing * kATile;  // 192 KB
 constexpr int kDrainChunks = 512 / kBK;        // exactness bound of the FP32 accumulation: 512 of K
 constexpr int kThreads = 320;                  // 10 warps
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+constexpr int kSmemBytes = kPipeBytes + 1024 + 256;
 constexpr int kMaxK = 4096;
 constexpr int kColSplitK = 256;                // K rows per block of the batched column split
 
@@ -212,25 +216,14 @@ __global__ void transpose_kernel(const double* __restrict__ B, int ldb, int rows
 }
 
 struct Smem {
-  uint64_t full[kStages];
-  uint64_t empty[kStages];
+  uint64_t bfull[kBBufs];
+  uint64_t bempty[kBBufs];
+  uint64_t afull[kARing];
+  uint64_t aempty[kARing];
   uint64_t acc_full;
   uint64_t acc_empty;
   uint32_t tmem_base;
 };
-
-// Shared-memory descriptor, K-major operand with the 64-byte swizzle: rows of
-// 64 B (32 BF16 of K), 8-row core groups 512 B apart, descriptor version 1,
-// layout type 4 (SWIZZLE_64B).
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
-  d |= static_cast<uint64_t>(1) << 16;
-  d |= static_cast<uint64_t>(512 >> 4) << 32;
-  d |= static_cast<uint64_t>(1) << 46;
-  d |= static_cast<uint64_t>(4) << 61;
-  return d;
-}
 
 // Correctly rounded (to nearest, ties to even) double of S 2^E for the exact
 // integer S = TA 2^28 + TB, in integer arithmetic (the FP64 pipe is the slow
@@ -268,7 +261,7 @@ __device__ __forceinline__ bool exact_sum_to_double(long long TA, long long TB, 
   return true;
 }
 
-// alpha = +-2^k (k small): returns true with k and the sign, so the scaling is exact in the exponent.
+// alpha = +-2^k: returns true with k and the sign, so the scaling is exact in the exponent.
 __device__ __forceinline__ bool pow2_of(double alpha, int* k, bool* neg) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(alpha);
   const int E = (int)((b >> 52) & 0x7FF);
@@ -290,15 +283,20 @@ __device__ __forceinline__ void ozaki_tile(const CUtensorMap* map_a_p, const CUt
   const CUtensorMap& map_b = *map_b_p;
   const uint32_t raw_addr = smem_u32(smem_raw);
   const uint32_t base = (raw_addr + 1023u) & ~1023u;
-  Smem* sm = reinterpret_cast<Smem*>(smem_raw + (base - raw_addr) + kStages * kStageBytes);
+  const uint32_t bbase = base, abase = base + kBBufs * kBSet;
+  Smem* sm = reinterpret_cast<Smem*>(smem_raw + (base - raw_addr) + kPipeBytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nkc = K_pad / kBK;
   const int ndrain = (nkc + kDrainChunks - 1) / kDrainChunks;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(smem_u32(&sm->full[s]), 1);
-      mbar_init(smem_u32(&sm->empty[s]), 1);
+    for (int b = 0; b < kBBufs; ++b) {
+      mbar_init(smem_u32(&sm->bfull[b]), 1);
+      mbar_init(smem_u32(&sm->bempty[b]), 1);
+    }
+    for (int a = 0; a < kARing; ++a) {
+      mbar_init(smem_u32(&sm->afull[a]), 1);
+      mbar_init(smem_u32(&sm->aempty[a]), 1);
     }
     mbar_init(smem_u32(&sm->acc_full), 1);
     mbar_init(smem_u32(&sm->acc_empty), 8);  // one arrive per epilogue warp
@@ -310,25 +308,35 @@ __device__ __forceinline__ void ozaki_tile(const CUtensorMap* map_a_p, const CUt
   fence_after();
   const uint32_t tmem = sm->tmem_base;
 
+  // Per K chunk: the 8 B slices as one set (double-buffered), then the 8 A
+  // slices one by one through a ring; A slice p meets B slices q <= 7 - p
+  // (0-based), the pairs with p + q <= 9 (1-based).
   if (warp == 0) {
     if (lane == 0) {
       bool ok = true;
+      int issued_b = 0, issued_a = 0;
       for (int kc = 0; kc < nkc && ok; ++kc) {
-        const int s = kc % kStages;
-        const uint32_t ph = (kc / kStages) & 1u;
-        if (!mbar_wait(smem_u32(&sm->empty[s]), ph ^ 1u, err, 11)) { ok = false; break; }
-        const uint32_t full = smem_u32(&sm->full[s]);
-        mbar_arrive_expect_tx(full, kStageBytes);
-        const uint32_t st = base + s * kStageBytes;
+        const int bs = kc % kBBufs;
+        if (!mbar_wait(smem_u32(&sm->bempty[bs]), ((kc / kBBufs) & 1u) ^ 1u, err, 11)) { ok = false; break; }
+        const uint32_t bf = smem_u32(&sm->bfull[bs]);
+        mbar_arrive_expect_tx(bf, kBSet);
 #pragma unroll
+        for (int q = 0; q < kS; ++q) tma_load_2d(bbase + bs * kBSet + q * kBTile, &map_b, kc * kBK, q * N_pad + n0, bf);
+        ++issued_b;
         for (int p = 0; p < kS; ++p) {
-          tma_load_2d(st + p * kATile, &map_a, kc * kBK, p * M_pad + m0, full);
-          tma_load_2d(st + kS * kATile + p * kBTile, &map_b, kc * kBK, p * N_pad + n0, full);
+          const int it = kc * kS + p, as = it % kARing;
+          if (!mbar_wait(smem_u32(&sm->aempty[as]), ((it / kARing) & 1u) ^ 1u, err, 12)) { ok = false; break; }
+          const uint32_t af = smem_u32(&sm->afull[as]);
+          mbar_arrive_expect_tx(af, kATile);
+          tma_load_2d(abase + as * kATile, &map_a, kc * kBK, p * M_pad + m0, af);
+          ++issued_a;
         }
       }
       // wait for the copies still in flight before the CTA may exit
-      for (int u = (nkc > kStages ? nkc - kStages : 0); u < nkc; ++u)
-        mbar_wait(smem_u32(&sm->full[u % kStages]), (u / kStages) & 1u, err, 12);
+      for (int u = (issued_b > kBBufs ? issued_b - kBBufs : 0); u < issued_b; ++u)
+        mbar_wait(smem_u32(&sm->bfull[u % kBBufs]), (u / kBBufs) & 1u, err, 16);
+      for (int u = (issued_a > kARing ? issued_a - kARing : 0); u < issued_a; ++u)
+        mbar_wait(smem_u32(&sm->afull[u % kARing]), (u / kARing) & 1u, err, 17);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -340,22 +348,27 @@ __device__ __forceinline__ void ozaki_tile(const CUtensorMap* map_a_p, const CUt
           if (!mbar_wait(smem_u32(&sm->acc_empty), (drain - 1) & 1u, err, 13)) { ok = false; break; }
           fence_after();
         }
-        const int s = kc % kStages;
-        if (!mbar_wait(smem_u32(&sm->full[s]), (kc / kStages) & 1u, err, 14)) { ok = false; break; }
+        const int bs = kc % kBBufs;
+        if (!mbar_wait(smem_u32(&sm->bfull[bs]), (kc / kBBufs) & 1u, err, 14)) { ok = false; break; }
         fence_after();
-        const uint32_t st = base + s * kStageBytes;
-        for (int t = 2; t <= kS + 1; ++t) {
-          const uint32_t d_tmem = tmem + (uint32_t)((t - 2) * kBN);
-          for (int p = max(1, t - kS); p <= min(kS, t - 1); ++p) {
-            const int q = t - p;
-            const uint32_t sa = st + (p - 1) * kATile, sb = st + kS * kATile + (q - 1) * kBTile;
+        const uint32_t sb0 = bbase + bs * kBSet;
+        for (int p = 0; p < kS && ok; ++p) {
+          const int it = kc * kS + p, as = it % kARing;
+          if (!mbar_wait(smem_u32(&sm->afull[as]), (it / kARing) & 1u, err, 18)) { ok = false; break; }
+          fence_after();
+          const uint32_t sa = abase + as * kATile;
+          for (int q = 0; q + p < kS; ++q) {  // digit position t = p + q (0-based), accumulator t
+            const uint32_t d_tmem = tmem + (uint32_t)((p + q) * kBN);
+            const uint32_t sb = sb0 + q * kBTile;
 #pragma unroll
             for (int kk = 0; kk < kBK / 16; ++kk)
-              mma_bf16(d_tmem, sdesc_sw64(sa + kk * 32), sdesc_sw64(sb + kk * 32), idesc,
-                       (in_drain > 0 || p > max(1, t - kS) || kk > 0) ? 1u : 0u);
+              mma_bf16(d_tmem, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
+                       (in_drain > 0 || p > 0 || kk > 0) ? 1u : 0u);
           }
+          mma_commit(smem_u32(&sm->aempty[as]));
         }
-        mma_commit(smem_u32(&sm->empty[s]));
+        if (!ok) break;
+        mma_commit(smem_u32(&sm->bempty[bs]));
         if (in_drain == kDrainChunks - 1 || kc == nkc - 1) mma_commit(smem_u32(&sm->acc_full));
       }
     }
@@ -465,10 +478,10 @@ ozaki_gemm_batched_kernel(const CUtensorMap* __restrict__ maps, const OzTile* __
 }  // namespace
 
 bool make_ozaki_maps(void* map_a_host, void* map_b_host, const void* sa, const void* sb, int mpa, int mpb, int kp) {
-  return tc::make_map_bf16_sw64(static_cast<CUtensorMap*>(map_a_host), sa, (uint64_t)kp, (uint64_t)kS * mpa,
-                                (uint64_t)kp, kBM) &&
-         tc::make_map_bf16_sw64(static_cast<CUtensorMap*>(map_b_host), sb, (uint64_t)kp, (uint64_t)kS * mpb,
-                                (uint64_t)kp, kBN);
+  return tc::make_map_bf16(static_cast<CUtensorMap*>(map_a_host), sa, (uint64_t)kp, (uint64_t)kS * mpa, (uint64_t)kp,
+                           kBM) &&
+         tc::make_map_bf16(static_cast<CUtensorMap*>(map_b_host), sb, (uint64_t)kp, (uint64_t)kS * mpb, (uint64_t)kp,
+                           kBN);
 }
 
 cudaError_t bgemm_prepare() {
@@ -533,8 +546,8 @@ cudaError_t dgemm_ozaki(int M, int N, int K, double alpha, const double* A, int 
   split_rows_kernel<<<(np * 32 + 255) / 256, 256, 0, st>>>(bt, K, N, K, np, kp, sb, eb);
   count_launch(3);
   CUtensorMap ma, mb;
-  if (!tc::make_map_bf16_sw64(&ma, sa, (uint64_t)kp, (uint64_t)kS * mp, (uint64_t)kp, kBM)) return cudaErrorInvalidValue;
-  if (!tc::make_map_bf16_sw64(&mb, sb, (uint64_t)kp, (uint64_t)kS * np, (uint64_t)kp, kBN)) return cudaErrorInvalidValue;
+  if (!tc::make_map_bf16(&ma, sa, (uint64_t)kp, (uint64_t)kS * mp, (uint64_t)kp, kBM)) return cudaErrorInvalidValue;
+  if (!tc::make_map_bf16(&mb, sb, (uint64_t)kp, (uint64_t)kS * np, (uint64_t)kp, kBN)) return cudaErrorInvalidValue;
   static const cudaError_t attr =  // once per process (thread-safe initialisation)
       cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (attr != cudaSuccess) return attr;

@@ -192,7 +192,7 @@ struct ApplyJob {
   const double* oa;
   float* Z;
   int64_t n, n_pad;
-  int32_t m, cloud, bx, pad_;  // bx: 256-point blocks
+  int32_t m, cloud, bx, pad_;  // bx: 512-point blocks (apply), m rows (small product)
 };
 // Step a4 (phi1) for one cloud on the emulated-FP64 path.  Matrix "slots":
 // slot k >= 0 is work + k m^2; kSlotM is M, kSlotG is G.

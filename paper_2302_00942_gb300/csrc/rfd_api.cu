@@ -268,7 +268,7 @@ rfd_status build_desc(rfd_plan_s* pl) {
   d.fill = FillJob{pl->n, pl->n_pad, psi, pl->cpad, (int)((pl->n_pad + 255) / 256), 0, pl->fsplit ? 1 : 0, m,
                    pl->rows_alloc};
   d.apply = ApplyJob{pl->d_xyz,  pl->d_omega_hi, pl->d_omega_lo, pl->d_G, pl->d_Y, pl->d_oa, pl->d_Z,
-                     pl->n,      pl->n_pad,      m, 0, (int)((pl->n + 255) / 256), 0};
+                     pl->n,      pl->n_pad,      m, 0, (int)((pl->n + 511) / 512), 0};
   // step a4 on the emulated path: slots in the FP64 workspace, Ozaki slices after them
   PhiCloud& pc = d.phi;
   pc = PhiCloud{};

@@ -30,19 +30,6 @@ bool make_map_bf16(CUtensorMap* map, const void* base, uint64_t cols, uint64_t r
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool make_map_bf16_sw64(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t row_stride,
-                        uint32_t box_rows) {
-  auto enc = encode_fn();
-  if (!enc) return false;
-  const cuuint64_t dims[2] = {cols, rows};
-  const cuuint64_t strides[1] = {row_stride * 2};
-  const cuuint32_t box[2] = {32u, box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 bool make_map_bf16_blocked(CUtensorMap* map, const void* base, uint64_t rows, uint64_t rows_alloc, uint64_t nblocks,
                            uint32_t box_rows) {
   auto enc = encode_fn();

@@ -128,9 +128,6 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
 // elements), box = 64 columns (128 B) x box_rows, 128-byte swizzle.
 bool make_map_bf16(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t row_stride,
                    uint32_t box_rows);
-// The same with a box of 32 columns (64 B) x box_rows and the 64-byte swizzle.
-bool make_map_bf16_sw64(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t row_stride,
-                        uint32_t box_rows);
 // 3-D bf16 tensor map over a blocked buffer: blocks of 64 columns (points),
 // each holding `rows_alloc` rows of 64 elements; the map covers rows
 // [0, rows) of every block (base may point at a later row) and nblocks
