@@ -29,8 +29,9 @@
 // while the 8 slices of the A tile stream through a 4-deep ring (16 KB each,
 // 128-byte swizzle); A slice p is multiplied with B slices q <= 9 - p, so each
 // slice is read from L2 once per chunk and serves every pair it belongs to.
-// Warp 0 issues the TMA loads, warp 1 the tcgen05.mma (144 per chunk) into the
-// eight 64-column TMEM accumulators, warps 2..9 drain them (two warps per TMEM
+// Warp 0 issues the TMA loads, warp 1 the tcgen05.mma into the eight adjacent
+// 64-column TMEM accumulators (A slice p against the concatenated B slices
+// lands on accumulators p..7 at once: 12 wide MMAs per 16 of K), warps 2..9 drain them (two warps per TMEM
 // lane quarter, 32 columns each) into exact integer sums and write the tile
 // through shared memory with coalesced rows.  Waits are bounded (2 s) and
 // record an error code instead of hanging.
@@ -340,7 +341,6 @@ __device__ __forceinline__ void ozaki_tile(const CUtensorMap* map_a_p, const CUt
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(kBM, kBN);
       bool ok = true;
       for (int kc = 0; kc < nkc && ok; ++kc) {
         const int drain = kc / kDrainChunks, in_drain = kc % kDrainChunks;
@@ -357,13 +357,19 @@ __device__ __forceinline__ void ozaki_tile(const CUtensorMap* map_a_p, const CUt
           if (!mbar_wait(smem_u32(&sm->afull[as]), (it / kARing) & 1u, err, 18)) { ok = false; break; }
           fence_after();
           const uint32_t sa = abase + as * kATile;
-          for (int q = 0; q + p < kS; ++q) {  // digit position t = p + q (0-based), accumulator t
-            const uint32_t d_tmem = tmem + (uint32_t)((p + q) * kBN);
-            const uint32_t sb = sb0 + q * kBTile;
+          // A_p times the concatenated slices [B_0 .. B_(7-p)] (rows q*64 + j of the B set): column
+          // block q of the product is pair (p, q), digit position t = p + q, whose accumulator sits at
+          // TMEM columns t*64, so the whole product lands at columns p*64 .. 511 -- one or two wide
+          // MMAs (N <= 256) instead of 8 - p narrow ones.
+          const int ncols = (kS - p) * kBN;
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk)
-              mma_bf16(d_tmem, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
-                       (in_drain > 0 || p > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            const uint32_t acc = (in_drain > 0 || p > 0 || kk > 0) ? 1u : 0u;
+            for (int c0 = 0; c0 < ncols; c0 += 256) {
+              const int nc = min(256, ncols - c0);
+              mma_bf16(tmem + (uint32_t)(p * kBN + c0), sdesc_sw128(sa + kk * 32),
+                       sdesc_sw128(sb0 + (c0 / kBN) * kBTile + kk * 32), idesc_bf16(kBM, nc), acc);
+            }
           }
           mma_commit(smem_u32(&sm->aempty[as]));
         }
