@@ -499,12 +499,17 @@ cudaError_t bgemm_prepare() {
 cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* strip_prefix,
                          int col_strips, const OzTile* tiles, int num_tiles, const void* maps_dev, int a_slot,
                          int b_slot, int c_slot, int d_slot, double alpha, double beta, double diag, int mask_k,
-                         int* err, cudaStream_t st) {
+                         bool split_a, bool split_b, int* err, cudaStream_t st) {
   const cudaError_t attr = bgemm_prepare();
   if (attr != cudaSuccess) return attr;
-  bsplit_rows_kernel<<<(rows_a * 32 + 255) / 256, 256, 0, st>>>(pc, row_prefix_a, count, a_slot, mask_k);
-  bsplit_cols_kernel<<<col_strips, dim3(32, 8), 0, st>>>(pc, strip_prefix, count, b_slot, mask_k);
-  count_launch(2);
+  if (split_a) {
+    bsplit_rows_kernel<<<(rows_a * 32 + 255) / 256, 256, 0, st>>>(pc, row_prefix_a, count, a_slot, mask_k);
+    count_launch();
+  }
+  if (split_b) {
+    bsplit_cols_kernel<<<col_strips, dim3(32, 8), 0, st>>>(pc, strip_prefix, count, b_slot, mask_k);
+    count_launch();
+  }
   ozaki_gemm_batched_kernel<<<num_tiles, kThreads, kSmemBytes, st>>>(static_cast<const CUtensorMap*>(maps_dev), tiles,
                                                                      pc, c_slot, d_slot, alpha, beta, diag, mask_k,
                                                                      err);

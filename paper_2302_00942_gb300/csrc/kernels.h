@@ -241,12 +241,14 @@ cudaError_t launch_bfinite(const PhiCloud* pc, const int* prefix, int count, int
                            cudaStream_t st);
 // D = alpha A B + beta C + diag I on every cloud (emulated FP64): row split of
 // A (warp-row prefix over mpa rows), column split of B (prefix over
-// ozaki_col_split_blocks(m) per cloud) and the tensor-core products.  c_slot kNoSlot: no C.  Clouds with
-// s <= mask_k (mask_k >= 0) skip the product and copy C to D.
+// ozaki_col_split_blocks(m) per cloud) and the tensor-core products.  c_slot
+// kNoSlot: no C.  Clouds with s <= mask_k (mask_k >= 0) skip the product and
+// copy C to D.  split_a / split_b false: the slices already hold that operand
+// (split by the previous product over the same or a larger set of clouds).
 cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* strip_prefix,
                          int col_strips, const OzTile* tiles, int num_tiles, const void* maps_dev, int a_slot,
                          int b_slot, int c_slot, int d_slot, double alpha, double beta, double diag, int mask_k,
-                         int* err, cudaStream_t st);
+                         bool split_a, bool split_b, int* err, cudaStream_t st);
 // one-time kernel attribute set-up of launch_gram_tc / launch_bgemm (call before a stream capture)
 cudaError_t gram_tc_prepare();
 cudaError_t bgemm_prepare();

@@ -364,9 +364,19 @@ rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s) {
     for (double v : a) a4[i++] = v;
     return launch_bcombine(b->d_phi, b->d_elem_prefix, n, b->elem_blocks, dst, s4, a4, diag, kmode, mask, st);
   };
+  // the A / B slices hold the operands of the previous product: split only what changed
+  int last_a = kNoSlot, last_b = kNoSlot;
   auto gemm = [&](int a, int bb, int c, int d, double alpha, double beta, double diag, int mask) {
+    const bool sa = a != last_a, sb = bb != last_b;
+    last_a = a;
+    last_b = bb;
     return launch_bgemm(b->d_phi, n, b->d_rowa_prefix, b->rows_a, b->d_strip_prefix, b->col_strips, b->d_oz,
-                        b->n_oz, b->d_maps, a, bb, c, d, alpha, beta, diag, mask, b->d_err, st);
+                        b->n_oz, b->d_maps, a, bb, c, d, alpha, beta, diag, mask, sa, sb, b->d_err, st);
+  };
+  // a slot that is written no longer matches its slices
+  auto wrote = [&](int slot) {
+    if (slot == last_a) last_a = kNoSlot;
+    if (slot == last_b) last_b = kNoSlot;
   };
   // diagonal Pade, degree 5: b_k = (10-k)! 5! / (10! k! (5-k)!) with b_0 = 1
   double pb[6];
@@ -374,26 +384,37 @@ rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s) {
   for (int k = 0; k < 5; ++k) pb[k + 1] = pb[k] * double(5 - k) / (double(10 - k) * double(k + 1));
   if (max_s > 0) BCK(comb(sX, {sX}, {1.0}, 0.0, 2, -1));  // X = 2^-s X
   BCK(gemm(sX, sX, kNoSlot, sX2, 1.0, 0.0, 0.0, -1));
+  wrote(sX2);
   BCK(gemm(sX2, sX2, kNoSlot, sX4, 1.0, 0.0, 0.0, -1));
+  wrote(sX4);
   BCK(comb(sSp, {sX4, sX2}, {pb[5], pb[3]}, pb[1], 0, -1));
   BCK(comb(sVp, {sX4, sX2}, {pb[4], pb[2]}, pb[0], 0, -1));
+  wrote(sSp);
+  wrote(sVp);
   BCK(gemm(sX, sSp, sVp, sR, 1.0, -1.0, 1.0, -1));  // R = I - (Vp - Up), Up = X Sp
+  wrote(sR);
   BCK(gemm(sR, sSp, sSp, sF, 2.0, 2.0, 0.0, -1));   // F = (I + R) 2 Sp
+  wrote(sF);
   int F = sF, Fb = sFb, R = sR, R2 = sR2;
   for (int j = 1; j < kSolveFactors; ++j) {
     BCK(gemm(R, R, kNoSlot, R2, 1.0, 0.0, 0.0, -1));  // R^(2^j)
+    wrote(R2);
     std::swap(R, R2);
     BCK(gemm(R, F, F, Fb, 1.0, 1.0, 0.0, -1));  // F <- F + R^(2^j) F
+    wrote(Fb);
     std::swap(F, Fb);
   }
   if (max_s > 0) {
     int E = sE, E2 = sT1;
     BCK(gemm(sX, F, kNoSlot, E, 1.0, 0.0, 1.0, -1));  // E = I + X F
+    wrote(E);
     for (int k = 0; k < max_s; ++k) {
       BCK(gemm(E, F, F, Fb, 0.5, 0.5, 0.0, k));  // F <- (E F + F) / 2 (clouds with s <= k copy F)
+      wrote(Fb);
       std::swap(F, Fb);
       if (k + 1 < max_s) {
         BCK(gemm(E, E, kNoSlot, E2, 1.0, 0.0, 0.0, k + 1));  // E <- E^2 (clouds with s <= k + 1 skip)
+        wrote(E2);
         std::swap(E, E2);
       }
     }
