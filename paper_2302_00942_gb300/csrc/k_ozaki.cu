@@ -227,33 +227,51 @@ struct Smem {
 };
 
 // Correctly rounded (to nearest, ties to even) double of S 2^E for the exact
-// integer S = TA 2^28 + TB, in integer arithmetic (the FP64 pipe is the slow
-// one on this GPU).  S 2^(e-63) = T_A 2^(e-35) + T_B 2^(e-63), so this is the
-// same single rounding as summing the two exact FP64 terms.  Returns false
-// when the result is not a normal double (the caller takes the FP64 route).
+// integer S = TA 2^28 + TB (|TA| < 2^46, |TB| < 2^50), in 64-bit integer
+// arithmetic (the FP64 pipe is the slow one on this GPU).  S 2^(e-63) =
+// T_A 2^(e-35) + T_B 2^(e-63), so this is the same single rounding as summing
+// the two exact FP64 terms.  S = H 2^28 + r with 0 <= r < 2^28; |S| keeps that
+// form with |H| and the complement of r.  Returns false when the result is not
+// a normal double (the caller takes the FP64 route).
 __device__ __forceinline__ bool exact_sum_to_double(long long TA, long long TB, int E, bool flip, double* out) {
-  const __int128 S = ((__int128)TA << 28) + (__int128)TB;
-  if (S == 0) {
+  const long long H = TA + (TB >> 28);
+  unsigned long long r = (unsigned long long)(TB & ((1ll << 28) - 1));
+  unsigned long long Hm;
+  if (H < 0) {
+    if (r) {
+      Hm = (unsigned long long)(-H - 1);
+      r = (1ull << 28) - r;
+    } else {
+      Hm = (unsigned long long)(-H);
+    }
+  } else {
+    Hm = (unsigned long long)H;
+  }
+  if (Hm == 0 && r == 0) {
     *out = 0.0;
     return true;
   }
-  const bool neg = (S < 0) != flip;
-  const unsigned __int128 mag = (S < 0) ? (unsigned __int128)(-S) : (unsigned __int128)S;
-  const unsigned long long hi = (unsigned long long)(mag >> 64), lo = (unsigned long long)mag;
-  int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  const bool neg = (H < 0) != flip;
+  int msb;
   unsigned long long q;
-  if (msb > 52) {
-    const int sh = msb - 52;
-    q = (unsigned long long)(mag >> sh);
-    const unsigned __int128 rem = mag & ((((unsigned __int128)1) << sh) - 1);
-    const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
-    if (rem > half || (rem == half && (q & 1ull))) ++q;
-    if (q >> 53) {
-      q >>= 1;
-      ++msb;
-    }
+  if (Hm == 0) {
+    msb = 63 - __clzll((long long)r);
+    q = r << (52 - msb);
   } else {
-    q = lo << (52 - msb);
+    const int mh = 63 - __clzll((long long)Hm);
+    msb = mh + 28;
+    if (msb <= 52) {
+      q = ((Hm << 28) | r) << (52 - msb);
+    } else {
+      const int sh = msb - 52;  // 1 .. 27: the dropped bits all lie in r
+      q = (Hm << (28 - sh)) + (r >> sh);
+      const unsigned long long rem = r & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+      if (rem > half || (rem == half && (q & 1ull))) ++q;
+      if (q >> 53) {
+        q >>= 1;
+        ++msb;
+      }
+    }
   }
   const int be = msb + E + 1023;
   if (be < 1 || be > 2046) return false;
@@ -386,44 +404,70 @@ __device__ __forceinline__ void ozaki_tile(const CUtensorMap* map_a_p, const CUt
     const int row = quarter * 32 + lane;
     const int col0 = half * 32;
     const int gi = m0 + row;
-    long long TA[32], TB[32];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) { TA[c] = 0; TB[c] = 0; }
+    double* tile = reinterpret_cast<double*>(smem_raw + (base - raw_addr));  // kBM rows x (kBN + 1)
+    const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
+    int ak = 0;
+    bool aneg = false;
+    const bool ap2 = pow2_of(alpha, &ak, &aneg);
+    const int eri = ea[gi < M_pad ? gi : 0];
+    // alpha 2^e (T_A 2^-35 + T_B 2^-63), correctly rounded, into the shared-memory tile
+    auto emit = [&](int c, long long ta, long long tb) {
+      const int e = eri + eb[n0 + col0 + c];
+      double v;
+      if (!(ap2 && exact_sum_to_double(ta, tb, e - 63 + ak, aneg, &v)))
+        v = alpha * (ldexp((double)ta, e - 35) + ldexp((double)tb, e - 63));
+      tile[row * (kBN + 1) + col0 + c] = v;
+    };
     bool ok = true;
-    for (int d = 0; d < ndrain && ok; ++d) {
-      if (!mbar_wait(smem_u32(&sm->acc_full), d & 1u, err, 15)) { ok = false; break; }
-      fence_after();
+    if (ndrain == 1) {
+      // one drain (K <= 512): 8 columns at a time, the eight digit positions loaded under one wait
+      ok = mbar_wait(smem_u32(&sm->acc_full), 0u, err, 15);
+      if (ok) {
+        fence_after();
 #pragma unroll 1
-      for (int t = 2; t <= kS + 1; ++t) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((t - 2) * kBN + col0), v);
-        const int sh = (t <= 5) ? kBeta * (5 - t) : kBeta * (kS + 1 - t);
-        if (t <= 5) {
+        for (int g = 0; g < 32; g += 8) {
+          uint32_t r[8][8];
 #pragma unroll
-          for (int c = 0; c < 32; ++c) TA[c] += (long long)__float2int_rn(v[c]) << sh;
-        } else {
+          for (int t = 0; t < kS; ++t) tmem_ld8_nowait(taddr + (uint32_t)(t * kBN + g), r[t]);
+          tmem_wait_ld();
 #pragma unroll
-          for (int c = 0; c < 32; ++c) TB[c] += (long long)__float2int_rn(v[c]) << sh;
+          for (int c = 0; c < 8; ++c) {
+            long long ta = 0, tb = 0;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) ta += (long long)__float2int_rn(__uint_as_float(r[t][c])) << (kBeta * (3 - t));
+#pragma unroll
+            for (int t = 4; t < kS; ++t) tb += (long long)__float2int_rn(__uint_as_float(r[t][c])) << (kBeta * (7 - t));
+            emit(g + c, ta, tb);
+          }
         }
       }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&sm->acc_empty));
-    }
-    // the tile of alpha A B, correctly rounded, into shared memory (the stages are idle now) ...
-    double* tile = reinterpret_cast<double*>(smem_raw + (base - raw_addr));  // kBM rows x (kBN + 1)
-    if (ok) {
-      int ak = 0;
-      bool aneg = false;
-      const bool ap2 = pow2_of(alpha, &ak, &aneg);
-      const int eri = ea[gi < M_pad ? gi : 0];
+    } else {
+      long long TA[32], TB[32];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        const int e = eri + eb[n0 + col0 + c];
-        double v;
-        if (!(ap2 && exact_sum_to_double(TA[c], TB[c], e - 63 + ak, aneg, &v)))
-          v = alpha * (ldexp((double)TA[c], e - 35) + ldexp((double)TB[c], e - 63));
-        tile[row * (kBN + 1) + col0 + c] = v;
+      for (int c = 0; c < 32; ++c) { TA[c] = 0; TB[c] = 0; }
+      for (int d = 0; d < ndrain && ok; ++d) {
+        if (!mbar_wait(smem_u32(&sm->acc_full), d & 1u, err, 15)) { ok = false; break; }
+        fence_after();
+#pragma unroll 1
+        for (int t = 2; t <= kS + 1; ++t) {
+          float v[32];
+          tmem_ld32(taddr + (uint32_t)((t - 2) * kBN), v);
+          const int sh = (t <= 5) ? kBeta * (5 - t) : kBeta * (kS + 1 - t);
+          if (t <= 5) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) TA[c] += (long long)__float2int_rn(v[c]) << sh;
+          } else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) TB[c] += (long long)__float2int_rn(v[c]) << sh;
+          }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&sm->acc_empty));
+      }
+      if (ok) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) emit(c, TA[c], TB[c]);
       }
     }
     asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 epilogue warps
