@@ -60,16 +60,18 @@ cudaError_t launch_gram_simt(const float* psi, int64_t n_pad, const GramUnit* un
                              float* partials, cudaStream_t st);
 
 // BF16 tensor-core form (tcgen05 + TMA): one CTA per (tile, lane); a tile is
-// 128 rows x (<= 256 Gram columns + cpad field columns).  Partial rows have
-// kTcLd floats: Gram part at column 0, field part at column kTcBNMax.
+// 128 rows x (Gram columns + field columns <= 256).  Partial rows have kTcLd
+// floats: Gram part at column 0, field part at column kTcBNMax.
 constexpr int kTcBM = 128;
 constexpr int kTcBNMax = 256;
 constexpr int kTcBK = 64;
 constexpr int kTcLd = 512;
 // One CTA of the tensor-core reductions: tile rows i0.. of one cloud's Psi
-// against a Gram block j0.. (nj_mma > 0) and/or the cloud's cpad field rows
-// (has_f), over the 64-point blocks kb = lane, lane + nlanes, ... < kb_total.
-// maps[map + 0/1/2]: the cloud's A (box 64 x 128), B (64 x 256), F (64 x cpad) maps.
+// against Gram rows j0 .. j0 + nj_mma (nj_mma a multiple of 16, may be 0)
+// followed by the cloud's cpad field rows (has_f), one MMA of N = nj_mma (+
+// cpad), over the 64-point blocks kb = lane, lane + nlanes, ... < kb_total.
+// maps[map + 0/1/2/5]: the cloud's A (box 128 rows), B (64 rows), F (cpad rows)
+// and B (16 rows) maps; b_rows: rows of the B map (m).
 struct TcUnit {
   float* out;          // this CTA's partial tile: 128 rows x kTcLd floats
   int32_t map;
@@ -79,7 +81,9 @@ struct TcUnit {
 };
 // Encodes the three tensor maps of a cloud's bf16 feature matrix Psi
 // ([rows_alloc][n_pad], rows 0..m-1 features, m..m+cpad-1 field) into maps[0..2].
-bool make_gram_maps(void* maps_host3, const void* psi, int64_t n_pad, int m, int cpad, int rows_alloc);
+// maps_host3[0..2]: A (box min(128, m) rows), B (box min(64, m) rows), F rows (box cpad rows);
+// map_b16: B with a box of min(16, m) rows.
+bool make_gram_maps(void* maps_host3, void* map_b16, const void* psi, int64_t n_pad, int m, int cpad, int rows_alloc);
 // One launch per phase of kGramPhaseBlocks 64-point blocks (max_kb: the largest
 // point-block count of the units' clouds); later phases add to the partials.
 constexpr int kGramPhaseBlocks = 4096;

@@ -163,74 +163,85 @@ void build_tiles_simt(rfd_plan_s* pl, bool with_gram, bool with_field, TileSet& 
 }
 
 // ---- BF16 tensor-core form: the plan's batched-path descriptors -------------
-// Number of compute tiles of a mode (see build_desc) and the partial slots the
-// plan needs: max over modes of tiles x lanes (lanes = SMs / tiles, >= 1).
-int tc_tiles(int m, int mode) {
-  if (mode == kModeIntegrate) return (m + kTcBM - 1) / kTcBM;
-  int t = 0;
-  for (int i0 = 0; i0 < m; i0 += kTcBM)
-    for (int j0 = 0; j0 < m; j0 += kTcBNMax)
-      if (j0 + std::min(kTcBNMax, m - j0) - 1 >= i0) ++t;
-  return t;
+// Compute tiles of one mode.  For each block of 128 feature rows i0.., the
+// Gram columns [i0, m) (the upper triangle and the diagonal block) and, when
+// the mode has a field, the cpad field columns are cut into tiles of at most
+// 256 columns (multiples of 16, as even as possible); the field rides on the
+// last tile, whose B operand is its Gram rows followed by the F rows, so one
+// MMA covers both (a separate field-only tile if it does not fit).  Without
+// Gram work (integrate) every row block gets a field-only tile.
+struct GramCT {
+  int i0, j0, ni, nj, nj_mma;  // nj: real Gram columns, nj_mma: padded width (multiple of 16)
+  bool f;
+};
+
+std::vector<GramCT> gram_tiles(int m, int cpad, int mode) {
+  const bool with_gram = mode != kModeIntegrate, with_field = mode != kModeFeatures;
+  std::vector<GramCT> ct;
+  for (int i0 = 0; i0 < m; i0 += kTcBM) {
+    const int ni = std::min(kTcBM, m - i0);
+    if (!with_gram) {
+      ct.push_back(GramCT{i0, -1, ni, 0, 0, true});
+      continue;
+    }
+    const int Gp = (int)round_up(m - i0, 16), Fw = with_field ? cpad : 0;
+    int units = (Gp + Fw) / 16, k = (units * 16 + kTcBNMax - 1) / kTcBNMax;
+    bool field_here = Fw > 0;
+    if (field_here && (units / k) * 16 < Fw) {  // the field does not fit the last tile: a tile of its own
+      field_here = false;
+      units = Gp / 16;
+      k = (Gp + kTcBNMax - 1) / kTcBNMax;
+    }
+    int col = i0;
+    for (int t = 0; t < k; ++t) {
+      const int w = (units / k + (t < units % k ? 1 : 0)) * 16;
+      const bool f = field_here && t == k - 1;
+      const int gw = f ? w - Fw : w;
+      ct.push_back(GramCT{i0, col, ni, std::max(0, std::min(gw, m - col)), gw, f});
+      col += gw;
+    }
+    if (Fw > 0 && !field_here) ct.push_back(GramCT{i0, -1, ni, 0, 0, true});
+  }
+  return ct;
 }
 
-int tc_partial_slots(int m, int64_t n_pad, int sms) {
+int tc_partial_slots(int m, int cpad, int64_t n_pad, int sms) {
   int slots = 1;
   for (int mode = 0; mode < 3; ++mode) {
-    const int T = tc_tiles(m, mode);
+    const int T = (int)gram_tiles(m, cpad, mode).size();
     const int L = (int)std::max<int64_t>(1, std::min<int64_t>(n_pad / kTcBK, sms / std::max(T, 1)));
     slots = std::max(slots, T * L);
   }
   return slots;
 }
 
-// Compute tiles: 128 feature rows x up to 256 Gram rows on the upper triangle
-// of Phi^T Phi; a row block's field part (Phi^T F, cpad columns) rides on the
-// tile whose Gram block holds the row block's diagonal (or on a field-only
-// tile when there is no Gram work).  Each tile gets L lanes of the point axis,
-// L = SMs / tiles, so a lone cloud fills the GPU in one wave.
+// Each tile gets L lanes of the point axis, L = SMs / tiles, so a lone cloud
+// fills the GPU in one wave.
 rfd_status build_desc(rfd_plan_s* pl) {
   PlanDesc& d = pl->desc;
   const int m = pl->m;
   const int64_t kb_total = pl->n_pad / kTcBK;
-  const int a_rows = std::min(kTcBM, m), b_rows = std::min(kTcBNMax, m);
+  const int a_rows = std::min(kTcBM, m);
   for (int mode = 0; mode < 3; ++mode) {
-    const bool with_gram = mode != kModeIntegrate, with_field = mode != kModeFeatures;
-    struct CT {
-      int i0, j0, ni, nj;
-      bool f;
-    };
-    std::vector<CT> ct;
-    for (int i0 = 0; i0 < m; i0 += kTcBM) {
-      const int ni = std::min(kTcBM, m - i0);
-      if (!with_gram) {
-        ct.push_back(CT{i0, -1, ni, 0, true});
-        continue;
-      }
-      for (int j0 = 0; j0 < m; j0 += kTcBNMax) {
-        const int nj = std::min(kTcBNMax, m - j0);
-        if (j0 + nj - 1 < i0) continue;  // entirely below the diagonal
-        ct.push_back(CT{i0, j0, ni, nj, with_field && j0 == (i0 / kTcBNMax) * kTcBNMax});
-      }
-    }
+    const std::vector<GramCT> ct = gram_tiles(m, pl->cpad, mode);
     const int T = (int)ct.size();
     const int L = (int)std::max<int64_t>(1, std::min<int64_t>(kb_total, pl->sms / std::max(T, 1)));
     for (int t = 0; t < T; ++t) {
-      const CT& c = ct[t];
+      const GramCT& c = ct[t];
       for (int l = 0; l < L; ++l) {
         TcUnit u{};
         u.out = pl->d_part + (int64_t)(t * L + l) * pl->slot_elems;
         u.map = 0;
         u.i0 = c.i0;
         u.j0 = c.j0;
-        u.nj_mma = c.nj > 0 ? (int)round_up(c.nj, 16) : 0;
+        u.nj_mma = c.nj_mma;
         u.has_f = c.f ? 1 : 0;
         u.cpad = pl->cpad;
         u.lane = l;
         u.nlanes = L;
         u.kb_total = (int)kb_total;
         u.a_rows = a_rows;
-        u.b_rows = b_rows;
+        u.b_rows = m;
         d.units[mode].push_back(u);
       }
       // reduce tiles: .count holds the compute tile index until a batch assigns lanes
@@ -294,7 +305,7 @@ rfd_status build_desc(rfd_plan_s* pl) {
   pc.map_b = 4;
   for (int m0 = 0; m0 < pc.mpa; m0 += 128)
     for (int n0 = 0; n0 < pc.mpb; n0 += 64) d.oz.push_back(OzTile{0, m0, n0, 0});
-  if (!make_gram_maps(d.maps[0], pl->d_psi, pl->n_pad, m, pl->cpad, pl->rows_alloc))
+  if (!make_gram_maps(d.maps[0], d.maps[5], pl->d_psi, pl->n_pad, m, pl->cpad, pl->rows_alloc))
     return fail(RFD_ECUDA, "tensor-map encoding of the feature matrix failed");
   if (!make_ozaki_maps(d.maps[3], d.maps[4], pc.sa, pc.sb, pc.mpa, pc.mpb, pc.kp))
     return fail(RFD_ECUDA, "tensor-map encoding of the FP64-emulation slices failed");
@@ -530,7 +541,7 @@ rfd_status plan_prepare(const rfd_params& p, cudaStream_t stream, rfd_plan_s** o
     build_tiles_simt(pl, false, true, pl->field_only);
     build_tiles_simt(pl, true, true, pl->both);
   }
-  pl->part_slots = pl->bf16 ? tc_partial_slots(pl->m, pl->n_pad, pl->sms)
+  pl->part_slots = pl->bf16 ? tc_partial_slots(pl->m, pl->cpad, pl->n_pad, pl->sms)
                             : std::max({pl->gram_only.slots, pl->field_only.slots, pl->both.slots});
   pl->slot_elems = pl->bf16 ? (int64_t)kTcBM * kTcLd : (int64_t)kSimtTile * kSimtTile;
   pl->rows_alloc = (int)std::max<int64_t>(round_up(p.m, 128), p.m + round_up(pl->cpad, 128));

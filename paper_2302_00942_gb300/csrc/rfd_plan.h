@@ -12,7 +12,7 @@ namespace rfd {
 
 constexpr int kRing = 64;
 constexpr int kTensorMapBytes = 128;
-constexpr int kMapsPerCloud = 5;  // Gram A / B / F maps, Ozaki slice maps A / B
+constexpr int kMapsPerCloud = 6;  // Gram A / B (64-row box) / F maps, Ozaki slice maps A / B, Gram B (16-row box)
 
 // CUDA-event timing of the path's steps (RFD_FLAG_TIMING): a ring of per-call
 // event sets, folded into per-step sums when the stream is synchronised.
