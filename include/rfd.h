@@ -89,6 +89,12 @@ typedef struct rfd_plan_s* rfd_plan_t;
 #define RFD_FLAG_GRAPH 4        /* batches only: replay each call's launches from CUDA graphs,
                                    captured on first use per call shape (per-step timings are
                                    then not recorded) */
+#define RFD_FLAG_AUTOTUNE 8     /* BF16 plans and batches: after the first features pass, time the
+                                   tensor-core reductions for a few split-K lane counts (plans) or
+                                   wave targets (batches) and point-axis phase lengths on the
+                                   cloud's own features, and keep the fastest (cached per bucket:
+                                   m, point count and field width for plans; cloud count and work
+                                   for batches).  That first call returns after the tuning. */
 
 /* Indices of rfd_stats.step_ms */
 enum {
@@ -118,6 +124,10 @@ typedef struct {
   double step_ms[RFD_NUM_STEPS];
   int64_t timed_calls;
   int64_t kernel_launches;
+  int32_t tune_lanes_pct;    /* reductions' launch parameters in use (RFD_FLAG_AUTOTUNE picks them): */
+  int32_t tune_waves;        /*   split-K lanes (% of SMs per tile), waves a batch plans for, */
+  int32_t tune_phase_blocks; /*   point-axis phase length (64-point blocks)                  */
+  int32_t tuned;             /* 1 once the autotuner has chosen them                        */
 } rfd_stats;
 
 /* ---------------------------------------------------------------------------

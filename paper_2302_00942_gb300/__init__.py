@@ -22,7 +22,7 @@ __all__ = [
     "lib", "lib_path", "rfd_sample_frequencies", "rfd_plan", "rfd_plan_destroy", "rfd_features",
     "rfd_integrate", "rfd_gfi", "rfd_phi1", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
     "rfd_version", "RFD_FLAG_TIMING", "STEP_NAMES", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "Plan", "Batch", "rfd_batch_item", "HEADER_SYMBOLS",
-    "RFD_FLAG_NATIVE_FP64", "RFD_FLAG_GRAPH", "Server", "rfd_request", "rfd_result", "rfd_server_config",
+    "RFD_FLAG_NATIVE_FP64", "RFD_FLAG_GRAPH", "RFD_FLAG_AUTOTUNE", "Server", "rfd_request", "rfd_result", "rfd_server_config",
     "rfd_server_stats",
 ]
 
@@ -44,6 +44,7 @@ class rfd_params(ctypes.Structure):
 RFD_FLAG_TIMING = 1
 RFD_FLAG_NATIVE_FP64 = 2
 RFD_FLAG_GRAPH = 4
+RFD_FLAG_AUTOTUNE = 8
 STEP_NAMES = ("features", "field", "gram", "reduce", "phi1", "small", "apply")
 
 
@@ -51,7 +52,8 @@ class rfd_stats(ctypes.Structure):
     _fields_ = [("norm1", ctypes.c_double), ("pade_degree", ctypes.c_int32), ("squarings", ctypes.c_int32),
                 ("nonfinite", ctypes.c_int32), ("splits", ctypes.c_int32), ("phi1_emulated", ctypes.c_int32),
                 ("phi1_gemms", ctypes.c_int32), ("step_ms", ctypes.c_double * len(STEP_NAMES)), ("timed_calls", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("tune_lanes_pct", ctypes.c_int32), ("tune_waves", ctypes.c_int32),
+                ("tune_phase_blocks", ctypes.c_int32), ("tuned", ctypes.c_int32)]
 
 
 class rfd_batch_item(ctypes.Structure):
@@ -271,12 +273,13 @@ class Plan:
     """
 
     def __init__(self, n, m, eps, lam, seed=0, max_channels=3, precision=RFD_BF16_TC, stream=None,
-                 freq_sigma=0.0, freq_radius=0.0, timing=False, native_fp64=False):
+                 freq_sigma=0.0, freq_radius=0.0, timing=False, native_fp64=False, autotune=False):
         self.n, self.m, self.max_channels = int(n), int(m), int(max_channels)
         self.handle = None
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
         self.handle = rfd_plan(n, m, eps, lam, seed, max_channels, precision, s, freq_sigma, freq_radius,
-                               (RFD_FLAG_TIMING if timing else 0) | (RFD_FLAG_NATIVE_FP64 if native_fp64 else 0))
+                               (RFD_FLAG_TIMING if timing else 0) | (RFD_FLAG_NATIVE_FP64 if native_fp64 else 0) |
+                               (RFD_FLAG_AUTOTUNE if autotune else 0))
 
     @staticmethod
     def _chk(t, shape_last=None):
@@ -337,13 +340,13 @@ class Batch:
     tensor, "out": (N, c) tensor or None}; all float32 CUDA, row-major.
     """
 
-    def __init__(self, plans, stream=None, timing=False, graph=False):
+    def __init__(self, plans, stream=None, timing=False, graph=False, autotune=False):
         self.plans = list(plans)
         self.handle = None
         arr = (ctypes.c_void_p * len(self.plans))(*[p.handle for p in self.plans])
         h = ctypes.c_void_p()
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
-        flags = (RFD_FLAG_TIMING if timing else 0) | (RFD_FLAG_GRAPH if graph else 0)
+        flags = (RFD_FLAG_TIMING if timing else 0) | (RFD_FLAG_GRAPH if graph else 0) | (RFD_FLAG_AUTOTUNE if autotune else 0)
         _check(lib.rfd_batch_create(arr, len(self.plans), flags, s, ctypes.byref(h)), "rfd_batch_create")
         self.handle = h.value
 

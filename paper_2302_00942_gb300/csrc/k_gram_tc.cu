@@ -209,7 +209,7 @@ cudaError_t gram_tc_prepare() {
 }
 
 cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_units, int max_cpad, int max_kb,
-                           int* err, cudaStream_t st) {
+                           int phase_blocks, int* err, cudaStream_t st) {
   if (num_units <= 0) return cudaSuccess;
   if (max_cpad < 16 || max_cpad > 256) return cudaErrorInvalidValue;
   const int stage_bytes = stage_bytes_for(max_cpad);
@@ -219,12 +219,13 @@ cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_un
   const int smem = stages * stage_bytes + kSmemExtra;
   const cudaError_t attr = gram_tc_prepare();
   if (attr != cudaSuccess) return attr;
-  // the point axis in phases of kGramPhaseBlocks 64-point blocks, one launch each, so that the
+  // the point axis in phases of phase_blocks 64-point blocks, one launch each, so that the
   // lanes of a tile restart in step (and the slab they share stays in L2) every phase
-  const int phases = max_kb > 0 ? (max_kb + kGramPhaseBlocks - 1) / kGramPhaseBlocks : 1;
+  if (phase_blocks < 1) phase_blocks = kGramPhaseBlocks;
+  const int phases = max_kb > 0 ? (max_kb + phase_blocks - 1) / phase_blocks : 1;
   for (int ph = 0; ph < phases; ++ph) {
     gram_tc_kernel<<<num_units, kThreads, smem, st>>>(static_cast<const CUtensorMap*>(maps_dev), units, stages,
-                                                      stage_bytes, ph * kGramPhaseBlocks, kGramPhaseBlocks, err);
+                                                      stage_bytes, ph * phase_blocks, phase_blocks, err);
     const cudaError_t e = launched();
     if (e != cudaSuccess) return e;
   }

@@ -84,11 +84,11 @@ struct TcUnit {
 // maps_host3[0..2]: A (box min(128, m) rows), B (box min(64, m) rows), F rows (box cpad rows);
 // map_b16: B with a box of min(16, m) rows.
 bool make_gram_maps(void* maps_host3, void* map_b16, const void* psi, int64_t n_pad, int m, int cpad, int rows_alloc);
-// One launch per phase of kGramPhaseBlocks 64-point blocks (max_kb: the largest
+// One launch per phase of phase_blocks 64-point blocks (max_kb: the largest
 // point-block count of the units' clouds); later phases add to the partials.
-constexpr int kGramPhaseBlocks = 4096;
+constexpr int kGramPhaseBlocks = 4096;  // default phase length
 cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_units, int max_cpad, int max_kb,
-                           int* err, cudaStream_t st);
+                           int phase_blocks, int* err, cudaStream_t st);
 bool tc_gram_supported();
 
 // Sum the split-K partials of every tile in a fixed order (Kahan) and apply

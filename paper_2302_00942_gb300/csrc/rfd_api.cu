@@ -9,7 +9,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
 #include "kernels.h"
@@ -29,6 +32,9 @@ struct rfd_batch_s {
   std::vector<rfd_plan_t> plans;
   Timing timing;
   cudaStream_t stream = nullptr;
+  int options = 0;
+  GramTuning tune;
+  bool autotune = false, tuned = false;
 };
 
 namespace {
@@ -205,11 +211,13 @@ std::vector<GramCT> gram_tiles(int m, int cpad, int mode) {
   return ct;
 }
 
-int tc_partial_slots(int m, int cpad, int64_t n_pad, int sms) {
+constexpr int kTuneLanesMax = 200;  // the largest lanes_pct the autotuner tries
+
+int tc_partial_slots(int m, int cpad, int64_t n_pad, int sms, int lanes_pct) {
   int slots = 1;
   for (int mode = 0; mode < 3; ++mode) {
     const int T = (int)gram_tiles(m, cpad, mode).size();
-    const int L = (int)std::max<int64_t>(1, std::min<int64_t>(n_pad / kTcBK, sms / std::max(T, 1)));
+    const int L = (int)std::max<int64_t>(1, std::min<int64_t>(n_pad / kTcBK, (int64_t)sms * lanes_pct / 100 / std::max(T, 1)));
     slots = std::max(slots, T * L);
   }
   return slots;
@@ -219,13 +227,19 @@ int tc_partial_slots(int m, int cpad, int64_t n_pad, int sms) {
 // fills the GPU in one wave.
 rfd_status build_desc(rfd_plan_s* pl) {
   PlanDesc& d = pl->desc;
+  for (int mode = 0; mode < 3; ++mode) {
+    d.units[mode].clear();
+    d.red[mode].clear();
+  }
+  d.oz.clear();
   const int m = pl->m;
   const int64_t kb_total = pl->n_pad / kTcBK;
   const int a_rows = std::min(kTcBM, m);
   for (int mode = 0; mode < 3; ++mode) {
     const std::vector<GramCT> ct = gram_tiles(m, pl->cpad, mode);
     const int T = (int)ct.size();
-    const int L = (int)std::max<int64_t>(1, std::min<int64_t>(kb_total, pl->sms / std::max(T, 1)));
+    const int L = (int)std::max<int64_t>(
+        1, std::min<int64_t>(kb_total, (int64_t)pl->sms * pl->tune.lanes_pct / 100 / std::max(T, 1)));
     for (int t = 0; t < T; ++t) {
       const GramCT& c = ct[t];
       for (int l = 0; l < L; ++l) {
@@ -388,12 +402,88 @@ struct CallScope {
   ~CallScope() { t->end_call(); }
 };
 
+// ---- autotuner -------------------------------------------------------------
+// Picks the launch parameters of the tensor-core reductions by timing them on
+// the cloud's own features after its first features pass: split-K lanes of a
+// lone cloud (50 / 100 / 200 % of SMs per tile) or the waves a batch plans
+// for (2 / 4 / 8), times the phase length of the point axis (2048 / 4096 /
+// 8192 blocks of 64 points).  Choices are kept per bucket -- (m, log2 of the
+// point blocks, field width) for plans, (clouds, log2 of the work) for batches
+// -- and reused without timing by later plans / batches of the same bucket.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, GramTuning> g_plan_tune;
+std::map<std::pair<int, int>, GramTuning> g_batch_tune;
+constexpr int kTunePhases[3] = {2048, 4096, 8192};
+
+int ilog2(double x) { return x < 1.0 ? 0 : (int)std::floor(std::log2(x)); }
+
+// Rebuilds the plan's descriptors and its batch of one for pl->tune.
+rfd_status rebuild_self(rfd_plan_s* pl) {
+  RFD_CUDA(cudaStreamSynchronize(pl->stream));
+  rfd_status s = build_desc(pl);
+  if (s != RFD_OK) return s;
+  BatchImpl* nb = nullptr;
+  rfd_plan_s* self = pl;
+  if ((s = batch_build(&self, 1, pl->stream, pl->mem, 0, pl->tune, &nb)) != RFD_OK) return s;
+  RFD_CUDA(cudaStreamSynchronize(pl->stream));
+  batch_free(pl->self);
+  pl->self = nb;
+  pl->stats.splits = pl->desc.units[kModeGfi].empty() ? 0 : pl->desc.units[kModeGfi][0].nlanes;
+  return RFD_OK;
+}
+
+rfd_status tune_plan(rfd_plan_s* pl, int mode) {
+  const auto key = std::make_tuple(pl->m, ilog2((double)(pl->n_pad / kTcBK)), pl->cpad);
+  pl->tuned = true;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_plan_tune.find(key);
+    if (it != g_plan_tune.end()) {
+      pl->tune = it->second;
+      return rebuild_self(pl);
+    }
+  }
+  RFD_CUDA(cudaStreamSynchronize(pl->stream));  // the features of the first pass are in place
+  float best = 1e30f;
+  GramTuning best_t = pl->tune;
+  for (int lp : {50, 100, kTuneLanesMax}) {
+    pl->tune.lanes_pct = lp;
+    rfd_status s = build_desc(pl);
+    BatchImpl* tb = nullptr;
+    rfd_plan_s* self = pl;
+    if (s == RFD_OK) s = batch_build(&self, 1, pl->stream, cuda_mem(), 0, pl->tune, &tb);
+    if (s != RFD_OK) return s;
+    for (int ph : kTunePhases) {
+      batch_set_phase(tb, ph);
+      float ms = 0.f;
+      s = batch_time_gram(tb, mode, 2, &ms);
+      if (s != RFD_OK) break;
+      if (ms < best) {
+        best = ms;
+        best_t = pl->tune;
+        best_t.phase_blocks = ph;
+      }
+    }
+    cudaStreamSynchronize(pl->stream);
+    batch_free(tb);
+    if (s != RFD_OK) return s;
+  }
+  pl->tune = best_t;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_plan_tune[key] = best_t;
+  }
+  return rebuild_self(pl);
+}
+
 rfd_status run_plan(rfd_plan_s* pl, int mode, const float* pts, const float* F, int c, int64_t ldF, float* out,
                     int64_t ldOut) {
   CallScope call(&pl->timing, pl->stream);
   if (pl->bf16) {
     CloudCall cc{pts, F, out, ldF, ldOut, c, 0};
-    return batch_run(pl->self, mode, &cc, &pl->timing);
+    rfd_status s = batch_run(pl->self, mode, &cc, &pl->timing);
+    if (s == RFD_OK && pl->autotune && !pl->tuned && mode != kModeIntegrate) s = tune_plan(pl, mode);
+    return s;
   }
   cudaStream_t st = pl->stream;
   void* rows = static_cast<uint8_t*>(pl->d_psi) + (size_t)pl->m * pl->n_pad * 4;
@@ -487,7 +577,8 @@ rfd_status plan_prepare(const rfd_params& p, cudaStream_t stream, rfd_plan_s** o
   if (p.max_channels < 1 || p.max_channels > kMaxChannels) return fail(RFD_EINVAL, "max_channels must be in [1, 256]");
   if (!std::isfinite(p.lambda)) return fail(RFD_EINVAL, "lambda must be finite");
   if (p.precision != RFD_FP32_PLAIN && p.precision != RFD_BF16_TC) return fail(RFD_EINVAL, "unknown precision");
-  if (p.flags & ~(RFD_FLAG_TIMING | RFD_FLAG_NATIVE_FP64)) return fail(RFD_EINVAL, "unknown bits in flags");
+  if (p.flags & ~(RFD_FLAG_TIMING | RFD_FLAG_NATIVE_FP64 | RFD_FLAG_AUTOTUNE))
+    return fail(RFD_EINVAL, "unknown bits in flags");
   if (p.n > (int64_t)1 << 31) return fail(RFD_EINVAL, "n must be < 2^31");
   auto* pl = new (std::nothrow) rfd_plan_s();
   if (!pl) return fail(RFD_ENOMEM, "host allocation failed");
@@ -541,7 +632,8 @@ rfd_status plan_prepare(const rfd_params& p, cudaStream_t stream, rfd_plan_s** o
     build_tiles_simt(pl, false, true, pl->field_only);
     build_tiles_simt(pl, true, true, pl->both);
   }
-  pl->part_slots = pl->bf16 ? tc_partial_slots(pl->m, pl->cpad, pl->n_pad, pl->sms)
+  pl->autotune = pl->bf16 && (p.flags & RFD_FLAG_AUTOTUNE);
+  pl->part_slots = pl->bf16 ? tc_partial_slots(pl->m, pl->cpad, pl->n_pad, pl->sms, pl->autotune ? kTuneLanesMax : 100)
                             : std::max({pl->gram_only.slots, pl->field_only.slots, pl->both.slots});
   pl->slot_elems = pl->bf16 ? (int64_t)kTcBM * kTcLd : (int64_t)kSimtTile * kSimtTile;
   pl->rows_alloc = (int)std::max<int64_t>(round_up(p.m, 128), p.m + round_up(pl->cpad, 128));
@@ -605,7 +697,7 @@ rfd_status plan_materialize(rfd_plan_s* pl, MemSource* mem, bool self_batch, boo
     if ((st2 = build_desc(pl)) != RFD_OK) return bail(st2);
     if (self_batch) {
       rfd_plan_s* self = pl;
-      if ((st2 = batch_build(&self, 1, st, mem, 0, &pl->self)) != RFD_OK) return bail(st2);
+      if ((st2 = batch_build(&self, 1, st, mem, 0, pl->tune, &pl->self)) != RFD_OK) return bail(st2);
     }
     pl->stats.splits = pl->desc.units[kModeGfi].empty() ? 0 : pl->desc.units[kModeGfi][0].nlanes;
   } else {
@@ -736,6 +828,10 @@ rfd_status rfd_plan_stats(rfd_plan_t pl, rfd_stats* out) {
   pl->timing.fold(pl->stream);
   *out = pl->stats;
   fill_stats(pl->timing, out);
+  out->tune_lanes_pct = pl->tune.lanes_pct;
+  out->tune_waves = pl->tune.waves;
+  out->tune_phase_blocks = pl->tune.phase_blocks;
+  out->tuned = pl->tuned ? 1 : 0;
   return RFD_OK;
 }
 
@@ -750,7 +846,7 @@ rfd_status rfd_plan_stats_reset(rfd_plan_t pl) {
 rfd_status rfd_batch_create(const rfd_plan_t* plans, int32_t count, int32_t flags, void* cuda_stream,
                             rfd_batch_t* out) {
   if (!plans || !out || count < 1) return fail(RFD_EINVAL, "null plans / output or count < 1");
-  if (flags & ~(RFD_FLAG_TIMING | RFD_FLAG_GRAPH)) return fail(RFD_EINVAL, "unknown bits in flags");
+  if (flags & ~(RFD_FLAG_TIMING | RFD_FLAG_GRAPH | RFD_FLAG_AUTOTUNE)) return fail(RFD_EINVAL, "unknown bits in flags");
   *out = nullptr;
   std::vector<rfd_plan_s*> v(plans, plans + count);
   for (int i = 0; i < count; ++i) {
@@ -763,8 +859,9 @@ rfd_status rfd_batch_create(const rfd_plan_t* plans, int32_t count, int32_t flag
   if (!b) return fail(RFD_ENOMEM, "host allocation failed");
   b->plans = v;
   b->stream = static_cast<cudaStream_t>(cuda_stream);
-  rfd_status s = batch_build(v.data(), count, b->stream, cuda_mem(), (flags & RFD_FLAG_GRAPH) ? kBatchGraphs : 0,
-                             &b->impl);
+  b->options = (flags & RFD_FLAG_GRAPH) ? kBatchGraphs : 0;
+  b->autotune = (flags & RFD_FLAG_AUTOTUNE) != 0;
+  rfd_status s = batch_build(v.data(), count, b->stream, cuda_mem(), b->options, b->tune, &b->impl);
   if (s == RFD_OK && (flags & RFD_FLAG_TIMING)) {
     cudaError_t ce = b->timing.init();
     if (ce != cudaSuccess) s = cuda_fail("event creation", ce);
@@ -789,6 +886,59 @@ rfd_status rfd_batch_destroy(rfd_batch_t b) {
   return RFD_OK;
 }
 
+// Batch autotuning (see tune_plan): waves x phase length, timed on the batch's own features.
+static rfd_status tune_batch(rfd_batch_t b, int mode) {
+  b->tuned = true;
+  double work = 0.0;
+  for (rfd_plan_s* pl : b->plans) work += (double)pl->desc.units[kModeGfi].size() * (double)(pl->n_pad / kTcBK);
+  const auto key = std::make_pair((int)b->plans.size(), ilog2(work));
+  GramTuning best_t = b->tune;
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_batch_tune.find(key);
+    if (it != g_batch_tune.end()) {
+      best_t = it->second;
+      cached = true;
+    }
+  }
+  RFD_CUDA(cudaStreamSynchronize(b->stream));
+  if (!cached) {
+    float best = 1e30f;
+    for (int waves : {2, 4, 8}) {
+      GramTuning t = b->tune;
+      t.waves = waves;
+      BatchImpl* tb = nullptr;
+      rfd_status s = batch_build(b->plans.data(), (int)b->plans.size(), b->stream, cuda_mem(), 0, t, &tb);
+      if (s != RFD_OK) return s;
+      for (int ph : kTunePhases) {
+        batch_set_phase(tb, ph);
+        float ms = 0.f;
+        s = batch_time_gram(tb, mode, 2, &ms);
+        if (s != RFD_OK) break;
+        if (ms < best) {
+          best = ms;
+          best_t = t;
+          best_t.phase_blocks = ph;
+        }
+      }
+      cudaStreamSynchronize(b->stream);
+      batch_free(tb);
+      if (s != RFD_OK) return s;
+    }
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_batch_tune[key] = best_t;
+  }
+  b->tune = best_t;
+  BatchImpl* nb = nullptr;
+  rfd_status s = batch_build(b->plans.data(), (int)b->plans.size(), b->stream, cuda_mem(), b->options, b->tune, &nb);
+  if (s != RFD_OK) return s;
+  RFD_CUDA(cudaStreamSynchronize(b->stream));
+  batch_free(b->impl);
+  b->impl = nb;
+  return RFD_OK;
+}
+
 static rfd_status batch_call(rfd_batch_t b, int mode, const rfd_batch_item* items) {
   if (!b || !items) return fail(RFD_EINVAL, "null batch or items");
   std::vector<CloudCall> calls(b->plans.size());
@@ -807,7 +957,9 @@ static rfd_status batch_call(rfd_batch_t b, int mode, const rfd_batch_item* item
     calls[k] = CloudCall{it.d_points, it.d_F, it.d_out, it.ldF, it.ldOut, c, 0};
   }
   CallScope call(&b->timing, b->stream);
-  return batch_run(b->impl, mode, calls.data(), &b->timing);
+  rfd_status s = batch_run(b->impl, mode, calls.data(), &b->timing);
+  if (s == RFD_OK && b->autotune && !b->tuned && mode != kModeIntegrate) s = tune_batch(b, mode);
+  return s;
 }
 
 rfd_status rfd_batch_features(rfd_batch_t b, const rfd_batch_item* items) { return batch_call(b, kModeFeatures, items); }
@@ -828,6 +980,10 @@ rfd_status rfd_batch_stats(rfd_batch_t b, rfd_stats* out) {
   b->timing.fold(b->stream);
   *out = rfd_stats{};
   fill_stats(b->timing, out);
+  out->tune_lanes_pct = b->tune.lanes_pct;
+  out->tune_waves = b->tune.waves;
+  out->tune_phase_blocks = b->tune.phase_blocks;
+  out->tuned = b->tuned ? 1 : 0;
   return RFD_OK;
 }
 

@@ -90,6 +90,7 @@ struct BatchImpl {
   OzTile* d_oz = nullptr;
   int n_oz = 0;
   int max_m = 0, max_cpad = 16, max_kb = 0;
+  int phase_blocks = kGramPhaseBlocks;
   bool phi_batched = true;  // all clouds on the emulated path (no native-FP64 flag)
   // per-call device words
   CloudCall* d_calls = nullptr;  // followed by the apply-block prefix (count + 1 ints)
@@ -133,7 +134,7 @@ void batch_free(BatchImpl* b) {
 }
 
 rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, MemSource* mem, int options,
-                       BatchImpl** out) {
+                       const GramTuning& tune, BatchImpl** out) {
   *out = nullptr;
   auto* b = new (std::nothrow) BatchImpl();
   if (!b) return fail(RFD_ENOMEM, "host allocation failed");
@@ -142,6 +143,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   b->st = st;
   b->mem = mem;
   b->options = options;
+  b->phase_blocks = tune.phase_blocks;
   auto bail = [&](rfd_status s, const std::string& msg) {
     batch_free(b);
     return fail(s, msg);
@@ -151,7 +153,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   double work = 0.0;
   for (int k = 0; k < count; ++k)
     work += (double)plans[k]->desc.units[kModeGfi].size() * (double)(plans[k]->n_pad / kTcBK);
-  const double target = (count == 1) ? 1e300 : std::max(1.0, work / (4.0 * sms));  // k-blocks per CTA
+  const double target = (count == 1) ? 1e300 : std::max(1.0, work / (tune.waves * (double)sms));  // k-blocks per CTA
   std::vector<TcUnit> units[3];
   std::vector<RedTile> red[3];
   std::vector<unsigned char> maps((size_t)count * kMapsPerCloud * kTensorMapBytes);
@@ -513,7 +515,8 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
     }
     {
       StepScope sc(t, s, RFD_STEP_GRAM);
-      BCK(launch_gram_tc(b->d_maps, b->d_units[mode], b->n_units[mode], b->max_cpad, b->max_kb, b->d_err, s));
+      BCK(launch_gram_tc(b->d_maps, b->d_units[mode], b->n_units[mode], b->max_cpad, b->max_kb, b->phase_blocks,
+                         b->d_err, s));
     }
     StepScope sc(t, s, RFD_STEP_REDUCE);
     BCK(launch_reduce_batched(b->d_red[mode], b->n_red[mode], b->d_calls, s));
@@ -635,6 +638,30 @@ void Timing::reset(cudaStream_t st) {
   for (double& v : sum) v = 0.0;
   calls = 0;
   launches = 0;
+}
+
+void batch_set_phase(BatchImpl* b, int phase_blocks) { b->phase_blocks = phase_blocks; }
+
+rfd_status batch_time_gram(BatchImpl* b, int mode, int reps, float* ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  auto launch = [&] {
+    return launch_gram_tc(b->d_maps, b->d_units[mode], b->n_units[mode], b->max_cpad, b->max_kb, b->phase_blocks,
+                          b->d_err, b->st);
+  };
+  cudaError_t e = launch();  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, b->st);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+  if (e == cudaSuccess) e = cudaEventRecord(e1, b->st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail2("Gram timing", e);
+  *ms = t / (float)reps;
+  return RFD_OK;
 }
 
 rfd_status batch_check_error(BatchImpl* b, int* bad) {

@@ -97,6 +97,15 @@ MemSource* cuda_mem();  // cudaMalloc / cudaMallocHost, with the allocation-fail
 // Batch options
 enum : int { kBatchGraphs = 1 };  // replay the batch's launches from CUDA graphs
 
+// Launch parameters of the tensor-core reductions that the autotuner varies:
+// the split-K lanes of a lone cloud (percent of SMs / tiles), the waves of CTAs
+// a batch plans for, and the phase length of the point axis.
+struct GramTuning {
+  int lanes_pct = 100;
+  int waves = 4;
+  int phase_blocks = kGramPhaseBlocks;
+};
+
 }  // namespace rfd
 
 struct rfd_plan_s {
@@ -133,6 +142,8 @@ struct rfd_plan_s {
   rfd_stats stats{};
   std::vector<void*> allocs;       // temporary owners only (rfd_phi1, debug GEMM)
   rfd::MemSource* mem = nullptr;   // source of the plan's single device chunk
+  rfd::GramTuning tune;            // tensor-core reduction launch parameters
+  bool autotune = false, tuned = false;
   void* chunk = nullptr;
   size_t chunk_bytes = 0;
   rfd::Timing timing;
@@ -151,7 +162,7 @@ void plan_destroy(rfd_plan_s* pl);  // frees without synchronising (the caller h
 // Builds / frees the device tables of a batch over the given BF16 plans (one
 // device and one pinned block from `mem`; uploads are asynchronous on `st`).
 rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, MemSource* mem, int options,
-                       BatchImpl** out);
+                       const GramTuning& tune, BatchImpl** out);
 void batch_free(BatchImpl* b);  // the caller has synchronised the batch's stream
 size_t batch_device_bytes(BatchImpl* b);
 // Runs one batched call.  calls: one CloudCall per plan (pts / F / out as the
@@ -164,5 +175,9 @@ cudaStream_t batch_stream(BatchImpl* b);
 // RFD_ENUMERIC if some cloud's G is not finite (bad[k] = 1 for those clouds when
 // bad is given).
 rfd_status batch_check_error(BatchImpl* b, int* bad = nullptr);
+// Times the Gram launches of one batched call of `mode` (the features must be
+// in place): mean ms over `reps` launches after one warm-up.
+rfd_status batch_time_gram(BatchImpl* b, int mode, int reps, float* ms);
+void batch_set_phase(BatchImpl* b, int phase_blocks);
 
 }  // namespace rfd

@@ -214,7 +214,7 @@ void run_group(rfd_server_s* s, std::vector<Req*>& group, int mode, cudaStream_t
     calls.push_back(CloudCall{q->r.d_points, q->r.d_F, q->r.d_out, q->r.ldF, q->r.ldOut, q->r.c, 0});
   }
   BatchImpl* b = nullptr;
-  rfd_status bs = batch_build(plans.data(), (int)plans.size(), stream, &s->table_mem, 0, &b);
+  rfd_status bs = batch_build(plans.data(), (int)plans.size(), stream, &s->table_mem, 0, GramTuning{}, &b);
   if (bs == RFD_ENOMEM && group.size() > 1) {
     const size_t h = group.size() / 2;
     std::vector<Req*> a(group.begin(), group.begin() + h), c(group.begin() + h, group.end());

@@ -135,3 +135,36 @@ def test_nonfinite_G_is_reported_at_sync():
     assert e.value.status == rfd.RFD_EINVAL
     p.sync()   # the flags were cleared by the first sync
     p.close()
+
+
+def test_autotuned_batch_and_plan():
+    specs = _specs(count=5, seed=21)
+    clouds = [synth.make_cloud(s) for s in specs]
+    stream = torch.cuda.current_stream(DEV)
+    plans = _plans(specs, stream)
+    batch = rfd.Batch(plans, stream=stream, autotune=True)
+    items = [{"points": torch.from_numpy(p).to(DEV), "F": torch.from_numpy(F).to(DEV)} for p, F in clouds]
+    for rep in range(2):   # the first call tunes, the second runs the chosen tables
+        outs = batch.gfi(items)
+        batch.sync()
+        for k, s in enumerate(specs):
+            ref = oracle.rfd_gfi(clouds[k][0], clouds[k][1], s.eps, _lam(s), s.m, s.seed)
+            assert oracle.rel_frobenius(outs[k].cpu().numpy(), ref) <= TOL
+    st = batch.stats()
+    assert st["tuned"] == 1 and st["tune_waves"] in (2, 4, 8) and st["tune_phase_blocks"] in (2048, 4096, 8192)
+    batch.close()
+    # a lone autotuned plan, then a second plan of the same bucket (taken from the cache)
+    s = specs[0]
+    for _ in range(2):
+        p = rfd.Plan(s.n, s.m, s.eps, _lam(s), s.seed, max_channels=8, precision=rfd.RFD_BF16_TC, autotune=True)
+        P, Fd = items[0]["points"], items[0]["F"]
+        for rep in range(2):
+            out = p.gfi(P, Fd)
+            p.sync()
+            ref = oracle.rfd_gfi(clouds[0][0], clouds[0][1], s.eps, _lam(s), s.m, s.seed)
+            assert oracle.rel_frobenius(out.cpu().numpy(), ref) <= TOL
+        st = p.stats()
+        assert st["tuned"] == 1 and st["tune_lanes_pct"] in (50, 100, 200)
+        p.close()
+    for p in plans:
+        p.close()

@@ -74,7 +74,7 @@ def test_sampler_acceptance_limit():
 
 
 @pytest.mark.parametrize("kw", [dict(n=0), dict(m=7), dict(m=8192), dict(max_channels=0), dict(max_channels=300),
-                                dict(lam=float("inf")), dict(precision=5), dict(flags=8), dict(eps=0.0)])
+                                dict(lam=float("inf")), dict(precision=5), dict(flags=16), dict(eps=0.0)])
 def test_plan_rejects_invalid_before_device_work(kw):
     args = dict(n=100, m=64, eps=0.1, lam=0.1, seed=0, max_channels=3, precision=rfd.RFD_BF16_TC, flags=0)
     args.update(kw)
