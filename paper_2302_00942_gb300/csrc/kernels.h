@@ -59,25 +59,30 @@ constexpr int kSimtK = 16;
 cudaError_t launch_gram_simt(const float* psi, int64_t n_pad, const GramUnit* units, int num_units,
                              float* partials, cudaStream_t st);
 
-// BF16 tensor-core form (tcgen05 + TMA): one CTA per (tile, lane); a tile is
-// 128 rows x (Gram columns + field columns <= 256).  Partial rows have kTcLd
-// floats: Gram part at column 0, field part at column kTcBNMax.
+// BF16 tensor-core form (tcgen05 + TMA): one CTA per (tile pair, lane).  A
+// logical tile is 128 rows x (Gram columns + field columns <= 256); partial
+// rows have kTcLd floats: Gram part at column 0, field part at column kTcBNMax.
 constexpr int kTcBM = 128;
 constexpr int kTcBNMax = 256;
 constexpr int kTcBK = 64;
 constexpr int kTcLd = 512;
-// One CTA of the tensor-core reductions: tile rows i0.. of one cloud's Psi
-// against Gram rows j0 .. j0 + nj_mma (nj_mma a multiple of 16, may be 0)
-// followed by the cloud's cpad field rows (has_f), one MMA of N = nj_mma (+
-// cpad), over the 64-point blocks kb = lane, lane + nlanes, ... < kb_total.
+// One CTA of the tensor-core reductions: rows i0 .. i0+127 (half 0) and, when
+// out1 is set, rows i0+128 .. i0+255 (half 1) of one cloud's Psi against the
+// same B rows -- Gram rows j0 .. j0 + nj_mma (nj_mma a multiple of 16, may be
+// 0) followed by the cloud's cpad field rows (has_f) -- over the 64-point
+// blocks kb = lane, lane + nlanes, ... < kb_total.  Half 0 is one MMA of
+// N = nj_mma (+ cpad) per 16 points; half 1 skips the first skip1 B rows (the
+// part of a diagonal tile below the diagonal), N = nj_mma - skip1 (+ cpad).
 // maps[map + 0/1/2/5]: the cloud's A (box 128 rows), B (64 rows), F (cpad rows)
-// and B (16 rows) maps; b_rows: rows of the B map (m).
+// and B (16 rows) maps; b_rows: rows of the B map (m).  slot: the logical tile
+// index of half 0 in the plan's partial buffer (half 1: slot + 1).
 struct TcUnit {
-  float* out;          // this CTA's partial tile: 128 rows x kTcLd floats
+  float* out;   // half 0 partial: 128 rows x kTcLd floats
+  float* out1;  // half 1 partial, or null when the unit has one half
   int32_t map;
   int32_t i0, j0, nj_mma, has_f, cpad;
   int32_t lane, nlanes, kb_total, a_rows, b_rows;
-  int32_t pad_;
+  int32_t slot, skip1, pad_;
 };
 // Encodes the three tensor maps of a cloud's bf16 feature matrix Psi
 // ([rows_alloc][n_pad], rows 0..m-1 features, m..m+cpad-1 field) into maps[0..2].
@@ -87,7 +92,8 @@ bool make_gram_maps(void* maps_host3, void* map_b16, const void* psi, int64_t n_
 // One launch per phase of phase_blocks 64-point blocks (max_kb: the largest
 // point-block count of the units' clouds); later phases add to the partials.
 constexpr int kGramPhaseBlocks = 4096;  // default phase length
-cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_units, int max_cpad, int max_kb,
+// a_boxes: 2 when some unit has a second half (stages hold two A boxes), else 1.
+cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_units, int a_boxes, int max_kb,
                            int phase_blocks, int* err, cudaStream_t st);
 bool tc_gram_supported();
 

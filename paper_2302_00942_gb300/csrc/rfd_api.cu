@@ -169,25 +169,30 @@ void build_tiles_simt(rfd_plan_s* pl, bool with_gram, bool with_field, TileSet& 
 }
 
 // ---- BF16 tensor-core form: the plan's batched-path descriptors -------------
-// Compute tiles of one mode.  For each block of 128 feature rows i0.., the
-// Gram columns [i0, m) (the upper triangle and the diagonal block) and, when
-// the mode has a field, the cpad field columns are cut into tiles of at most
-// 256 columns (multiples of 16, as even as possible); the field rides on the
-// last tile, whose B operand is its Gram rows followed by the F rows, so one
-// MMA covers both (a separate field-only tile if it does not fit).  Without
-// Gram work (integrate) every row block gets a field-only tile.
+// Compute tiles of one mode.  For each block of 256 feature rows i0.. (two
+// halves of 128 rows that share their B rows), the Gram columns [i0, m) (the
+// upper triangle and the diagonal blocks) and, when the mode has a field, the
+// cpad field columns are cut into tiles of at most 256 columns (multiples of
+// 16, as even as possible); the field rides on the last tile, whose B operand
+// is its Gram rows followed by the F rows, so one MMA per half covers both (a
+// separate field-only tile if it does not fit).  Half 1 (rows i0+128..) skips
+// the first min(128, width) columns of the block's first tile, which lie below
+// the diagonal.  Without Gram work (integrate) every row block gets a
+// field-only tile.
 struct GramCT {
-  int i0, j0, ni, nj, nj_mma;  // nj: real Gram columns, nj_mma: padded width (multiple of 16)
+  int i0, j0, ni, nj, nj_mma;  // half 0: nj real Gram columns, nj_mma padded width (multiple of 16)
   bool f;
+  int ni1, nj1, skip1;  // half 1 (rows i0 + 128 ..; ni1 = 0: absent): Gram columns j0 + skip1 .., nj1 real
 };
 
 std::vector<GramCT> gram_tiles(int m, int cpad, int mode) {
   const bool with_gram = mode != kModeIntegrate, with_field = mode != kModeFeatures;
   std::vector<GramCT> ct;
-  for (int i0 = 0; i0 < m; i0 += kTcBM) {
+  for (int i0 = 0; i0 < m; i0 += 2 * kTcBM) {
     const int ni = std::min(kTcBM, m - i0);
+    const int ni1 = std::max(0, std::min(kTcBM, m - i0 - kTcBM));
     if (!with_gram) {
-      ct.push_back(GramCT{i0, -1, ni, 0, 0, true});
+      ct.push_back(GramCT{i0, -1, ni, 0, 0, true, ni1, 0, 0});
       continue;
     }
     const int Gp = (int)round_up(m - i0, 16), Fw = with_field ? cpad : 0;
@@ -203,12 +208,30 @@ std::vector<GramCT> gram_tiles(int m, int cpad, int mode) {
       const int w = (units / k + (t < units % k ? 1 : 0)) * 16;
       const bool f = field_here && t == k - 1;
       const int gw = f ? w - Fw : w;
-      ct.push_back(GramCT{i0, col, ni, std::max(0, std::min(gw, m - col)), gw, f});
+      GramCT c{i0, col, ni, std::max(0, std::min(gw, m - col)), gw, f, 0, 0, 0};
+      if (ni1 > 0) {
+        c.skip1 = (col == i0) ? std::min(kTcBM, gw) : 0;
+        c.nj1 = std::max(0, std::min(gw - c.skip1, m - col - c.skip1));
+        if (gw - c.skip1 > 0 || f) c.ni1 = ni1;
+      }
+      ct.push_back(c);
       col += gw;
     }
-    if (Fw > 0 && !field_here) ct.push_back(GramCT{i0, -1, ni, 0, 0, true});
+    if (Fw > 0 && !field_here) ct.push_back(GramCT{i0, -1, ni, 0, 0, true, ni1, 0, 0});
   }
   return ct;
+}
+
+// Logical 128-row tiles (halves) of a mode: each has its own partial slots.
+int gram_halves(const std::vector<GramCT>& ct) {
+  int h = 0;
+  for (const GramCT& c : ct) h += c.ni1 > 0 ? 2 : 1;
+  return h;
+}
+
+// Lanes of the point axis per compute tile: the tiles' CTAs fill lanes_pct % of the SMs.
+int gram_lanes(int64_t kb_total, int sms, int lanes_pct, int tiles) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(kb_total, (int64_t)sms * lanes_pct / 100 / std::max(tiles, 1)));
 }
 
 constexpr int kTuneLanesMax = 200;  // the largest lanes_pct the autotuner tries
@@ -216,15 +239,15 @@ constexpr int kTuneLanesMax = 200;  // the largest lanes_pct the autotuner tries
 int tc_partial_slots(int m, int cpad, int64_t n_pad, int sms, int lanes_pct) {
   int slots = 1;
   for (int mode = 0; mode < 3; ++mode) {
-    const int T = (int)gram_tiles(m, cpad, mode).size();
-    const int L = (int)std::max<int64_t>(1, std::min<int64_t>(n_pad / kTcBK, (int64_t)sms * lanes_pct / 100 / std::max(T, 1)));
-    slots = std::max(slots, T * L);
+    const std::vector<GramCT> ct = gram_tiles(m, cpad, mode);
+    slots = std::max(slots, gram_halves(ct) * gram_lanes(n_pad / kTcBK, sms, lanes_pct, (int)ct.size()));
   }
   return slots;
 }
 
-// Each tile gets L lanes of the point axis, L = SMs / tiles, so a lone cloud
-// fills the GPU in one wave.
+// Each compute tile gets L lanes of the point axis, L = SMs / tiles, so a lone
+// cloud fills the GPU in one wave.  Partial slot of half h (logical tile s) in
+// lane l: s * L + l.
 rfd_status build_desc(rfd_plan_s* pl) {
   PlanDesc& d = pl->desc;
   for (int mode = 0; mode < 3; ++mode) {
@@ -238,13 +261,15 @@ rfd_status build_desc(rfd_plan_s* pl) {
   for (int mode = 0; mode < 3; ++mode) {
     const std::vector<GramCT> ct = gram_tiles(m, pl->cpad, mode);
     const int T = (int)ct.size();
-    const int L = (int)std::max<int64_t>(
-        1, std::min<int64_t>(kb_total, (int64_t)pl->sms * pl->tune.lanes_pct / 100 / std::max(T, 1)));
+    const int L = gram_lanes(kb_total, pl->sms, pl->tune.lanes_pct, T);
+    int slot = 0;
     for (int t = 0; t < T; ++t) {
       const GramCT& c = ct[t];
+      const bool two = c.ni1 > 0;
       for (int l = 0; l < L; ++l) {
         TcUnit u{};
-        u.out = pl->d_part + (int64_t)(t * L + l) * pl->slot_elems;
+        u.out = pl->d_part + (int64_t)(slot * L + l) * pl->slot_elems;
+        u.out1 = two ? pl->d_part + (int64_t)((slot + 1) * L + l) * pl->slot_elems : nullptr;
         u.map = 0;
         u.i0 = c.i0;
         u.j0 = c.j0;
@@ -256,35 +281,41 @@ rfd_status build_desc(rfd_plan_s* pl) {
         u.kb_total = (int)kb_total;
         u.a_rows = a_rows;
         u.b_rows = m;
+        u.slot = slot;
+        u.skip1 = c.skip1;
         d.units[mode].push_back(u);
       }
-      // reduce tiles: .count holds the compute tile index until a batch assigns lanes
-      RedTile r{};
-      r.M = pl->d_M;
-      r.Y = pl->d_Y;
-      r.oa = pl->d_oa;
-      r.ob = pl->d_ob;
-      r.slot_elems = pl->slot_elems;
-      r.i0 = c.i0;
-      r.ni = c.ni;
-      r.count = t;
-      r.ld = kTcLd;
-      r.m = m;
-      if (c.nj > 0) {
-        r.j0 = c.j0;
-        r.nj = c.nj;
-        r.kind = kTileGram;
-        r.col_off = 0;
-        d.red[mode].push_back(r);
+      // reduce tiles: .count holds the logical tile (slot) index until a batch assigns lanes
+      for (int h = 0; h < (two ? 2 : 1); ++h) {
+        RedTile r{};
+        r.M = pl->d_M;
+        r.Y = pl->d_Y;
+        r.oa = pl->d_oa;
+        r.ob = pl->d_ob;
+        r.slot_elems = pl->slot_elems;
+        r.i0 = c.i0 + h * kTcBM;
+        r.ni = h ? c.ni1 : c.ni;
+        r.count = slot + h;
+        r.ld = kTcLd;
+        r.m = m;
+        const int nj = h ? c.nj1 : c.nj;
+        if (nj > 0) {
+          r.j0 = c.j0 + (h ? c.skip1 : 0);
+          r.nj = nj;
+          r.kind = kTileGram;
+          r.col_off = 0;
+          d.red[mode].push_back(r);
+        }
+        if (c.f) {
+          r.j0 = m;
+          r.nj = pl->cpad;
+          r.fsplit = pl->fsplit ? 1 : 0;
+          r.kind = kTileField;
+          r.col_off = kTcBNMax;
+          d.red[mode].push_back(r);
+        }
       }
-      if (c.f) {
-        r.j0 = m;
-        r.nj = pl->cpad;
-        r.fsplit = pl->fsplit ? 1 : 0;
-        r.kind = kTileField;
-        r.col_off = kTcBNMax;
-        d.red[mode].push_back(r);
-      }
+      slot += two ? 2 : 1;
     }
   }
   auto* psi = static_cast<__nv_bfloat16_raw*>(pl->d_psi);

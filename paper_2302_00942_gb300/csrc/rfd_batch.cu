@@ -90,6 +90,7 @@ struct BatchImpl {
   OzTile* d_oz = nullptr;
   int n_oz = 0;
   int max_m = 0, max_cpad = 16, max_kb = 0;
+  int a_boxes = 1;  // 2 when some Gram unit has a second 128-row half
   int phase_blocks = kGramPhaseBlocks;
   bool phi_batched = true;  // all clouds on the emulated path (no native-FP64 flag)
   // per-call device words
@@ -186,11 +187,13 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
           u.lane = l;
           u.nlanes = L;
           u.map += k * kMapsPerCloud;
-          u.out = pl->d_part + (int64_t)(t * L + l) * pl->slot_elems;
+          u.out = pl->d_part + (int64_t)(u.slot * L + l) * pl->slot_elems;
+          if (u.out1) u.out1 = pl->d_part + (int64_t)((u.slot + 1) * L + l) * pl->slot_elems;
+          if (u.out1) b->a_boxes = 2;
           units[mode].push_back(u);
         }
       for (RedTile r : d.red[mode]) {
-        // red tiles of the plan are per compute tile t (stored in .count as t): remap to lanes
+        // red tiles of the plan are per logical tile (its slot index stored in .count): remap to lanes
         const int t = r.count;
         r.part = pl->d_part + (int64_t)t * L * pl->slot_elems;
         r.count = L;
@@ -515,7 +518,7 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
     }
     {
       StepScope sc(t, s, RFD_STEP_GRAM);
-      BCK(launch_gram_tc(b->d_maps, b->d_units[mode], b->n_units[mode], b->max_cpad, b->max_kb, b->phase_blocks,
+      BCK(launch_gram_tc(b->d_maps, b->d_units[mode], b->n_units[mode], b->a_boxes, b->max_kb, b->phase_blocks,
                          b->d_err, s));
     }
     StepScope sc(t, s, RFD_STEP_REDUCE);
@@ -647,7 +650,7 @@ rfd_status batch_time_gram(BatchImpl* b, int mode, int reps, float* ms) {
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
   auto launch = [&] {
-    return launch_gram_tc(b->d_maps, b->d_units[mode], b->n_units[mode], b->max_cpad, b->max_kb, b->phase_blocks,
+    return launch_gram_tc(b->d_maps, b->d_units[mode], b->n_units[mode], b->a_boxes, b->max_kb, b->phase_blocks,
                           b->d_err, b->st);
   };
   cudaError_t e = launch();  // warm-up
