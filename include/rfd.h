@@ -199,7 +199,7 @@ RFD_API rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double*
  * result) for code in which cudaMalloc/cudaFree are not allowed -- a
  * latency-critical loop where an allocation could synchronise the device, or a
  * process whose device memory is owned by another allocator.  It calls no
- * allocating routine: its workspace is a fixed 3.25 MiB __device__ array that
+ * allocating routine: its workspace is a fixed 3.75 MiB __device__ array that
  * every GPU loading the library holds until the process exits, so it only
  * serves 1 <= m <= 128 (RFD_EINVAL with a message beyond that).  The first call
  * on each device looks up that array's device address (cudaGetSymbolAddress);

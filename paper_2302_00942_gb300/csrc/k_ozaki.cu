@@ -1,43 +1,49 @@
-// FP64-accurate GEMM on the BF16 tensor cores by error-free splitting
-// (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix
-// multiplication by using fast routines of matrix multiplication and its
-// applications", Numer. Algorithms 59 (2012)), used for the m x m products of
-// step a4 (G = lambda phi1(lambda M)): GB300 runs native FP64 at ~1 TFLOP/s,
-// the BF16 tensor cores at ~2 PFLOP/s.
+// FP64-accurate GEMM on the BF16 tensor cores by modular integer arithmetic,
+// the Chinese-remainder form of the Ozaki scheme (Ozaki, Uchino, Imamura,
+// "Ozaki Scheme II: a GEMM-oriented emulation of floating-point matrix
+// multiplication using an integer modular technique", 2025), used for the
+// m x m products of step a4 (G = lambda phi1(lambda M)): GB300 runs native
+// FP64 at ~1 TFLOP/s, the BF16 tensor cores at ~2 PFLOP/s.
 //
-// Splitting.  Row i of A is scaled by 2^-e_i (|A[i,:]| < 2^(e_i - 1)) so that
-// a = A[i,k] 2^-e_i has |a| < 1/2, and the integer X = a 2^56 (exact up to the
-// bits below 2^-56) is written in balanced base 128:
-//     X = sum_{p=1..8} d_p 128^(8-p),   |d_p| <= 64,
-// so A[i,k] = 2^e_i sum_p d_p 2^-7p + O(2^(e_i - 57)) with integers d_p,
-// exact in BF16.  Columns of B are cut the same way (the kernel splits the
-// rows of B^T).
+// Integers.  Row i of A is scaled by a power of two so that its largest entry
+// becomes an integer of k bits (k = 57 for K <= 1024, 56 up to K = 4096, see
+// crt::kbits); every entry becomes the integer X = trunc(A[i,l] 2^-ea_i),
+// |X| < 2^k, exact except for bits below 2^-k of the row's largest entry.
+// Columns of B likewise (exponents eb_j).  The product C' = X Y is then an
+// exact integer with |C'| < K 2^2k <= P / 2, and C = 2^(ea_i + eb_j) C'.
 //
-// Products.  The slice products with p + q <= 9 (36 pairs; the rest lie below
-// 2^-63 of |A||B|) are summed on the tensor cores per digit position
-// t = p + q into one FP32 accumulator each: E_t = sum_{p+q=t} A_p B_q has
-// |E_t| <= (t - 1) 64^2 K' <= 2^24 over K' <= 512 columns of K, so every
-// partial sum is an integer the FP32 accumulation holds exactly.  After every
-// 512 columns of K the eight accumulators are drained into exact int64 sums
-//     T_A = sum_{t=2..5} E_t 2^(7 (5 - t)),   T_B = sum_{t=6..9} E_t 2^(7 (9 - t)),
-// and C[i,j] = 2^(e_i+f_j) (T_A 2^-35 + T_B 2^-63): the only roundings are the
-// two conversions to FP64 and their sum, so the result carries FP64 accuracy
-// relative to |A||B|, for any K.
+// Residues.  For each of 16 pairwise coprime moduli p_j <= 256 (product
+// P ~ 2^125.19) the residues X mod p_j, Y mod p_j in the symmetric range
+// (|r| <= 128) are exact BF16 integers, and the BF16 product of the residue
+// matrices accumulates exactly in FP32: a partial sum over 1024 of K is an
+// integer of magnitude <= 1024 128^2 = 2^24.  Its value mod p_j is C' mod p_j
+// (segments of 1024 of K add their residues mod p_j).
 //
-// Kernel layout: one CTA per 128 x 64 output tile.  Per 64-column chunk of K
-// the 8 slices of the B tile stay resident as one set (64 KB, double-buffered)
-// while the 8 slices of the A tile stream through a 4-deep ring (16 KB each,
-// 128-byte swizzle); A slice p is multiplied with B slices q <= 9 - p, so each
-// slice is read from L2 once per chunk and serves every pair it belongs to.
-// Warp 0 issues the TMA loads, warp 1 the tcgen05.mma into the eight adjacent
-// 64-column TMEM accumulators (A slice p against the concatenated B slices
-// lands on accumulators p..7 at once: 12 wide MMAs per 16 of K), warps 2..9 drain them (two warps per TMEM
-// lane quarter, 32 columns each) into exact integer sums and write the tile
-// through shared memory with coalesced rows.  Waits are bounded (2 s) and
-// record an error code instead of hanging.
+// Reconstruction.  C' = sum_j r_j W_j (mod P) with the constants W_j of
+// crt_math.h, formed in 128-bit integer arithmetic and brought into (-P/2, P/2)
+// by the nearest integer to S / P (an FP32 sum: its error is far inside the
+// margin); the exact C' times 2^(ea_i + eb_j) is rounded once, to nearest
+// even.  So the result carries FP64 accuracy relative to |A| |B| for any K.
+//
+// 16 BF16 products per FP64 product, where digit splitting needs 36 slice
+// products (8 slices of 7 bits, pairs p + q <= 9) and eight TMEM accumulators.
+//
+// Kernel layout.  The residue GEMM: one CTA per (output tile, group of
+// moduli): 128 or 256 rows (two M = 128 halves sharing the B rows) x up to 256
+// columns x G moduli with halves x G x columns <= 512 TMEM columns.  The
+// pipeline walks (64-wide K chunk, modulus) stages -- one or two 16 KB A boxes
+// and N/64 8 KB B boxes, 128-byte swizzle, 3 stages of 64 KB.  Warp 0 issues
+// the TMA loads, warp 1 one tcgen05.mma of 128 x N x 16 per half per 16 of K,
+// warps 2..9 drain the FP32 sums into residues (FP32 floor arithmetic, exact
+// below 2^24) and store them as bytes, planes [16][mp][np].  A second kernel
+// reconstructs each entry and applies D = alpha A B + beta C + diag I.  Waits
+// are bounded (2 s) and record an error code instead of hanging.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cstdint>
+#include <vector>
+#include "crt_math.h"
 #include "kernels.h"
 #include "tc_common.cuh"
 
@@ -46,68 +52,151 @@ namespace rfd {
 namespace {
 
 using namespace tc;
+using crt::kNumMod;
 
-constexpr int kS = 8;             // slices per operand
-constexpr int kBeta = 7;          // bits per slice
-constexpr int kBM = 128, kBN = 64, kBK = 64;
-constexpr int kATile = kBM * kBK * 2;          // 16 KB: one slice of the A tile (128-byte rows)
-constexpr int kBTile = kBN * kBK * 2;          // 8 KB: one slice of the B tile
-constexpr int kBSet = kS * kBTile;             // 64 KB: all slices of the B tile for one K chunk
-constexpr int kBBufs = 2;                      // B sets in flight
-constexpr int kARing = 4;                      // A slices in flight
-constexpr int kPipeBytes = kBBufs * kBSet + kARing * kATile;  // 192 KB
-constexpr int kDrainChunks = 512 / kBK;        // exactness bound of the FP32 accumulation: 512 of K
-constexpr int kThreads = 320;                  // 10 warps
-constexpr int kSmemBytes = kPipeBytes + 1024 + 256;
+constexpr int kBM = 128, kBK = 64, kBNMax = 256, kBBox = 64;
+constexpr int kABytes = kBM * kBK * 2;                                 // 16 KB: 128 rows of 64 K
+constexpr int kBBoxBytes = kBBox * kBK * 2;                            // 8 KB: 64 rows of 64 K
+constexpr int kMaxStages = 8;
+constexpr int kMaxBufs = 8;     // TMEM buffers (512 columns / the width of a unit)
+constexpr int kThreads = 320;  // 10 warps
+constexpr int kEpiWarps = 8;
+constexpr int kSmemLimit = 232448;  // opt-in shared memory per CTA on sm_103
+constexpr int kSmemExtra = 1024 + 512;  // alignment slack + barriers
 constexpr int kMaxK = 4096;
-constexpr int kColSplitK = 256;                // K rows per block of the batched column split
+constexpr int kColSplitK = 64;   // K rows per block of the column split
+constexpr int kRowSeg = 256;     // columns per warp of the row split
+constexpr int kChunksPerSeg = crt::kSegK / kBK;
 
-// Row-wise split of a row-major FP64 matrix X (rows x cols, ld) into kS BF16
-// slices [kS][rows_pad][cols_pad] (zero padded) and per-row exponents.
-//
-// Done on the bit pattern with integer operations (FP64 arithmetic is the
-// slow pipe on this GPU): with E the biased exponent of an entry, Emax the
-// largest in its row and mant its 53-bit significand, e = Emax - 1021 gives
-// |a| = |x| 2^-e < 1/2 and X = a 2^56 = +-(mant << (E - Emax + 2)) (low bits
-// dropped when the shift is negative).  The balanced base-128 digits come
-// from the least significant end: d = ((X + 64) mod 128) - 64, X <- (X - d) / 128,
-// the last quotient being the leading digit (|d_1| <= 64 since |X| < 2^55).
-__device__ __forceinline__ void split_row(const double* __restrict__ X, int ld, int rows, int cols, int rows_pad,
-                                          int cols_pad, __nv_bfloat16* __restrict__ slices, int* __restrict__ exps,
-                                          int i, int lane) {
+const crt::Constants& constants() {
+  static const crt::Constants c = [] {  // once per process (thread-safe initialisation)
+    crt::Constants v{};
+    crt::make_constants(&v);
+    return v;
+  }();
+  return c;
+}
+
+// Residues of 8 consecutive integers X[e] (limbs L[e]) modulo p_j, j = J .. 15,
+// as BF16 integers: plane j gets one 16-byte store at dst + j plane.  A residue
+// is an FP32 integer with at most 8 significant bits, so its BF16 pattern is
+// the upper half of its FP32 pattern.
+__device__ __forceinline__ uint32_t bf16_pair(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+template <int J>
+__device__ __forceinline__ void store_residues8(const crt::Limbs (&L)[8], const long long (&X)[8],
+                                                __nv_bfloat16* dst, size_t plane) {
+  uint4 w;
+  w.x = bf16_pair(crt::residue<J>(L[0], X[0]), crt::residue<J>(L[1], X[1]));
+  w.y = bf16_pair(crt::residue<J>(L[2], X[2]), crt::residue<J>(L[3], X[3]));
+  w.z = bf16_pair(crt::residue<J>(L[4], X[4]), crt::residue<J>(L[5], X[5]));
+  w.w = bf16_pair(crt::residue<J>(L[6], X[6]), crt::residue<J>(L[7], X[7]));
+  *reinterpret_cast<uint4*>(dst + J * plane) = w;
+  if constexpr (J + 1 < kNumMod) store_residues8<J + 1>(L, X, dst, plane);
+}
+
+// Row split of the row-major FP64 matrix X (rows x cols, ld) into the residue
+// planes res [16][rows_pad][cols_pad] (zero padded, cols_pad a multiple of
+// 64) and the row exponents exps (entry = int 2^exps[i]), integer operations
+// only (the FP64 pipe is the slow one on this GPU).  L = 8, 16 or 32 lanes
+// (cols_pad 64, 128, more) take a row, 8 consecutive columns each: a warp covers 32 / L rows, or
+// one 256-column segment of a row (every segment takes the largest exponent
+// over the whole row; segment 0 stores it).  Warp w of row_split_warps().
+__host__ __device__ __forceinline__ int row_split_lanes(int cols_pad) {
+  return cols_pad <= 64 ? 8 : (cols_pad <= 128 ? 16 : 32);  // a power of two (the shuffle reduction)
+}
+__host__ __device__ __forceinline__ int row_split_segs(int cols_pad) { return (cols_pad + kRowSeg - 1) / kRowSeg; }
+__device__ __forceinline__ void split_rows_warp(const double* __restrict__ X, int ld, int rows, int cols,
+                                                int rows_pad, int cols_pad, int sh0,
+                                                __nv_bfloat16* __restrict__ res, int* __restrict__ exps, int w,
+                                                int lane) {
+  const int L = row_split_lanes(cols_pad), segs = row_split_segs(cols_pad);
+  const int i = (w / segs) * (32 / L) + lane / L, seg = w % segs, sub = lane % L;
   int emax = 0;  // largest biased exponent in the row (0: all entries zero or subnormal)
   if (i < rows)
-    for (int k = lane; k < cols; k += 32)
-      emax = max(emax, (int)((__double_as_longlong(X[(size_t)i * ld + k]) >> 52) & 0x7FF));
-  for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+    for (int k = sub; k < cols; k += L) emax = max(emax, (int)((__double_as_longlong(X[(size_t)i * ld + k]) >> 52) & 0x7FF));
+  for (int off = L / 2; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
   if (emax == 0) emax = 1;  // subnormal-only rows: scale as the smallest normal binade
-  if (lane == 0) exps[i] = emax - 1021;  // |X[i, :]| < 2^(emax - 1022) = 2^(e - 1)
-  const size_t plane = (size_t)rows_pad * cols_pad;
-  for (int k = lane; k < cols_pad; k += 32) {
-    long long v = 0;
-    if (i < rows && k < cols) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(X[(size_t)i * ld + k]);
-      const int E = (int)((b >> 52) & 0x7FF);
-      const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
-      const int sh = (E ? E : 1) - emax + 2;
-      const unsigned long long F = (sh >= 0) ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0ull);
-      v = (b >> 63) ? -(long long)F : (long long)F;
-    }
+  if (sub == 0 && seg == 0 && i < rows_pad) exps[i] = emax - 1075 - sh0;
+  const int k0 = seg * kRowSeg + sub * 8;
+  if (i >= rows_pad || k0 >= cols_pad) return;
+  long long v[8];
+  crt::Limbs limbs[8];
 #pragma unroll
-    for (int p = kS; p >= 2; --p) {
-      const long long d = ((v + 64) & 127) - 64;
-      slices[(p - 1) * plane + (size_t)i * cols_pad + k] = __int2bfloat16_rn((int)d);
-      v = (v - d) >> kBeta;
+  for (int e = 0; e < 8; ++e) {
+    const int k = k0 + e;
+    v[e] = 0;
+    if (i < rows && k < cols) v[e] = crt::scaled_int((unsigned long long)__double_as_longlong(X[(size_t)i * ld + k]), emax, sh0);
+    limbs[e] = crt::limbs_of(v[e]);
+  }
+  store_residues8<0>(limbs, v, res + (size_t)i * cols_pad + k0, (size_t)rows_pad * cols_pad);
+}
+__host__ __device__ __forceinline__ int row_split_warps(int rows_pad, int cols_pad) {
+  return rows_pad / (32 / row_split_lanes(cols_pad)) * row_split_segs(cols_pad);
+}
+
+// Largest biased exponents of columns j0 .. j0 + 31 of the row-major FP64
+// matrix B (K x N, ld) over the K rows kr * 64 .. + 63, into
+// part[kr * N_pad + j] (0: all zero or subnormal).  256 threads.
+__device__ __forceinline__ void col_exponents(const double* __restrict__ B, int ld, int K, int N, int N_pad,
+                                              int* __restrict__ part, int j0, int kr) {
+  const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+  __shared__ int red[8][32];
+  int e = 0;
+  if (j0 + tx < N)
+#pragma unroll
+    for (int q = 0; q < kColSplitK / 8; ++q) {
+      const int k = kr * kColSplitK + ty + 8 * q;
+      if (k < K) e = max(e, (int)((__double_as_longlong(B[(size_t)k * ld + j0 + tx]) >> 52) & 0x7FF));
     }
-    slices[(size_t)i * cols_pad + k] = __int2bfloat16_rn((int)v);
+  red[ty][tx] = e;
+  __syncthreads();
+  if (ty == 0) {
+    for (int y = 1; y < 8; ++y) e = max(e, red[y][tx]);
+    part[(size_t)kr * N_pad + j0 + tx] = e;
   }
 }
 
-__global__ void split_rows_kernel(const double* __restrict__ X, int ld, int rows, int cols, int rows_pad,
-                                  int cols_pad, __nv_bfloat16* __restrict__ slices, int* __restrict__ exps) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= rows_pad) return;
-  split_row(X, ld, rows, cols, rows_pad, cols_pad, slices, exps, warp, lane);
+// Columns j0 .. j0 + 31 of the row-major FP64 matrix B (K x N, ld) over the
+// K rows kr * 64 .. + 63 into the residue planes of B^T, res [16][N_pad][K_pad],
+// and the column exponents exps (range 0 stores them), from the per-range
+// exponents part of col_exponents.  The 64 x 32 tile is staged in shared
+// memory; thread t takes column t / 8 and 8 consecutive rows of K, so every
+// plane gets one 16-byte store per thread.  256 threads.
+__device__ __forceinline__ void split_cols(const double* __restrict__ B, int ld, int K, int N, int K_pad, int N_pad,
+                                           int sh0, __nv_bfloat16* __restrict__ res, int* __restrict__ exps,
+                                           const int* __restrict__ part, int j0, int kr) {
+  const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+  __shared__ double tile[kColSplitK][33];
+  __shared__ int emax_s[32];
+  if (ty == 0) {
+    int e = 0;
+    for (int r = 0; r < K_pad / kColSplitK; ++r) e = max(e, part[(size_t)r * N_pad + j0 + tx]);
+    if (e == 0) e = 1;  // subnormal-only columns: scale as the smallest normal binade
+    emax_s[tx] = e;
+    if (kr == 0) exps[j0 + tx] = e - 1075 - sh0;
+  }
+  const size_t plane = (size_t)N_pad * K_pad;
+  const int col = t >> 3, kg = (t & 7) * 8;
+  {
+    const int k0 = kr * kColSplitK;
+    for (int y = ty; y < kColSplitK; y += 8) {
+      const int k = k0 + y, j = j0 + tx;
+      tile[y][tx] = (k < K && j < N) ? B[(size_t)k * ld + j] : 0.0;
+    }
+    __syncthreads();
+    const int emax = emax_s[col];
+    long long v[8];
+    crt::Limbs limbs[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      v[q] = crt::scaled_int((unsigned long long)__double_as_longlong(tile[kg + q][col]), emax, sh0);
+      limbs[q] = crt::limbs_of(v[q]);
+    }
+    store_residues8<0>(limbs, v, res + (size_t)(j0 + col) * K_pad + k0 + kg, plane);
+    __syncthreads();
+  }
 }
 
 __device__ __forceinline__ int find_job(const int* __restrict__ prefix, int count, int b) {
@@ -126,161 +215,172 @@ __device__ __forceinline__ double* pc_slot(const PhiCloud& pc, int slot) {
   return slot == kSlotM ? const_cast<double*>(pc.M) : (slot == kSlotG ? pc.G : pc.work + (size_t)slot * pc.m * pc.m);
 }
 
-// Batched row split of the A operand: one warp per padded row of every cloud
-// (prefix over mpa rows): slot (m x m) -> sa [8][mpa][kp], ea.
-__global__ void bsplit_rows_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
-                                   int slot, int mask_k) {
-  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (wg >= __ldg(prefix + count)) return;
-  const int j = find_job(prefix, count, wg);
-  const PhiCloud pc = pcs[j];
-  if (mask_k >= 0 && pc.s <= mask_k) return;
-  const int i = wg - prefix[j];
-  split_row(pc_slot(pc, slot), pc.m, pc.m, pc.m, pc.mpa, pc.kp, reinterpret_cast<__nv_bfloat16*>(pc.sa), pc.ea, i,
-            lane);
-}
-
-// Batched column split of B = slot (m x m, row-major) straight into the B^T
-// slices sb [8][mpb][kp] and the column exponents eb: one block per strip of
-// 32 columns and range of kColSplitK rows of K (prefix over strips x ranges
-// per cloud).  Each block first takes its columns' largest exponents over the
-// whole column (every range computes the same value; range 0 stores it), then
-// stages 32 x 32 tiles of its K range in shared memory so that the digit
-// planes are written along K (coalesced).  Digits as split_row.
-__global__ void bsplit_cols_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
-                                   int slot, int mask_k) {
-  const int jc = find_job(prefix, count, blockIdx.x);
-  const PhiCloud pc = pcs[jc];
-  if (mask_k >= 0 && pc.s <= mask_k) return;
-  const int m = pc.m;
-  const int nranges = (pc.kp + kColSplitK - 1) / kColSplitK;
-  const int local = blockIdx.x - prefix[jc];
-  const int j0 = (local / nranges) * 32, kr = local % nranges;
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  const double* B = pc_slot(pc, slot);
-  __shared__ double tile[32][33];
-  __shared__ int red[8][32];
-  __shared__ int emax_s[32];
-  int e = 0;
-  if (j0 + tx < m)
-    for (int k = ty; k < m; k += 8) e = max(e, (int)((__double_as_longlong(B[(size_t)k * m + j0 + tx]) >> 52) & 0x7FF));
-  red[ty][tx] = e;
-  __syncthreads();
-  if (ty == 0) {
-    for (int y = 1; y < 8; ++y) e = max(e, red[y][tx]);
-    if (e == 0) e = 1;
-    emax_s[tx] = e;
-    if (kr == 0) pc.eb[j0 + tx] = e - 1021;
-  }
-  __syncthreads();
-  auto* sb = reinterpret_cast<__nv_bfloat16*>(pc.sb);
-  const size_t plane = (size_t)pc.mpb * pc.kp;
-  const int k_end = min(pc.kp, (kr + 1) * kColSplitK);
-  for (int k0 = kr * kColSplitK; k0 < k_end; k0 += 32) {
-    for (int y = ty; y < 32; y += 8) {
-      const int k = k0 + y, j = j0 + tx;
-      tile[y][tx] = (k < m && j < m) ? B[(size_t)k * m + j] : 0.0;
-    }
-    __syncthreads();
-    for (int y = ty; y < 32; y += 8) {  // y: column offset (row of B^T), tx: K offset
-      const int j = j0 + y, k = k0 + tx;
-      const unsigned long long b = (unsigned long long)__double_as_longlong(tile[tx][y]);
-      const int E = (int)((b >> 52) & 0x7FF);
-      const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
-      const int sh = (E ? E : 1) - emax_s[y] + 2;
-      const unsigned long long F = (sh >= 0) ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0ull);
-      long long v = (b >> 63) ? -(long long)F : (long long)F;
-#pragma unroll
-      for (int p = kS; p >= 2; --p) {
-        const long long d = ((v + 64) & 127) - 64;
-        sb[(p - 1) * plane + (size_t)j * pc.kp + k] = __int2bfloat16_rn((int)d);
-        v = (v - d) >> kBeta;
-      }
-      sb[(size_t)j * pc.kp + k] = __int2bfloat16_rn((int)v);
-    }
-    __syncthreads();
-  }
-}
-
-__global__ void transpose_kernel(const double* __restrict__ B, int ldb, int rows, int cols, double* __restrict__ Bt) {
-  __shared__ double tile[32][33];
-  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-    const int r = r0 + y, c = c0 + threadIdx.x;
-    tile[y][threadIdx.x] = (r < rows && c < cols) ? B[(size_t)r * ldb + c] : 0.0;
-  }
-  __syncthreads();
-  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-    const int c = c0 + y, r = r0 + threadIdx.x;
-    if (c < cols && r < rows) Bt[(size_t)c * rows + r] = tile[threadIdx.x][y];
-  }
-}
-
 struct Smem {
-  uint64_t bfull[kBBufs];
-  uint64_t bempty[kBBufs];
-  uint64_t afull[kARing];
-  uint64_t aempty[kARing];
-  uint64_t acc_full;
-  uint64_t acc_empty;
+  uint64_t full[kMaxStages];
+  uint64_t empty[kMaxStages];
+  uint64_t acc_full[kMaxBufs];
+  uint64_t acc_empty[kMaxBufs];
   uint32_t tmem_base;
 };
 
-// Correctly rounded (to nearest, ties to even) double of S 2^E for the exact
-// integer S = TA 2^28 + TB (|TA| < 2^46, |TB| < 2^50), in 64-bit integer
-// arithmetic (the FP64 pipe is the slow one on this GPU).  S 2^(e-63) =
-// T_A 2^(e-35) + T_B 2^(e-63), so this is the same single rounding as summing
-// the two exact FP64 terms.  S = H 2^28 + r with 0 <= r < 2^28; |S| keeps that
-// form with |H| and the complement of r.  Returns false when the result is not
-// a normal double (the caller takes the FP64 route).
-__device__ __forceinline__ bool exact_sum_to_double(long long TA, long long TB, int E, bool flip, double* out) {
-  const long long H = TA + (TB >> 28);
-  unsigned long long r = (unsigned long long)(TB & ((1ll << 28) - 1));
-  unsigned long long Hm;
-  if (H < 0) {
-    if (r) {
-      Hm = (unsigned long long)(-H - 1);
-      r = (1ull << 28) - r;
-    } else {
-      Hm = (unsigned long long)(-H);
+// One CTA of the residue GEMM: rows m0 .. m0 + 128 nh of the A residues
+// against rows n0 .. n0 + nb of the B^T residues for the moduli g0 .. g0 + G - 1
+// in turn, over K_pad; residues of the products into the planes res
+// [16][mp][np] (bytes, in [0, p)).  A unit is one modulus over one segment of
+// at most 1024 of K (the FP32 exactness bound); unit u accumulates in TMEM
+// buffer u mod nbuf (nh nb columns: half h at + h nb), so the epilogue drains
+// one unit while the MMAs of the next run.  Stages (64 of K of one modulus)
+// follow the units in order.
+__device__ __forceinline__ void residue_tile(const CUtensorMap* map_a, const CUtensorMap* map_b,
+                                             const crt::Constants& cc, int K_pad, int m0, int n0, int nb, int nh,
+                                             int g0, int G, uint8_t* __restrict__ res, int mp, int np, int stages,
+                                             int stage_bytes, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw_addr = smem_u32(smem_raw);
+  const uint32_t base = (raw_addr + 1023u) & ~1023u;
+  Smem* sm = reinterpret_cast<Smem*>(smem_raw + (base - raw_addr) + stages * stage_bytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunks = K_pad / kBK;
+  const int nseg = (nchunks + kChunksPerSeg - 1) / kChunksPerSeg;
+  const int units = G * nseg;
+  const int width = nh * nb;                           // TMEM columns of one unit
+  const int nbuf = min(kMaxBufs, (int)(512 / width));  // >= 1
+  const uint32_t b_off = (uint32_t)nh * kABytes;       // B rows after the A box(es) in a stage
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(smem_u32(&sm->full[s]), 1);
+      mbar_init(smem_u32(&sm->empty[s]), 1);
     }
-  } else {
-    Hm = (unsigned long long)H;
+    for (int q = 0; q < nbuf; ++q) {
+      mbar_init(smem_u32(&sm->acc_full[q]), 1);
+      mbar_init(smem_u32(&sm->acc_empty[q]), kEpiWarps);
+    }
+    fence_mbar_init();
   }
-  if (Hm == 0 && r == 0) {
-    *out = 0.0;
-    return true;
-  }
-  const bool neg = (H < 0) != flip;
-  int msb;
-  unsigned long long q;
-  if (Hm == 0) {
-    msb = 63 - __clzll((long long)r);
-    q = r << (52 - msb);
-  } else {
-    const int mh = 63 - __clzll((long long)Hm);
-    msb = mh + 28;
-    if (msb <= 52) {
-      q = ((Hm << 28) | r) << (52 - msb);
-    } else {
-      const int sh = msb - 52;  // 1 .. 27: the dropped bits all lie in r
-      q = (Hm << (28 - sh)) + (r >> sh);
-      const unsigned long long rem = r & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-      if (rem > half || (rem == half && (q & 1ull))) ++q;
-      if (q >> 53) {
-        q >>= 1;
-        ++msb;
+  if (warp == 1) tmem_alloc(smem_u32(&sm->tmem_base), 512);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = sm->tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      const uint32_t tx = (uint32_t)(nh * kBM + nb) * kBK * 2;
+      int i = 0;
+      bool ok = true;
+      for (int u = 0; u < units && ok; ++u) {
+        const int g = g0 + u / nseg, seg = u % nseg;
+        const int c1 = min(nchunks, (seg + 1) * kChunksPerSeg);
+        for (int c = seg * kChunksPerSeg; c < c1; ++c, ++i) {
+          const int s = i % stages;
+          const uint32_t ph = (uint32_t)(i / stages) & 1u;
+          if (!mbar_wait(smem_u32(&sm->empty[s]), ph ^ 1u, err, 11)) {
+            ok = false;
+            break;
+          }
+          const uint32_t full = smem_u32(&sm->full[s]);
+          mbar_arrive_expect_tx(full, tx);
+          const uint32_t sa = base + s * stage_bytes, sb = sa + b_off;
+          tma_load_3d(sa, map_a, c * kBK, m0, g, full);
+          if (nh == 2) tma_load_3d(sa + kABytes, map_a, c * kBK, m0 + kBM, g, full);
+          for (int q = 0; q < nb / kBBox; ++q)
+            tma_load_3d(sb + q * kBBoxBytes, map_b, c * kBK, n0 + q * kBBox, g, full);
+        }
+      }
+      // our copies into the last stages must land before the CTA exits
+      for (int t = (i > stages ? i - stages : 0); t < i; ++t)
+        mbar_wait(smem_u32(&sm->full[t % stages]), (uint32_t)(t / stages) & 1u, err, 12);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      const uint32_t idesc = idesc_bf16(kBM, nb);
+      int i = 0;
+      bool ok = true;
+      for (int u = 0; u < units && ok; ++u) {
+        const int seg = u % nseg, q = u % nbuf;
+        // the buffer's previous unit must have been drained
+        if (u >= nbuf && !mbar_wait(smem_u32(&sm->acc_empty[q]), (uint32_t)(u / nbuf - 1) & 1u, err, 13)) break;
+        const int c0 = seg * kChunksPerSeg, c1 = min(nchunks, c0 + kChunksPerSeg);
+        for (int c = c0; c < c1; ++c, ++i) {
+          const int s = i % stages;
+          const uint32_t ph = (uint32_t)(i / stages) & 1u;
+          if (!mbar_wait(smem_u32(&sm->full[s]), ph, err, 14)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t sa = base + s * stage_bytes, sb = sa + b_off;
+          for (int h = 0; h < nh; ++h) {
+            const uint32_t d = tmem + (uint32_t)(q * width + h * nb);
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk)
+              mma_bf16(d, sdesc_sw128(sa + h * kABytes + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
+                       (c > c0 || kk > 0) ? 1u : 0u);
+          }
+          mma_commit(smem_u32(&sm->empty[s]));  // frees the stage when these MMAs finish
+        }
+        if (ok) mma_commit(smem_u32(&sm->acc_full[q]));  // the unit's sums are complete
       }
     }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue (warps 2..9, two per TMEM lane quarter) ----------------
+    const int quarter = warp & 3, sub = (warp - 2) >> 2;
+    const int per_half = nb / 32, nq = nh * per_half;
+    const size_t plane = (size_t)mp * np;
+    for (int u = 0; u < units; ++u) {
+      const int g = g0 + u / nseg, seg = u % nseg, qb = u % nbuf;
+      if (!mbar_wait(smem_u32(&sm->acc_full[qb]), (uint32_t)(u / nbuf) & 1u, err, 15)) break;
+      fence_after();
+      const float p = cc.p[g], ip = cc.inv_p[g];
+      for (int q = sub; q < nq; q += 2) {
+        const int h = q / per_half, c0 = (q % per_half) * 32;
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(qb * width + h * nb + c0), v);
+        const int row = m0 + h * kBM + quarter * 32 + lane;
+        uint8_t* dst = res + g * plane + (size_t)row * np + n0 + c0;
+        uint32_t old[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (seg > 0) {
+          const uint4 a = reinterpret_cast<const uint4*>(dst)[0], b = reinterpret_cast<const uint4*>(dst)[1];
+          old[0] = a.x; old[1] = a.y; old[2] = a.z; old[3] = a.w;
+          old[4] = b.x; old[5] = b.y; old[6] = b.z; old[7] = b.w;
+        }
+        uint32_t w[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          uint32_t packed = 0;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const float x = v[4 * e + b];  // an exact integer, |x| <= 2^24
+            float r = fmaf(-floorf(x * ip), p, x);  // x - q p, exact; q may be off by one
+            if (r < 0.f) r += p;
+            if (r >= p) r -= p;
+            uint32_t t = (uint32_t)r;
+            if (seg > 0) {
+              t += (old[e] >> (8 * b)) & 0xFFu;
+              if (t >= (uint32_t)p) t -= (uint32_t)p;
+            }
+            packed |= t << (8 * b);
+          }
+          w[e] = packed;
+        }
+        reinterpret_cast<uint4*>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        reinterpret_cast<uint4*>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&sm->acc_empty[qb]));
+    }
   }
-  const int be = msb + E + 1023;
-  if (be < 1 || be > 2046) return false;
-  *out = __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) |
-                                          (q & 0xFFFFFFFFFFFFFull)));
-  return true;
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) tmem_dealloc(tmem, 512);
 }
 
-// alpha = +-2^k: returns true with k and the sign, so the scaling is exact in the exponent.
 __device__ __forceinline__ bool pow2_of(double alpha, int* k, bool* neg) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(alpha);
   const int E = (int)((b >> 52) & 0x7FF);
@@ -290,260 +390,216 @@ __device__ __forceinline__ bool pow2_of(double alpha, int* k, bool* neg) {
   return true;
 }
 
-// One 128 x 64 output tile (m0, n0) of C = alpha A B + beta C from the slice
-// tensor maps (A: rows p M_pad + i, B^T: rows q N_pad + j; K_pad columns).
-// D = alpha A B + beta C + diag I (C may be null when beta == 0; D may equal C).
-__device__ __forceinline__ void ozaki_tile(const CUtensorMap* map_a_p, const CUtensorMap* map_b_p, int M, int N,
-                                           int M_pad, int N_pad, int K_pad, const int* __restrict__ ea,
-                                           const int* __restrict__ eb, double alpha, double beta, const double* C,
-                                           double* D, int ldc, double diag, int m0, int n0, int* err) {
-  extern __shared__ uint8_t smem_raw[];
-  const CUtensorMap& map_a = *map_a_p;
-  const CUtensorMap& map_b = *map_b_p;
-  const uint32_t raw_addr = smem_u32(smem_raw);
-  const uint32_t base = (raw_addr + 1023u) & ~1023u;
-  const uint32_t bbase = base, abase = base + kBBufs * kBSet;
-  Smem* sm = reinterpret_cast<Smem*>(smem_raw + (base - raw_addr) + kPipeBytes);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nkc = K_pad / kBK;
-  const int ndrain = (nkc + kDrainChunks - 1) / kDrainChunks;
-
-  if (threadIdx.x == 0) {
-    for (int b = 0; b < kBBufs; ++b) {
-      mbar_init(smem_u32(&sm->bfull[b]), 1);
-      mbar_init(smem_u32(&sm->bempty[b]), 1);
-    }
-    for (int a = 0; a < kARing; ++a) {
-      mbar_init(smem_u32(&sm->afull[a]), 1);
-      mbar_init(smem_u32(&sm->aempty[a]), 1);
-    }
-    mbar_init(smem_u32(&sm->acc_full), 1);
-    mbar_init(smem_u32(&sm->acc_empty), 8);  // one arrive per epilogue warp
-    fence_mbar_init();
-  }
-  if (warp == 1) tmem_alloc(smem_u32(&sm->tmem_base), 512);
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = sm->tmem_base;
-
-  // Per K chunk: the 8 B slices as one set (double-buffered), then the 8 A
-  // slices one by one through a ring; A slice p meets B slices q <= 7 - p
-  // (0-based), the pairs with p + q <= 9 (1-based).
-  if (warp == 0) {
-    if (lane == 0) {
-      bool ok = true;
-      int issued_b = 0, issued_a = 0;
-      for (int kc = 0; kc < nkc && ok; ++kc) {
-        const int bs = kc % kBBufs;
-        if (!mbar_wait(smem_u32(&sm->bempty[bs]), ((kc / kBBufs) & 1u) ^ 1u, err, 11)) { ok = false; break; }
-        const uint32_t bf = smem_u32(&sm->bfull[bs]);
-        mbar_arrive_expect_tx(bf, kBSet);
-#pragma unroll
-        for (int q = 0; q < kS; ++q) tma_load_2d(bbase + bs * kBSet + q * kBTile, &map_b, kc * kBK, q * N_pad + n0, bf);
-        ++issued_b;
-        for (int p = 0; p < kS; ++p) {
-          const int it = kc * kS + p, as = it % kARing;
-          if (!mbar_wait(smem_u32(&sm->aempty[as]), ((it / kARing) & 1u) ^ 1u, err, 12)) { ok = false; break; }
-          const uint32_t af = smem_u32(&sm->afull[as]);
-          mbar_arrive_expect_tx(af, kATile);
-          tma_load_2d(abase + as * kATile, &map_a, kc * kBK, p * M_pad + m0, af);
-          ++issued_a;
-        }
-      }
-      // wait for the copies still in flight before the CTA may exit
-      for (int u = (issued_b > kBBufs ? issued_b - kBBufs : 0); u < issued_b; ++u)
-        mbar_wait(smem_u32(&sm->bfull[u % kBBufs]), (u / kBBufs) & 1u, err, 16);
-      for (int u = (issued_a > kARing ? issued_a - kARing : 0); u < issued_a; ++u)
-        mbar_wait(smem_u32(&sm->afull[u % kARing]), (u / kARing) & 1u, err, 17);
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      bool ok = true;
-      for (int kc = 0; kc < nkc && ok; ++kc) {
-        const int drain = kc / kDrainChunks, in_drain = kc % kDrainChunks;
-        if (in_drain == 0 && drain > 0) {  // the epilogue must have read the previous sums
-          if (!mbar_wait(smem_u32(&sm->acc_empty), (drain - 1) & 1u, err, 13)) { ok = false; break; }
-          fence_after();
-        }
-        const int bs = kc % kBBufs;
-        if (!mbar_wait(smem_u32(&sm->bfull[bs]), (kc / kBBufs) & 1u, err, 14)) { ok = false; break; }
-        fence_after();
-        const uint32_t sb0 = bbase + bs * kBSet;
-        for (int p = 0; p < kS && ok; ++p) {
-          const int it = kc * kS + p, as = it % kARing;
-          if (!mbar_wait(smem_u32(&sm->afull[as]), (it / kARing) & 1u, err, 18)) { ok = false; break; }
-          fence_after();
-          const uint32_t sa = abase + as * kATile;
-          // A_p times the concatenated slices [B_0 .. B_(7-p)] (rows q*64 + j of the B set): column
-          // block q of the product is pair (p, q), digit position t = p + q, whose accumulator sits at
-          // TMEM columns t*64, so the whole product lands at columns p*64 .. 511 -- one or two wide
-          // MMAs (N <= 256) instead of 8 - p narrow ones.
-          const int ncols = (kS - p) * kBN;
-#pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk) {
-            const uint32_t acc = (in_drain > 0 || p > 0 || kk > 0) ? 1u : 0u;
-            for (int c0 = 0; c0 < ncols; c0 += 256) {
-              const int nc = min(256, ncols - c0);
-              mma_bf16(tmem + (uint32_t)(p * kBN + c0), sdesc_sw128(sa + kk * 32),
-                       sdesc_sw128(sb0 + (c0 / kBN) * kBTile + kk * 32), idesc_bf16(kBM, nc), acc);
-            }
-          }
-          mma_commit(smem_u32(&sm->aempty[as]));
-        }
-        if (!ok) break;
-        mma_commit(smem_u32(&sm->bempty[bs]));
-        if (in_drain == kDrainChunks - 1 || kc == nkc - 1) mma_commit(smem_u32(&sm->acc_full));
-      }
-    }
-    __syncwarp();
+// alpha (A B)[i, j] from the residues r and the exponent e = ea_i + eb_j:
+// correctly rounded when alpha is a power of two and the result is a normal
+// double.
+__device__ __forceinline__ double product_entry(const crt::Constants& cc, const uint32_t (&r)[kNumMod], int e,
+                                                double alpha) {
+  unsigned long long lo, hi;
+  crt::reconstruct(r, cc, &lo, &hi);
+  int ak = 0;
+  bool aneg = false;
+  double v;
+  if (pow2_of(alpha, &ak, &aneg)) {
+    if (!crt::to_double(lo, hi, e + ak, aneg, &v)) v = alpha * crt::to_double_plain(lo, hi, e);
   } else {
-    // epilogue: two warps per TMEM lane quarter, 32 columns each
-    const int quarter = warp & 3;
-    const int half = (warp - 2) >> 2;
-    const int row = quarter * 32 + lane;
-    const int col0 = half * 32;
-    const int gi = m0 + row;
-    double* tile = reinterpret_cast<double*>(smem_raw + (base - raw_addr));  // kBM rows x (kBN + 1)
-    const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
-    int ak = 0;
-    bool aneg = false;
-    const bool ap2 = pow2_of(alpha, &ak, &aneg);
-    const int eri = ea[gi < M_pad ? gi : 0];
-    // alpha 2^e (T_A 2^-35 + T_B 2^-63), correctly rounded, into the shared-memory tile
-    auto emit = [&](int c, long long ta, long long tb) {
-      const int e = eri + eb[n0 + col0 + c];
-      double v;
-      if (!(ap2 && exact_sum_to_double(ta, tb, e - 63 + ak, aneg, &v)))
-        v = alpha * (ldexp((double)ta, e - 35) + ldexp((double)tb, e - 63));
-      tile[row * (kBN + 1) + col0 + c] = v;
-    };
-    bool ok = true;
-    if (ndrain == 1) {
-      // one drain (K <= 512): 8 columns at a time, the eight digit positions loaded under one wait
-      ok = mbar_wait(smem_u32(&sm->acc_full), 0u, err, 15);
-      if (ok) {
-        fence_after();
-#pragma unroll 1
-        for (int g = 0; g < 32; g += 8) {
-          uint32_t r[8][8];
-#pragma unroll
-          for (int t = 0; t < kS; ++t) tmem_ld8_nowait(taddr + (uint32_t)(t * kBN + g), r[t]);
-          tmem_wait_ld();
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            long long ta = 0, tb = 0;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) ta += (long long)__float2int_rn(__uint_as_float(r[t][c])) << (kBeta * (3 - t));
-#pragma unroll
-            for (int t = 4; t < kS; ++t) tb += (long long)__float2int_rn(__uint_as_float(r[t][c])) << (kBeta * (7 - t));
-            emit(g + c, ta, tb);
-          }
-        }
-      }
-    } else {
-      long long TA[32], TB[32];
-#pragma unroll
-      for (int c = 0; c < 32; ++c) { TA[c] = 0; TB[c] = 0; }
-      for (int d = 0; d < ndrain && ok; ++d) {
-        if (!mbar_wait(smem_u32(&sm->acc_full), d & 1u, err, 15)) { ok = false; break; }
-        fence_after();
-#pragma unroll 1
-        for (int t = 2; t <= kS + 1; ++t) {
-          float v[32];
-          tmem_ld32(taddr + (uint32_t)((t - 2) * kBN), v);
-          const int sh = (t <= 5) ? kBeta * (5 - t) : kBeta * (kS + 1 - t);
-          if (t <= 5) {
-#pragma unroll
-            for (int c = 0; c < 32; ++c) TA[c] += (long long)__float2int_rn(v[c]) << sh;
-          } else {
-#pragma unroll
-            for (int c = 0; c < 32; ++c) TB[c] += (long long)__float2int_rn(v[c]) << sh;
-          }
-        }
-        fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&sm->acc_empty));
-      }
-      if (ok) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) emit(c, TA[c], TB[c]);
-      }
-    }
-    asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 epilogue warps
-    // ... then out with coalesced rows: D = tile + beta C (+ diag on the diagonal)
-    if (ok) {
-      const int ew = warp - 2;
-      for (int r = ew; r < kBM; r += 8) {
-        const int i = m0 + r;
-        if (i >= M) break;
-        for (int jj = lane; jj < kBN; jj += 32) {
-          const int j = n0 + jj;
-          if (j >= N) continue;
-          double v = tile[r * (kBN + 1) + jj];
-          if (beta != 0.0) v = fma(beta, C[(size_t)i * ldc + j], v);
-          if (i == j) v += diag;
-          D[(size_t)i * ldc + j] = v;
-        }
-      }
-    }
+    if (!crt::to_double(lo, hi, e, false, &v)) v = crt::to_double_plain(lo, hi, e);
+    v *= alpha;
   }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  if (warp == 1) tmem_dealloc(tmem, 512);
+  return v;
+}
+
+// D[i, j0 .. j0 + 3] (columns < ncols) = alpha (A B) + beta C + diag I from
+// the residue planes (one 4-byte load per plane; res_row = row i of plane 0).
+__device__ __forceinline__ void combine4(const crt::Constants& cc, const uint8_t* __restrict__ res_row, size_t plane,
+                                         int i, int j0, int ncols, int ea_i, const int* __restrict__ eb,
+                                         double alpha, double beta, const double* C, double* D, double diag) {
+  uint32_t w[kNumMod];
+#pragma unroll
+  for (int j = 0; j < kNumMod; ++j) w[j] = __ldg(reinterpret_cast<const uint32_t*>(res_row + j * plane + j0));
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int jj = j0 + q;
+    if (jj >= ncols) break;
+    uint32_t r[kNumMod];
+#pragma unroll
+    for (int j = 0; j < kNumMod; ++j) r[j] = (w[j] >> (8 * q)) & 0xFFu;
+    double v = product_entry(cc, r, ea_i + eb[jj], alpha);
+    if (beta != 0.0) v = fma(beta, C[jj], v);
+    if (i == jj) v += diag;
+    D[jj] = v;
+  }
+}
+
+// ---- batched kernels (one table entry per cloud, slots resolved per call) ----
+
+// Row split of the A operand, every cloud (warp prefix over ozaki_row_split_warps(m)).
+__global__ void bsplit_rows_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
+                                   int slot, int mask_k) {
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (wg >= __ldg(prefix + count)) return;
+  const int j = find_job(prefix, count, wg);
+  const PhiCloud pc = pcs[j];
+  if (mask_k >= 0 && pc.s <= mask_k) return;
+  split_rows_warp(pc_slot(pc, slot), pc.m, pc.m, pc.m, pc.mpa, pc.kp, pc.kbits - 53,
+                  reinterpret_cast<__nv_bfloat16*>(pc.sa), pc.ea, wg - prefix[j], lane);
+}
+
+// Column exponents and column split of the B operand: one block per strip of
+// 32 columns and range of 64 rows of K (prefix over strips x ranges per cloud).
+__global__ void bcol_exponents_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
+                                      int slot, int mask_k) {
+  const int jc = find_job(prefix, count, blockIdx.x);
+  const PhiCloud pc = pcs[jc];
+  if (mask_k >= 0 && pc.s <= mask_k) return;
+  const int nranges = pc.kp / kColSplitK, local = blockIdx.x - prefix[jc];
+  col_exponents(pc_slot(pc, slot), pc.m, pc.m, pc.m, pc.mpb, pc.ebp, (local / nranges) * 32, local % nranges);
+}
+__global__ void bsplit_cols_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
+                                   int slot, int mask_k) {
+  const int jc = find_job(prefix, count, blockIdx.x);
+  const PhiCloud pc = pcs[jc];
+  if (mask_k >= 0 && pc.s <= mask_k) return;
+  const int nranges = pc.kp / kColSplitK, local = blockIdx.x - prefix[jc];
+  split_cols(pc_slot(pc, slot), pc.m, pc.m, pc.m, pc.kp, pc.mpb, pc.kbits - 53,
+             reinterpret_cast<__nv_bfloat16*>(pc.sb), pc.eb, pc.ebp, (local / nranges) * 32, local % nranges);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-ozaki_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int M,
-                  int N, int M_pad, int N_pad, int K_pad, const int* __restrict__ ea, const int* __restrict__ eb,
-                  double alpha, double beta, double* C, int ldc, int* err) {
-  ozaki_tile(&map_a, &map_b, M, N, M_pad, N_pad, K_pad, ea, eb, alpha, beta, C, C, ldc, 0.0, blockIdx.y * kBM,
-             blockIdx.x * kBN, err);
-}
-
-// Batched: one CTA per OzTile of any cloud; D = alpha A B + beta C + diag I on
-// the cloud's slots (c_slot kNoSlot: no C).  A cloud with s <= mask_k skips
-// the product: its tile of D becomes a copy of C (if any).
-__global__ void __launch_bounds__(kThreads, 1)
-ozaki_gemm_batched_kernel(const CUtensorMap* __restrict__ maps, const OzTile* __restrict__ tiles,
-                          const PhiCloud* __restrict__ pcs, int c_slot, int d_slot, double alpha, double beta,
-                          double diag, int mask_k, int* err) {
+bresidue_gemm_kernel(const CUtensorMap* __restrict__ maps, const OzTile* __restrict__ tiles,
+                     const PhiCloud* __restrict__ pcs, const __grid_constant__ crt::Constants cc, int stages,
+                     int stage_bytes, int mask_k, int* err) {
   const OzTile t = tiles[blockIdx.x];
   const PhiCloud pc = pcs[t.cloud];
-  const double* C = (c_slot == kNoSlot) ? nullptr : pc_slot(pc, c_slot);
-  double* D = pc_slot(pc, d_slot);
+  if (mask_k >= 0 && pc.s <= mask_k) return;
+  residue_tile(maps + pc.map_a, maps + pc.map_b, cc, pc.kp, t.m0, t.n0, t.nb, t.nh, t.g0, t.ng, pc.res, pc.mpa,
+               pc.mpb, stages, stage_bytes, err);
+}
+
+// D = alpha A B + beta C + diag I, one thread per 4 consecutive entries of a
+// row (prefix over blocks of 256 such groups per cloud, m ceil(m / 4) groups).
+// A cloud with s <= mask_k skipped the product: its D becomes a copy of C (if
+// any).
+__global__ void bcombine_product_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
+                                        const __grid_constant__ crt::Constants cc, int c_slot, int d_slot,
+                                        double alpha, double beta, double diag, int mask_k) {
+  const int jc = find_job(prefix, count, blockIdx.x);
+  const PhiCloud pc = pcs[jc];
+  const int m = pc.m, gpr = (m + 3) / 4;
+  const int64_t g = (int64_t)(blockIdx.x - prefix[jc]) * blockDim.x + threadIdx.x;
+  if (g >= (int64_t)m * gpr) return;
+  const int i = (int)(g / gpr), j0 = (int)(g % gpr) * 4;
+  const double* C = (c_slot == kNoSlot) ? nullptr : pc_slot(pc, c_slot) + (size_t)i * m;
+  double* D = pc_slot(pc, d_slot) + (size_t)i * m;
   if (mask_k >= 0 && pc.s <= mask_k) {
     if (C && C != D)
-      for (int e = threadIdx.x; e < kBM * kBN; e += blockDim.x) {
-        const int i = t.m0 + e / kBN, j = t.n0 + e % kBN;
-        if (i < pc.m && j < pc.m) D[(size_t)i * pc.m + j] = C[(size_t)i * pc.m + j];
-      }
+      for (int j = j0; j < min(m, j0 + 4); ++j) D[j] = C[j];
     return;
   }
-  ozaki_tile(maps + pc.map_a, maps + pc.map_b, pc.m, pc.m, pc.mpa, pc.mpb, pc.kp, pc.ea, pc.eb, alpha, beta, C, D,
-             pc.m, diag, t.m0, t.n0, err);
+  combine4(cc, pc.res + (size_t)i * pc.mpb, (size_t)pc.mpa * pc.mpb, i, j0, m, pc.ea[i], pc.eb, alpha, beta, C, D,
+           diag);
+}
+
+// ---- single product (general M, N, K) ----
+
+__global__ void split_rows_kernel(const double* __restrict__ X, int ld, int rows, int cols, int rows_pad,
+                                  int cols_pad, int sh0, __nv_bfloat16* __restrict__ res, int* __restrict__ exps) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= row_split_warps(rows_pad, cols_pad)) return;
+  split_rows_warp(X, ld, rows, cols, rows_pad, cols_pad, sh0, res, exps, warp, lane);
+}
+
+__global__ void col_exponents_kernel(const double* __restrict__ B, int ld, int K, int N, int N_pad,
+                                     int* __restrict__ part) {
+  col_exponents(B, ld, K, N, N_pad, part, blockIdx.x * 32, blockIdx.y);
+}
+__global__ void split_cols_kernel(const double* __restrict__ B, int ld, int K, int N, int K_pad, int N_pad, int sh0,
+                                  __nv_bfloat16* __restrict__ res, int* __restrict__ exps, const int* __restrict__ part) {
+  split_cols(B, ld, K, N, K_pad, N_pad, sh0, res, exps, part, blockIdx.x * 32, blockIdx.y);
+}
+
+// grid (column tiles of 256, row tiles of 256, 16 moduli); stages of 64 KB
+__global__ void __launch_bounds__(kThreads, 1)
+residue_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                    const __grid_constant__ crt::Constants cc, int K_pad, int mp, int np, uint8_t* res, int stages,
+                    int* err) {
+  const int n0 = blockIdx.x * kBNMax, m0 = blockIdx.y * 2 * kBM;
+  residue_tile(&map_a, &map_b, cc, K_pad, m0, n0, min(kBNMax, np - n0), (m0 + kBM < mp) ? 2 : 1, blockIdx.z, 1, res,
+               mp, np, stages, 2 * kABytes + kBNMax * kBK * 2, err);
+}
+
+__global__ void combine_product_kernel(const __grid_constant__ crt::Constants cc, const uint8_t* __restrict__ res,
+                                       const int* __restrict__ ea, const int* __restrict__ eb, int M, int N, int mp,
+                                       int np, double alpha, double beta, double* C, int ldc) {
+  const int gpr = (N + 3) / 4;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (int64_t)M * gpr) return;
+  const int i = (int)(g / gpr), j0 = (int)(g % gpr) * 4;
+  double* Ci = C + (size_t)i * ldc;
+  combine4(cc, res + (size_t)i * np, (size_t)mp * np, i, j0, N, ea[i], eb, alpha, beta, Ci, Ci, 0.0);
 }
 
 }  // namespace
 
 bool make_ozaki_maps(void* map_a_host, void* map_b_host, const void* sa, const void* sb, int mpa, int mpb, int kp) {
-  return tc::make_map_bf16(static_cast<CUtensorMap*>(map_a_host), sa, (uint64_t)kp, (uint64_t)kS * mpa, (uint64_t)kp,
-                           kBM) &&
-         tc::make_map_bf16(static_cast<CUtensorMap*>(map_b_host), sb, (uint64_t)kp, (uint64_t)kS * mpb, (uint64_t)kp,
-                           kBN);
+  return tc::make_map_bf16_3d(static_cast<CUtensorMap*>(map_a_host), sa, (uint64_t)kp, (uint64_t)mpa, kNumMod, kBM) &&
+         tc::make_map_bf16_3d(static_cast<CUtensorMap*>(map_b_host), sb, (uint64_t)kp, (uint64_t)mpb, kNumMod,
+                              kBBox);
 }
 
 cudaError_t bgemm_prepare() {
-  static const cudaError_t attr =  // once per process (thread-safe initialisation)
-      cudaFuncSetAttribute(ozaki_gemm_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  static const cudaError_t attr = [] {  // once per process (thread-safe initialisation)
+    constants();
+    cudaError_t e = cudaFuncSetAttribute(bresidue_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(residue_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    return e;
+  }();
   return attr;
 }
 
+// stages of stage_bytes that fit the shared memory (2 .. kMaxStages), 0 if none
+int stages_for(int stage_bytes) {
+  const int s = (kSmemLimit - kSmemExtra) / stage_bytes;
+  return s < 2 ? 0 : (s > kMaxStages ? kMaxStages : s);
+}
+
+void ozaki_batch_tiles(const std::vector<int>& ms, int sms, std::vector<OzTile>* out, int* stage_bytes) {
+  out->clear();
+  // tiles of one modulus first (half pairs for m >= 512, where the B reuse pays)
+  std::vector<OzTile> base;
+  for (int k = 0; k < (int)ms.size(); ++k) {
+    const OzLayout L = ozaki_layout(ms[k], ms[k], ms[k]);
+    const bool pairs = ms[k] >= 512;
+    for (int m0 = 0; m0 < L.mp; m0 += (pairs ? 2 : 1) * kBM) {
+      const int nh = (pairs && m0 + kBM < L.mp) ? 2 : 1;
+      for (int n0 = 0; n0 < L.np; n0 += kBNMax) base.push_back(OzTile{k, m0, n0, std::min(kBNMax, L.np - n0), nh, 0, 1, 0});
+    }
+  }
+  // moduli per CTA: the largest power of two <= 16 that leaves two CTAs per SM
+  int G = kNumMod;
+  while (G > 1 && (int64_t)base.size() * (kNumMod / G) < 2 * (int64_t)sms) G /= 2;
+  int nh_max = 1, nb_max = kBBox;
+  for (const OzTile& t : base) {
+    nh_max = std::max(nh_max, t.nh);
+    nb_max = std::max(nb_max, t.nb);
+    for (int g0 = 0; g0 < kNumMod; g0 += G) {
+      OzTile u = t;
+      u.g0 = g0;
+      u.ng = G;
+      out->push_back(u);
+    }
+  }
+  *stage_bytes = nh_max * kABytes + nb_max * kBK * 2;
+}
+
+int ozaki_kbits(int K) { return crt::kbits(K); }
+
 cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* strip_prefix,
-                         int col_strips, const OzTile* tiles, int num_tiles, const void* maps_dev, int a_slot,
-                         int b_slot, int c_slot, int d_slot, double alpha, double beta, double diag, int mask_k,
-                         bool split_a, bool split_b, int* err, cudaStream_t st) {
+                         int col_strips, const OzTile* tiles, int num_tiles, int stage_bytes, const int* group_prefix,
+                         int group_blocks,
+                         const void* maps_dev, int a_slot, int b_slot, int c_slot, int d_slot, double alpha,
+                         double beta, double diag, int mask_k, bool split_a, bool split_b, int* err, cudaStream_t st) {
   const cudaError_t attr = bgemm_prepare();
   if (attr != cudaSuccess) return attr;
   if (split_a) {
@@ -551,13 +607,25 @@ cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a,
     count_launch();
   }
   if (split_b) {
-    bsplit_cols_kernel<<<col_strips, dim3(32, 8), 0, st>>>(pc, strip_prefix, count, b_slot, mask_k);
-    count_launch();
+    bcol_exponents_kernel<<<col_strips, 256, 0, st>>>(pc, strip_prefix, count, b_slot, mask_k);
+    bsplit_cols_kernel<<<col_strips, 256, 0, st>>>(pc, strip_prefix, count, b_slot, mask_k);
+    count_launch(2);
   }
-  ozaki_gemm_batched_kernel<<<num_tiles, kThreads, kSmemBytes, st>>>(static_cast<const CUtensorMap*>(maps_dev), tiles,
-                                                                     pc, c_slot, d_slot, alpha, beta, diag, mask_k,
-                                                                     err);
+  const int stages = stages_for(stage_bytes);
+  if (stages == 0) return cudaErrorInvalidValue;
+  bresidue_gemm_kernel<<<num_tiles, kThreads, stages * stage_bytes + kSmemExtra, st>>>(
+      static_cast<const CUtensorMap*>(maps_dev), tiles, pc, constants(), stages, stage_bytes, mask_k, err);
+  count_launch();
+  bcombine_product_kernel<<<group_blocks, 256, 0, st>>>(pc, group_prefix, count, constants(), c_slot, d_slot, alpha,
+                                                        beta, diag, mask_k);
   return launched();
+}
+
+int ozaki_combine_blocks(int m) { return (int)(((int64_t)m * ((m + 3) / 4) + 255) / 256); }
+
+int ozaki_row_split_warps(int m) {
+  const OzLayout L = ozaki_layout(m, m, m);
+  return row_split_warps(L.mp, L.kp);
 }
 
 int ozaki_col_split_blocks(int m) {
@@ -568,15 +636,16 @@ int ozaki_col_split_blocks(int m) {
 OzLayout ozaki_layout(int M, int N, int K) {
   OzLayout L{};
   L.mp = (M + kBM - 1) / kBM * kBM;
-  L.np = (N + kBN - 1) / kBN * kBN;
+  L.np = (N + kBBox - 1) / kBBox * kBBox;
   L.kp = (K + kBK - 1) / kBK * kBK;
   auto a256 = [](size_t x) { return (x + 255) & ~size_t(255); };
   L.sa = 0;
-  L.sb = a256(L.sa + (size_t)kS * L.mp * L.kp * 2);
-  L.ea = a256(L.sb + (size_t)kS * L.np * L.kp * 2);
+  L.sb = a256(L.sa + (size_t)kNumMod * L.mp * L.kp * 2);
+  L.ea = a256(L.sb + (size_t)kNumMod * L.np * L.kp * 2);
   L.eb = a256(L.ea + (size_t)L.mp * 4);
-  L.bt = a256(L.eb + (size_t)L.np * 4);
-  L.bytes = a256(L.bt + (size_t)N * K * 8);
+  L.ebp = a256(L.eb + (size_t)L.np * 4);
+  L.res = a256(L.ebp + (size_t)(L.kp / kColSplitK) * L.np * 4);
+  L.bytes = a256(L.res + (size_t)kNumMod * L.mp * L.np);
   return L;
 }
 
@@ -588,26 +657,31 @@ cudaError_t dgemm_ozaki(int M, int N, int K, double alpha, const double* A, int 
                         double beta, double* C, int ldc, void* work, int* err, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (K < 1 || K > kMaxK) return cudaErrorInvalidValue;
+  const cudaError_t attr = bgemm_prepare();
+  if (attr != cudaSuccess) return attr;
   const OzLayout L = ozaki_layout(M, N, K);
-  const int mp = L.mp, np = L.np, kp = L.kp;
+  const int mp = L.mp, np = L.np, kp = L.kp, sh0 = crt::kbits(K) - 53;
   uint8_t* w = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(work) + 255) & ~uintptr_t(255));
   auto* sa = reinterpret_cast<__nv_bfloat16*>(w + L.sa);
   auto* sb = reinterpret_cast<__nv_bfloat16*>(w + L.sb);
   int* ea = reinterpret_cast<int*>(w + L.ea);
   int* eb = reinterpret_cast<int*>(w + L.eb);
-  double* bt = reinterpret_cast<double*>(w + L.bt);
-  split_rows_kernel<<<(mp * 32 + 255) / 256, 256, 0, st>>>(A, lda, M, K, mp, kp, sa, ea);
-  transpose_kernel<<<dim3((N + 31) / 32, (K + 31) / 32), dim3(32, 8), 0, st>>>(B, ldb, K, N, bt);
-  split_rows_kernel<<<(np * 32 + 255) / 256, 256, 0, st>>>(bt, K, N, K, np, kp, sb, eb);
+  int* ebp = reinterpret_cast<int*>(w + L.ebp);
+  uint8_t* res = w + L.res;
+  split_rows_kernel<<<(row_split_warps(mp, kp) * 32 + 255) / 256, 256, 0, st>>>(A, lda, M, K, mp, kp, sh0, sa, ea);
+  const dim3 strips(np / 32, kp / kColSplitK);
+  col_exponents_kernel<<<strips, 256, 0, st>>>(B, ldb, K, N, np, ebp);
+  split_cols_kernel<<<strips, 256, 0, st>>>(B, ldb, K, N, kp, np, sh0, sb, eb, ebp);
   count_launch(3);
   CUtensorMap ma, mb;
-  if (!tc::make_map_bf16(&ma, sa, (uint64_t)kp, (uint64_t)kS * mp, (uint64_t)kp, kBM)) return cudaErrorInvalidValue;
-  if (!tc::make_map_bf16(&mb, sb, (uint64_t)kp, (uint64_t)kS * np, (uint64_t)kp, kBN)) return cudaErrorInvalidValue;
-  static const cudaError_t attr =  // once per process (thread-safe initialisation)
-      cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-  if (attr != cudaSuccess) return attr;
-  ozaki_gemm_kernel<<<dim3(np / kBN, mp / kBM), kThreads, kSmemBytes, st>>>(ma, mb, M, N, mp, np, kp, ea, eb, alpha,
-                                                                           beta, C, ldc, err);
+  if (!make_ozaki_maps(&ma, &mb, sa, sb, mp, np, kp)) return cudaErrorInvalidValue;
+  residue_gemm_kernel<<<dim3((np + kBNMax - 1) / kBNMax, (mp + 2 * kBM - 1) / (2 * kBM), kNumMod), kThreads,
+                        3 * (2 * kABytes + kBNMax * kBK * 2) + kSmemExtra, st>>>(ma, mb, constants(), kp, mp, np, res, 3,
+                                                                                  err);
+  count_launch();
+  const int64_t groups = (int64_t)M * ((N + 3) / 4);
+  combine_product_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(constants(), res, ea, eb, M, N, mp, np,
+                                                                           alpha, beta, C, ldc);
   return launched();
 }
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cuda_bf16.h>
+#include <vector>
 
 namespace rfd {
 
@@ -122,18 +123,23 @@ cudaError_t dcombine(int m, int n, double* D, int ldd, double a0, const double* 
                      double diag, int ldx, cudaStream_t st);
 cudaError_t dnorm1(int m, const double* X, int ldx, double* out, cudaStream_t st);  // max column abs-sum
 cudaError_t dfinite_check(int m, int n, const double* X, int ldx, int* flag, cudaStream_t st);
-// FP64-accurate C = alpha A B + beta C on the BF16 tensor cores (Ozaki
-// splitting, k_ozaki.cu); K <= 1024.  `work` holds ozaki_workspace_bytes(M, N, K).
+// FP64-accurate C = alpha A B + beta C on the BF16 tensor cores (the modular
+// form of the Ozaki scheme, k_ozaki.cu); K <= 4096.  `work` holds
+// ozaki_workspace_bytes(M, N, K).
 // Workspace layout of the emulated FP64 GEMM (byte offsets from a 256-byte
-// aligned base): A slices [8][mp][kp] and B^T slices [8][np][kp] (BF16),
-// exponents, B^T scratch.  The single source of the padded sizes.
+// aligned base): A residues [16][mp][kp] and B^T residues [16][np][kp] (BF16),
+// exponents, residues of the product [16][mp][np] (bytes).  The single source
+// of the padded sizes.
 struct OzLayout {
   int mp, np, kp;
-  size_t sa, sb, ea, eb, bt, bytes;
+  size_t sa, sb, ea, eb, ebp, res, bytes;  // ebp: per-64-row column exponents [kp / 64][np]
 };
 OzLayout ozaki_layout(int M, int N, int K);
 size_t ozaki_workspace_bytes(int M, int N, int K);  // layout bytes + alignment slack
 int ozaki_col_split_blocks(int m);  // blocks of the batched column split of an m x m operand
+int ozaki_combine_blocks(int m);    // blocks of the batched reconstruction of an m x m product
+int ozaki_row_split_warps(int m);   // warps of the batched row split of an m x m operand
+int ozaki_kbits(int K);             // bits of the scaled integers for contractions of length K
 bool ozaki_supported(int K);
 cudaError_t dgemm_ozaki(int M, int N, int K, double alpha, const double* A, int lda, const double* B, int ldb,
                         double beta, double* C, int ldc, void* work, int* err, cudaStream_t st);
@@ -211,19 +217,29 @@ struct PhiCloud {
   double* work;
   const double* M;
   double* G;
-  __nv_bfloat16_raw* sa;  // A-operand slices [8][mpa][kp]
-  __nv_bfloat16_raw* sb;  // B-operand slices [8][mpb][kp]
+  __nv_bfloat16_raw* sa;  // A-operand residues [16][mpa][kp]
+  __nv_bfloat16_raw* sb;  // B^T-operand residues [16][mpb][kp]
   int* ea;                // row exponents of A (mpa)
   int* eb;                // column exponents of B (mpb)
+  int* ebp;               // column exponents of B per 64 rows of K ([kp / 64][mpb])
+  uint8_t* res;           // residues of the product [16][mpa][mpb]
   int* flag;              // finiteness flag
   double lambda, scale;   // scale = 2^-s (set per call)
   int32_t m, mpa, mpb, kp;
   int32_t map_a, map_b;   // tensor maps of sa / sb
-  int32_t s, pad_;        // squarings (set per call)
+  int32_t s, kbits;       // squarings (set per call); bits of the scaled integers (ozaki_kbits(m))
 };
+// One CTA of the residue GEMM: rows m0 .. m0 + 128 nh, columns n0 .. n0 + nb,
+// moduli g0 .. g0 + ng - 1 (in turn) of one cloud's product.
 struct OzTile {
-  int32_t cloud, m0, n0, pad_;
+  int32_t cloud, m0, n0, nb, nh, g0, ng, pad_;
 };
+// The residue-GEMM CTAs of a batch of m x m products (cloud k of size ms[k]):
+// 256-row tiles (two 128-row halves sharing the B rows) for m >= 512, 128-row
+// tiles below, up to 256 columns; each CTA takes G moduli in turn, G the
+// largest power of two <= 16 that leaves two CTAs per SM.  *stage_bytes: the
+// pipeline stage size of the launch.
+void ozaki_batch_tiles(const std::vector<int>& ms, int sms, std::vector<OzTile>* out, int* stage_bytes);
 
 cudaError_t launch_features_batched(const FeatJob* jobs, const int* prefix, int count, int total_blocks,
                                     const CloudCall* calls, cudaStream_t st);
@@ -250,19 +266,22 @@ cudaError_t launch_bselect(PhiCloud* pc, int count, const double* norms, double 
 cudaError_t launch_bfinite(const PhiCloud* pc, const int* prefix, int count, int total_blocks, int slot,
                            cudaStream_t st);
 // D = alpha A B + beta C + diag I on every cloud (emulated FP64): row split of
-// A (warp-row prefix over mpa rows), column split of B (prefix over
-// ozaki_col_split_blocks(m) per cloud) and the tensor-core products.  c_slot
-// kNoSlot: no C.  Clouds with s <= mask_k (mask_k >= 0) skip the product and
-// copy C to D.  split_a / split_b false: the slices already hold that operand
-// (split by the previous product over the same or a larger set of clouds).
+// A (warp prefix over ozaki_row_split_warps(m) per cloud), column split of B (prefix over
+// ozaki_col_split_blocks(m) per cloud), the residue GEMM over the tiles and the
+// reconstruction (prefix over ozaki_combine_blocks(m) per cloud).
+// c_slot kNoSlot: no C.  Clouds with s <= mask_k (mask_k >= 0) skip the
+// product and copy C to D.  split_a / split_b false: the residues already hold
+// that operand (split by the previous product over the same or a larger set of
+// clouds).
 cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* strip_prefix,
-                         int col_strips, const OzTile* tiles, int num_tiles, const void* maps_dev, int a_slot,
-                         int b_slot, int c_slot, int d_slot, double alpha, double beta, double diag, int mask_k,
-                         bool split_a, bool split_b, int* err, cudaStream_t st);
+                         int col_strips, const OzTile* tiles, int num_tiles, int stage_bytes, const int* group_prefix,
+                         int group_blocks,
+                         const void* maps_dev, int a_slot, int b_slot, int c_slot, int d_slot, double alpha,
+                         double beta, double diag, int mask_k, bool split_a, bool split_b, int* err, cudaStream_t st);
 // one-time kernel attribute set-up of launch_gram_tc / launch_bgemm (call before a stream capture)
 cudaError_t gram_tc_prepare();
 cudaError_t bgemm_prepare();
-// tensor maps of a cloud's Ozaki slice buffers (A: box 64 x 128 rows, B: box 64 x 64 rows)
+// tensor maps of a cloud's residue buffers (A: box 64 x 128 rows, B: box 64 x 64 rows, one modulus)
 bool make_ozaki_maps(void* map_a_host, void* map_b_host, const void* sa, const void* sb, int mpa, int mpb, int kp);
 
 }  // namespace rfd

@@ -254,7 +254,6 @@ rfd_status build_desc(rfd_plan_s* pl) {
     d.units[mode].clear();
     d.red[mode].clear();
   }
-  d.oz.clear();
   const int m = pl->m;
   const int64_t kb_total = pl->n_pad / kTcBK;
   const int a_rows = std::min(kTcBM, m);
@@ -325,7 +324,7 @@ rfd_status build_desc(rfd_plan_s* pl) {
                    pl->rows_alloc};
   d.apply = ApplyJob{pl->d_xyz,  pl->d_omega_hi, pl->d_omega_lo, pl->d_G, pl->d_Y, pl->d_oa, pl->d_Z,
                      pl->n,      pl->n_pad,      m, 0, (int)((pl->n + 511) / 512), 0};
-  // step a4 on the emulated path: slots in the FP64 workspace, Ozaki slices after them
+  // step a4 on the emulated path: slots in the FP64 workspace, the residue buffers after them
   PhiCloud& pc = d.phi;
   pc = PhiCloud{};
   pc.work = pl->d_work;
@@ -344,16 +343,17 @@ rfd_status build_desc(rfd_plan_s* pl) {
   pc.sb = reinterpret_cast<__nv_bfloat16_raw*>(oz + L.sb);
   pc.ea = reinterpret_cast<int*>(oz + L.ea);
   pc.eb = reinterpret_cast<int*>(oz + L.eb);
+  pc.ebp = reinterpret_cast<int*>(oz + L.ebp);
+  pc.res = oz + L.res;
+  pc.kbits = ozaki_kbits(m);
   pc.lambda = pl->p.lambda;
   pc.scale = 1.0;
   pc.map_a = 3;
   pc.map_b = 4;
-  for (int m0 = 0; m0 < pc.mpa; m0 += 128)
-    for (int n0 = 0; n0 < pc.mpb; n0 += 64) d.oz.push_back(OzTile{0, m0, n0, 0});
   if (!make_gram_maps(d.maps[0], d.maps[5], pl->d_psi, pl->n_pad, m, pl->cpad, pl->rows_alloc))
     return fail(RFD_ECUDA, "tensor-map encoding of the feature matrix failed");
   if (!make_ozaki_maps(d.maps[3], d.maps[4], pc.sa, pc.sb, pc.mpa, pc.mpb, pc.kp))
-    return fail(RFD_ECUDA, "tensor-map encoding of the FP64-emulation slices failed");
+    return fail(RFD_ECUDA, "tensor-map encoding of the FP64-emulation residues failed");
   return RFD_OK;
 }
 

@@ -83,11 +83,14 @@ struct BatchImpl {
   PhiCloud* d_phi = nullptr;
   int* d_elem_prefix = nullptr;
   int elem_blocks = 0;
+  int* d_grp_prefix = nullptr;  // blocks of the product reconstruction (8 entries per thread)
+  int grp_blocks = 0;
   int* d_rowa_prefix = nullptr;
   int rows_a = 0;
   int* d_strip_prefix = nullptr;  // blocks of the B operand's column split
   int col_strips = 0;
   OzTile* d_oz = nullptr;
+  int oz_stage_bytes = 0;  // pipeline stage of the residue GEMM
   int n_oz = 0;
   int max_m = 0, max_cpad = 16, max_kb = 0;
   int a_boxes = 1;  // 2 when some Gram unit has a second 128-row half
@@ -162,7 +165,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   std::vector<FillJob> fill;
   std::vector<ApplyJob> apply;
   std::vector<PhiCloud> phi;
-  std::vector<int> feat_n, fill_n, small_n, elem_n, rowa_n, strip_n;
+  std::vector<int> feat_n, fill_n, small_n, elem_n, grp_n, rowa_n, strip_n;
   std::vector<OzTile> oz;
   for (int k = 0; k < count; ++k) {
     rfd_plan_s* pl = plans[k];
@@ -221,21 +224,24 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
     pc.scale = 1.0;
     phi.push_back(pc);
     elem_n.push_back((int)(((int64_t)pl->m * pl->m + 255) / 256));
-    rowa_n.push_back(pc.mpa);
+    grp_n.push_back(ozaki_combine_blocks(pl->m));
+    rowa_n.push_back(ozaki_row_split_warps(pl->m));
     strip_n.push_back(ozaki_col_split_blocks(pl->m));
-    for (OzTile o : d.oz) {
-      o.cloud = k;
-      oz.push_back(o);
-    }
   }
   const std::vector<int> pre_feat = prefix_of(feat_n), pre_fill = prefix_of(fill_n), pre_small = prefix_of(small_n),
-                         pre_elem = prefix_of(elem_n), pre_rowa = prefix_of(rowa_n), pre_strip = prefix_of(strip_n);
+                         pre_elem = prefix_of(elem_n), pre_grp = prefix_of(grp_n), pre_rowa = prefix_of(rowa_n), pre_strip = prefix_of(strip_n);
   b->feat_blocks = pre_feat.back();
   b->fill_blocks = pre_fill.back();
   b->small_rows = pre_small.back();
   b->elem_blocks = pre_elem.back();
+  b->grp_blocks = pre_grp.back();
   b->rows_a = pre_rowa.back();
   b->col_strips = pre_strip.back();
+  {
+    std::vector<int> ms;
+    for (int k = 0; k < count; ++k) ms.push_back(plans[k]->m);
+    ozaki_batch_tiles(ms, sms, &oz, &b->oz_stage_bytes);
+  }
   b->n_oz = (int)oz.size();
   // --- one device block: the tables, then the per-call words
   struct Sec {
@@ -260,7 +266,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   }
   const size_t o_feat = vtable(feat), o_feat_pre = vtable(pre_feat), o_fill = vtable(fill),
                o_fill_pre = vtable(pre_fill), o_apply = vtable(apply), o_small_pre = vtable(pre_small),
-               o_phi = vtable(phi), o_elem_pre = vtable(pre_elem), o_rowa_pre = vtable(pre_rowa),
+               o_phi = vtable(phi), o_elem_pre = vtable(pre_elem), o_grp_pre = vtable(pre_grp), o_rowa_pre = vtable(pre_rowa),
                o_strip_pre = vtable(pre_strip), o_oz = vtable(oz);
   const size_t table_bytes = L.total;
   b->stage_bytes = (size_t)count * sizeof(CloudCall) + (size_t)(count + 1) * sizeof(int);
@@ -295,6 +301,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   b->d_small_prefix = reinterpret_cast<int*>(D + o_small_pre);
   b->d_phi = reinterpret_cast<PhiCloud*>(D + o_phi);
   b->d_elem_prefix = reinterpret_cast<int*>(D + o_elem_pre);
+  b->d_grp_prefix = reinterpret_cast<int*>(D + o_grp_pre);
   b->d_rowa_prefix = reinterpret_cast<int*>(D + o_rowa_pre);
   b->d_strip_prefix = reinterpret_cast<int*>(D + o_strip_pre);
   b->d_oz = reinterpret_cast<OzTile*>(D + o_oz);
@@ -369,16 +376,17 @@ rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s) {
     for (double v : a) a4[i++] = v;
     return launch_bcombine(b->d_phi, b->d_elem_prefix, n, b->elem_blocks, dst, s4, a4, diag, kmode, mask, st);
   };
-  // the A / B slices hold the operands of the previous product: split only what changed
+  // the A / B residues hold the operands of the previous product: split only what changed
   int last_a = kNoSlot, last_b = kNoSlot;
   auto gemm = [&](int a, int bb, int c, int d, double alpha, double beta, double diag, int mask) {
     const bool sa = a != last_a, sb = bb != last_b;
     last_a = a;
     last_b = bb;
     return launch_bgemm(b->d_phi, n, b->d_rowa_prefix, b->rows_a, b->d_strip_prefix, b->col_strips, b->d_oz,
-                        b->n_oz, b->d_maps, a, bb, c, d, alpha, beta, diag, mask, sa, sb, b->d_err, st);
+                        b->n_oz, b->oz_stage_bytes, b->d_grp_prefix, b->grp_blocks, b->d_maps, a, bb, c, d, alpha, beta, diag, mask, sa,
+                        sb, b->d_err, st);
   };
-  // a slot that is written no longer matches its slices
+  // a slot that is written no longer matches its residues
   auto wrote = [&](int slot) {
     if (slot == last_a) last_a = kNoSlot;
     if (slot == last_b) last_b = kNoSlot;

@@ -26,8 +26,8 @@ namespace {
 
 constexpr int kNoAllocMaxM = 128;
 // phi1_workspace_doubles(128) doubles (FP64 Pade buffers + the tensor-core
-// GEMM's slices) plus pivots and a few status words, rounded up: 3.25 MiB.
-constexpr size_t kNoAllocScratchBytes = (size_t)13 << 18;
+// GEMM's residue buffers) plus pivots and a few status words, rounded up: 3.75 MiB.
+constexpr size_t kNoAllocScratchBytes = (size_t)15 << 18;
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_phi1_scratch[kNoAllocScratchBytes];

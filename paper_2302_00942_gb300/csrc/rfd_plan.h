@@ -76,7 +76,6 @@ struct PlanDesc {
   FillJob fill{};
   ApplyJob apply{};
   PhiCloud phi{};
-  std::vector<OzTile> oz;
   unsigned char maps[kMapsPerCloud][kTensorMapBytes];
 };
 

@@ -143,6 +143,10 @@ bool make_map_bf16(CUtensorMap* map, const void* base, uint64_t cols, uint64_t r
 // blocks; box = 64 x box_rows x 1, 128-byte swizzle.
 bool make_map_bf16_blocked(CUtensorMap* map, const void* base, uint64_t rows, uint64_t rows_alloc, uint64_t nblocks,
                            uint32_t box_rows);
+// 3-D bf16 tensor map over planes of a row-major [rows][cols] buffer
+// ([planes][rows][cols], cols a multiple of 8), box = 64 columns x box_rows x 1.
+bool make_map_bf16_3d(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t planes,
+                      uint32_t box_rows);
 bool sm103_available();
 
 }  // namespace tc
