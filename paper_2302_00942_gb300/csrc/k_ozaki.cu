@@ -218,41 +218,84 @@ __device__ __forceinline__ double* pc_slot(const PhiCloud& pc, int slot) {
 struct Smem {
   uint64_t full[kMaxStages];
   uint64_t empty[kMaxStages];
-  uint64_t acc_full[kMaxBufs];
-  uint64_t acc_empty[kMaxBufs];
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
   uint32_t tmem_base;
 };
 
-// One CTA of the residue GEMM: rows m0 .. m0 + 128 nh of the A residues
-// against rows n0 .. n0 + nb of the B^T residues for the moduli g0 .. g0 + G - 1
-// in turn, over K_pad; residues of the products into the planes res
-// [16][mp][np] (bytes, in [0, p)).  A unit is one modulus over one segment of
-// at most 1024 of K (the FP32 exactness bound); unit u accumulates in TMEM
-// buffer u mod nbuf (nh nb columns: half h at + h nb), so the epilogue drains
-// one unit while the MMAs of the next run.  Stages (64 of K of one modulus)
-// follow the units in order.
-__device__ __forceinline__ void residue_tile(const CUtensorMap* map_a, const CUtensorMap* map_b,
-                                             const crt::Constants& cc, int K_pad, int m0, int n0, int nb, int nh,
-                                             int g0, int G, uint8_t* __restrict__ res, int mp, int np, int stages,
-                                             int stage_bytes, int* err) {
+// cluster-scope helpers (2-CTA clusters that share the B rows of a tile pair)
+__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, int32_t z,
+                                               uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
+      "%3, %4}], [%5], %6;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_index() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// One work item of the residue GEMM: rows m0 + 128 rank .. + 127 (rank: the
+// CTA's place in its cluster) of the A residues against rows n0 .. n0 + nb of
+// the B^T residues, for the moduli g0 .. g0 + G - 1 in turn, over kp of K;
+// residues of the products into res planes [16][mp][np] (bytes in [0, p)).
+struct Item {
+  const CUtensorMap* ma;
+  const CUtensorMap* mb;
+  uint8_t* res;
+  int kp, mp, np, m0, n0, nb, g0, G;
+  bool skip;  // the cloud skips this product (every CTA of a cluster sees the same)
+};
+
+// The residue GEMM, persistent: cluster c takes items c, c + clusters, ...  A
+// unit is one modulus over one segment of at most 1024 of K (the FP32
+// exactness bound); units alternate between two TMEM buffers of 256 columns,
+// so the epilogue drains one unit while the MMAs of the next run.  With CL = 2
+// the two CTAs of a cluster take the two 128-row halves of a 256-row tile: each
+// loads its own A rows and half of the B boxes, multicast to both, and each
+// MMA commit frees the stage in both CTAs (a stage is refilled only when both
+// have consumed it).  Stages (64 of K of one modulus) follow the units in order.
+template <int CL, typename ItemFn>
+__device__ __forceinline__ void residue_gemm_core(ItemFn item_of, int num_items, const crt::Constants& cc,
+                                                  int stages, int stage_bytes, int* err) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
   const uint32_t base = (raw_addr + 1023u) & ~1023u;
   Smem* sm = reinterpret_cast<Smem*>(smem_raw + (base - raw_addr) + stages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nchunks = K_pad / kBK;
-  const int nseg = (nchunks + kChunksPerSeg - 1) / kChunksPerSeg;
-  const int units = G * nseg;
-  const int width = nh * nb;                           // TMEM columns of one unit
-  const int nbuf = min(kMaxBufs, (int)(512 / width));  // >= 1
-  const uint32_t b_off = (uint32_t)nh * kABytes;       // B rows after the A box(es) in a stage
+  const int rank = CL > 1 ? (int)cluster_rank() : 0;
+  const int cid = CL > 1 ? (int)cluster_index() : (int)blockIdx.x;
+  const int ncl = CL > 1 ? (int)cluster_count() : (int)gridDim.x;
+  constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(smem_u32(&sm->full[s]), 1);
-      mbar_init(smem_u32(&sm->empty[s]), 1);
+      mbar_init(smem_u32(&sm->empty[s]), CL);  // one release from the MMA of every CTA of the cluster
     }
-    for (int q = 0; q < nbuf; ++q) {
+    for (int q = 0; q < 2; ++q) {
       mbar_init(smem_u32(&sm->acc_full[q]), 1);
       mbar_init(smem_u32(&sm->acc_empty[q]), kEpiWarps);
     }
@@ -262,123 +305,152 @@ __device__ __forceinline__ void residue_tile(const CUtensorMap* map_a, const CUt
   fence_before();
   __syncthreads();
   fence_after();
+  if (CL > 1) cluster_sync_all();  // the peer's barriers exist before any multicast or remote release
   const uint32_t tmem = sm->tmem_base;
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
-      const uint32_t tx = (uint32_t)(nh * kBM + nb) * kBK * 2;
       int i = 0;
       bool ok = true;
-      for (int u = 0; u < units && ok; ++u) {
-        const int g = g0 + u / nseg, seg = u % nseg;
-        const int c1 = min(nchunks, (seg + 1) * kChunksPerSeg);
-        for (int c = seg * kChunksPerSeg; c < c1; ++c, ++i) {
-          const int s = i % stages;
-          const uint32_t ph = (uint32_t)(i / stages) & 1u;
-          if (!mbar_wait(smem_u32(&sm->empty[s]), ph ^ 1u, err, 11)) {
-            ok = false;
-            break;
+      for (int it = cid; it < num_items && ok; it += ncl) {
+        const Item I = item_of(it);
+        if (I.skip) continue;
+        const int nchunks = I.kp / kBK, nseg = (nchunks + kChunksPerSeg - 1) / kChunksPerSeg;
+        const uint32_t tx = (uint32_t)(kBM + I.nb) * kBK * 2;  // own A rows + every B box (own and multicast)
+        for (int u = 0; u < I.G * nseg && ok; ++u) {
+          const int g = I.g0 + u / nseg, seg = u % nseg;
+          const int c1 = min(nchunks, (seg + 1) * kChunksPerSeg);
+          for (int c = seg * kChunksPerSeg; c < c1; ++c, ++i) {
+            const int s = i % stages;
+            if (!mbar_wait(smem_u32(&sm->empty[s]), ((uint32_t)(i / stages) & 1u) ^ 1u, err, 11)) {
+              ok = false;
+              break;
+            }
+            const uint32_t full = smem_u32(&sm->full[s]);
+            mbar_arrive_expect_tx(full, tx);
+            const uint32_t sa = base + s * stage_bytes, sb = sa + kABytes;
+            tma_load_3d(sa, I.ma, c * kBK, I.m0 + kBM * rank, g, full);
+            for (int q = rank; q < I.nb / kBBox; q += CL) {
+              if (CL > 1)
+                tma_load_3d_mc(sb + q * kBBoxBytes, I.mb, c * kBK, I.n0 + q * kBBox, g, full, kMask);
+              else
+                tma_load_3d(sb + q * kBBoxBytes, I.mb, c * kBK, I.n0 + q * kBBox, g, full);
+            }
           }
-          const uint32_t full = smem_u32(&sm->full[s]);
-          mbar_arrive_expect_tx(full, tx);
-          const uint32_t sa = base + s * stage_bytes, sb = sa + b_off;
-          tma_load_3d(sa, map_a, c * kBK, m0, g, full);
-          if (nh == 2) tma_load_3d(sa + kABytes, map_a, c * kBK, m0 + kBM, g, full);
-          for (int q = 0; q < nb / kBBox; ++q)
-            tma_load_3d(sb + q * kBBoxBytes, map_b, c * kBK, n0 + q * kBBox, g, full);
         }
       }
-      // our copies into the last stages must land before the CTA exits
+      // every stage this CTA filled has been released by every CTA of the cluster: no copy
+      // into, or release of, this CTA's shared memory is still in flight when it exits
       for (int t = (i > stages ? i - stages : 0); t < i; ++t)
-        mbar_wait(smem_u32(&sm->full[t % stages]), (uint32_t)(t / stages) & 1u, err, 12);
+        mbar_wait(smem_u32(&sm->empty[t % stages]), (uint32_t)(t / stages) & 1u, err, 12);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      const uint32_t idesc = idesc_bf16(kBM, nb);
-      int i = 0;
+      int i = 0, ug = 0;
       bool ok = true;
-      for (int u = 0; u < units && ok; ++u) {
-        const int seg = u % nseg, q = u % nbuf;
-        // the buffer's previous unit must have been drained
-        if (u >= nbuf && !mbar_wait(smem_u32(&sm->acc_empty[q]), (uint32_t)(u / nbuf - 1) & 1u, err, 13)) break;
-        const int c0 = seg * kChunksPerSeg, c1 = min(nchunks, c0 + kChunksPerSeg);
-        for (int c = c0; c < c1; ++c, ++i) {
-          const int s = i % stages;
-          const uint32_t ph = (uint32_t)(i / stages) & 1u;
-          if (!mbar_wait(smem_u32(&sm->full[s]), ph, err, 14)) {
+      for (int it = cid; it < num_items && ok; it += ncl) {
+        const Item I = item_of(it);
+        if (I.skip) continue;
+        const uint32_t idesc = idesc_bf16(kBM, I.nb);
+        const int nchunks = I.kp / kBK, nseg = (nchunks + kChunksPerSeg - 1) / kChunksPerSeg;
+        for (int u = 0; u < I.G * nseg && ok; ++u, ++ug) {
+          const int seg = u % nseg, q = ug & 1;
+          // the buffer's previous unit must have been drained
+          if (ug >= 2 && !mbar_wait(smem_u32(&sm->acc_empty[q]), (uint32_t)((ug >> 1) - 1) & 1u, err, 13)) {
             ok = false;
             break;
           }
-          fence_after();
-          const uint32_t sa = base + s * stage_bytes, sb = sa + b_off;
-          for (int h = 0; h < nh; ++h) {
-            const uint32_t d = tmem + (uint32_t)(q * width + h * nb);
+          const int c0 = seg * kChunksPerSeg, c1 = min(nchunks, c0 + kChunksPerSeg);
+          for (int c = c0; c < c1; ++c, ++i) {
+            const int s = i % stages;
+            if (!mbar_wait(smem_u32(&sm->full[s]), (uint32_t)(i / stages) & 1u, err, 14)) {
+              ok = false;
+              break;
+            }
+            fence_after();
+            const uint32_t sa = base + s * stage_bytes, sb = sa + kABytes;
 #pragma unroll
             for (int kk = 0; kk < kBK / 16; ++kk)
-              mma_bf16(d, sdesc_sw128(sa + h * kABytes + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
+              mma_bf16(tmem + (uint32_t)(q * 256), sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
                        (c > c0 || kk > 0) ? 1u : 0u);
+            if (CL > 1)
+              mma_commit_mc(smem_u32(&sm->empty[s]), kMask);  // frees the stage in every CTA of the cluster
+            else
+              mma_commit(smem_u32(&sm->empty[s]));
           }
-          mma_commit(smem_u32(&sm->empty[s]));  // frees the stage when these MMAs finish
+          if (ok) mma_commit(smem_u32(&sm->acc_full[q]));  // the unit's sums are complete
         }
-        if (ok) mma_commit(smem_u32(&sm->acc_full[q]));  // the unit's sums are complete
       }
     }
     __syncwarp();
   } else {
     // ---------------- epilogue (warps 2..9, two per TMEM lane quarter) ----------------
     const int quarter = warp & 3, sub = (warp - 2) >> 2;
-    const int per_half = nb / 32, nq = nh * per_half;
-    const size_t plane = (size_t)mp * np;
-    for (int u = 0; u < units; ++u) {
-      const int g = g0 + u / nseg, seg = u % nseg, qb = u % nbuf;
-      if (!mbar_wait(smem_u32(&sm->acc_full[qb]), (uint32_t)(u / nbuf) & 1u, err, 15)) break;
-      fence_after();
-      const float p = cc.p[g], ip = cc.inv_p[g];
-      for (int q = sub; q < nq; q += 2) {
-        const int h = q / per_half, c0 = (q % per_half) * 32;
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(qb * width + h * nb + c0), v);
-        const int row = m0 + h * kBM + quarter * 32 + lane;
-        uint8_t* dst = res + g * plane + (size_t)row * np + n0 + c0;
-        uint32_t old[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (seg > 0) {
-          const uint4 a = reinterpret_cast<const uint4*>(dst)[0], b = reinterpret_cast<const uint4*>(dst)[1];
-          old[0] = a.x; old[1] = a.y; old[2] = a.z; old[3] = a.w;
-          old[4] = b.x; old[5] = b.y; old[6] = b.z; old[7] = b.w;
+    int ug = 0;
+    bool ok = true;
+    for (int it = cid; it < num_items && ok; it += ncl) {
+      const Item I = item_of(it);
+      if (I.skip) continue;
+      const int nchunks = I.kp / kBK, nseg = (nchunks + kChunksPerSeg - 1) / kChunksPerSeg;
+      const size_t plane = (size_t)I.mp * I.np;
+      const int row0 = I.m0 + kBM * rank;
+      const bool rows_ok = row0 < I.mp;  // a cluster's second half may lie past the padded rows
+      for (int u = 0; u < I.G * nseg; ++u, ++ug) {
+        const int g = I.g0 + u / nseg, seg = u % nseg, q = ug & 1;
+        if (!mbar_wait(smem_u32(&sm->acc_full[q]), (uint32_t)(ug >> 1) & 1u, err, 15)) {
+          ok = false;
+          break;
         }
-        uint32_t w[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          uint32_t packed = 0;
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const float x = v[4 * e + b];  // an exact integer, |x| <= 2^24
-            float r = fmaf(-floorf(x * ip), p, x);  // x - q p, exact; q may be off by one
-            if (r < 0.f) r += p;
-            if (r >= p) r -= p;
-            uint32_t t = (uint32_t)r;
-            if (seg > 0) {
-              t += (old[e] >> (8 * b)) & 0xFFu;
-              if (t >= (uint32_t)p) t -= (uint32_t)p;
-            }
-            packed |= t << (8 * b);
+        fence_after();
+        const float p = cc.p[g], ip = cc.inv_p[g];
+        const int row = row0 + quarter * 32 + lane;
+        for (int cq = sub; cq < I.nb / 32; cq += 2) {
+          const int c0 = cq * 32;
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(q * 256 + c0), v);
+          if (!rows_ok) continue;
+          uint8_t* dst = I.res + g * plane + (size_t)row * I.np + I.n0 + c0;
+          uint32_t old[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+          if (seg > 0) {
+            const uint4 a = reinterpret_cast<const uint4*>(dst)[0], b = reinterpret_cast<const uint4*>(dst)[1];
+            old[0] = a.x; old[1] = a.y; old[2] = a.z; old[3] = a.w;
+            old[4] = b.x; old[5] = b.y; old[6] = b.z; old[7] = b.w;
           }
-          w[e] = packed;
+          uint32_t w[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            uint32_t packed = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const float x = v[4 * e + b];  // an exact integer, |x| <= 2^24
+              float r = fmaf(-floorf(x * ip), p, x);  // x - q p, exact; q may be off by one
+              if (r < 0.f) r += p;
+              if (r >= p) r -= p;
+              uint32_t t = (uint32_t)r;
+              if (seg > 0) {
+                t += (old[e] >> (8 * b)) & 0xFFu;
+                if (t >= (uint32_t)p) t -= (uint32_t)p;
+              }
+              packed |= t << (8 * b);
+            }
+            w[e] = packed;
+          }
+          reinterpret_cast<uint4*>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+          reinterpret_cast<uint4*>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
         }
-        reinterpret_cast<uint4*>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
-        reinterpret_cast<uint4*>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&sm->acc_empty[q]));
       }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&sm->acc_empty[qb]));
     }
   }
   fence_before();
   __syncthreads();
   fence_after();
   if (warp == 1) tmem_dealloc(tmem, 512);
+  if (CL > 1) cluster_sync_all();  // no CTA leaves while its peer may still address it
 }
 
 __device__ __forceinline__ bool pow2_of(double alpha, int* k, bool* neg) {
@@ -465,15 +537,30 @@ __global__ void bsplit_cols_kernel(const PhiCloud* __restrict__ pcs, const int* 
              reinterpret_cast<__nv_bfloat16*>(pc.sb), pc.eb, pc.ebp, (local / nranges) * 32, local % nranges);
 }
 
+template <int CL>
 __global__ void __launch_bounds__(kThreads, 1)
-bresidue_gemm_kernel(const CUtensorMap* __restrict__ maps, const OzTile* __restrict__ tiles,
+bresidue_gemm_kernel(const CUtensorMap* __restrict__ maps, const OzTile* __restrict__ tiles, int num_tiles,
                      const PhiCloud* __restrict__ pcs, const __grid_constant__ crt::Constants cc, int stages,
                      int stage_bytes, int mask_k, int* err) {
-  const OzTile t = tiles[blockIdx.x];
-  const PhiCloud pc = pcs[t.cloud];
-  if (mask_k >= 0 && pc.s <= mask_k) return;
-  residue_tile(maps + pc.map_a, maps + pc.map_b, cc, pc.kp, t.m0, t.n0, t.nb, t.nh, t.g0, t.ng, pc.res, pc.mpa,
-               pc.mpb, stages, stage_bytes, err);
+  auto item_of = [&](int it) {
+    const OzTile t = tiles[it];
+    const PhiCloud& pc = pcs[t.cloud];
+    Item I;
+    I.ma = maps + pc.map_a;
+    I.mb = maps + pc.map_b;
+    I.res = pc.res;
+    I.kp = pc.kp;
+    I.mp = pc.mpa;
+    I.np = pc.mpb;
+    I.m0 = t.m0;
+    I.n0 = t.n0;
+    I.nb = t.nb;
+    I.g0 = t.g0;
+    I.G = t.ng;
+    I.skip = mask_k >= 0 && pc.s <= mask_k;
+    return I;
+  };
+  residue_gemm_core<CL>(item_of, num_tiles, cc, stages, stage_bytes, err);
 }
 
 // D = alpha A B + beta C + diag I, one thread per 4 consecutive entries of a
@@ -518,14 +605,31 @@ __global__ void split_cols_kernel(const double* __restrict__ B, int ld, int K, i
   split_cols(B, ld, K, N, K_pad, N_pad, sh0, res, exps, part, blockIdx.x * 32, blockIdx.y);
 }
 
-// grid (column tiles of 256, row tiles of 256, 16 moduli); stages of 64 KB
+// items (row tile of 128 CL, column tile of 256, modulus), one modulus each
+template <int CL>
 __global__ void __launch_bounds__(kThreads, 1)
 residue_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                     const __grid_constant__ crt::Constants cc, int K_pad, int mp, int np, uint8_t* res, int stages,
-                    int* err) {
-  const int n0 = blockIdx.x * kBNMax, m0 = blockIdx.y * 2 * kBM;
-  residue_tile(&map_a, &map_b, cc, K_pad, m0, n0, min(kBNMax, np - n0), (m0 + kBM < mp) ? 2 : 1, blockIdx.z, 1, res,
-               mp, np, stages, 2 * kABytes + kBNMax * kBK * 2, err);
+                    int stage_bytes, int* err) {
+  const int ntn = (np + kBNMax - 1) / kBNMax, ntm = (mp + kBM * CL - 1) / (kBM * CL);
+  auto item_of = [&](int it) {
+    Item I;
+    I.ma = &map_a;
+    I.mb = &map_b;
+    I.res = res;
+    I.kp = K_pad;
+    I.mp = mp;
+    I.np = np;
+    I.g0 = it % kNumMod;
+    I.G = 1;
+    const int t = it / kNumMod;
+    I.n0 = (t % ntn) * kBNMax;
+    I.m0 = (t / ntn) * kBM * CL;
+    I.nb = min(kBNMax, np - I.n0);
+    I.skip = false;
+    return I;
+  };
+  residue_gemm_core<CL>(item_of, ntn * ntm * kNumMod, cc, stages, stage_bytes, err);
 }
 
 __global__ void combine_product_kernel(const __grid_constant__ crt::Constants cc, const uint8_t* __restrict__ res,
@@ -547,15 +651,47 @@ bool make_ozaki_maps(void* map_a_host, void* map_b_host, const void* sa, const v
                               kBBox);
 }
 
-cudaError_t bgemm_prepare() {
-  static const cudaError_t attr = [] {  // once per process (thread-safe initialisation)
+namespace {
+
+// Co-resident CTAs of the residue GEMM (1 per SM, shared memory bound) and
+// co-resident 2-CTA clusters; the persistent grids use these counts.
+struct GemmSlots {
+  cudaError_t status;
+  int ctas, clusters2;
+};
+const GemmSlots& gemm_slots() {
+  static const GemmSlots g = [] {  // once per process (thread-safe initialisation)
+    GemmSlots r{cudaSuccess, 0, 0};
     constants();
-    cudaError_t e = cudaFuncSetAttribute(bresidue_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(residue_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
-    return e;
+    int dev = 0;
+    r.status = cudaGetDevice(&dev);
+    if (r.status == cudaSuccess) r.status = cudaDeviceGetAttribute(&r.ctas, cudaDevAttrMultiProcessorCount, dev);
+    auto attr = [&](auto kern) {
+      if (r.status == cudaSuccess)
+        r.status = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    };
+    attr(bresidue_gemm_kernel<1>);
+    attr(bresidue_gemm_kernel<2>);
+    attr(residue_gemm_kernel<1>);
+    attr(residue_gemm_kernel<2>);
+    if (r.status == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute la[1];
+      la[0].id = cudaLaunchAttributeClusterDimension;
+      la[0].val.clusterDim.x = 2;
+      la[0].val.clusterDim.y = 1;
+      la[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(2 * r.ctas);
+      cfg.blockDim = dim3(kThreads);
+      cfg.dynamicSmemBytes = kSmemLimit;
+      cfg.attrs = la;
+      cfg.numAttrs = 1;
+      r.status = cudaOccupancyMaxActiveClusters(&r.clusters2, bresidue_gemm_kernel<2>, &cfg);
+      if (r.status == cudaSuccess && r.clusters2 < 1) r.status = cudaErrorInvalidConfiguration;
+    }
+    return r;
   }();
-  return attr;
+  return g;
 }
 
 // stages of stage_bytes that fit the shared memory (2 .. kMaxStages), 0 if none
@@ -564,40 +700,77 @@ int stages_for(int stage_bytes) {
   return s < 2 ? 0 : (s > kMaxStages ? kMaxStages : s);
 }
 
-void ozaki_batch_tiles(const std::vector<int>& ms, int sms, std::vector<OzTile>* out, int* stage_bytes) {
+// A persistent launch with clusters of CL CTAs: grid = CL x (co-resident clusters, at most one per item).
+template <int CL, typename Kern, typename... Args>
+cudaError_t launch_persistent(Kern kern, int items, int smem, cudaStream_t st, Args... args) {
+  const GemmSlots& g = gemm_slots();
+  if (g.status != cudaSuccess) return g.status;
+  const int clusters = std::max(1, std::min(items, CL > 1 ? g.clusters2 : g.ctas));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute la[1];
+  la[0].id = cudaLaunchAttributeClusterDimension;
+  la[0].val.clusterDim.x = CL;
+  la[0].val.clusterDim.y = 1;
+  la[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(CL * clusters);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = la;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+}  // namespace
+
+cudaError_t bgemm_prepare() { return gemm_slots().status; }
+
+void ozaki_batch_tiles(const std::vector<int>& ms, int sms, std::vector<OzTile>* out, int* stage_bytes,
+                       int* cluster) {
+  (void)sms;
   out->clear();
-  // tiles of one modulus first (half pairs for m >= 512, where the B reuse pays)
-  std::vector<OzTile> base;
+  // 2-CTA clusters (tile pairs sharing B) when every cloud has at least two 128-row tiles
+  int CL = 2;
+  for (int m : ms)
+    if (ozaki_layout(m, m, m).mp < 2 * kBM) CL = 1;
+  int nb_max = kBBox;
   for (int k = 0; k < (int)ms.size(); ++k) {
     const OzLayout L = ozaki_layout(ms[k], ms[k], ms[k]);
-    const bool pairs = ms[k] >= 512;
-    for (int m0 = 0; m0 < L.mp; m0 += (pairs ? 2 : 1) * kBM) {
-      const int nh = (pairs && m0 + kBM < L.mp) ? 2 : 1;
-      for (int n0 = 0; n0 < L.np; n0 += kBNMax) base.push_back(OzTile{k, m0, n0, std::min(kBNMax, L.np - n0), nh, 0, 1, 0});
-    }
+    for (int m0 = 0; m0 < L.mp; m0 += CL * kBM)
+      for (int n0 = 0; n0 < L.np; n0 += kBNMax) {
+        const int nb = std::min(kBNMax, L.np - n0);
+        nb_max = std::max(nb_max, nb);
+        for (int g = 0; g < kNumMod; ++g) out->push_back(OzTile{k, m0, n0, nb, L.kp, g, 1, 0});
+      }
   }
-  // moduli per CTA: the largest power of two <= 16 that leaves two CTAs per SM
-  int G = kNumMod;
-  while (G > 1 && (int64_t)base.size() * (kNumMod / G) < 2 * (int64_t)sms) G /= 2;
-  int nh_max = 1, nb_max = kBBox;
-  for (const OzTile& t : base) {
-    nh_max = std::max(nh_max, t.nh);
-    nb_max = std::max(nb_max, t.nb);
-    for (int g0 = 0; g0 < kNumMod; g0 += G) {
-      OzTile u = t;
-      u.g0 = g0;
-      u.ng = G;
-      out->push_back(u);
-    }
-  }
-  *stage_bytes = nh_max * kABytes + nb_max * kBK * 2;
+  // longest items first: the persistent CTAs take them round robin
+  std::stable_sort(out->begin(), out->end(),
+                   [](const OzTile& a, const OzTile& b) { return (int64_t)a.nb * a.kp > (int64_t)b.nb * b.kp; });
+  *stage_bytes = kABytes + nb_max * kBK * 2;
+  *cluster = CL;
 }
+
+namespace {
+// grid-stride launch of the batched residue GEMM over its items
+cudaError_t launch_bresidue(const void* maps_dev, const OzTile* tiles, int num_tiles, const PhiCloud* pc,
+                            int stage_bytes, int cluster, int mask_k, int* err, cudaStream_t st) {
+  const int stages = stages_for(stage_bytes);
+  if (stages == 0) return cudaErrorInvalidValue;
+  const int smem = stages * stage_bytes + kSmemExtra;
+  const auto* maps = static_cast<const CUtensorMap*>(maps_dev);
+  if (cluster == 2)
+    return launch_persistent<2>(bresidue_gemm_kernel<2>, num_tiles, smem, st, maps, tiles, num_tiles, pc, constants(),
+                                stages, stage_bytes, mask_k, err);
+  return launch_persistent<1>(bresidue_gemm_kernel<1>, num_tiles, smem, st, maps, tiles, num_tiles, pc, constants(),
+                              stages, stage_bytes, mask_k, err);
+}
+}  // namespace
 
 int ozaki_kbits(int K) { return crt::kbits(K); }
 
 cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* strip_prefix,
-                         int col_strips, const OzTile* tiles, int num_tiles, int stage_bytes, const int* group_prefix,
-                         int group_blocks,
+                         int col_strips, const OzTile* tiles, int num_tiles, int stage_bytes, int cluster,
+                         const int* group_prefix, int group_blocks,
                          const void* maps_dev, int a_slot, int b_slot, int c_slot, int d_slot, double alpha,
                          double beta, double diag, int mask_k, bool split_a, bool split_b, int* err, cudaStream_t st) {
   const cudaError_t attr = bgemm_prepare();
@@ -611,10 +784,8 @@ cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a,
     bsplit_cols_kernel<<<col_strips, 256, 0, st>>>(pc, strip_prefix, count, b_slot, mask_k);
     count_launch(2);
   }
-  const int stages = stages_for(stage_bytes);
-  if (stages == 0) return cudaErrorInvalidValue;
-  bresidue_gemm_kernel<<<num_tiles, kThreads, stages * stage_bytes + kSmemExtra, st>>>(
-      static_cast<const CUtensorMap*>(maps_dev), tiles, pc, constants(), stages, stage_bytes, mask_k, err);
+  const cudaError_t e = launch_bresidue(maps_dev, tiles, num_tiles, pc, stage_bytes, cluster, mask_k, err, st);
+  if (e != cudaSuccess) return e;
   count_launch();
   bcombine_product_kernel<<<group_blocks, 256, 0, st>>>(pc, group_prefix, count, constants(), c_slot, d_slot, alpha,
                                                         beta, diag, mask_k);
@@ -675,10 +846,19 @@ cudaError_t dgemm_ozaki(int M, int N, int K, double alpha, const double* A, int 
   count_launch(3);
   CUtensorMap ma, mb;
   if (!make_ozaki_maps(&ma, &mb, sa, sb, mp, np, kp)) return cudaErrorInvalidValue;
-  residue_gemm_kernel<<<dim3((np + kBNMax - 1) / kBNMax, (mp + 2 * kBM - 1) / (2 * kBM), kNumMod), kThreads,
-                        3 * (2 * kABytes + kBNMax * kBK * 2) + kSmemExtra, st>>>(ma, mb, constants(), kp, mp, np, res, 3,
-                                                                                  err);
-  count_launch();
+  {
+    const int stage_bytes = kABytes + kBNMax * kBK * 2, stages = stages_for(stage_bytes);
+    const int smem = stages * stage_bytes + kSmemExtra, ntn = (np + kBNMax - 1) / kBNMax;
+    cudaError_t e;
+    if (mp >= 2 * kBM)
+      e = launch_persistent<2>(residue_gemm_kernel<2>, ntn * ((mp + 2 * kBM - 1) / (2 * kBM)) * kNumMod, smem, st, ma,
+                               mb, constants(), kp, mp, np, res, stages, stage_bytes, err);
+    else
+      e = launch_persistent<1>(residue_gemm_kernel<1>, ntn * (mp / kBM) * kNumMod, smem, st, ma, mb, constants(), kp,
+                               mp, np, res, stages, stage_bytes, err);
+    if (e != cudaSuccess) return e;
+    count_launch();
+  }
   const int64_t groups = (int64_t)M * ((N + 3) / 4);
   combine_product_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(constants(), res, ea, eb, M, N, mp, np,
                                                                            alpha, beta, C, ldc);

@@ -229,17 +229,19 @@ struct PhiCloud {
   int32_t map_a, map_b;   // tensor maps of sa / sb
   int32_t s, kbits;       // squarings (set per call); bits of the scaled integers (ozaki_kbits(m))
 };
-// One CTA of the residue GEMM: rows m0 .. m0 + 128 nh, columns n0 .. n0 + nb,
-// moduli g0 .. g0 + ng - 1 (in turn) of one cloud's product.
+// One work item of the residue GEMM: rows m0 .. (128 per CTA of a cluster),
+// columns n0 .. n0 + nb, moduli g0 .. g0 + ng - 1 of one cloud's product (kp:
+// the padded K, for ordering the items by cost).
 struct OzTile {
-  int32_t cloud, m0, n0, nb, nh, g0, ng, pad_;
+  int32_t cloud, m0, n0, nb, kp, g0, ng, pad_;
 };
-// The residue-GEMM CTAs of a batch of m x m products (cloud k of size ms[k]):
-// 256-row tiles (two 128-row halves sharing the B rows) for m >= 512, 128-row
-// tiles below, up to 256 columns; each CTA takes G moduli in turn, G the
-// largest power of two <= 16 that leaves two CTAs per SM.  *stage_bytes: the
-// pipeline stage size of the launch.
-void ozaki_batch_tiles(const std::vector<int>& ms, int sms, std::vector<OzTile>* out, int* stage_bytes);
+// The residue-GEMM work items of a batch of m x m products (cloud k of size
+// ms[k]), longest first: one per (row tile, column tile of <= 256, modulus).
+// *cluster = 2 when every cloud has two or more 128-row tiles: the two CTAs of
+// a cluster take the halves of a 256-row tile and share its B rows by
+// multicast; else 1 (128-row tiles).  *stage_bytes: the pipeline stage size.
+void ozaki_batch_tiles(const std::vector<int>& ms, int sms, std::vector<OzTile>* out, int* stage_bytes,
+                       int* cluster);
 
 cudaError_t launch_features_batched(const FeatJob* jobs, const int* prefix, int count, int total_blocks,
                                     const CloudCall* calls, cudaStream_t st);
@@ -274,8 +276,8 @@ cudaError_t launch_bfinite(const PhiCloud* pc, const int* prefix, int count, int
 // that operand (split by the previous product over the same or a larger set of
 // clouds).
 cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* strip_prefix,
-                         int col_strips, const OzTile* tiles, int num_tiles, int stage_bytes, const int* group_prefix,
-                         int group_blocks,
+                         int col_strips, const OzTile* tiles, int num_tiles, int stage_bytes, int cluster,
+                         const int* group_prefix, int group_blocks,
                          const void* maps_dev, int a_slot, int b_slot, int c_slot, int d_slot, double alpha,
                          double beta, double diag, int mask_k, bool split_a, bool split_b, int* err, cudaStream_t st);
 // one-time kernel attribute set-up of launch_gram_tc / launch_bgemm (call before a stream capture)

@@ -91,6 +91,7 @@ struct BatchImpl {
   int col_strips = 0;
   OzTile* d_oz = nullptr;
   int oz_stage_bytes = 0;  // pipeline stage of the residue GEMM
+  int oz_cluster = 1;      // CTAs per cluster of the residue GEMM
   int n_oz = 0;
   int max_m = 0, max_cpad = 16, max_kb = 0;
   int a_boxes = 1;  // 2 when some Gram unit has a second 128-row half
@@ -240,7 +241,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   {
     std::vector<int> ms;
     for (int k = 0; k < count; ++k) ms.push_back(plans[k]->m);
-    ozaki_batch_tiles(ms, sms, &oz, &b->oz_stage_bytes);
+    ozaki_batch_tiles(ms, sms, &oz, &b->oz_stage_bytes, &b->oz_cluster);
   }
   b->n_oz = (int)oz.size();
   // --- one device block: the tables, then the per-call words
@@ -383,7 +384,7 @@ rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s) {
     last_a = a;
     last_b = bb;
     return launch_bgemm(b->d_phi, n, b->d_rowa_prefix, b->rows_a, b->d_strip_prefix, b->col_strips, b->d_oz,
-                        b->n_oz, b->oz_stage_bytes, b->d_grp_prefix, b->grp_blocks, b->d_maps, a, bb, c, d, alpha, beta, diag, mask, sa,
+                        b->n_oz, b->oz_stage_bytes, b->oz_cluster, b->d_grp_prefix, b->grp_blocks, b->d_maps, a, bb, c, d, alpha, beta, diag, mask, sa,
                         sb, b->d_err, st);
   };
   // a slot that is written no longer matches its residues
