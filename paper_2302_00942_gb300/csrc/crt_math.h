@@ -96,6 +96,7 @@ struct Limbs {
 RFD_HD Limbs limbs_of(long long X) {
   const bool neg = X < 0;
   const unsigned long long a = neg ? (unsigned long long)(-X) : (unsigned long long)X;
+  const float sg = neg ? -1.0f : 1.0f;
   Limbs L;
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
@@ -105,9 +106,20 @@ RFD_HD Limbs limbs_of(long long X) {
 #else
     const float f = (float)v;
 #endif
-    L.x[i] = neg ? -f : f;
+    L.x[i] = f * sg;
   }
   return L;
+}
+
+// The integer nearest to x (ties to even) for |x| < 2^22, by the FP32 add of
+// 1.5 2^23 (whose unit in the last place is 1): no rounding or conversion unit.
+RFD_HD float rint_small(float x) {
+#if defined(__CUDA_ARCH__)
+  return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+#else
+  volatile float t = x + 12582912.0f;
+  return t - 12582912.0f;
+#endif
 }
 
 // X mod p_j in a symmetric range, |r| <= 128, as an FP32 integer.  For p < 256:
@@ -119,13 +131,18 @@ template <int j>
 RFD_HD float residue(const Limbs& L, long long X) {
   constexpr uint32_t p = modulus(j);
   if constexpr (p == 256) {
-    return (float)((int)(((unsigned long long)X + 128ull) & 255ull) - 128);
+    const uint32_t u = (uint32_t)(((unsigned long long)X + 128ull) & 255ull);
+#if defined(__CUDA_ARCH__)
+    return __uint_as_float(0x4B000000u | u) - 8388736.0f;  // u - 128, exact
+#else
+    return (float)u - 128.0f;
+#endif
   } else {
     constexpr float c1 = (float)((1ull << 12) % p), c2 = (float)((1ull << 24) % p), c3 = (float)((1ull << 36) % p),
                     c4 = (float)((1ull << 48) % p);
     constexpr float fp = (float)p, ip = 1.0f / (float)p;
     const float s = fmaf(L.x[4], c4, fmaf(L.x[3], c3, fmaf(L.x[2], c2, fmaf(L.x[1], c1, L.x[0]))));
-    return fmaf(-fp, rintf(s * ip), s);
+    return fmaf(-fp, rint_small(s * ip), s);
   }
 }
 

@@ -425,7 +425,7 @@ __device__ __forceinline__ void residue_gemm_core(ItemFn item_of, int num_items,
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
               const float x = v[4 * e + b];  // an exact integer, |x| <= 2^24
-              float r = fmaf(-floorf(x * ip), p, x);  // x - q p, exact; q may be off by one
+              float r = fmaf(-crt::rint_small(x * ip), p, x);  // x - q p, exact, |r| <= p / 2 + 1
               if (r < 0.f) r += p;
               if (r >= p) r -= p;
               uint32_t t = (uint32_t)r;
@@ -506,9 +506,8 @@ __device__ __forceinline__ void combine4(const crt::Constants& cc, const uint8_t
 // ---- batched kernels (one table entry per cloud, slots resolved per call) ----
 
 // Row split of the A operand, every cloud (warp prefix over ozaki_row_split_warps(m)).
-__global__ void bsplit_rows_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
-                                   int slot, int mask_k) {
-  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ void bsplit_rows_warp(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix,
+                                                 int count, int slot, int mask_k, int wg, int lane) {
   if (wg >= __ldg(prefix + count)) return;
   const int j = find_job(prefix, count, wg);
   const PhiCloud pc = pcs[j];
@@ -516,16 +515,33 @@ __global__ void bsplit_rows_kernel(const PhiCloud* __restrict__ pcs, const int* 
   split_rows_warp(pc_slot(pc, slot), pc.m, pc.m, pc.m, pc.mpa, pc.kp, pc.kbits - 53,
                   reinterpret_cast<__nv_bfloat16*>(pc.sa), pc.ea, wg - prefix[j], lane);
 }
-
-// Column exponents and column split of the B operand: one block per strip of
-// 32 columns and range of 64 rows of K (prefix over strips x ranges per cloud).
-__global__ void bcol_exponents_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
-                                      int slot, int mask_k) {
-  const int jc = find_job(prefix, count, blockIdx.x);
+// Column exponents of the B operand: one block per strip of 32 columns and
+// range of 64 rows of K (prefix over strips x ranges per cloud).
+__device__ __forceinline__ void bcol_exponents_block(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix,
+                                                     int count, int slot, int mask_k, int b) {
+  const int jc = find_job(prefix, count, b);
   const PhiCloud pc = pcs[jc];
   if (mask_k >= 0 && pc.s <= mask_k) return;
-  const int nranges = pc.kp / kColSplitK, local = blockIdx.x - prefix[jc];
+  const int nranges = pc.kp / kColSplitK, local = b - prefix[jc];
   col_exponents(pc_slot(pc, slot), pc.m, pc.m, pc.m, pc.mpb, pc.ebp, (local / nranges) * 32, local % nranges);
+}
+__global__ void bsplit_rows_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
+                                   int slot, int mask_k) {
+  bsplit_rows_warp(pcs, prefix, count, slot, mask_k, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31);
+}
+__global__ void bcol_exponents_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
+                                      int slot, int mask_k) {
+  bcol_exponents_block(pcs, prefix, count, slot, mask_k, blockIdx.x);
+}
+// both in one launch (independent work): blocks [0, row_blocks) split A, the rest take B's exponents
+__global__ void bsplit_rows_col_exponents_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ row_prefix,
+                                                 const int* __restrict__ strip_prefix, int count, int a_slot,
+                                                 int b_slot, int mask_k, int row_blocks) {
+  if ((int)blockIdx.x < row_blocks)
+    bsplit_rows_warp(pcs, row_prefix, count, a_slot, mask_k, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                     threadIdx.x & 31);
+  else
+    bcol_exponents_block(pcs, strip_prefix, count, b_slot, mask_k, blockIdx.x - row_blocks);
 }
 __global__ void bsplit_cols_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
                                    int slot, int mask_k) {
@@ -775,14 +791,21 @@ cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a,
                          double beta, double diag, int mask_k, bool split_a, bool split_b, int* err, cudaStream_t st) {
   const cudaError_t attr = bgemm_prepare();
   if (attr != cudaSuccess) return attr;
-  if (split_a) {
-    bsplit_rows_kernel<<<(rows_a * 32 + 255) / 256, 256, 0, st>>>(pc, row_prefix_a, count, a_slot, mask_k);
+  const int row_blocks = (rows_a * 32 + 255) / 256;
+  if (split_a && split_b) {
+    bsplit_rows_col_exponents_kernel<<<row_blocks + col_strips, 256, 0, st>>>(pc, row_prefix_a, strip_prefix, count,
+                                                                             a_slot, b_slot, mask_k, row_blocks);
+    count_launch();
+  } else if (split_a) {
+    bsplit_rows_kernel<<<row_blocks, 256, 0, st>>>(pc, row_prefix_a, count, a_slot, mask_k);
+    count_launch();
+  } else if (split_b) {
+    bcol_exponents_kernel<<<col_strips, 256, 0, st>>>(pc, strip_prefix, count, b_slot, mask_k);
     count_launch();
   }
   if (split_b) {
-    bcol_exponents_kernel<<<col_strips, 256, 0, st>>>(pc, strip_prefix, count, b_slot, mask_k);
     bsplit_cols_kernel<<<col_strips, 256, 0, st>>>(pc, strip_prefix, count, b_slot, mask_k);
-    count_launch(2);
+    count_launch();
   }
   const cudaError_t e = launch_bresidue(maps_dev, tiles, num_tiles, pc, stage_bytes, cluster, mask_k, err, st);
   if (e != cudaSuccess) return e;
