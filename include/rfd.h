@@ -78,14 +78,26 @@ typedef struct {
   int32_t flags;         /* RFD_FLAG_* bits (0 = none)                            */
   double freq_sigma;     /* sigma of the truncated Gaussian (0 => 1/(2 eps))      */
   double freq_radius;    /* truncation half-width R (0 => 1/eps)                  */
+  int32_t kernel;        /* rfd_kernel: the eps-NN indicator f (0 = L-infinity cube) */
+  int32_t reserved_;     /* must be 0                                             */
 } rfd_params;
+
+/* The threshold function f of the eps-NN graph, W(i, j) = f(x_i - x_j) (Sec. 2.4),
+ * and with it tau = the Fourier transform of f (2 pi convention):
+ *   RFD_KERNEL_CUBE: f = 1[||z||_inf <= eps], tau(w) = prod_d sin(2 pi eps w_d) / (pi w_d)
+ *                    (the product of per-coordinate sincs printed in Sec. 2.4);
+ *   RFD_KERNEL_BALL: f = 1[||z||_2 <= eps], tau(w) = 4 pi (sin(q eps) - q eps cos(q eps)) / q^3,
+ *                    q = 2 pi ||w||_2 (the Bessel-function case of Sec. 2.4 in d = 3:
+ *                    4 pi eps^3 j_1(q eps) / (q eps)). */
+typedef enum { RFD_KERNEL_CUBE = 0, RFD_KERNEL_BALL = 1 } rfd_kernel;
 
 typedef struct rfd_plan_s* rfd_plan_t;
 
 /* rfd_params.flags bits */
 #define RFD_FLAG_TIMING 1       /* record CUDA events around every step (see rfd_stats.step_ms) */
 #define RFD_FLAG_NATIVE_FP64 2  /* step a4 products in native FP64 instead of the FP64-accurate
-                                   Ozaki-split emulation on the BF16 tensor cores (the default) */
+                                   modular (Chinese-remainder) emulation on the BF16 tensor cores
+                                   (the default) */
 #define RFD_FLAG_GRAPH 4        /* batches only: replay each call's launches from CUDA graphs,
                                    captured on first use per call shape (per-step timings are
                                    then not recorded) */
@@ -144,6 +156,12 @@ typedef struct {
  * --------------------------------------------------------------------------- */
 RFD_API rfd_status rfd_sample_frequencies(int32_t m, double eps, uint64_t seed, double freq_sigma,
                                   double freq_radius, double* omega_out, double* r_out);
+
+/* The same draw for the threshold function `kernel` (rfd_kernel): omega_out is
+ * identical for every kernel, r_out = tau_kernel(w_j)/p(w_j).  RFD_EINVAL for an
+ * unknown kernel. */
+RFD_API rfd_status rfd_sample_weights(int32_t m, double eps, uint64_t seed, double freq_sigma, double freq_radius,
+                                      int32_t kernel, double* omega_out, double* r_out);
 
 /* Create a plan: validate params, run step a1 on the host, upload the
  * frequencies and column scales, and allocate every device buffer the plan

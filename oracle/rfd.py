@@ -20,7 +20,10 @@ with the readings of the paper used throughout this project:
     per-coordinate sincs printed for tau in Sec. 2.4 is the Fourier transform of
     that cube (an L1 ball's transform does not factor).  With the 2 pi
     convention of Sec. 2.4, tau(w) = prod_d sin(2 pi eps w_d) / (pi w_d)
-    (value 2 eps at w_d = 0).
+    (value 2 eps at w_d = 0).  The L2 ball 1[||z||_2 <= eps], whose transform
+    Sec. 2.4 names as a Bessel function, is the second threshold function
+    (kernel="ball"): tau(w) = 4 pi eps^3 j_1(2 pi eps |w|) / (2 pi eps |w|),
+    j_1 the spherical Bessel function of order one.
   * P is a per-coordinate Gaussian N(0, sigma^2) truncated to [-R, R]
     ("(truncated) Gaussian", Sec. 2.4; App. A.4), default sigma = 1/(2 eps),
     R = 1/eps.
@@ -114,10 +117,24 @@ def sample_frequencies(m: int, eps: float, seed: int, sigma: float = 0.0,
     return omega
 
 
-def tau(omega: np.ndarray, eps: float) -> np.ndarray:
-    """Fourier transform of 1[||z||_inf <= eps] (Sec. 2.4, the product of
-    per-coordinate sincs), 2 pi convention: prod_d sin(2 pi eps w_d)/(pi w_d)."""
+def tau(omega: np.ndarray, eps: float, kernel: str = "cube") -> np.ndarray:
+    """Fourier transform of the threshold function f (Sec. 2.4), 2 pi convention.
+
+    kernel="cube": f = 1[||z||_inf <= eps], the product of per-coordinate sincs,
+    prod_d sin(2 pi eps w_d)/(pi w_d).
+    kernel="ball": f = 1[||z||_2 <= eps] in R^3 (the Bessel case of Sec. 2.4):
+    the transform of a radial function is radial, and for the ball it is
+    (4/3) pi eps^3 * 3 j_1(x)/x with x = 2 pi eps |w| (j_1 from SciPy; the
+    value at w = 0 is the ball's volume).
+    """
     w = np.asarray(omega, dtype=np.float64)
+    if kernel == "ball":
+        x = 2.0 * np.pi * eps * np.linalg.norm(w, axis=-1)
+        safe = np.where(x == 0.0, 1.0, x)
+        ratio = np.where(x == 0.0, 1.0 / 3.0, scipy.special.spherical_jn(1, safe) / safe)
+        return 4.0 * np.pi * eps ** 3 * ratio
+    if kernel != "cube":
+        raise ValueError(f"unknown kernel {kernel!r}")
     safe = np.where(w == 0.0, 1.0, w)
     per = np.where(w == 0.0, 2.0 * eps, np.sin(2.0 * np.pi * eps * w) / (np.pi * safe))
     return np.prod(per, axis=-1)
@@ -133,11 +150,12 @@ def density(omega: np.ndarray, sigma: float, radius: float) -> np.ndarray:
     return np.prod(per, axis=-1)
 
 
-def weights(omega: np.ndarray, eps: float, sigma: float = 0.0, radius: float = 0.0) -> np.ndarray:
+def weights(omega: np.ndarray, eps: float, sigma: float = 0.0, radius: float = 0.0,
+            kernel: str = "cube") -> np.ndarray:
     """r_j = tau(w_j) / p(w_j)  (Sec. 2.4: nu_j^2)."""
     sigma = sigma or default_sigma(eps)
     radius = radius or default_radius(eps)
-    return tau(omega, eps) / density(omega, sigma, radius)
+    return tau(omega, eps, kernel) / density(omega, sigma, radius)
 
 
 # ---------------------------------------------------------------------------
@@ -184,11 +202,11 @@ def phi1(X: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------------------
 # The whole estimator, steps a1..a6, in the paper's order
 # ---------------------------------------------------------------------------
-def rfd_gfi(points, F, eps, lam, m, seed, sigma=0.0, radius=0.0, *, return_parts=False):
+def rfd_gfi(points, F, eps, lam, m, seed, sigma=0.0, radius=0.0, *, return_parts=False, kernel="cube"):
     """out = F + A (G (B^T F)),  G = lambda phi1(lambda B^T A)  (Sec. 2.4)."""
     F64 = np.asarray(F, dtype=np.float64)
     omega = sample_frequencies(m, eps, seed, sigma, radius)
-    r = weights(omega, eps, sigma, radius)
+    r = weights(omega, eps, sigma, radius, kernel)
     A, B = factors(points, omega, r)
     M = B.T @ A                 # m x m   (pre-processing, Sec. 2.4)
     Y = B.T @ F64               # m x c   (inference)
@@ -219,10 +237,12 @@ def dense_lowrank_gfi(A: np.ndarray, B: np.ndarray, F: np.ndarray, lam: float) -
     return V @ (np.exp(lam * e)[:, None] * (V.T @ np.asarray(F, dtype=np.float64)))
 
 
-def exact_adjacency(points: np.ndarray, eps: float) -> np.ndarray:
-    """W(i,j) = 1[||n_i - n_j||_inf <= eps] (Eq. w; diagonal f(0) = 1)."""
+def exact_adjacency(points: np.ndarray, eps: float, kernel: str = "cube") -> np.ndarray:
+    """W(i,j) = 1[||n_i - n_j|| <= eps] (Eq. w; diagonal f(0) = 1), with the
+    L-infinity norm (kernel="cube") or the L2 norm (kernel="ball")."""
     X = np.asarray(points, dtype=np.float64)
-    d = np.abs(X[:, None, :] - X[None, :, :]).max(axis=2)
+    diff = X[:, None, :] - X[None, :, :]
+    d = np.linalg.norm(diff, axis=2) if kernel == "ball" else np.abs(diff).max(axis=2)
     return (d <= eps).astype(np.float64)
 
 

@@ -19,7 +19,7 @@ import numpy as np
 __all__ = [
     "RFD_OK", "RFD_EINVAL", "RFD_ENOMEM", "RFD_ECUDA", "RFD_ENOTREADY", "RFD_ETIMEDOUT", "RFD_ENUMERIC",
     "RFD_EBUSY", "RFD_ENOTSUP", "RFD_FP32_PLAIN", "RFD_BF16_TC", "RfdError", "rfd_params", "rfd_stats",
-    "lib", "lib_path", "rfd_sample_frequencies", "rfd_plan", "rfd_plan_destroy", "rfd_features",
+    "lib", "lib_path", "rfd_sample_frequencies", "rfd_sample_weights", "RFD_KERNEL_CUBE", "RFD_KERNEL_BALL", "rfd_plan", "rfd_plan_destroy", "rfd_features",
     "rfd_integrate", "rfd_gfi", "rfd_phi1", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
     "rfd_version", "RFD_FLAG_TIMING", "STEP_NAMES", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "Plan", "Batch", "rfd_batch_item", "HEADER_SYMBOLS",
     "RFD_FLAG_NATIVE_FP64", "RFD_FLAG_GRAPH", "RFD_FLAG_AUTOTUNE", "Server", "rfd_request", "rfd_result", "rfd_server_config",
@@ -38,7 +38,11 @@ class rfd_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int32), ("max_channels", ctypes.c_int32),
                 ("eps", ctypes.c_double), ("lambda_", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("precision", ctypes.c_int32), ("flags", ctypes.c_int32), ("freq_sigma", ctypes.c_double),
-                ("freq_radius", ctypes.c_double)]
+                ("freq_radius", ctypes.c_double), ("kernel", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+
+
+RFD_KERNEL_CUBE, RFD_KERNEL_BALL = 0, 1  # rfd_kernel: the eps-NN threshold function
+KERNELS = {"cube": RFD_KERNEL_CUBE, "ball": RFD_KERNEL_BALL}
 
 
 RFD_FLAG_TIMING = 1
@@ -107,6 +111,7 @@ def _load():
     DP = ctypes.POINTER(ctypes.c_double)
     sig = {
         "rfd_sample_frequencies": (I32, [I32, D, U64, D, D, DP, DP]),
+        "rfd_sample_weights": (I32, [I32, D, U64, D, D, I32, DP, DP]),
         "rfd_plan": (I32, [ctypes.POINTER(rfd_params), P, ctypes.POINTER(P)]),
         "rfd_plan_destroy": (I32, [P]),
         "rfd_features": (I32, [P, P]),
@@ -146,7 +151,7 @@ def _load():
 lib = _load()
 
 # Every function include/rfd.h and include/rfd_testing.h declare (checked against the headers by a test).
-HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
+HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_sample_weights", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
                   "rfd_gfi", "rfd_phi1", "rfd_phi1_noalloc", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
                   "rfd_version", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "rfd_batch_create",
                   "rfd_batch_destroy", "rfd_batch_features", "rfd_batch_integrate", "rfd_batch_gfi",
@@ -186,10 +191,21 @@ def rfd_sample_frequencies(m: int, eps: float, seed: int, freq_sigma: float = 0.
     return om, r
 
 
+def rfd_sample_weights(m: int, eps: float, seed: int, freq_sigma: float = 0.0, freq_radius: float = 0.0,
+                       kernel: str = "cube"):
+    """Step a1 for the threshold function `kernel` ("cube" or "ball"): (omega, r)."""
+    om = np.zeros((m // 2, 3), dtype=np.float64)
+    r = np.zeros(m // 2, dtype=np.float64)
+    _check(lib.rfd_sample_weights(m, eps, seed, freq_sigma, freq_radius, KERNELS[kernel],
+                                  om.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  r.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "rfd_sample_weights")
+    return om, r
+
+
 def rfd_plan(n, m, eps, lam, seed=0, max_channels=3, precision=RFD_BF16_TC, stream=None, freq_sigma=0.0,
-             freq_radius=0.0, flags=0) -> int:
+             freq_radius=0.0, flags=0, kernel="cube") -> int:
     p = rfd_params(n=n, m=m, max_channels=max_channels, eps=eps, lambda_=lam, seed=seed, precision=precision,
-                   flags=flags, freq_sigma=freq_sigma, freq_radius=freq_radius)
+                   flags=flags, freq_sigma=freq_sigma, freq_radius=freq_radius, kernel=KERNELS[kernel])
     h = ctypes.c_void_p()
     _check(lib.rfd_plan(ctypes.byref(p), stream, ctypes.byref(h)), "rfd_plan")
     return h.value
@@ -273,13 +289,13 @@ class Plan:
     """
 
     def __init__(self, n, m, eps, lam, seed=0, max_channels=3, precision=RFD_BF16_TC, stream=None,
-                 freq_sigma=0.0, freq_radius=0.0, timing=False, native_fp64=False, autotune=False):
+                 freq_sigma=0.0, freq_radius=0.0, timing=False, native_fp64=False, autotune=False, kernel="cube"):
         self.n, self.m, self.max_channels = int(n), int(m), int(max_channels)
         self.handle = None
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
         self.handle = rfd_plan(n, m, eps, lam, seed, max_channels, precision, s, freq_sigma, freq_radius,
                                (RFD_FLAG_TIMING if timing else 0) | (RFD_FLAG_NATIVE_FP64 if native_fp64 else 0) |
-                               (RFD_FLAG_AUTOTUNE if autotune else 0))
+                               (RFD_FLAG_AUTOTUNE if autotune else 0), kernel)
 
     @staticmethod
     def _chk(t, shape_last=None):

@@ -611,6 +611,8 @@ rfd_status plan_prepare(const rfd_params& p, cudaStream_t stream, rfd_plan_s** o
   if (p.flags & ~(RFD_FLAG_TIMING | RFD_FLAG_NATIVE_FP64 | RFD_FLAG_AUTOTUNE))
     return fail(RFD_EINVAL, "unknown bits in flags");
   if (p.n > (int64_t)1 << 31) return fail(RFD_EINVAL, "n must be < 2^31");
+  if (p.kernel != RFD_KERNEL_CUBE && p.kernel != RFD_KERNEL_BALL) return fail(RFD_EINVAL, "unknown kernel");
+  if (p.reserved_ != 0) return fail(RFD_EINVAL, "rfd_params.reserved_ must be 0");
   auto* pl = new (std::nothrow) rfd_plan_s();
   if (!pl) return fail(RFD_ENOMEM, "host allocation failed");
   pl->p = p;
@@ -625,7 +627,7 @@ rfd_status plan_prepare(const rfd_params& p, cudaStream_t stream, rfd_plan_s** o
   pl->cpad = (int)round_up(pl->fsplit ? 2 * p.max_channels : p.max_channels, 16);
   pl->omega.resize((size_t)pl->h * 3);
   pl->r.resize(pl->h);
-  rfd_status st = sample_frequencies_host(p.m, p.eps, p.seed, p.freq_sigma, p.freq_radius, pl->omega.data(),
+  rfd_status st = sample_frequencies_host(p.m, p.eps, p.seed, p.freq_sigma, p.freq_radius, p.kernel, pl->omega.data(),
                                           pl->r.data());
   if (st != RFD_OK) {
     delete pl;

@@ -8,9 +8,14 @@
 // of this stream agree bit for bit except when u2 falls within an ulp of the
 // acceptance threshold.
 //
-// tau is the Fourier transform of the L-infinity cube indicator
-// 1[||z||_inf <= eps] with the 2 pi convention of Sec. 2.4:
-// tau(w) = prod_d sin(2 pi eps w_d) / (pi w_d), 2 eps at w_d = 0.
+// tau is the Fourier transform of the eps-NN threshold function f with the
+// 2 pi convention of Sec. 2.4 (f(z) = int exp(2 pi i w.z) tau(w) dw):
+//  - the L-infinity cube 1[||z||_inf <= eps]:
+//    tau(w) = prod_d sin(2 pi eps w_d) / (pi w_d), 2 eps at w_d = 0;
+//  - the L2 ball 1[||z||_2 <= eps] (the Bessel-function case of Sec. 2.4):
+//    tau(w) = int_{|z| <= eps} cos(2 pi w.z) dz = 4 pi (sin x - x cos x) / q^3,
+//    q = 2 pi |w|, x = q eps (4 pi eps^3 / 3 at w = 0; a series below x = 0.1,
+//    where sin x - x cos x cancels).
 //
 // This file must be compiled without floating-point contraction
 // (-ffp-contract=off) so that R (2 u1 - 1) is two rounded operations.
@@ -49,6 +54,19 @@ double sinc_cube(double w, double eps) {  // one coordinate of tau
   return std::sin(2.0 * kPi * eps * w) / (kPi * w);
 }
 
+double tau_ball(const double (&w)[3], double eps) {
+  const double q = 2.0 * kPi * std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  const double x = q * eps;
+  if (x < 0.1) {
+    // (sin x - x cos x) / x^3 = sum_k (-1)^k x^(2k) / ((2k+1)! (2k+3)) ... written out to x^10
+    const double x2 = x * x;
+    const double s = 1.0 / 3.0 - x2 * (1.0 / 30.0 - x2 * (1.0 / 840.0 - x2 * (1.0 / 45360.0 -
+                     x2 * (1.0 / 3991680.0 - x2 / 518918400.0))));
+    return 4.0 * kPi * eps * eps * eps * s;
+  }
+  return 4.0 * kPi * (std::sin(x) - x * std::cos(x)) / (q * q * q);
+}
+
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -62,8 +80,9 @@ double default_sigma(double eps) { return 1.0 / (2.0 * eps); }
 double default_radius(double eps) { return 1.0 / eps; }
 
 rfd_status sample_frequencies_host(int m, double eps, uint64_t seed, double sigma,
-                                   double radius, double* omega, double* r) {
+                                   double radius, int kernel, double* omega, double* r) {
   if (m < 2 || (m & 1)) return fail(RFD_EINVAL, "m must be even and >= 2");
+  if (kernel != RFD_KERNEL_CUBE && kernel != RFD_KERNEL_BALL) return fail(RFD_EINVAL, "unknown kernel");
   if (!(eps > 0.0) || !std::isfinite(eps)) return fail(RFD_EINVAL, "eps must be finite and > 0");
   if (sigma == 0.0) sigma = default_sigma(eps);
   if (radius == 0.0) radius = default_radius(eps);
@@ -94,10 +113,11 @@ rfd_status sample_frequencies_host(int m, double eps, uint64_t seed, double sigm
     if (r) {
       double tau = 1.0, p = 1.0;
       for (int d = 0; d < 3; ++d) {
-        tau *= sinc_cube(w3[d], eps);
+        if (kernel == RFD_KERNEL_CUBE) tau *= sinc_cube(w3[d], eps);
         const double a = w3[d] / sigma;
         p *= std::exp(-0.5 * a * a) / norm;
       }
+      if (kernel == RFD_KERNEL_BALL) tau = tau_ball(w3, eps);
       r[j] = tau / p;
     }
   }
@@ -108,5 +128,10 @@ rfd_status sample_frequencies_host(int m, double eps, uint64_t seed, double sigm
 
 extern "C" rfd_status rfd_sample_frequencies(int32_t m, double eps, uint64_t seed, double freq_sigma,
                                              double freq_radius, double* omega_out, double* r_out) {
-  return rfd::sample_frequencies_host(m, eps, seed, freq_sigma, freq_radius, omega_out, r_out);
+  return rfd::sample_frequencies_host(m, eps, seed, freq_sigma, freq_radius, RFD_KERNEL_CUBE, omega_out, r_out);
+}
+
+extern "C" rfd_status rfd_sample_weights(int32_t m, double eps, uint64_t seed, double freq_sigma, double freq_radius,
+                                         int32_t kernel, double* omega_out, double* r_out) {
+  return rfd::sample_frequencies_host(m, eps, seed, freq_sigma, freq_radius, kernel, omega_out, r_out);
 }

@@ -13,9 +13,10 @@ void set_error(const std::string& msg);
 rfd_status fail(rfd_status st, const std::string& msg);
 
 // Step a1 on the host (Sec. 2.4): frequencies from the truncated Gaussian and
-// weights r = tau/p.  Returns RFD_OK or RFD_EINVAL.
+// weights r = tau/p for the threshold function `kernel` (rfd_kernel).
+// Returns RFD_OK or RFD_EINVAL.
 rfd_status sample_frequencies_host(int m, double eps, uint64_t seed, double sigma,
-                                   double radius, double* omega, double* r);
+                                   double radius, int kernel, double* omega, double* r);
 double default_sigma(double eps);
 double default_radius(double eps);
 

@@ -25,7 +25,8 @@ def _cuda(x):
     return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
 
 
-def gpu_gfi(pts, F, eps, lam, m, seed, precision, *, api="gfi", max_channels=None, ld=None, inplace=False):
+def gpu_gfi(pts, F, eps, lam, m, seed, precision, *, api="gfi", max_channels=None, ld=None, inplace=False,
+            kernel="cube"):
     n, c = F.shape
     ld = ld or c
     Fp = np.zeros((n, ld), np.float32)
@@ -33,7 +34,7 @@ def gpu_gfi(pts, F, eps, lam, m, seed, precision, *, api="gfi", max_channels=Non
     P, Ft = _cuda(pts), _cuda(Fp)
     out = Ft if inplace else torch.full((n, ld), float("nan"), device=DEV)
     plan = rfd.Plan(n, m, eps, lam, seed, max_channels=max_channels or c, precision=precision,
-                    stream=torch.cuda.current_stream(DEV))
+                    stream=torch.cuda.current_stream(DEV), kernel=kernel)
     try:
         if api == "gfi":
             rfd.rfd_gfi(plan.handle, P, Ft, c, ld, out, ld)
@@ -172,6 +173,22 @@ def test_torus_config(prec):
     err = oracle.rel_frobenius(out, ref)
     print(f"torus N={spec.n} m={spec.m} c={spec.c} prec={prec} err={err:.3e} stats={stats}")
     assert err <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", ["small", "torus"])
+def test_ball_kernel_matches_oracle(prec, name):
+    """The L2-ball threshold function (tau = the ball's Fourier transform, the
+    Bessel case of Sec. 2.4): only step a1's weights change; the whole path
+    against the oracle with the same kernel."""
+    spec, pts, F, lam = small_case(name)
+    ref, parts = oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, return_parts=True, kernel="ball")
+    out, stats, (om, r, G) = gpu_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, prec, kernel="ball")
+    err = oracle.rel_frobenius(out, ref)
+    print(f"ball {name} precision {prec}: rel err {err:.3e}, inc {oracle.rel_frobenius(F, ref):.3e}")
+    assert err <= TOL[prec]
+    np.testing.assert_array_equal(om, parts["omega"])
+    np.testing.assert_allclose(r, parts["r"], rtol=1e-13)
 
 
 def test_invalid_arguments_and_alloc_failure():
