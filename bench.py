@@ -34,6 +34,7 @@ import synth  # noqa: E402
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (profiling recipe's table); a DFMA probe measured ~1.0
 MUFU_PER_SM_CLK = 16            # sin or cos results per SM per clock (SFU)
+GRAM_DRAM_BYTES_PER_BLOCK = 548.98e6 / 4096  # Gram kernel DRAM bytes per 64-point block, m = 1024 (ncu)
 
 
 def load_peaks():
@@ -64,6 +65,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the serving trace (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the reductions' default launch parameters (a fixed launch sequence for profiling)")
     ap.add_argument("--sections", default="main,batched,serving",
                     help="comma list of main, batched, serving (profiling runs select one; the JSON line then "
                          "carries only what ran)")
@@ -417,7 +420,7 @@ def main():
     out = torch.empty_like(Ft)
     prec = rfd.RFD_BF16_TC if args.precision == "bf16" else rfd.RFD_FP32_PLAIN
     plan = rfd.Plan(n, m, spec.eps, lam, spec.seed, max_channels=c, precision=prec, stream=stream, timing=True,
-                    autotune=(prec == rfd.RFD_BF16_TC))
+                    autotune=(prec == rfd.RFD_BF16_TC and not args.no_autotune))
 
     for _ in range(args.warmup):
         plan.gfi(P, Ft, out)
@@ -539,7 +542,17 @@ def main():
     # the dominant single kernel: the Gram kernel is one launch per step (the phi1 step is ~50 launches)
     roof = {k: v for k, v in step_roof["gram"].items() if k != "work"}
     roof["kernel"] = "gram_tc_kernel (step a3)"
+    # DRAM bytes of the Gram kernel per 64-point block of the feature matrix, from one ncu capture
+    # (profiles/gram_tc_262k_m1024.md: dram__bytes_read.sum + dram__bytes_write.sum = 548.98 MB over
+    # 4096 blocks at m = 1024, field rows padded to 16); the kernel reads the matrix once, so the
+    # bytes scale with the blocks a launch covers.  Null for other shapes.
     roof["traffic"] = None
+    cpad = -(-min(2 * c, 256) // 16) * 16 if prec == rfd.RFD_BF16_TC and 2 * c <= 256 else None
+    if prec == rfd.RFD_BF16_TC and m == 1024 and cpad == 16:
+        nblocks = -(-n // 128) * 2  # points padded to 128, blocks of 64
+        phase = st["tune_phase_blocks"] or 4096
+        launches = -(-nblocks // phase)
+        roof["traffic"] = GRAM_DRAM_BYTES_PER_BLOCK * nblocks / launches
     roof["peak_source"] = f"{peak_src} (sustained bf16)"
     roof["dominant_step"] = dom
     # whole-path roofline: slower of HBM bytes at peak bandwidth and tensor flops at peak
