@@ -29,10 +29,14 @@ RFD_HD constexpr uint32_t modulus(int j) {
        : j == 12 ? 199u : j == 13 ? 197u : j == 14 ? 193u : 191u;
 }
 
-// Reconstruction constants: with M_j = P / p_j and w_j = M_j^-1 mod p_j,
-// W_j = M_j w_j < P satisfies W_j = 1 (mod p_j) and 0 (mod p_i, i != j), so
-// C = sum_j r_j W_j (mod P); and sum_j r_j W_j / P = sum_j r_j w_j / p_j exactly.
+// Reconstruction constants for the first nmod moduli (P = their product): with
+// M_j = P / p_j and w_j = M_j^-1 mod p_j, W_j = M_j w_j < P satisfies
+// W_j = 1 (mod p_j) and 0 (mod p_i, i != j), so C = sum_j r_j W_j (mod P); and
+// sum_j r_j W_j / P = sum_j r_j w_j / p_j exactly.  Entries j >= nmod are zero,
+// so a residue there contributes nothing.
 struct Constants {
+  int32_t nmod;            // moduli in use (the first nmod of modulus())
+  int32_t pad_;
   uint32_t W[kNumMod][4];  // W_j, 32-bit words from the least significant
   uint32_t P[4];           // P, 32-bit words
   float c[kNumMod];        // w_j / p_j (rounded to FP32)
@@ -42,10 +46,12 @@ struct Constants {
 
 // Computed once on the host (128-bit integer arithmetic).  Returns false if the
 // moduli were not pairwise coprime (no inverse).
-inline bool make_constants(Constants* out) {
+inline bool make_constants(Constants* out, int nmod = kNumMod) {
+  *out = Constants{};
+  out->nmod = nmod;
   unsigned __int128 P = 1;
-  for (int j = 0; j < kNumMod; ++j) P *= modulus(j);
-  for (int j = 0; j < kNumMod; ++j) {
+  for (int j = 0; j < nmod; ++j) P *= modulus(j);
+  for (int j = 0; j < nmod; ++j) {
     const uint32_t p = modulus(j);
     const unsigned __int128 Mj = P / p;
     const uint32_t mj = (uint32_t)(Mj % p);
@@ -66,12 +72,13 @@ inline bool make_constants(Constants* out) {
   return true;
 }
 
-// Bits of the scaled integers for a contraction of length K: the largest k <= 57
-// with K 2^(2k) <= P / 2, so that |C| < K 2^(2k) stays inside the symmetric
-// range of the residues (k = 57 up to K = 1024, 56 up to K = 4096).
-inline int kbits(int K) {
+// Bits of the scaled integers for a contraction of length K over the first nmod
+// moduli: the largest k <= 57 with K 2^(2k) <= P / 2, so that |C| < K 2^(2k)
+// stays inside the symmetric range of the residues (all 16 moduli: k = 57 up to
+// K = 1024, 56 up to K = 4096).  0 if none.
+inline int kbits(int K, int nmod = kNumMod) {
   unsigned __int128 P = 1;
-  for (int j = 0; j < kNumMod; ++j) P *= modulus(j);
+  for (int j = 0; j < nmod; ++j) P *= modulus(j);
   for (int k = kMaxKBits; k > 0; --k)
     if (((unsigned __int128)(uint64_t)K << (2 * k)) <= P / 2) return k;
   return 0;
@@ -159,12 +166,13 @@ RFD_HD void fold_columns(unsigned long long t0, unsigned long long t1, unsigned 
 // 16 2^8 2^32 = 2^44) and q = the integer nearest to S / P; the signed result
 // C = S - q P (mod 2^128) is exact whenever |C| < P / 2 (the FP32 sum for q
 // errs by < 0.01, far inside the margin |C / P| <= 0.44).
+template <int NM = kNumMod>
 RFD_HD void reconstruct(const uint32_t (&r)[kNumMod], const Constants& cc, unsigned long long* lo_out,
                         unsigned long long* hi_out) {
   unsigned long long t0 = 0, t1 = 0, t2 = 0, t3 = 0;
   float qf = 0.f;
 #pragma unroll
-  for (int j = 0; j < kNumMod; ++j) {
+  for (int j = 0; j < NM; ++j) {  // the first NM moduli (cc.nmod == NM, or W_j = 0 beyond cc.nmod)
     const unsigned long long rj = r[j];
     t0 += rj * cc.W[j][0];
     t1 += rj * cc.W[j][1];

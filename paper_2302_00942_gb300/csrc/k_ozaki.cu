@@ -68,13 +68,17 @@ constexpr int kColSplitK = 64;   // K rows per block of the column split
 constexpr int kRowSeg = 256;     // columns per warp of the row split
 constexpr int kChunksPerSeg = crt::kSegK / kBK;
 
-const crt::Constants& constants() {
-  static const crt::Constants c = [] {  // once per process (thread-safe initialisation)
-    crt::Constants v{};
-    crt::make_constants(&v);
+// reconstruction constants for the first nmod moduli, nmod = 1..16
+struct ConstantSets {
+  crt::Constants c[kNumMod + 1];
+};
+const crt::Constants& constants(int nmod = kNumMod) {
+  static const ConstantSets sets = [] {  // once per process (thread-safe initialisation)
+    ConstantSets v{};
+    for (int n = 1; n <= kNumMod; ++n) crt::make_constants(&v.c[n], n);
     return v;
   }();
-  return c;
+  return sets.c[nmod < 1 ? 1 : (nmod > kNumMod ? kNumMod : nmod)];
 }
 
 // Residues of 8 consecutive integers X[e] (limbs L[e]) modulo p_j, j = J .. 15,
@@ -86,14 +90,15 @@ __device__ __forceinline__ uint32_t bf16_pair(float lo, float hi) {
 }
 template <int J>
 __device__ __forceinline__ void store_residues8(const crt::Limbs (&L)[8], const long long (&X)[8],
-                                                __nv_bfloat16* dst, size_t plane) {
+                                                __nv_bfloat16* dst, size_t plane, int nmod) {
+  if (J >= nmod) return;  // planes of the moduli in use only
   uint4 w;
   w.x = bf16_pair(crt::residue<J>(L[0], X[0]), crt::residue<J>(L[1], X[1]));
   w.y = bf16_pair(crt::residue<J>(L[2], X[2]), crt::residue<J>(L[3], X[3]));
   w.z = bf16_pair(crt::residue<J>(L[4], X[4]), crt::residue<J>(L[5], X[5]));
   w.w = bf16_pair(crt::residue<J>(L[6], X[6]), crt::residue<J>(L[7], X[7]));
   *reinterpret_cast<uint4*>(dst + J * plane) = w;
-  if constexpr (J + 1 < kNumMod) store_residues8<J + 1>(L, X, dst, plane);
+  if constexpr (J + 1 < kNumMod) store_residues8<J + 1>(L, X, dst, plane, nmod);
 }
 
 // Row split of the row-major FP64 matrix X (rows x cols, ld) into the residue
@@ -107,16 +112,42 @@ __host__ __device__ __forceinline__ int row_split_lanes(int cols_pad) {
   return cols_pad <= 64 ? 8 : (cols_pad <= 128 ? 16 : 32);  // a power of two (the shuffle reduction)
 }
 __host__ __device__ __forceinline__ int row_split_segs(int cols_pad) { return (cols_pad + kRowSeg - 1) / kRowSeg; }
+// Largest biased exponent of row i (0: all entries zero or subnormal, or i >= rows)
+// into eraw[i]; one warp, the row's loads issued back to back.
+__device__ __forceinline__ void row_exponent_warp(const double* __restrict__ X, int ld, int rows, int cols,
+                                                  int* __restrict__ eraw, int i, int lane) {
+  int emax = 0;
+  if (i < rows) {
+    const double* row = X + (size_t)i * ld;
+    int k = lane;
+    for (; k + 7 * 32 < cols; k += 8 * 32) {
+      unsigned long long b[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) b[q] = (unsigned long long)__double_as_longlong(row[k + q * 32]);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) emax = max(emax, (int)((b[q] >> 52) & 0x7FF));
+    }
+    for (; k < cols; k += 32) emax = max(emax, (int)((__double_as_longlong(row[k]) >> 52) & 0x7FF));
+  }
+  for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+  if (lane == 0) eraw[i] = emax;
+}
+
+// eraw: the rows' largest biased exponents from row_exponent_warp, or null (taken here)
 __device__ __forceinline__ void split_rows_warp(const double* __restrict__ X, int ld, int rows, int cols,
-                                                int rows_pad, int cols_pad, int sh0,
-                                                __nv_bfloat16* __restrict__ res, int* __restrict__ exps, int w,
-                                                int lane) {
+                                                int rows_pad, int cols_pad, int sh0, int nmod,
+                                                __nv_bfloat16* __restrict__ res, int* __restrict__ exps,
+                                                const int* __restrict__ eraw, int w, int lane) {
   const int L = row_split_lanes(cols_pad), segs = row_split_segs(cols_pad);
   const int i = (w / segs) * (32 / L) + lane / L, seg = w % segs, sub = lane % L;
   int emax = 0;  // largest biased exponent in the row (0: all entries zero or subnormal)
-  if (i < rows)
-    for (int k = sub; k < cols; k += L) emax = max(emax, (int)((__double_as_longlong(X[(size_t)i * ld + k]) >> 52) & 0x7FF));
-  for (int off = L / 2; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+  if (eraw) {
+    if (i < rows) emax = eraw[i];
+  } else {
+    if (i < rows)
+      for (int k = sub; k < cols; k += L) emax = max(emax, (int)((__double_as_longlong(X[(size_t)i * ld + k]) >> 52) & 0x7FF));
+    for (int off = L / 2; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+  }
   if (emax == 0) emax = 1;  // subnormal-only rows: scale as the smallest normal binade
   if (sub == 0 && seg == 0 && i < rows_pad) exps[i] = emax - 1075 - sh0;
   const int k0 = seg * kRowSeg + sub * 8;
@@ -130,7 +161,7 @@ __device__ __forceinline__ void split_rows_warp(const double* __restrict__ X, in
     if (i < rows && k < cols) v[e] = crt::scaled_int((unsigned long long)__double_as_longlong(X[(size_t)i * ld + k]), emax, sh0);
     limbs[e] = crt::limbs_of(v[e]);
   }
-  store_residues8<0>(limbs, v, res + (size_t)i * cols_pad + k0, (size_t)rows_pad * cols_pad);
+  store_residues8<0>(limbs, v, res + (size_t)i * cols_pad + k0, (size_t)rows_pad * cols_pad, nmod);
 }
 __host__ __device__ __forceinline__ int row_split_warps(int rows_pad, int cols_pad) {
   return rows_pad / (32 / row_split_lanes(cols_pad)) * row_split_segs(cols_pad);
@@ -165,7 +196,7 @@ __device__ __forceinline__ void col_exponents(const double* __restrict__ B, int 
 // memory; thread t takes column t / 8 and 8 consecutive rows of K, so every
 // plane gets one 16-byte store per thread.  256 threads.
 __device__ __forceinline__ void split_cols(const double* __restrict__ B, int ld, int K, int N, int K_pad, int N_pad,
-                                           int sh0, __nv_bfloat16* __restrict__ res, int* __restrict__ exps,
+                                           int sh0, int nmod, __nv_bfloat16* __restrict__ res, int* __restrict__ exps,
                                            const int* __restrict__ part, int j0, int kr) {
   const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
   __shared__ double tile[kColSplitK][33];
@@ -194,7 +225,7 @@ __device__ __forceinline__ void split_cols(const double* __restrict__ B, int ld,
       v[q] = crt::scaled_int((unsigned long long)__double_as_longlong(tile[kg + q][col]), emax, sh0);
       limbs[q] = crt::limbs_of(v[q]);
     }
-    store_residues8<0>(limbs, v, res + (size_t)(j0 + col) * K_pad + k0 + kg, plane);
+    store_residues8<0>(limbs, v, res + (size_t)(j0 + col) * K_pad + k0 + kg, plane, nmod);
     __syncthreads();
   }
 }
@@ -465,10 +496,11 @@ __device__ __forceinline__ bool pow2_of(double alpha, int* k, bool* neg) {
 // alpha (A B)[i, j] from the residues r and the exponent e = ea_i + eb_j:
 // correctly rounded when alpha is a power of two and the result is a normal
 // double.
+template <int NM>
 __device__ __forceinline__ double product_entry(const crt::Constants& cc, const uint32_t (&r)[kNumMod], int e,
                                                 double alpha) {
   unsigned long long lo, hi;
-  crt::reconstruct(r, cc, &lo, &hi);
+  crt::reconstruct<NM>(r, cc, &lo, &hi);
   int ak = 0;
   bool aneg = false;
   double v;
@@ -483,12 +515,14 @@ __device__ __forceinline__ double product_entry(const crt::Constants& cc, const 
 
 // D[i, j0 .. j0 + 3] (columns < ncols) = alpha (A B) + beta C + diag I from
 // the residue planes (one 4-byte load per plane; res_row = row i of plane 0).
+template <int NM>
 __device__ __forceinline__ void combine4(const crt::Constants& cc, const uint8_t* __restrict__ res_row, size_t plane,
                                          int i, int j0, int ncols, int ea_i, const int* __restrict__ eb,
                                          double alpha, double beta, const double* C, double* D, double diag) {
   uint32_t w[kNumMod];
 #pragma unroll
-  for (int j = 0; j < kNumMod; ++j) w[j] = __ldg(reinterpret_cast<const uint32_t*>(res_row + j * plane + j0));
+  for (int j = 0; j < kNumMod; ++j)  // the first NM moduli are in use (cc.nmod == NM)
+    w[j] = j < NM ? __ldg(reinterpret_cast<const uint32_t*>(res_row + j * plane + j0)) : 0u;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int jj = j0 + q;
@@ -496,7 +530,7 @@ __device__ __forceinline__ void combine4(const crt::Constants& cc, const uint8_t
     uint32_t r[kNumMod];
 #pragma unroll
     for (int j = 0; j < kNumMod; ++j) r[j] = (w[j] >> (8 * q)) & 0xFFu;
-    double v = product_entry(cc, r, ea_i + eb[jj], alpha);
+    double v = product_entry<NM>(cc, r, ea_i + eb[jj], alpha);
     if (beta != 0.0) v = fma(beta, C[jj], v);
     if (i == jj) v += diag;
     D[jj] = v;
@@ -505,15 +539,25 @@ __device__ __forceinline__ void combine4(const crt::Constants& cc, const uint8_t
 
 // ---- batched kernels (one table entry per cloud, slots resolved per call) ----
 
-// Row split of the A operand, every cloud (warp prefix over ozaki_row_split_warps(m)).
+// Row split of the A operand, every cloud (warp prefix over ozaki_row_split_warps(m)),
+// from the row exponents of the exponent pass.
 __device__ __forceinline__ void bsplit_rows_warp(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix,
-                                                 int count, int slot, int mask_k, int wg, int lane) {
+                                                 int count, int slot, int nmod, int mask_k, int wg, int lane) {
   if (wg >= __ldg(prefix + count)) return;
   const int j = find_job(prefix, count, wg);
   const PhiCloud pc = pcs[j];
   if (mask_k >= 0 && pc.s <= mask_k) return;
-  split_rows_warp(pc_slot(pc, slot), pc.m, pc.m, pc.m, pc.mpa, pc.kp, pc.kbits - 53,
-                  reinterpret_cast<__nv_bfloat16*>(pc.sa), pc.ea, wg - prefix[j], lane);
+  split_rows_warp(pc_slot(pc, slot), pc.m, pc.m, pc.m, pc.mpa, pc.kp, pc.kbits_n[nmod - 1] - 53, nmod,
+                  reinterpret_cast<__nv_bfloat16*>(pc.sa), pc.ea, pc.eap, wg - prefix[j], lane);
+}
+// Row exponents of the A operand: one warp per padded row (block b: 8 rows; prefix over mpa / 8 blocks).
+__device__ __forceinline__ void brow_exponents_block(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix,
+                                                     int count, int slot, int mask_k, int b) {
+  const int jc = find_job(prefix, count, b);
+  const PhiCloud pc = pcs[jc];
+  if (mask_k >= 0 && pc.s <= mask_k) return;
+  row_exponent_warp(pc_slot(pc, slot), pc.m, pc.m, pc.m, pc.eap, (b - prefix[jc]) * 8 + (threadIdx.x >> 5),
+                    threadIdx.x & 31);
 }
 // Column exponents of the B operand: one block per strip of 32 columns and
 // range of 64 rows of K (prefix over strips x ranges per cloud).
@@ -525,32 +569,35 @@ __device__ __forceinline__ void bcol_exponents_block(const PhiCloud* __restrict_
   const int nranges = pc.kp / kColSplitK, local = b - prefix[jc];
   col_exponents(pc_slot(pc, slot), pc.m, pc.m, pc.m, pc.mpb, pc.ebp, (local / nranges) * 32, local % nranges);
 }
-__global__ void bsplit_rows_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
-                                   int slot, int mask_k) {
-  bsplit_rows_warp(pcs, prefix, count, slot, mask_k, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31);
-}
-__global__ void bcol_exponents_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
-                                      int slot, int mask_k) {
-  bcol_exponents_block(pcs, prefix, count, slot, mask_k, blockIdx.x);
-}
-// both in one launch (independent work): blocks [0, row_blocks) split A, the rest take B's exponents
-__global__ void bsplit_rows_col_exponents_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ row_prefix,
-                                                 const int* __restrict__ strip_prefix, int count, int a_slot,
-                                                 int b_slot, int mask_k, int row_blocks) {
+// The exponent pass of a product: blocks [0, row_blocks) take A's row exponents
+// (a_slot >= 0 ... when split), the rest B's column exponents.  256 threads.
+__global__ void bexponents_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ rexp_prefix,
+                                  const int* __restrict__ strip_prefix, int count, int a_slot, int b_slot, int mask_k,
+                                  int row_blocks) {
   if ((int)blockIdx.x < row_blocks)
-    bsplit_rows_warp(pcs, row_prefix, count, a_slot, mask_k, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                     threadIdx.x & 31);
+    brow_exponents_block(pcs, rexp_prefix, count, a_slot, mask_k, blockIdx.x);
   else
     bcol_exponents_block(pcs, strip_prefix, count, b_slot, mask_k, blockIdx.x - row_blocks);
 }
-__global__ void bsplit_cols_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
-                                   int slot, int mask_k) {
-  const int jc = find_job(prefix, count, blockIdx.x);
+__device__ __forceinline__ void bsplit_cols_block(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix,
+                                                  int count, int slot, int nmod, int mask_k, int b) {
+  const int jc = find_job(prefix, count, b);
   const PhiCloud pc = pcs[jc];
   if (mask_k >= 0 && pc.s <= mask_k) return;
-  const int nranges = pc.kp / kColSplitK, local = blockIdx.x - prefix[jc];
-  split_cols(pc_slot(pc, slot), pc.m, pc.m, pc.m, pc.kp, pc.mpb, pc.kbits - 53,
+  const int nranges = pc.kp / kColSplitK, local = b - prefix[jc];
+  split_cols(pc_slot(pc, slot), pc.m, pc.m, pc.m, pc.kp, pc.mpb, pc.kbits_n[nmod - 1] - 53, nmod,
              reinterpret_cast<__nv_bfloat16*>(pc.sb), pc.eb, pc.ebp, (local / nranges) * 32, local % nranges);
+}
+// The split pass of a product: blocks [0, row_blocks) split A's rows (8 warps
+// each), the rest B's columns.  256 threads.
+__global__ void bsplit_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ row_prefix,
+                              const int* __restrict__ strip_prefix, int count, int a_slot, int b_slot, int nmod,
+                              int mask_k, int row_blocks) {
+  if ((int)blockIdx.x < row_blocks)
+    bsplit_rows_warp(pcs, row_prefix, count, a_slot, nmod, mask_k, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                     threadIdx.x & 31);
+  else
+    bsplit_cols_block(pcs, strip_prefix, count, b_slot, nmod, mask_k, blockIdx.x - row_blocks);
 }
 
 template <int CL>
@@ -558,8 +605,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 bresidue_gemm_kernel(const CUtensorMap* __restrict__ maps, const OzTile* __restrict__ tiles, int num_tiles,
                      const PhiCloud* __restrict__ pcs, const __grid_constant__ crt::Constants cc, int stages,
                      int stage_bytes, int mask_k, int* err) {
+  const int nmod = cc.nmod;
+  // item a = (tile a / nmod, modulus a mod nmod): the moduli in use only, spread over the clusters
   auto item_of = [&](int it) {
-    const OzTile t = tiles[it];
+    const OzTile t = tiles[it / nmod];
     const PhiCloud& pc = pcs[t.cloud];
     Item I;
     I.ma = maps + pc.map_a;
@@ -571,18 +620,19 @@ bresidue_gemm_kernel(const CUtensorMap* __restrict__ maps, const OzTile* __restr
     I.m0 = t.m0;
     I.n0 = t.n0;
     I.nb = t.nb;
-    I.g0 = t.g0;
-    I.G = t.ng;
+    I.g0 = it % nmod;
+    I.G = 1;
     I.skip = mask_k >= 0 && pc.s <= mask_k;
     return I;
   };
-  residue_gemm_core<CL>(item_of, num_tiles, cc, stages, stage_bytes, err);
+  residue_gemm_core<CL>(item_of, num_tiles * nmod, cc, stages, stage_bytes, err);
 }
 
 // D = alpha A B + beta C + diag I, one thread per 4 consecutive entries of a
 // row (prefix over blocks of 256 such groups per cloud, m ceil(m / 4) groups).
 // A cloud with s <= mask_k skipped the product: its D becomes a copy of C (if
 // any).
+template <int NM>
 __global__ void bcombine_product_kernel(const PhiCloud* __restrict__ pcs, const int* __restrict__ prefix, int count,
                                         const __grid_constant__ crt::Constants cc, int c_slot, int d_slot,
                                         double alpha, double beta, double diag, int mask_k) {
@@ -599,7 +649,7 @@ __global__ void bcombine_product_kernel(const PhiCloud* __restrict__ pcs, const 
       for (int j = j0; j < min(m, j0 + 4); ++j) D[j] = C[j];
     return;
   }
-  combine4(cc, pc.res + (size_t)i * pc.mpb, (size_t)pc.mpa * pc.mpb, i, j0, m, pc.ea[i], pc.eb, alpha, beta, C, D,
+  combine4<NM>(cc, pc.res + (size_t)i * pc.mpb, (size_t)pc.mpa * pc.mpb, i, j0, m, pc.ea[i], pc.eb, alpha, beta, C, D,
            diag);
 }
 
@@ -609,7 +659,7 @@ __global__ void split_rows_kernel(const double* __restrict__ X, int ld, int rows
                                   int cols_pad, int sh0, __nv_bfloat16* __restrict__ res, int* __restrict__ exps) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= row_split_warps(rows_pad, cols_pad)) return;
-  split_rows_warp(X, ld, rows, cols, rows_pad, cols_pad, sh0, res, exps, warp, lane);
+  split_rows_warp(X, ld, rows, cols, rows_pad, cols_pad, sh0, kNumMod, res, exps, nullptr, warp, lane);
 }
 
 __global__ void col_exponents_kernel(const double* __restrict__ B, int ld, int K, int N, int N_pad,
@@ -618,7 +668,7 @@ __global__ void col_exponents_kernel(const double* __restrict__ B, int ld, int K
 }
 __global__ void split_cols_kernel(const double* __restrict__ B, int ld, int K, int N, int K_pad, int N_pad, int sh0,
                                   __nv_bfloat16* __restrict__ res, int* __restrict__ exps, const int* __restrict__ part) {
-  split_cols(B, ld, K, N, K_pad, N_pad, sh0, res, exps, part, blockIdx.x * 32, blockIdx.y);
+  split_cols(B, ld, K, N, K_pad, N_pad, sh0, kNumMod, res, exps, part, blockIdx.x * 32, blockIdx.y);
 }
 
 // items (row tile of 128 CL, column tile of 256, modulus), one modulus each
@@ -656,7 +706,7 @@ __global__ void combine_product_kernel(const __grid_constant__ crt::Constants cc
   if (g >= (int64_t)M * gpr) return;
   const int i = (int)(g / gpr), j0 = (int)(g % gpr) * 4;
   double* Ci = C + (size_t)i * ldc;
-  combine4(cc, res + (size_t)i * np, (size_t)mp * np, i, j0, N, ea[i], eb, alpha, beta, Ci, Ci, 0.0);
+  combine4<kNumMod>(cc, res + (size_t)i * np, (size_t)mp * np, i, j0, N, ea[i], eb, alpha, beta, Ci, Ci, 0.0);
 }
 
 }  // namespace
@@ -756,10 +806,10 @@ void ozaki_batch_tiles(const std::vector<int>& ms, int sms, std::vector<OzTile>*
       for (int n0 = 0; n0 < L.np; n0 += kBNMax) {
         const int nb = std::min(kBNMax, L.np - n0);
         nb_max = std::max(nb_max, nb);
-        for (int g = 0; g < kNumMod; ++g) out->push_back(OzTile{k, m0, n0, nb, L.kp, g, 1, 0});
+        out->push_back(OzTile{k, m0, n0, nb, L.kp, 0, kNumMod, 0});
       }
   }
-  // longest items first: the persistent CTAs take them round robin
+  // longest tiles first: the persistent CTAs take their (tile, modulus) items round robin
   std::stable_sort(out->begin(), out->end(),
                    [](const OzTile& a, const OzTile& b) { return (int64_t)a.nb * a.kp > (int64_t)b.nb * b.kp; });
   *stage_bytes = kABytes + nb_max * kBK * 2;
@@ -769,53 +819,65 @@ void ozaki_batch_tiles(const std::vector<int>& ms, int sms, std::vector<OzTile>*
 namespace {
 // grid-stride launch of the batched residue GEMM over its items
 cudaError_t launch_bresidue(const void* maps_dev, const OzTile* tiles, int num_tiles, const PhiCloud* pc,
-                            int stage_bytes, int cluster, int mask_k, int* err, cudaStream_t st) {
+                            int stage_bytes, int cluster, int nmod, int mask_k, int* err, cudaStream_t st) {
   const int stages = stages_for(stage_bytes);
   if (stages == 0) return cudaErrorInvalidValue;
   const int smem = stages * stage_bytes + kSmemExtra;
   const auto* maps = static_cast<const CUtensorMap*>(maps_dev);
   if (cluster == 2)
-    return launch_persistent<2>(bresidue_gemm_kernel<2>, num_tiles, smem, st, maps, tiles, num_tiles, pc, constants(),
-                                stages, stage_bytes, mask_k, err);
-  return launch_persistent<1>(bresidue_gemm_kernel<1>, num_tiles, smem, st, maps, tiles, num_tiles, pc, constants(),
-                              stages, stage_bytes, mask_k, err);
+    return launch_persistent<2>(bresidue_gemm_kernel<2>, num_tiles * nmod, smem, st, maps, tiles, num_tiles, pc,
+                                constants(nmod), stages, stage_bytes, mask_k, err);
+  return launch_persistent<1>(bresidue_gemm_kernel<1>, num_tiles * nmod, smem, st, maps, tiles, num_tiles, pc,
+                              constants(nmod), stages, stage_bytes, mask_k, err);
 }
 }  // namespace
 
-int ozaki_kbits(int K) { return crt::kbits(K); }
+int ozaki_kbits(int K, int nmod) { return crt::kbits(K, nmod); }
 
-cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* strip_prefix,
+int ozaki_moduli_for_bits(int K, int k) {
+  for (int n = 1; n <= kNumMod; ++n)
+    if (crt::kbits(K, n) >= k) return n;
+  return kNumMod;
+}
+
+namespace {
+// the reconstruction kernel specialised for the moduli count in use (1 .. 16)
+template <int NM = 1, typename... Args>
+void launch_bcombine_product(int nmod, int blocks, cudaStream_t st, Args... args) {
+  if constexpr (NM < kNumMod) {
+    if (nmod != NM) return launch_bcombine_product<NM + 1>(nmod, blocks, st, args...);
+  }
+  bcombine_product_kernel<NM><<<blocks, 256, 0, st>>>(args...);
+}
+}  // namespace
+
+cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* rexp_prefix,
+                         int rexp_blocks, const int* strip_prefix,
                          int col_strips, const OzTile* tiles, int num_tiles, int stage_bytes, int cluster,
-                         const int* group_prefix, int group_blocks,
+                         const int* group_prefix, int group_blocks, int nmod,
                          const void* maps_dev, int a_slot, int b_slot, int c_slot, int d_slot, double alpha,
                          double beta, double diag, int mask_k, bool split_a, bool split_b, int* err, cudaStream_t st) {
   const cudaError_t attr = bgemm_prepare();
   if (attr != cudaSuccess) return attr;
-  const int row_blocks = (rows_a * 32 + 255) / 256;
-  if (split_a && split_b) {
-    bsplit_rows_col_exponents_kernel<<<row_blocks + col_strips, 256, 0, st>>>(pc, row_prefix_a, strip_prefix, count,
-                                                                             a_slot, b_slot, mask_k, row_blocks);
-    count_launch();
-  } else if (split_a) {
-    bsplit_rows_kernel<<<row_blocks, 256, 0, st>>>(pc, row_prefix_a, count, a_slot, mask_k);
-    count_launch();
-  } else if (split_b) {
-    bcol_exponents_kernel<<<col_strips, 256, 0, st>>>(pc, strip_prefix, count, b_slot, mask_k);
-    count_launch();
+  if (split_a || split_b) {
+    // exponents of what changes, then its residues (row blocks first, column blocks after)
+    const int reb = split_a ? rexp_blocks : 0, cb = split_b ? col_strips : 0;
+    bexponents_kernel<<<reb + cb, 256, 0, st>>>(pc, rexp_prefix, strip_prefix, count, a_slot, b_slot, mask_k, reb);
+    const int rsb = split_a ? (rows_a * 32 + 255) / 256 : 0;
+    bsplit_kernel<<<rsb + cb, 256, 0, st>>>(pc, row_prefix_a, strip_prefix, count, a_slot, b_slot, nmod, mask_k, rsb);
+    count_launch(2);
   }
-  if (split_b) {
-    bsplit_cols_kernel<<<col_strips, 256, 0, st>>>(pc, strip_prefix, count, b_slot, mask_k);
-    count_launch();
-  }
-  const cudaError_t e = launch_bresidue(maps_dev, tiles, num_tiles, pc, stage_bytes, cluster, mask_k, err, st);
+  const cudaError_t e = launch_bresidue(maps_dev, tiles, num_tiles, pc, stage_bytes, cluster, nmod, mask_k, err, st);
   if (e != cudaSuccess) return e;
   count_launch();
-  bcombine_product_kernel<<<group_blocks, 256, 0, st>>>(pc, group_prefix, count, constants(), c_slot, d_slot, alpha,
-                                                        beta, diag, mask_k);
+  launch_bcombine_product(nmod, group_blocks, st, pc, group_prefix, count, constants(nmod), c_slot, d_slot, alpha,
+                          beta, diag, mask_k);
   return launched();
 }
 
 int ozaki_combine_blocks(int m) { return (int)(((int64_t)m * ((m + 3) / 4) + 255) / 256); }
+
+int ozaki_row_exponent_blocks(int m) { return ozaki_layout(m, m, m).mp / 8; }
 
 int ozaki_row_split_warps(int m) {
   const OzLayout L = ozaki_layout(m, m, m);
@@ -837,7 +899,8 @@ OzLayout ozaki_layout(int M, int N, int K) {
   L.sb = a256(L.sa + (size_t)kNumMod * L.mp * L.kp * 2);
   L.ea = a256(L.sb + (size_t)kNumMod * L.np * L.kp * 2);
   L.eb = a256(L.ea + (size_t)L.mp * 4);
-  L.ebp = a256(L.eb + (size_t)L.np * 4);
+  L.eap = a256(L.eb + (size_t)L.np * 4);
+  L.ebp = a256(L.eap + (size_t)L.mp * 4);
   L.res = a256(L.ebp + (size_t)(L.kp / kColSplitK) * L.np * 4);
   L.bytes = a256(L.res + (size_t)kNumMod * L.mp * L.np);
   return L;

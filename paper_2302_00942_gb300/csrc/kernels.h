@@ -132,14 +132,16 @@ cudaError_t dfinite_check(int m, int n, const double* X, int ldx, int* flag, cud
 // of the padded sizes.
 struct OzLayout {
   int mp, np, kp;
-  size_t sa, sb, ea, eb, ebp, res, bytes;  // ebp: per-64-row column exponents [kp / 64][np]
+  size_t sa, sb, ea, eb, eap, ebp, res, bytes;  // eap: raw row exponents [mp]; ebp: per-64-row column exponents [kp / 64][np]
 };
 OzLayout ozaki_layout(int M, int N, int K);
 size_t ozaki_workspace_bytes(int M, int N, int K);  // layout bytes + alignment slack
 int ozaki_col_split_blocks(int m);  // blocks of the batched column split of an m x m operand
 int ozaki_combine_blocks(int m);    // blocks of the batched reconstruction of an m x m product
 int ozaki_row_split_warps(int m);   // warps of the batched row split of an m x m operand
-int ozaki_kbits(int K);             // bits of the scaled integers for contractions of length K
+int ozaki_row_exponent_blocks(int m);  // blocks (8 rows each) of the batched row-exponent pass
+int ozaki_kbits(int K, int nmod);   // bits of the scaled integers (length-K contractions, first nmod moduli)
+int ozaki_moduli_for_bits(int K, int k);  // fewest moduli that give k bits at length K (16 at most)
 bool ozaki_supported(int K);
 cudaError_t dgemm_ozaki(int M, int N, int K, double alpha, const double* A, int lda, const double* B, int ldb,
                         double beta, double* C, int ldc, void* work, int* err, cudaStream_t st);
@@ -222,21 +224,23 @@ struct PhiCloud {
   int* ea;                // row exponents of A (mpa)
   int* eb;                // column exponents of B (mpb)
   int* ebp;               // column exponents of B per 64 rows of K ([kp / 64][mpb])
+  int* eap;               // largest biased exponents of A's rows (mpa)
   uint8_t* res;           // residues of the product [16][mpa][mpb]
   int* flag;              // finiteness flag
   double lambda, scale;   // scale = 2^-s (set per call)
   int32_t m, mpa, mpb, kp;
   int32_t map_a, map_b;   // tensor maps of sa / sb
-  int32_t s, kbits;       // squarings (set per call); bits of the scaled integers (ozaki_kbits(m))
+  int32_t s, pad_;        // squarings (set per call)
+  int8_t kbits_n[16];     // bits of the scaled integers with the first n moduli: ozaki_kbits(m, n), n = 1..16
 };
-// One work item of the residue GEMM: rows m0 .. (128 per CTA of a cluster),
-// columns n0 .. n0 + nb, moduli g0 .. g0 + ng - 1 of one cloud's product (kp:
-// the padded K, for ordering the items by cost).
+// One tile of the residue GEMM: rows m0 .. (128 per CTA of a cluster), columns
+// n0 .. n0 + nb of one cloud's product (kp: the padded K, for ordering the tiles
+// by cost); a launch with nmod moduli has the work items (tile, modulus g < nmod).
 struct OzTile {
   int32_t cloud, m0, n0, nb, kp, g0, ng, pad_;
 };
-// The residue-GEMM work items of a batch of m x m products (cloud k of size
-// ms[k]), longest first: one per (row tile, column tile of <= 256, modulus).
+// The residue-GEMM tiles of a batch of m x m products (cloud k of size ms[k]),
+// longest first: one per (row tile, column tile of <= 256).
 // *cluster = 2 when every cloud has two or more 128-row tiles: the two CTAs of
 // a cluster take the halves of a 256-row tile and share its B rows by
 // multicast; else 1 (128-row tiles).  *stage_bytes: the pipeline stage size.
@@ -267,17 +271,21 @@ cudaError_t launch_bselect(PhiCloud* pc, int count, const double* norms, double 
 // sets a cloud's flag when an entry of the slot is not finite (flags are sticky)
 cudaError_t launch_bfinite(const PhiCloud* pc, const int* prefix, int count, int total_blocks, int slot,
                            cudaStream_t st);
-// D = alpha A B + beta C + diag I on every cloud (emulated FP64): row split of
+// D = alpha A B + beta C + diag I on every cloud (emulated FP64): exponent pass
+// (A's rows: prefix over ozaki_row_exponent_blocks(m) per cloud), row split of
 // A (warp prefix over ozaki_row_split_warps(m) per cloud), column split of B (prefix over
 // ozaki_col_split_blocks(m) per cloud), the residue GEMM over the tiles and the
 // reconstruction (prefix over ozaki_combine_blocks(m) per cloud).
+// nmod: the moduli used (the first nmod; fewer when the product only needs
+// k = kbits(m, nmod) bits relative to its operands' row and column maxima).
 // c_slot kNoSlot: no C.  Clouds with s <= mask_k (mask_k >= 0) skip the
 // product and copy C to D.  split_a / split_b false: the residues already hold
 // that operand (split by the previous product over the same or a larger set of
 // clouds).
-cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* strip_prefix,
+cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* rexp_prefix,
+                         int rexp_blocks, const int* strip_prefix,
                          int col_strips, const OzTile* tiles, int num_tiles, int stage_bytes, int cluster,
-                         const int* group_prefix, int group_blocks,
+                         const int* group_prefix, int group_blocks, int nmod,
                          const void* maps_dev, int a_slot, int b_slot, int c_slot, int d_slot, double alpha,
                          double beta, double diag, int mask_k, bool split_a, bool split_b, int* err, cudaStream_t st);
 // one-time kernel attribute set-up of launch_gram_tc / launch_bgemm (call before a stream capture)

@@ -344,8 +344,9 @@ rfd_status build_desc(rfd_plan_s* pl) {
   pc.ea = reinterpret_cast<int*>(oz + L.ea);
   pc.eb = reinterpret_cast<int*>(oz + L.eb);
   pc.ebp = reinterpret_cast<int*>(oz + L.ebp);
+  pc.eap = reinterpret_cast<int*>(oz + L.eap);
   pc.res = oz + L.res;
-  pc.kbits = ozaki_kbits(m);
+  for (int nm = 1; nm <= 16; ++nm) pc.kbits_n[nm - 1] = (int8_t)ozaki_kbits(m, nm);
   pc.lambda = pl->p.lambda;
   pc.scale = 1.0;
   pc.map_a = 3;

@@ -83,6 +83,8 @@ struct BatchImpl {
   PhiCloud* d_phi = nullptr;
   int* d_elem_prefix = nullptr;
   int elem_blocks = 0;
+  int* d_rexp_prefix = nullptr;  // blocks of the row-exponent pass (8 rows each)
+  int rexp_blocks = 0;
   int* d_grp_prefix = nullptr;  // blocks of the product reconstruction (8 entries per thread)
   int grp_blocks = 0;
   int* d_rowa_prefix = nullptr;
@@ -166,7 +168,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   std::vector<FillJob> fill;
   std::vector<ApplyJob> apply;
   std::vector<PhiCloud> phi;
-  std::vector<int> feat_n, fill_n, small_n, elem_n, grp_n, rowa_n, strip_n;
+  std::vector<int> feat_n, fill_n, small_n, elem_n, grp_n, rowa_n, rexp_n, strip_n;
   std::vector<OzTile> oz;
   for (int k = 0; k < count; ++k) {
     rfd_plan_s* pl = plans[k];
@@ -227,15 +229,17 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
     elem_n.push_back((int)(((int64_t)pl->m * pl->m + 255) / 256));
     grp_n.push_back(ozaki_combine_blocks(pl->m));
     rowa_n.push_back(ozaki_row_split_warps(pl->m));
+    rexp_n.push_back(ozaki_row_exponent_blocks(pl->m));
     strip_n.push_back(ozaki_col_split_blocks(pl->m));
   }
   const std::vector<int> pre_feat = prefix_of(feat_n), pre_fill = prefix_of(fill_n), pre_small = prefix_of(small_n),
-                         pre_elem = prefix_of(elem_n), pre_grp = prefix_of(grp_n), pre_rowa = prefix_of(rowa_n), pre_strip = prefix_of(strip_n);
+                         pre_elem = prefix_of(elem_n), pre_grp = prefix_of(grp_n), pre_rexp = prefix_of(rexp_n), pre_rowa = prefix_of(rowa_n), pre_strip = prefix_of(strip_n);
   b->feat_blocks = pre_feat.back();
   b->fill_blocks = pre_fill.back();
   b->small_rows = pre_small.back();
   b->elem_blocks = pre_elem.back();
   b->grp_blocks = pre_grp.back();
+  b->rexp_blocks = pre_rexp.back();
   b->rows_a = pre_rowa.back();
   b->col_strips = pre_strip.back();
   {
@@ -267,7 +271,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   }
   const size_t o_feat = vtable(feat), o_feat_pre = vtable(pre_feat), o_fill = vtable(fill),
                o_fill_pre = vtable(pre_fill), o_apply = vtable(apply), o_small_pre = vtable(pre_small),
-               o_phi = vtable(phi), o_elem_pre = vtable(pre_elem), o_grp_pre = vtable(pre_grp), o_rowa_pre = vtable(pre_rowa),
+               o_phi = vtable(phi), o_elem_pre = vtable(pre_elem), o_grp_pre = vtable(pre_grp), o_rexp_pre = vtable(pre_rexp), o_rowa_pre = vtable(pre_rowa),
                o_strip_pre = vtable(pre_strip), o_oz = vtable(oz);
   const size_t table_bytes = L.total;
   b->stage_bytes = (size_t)count * sizeof(CloudCall) + (size_t)(count + 1) * sizeof(int);
@@ -303,6 +307,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   b->d_phi = reinterpret_cast<PhiCloud*>(D + o_phi);
   b->d_elem_prefix = reinterpret_cast<int*>(D + o_elem_pre);
   b->d_grp_prefix = reinterpret_cast<int*>(D + o_grp_pre);
+  b->d_rexp_prefix = reinterpret_cast<int*>(D + o_rexp_pre);
   b->d_rowa_prefix = reinterpret_cast<int*>(D + o_rowa_pre);
   b->d_strip_prefix = reinterpret_cast<int*>(D + o_strip_pre);
   b->d_oz = reinterpret_cast<OzTile*>(D + o_oz);
@@ -377,15 +382,29 @@ rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s) {
     for (double v : a) a4[i++] = v;
     return launch_bcombine(b->d_phi, b->d_elem_prefix, n, b->elem_blocks, dst, s4, a4, diag, kmode, mask, st);
   };
-  // the A / B residues hold the operands of the previous product: split only what changed
-  int last_a = kNoSlot, last_b = kNoSlot;
-  auto gemm = [&](int a, int bb, int c, int d, double alpha, double beta, double diag, int mask) {
-    const bool sa = a != last_a, sb = bb != last_b;
+  // Moduli per product.  A product whose result enters F scaled by a factor Q with
+  // max|Q| <= q only needs k = 53 - log2(1/q) bits of its operands for FP64 accuracy
+  // relative to F (the emulation errs by ~2^-k K max|Q| max|F| per entry, like an FP64
+  // product's K u |Q||F|).  In the product-form solve Q = R^(2^j) with
+  // ||R||_1 <= p_5(theta_5) - 1 < 0.135 (so max|R^(2^j)| <= 0.135^(2^j)); the fewest
+  // moduli that give those bits for the batch's largest m are used.
+  const int kfull = 16;
+  auto moduli_for = [&](double q) {
+    const int k = (int)std::ceil(53.0 + std::log2(q));
+    return std::min(kfull, ozaki_moduli_for_bits(std::max(b->max_m, 1), k));
+  };
+  constexpr double kRBound = 0.135;
+  // the A / B residues hold the operands of the previous product (split with the same
+  // number of moduli, hence the same integer width): split only what changed
+  int last_a = kNoSlot, last_b = kNoSlot, last_na = 0, last_nb = 0;
+  auto gemm = [&](int a, int bb, int c, int d, double alpha, double beta, double diag, int mask, int nmod) {
+    const bool sa = a != last_a || nmod != last_na, sb = bb != last_b || nmod != last_nb;
     last_a = a;
     last_b = bb;
-    return launch_bgemm(b->d_phi, n, b->d_rowa_prefix, b->rows_a, b->d_strip_prefix, b->col_strips, b->d_oz,
-                        b->n_oz, b->oz_stage_bytes, b->oz_cluster, b->d_grp_prefix, b->grp_blocks, b->d_maps, a, bb, c, d, alpha, beta, diag, mask, sa,
-                        sb, b->d_err, st);
+    last_na = last_nb = nmod;
+    return launch_bgemm(b->d_phi, n, b->d_rowa_prefix, b->rows_a, b->d_rexp_prefix, b->rexp_blocks, b->d_strip_prefix, b->col_strips, b->d_oz,
+                        b->n_oz, b->oz_stage_bytes, b->oz_cluster, b->d_grp_prefix, b->grp_blocks, nmod, b->d_maps, a,
+                        bb, c, d, alpha, beta, diag, mask, sa, sb, b->d_err, st);
   };
   // a slot that is written no longer matches its residues
   auto wrote = [&](int slot) {
@@ -397,37 +416,38 @@ rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s) {
   pb[0] = 1.0;
   for (int k = 0; k < 5; ++k) pb[k + 1] = pb[k] * double(5 - k) / (double(10 - k) * double(k + 1));
   if (max_s > 0) BCK(comb(sX, {sX}, {1.0}, 0.0, 2, -1));  // X = 2^-s X
-  BCK(gemm(sX, sX, kNoSlot, sX2, 1.0, 0.0, 0.0, -1));
+  BCK(gemm(sX, sX, kNoSlot, sX2, 1.0, 0.0, 0.0, -1, kfull));
   wrote(sX2);
-  BCK(gemm(sX2, sX2, kNoSlot, sX4, 1.0, 0.0, 0.0, -1));
+  BCK(gemm(sX2, sX2, kNoSlot, sX4, 1.0, 0.0, 0.0, -1, kfull));
   wrote(sX4);
   BCK(comb(sSp, {sX4, sX2}, {pb[5], pb[3]}, pb[1], 0, -1));
   BCK(comb(sVp, {sX4, sX2}, {pb[4], pb[2]}, pb[0], 0, -1));
   wrote(sSp);
   wrote(sVp);
-  BCK(gemm(sX, sSp, sVp, sR, 1.0, -1.0, 1.0, -1));  // R = I - (Vp - Up), Up = X Sp
+  BCK(gemm(sX, sSp, sVp, sR, 1.0, -1.0, 1.0, -1, kfull));  // R = I - (Vp - Up), Up = X Sp
   wrote(sR);
-  BCK(gemm(sR, sSp, sSp, sF, 2.0, 2.0, 0.0, -1));   // F = (I + R) 2 Sp
+  BCK(gemm(sR, sSp, sSp, sF, 2.0, 2.0, 0.0, -1, moduli_for(kRBound)));  // F = (I + R) 2 Sp
   wrote(sF);
   int F = sF, Fb = sFb, R = sR, R2 = sR2;
   for (int j = 1; j < kSolveFactors; ++j) {
-    BCK(gemm(R, R, kNoSlot, R2, 1.0, 0.0, 0.0, -1));  // R^(2^j)
+    const int nm = moduli_for(std::pow(kRBound, (double)(1 << j)));
+    BCK(gemm(R, R, kNoSlot, R2, 1.0, 0.0, 0.0, -1, nm));  // R^(2^j)
     wrote(R2);
     std::swap(R, R2);
-    BCK(gemm(R, F, F, Fb, 1.0, 1.0, 0.0, -1));  // F <- F + R^(2^j) F
+    BCK(gemm(R, F, F, Fb, 1.0, 1.0, 0.0, -1, nm));  // F <- F + R^(2^j) F
     wrote(Fb);
     std::swap(F, Fb);
   }
   if (max_s > 0) {
     int E = sE, E2 = sT1;
-    BCK(gemm(sX, F, kNoSlot, E, 1.0, 0.0, 1.0, -1));  // E = I + X F
+    BCK(gemm(sX, F, kNoSlot, E, 1.0, 0.0, 1.0, -1, kfull));  // E = I + X F
     wrote(E);
     for (int k = 0; k < max_s; ++k) {
-      BCK(gemm(E, F, F, Fb, 0.5, 0.5, 0.0, k));  // F <- (E F + F) / 2 (clouds with s <= k copy F)
+      BCK(gemm(E, F, F, Fb, 0.5, 0.5, 0.0, k, kfull));  // F <- (E F + F) / 2 (clouds with s <= k copy F)
       wrote(Fb);
       std::swap(F, Fb);
       if (k + 1 < max_s) {
-        BCK(gemm(E, E, kNoSlot, E2, 1.0, 0.0, 0.0, k + 1));  // E <- E^2 (clouds with s <= k + 1 skip)
+        BCK(gemm(E, E, kNoSlot, E2, 1.0, 0.0, 0.0, k + 1, kfull));  // E <- E^2 (clouds with s <= k + 1 skip)
         wrote(E2);
         std::swap(E, E2);
       }
