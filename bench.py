@@ -419,13 +419,18 @@ def main():
     Ft = torch.from_numpy(F).to(dev)
     out = torch.empty_like(Ft)
     prec = rfd.RFD_BF16_TC if args.precision == "bf16" else rfd.RFD_FP32_PLAIN
+    tune = prec == rfd.RFD_BF16_TC and not args.no_autotune
+    # the timed plan replays each call from CUDA graphs (BF16 form); a second plan with per-step
+    # CUDA events gives the step breakdown (events between kernels would sit in the timed path)
+    gplan = rfd.Plan(n, m, spec.eps, lam, spec.seed, max_channels=c, precision=prec, stream=stream, autotune=tune,
+                     graph=(prec == rfd.RFD_BF16_TC))
     plan = rfd.Plan(n, m, spec.eps, lam, spec.seed, max_channels=c, precision=prec, stream=stream, timing=True,
-                    autotune=(prec == rfd.RFD_BF16_TC and not args.no_autotune))
+                    autotune=tune)
 
     for _ in range(args.warmup):
-        plan.gfi(P, Ft, out)
-    plan.sync()
-    plan.stats_reset()
+        gplan.gfi(P, Ft, out)
+    gplan.sync()
+    gplan.stats_reset()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -434,15 +439,25 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        plan.gfi(P, Ft, out)
+        gplan.gfi(P, Ft, out)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     D.barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = D.max(ms)
-    st = plan.stats()
+    gst = gplan.stats()
     out_bf = out.clone()
+    # step breakdown (per-step events), outside the timed region
+    for _ in range(max(1, min(args.warmup, 3))):
+        plan.gfi(P, Ft, out)
+    plan.sync()
+    plan.stats_reset()
+    for _ in range(args.steps):
+        plan.gfi(P, Ft, out)
+    plan.sync()
+    st = plan.stats()
+    st["kernel_launches"] = gst["kernel_launches"]
 
     # warm: a new field on the resident features and G (rfd_integrate: steps a3(Y) to a6)
     F2 = torch.from_numpy(synth.gaussian_field(n, c, spec.seed + 1)).to(dev)
@@ -459,8 +474,17 @@ def main():
         plan.integrate(F2, out2)
     w1.record(stream)
     torch.cuda.synchronize(dev)
-    warm_ms = D.max(w0.elapsed_time(w1) / args.steps)
     wst = plan.stats()
+    for _ in range(2):
+        gplan.integrate(F2, out2)
+    gplan.sync()
+    torch.cuda.synchronize(dev)
+    w0.record(stream)
+    for _ in range(args.steps):
+        gplan.integrate(F2, out2)
+    w1.record(stream)
+    torch.cuda.synchronize(dev)
+    warm_ms = D.max(w0.elapsed_time(w1) / args.steps)
 
     # end to end: host buffers, H2D of the step's inputs and D2H of its result inside the timed region
     Ph = torch.from_numpy(pts).pin_memory()
@@ -474,13 +498,14 @@ def main():
     for _ in range(args.e2e_steps):
         Pd.copy_(Ph, non_blocking=True)
         Fd.copy_(Fh, non_blocking=True)
-        rfd.rfd_gfi(plan.handle, Pd, Fd, c, c, Od, c)
+        rfd.rfd_gfi(gplan.handle, Pd, Fd, c, c, Od, c)
         Oh.copy_(Od, non_blocking=True)
     a1.record(stream)
     torch.cuda.synchronize(dev)
     D.barrier()
     e2e_ms = D.max(a0.elapsed_time(a1) / args.e2e_steps)
     plan.close()
+    gplan.close()
 
     # FP32 plain form on the same inputs (the form the BF16 path must beat), and the BF16 form's
     # deviation from it (the FP32 form matches the FP64 oracle to <= 1e-5 in the parity tests)

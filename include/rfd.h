@@ -98,9 +98,9 @@ typedef struct rfd_plan_s* rfd_plan_t;
 #define RFD_FLAG_NATIVE_FP64 2  /* step a4 products in native FP64 instead of the FP64-accurate
                                    modular (Chinese-remainder) emulation on the BF16 tensor cores
                                    (the default) */
-#define RFD_FLAG_GRAPH 4        /* batches only: replay each call's launches from CUDA graphs,
-                                   captured on first use per call shape (per-step timings are
-                                   then not recorded) */
+#define RFD_FLAG_GRAPH 4        /* BF16 plans and batches: replay each call's launches from CUDA
+                                   graphs, captured on first use per call shape (per-step timings
+                                   are then not recorded; ignored by FP32 plain plans) */
 #define RFD_FLAG_AUTOTUNE 8     /* BF16 plans and batches: after the first features pass, time the
                                    tensor-core reductions for a few split-K lane counts (plans) or
                                    wave targets (batches) and point-axis phase lengths on the

@@ -289,13 +289,14 @@ class Plan:
     """
 
     def __init__(self, n, m, eps, lam, seed=0, max_channels=3, precision=RFD_BF16_TC, stream=None,
-                 freq_sigma=0.0, freq_radius=0.0, timing=False, native_fp64=False, autotune=False, kernel="cube"):
+                 freq_sigma=0.0, freq_radius=0.0, timing=False, native_fp64=False, autotune=False, kernel="cube",
+                 graph=False):
         self.n, self.m, self.max_channels = int(n), int(m), int(max_channels)
         self.handle = None
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
         self.handle = rfd_plan(n, m, eps, lam, seed, max_channels, precision, s, freq_sigma, freq_radius,
                                (RFD_FLAG_TIMING if timing else 0) | (RFD_FLAG_NATIVE_FP64 if native_fp64 else 0) |
-                               (RFD_FLAG_AUTOTUNE if autotune else 0), kernel)
+                               (RFD_FLAG_AUTOTUNE if autotune else 0) | (RFD_FLAG_GRAPH if graph else 0), kernel)
 
     @staticmethod
     def _chk(t, shape_last=None):

@@ -215,30 +215,22 @@ RFD_HD bool to_double(unsigned long long lo, unsigned long long hi, int E, bool 
     return true;
   }
   neg = neg != flip;
-  int msb = hi ? 127 - clz64(hi) : 63 - clz64(lo);
-  unsigned long long mant;
-  bool up = false;
-  if (msb <= 52) {
-    mant = lo << (52 - msb);  // exact
+  // normalise: the magnitude shifted left until its top bit is bit 127 of h:l
+  const int z = hi ? clz64(hi) : 64 + clz64(lo);  // leading zeros, 0 .. 127
+  unsigned long long h, l;
+  if (z >= 64) {
+    h = lo << (z - 64);
+    l = 0;
   } else {
-    const int sh = msb - 52;  // 1 .. 75 bits drop off
-    int cmp;                  // the dropped bits against half of the last kept unit
-    if (sh < 64) {
-      mant = (lo >> sh) | (hi << (64 - sh));
-      const unsigned long long rem = lo & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-      cmp = rem > half ? 1 : (rem == half ? 0 : -1);
-    } else if (sh == 64) {
-      mant = hi;
-      const unsigned long long half = 1ull << 63;
-      cmp = lo > half ? 1 : (lo == half ? 0 : -1);
-    } else {
-      mant = hi >> (sh - 64);
-      const unsigned long long rem_hi = hi & ((1ull << (sh - 64)) - 1), half_hi = 1ull << (sh - 65);
-      cmp = rem_hi > half_hi ? 1 : (rem_hi < half_hi ? -1 : (lo ? 1 : 0));
-    }
-    up = cmp > 0 || (cmp == 0 && (mant & 1ull));
+    h = z ? (hi << z) | (lo >> (64 - z)) : hi;
+    l = lo << z;
   }
-  mant += up ? 1ull : 0ull;
+  int msb = 127 - z;
+  // the top 53 bits, rounded to nearest even on the 75 below them (zeros for small values)
+  unsigned long long mant = h >> 11;
+  const unsigned long long rem = h & 0x7FFull;
+  const bool half = (rem >> 10) != 0, sticky = ((rem & 0x3FFull) | l) != 0;
+  mant += (half && (sticky || (mant & 1ull))) ? 1ull : 0ull;
   if (mant >> 53) {
     mant >>= 1;
     ++msb;

@@ -496,15 +496,14 @@ __device__ __forceinline__ bool pow2_of(double alpha, int* k, bool* neg) {
 // alpha (A B)[i, j] from the residues r and the exponent e = ea_i + eb_j:
 // correctly rounded when alpha is a power of two and the result is a normal
 // double.
+// alpha = (-1)^aneg 2^ak when ap2 (decoded once per thread by pow2_of)
 template <int NM>
 __device__ __forceinline__ double product_entry(const crt::Constants& cc, const uint32_t (&r)[kNumMod], int e,
-                                                double alpha) {
+                                                double alpha, bool ap2, int ak, bool aneg) {
   unsigned long long lo, hi;
   crt::reconstruct<NM>(r, cc, &lo, &hi);
-  int ak = 0;
-  bool aneg = false;
   double v;
-  if (pow2_of(alpha, &ak, &aneg)) {
+  if (ap2) {
     if (!crt::to_double(lo, hi, e + ak, aneg, &v)) v = alpha * crt::to_double_plain(lo, hi, e);
   } else {
     if (!crt::to_double(lo, hi, e, false, &v)) v = crt::to_double_plain(lo, hi, e);
@@ -523,6 +522,9 @@ __device__ __forceinline__ void combine4(const crt::Constants& cc, const uint8_t
 #pragma unroll
   for (int j = 0; j < kNumMod; ++j)  // the first NM moduli are in use (cc.nmod == NM)
     w[j] = j < NM ? __ldg(reinterpret_cast<const uint32_t*>(res_row + j * plane + j0)) : 0u;
+  int ak = 0;
+  bool aneg = false;
+  const bool ap2 = pow2_of(alpha, &ak, &aneg);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int jj = j0 + q;
@@ -530,7 +532,7 @@ __device__ __forceinline__ void combine4(const crt::Constants& cc, const uint8_t
     uint32_t r[kNumMod];
 #pragma unroll
     for (int j = 0; j < kNumMod; ++j) r[j] = (w[j] >> (8 * q)) & 0xFFu;
-    double v = product_entry<NM>(cc, r, ea_i + eb[jj], alpha);
+    double v = product_entry<NM>(cc, r, ea_i + eb[jj], alpha, ap2, ak, aneg);
     if (beta != 0.0) v = fma(beta, C[jj], v);
     if (i == jj) v += diag;
     D[jj] = v;

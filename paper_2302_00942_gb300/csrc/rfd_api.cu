@@ -449,6 +449,9 @@ constexpr int kTunePhases[3] = {2048, 4096, 8192};
 
 int ilog2(double x) { return x < 1.0 ? 0 : (int)std::floor(std::log2(x)); }
 
+// Options of a plan's batch of one: CUDA graphs when the plan asks for them.
+int self_options(const rfd_plan_s* pl) { return (pl->p.flags & RFD_FLAG_GRAPH) ? kBatchGraphs : 0; }
+
 // Rebuilds the plan's descriptors and its batch of one for pl->tune.
 rfd_status rebuild_self(rfd_plan_s* pl) {
   RFD_CUDA(cudaStreamSynchronize(pl->stream));
@@ -456,7 +459,7 @@ rfd_status rebuild_self(rfd_plan_s* pl) {
   if (s != RFD_OK) return s;
   BatchImpl* nb = nullptr;
   rfd_plan_s* self = pl;
-  if ((s = batch_build(&self, 1, pl->stream, pl->mem, 0, pl->tune, &nb)) != RFD_OK) return s;
+  if ((s = batch_build(&self, 1, pl->stream, pl->mem, self_options(pl), pl->tune, &nb)) != RFD_OK) return s;
   RFD_CUDA(cudaStreamSynchronize(pl->stream));
   batch_free(pl->self);
   pl->self = nb;
@@ -609,7 +612,7 @@ rfd_status plan_prepare(const rfd_params& p, cudaStream_t stream, rfd_plan_s** o
   if (p.max_channels < 1 || p.max_channels > kMaxChannels) return fail(RFD_EINVAL, "max_channels must be in [1, 256]");
   if (!std::isfinite(p.lambda)) return fail(RFD_EINVAL, "lambda must be finite");
   if (p.precision != RFD_FP32_PLAIN && p.precision != RFD_BF16_TC) return fail(RFD_EINVAL, "unknown precision");
-  if (p.flags & ~(RFD_FLAG_TIMING | RFD_FLAG_NATIVE_FP64 | RFD_FLAG_AUTOTUNE))
+  if (p.flags & ~(RFD_FLAG_TIMING | RFD_FLAG_NATIVE_FP64 | RFD_FLAG_AUTOTUNE | RFD_FLAG_GRAPH))
     return fail(RFD_EINVAL, "unknown bits in flags");
   if (p.n > (int64_t)1 << 31) return fail(RFD_EINVAL, "n must be < 2^31");
   if (p.kernel != RFD_KERNEL_CUBE && p.kernel != RFD_KERNEL_BALL) return fail(RFD_EINVAL, "unknown kernel");
@@ -731,7 +734,7 @@ rfd_status plan_materialize(rfd_plan_s* pl, MemSource* mem, bool self_batch, boo
     if ((st2 = build_desc(pl)) != RFD_OK) return bail(st2);
     if (self_batch) {
       rfd_plan_s* self = pl;
-      if ((st2 = batch_build(&self, 1, st, mem, 0, pl->tune, &pl->self)) != RFD_OK) return bail(st2);
+      if ((st2 = batch_build(&self, 1, st, mem, self_options(pl), pl->tune, &pl->self)) != RFD_OK) return bail(st2);
     }
     pl->stats.splits = pl->desc.units[kModeGfi].empty() ? 0 : pl->desc.units[kModeGfi][0].nlanes;
   } else {

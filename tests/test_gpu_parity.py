@@ -191,6 +191,34 @@ def test_ball_kernel_matches_oracle(prec, name):
     np.testing.assert_allclose(r, parts["r"], rtol=1e-13)
 
 
+def test_plan_graph_replay_is_bitwise_identical():
+    """A BF16 plan with RFD_FLAG_GRAPH replays each call's launches from CUDA graphs:
+    the output equals the plain plan's bit for bit, call after call (gfi and integrate)."""
+    spec, pts, F, lam = small_case("torus")
+    P, Ft = _cuda(pts), _cuda(F)
+    outs = {}
+    for graph in (False, True):
+        plan = rfd.Plan(spec.n, spec.m, spec.eps, lam, spec.seed, max_channels=F.shape[1],
+                        precision=rfd.RFD_BF16_TC, stream=torch.cuda.current_stream(DEV), graph=graph)
+        try:
+            res = []
+            for _ in range(3):
+                o = torch.empty_like(Ft)
+                plan.gfi(P, Ft, o)
+                res.append(o)
+            o2 = torch.empty_like(Ft)
+            plan.integrate(Ft * 0.5, o2)
+            res.append(o2)
+            plan.sync()
+            outs[graph] = [r.cpu().numpy() for r in res]
+        finally:
+            plan.close()
+    for a, b in zip(outs[False], outs[True]):
+        np.testing.assert_array_equal(a, b)
+    ref = oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed)
+    assert oracle.rel_frobenius(outs[True][2], ref) <= TOL[rfd.RFD_BF16_TC]
+
+
 def test_invalid_arguments_and_alloc_failure():
     spec, pts, F, lam = small_case()
     plan = rfd.Plan(spec.n, spec.m, spec.eps, lam, spec.seed, max_channels=3, precision=rfd.RFD_BF16_TC)
