@@ -39,9 +39,14 @@ __device__ __forceinline__ float round_int(float t) {
 }
 
 constexpr int kFeatThreads = 256;
-constexpr int kFeatPts = 512;   // 2 points per thread
+constexpr int kFeatPts = 512;   // 8 warps x one 64-point block
 constexpr int kFeatFreq = 32;
 
+// A warp takes one 64-point block of Psi and 32 frequencies: lane = 8 g + pl
+// handles points 8 pl .. 8 pl + 7 of the block and the frequencies
+// j0 + 4 t + g (t = 0..7), so each store instruction writes rows
+// j0 + 4t .. j0 + 4t + 3 of the block -- 4 adjacent rows of 128 bytes, one
+// contiguous 512-byte span -- with 16-byte stores.
 __global__ void __launch_bounds__(kFeatThreads)
 features_batched_kernel(const FeatJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
                         const CloudCall* __restrict__ calls) {
@@ -50,40 +55,53 @@ features_batched_kernel(const FeatJob* __restrict__ jobs, const int* __restrict_
   const int local = blockIdx.x - prefix[j];
   const int bxi = local % jb.bx, byi = local / jb.bx;
   const float* __restrict__ pts = calls[jb.cloud].pts;
-  auto* psi = reinterpret_cast<__nv_bfloat16*>(jb.psi);
   __shared__ float w_s[kFeatFreq][3];
   const int j0 = byi * kFeatFreq;
   const int jn = min(kFeatFreq, jb.h - j0);
   if (threadIdx.x < jn * 3) w_s[threadIdx.x / 3][threadIdx.x % 3] = jb.omega[(size_t)j0 * 3 + threadIdx.x];
   __syncthreads();
-  const int64_t p0 = (int64_t)bxi * kFeatPts + (int64_t)threadIdx.x * 2;
-  if (p0 >= jb.n_pad) return;
-  float x[2][3];
-  bool valid[2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, pl = lane & 7, g = lane >> 3;
+  const int64_t p0 = (int64_t)bxi * kFeatPts + warp * 64 + pl * 8;  // first of this lane's 8 points
+  if (p0 >= jb.n_pad) return;  // whole 64-point blocks: the warp exits together
+  float x[8][3];
+  bool valid[8];
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
+  for (int q = 0; q < 8; ++q) {
     valid[q] = (p0 + q) < jb.n;
 #pragma unroll
     for (int d = 0; d < 3; ++d) x[q][d] = valid[q] ? pts[(p0 + q) * 3 + d] : 0.f;
-    if (byi == 0 && valid[q])  // the cloud's own copy of its points, for the apply
-#pragma unroll
-      for (int d = 0; d < 3; ++d) jb.xyz[(p0 + q) * 3 + d] = x[q][d];
   }
-  const float two_pi = 6.283185307179586f;
-  for (int jj = 0; jj < jn; ++jj) {
-    const float w0 = w_s[jj][0], w1 = w_s[jj][1], w2 = w_s[jj][2];
-    float c[2], s[2];
+  if (byi == 0 && g == 0)  // the cloud's own copy of its points, for the apply
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const float t = fmaf(w0, x[q][0], fmaf(w1, x[q][1], w2 * x[q][2]));
-      const float a = two_pi * (t - round_int(t));   // |a| <= pi: MUFU sin/cos accurate to ~1e-6
-      c[q] = valid[q] ? __cosf(a) : 0.f;
-      s[q] = valid[q] ? __sinf(a) : 0.f;
+    for (int q = 0; q < 8; ++q)
+      if (valid[q])
+#pragma unroll
+        for (int d = 0; d < 3; ++d) jb.xyz[(p0 + q) * 3 + d] = x[q][d];
+  const float two_pi = 6.283185307179586f;
+  auto* psi = reinterpret_cast<uint4*>(jb.psi);
+  for (int t = 0; t < kFeatFreq / 4; ++t) {
+    const int jj = 4 * t + g;
+    if (jj >= jn) break;
+    const float w0 = w_s[jj][0], w1 = w_s[jj][1], w2 = w_s[jj][2];
+    uint32_t c2[4], s2[4];
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+      float c[2], sn[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const float tt = fmaf(w0, x[q + u][0], fmaf(w1, x[q + u][1], w2 * x[q + u][2]));
+        const float ang = two_pi * (tt - round_int(tt));  // |ang| <= pi: MUFU sin/cos accurate to ~1e-6
+        c[u] = valid[q + u] ? __cosf(ang) : 0.f;
+        sn[u] = valid[q + u] ? __sinf(ang) : 0.f;
+      }
+      const __nv_bfloat162 cb = __floats2bfloat162_rn(c[0], c[1]), sb = __floats2bfloat162_rn(sn[0], sn[1]);
+      c2[q / 2] = *reinterpret_cast<const uint32_t*>(&cb);
+      s2[q / 2] = *reinterpret_cast<const uint32_t*>(&sb);
     }
     const int jg = j0 + jj;
-    *reinterpret_cast<__nv_bfloat162*>(psi + psi_index(p0, jg, jb.rows_alloc)) = __floats2bfloat162_rn(c[0], c[1]);
-    *reinterpret_cast<__nv_bfloat162*>(psi + psi_index(p0, jb.h + jg, jb.rows_alloc)) =
-        __floats2bfloat162_rn(s[0], s[1]);
+    // 8 bf16 of row jg (and row h + jg) at points 8 pl .. of the block: one 16-byte store each
+    psi[psi_index(p0, jg, jb.rows_alloc) / 8] = make_uint4(c2[0], c2[1], c2[2], c2[3]);
+    psi[psi_index(p0, jb.h + jg, jb.rows_alloc) / 8] = make_uint4(s2[0], s2[1], s2[2], s2[3]);
   }
 }
 
