@@ -195,9 +195,9 @@ __global__ void __launch_bounds__(256)
 apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
                      const CloudCall* __restrict__ calls) {
   constexpr int kChunk = 64;
-  static_assert(CG % 4 == 0, "channel groups are float4 rows");
+  constexpr int CW = (CG + 3) / 4;  // float4 per row of Z in shared memory (CG channels used)
   __shared__ float4 w_s[kChunk];
-  __shared__ float4 zc[kChunk][CG / 4], zsn[kChunk][CG / 4];
+  __shared__ float4 zc[kChunk][CW], zsn[kChunk][CW];
   const int j = find_job(prefix, count, blockIdx.x);
   const ApplyJob jb = jobs[j];
   const CloudCall cc = calls[jb.cloud];
@@ -229,8 +229,8 @@ apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ 
       const float* w = jb.omega_hi + (size_t)(f0 + i) * 3;
       w_s[i] = i < fn ? make_float4(w[0], w[1], w[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (int i = threadIdx.x; i < kChunk * CG; i += blockDim.x) {
-      const int fr = i / CG, q = i % CG;
+    for (int i = threadIdx.x; i < kChunk * CW * 4; i += blockDim.x) {
+      const int fr = i / (CW * 4), q = i % (CW * 4);
       const bool ok = fr < fn && q < cg;
       reinterpret_cast<float*>(zc[fr])[q] = ok ? jb.Z[(size_t)(f0 + fr) * cc.c + ch0 + q] : 0.f;
       reinterpret_cast<float*>(zsn[fr])[q] = ok ? jb.Z[(size_t)(h + f0 + fr) * cc.c + ch0 + q] : 0.f;
@@ -247,15 +247,15 @@ apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ 
         sn[u] = __sinf(ang);
       }
 #pragma unroll
-      for (int q4 = 0; q4 < CG / 4; ++q4) {
-        const float4 a = zc[fr][q4], b = zsn[fr][q4];
+      for (int q4 = 0; q4 < CW; ++q4) {
+        const float4 a4 = zc[fr][q4], b4 = zsn[fr][q4];
+        const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          acc[u][4 * q4 + 0] = fmaf(cs[u], a.x, fmaf(sn[u], b.x, acc[u][4 * q4 + 0]));
-          acc[u][4 * q4 + 1] = fmaf(cs[u], a.y, fmaf(sn[u], b.y, acc[u][4 * q4 + 1]));
-          acc[u][4 * q4 + 2] = fmaf(cs[u], a.z, fmaf(sn[u], b.z, acc[u][4 * q4 + 2]));
-          acc[u][4 * q4 + 3] = fmaf(cs[u], a.w, fmaf(sn[u], b.w, acc[u][4 * q4 + 3]));
-        }
+        for (int e = 0; e < 4; ++e)
+          if (4 * q4 + e < CG)  // compile-time: the channels of the group only
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+              acc[u][4 * q4 + e] = fmaf(cs[u], a[e], fmaf(sn[u], b[e], acc[u][4 * q4 + e]));
       }
     }
   }
@@ -392,6 +392,7 @@ cudaError_t launch_apply_batched(const ApplyJob* jobs, const int* prefix, int co
                                  const CloudCall* calls, cudaStream_t st) {
   if (total_blocks <= 0) return cudaSuccess;
   switch (cg) {
+    case 3: apply_batched_kernel<3><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
     case 4: apply_batched_kernel<4><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
     case 8: apply_batched_kernel<8><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
     case 16: apply_batched_kernel<16><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;

@@ -514,7 +514,7 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   // per-call tables: the callers' buffers, and the apply blocks (they depend on c)
   int max_c = 1;
   for (int k = 0; k < n; ++k) max_c = std::max(max_c, calls[k].c);
-  const int cg = max_c <= 4 ? 4 : (max_c <= 8 ? 8 : (max_c <= 16 ? 16 : 32));
+  const int cg = max_c <= 3 ? 3 : (max_c <= 4 ? 4 : (max_c <= 8 ? 8 : (max_c <= 16 ? 16 : 32)));
   // a pinned staging buffer whose previous upload has been consumed
   const int slot = b->stage_next;
   b->stage_next = (slot + 1) % BatchImpl::kStageRing;
