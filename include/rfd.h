@@ -88,8 +88,13 @@ typedef struct {
  *                    (the product of per-coordinate sincs printed in Sec. 2.4);
  *   RFD_KERNEL_BALL: f = 1[||z||_2 <= eps], tau(w) = 4 pi (sin(q eps) - q eps cos(q eps)) / q^3,
  *                    q = 2 pi ||w||_2 (the Bessel-function case of Sec. 2.4 in d = 3:
- *                    4 pi eps^3 j_1(q eps) / (q eps)). */
-typedef enum { RFD_KERNEL_CUBE = 0, RFD_KERNEL_BALL = 1 } rfd_kernel;
+ *                    4 pi eps^3 j_1(q eps) / (q eps));
+ *   RFD_KERNEL_CUBE_L1: f = ||z||_1 1[||z||_inf <= eps] (the distance-weighted adjacency of the
+ *                    paper's brute-force baseline, on the cube of RFD_KERNEL_CUBE):
+ *                    tau(w) = sum_d g(w_d) prod_{e != d} sin(2 pi eps w_e) / (pi w_e) with
+ *                    g(w) = int_{-eps}^{eps} |z| cos(2 pi w z) dz = 2 eps^2 (sin x / x + (cos x - 1) / x^2),
+ *                    x = 2 pi eps w (eps^2 at w = 0). */
+typedef enum { RFD_KERNEL_CUBE = 0, RFD_KERNEL_BALL = 1, RFD_KERNEL_CUBE_L1 = 2 } rfd_kernel;
 
 typedef struct rfd_plan_s* rfd_plan_t;
 

@@ -133,10 +133,30 @@ def tau(omega: np.ndarray, eps: float, kernel: str = "cube") -> np.ndarray:
         safe = np.where(x == 0.0, 1.0, x)
         ratio = np.where(x == 0.0, 1.0 / 3.0, scipy.special.spherical_jn(1, safe) / safe)
         return 4.0 * np.pi * eps ** 3 * ratio
-    if kernel != "cube":
-        raise ValueError(f"unknown kernel {kernel!r}")
     safe = np.where(w == 0.0, 1.0, w)
     per = np.where(w == 0.0, 2.0 * eps, np.sin(2.0 * np.pi * eps * w) / (np.pi * safe))
+    if kernel == "cube_l1":
+        # f = ||z||_1 1[||z||_inf <= eps] = sum_d |z_d| prod_e 1[|z_e| <= eps]: the transform is
+        # sum_d T(w_d) prod_{e != d} S(w_e), S the sinc above and T the transform of
+        # |z| 1[|z| <= eps], 2 int_0^eps z cos(2 pi w z) dz, integrated by parts:
+        # T = 2 [eps sin(k eps) / k + (cos(k eps) - 1) / k^2], k = 2 pi w (eps^2 at w = 0;
+        # near 0 the same value from the Taylor series of the integrand, to x^10)
+        x = 2.0 * np.pi * eps * w
+        xs = np.where(np.abs(x) < 0.1, 1.0, x)
+        direct = np.sin(xs) / xs + (np.cos(xs) - 1.0) / (xs * xs)
+        x2 = x * x
+        series = sum(((-1) ** n) * (2 * n + 1) / math.factorial(2 * n + 2) * x2 ** n for n in range(6))
+        T = 2.0 * eps * eps * np.where(np.abs(x) < 0.1, series, direct)
+        out = np.zeros(w.shape[:-1])
+        for d in range(w.shape[-1]):
+            term = T[..., d]
+            for e in range(w.shape[-1]):
+                if e != d:
+                    term = term * per[..., e]
+            out = out + term
+        return out
+    if kernel != "cube":
+        raise ValueError(f"unknown kernel {kernel!r}")
     return np.prod(per, axis=-1)
 
 
@@ -238,12 +258,14 @@ def dense_lowrank_gfi(A: np.ndarray, B: np.ndarray, F: np.ndarray, lam: float) -
 
 
 def exact_adjacency(points: np.ndarray, eps: float, kernel: str = "cube") -> np.ndarray:
-    """W(i,j) = 1[||n_i - n_j|| <= eps] (Eq. w; diagonal f(0) = 1), with the
-    L-infinity norm (kernel="cube") or the L2 norm (kernel="ball")."""
+    """W(i,j) = f(n_i - n_j) (Eq. w): 1[||z||_inf <= eps] (kernel="cube", diagonal 1),
+    1[||z||_2 <= eps] ("ball"), ||z||_1 1[||z||_inf <= eps] ("cube_l1", diagonal 0)."""
     X = np.asarray(points, dtype=np.float64)
     diff = X[:, None, :] - X[None, :, :]
-    d = np.linalg.norm(diff, axis=2) if kernel == "ball" else np.abs(diff).max(axis=2)
-    return (d <= eps).astype(np.float64)
+    if kernel == "ball":
+        return (np.linalg.norm(diff, axis=2) <= eps).astype(np.float64)
+    inside = (np.abs(diff).max(axis=2) <= eps).astype(np.float64)
+    return inside * np.abs(diff).sum(axis=2) if kernel == "cube_l1" else inside
 
 
 def dense_exact_gfi(points, F, eps, lam) -> np.ndarray:

@@ -15,7 +15,11 @@
 //  - the L2 ball 1[||z||_2 <= eps] (the Bessel-function case of Sec. 2.4):
 //    tau(w) = int_{|z| <= eps} cos(2 pi w.z) dz = 4 pi (sin x - x cos x) / q^3,
 //    q = 2 pi |w|, x = q eps (4 pi eps^3 / 3 at w = 0; a series below x = 0.1,
-//    where sin x - x cos x cancels).
+//    where sin x - x cos x cancels);
+//  - the distance-weighted cube ||z||_1 1[||z||_inf <= eps]: the transform of
+//    |z_d| 1[|z_d| <= eps] times the sincs of the other coordinates, summed
+//    over d; int_{-eps}^{eps} |z| cos(2 pi w z) dz = 2 eps^2 (sin x / x +
+//    (cos x - 1) / x^2), x = 2 pi eps w (a series below x = 0.1).
 //
 // This file must be compiled without floating-point contraction
 // (-ffp-contract=off) so that R (2 u1 - 1) is two rounded operations.
@@ -54,6 +58,19 @@ double sinc_cube(double w, double eps) {  // one coordinate of tau
   return std::sin(2.0 * kPi * eps * w) / (kPi * w);
 }
 
+double abs_cube(double w, double eps) {  // int_{-eps}^{eps} |z| cos(2 pi w z) dz
+  const double x = 2.0 * kPi * eps * w;
+  double g;
+  if (std::fabs(x) < 0.1) {
+    // sum_n (-1)^n x^(2n) (2n + 1) / (2n + 2)!
+    const double x2 = x * x;
+    g = 0.5 - x2 * (1.0 / 8.0 - x2 * (1.0 / 144.0 - x2 * (1.0 / 5760.0 - x2 * (1.0 / 403200.0 - x2 / 43545600.0))));
+  } else {
+    g = std::sin(x) / x + (std::cos(x) - 1.0) / (x * x);
+  }
+  return 2.0 * eps * eps * g;
+}
+
 double tau_ball(const double (&w)[3], double eps) {
   const double q = 2.0 * kPi * std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
   const double x = q * eps;
@@ -82,7 +99,8 @@ double default_radius(double eps) { return 1.0 / eps; }
 rfd_status sample_frequencies_host(int m, double eps, uint64_t seed, double sigma,
                                    double radius, int kernel, double* omega, double* r) {
   if (m < 2 || (m & 1)) return fail(RFD_EINVAL, "m must be even and >= 2");
-  if (kernel != RFD_KERNEL_CUBE && kernel != RFD_KERNEL_BALL) return fail(RFD_EINVAL, "unknown kernel");
+  if (kernel != RFD_KERNEL_CUBE && kernel != RFD_KERNEL_BALL && kernel != RFD_KERNEL_CUBE_L1)
+    return fail(RFD_EINVAL, "unknown kernel");
   if (!(eps > 0.0) || !std::isfinite(eps)) return fail(RFD_EINVAL, "eps must be finite and > 0");
   if (sigma == 0.0) sigma = default_sigma(eps);
   if (radius == 0.0) radius = default_radius(eps);
@@ -118,6 +136,10 @@ rfd_status sample_frequencies_host(int m, double eps, uint64_t seed, double sigm
         p *= std::exp(-0.5 * a * a) / norm;
       }
       if (kernel == RFD_KERNEL_BALL) tau = tau_ball(w3, eps);
+      if (kernel == RFD_KERNEL_CUBE_L1) {
+        const double s0 = sinc_cube(w3[0], eps), s1 = sinc_cube(w3[1], eps), s2 = sinc_cube(w3[2], eps);
+        tau = abs_cube(w3[0], eps) * s1 * s2 + s0 * abs_cube(w3[1], eps) * s2 + s0 * s1 * abs_cube(w3[2], eps);
+      }
       r[j] = tau / p;
     }
   }
