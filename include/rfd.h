@@ -199,6 +199,23 @@ RFD_API rfd_status rfd_features(rfd_plan_t plan, const float* d_points);
 RFD_API rfd_status rfd_integrate(rfd_plan_t plan, const float* d_F, int32_t c, int64_t ldF,
                          float* d_out, int64_t ldOut);
 
+/* Entropic Wasserstein barycenter on the resident plan (App. C, Algorithm
+ * wass_barycenter; the steps of Solomon et al. 2015, Algorithm 2): for k input
+ * distributions mu^i (columns of d_mu: N x k float32 device, leading dimension
+ * ld_mu >= k), weights alpha (host, k doubles >= 0), area weights d_area (N
+ * float32 device) and `iters` passes, with the kernel action x -> exp(lambda
+ * W_hat) x of rfd_integrate on all k columns at once:
+ *   v^i = 1;  repeat: mu = 1;  w^i = mu^i / K(a v^i);  d^i = v^i K(a w^i);
+ *             mu = prod_i (d^i)^alpha_i;  then v^i = v^i mu / d^i.
+ * d_out (N float32 device) receives mu (1 everywhere for iters = 0).  Kernel
+ * outputs are lifted to 1e-30 before they divide or enter a power (the
+ * random-feature kernel need not be positive).  Requires rfd_features (or
+ * rfd_gfi) first and 1 <= k <= min(32, max_channels).  Asynchronous on the
+ * plan's stream (temporaries of 4 N k floats from the stream-ordered
+ * allocator); RFD_ENOMEM if they cannot be had. */
+RFD_API rfd_status rfd_barycenter(rfd_plan_t plan, const float* d_mu, int32_t k, int64_t ld_mu, const double* alpha,
+                                  const float* d_area, int32_t iters, float* d_out);
+
 /* One cold pass of the whole path (a2-a6) when F is known up front: the
  * reductions B^T A and B^T F share one pass over the feature matrix.
  * Arguments as rfd_features + rfd_integrate; leaves Phi and G resident. */

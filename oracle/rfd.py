@@ -295,3 +295,51 @@ def rel_frobenius(x: np.ndarray, ref: np.ndarray) -> float:
     """||x - ref||_F / ||ref||_F, the error measure used for every comparison."""
     ref = np.asarray(ref, dtype=np.float64)
     return float(np.linalg.norm(np.asarray(x, dtype=np.float64) - ref) / np.linalg.norm(ref))
+
+
+# ---------------------------------------------------------------------------
+# Wasserstein barycenter with the RFD integrator as the kernel action
+# (App. C, Algorithm wass_barycenter; Solomon et al. 2015, Algorithm 2)
+# ---------------------------------------------------------------------------
+BARY_FLOOR = 1e-30  # kernel outputs below this are lifted to it before division / powers
+
+
+def wasserstein_barycenter(apply_K, mus, area, alpha, iters):
+    """Entropic Wasserstein barycenter of the k distributions mus (N x k) with
+    weights alpha (k), area weights `area` (N) and the kernel action apply_K
+    (x -> K x for an N x k block), following the steps of the algorithm:
+
+        v^i = w^i = 1
+        repeat iters times:
+            mu = 1
+            w^i = mu^i / K(a * v^i)             (step 1)
+            d^i = v^i * K(a * w^i)              (step 2)
+            mu  = mu * (d^i)^alpha_i            (step 3)
+            v^i = v^i * mu / d^i                (step 4, after all i)
+        return mu
+
+    mu is reset at the start of each pass (as in Solomon et al.'s Algorithm 2,
+    which the paper says it follows); kernel outputs are lifted to BARY_FLOOR
+    before they divide or enter a power (the random-feature kernel need not be
+    positive).  All k columns of a step go through one kernel action."""
+    mus = np.asarray(mus, dtype=np.float64)
+    a = np.asarray(area, dtype=np.float64)[:, None]
+    alpha = np.asarray(alpha, dtype=np.float64)
+    v = np.ones_like(mus)
+    mu = np.ones(mus.shape[0])
+    for _ in range(iters):
+        w = mus / np.maximum(apply_K(a * v), BARY_FLOOR)
+        d = v * np.maximum(apply_K(a * w), BARY_FLOOR)
+        mu = np.exp(np.log(d) @ alpha)
+        v = v * mu[:, None] / d
+    return mu
+
+
+def rfd_barycenter(points, mus, area, alpha, iters, eps, lam, m, seed, sigma=0.0, radius=0.0, kernel="cube"):
+    """wasserstein_barycenter with K = exp(lambda W_hat) applied by the low-rank
+    identity (the same estimator as rfd_gfi, one plan for every application)."""
+    omega = sample_frequencies(m, eps, seed, sigma, radius)
+    r = weights(omega, eps, sigma, radius, kernel)
+    A, B = factors(points, omega, r)
+    G = lam * phi1(lam * (B.T @ A))
+    return wasserstein_barycenter(lambda X: X + A @ (G @ (B.T @ X)), mus, area, alpha, iters)

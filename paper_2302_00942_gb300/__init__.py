@@ -112,6 +112,7 @@ def _load():
     sig = {
         "rfd_sample_frequencies": (I32, [I32, D, U64, D, D, DP, DP]),
         "rfd_sample_weights": (I32, [I32, D, U64, D, D, I32, DP, DP]),
+        "rfd_barycenter": (I32, [P, P, I32, I64, DP, P, I32, P]),
         "rfd_plan": (I32, [ctypes.POINTER(rfd_params), P, ctypes.POINTER(P)]),
         "rfd_plan_destroy": (I32, [P]),
         "rfd_features": (I32, [P, P]),
@@ -151,7 +152,7 @@ def _load():
 lib = _load()
 
 # Every function include/rfd.h and include/rfd_testing.h declare (checked against the headers by a test).
-HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_sample_weights", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
+HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_sample_weights", "rfd_barycenter", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
                   "rfd_gfi", "rfd_phi1", "rfd_phi1_noalloc", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
                   "rfd_version", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "rfd_batch_create",
                   "rfd_batch_destroy", "rfd_batch_features", "rfd_batch_integrate", "rfd_batch_gfi",
@@ -316,6 +317,22 @@ class Plan:
         self._chk(F)
         out = torch.empty_like(F) if out is None else self._chk(out)
         rfd_integrate(self.handle, F, F.shape[1], F.stride(0), out, out.stride(0))
+        return out
+
+    def barycenter(self, mu, area, alpha, iters, out=None):
+        """Entropic Wasserstein barycenter of the columns of mu (N x k) on the
+        resident plan (rfd_barycenter): returns the N-vector barycenter."""
+        import torch
+        self._chk(mu)
+        if not (isinstance(area, torch.Tensor) and area.is_cuda and area.dtype == torch.float32 and area.dim() == 1
+                and area.is_contiguous()):
+            raise TypeError("area must be a contiguous float32 CUDA vector")
+        k = mu.shape[1]
+        al = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64).reshape(k))
+        out = torch.empty(mu.shape[0], dtype=torch.float32, device=mu.device) if out is None else out
+        _check(lib.rfd_barycenter(self.handle, mu.data_ptr(), k, mu.stride(0),
+                                  al.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), area.data_ptr(), int(iters),
+                                  out.data_ptr()), "rfd_barycenter")
         return out
 
     def gfi(self, points, F, out=None):
