@@ -216,6 +216,33 @@ RFD_API rfd_status rfd_integrate(rfd_plan_t plan, const float* d_F, int32_t c, i
 RFD_API rfd_status rfd_barycenter(rfd_plan_t plan, const float* d_mu, int32_t k, int64_t ld_mu, const double* alpha,
                                   const float* d_area, int32_t iters, float* d_out);
 
+/* Gromov-Wasserstein building blocks with implicit structure matrices (App.
+ * C.2).  The structure matrix of a cloud is its kernel C = exp(lambda W_hat),
+ * applied by its resident plan, never formed; matrices are float32 device,
+ * row-major.  Both plans must have run rfd_features (or rfd_gfi) and share
+ * one stream; n1, n2 are their point counts.
+ *   rfd_fm_apply: d_Y = C d_X for an n x ncols matrix (ldX, ldY >= ncols),
+ *     rfd_integrate over column chunks of at most max_channels; asynchronous.
+ *   rfd_gw_tensor_product: Algorithm tensor_prod with the square loss,
+ *     d_L (n1 x n2) = (C^{(.)2} p) 1^T + 1 (D^{(.)2} q)^T - 2 C T D^T, with
+ *     C^{(.)2} p = diag(C D_p C^T) from two actions of C (Eq. sq); d_T n1 x n2,
+ *     d_p (n1), d_q (n2); asynchronous (temporaries of 2 max(n1,n2)^2 + 3 n1 n2
+ *     floats from the stream-ordered allocator).
+ *   rfd_gw_line_search: Algorithm line_search, the optimal step of a
+ *     conditional-gradient (F)GW iteration for the transport G, direction dG,
+ *     feature cost M (all n1 x n2) and trade-off alpha: with c_CD = steps 1-2 of
+ *     tensor_prod, a1 = C dG D, b1 = C G D, a = -2 alpha <a1, dG>,
+ *     b = <(1 - alpha) M + alpha c_CD, dG> - 2 alpha (<a1, G> + <b1, dG>);
+ *     tau = clamp(-b / 2a, 0, 1) if a > 0, else 1 if a + b < 0, else 0.
+ *     out3 (host, 3 doubles) = {tau, a, b}; waits for the stream. */
+RFD_API rfd_status rfd_fm_apply(rfd_plan_t plan, const float* d_X, int64_t ncols, int64_t ldX, float* d_Y,
+                                int64_t ldY);
+RFD_API rfd_status rfd_gw_tensor_product(rfd_plan_t plan_C, rfd_plan_t plan_D, const float* d_T, const float* d_p,
+                                         const float* d_q, float* d_L);
+RFD_API rfd_status rfd_gw_line_search(rfd_plan_t plan_C, rfd_plan_t plan_D, double alpha, const float* d_G,
+                                      const float* d_dG, const float* d_M, const float* d_p, const float* d_q,
+                                      double* out3);
+
 /* One cold pass of the whole path (a2-a6) when F is known up front: the
  * reductions B^T A and B^T F share one pass over the feature matrix.
  * Arguments as rfd_features + rfd_integrate; leaves Phi and G resident. */

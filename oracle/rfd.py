@@ -343,3 +343,60 @@ def rfd_barycenter(points, mus, area, alpha, iters, eps, lam, m, seed, sigma=0.0
     A, B = factors(points, omega, r)
     G = lam * phi1(lam * (B.T @ A))
     return wasserstein_barycenter(lambda X: X + A @ (G @ (B.T @ X)), mus, area, alpha, iters)
+
+
+# ---------------------------------------------------------------------------
+# Gromov-Wasserstein tensor product and line search with implicit structure
+# matrices (App. C.2, Eq. sq, Algorithms tensor_prod and line_search)
+# ---------------------------------------------------------------------------
+def hadamard_square_action(apply_C, p):
+    """C^{(.)2} p = diag(C D_p C^T) (Eq. sq), with two actions of C: apply C to
+    D_p (its columns are p_j e_j), transpose, apply C again, take the diagonal."""
+    p = np.asarray(p, dtype=np.float64)
+    Y = apply_C(np.diag(p))          # C D_p
+    Z = apply_C(np.ascontiguousarray(Y.T))   # C (C D_p)^T = C D_p C^T
+    return np.diag(Z).copy()
+
+
+def gw_tensor_product(apply_C, apply_D, T, p, q):
+    """L(C, D, T) for the square loss (f1 = f2 = x^2, h1 = x, h2 = 2x),
+    Algorithm tensor_prod: w1 = (C^{(.)2} p) 1^T, w2 = 1 (D^{(.)2} q)^T,
+    w3 = (FM_D(FM_C(T)^T))^T = C T D^T; return w1 + w2 - 2 w3."""
+    T = np.asarray(T, dtype=np.float64)
+    v1 = hadamard_square_action(apply_C, p)
+    v2 = hadamard_square_action(apply_D, q)
+    w3 = apply_D(np.ascontiguousarray(apply_C(T).T)).T
+    return v1[:, None] + v2[None, :] - 2.0 * w3
+
+
+def gw_line_search(apply_C, apply_D, alpha, G, dG, M, p, q):
+    """Algorithm line_search: the optimal step tau of a conditional-gradient
+    (F)GW iteration, with c_CD from steps 1-2 of tensor_prod,
+    a1 = C dG D, b1 = C G D (D symmetric), a = -2 alpha <a1, dG>,
+    b = <(1 - alpha) M + alpha c_CD, dG> - 2 alpha (<a1, G> + <b1, dG>).
+    Returns (tau, a, b)."""
+    G = np.asarray(G, dtype=np.float64)
+    dG = np.asarray(dG, dtype=np.float64)
+    M = np.asarray(M, dtype=np.float64)
+    v1 = hadamard_square_action(apply_C, p)
+    v2 = hadamard_square_action(apply_D, q)
+    c_cd = v1[:, None] + v2[None, :]
+    a1 = apply_D(np.ascontiguousarray(apply_C(dG).T)).T
+    b1 = apply_D(np.ascontiguousarray(apply_C(G).T)).T
+    a = -2.0 * alpha * float(np.sum(a1 * dG))
+    b = float(np.sum(((1.0 - alpha) * M + alpha * c_cd) * dG)) - 2.0 * alpha * (float(np.sum(a1 * G)) +
+                                                                              float(np.sum(b1 * dG)))
+    if a > 0:
+        tau = min(1.0, max(0.0, -b / (2.0 * a)))
+    else:
+        tau = 1.0 if a + b < 0 else 0.0
+    return tau, a, b
+
+
+def rfd_kernel_action(points, eps, lam, m, seed, sigma=0.0, radius=0.0, kernel="cube"):
+    """x -> exp(lambda W_hat) x for the cloud (the FM of one resident plan)."""
+    omega = sample_frequencies(m, eps, seed, sigma, radius)
+    r = weights(omega, eps, sigma, radius, kernel)
+    A, B = factors(points, omega, r)
+    G = lam * phi1(lam * (B.T @ A))
+    return lambda X: X + A @ (G @ (B.T @ X))

@@ -19,7 +19,7 @@ import numpy as np
 __all__ = [
     "RFD_OK", "RFD_EINVAL", "RFD_ENOMEM", "RFD_ECUDA", "RFD_ENOTREADY", "RFD_ETIMEDOUT", "RFD_ENUMERIC",
     "RFD_EBUSY", "RFD_ENOTSUP", "RFD_FP32_PLAIN", "RFD_BF16_TC", "RfdError", "rfd_params", "rfd_stats",
-    "lib", "lib_path", "rfd_sample_frequencies", "rfd_sample_weights", "RFD_KERNEL_CUBE", "RFD_KERNEL_BALL", "rfd_plan", "rfd_plan_destroy", "rfd_features",
+    "lib", "lib_path", "gw_tensor_product", "gw_line_search", "rfd_sample_frequencies", "rfd_sample_weights", "RFD_KERNEL_CUBE", "RFD_KERNEL_BALL", "rfd_plan", "rfd_plan_destroy", "rfd_features",
     "rfd_integrate", "rfd_gfi", "rfd_phi1", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
     "rfd_version", "RFD_FLAG_TIMING", "STEP_NAMES", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "Plan", "Batch", "rfd_batch_item", "HEADER_SYMBOLS",
     "RFD_FLAG_NATIVE_FP64", "RFD_FLAG_GRAPH", "RFD_FLAG_AUTOTUNE", "Server", "rfd_request", "rfd_result", "rfd_server_config",
@@ -113,6 +113,9 @@ def _load():
         "rfd_sample_frequencies": (I32, [I32, D, U64, D, D, DP, DP]),
         "rfd_sample_weights": (I32, [I32, D, U64, D, D, I32, DP, DP]),
         "rfd_barycenter": (I32, [P, P, I32, I64, DP, P, I32, P]),
+        "rfd_fm_apply": (I32, [P, P, I64, I64, P, I64]),
+        "rfd_gw_tensor_product": (I32, [P, P, P, P, P, P]),
+        "rfd_gw_line_search": (I32, [P, P, D, P, P, P, P, P, DP]),
         "rfd_plan": (I32, [ctypes.POINTER(rfd_params), P, ctypes.POINTER(P)]),
         "rfd_plan_destroy": (I32, [P]),
         "rfd_features": (I32, [P, P]),
@@ -152,7 +155,8 @@ def _load():
 lib = _load()
 
 # Every function include/rfd.h and include/rfd_testing.h declare (checked against the headers by a test).
-HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_sample_weights", "rfd_barycenter", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
+HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_sample_weights", "rfd_barycenter", "rfd_fm_apply",
+                  "rfd_gw_tensor_product", "rfd_gw_line_search", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
                   "rfd_gfi", "rfd_phi1", "rfd_phi1_noalloc", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
                   "rfd_version", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "rfd_batch_create",
                   "rfd_batch_destroy", "rfd_batch_features", "rfd_batch_integrate", "rfd_batch_gfi",
@@ -335,6 +339,15 @@ class Plan:
                                   out.data_ptr()), "rfd_barycenter")
         return out
 
+    def fm_apply(self, X, out=None):
+        """Y = exp(lambda W_hat) X for an N x k float32 CUDA matrix (any k; rfd_fm_apply)."""
+        import torch
+        self._chk(X)
+        out = torch.empty_like(X) if out is None else self._chk(out)
+        _check(lib.rfd_fm_apply(self.handle, X.data_ptr(), X.shape[1], X.stride(0), out.data_ptr(), out.stride(0)),
+               "rfd_fm_apply")
+        return out
+
     def gfi(self, points, F, out=None):
         import torch
         self._chk(points)
@@ -498,3 +511,28 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def gw_tensor_product(plan_C, plan_D, T, p, q, out=None):
+    """Algorithm tensor_prod (App. C.2) on two resident plans: L = (C^2 p) 1^T + 1 (D^2 q)^T - 2 C T D^T."""
+    import torch
+    out = torch.empty_like(T) if out is None else out
+    for t in (T, p, q, out):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise TypeError("expected contiguous float32 CUDA tensors")
+    _check(lib.rfd_gw_tensor_product(plan_C.handle, plan_D.handle, T.data_ptr(), p.data_ptr(), q.data_ptr(),
+                                     out.data_ptr()), "rfd_gw_tensor_product")
+    return out
+
+
+def gw_line_search(plan_C, plan_D, alpha, G, dG, M, p, q):
+    """Algorithm line_search (App. C.2) on two resident plans: (tau, a, b)."""
+    import torch
+    for t in (G, dG, M, p, q):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise TypeError("expected contiguous float32 CUDA tensors")
+    res = np.zeros(3, dtype=np.float64)
+    _check(lib.rfd_gw_line_search(plan_C.handle, plan_D.handle, float(alpha), G.data_ptr(), dG.data_ptr(),
+                                  M.data_ptr(), p.data_ptr(), q.data_ptr(),
+                                  res.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "rfd_gw_line_search")
+    return float(res[0]), float(res[1]), float(res[2])
