@@ -67,7 +67,9 @@ def parse():
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the reductions' default launch parameters (a fixed launch sequence for profiling)")
-    ap.add_argument("--sections", default="main,batched,serving",
+    ap.add_argument("--gw-n", type=int, default=8192, help="points per cloud of the GW workload (0: skip)")
+    ap.add_argument("--gw-steps", type=int, default=5)
+    ap.add_argument("--sections", default="main,batched,serving,gw",
                     help="comma list of main, batched, serving (profiling runs select one; the JSON line then "
                          "carries only what ran)")
     return ap.parse_args()
@@ -287,6 +289,64 @@ def bench_batched(args, dev, stream, D):
 # ---------------------------------------------------------------------------
 # serving: Poisson arrivals of GFI requests through rfd_submit / rfd_poll
 # ---------------------------------------------------------------------------
+def bench_gw(args, dev, stream, D):
+    """One (F)GW conditional-gradient iteration's FM-heavy steps (App. C.2) between
+    two random 3-D distributions of gw_n points, at the experiments' m = 16,
+    eps = 0.3, lambda = -0.2 (x m/N): the tensor product L(C, D, T) and the line
+    search, on two resident BF16 plans (graph replay, 256-column chunks)."""
+    import torch
+    import paper_2302_00942_gb300 as rfd
+    n, m, eps, lam = args.gw_n, 16, 0.3, -0.2
+    X, Y, T, p, q, Gt, M = synth.gw_problem(n, n, seed=0)
+    lam_a = lam * m / n
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)  # noqa: E731
+    pc = rfd.Plan(n, m, eps, lam_a, 21, max_channels=256, precision=rfd.RFD_BF16_TC, stream=stream, graph=True)
+    pd = rfd.Plan(n, m, eps, lam_a, 22, max_channels=256, precision=rfd.RFD_BF16_TC, stream=stream, graph=True)
+    pc.features(cu(X))
+    pd.features(cu(Y))
+    Td, pv, qv = cu(T), cu(p), cu(q)
+    G = np.outer(p, q)
+    Gd, dGd, Md = cu(G), cu(Gt - G), cu(M)
+    L = rfd.gw_tensor_product(pc, pd, Td, pv, qv)  # warm-up (captures the graphs)
+    rfd.gw_line_search(pc, pd, 0.5, Gd, dGd, Md, pv, qv)
+    torch.cuda.synchronize(dev)
+    D.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k = max(1, args.gw_steps)
+    e0.record(stream)
+    for _ in range(k):
+        rfd.gw_tensor_product(pc, pd, Td, pv, qv, out=L)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    tp_ms = D.max(e0.elapsed_time(e1) / k)
+    e0.record(stream)
+    for _ in range(k):
+        ls = rfd.gw_line_search(pc, pd, 0.5, Gd, dGd, Md, pv, qv)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ls_ms = D.max(e0.elapsed_time(e1) / k)
+    io = 8.0 * n * n  # T in, L out (FP32)
+    peaks, _ = load_peaks()
+    res = {"workload": f"two uniform random 3-D clouds of {n} points, m={m}, eps={eps}, lambda={lam} x m/N, "
+                       "dense coupling T (n x n, FP32)",
+           "tensor_product_ms": tp_ms, "line_search_ms": ls_ms, "line_search": {"tau": ls[0], "a": ls[1], "b": ls[2]},
+           "tensor_product_io": {"bytes": io, "achieved_gbs": io / (tp_ms * 1e-3) / 1e9,
+                                 "frac_of_measured_hbm": io / (tp_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
+    if D.rank == 0 and D.ws == 1 and not args.no_cpu:
+        import oracle
+        ac = oracle.rfd_kernel_action(X, eps, lam_a, m, 21)
+        ad = oracle.rfd_kernel_action(Y, eps, lam_a, m, 22)
+        t0 = time.perf_counter()
+        Lref = oracle.gw_tensor_product(ac, ad, T, p, q)
+        t_or = time.perf_counter() - t0
+        res["cpu_baseline"] = {"tensor_product_ms": t_or * 1e3, "cores": cpu_cores(), "kind": "oracle",
+                               "sample": "one FP64 tensor product at the same size",
+                               "rel_err_vs_oracle": oracle.rel_frobenius(L.cpu().numpy(), Lref)}
+    pc.close()
+    pd.close()
+    return res
+
+
 def bench_serving(args, dev):
     import torch
     import paper_2302_00942_gb300 as rfd
@@ -403,6 +463,8 @@ def main():
             res["batched"] = bench_batched(args, dev, stream, D)
         if "serving" in sections and args.serve_seconds > 0:
             res["serving"] = bench_serving(args, dev)
+        if "gw" in sections and args.gw_n > 0:
+            res["gw"] = bench_gw(args, dev, stream, D)
         if rank == 0:
             print(json.dumps(res))
         D.close()
@@ -640,6 +702,8 @@ def main():
     if "serving" in sections and args.serve_seconds > 0 and prec == rfd.RFD_BF16_TC:
         res["serving"] = bench_serving(args, dev)
         res["p99_ms"] = res["serving"]["p99_ms"]
+    if "gw" in sections and args.gw_n > 0 and prec == rfd.RFD_BF16_TC:
+        res["gw"] = bench_gw(args, dev, stream, D)
     if rank == 0 and ws == 1 and not args.no_cpu:
         ns = min(args.cpu_sample, n)
         t = time_oracle(pts[:ns], F[:ns], spec.eps, lam, m, spec.seed)

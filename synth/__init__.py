@@ -22,7 +22,7 @@ import numpy as np
 
 __all__ = [
     "rng_for", "unit_sphere", "torus", "ellipsoid_union", "gaussian_field",
-    "CloudSpec", "config_single", "batched_specs", "serving_trace", "make_cloud",
+    "CloudSpec", "config_single", "batched_specs", "serving_trace", "make_cloud", "gw_problem",
 ]
 
 # stream ids keep the points, the field and the per-cloud parameters independent
@@ -30,6 +30,7 @@ _STREAM_POINTS = 1
 _STREAM_FIELD = 2
 _STREAM_PARAMS = 3
 _STREAM_ARRIVALS = 4
+_STREAM_GW = 5
 
 
 def rng_for(seed: int, stream: int, sub: int = 0) -> np.random.Generator:
@@ -213,3 +214,25 @@ def serving_trace(rate: float = 2000.0, duration: float = 10.0, seed: int = 0,
         lam = float(rng.uniform(lam_lo, lam_hi))
         out.append((t, CloudSpec(kind, n, m, c, eps, lam, seed * 7919 + i, scale=scale, sub=i), -1))
     return out
+
+
+def gw_problem(n1: int, n2: int, seed: int = 0):
+    """Inputs of one (F)GW conditional-gradient iteration between two random 3-D
+    point distributions (App. C.2 experiments: uniform in the unit cube).
+
+    Returns (X, Y, T, p, q, Gt, M): clouds X (n1 x 3) and Y (n2 x 3), a positive
+    coupling T (n1 x n2, sum 1) with marginals p, q, a second coupling Gt (the
+    linearised step's target, so dG = Gt - p q^T) and a feature-cost matrix M
+    (distances between random binary node labels, as the FGW experiments do).
+    All float64."""
+    rng = rng_for(seed, _STREAM_GW)
+    X = rng.uniform(0.0, 1.0, (n1, 3))
+    Y = rng.uniform(0.0, 1.0, (n2, 3))
+    T = rng.uniform(0.0, 1.0, (n1, n2))
+    T /= T.sum()
+    p, q = T.sum(1), T.sum(0)
+    Gt = rng.uniform(0.0, 1.0, (n1, n2))
+    Gt /= Gt.sum()
+    la, lb = rng.integers(0, 2, n1), rng.integers(0, 2, n2)
+    M = (la[:, None] != lb[None, :]).astype(np.float64)
+    return X, Y, T, p, q, Gt, M
