@@ -400,3 +400,42 @@ def rfd_kernel_action(points, eps, lam, m, seed, sigma=0.0, radius=0.0, kernel="
     A, B = factors(points, omega, r)
     G = lam * phi1(lam * (B.T @ A))
     return lambda X: X + A @ (G @ (B.T @ X))
+
+
+# ---- kernel eigenvalues (Sec. 3.3 point-cloud classification; App. E) --------
+
+def kernel_eigenvalues(A, B, lam, n, k=None, largest=False):
+    """The k smallest (largest=False, ascending) or k largest (descending) of
+    the N eigenvalues of exp(lam W_hat), W_hat = A B^T (N x N, rank <= m),
+    from the low-rank factors (Sec. 3.3: eigenvalues from the factorisation,
+    after Nakatsukasa 2019).
+
+    A B^T and the m x m matrix B^T A share their nonzero eigenvalues (with
+    multiplicity), so W_hat's spectrum is eig(B^T A) plus N - m zeros when
+    N >= m; when N < m, B^T A carries m - N extra zeros (rank <= N), and the
+    m - N eigenvalues of smallest modulus are dropped.  exp(lam W_hat) has the
+    eigenvalues exp(lam mu) of the same eigenvectors; each zero gives 1.
+    W_hat is symmetric, so every mu is real (eig of B^T A by LAPACK; the
+    imaginary parts are rounding)."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    m = A.shape[1]
+    mu = np.linalg.eigvals(B.T @ A)
+    assert np.all(np.abs(mu.imag) <= 1e-8 * max(1.0, np.abs(mu).max())), "complex eigenvalues"
+    mu = mu.real
+    if n < m:
+        mu = mu[np.argsort(np.abs(mu), kind="stable")[m - n:]]
+    kappa = np.concatenate([np.exp(lam * mu), np.ones(max(n - m, 0))])
+    kappa = np.sort(kappa)
+    if largest:
+        kappa = kappa[::-1]
+    return kappa[: (n if k is None else k)].copy()
+
+
+def rfd_kernel_eigenvalues(points, eps, lam, m, seed, k=None, largest=False, sigma=0.0, radius=0.0,
+                           kernel="cube"):
+    """kernel_eigenvalues of the cloud's RFD factors (same frequencies as rfd_gfi)."""
+    omega = sample_frequencies(m, eps, seed, sigma, radius)
+    r = weights(omega, eps, sigma, radius, kernel)
+    A, B = factors(points, omega, r)
+    return kernel_eigenvalues(A, B, lam, len(points), k, largest)
