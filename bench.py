@@ -69,7 +69,8 @@ def parse():
                     help="keep the reductions' default launch parameters (a fixed launch sequence for profiling)")
     ap.add_argument("--gw-n", type=int, default=8192, help="points per cloud of the GW workload (0: skip)")
     ap.add_argument("--gw-steps", type=int, default=5)
-    ap.add_argument("--sections", default="main,batched,serving,gw",
+    ap.add_argument("--eigen-clouds", type=int, default=1024, help="clouds of the kernel-eigenvalue workload (0: skip)")
+    ap.add_argument("--sections", default="main,batched,serving,gw,eigen",
                     help="comma list of main, batched, serving (profiling runs select one; the JSON line then "
                          "carries only what ran)")
     return ap.parse_args()
@@ -347,6 +348,66 @@ def bench_gw(args, dev, stream, D):
     return res
 
 
+def bench_eigen(args, dev, stream, D):
+    """Kernel eigenvalues for shape classification (Sec. 3.3): the 32 smallest
+    eigenvalues of exp(lambda W_hat) for every cloud of a batch of 2048-point
+    shapes (eps = 0.1, lambda = -0.1 x m/N, m = 64), from points: steps a2-a3
+    batched (graph replay), then one CTA per cloud on the m x m problem."""
+    import torch
+    import paper_2302_00942_gb300 as rfd
+    specs = synth.eigen_specs(count=args.eigen_clouds, seed=0)
+    clouds = [synth.make_cloud(s)[0] for s in specs]
+    lams = [s.lam * s.m / s.n for s in specs]
+    k = 32
+
+    def mk_plans():
+        return [rfd.Plan(s.n, s.m, s.eps, lam, s.seed, max_channels=1, precision=rfd.RFD_BF16_TC, stream=stream)
+                for s, lam in zip(specs, lams)]
+    plans = mk_plans()
+    items = [{"points": torch.from_numpy(p).to(dev)} for p in clouds]
+    gb = rfd.Batch(plans, stream=stream, graph=True)
+    out = gb.eigenvalues(items, k)
+    gb.eigenvalues(items, k, out=out)
+    torch.cuda.synchronize(dev)
+    D.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = 5
+    e0.record(stream)
+    for _ in range(steps):
+        gb.eigenvalues(items, k, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = D.max(e0.elapsed_time(e1) / steps)
+    gb.close()
+    tb = rfd.Batch(plans, stream=stream, timing=True)
+    tb.eigenvalues(items, k)
+    tb.stats_reset()
+    for _ in range(3):
+        tb.eigenvalues(items, k, out=out)
+    tb.sync()
+    st = tb.stats()
+    tb.close()
+    got = out.cpu().numpy()
+    for p in plans:
+        p.close()
+    n_cl = len(specs)
+    res = {"workload": f"{n_cl} shapes (sphere / torus / ellipsoid union, 2048 points each), m=64, eps=0.1, "
+                       f"lambda=-0.1 x m/N, k={k} smallest eigenvalues of exp(lambda W_hat)",
+           "value": D.ws * n_cl / (ms * 1e-3), "unit": "clouds/s", "ms_per_batch": ms,
+           "step_ms": {kk: round(v, 4) for kk, v in st["step_ms"].items() if v}}
+    if D.rank == 0 and D.ws == 1 and not args.no_cpu:
+        import oracle
+        sample = min(16, n_cl)
+        t0 = time.perf_counter()
+        refs = [oracle.rfd_kernel_eigenvalues(clouds[i], specs[i].eps, lams[i], specs[i].m, specs[i].seed, k=k)
+                for i in range(sample)]
+        t = time.perf_counter() - t0
+        err = max(float(np.max(np.abs(got[i] - refs[i]) / refs[i])) for i in range(sample))
+        res["cpu_baseline"] = {"value": sample / t, "unit": "clouds/s", "cores": cpu_cores(), "kind": "oracle",
+                               "sample": f"first {sample} clouds, FP64", "max_rel_err_vs_oracle": err}
+    return res
+
+
 def bench_serving(args, dev):
     import torch
     import paper_2302_00942_gb300 as rfd
@@ -465,6 +526,8 @@ def main():
             res["serving"] = bench_serving(args, dev)
         if "gw" in sections and args.gw_n > 0:
             res["gw"] = bench_gw(args, dev, stream, D)
+        if "eigen" in sections and args.eigen_clouds > 0:
+            res["eigen"] = bench_eigen(args, dev, stream, D)
         if rank == 0:
             print(json.dumps(res))
         D.close()
@@ -704,6 +767,8 @@ def main():
         res["p99_ms"] = res["serving"]["p99_ms"]
     if "gw" in sections and args.gw_n > 0 and prec == rfd.RFD_BF16_TC:
         res["gw"] = bench_gw(args, dev, stream, D)
+    if "eigen" in sections and args.eigen_clouds > 0 and prec == rfd.RFD_BF16_TC:
+        res["eigen"] = bench_eigen(args, dev, stream, D)
     if rank == 0 and ws == 1 and not args.no_cpu:
         ns = min(args.cpu_sample, n)
         t = time_oracle(pts[:ns], F[:ns], spec.eps, lam, m, spec.seed)

@@ -122,7 +122,8 @@ enum {
   RFD_STEP_PHI1 = 4,      /* a4: G = lambda phi1(lambda M), FP64   */
   RFD_STEP_SMALL = 5,     /* a5: Z = diag(s sgn r) G Y             */
   RFD_STEP_APPLY = 6,     /* a6: out = F + Phi Z                   */
-  RFD_NUM_STEPS = 7
+  RFD_STEP_EIGEN = 7,     /* kernel eigenvalues (m x m problem)    */
+  RFD_NUM_STEPS = 8
 };
 
 /* Statistics of a plan.  norm1 .. splits describe the last rfd_features /
@@ -243,6 +244,21 @@ RFD_API rfd_status rfd_gw_line_search(rfd_plan_t plan_C, rfd_plan_t plan_D, doub
                                       const float* d_dG, const float* d_M, const float* d_p, const float* d_q,
                                       double* out3);
 
+/* Eigenvalues of the cloud's RFD kernel exp(lambda W_hat) (Sec. 3.3: point-
+ * cloud classification by the kernel's k smallest eigenvalues, computed from
+ * the low-rank factorisation; App. E: graph classification by the k largest).
+ * W_hat = A B^T is symmetric of rank <= m: its nonzero eigenvalues are those
+ * of the m x m matrix M = B^T A, so exp(lambda W_hat) has the eigenvalues
+ * exp(lambda mu) for the m eigenvalues mu of M and 1 with multiplicity N - m
+ * (when N < m, the m - N eigenvalues of M of smallest modulus are the rank
+ * deficiency and are dropped).  Writes the k smallest (largest = 0,
+ * ascending) or the k largest (largest = 1, descending) of these N values to
+ * d_out (k float32, device).  Needs the resident M of rfd_features / rfd_gfi;
+ * 1 <= k <= N and m <= 128 (RFD_EINVAL otherwise).  Asynchronous on the
+ * plan's stream; M is unchanged.  FP32 arithmetic from the FP64 M (Cholesky
+ * of M diag(sgn r), then cyclic Jacobi on the symmetric m x m matrix). */
+RFD_API rfd_status rfd_eigenvalues(rfd_plan_t plan, int32_t k, int32_t largest, float* d_out);
+
 /* One cold pass of the whole path (a2-a6) when F is known up front: the
  * reductions B^T A and B^T F share one pass over the feature matrix.
  * Arguments as rfd_features + rfd_integrate; leaves Phi and G resident. */
@@ -333,6 +349,14 @@ RFD_API rfd_status rfd_batch_sync(rfd_batch_t batch);
 /* Step timings / launch count of the batch (RFD_FLAG_TIMING), as rfd_plan_stats. */
 RFD_API rfd_status rfd_batch_stats(rfd_batch_t batch, rfd_stats* out);
 RFD_API rfd_status rfd_batch_stats_reset(rfd_batch_t batch);
+/* Batched rfd_eigenvalues from points: steps a2-a3 for every cloud
+ * (items[k].d_points; d_F, d_out and c unused), no step a4 (each plan's G is
+ * left invalid: run rfd_batch_features before integrating), then the k
+ * smallest / largest eigenvalues of every cloud's exp(lambda W_hat) into
+ * d_out (count x k float32, device, row k per cloud).  Every plan needs
+ * m <= 128 and N >= k.  Asynchronous on the batch stream. */
+RFD_API rfd_status rfd_batch_eigenvalues(rfd_batch_t batch, const rfd_batch_item* items, int32_t k, int32_t largest,
+                                         float* d_out);
 
 /* ---------------------------------------------------------------------------
  * Serving: a request loop for GFI requests (the paper's graph field

@@ -49,7 +49,7 @@ RFD_FLAG_TIMING = 1
 RFD_FLAG_NATIVE_FP64 = 2
 RFD_FLAG_GRAPH = 4
 RFD_FLAG_AUTOTUNE = 8
-STEP_NAMES = ("features", "field", "gram", "reduce", "phi1", "small", "apply")
+STEP_NAMES = ("features", "field", "gram", "reduce", "phi1", "small", "apply", "eigen")
 
 
 class rfd_stats(ctypes.Structure):
@@ -116,6 +116,7 @@ def _load():
         "rfd_fm_apply": (I32, [P, P, I64, I64, P, I64]),
         "rfd_gw_tensor_product": (I32, [P, P, P, P, P, P]),
         "rfd_gw_line_search": (I32, [P, P, D, P, P, P, P, P, DP]),
+        "rfd_eigenvalues": (I32, [P, I32, I32, P]),
         "rfd_plan": (I32, [ctypes.POINTER(rfd_params), P, ctypes.POINTER(P)]),
         "rfd_plan_destroy": (I32, [P]),
         "rfd_features": (I32, [P, P]),
@@ -136,6 +137,7 @@ def _load():
         "rfd_batch_features": (I32, [P, ctypes.POINTER(rfd_batch_item)]),
         "rfd_batch_integrate": (I32, [P, ctypes.POINTER(rfd_batch_item)]),
         "rfd_batch_gfi": (I32, [P, ctypes.POINTER(rfd_batch_item)]),
+        "rfd_batch_eigenvalues": (I32, [P, ctypes.POINTER(rfd_batch_item), I32, I32, P]),
         "rfd_batch_sync": (I32, [P]),
         "rfd_batch_stats": (I32, [P, ctypes.POINTER(rfd_stats)]),
         "rfd_batch_stats_reset": (I32, [P]),
@@ -156,7 +158,7 @@ lib = _load()
 
 # Every function include/rfd.h and include/rfd_testing.h declare (checked against the headers by a test).
 HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_sample_weights", "rfd_barycenter", "rfd_fm_apply",
-                  "rfd_gw_tensor_product", "rfd_gw_line_search", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
+                  "rfd_gw_tensor_product", "rfd_gw_line_search", "rfd_eigenvalues", "rfd_batch_eigenvalues", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
                   "rfd_gfi", "rfd_phi1", "rfd_phi1_noalloc", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
                   "rfd_version", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "rfd_batch_create",
                   "rfd_batch_destroy", "rfd_batch_features", "rfd_batch_integrate", "rfd_batch_gfi",
@@ -348,6 +350,14 @@ class Plan:
                "rfd_fm_apply")
         return out
 
+    def eigenvalues(self, k, largest=False, out=None):
+        """The k smallest (ascending) or largest (descending) eigenvalues of
+        exp(lambda W_hat) from the resident M (rfd_eigenvalues): float32 CUDA (k,)."""
+        import torch
+        out = torch.empty(int(k), dtype=torch.float32, device="cuda") if out is None else out
+        _check(lib.rfd_eigenvalues(self.handle, int(k), 1 if largest else 0, out.data_ptr()), "rfd_eigenvalues")
+        return out
+
     def gfi(self, points, F, out=None):
         import torch
         self._chk(points)
@@ -429,6 +439,17 @@ class Batch:
         arr, outs = self._items(items, True)
         _check(lib.rfd_batch_integrate(self.handle, arr), "rfd_batch_integrate")
         return outs
+
+    def eigenvalues(self, items, k, largest=False, out=None):
+        """Steps a2-a3 from items[i]["points"], then every cloud's k smallest /
+        largest kernel eigenvalues (rfd_batch_eigenvalues): float32 CUDA (count, k)."""
+        import torch
+        arr, _ = self._items(items, False)
+        if out is None:
+            out = torch.empty((len(self.plans), int(k)), dtype=torch.float32, device=items[0]["points"].device)
+        _check(lib.rfd_batch_eigenvalues(self.handle, arr, int(k), 1 if largest else 0, out.data_ptr()),
+               "rfd_batch_eigenvalues")
+        return out
 
     def sync(self):
         _check(lib.rfd_batch_sync(self.handle), "rfd_batch_sync")

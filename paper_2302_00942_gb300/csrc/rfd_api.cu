@@ -1006,6 +1006,24 @@ rfd_status rfd_batch_integrate(rfd_batch_t b, const rfd_batch_item* items) {
 }
 rfd_status rfd_batch_gfi(rfd_batch_t b, const rfd_batch_item* items) { return batch_call(b, kModeGfi, items); }
 
+rfd_status rfd_batch_eigenvalues(rfd_batch_t b, const rfd_batch_item* items, int32_t k, int32_t largest,
+                                 float* d_out) {
+  if (!b || !items || !d_out) return fail(RFD_EINVAL, "null batch, items or output");
+  if (largest != 0 && largest != 1) return fail(RFD_EINVAL, "largest must be 0 or 1");
+  const int n = (int)b->plans.size();
+  rfd_status s = check_eigen_args(b->plans.data(), n, k);
+  if (s != RFD_OK) return s;
+  std::vector<CloudCall> calls((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    if (!items[i].d_points) return fail(RFD_EINVAL, "null points for item " + std::to_string(i));
+    calls[i] = CloudCall{items[i].d_points, nullptr, nullptr, 0, 0, 1, 0};
+  }
+  CallScope call(&b->timing, b->stream);
+  s = batch_run(b->impl, kModeGram, calls.data(), &b->timing);
+  if (s == RFD_OK) s = batch_eigenvalues(b->plans.data(), n, k, largest, d_out, b->stream, &b->timing);
+  return s;
+}
+
 rfd_status rfd_batch_sync(rfd_batch_t b) {
   if (!b) return fail(RFD_EINVAL, "null batch");
   RFD_CUDA(cudaStreamSynchronize(b->stream));

@@ -510,6 +510,8 @@ rfd_status run_segment(BatchImpl* b, const int (&key)[4], bool graph, Timing* tm
 
 rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm) {
   cudaStream_t st = b->st;
+  const bool gram_only = mode == kModeGram;
+  if (gram_only) mode = kModeFeatures;
   const int n = b->count;
   // per-call tables: the callers' buffers, and the apply blocks (they depend on c)
   int max_c = 1;
@@ -533,11 +535,12 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
                                                            (size_t)n * sizeof(CloudCall));
   BCK(cudaMemcpyAsync(b->d_calls, stage, b->stage_bytes, cudaMemcpyHostToDevice, st));
   BCK(cudaEventRecord(b->stage_done[slot], st));
-  const bool with_phi = mode != kModeIntegrate, with_apply = mode != kModeFeatures;
+  const bool with_feat = mode != kModeIntegrate, with_phi = with_feat && !gram_only;
+  const bool with_apply = mode != kModeFeatures;
   const bool graph = (b->options & kBatchGraphs) && (!with_phi || b->phi_batched);
 
   auto reductions = [&](cudaStream_t s, Timing* t) -> rfd_status {
-    if (with_phi) {
+    if (with_feat) {
       StepScope sc(t, s, RFD_STEP_FEATURES);
       BCK(launch_features_batched(b->d_feat, b->d_feat_prefix, n, b->feat_blocks, b->d_calls, s));
     }
@@ -564,6 +567,11 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
     return RFD_OK;
   };
 
+  if (gram_only) {  // steps a2-a3: M only, and G no longer matches the points
+    for (rfd_plan_s* pl : b->plans) pl->have_G = false;
+    const int key[4] = {mode, -3, 0, 0};
+    return run_segment(b, key, graph, tm, reductions);
+  }
   if (!with_phi) {
     const int key[4] = {mode, -1, cg, apply_blocks};
     return run_segment(b, key, graph, tm, [&](cudaStream_t s, Timing* t) -> rfd_status {

@@ -1,0 +1,408 @@
+// Eigenvalues of a cloud's RFD kernel exp(lambda W_hat) from its low-rank
+// factors (Sec. 3.3, point-cloud classification by the kernel's k smallest
+// eigenvalues; App. E, graph classification by the k largest; the
+// factorisation route after Nakatsukasa 2019).
+//
+// W_hat = A B^T = Phi Omega_b Sigma Omega_b Phi^T, Sigma = diag(sgn r), is
+// symmetric of rank <= m.  Its nonzero eigenvalues are those of the m x m
+// matrix M = B^T A = P Sigma with P = Omega_b Phi^T Phi Omega_b = M Sigma
+// (symmetric positive semidefinite).  With P = L L^T (Cholesky; a column whose
+// pivot falls below the rounding level of P is dropped, the semidefinite
+// case), eig(P Sigma) = eig(L^T Sigma L): a symmetric m x m matrix, here
+// diagonalised by cyclic Jacobi rotations (round-robin ordering, m/2 disjoint
+// rotations at a time).  exp(lambda W_hat) then has the eigenvalues
+// exp(lambda mu) and, for the N - m directions W_hat annihilates, 1; when
+// N < m, the m - N eigenvalues of smallest modulus belong to the rank
+// deficiency and are dropped.
+//
+// One CTA per cloud, all in shared memory: the Cholesky factor in FP64, the
+// Jacobi iteration in FP32 with its rotations accumulated, and each
+// eigenvalue then taken as the FP64 Rayleigh quotient of its FP32 eigenvector
+// on the FP64 factor (error second order in the eigenvector's, so the FP32
+// rotations do not limit the eigenvalues).  No device-side waits.
+#include <cuda_runtime.h>
+#include <cmath>
+#include <string>
+#include <vector>
+#include "kernels.h"
+#include "rfd_internal.h"
+#include "rfd_plan.h"
+
+namespace rfd {
+
+namespace {
+
+constexpr int kEigThreads = 256;
+constexpr int kEigMaxM = 128;
+constexpr int kMaxSweeps = 20;
+// stop when off(H) <= kOffTol ||H||_F: the eigenvectors are then good to ~1e-5,
+// and the FP64 Rayleigh quotients good to ~1e-10 relative (second order)
+constexpr float kOffTol = 1e-5f;
+
+struct EigJob {
+  const double* M;   // m x m, row-major: M = B^T A
+  const double* oa;  // column scales of A (sign of r)
+  double lambda;
+  int64_t n;
+  int32_t m, pad_;
+};
+
+// shared memory: L (FP64, packed lower triangle), the Jacobi iterate H and the
+// accumulated rotations V (FP32, m x (m+1)), then small arrays
+size_t eig_smem_bytes(int m) {
+  const size_t ld = (size_t)m + 1, tri = (size_t)m * (m + 1) / 2;
+  return tri * sizeof(double) + 2 * m * ld * sizeof(float) + (size_t)m * 2 * sizeof(double) +
+         (size_t)(3 * m + 64) * sizeof(float) + (size_t)2 * m * sizeof(int);
+}
+
+__device__ float block_sum(float v, float* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  float s = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // j <= i
+
+// insertion sort of x[0, cnt) by key(x) ascending (one thread; cnt <= 128)
+template <typename Key>
+__device__ void sort_small(double* x, int cnt, Key key) {
+  for (int i = 1; i < cnt; ++i) {
+    const double v = x[i];
+    int j = i - 1;
+    while (j >= 0 && key(x[j]) > key(v)) {
+      x[j + 1] = x[j];
+      --j;
+    }
+    x[j + 1] = v;
+  }
+}
+
+template <int MAXM>
+__global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob* __restrict__ jobs, int k,
+                                                                   int largest, float* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const EigJob jb = jobs[blockIdx.x];
+  const int m = jb.m, ld = m + 1, half = m / 2, tid = threadIdx.x, nt = blockDim.x;
+  double* L = reinterpret_cast<double*>(smem_raw);      // P, then its Cholesky factor (packed lower)
+  double* mu = L + (size_t)m * (m + 1) / 2;             // 2m: eigenvalues, kernel eigenvalues
+  float* H = reinterpret_cast<float*>(mu + 2 * m);      // L^T Sigma L, then the Jacobi iterate
+  float* V = H + m * ld;                                // accumulated rotations (columns: eigenvectors)
+  float* sig = V + m * ld;                              // Sigma
+  float* cs = sig + m;                                  // rotation (c, s, t) of each pair
+  float* red = cs + 2 * m;                              // 64 floats of reduction scratch
+  int* pq = reinterpret_cast<int*>(red + 64);           // (p, q) of each pair
+
+  // P = M Sigma, symmetrised (M Sigma is symmetric up to rounding), FP64
+  for (int i = tid; i < m; i += nt) sig[i] = jb.oa[i] < 0.0 ? -1.f : 1.f;
+  for (int e = tid; e < m * m; e += nt) {
+    const int i = e / m, j = e % m;
+    if (j > i) continue;
+    const double si = jb.oa[i] < 0.0 ? -1.0 : 1.0, sj = jb.oa[j] < 0.0 ? -1.0 : 1.0;
+    L[tri(i, j)] = 0.5 * (jb.M[(size_t)i * m + j] * sj + jb.M[(size_t)j * m + i] * si);
+  }
+  __syncthreads();
+  double dmax = 0.0;
+  for (int i = 0; i < m; ++i) dmax = fmax(dmax, L[tri(i, i)]);
+  const double tol = dmax * (double)m * 4e-16;
+
+  // Cholesky P = L L^T (FP64), right-looking; a pivot <= tol drops its column
+  for (int j = 0; j < m; ++j) {
+    const double d = L[tri(j, j)];
+    const double piv = d > tol ? sqrt(d) : 0.0;
+    __syncthreads();
+    if (tid == 0) L[tri(j, j)] = piv;
+    const double inv = piv > 0.0 ? 1.0 / piv : 0.0;
+    for (int i = j + 1 + tid; i < m; i += nt) L[tri(i, j)] *= inv;
+    __syncthreads();
+    const int t = m - j - 1;
+    for (int e = tid; e < t * t; e += nt) {
+      const int i = j + 1 + e / t, l = j + 1 + e % t;
+      if (l <= i) L[tri(i, l)] -= L[tri(i, j)] * L[tri(l, j)];
+    }
+    __syncthreads();
+  }
+
+  // H = L^T Sigma L in FP32 (it only seeds the FP32 iteration; the eigenvalues
+  // come from the FP64 factor below): an FP32 copy of L in V's space first
+  for (int e = tid; e < m * m; e += nt) {
+    const int i = e / m, j = e % m;
+    V[i * ld + j] = j <= i ? (float)L[tri(i, j)] : 0.f;
+  }
+  __syncthreads();
+  for (int e = tid; e < m * m; e += nt) {
+    const int a = e / m, b = e % m;
+    if (a > b) continue;
+    float s = 0.f;
+    for (int i = b; i < m; ++i) s = fmaf(V[i * ld + a] * sig[i], V[i * ld + b], s);
+    H[a * ld + b] = s;
+    H[b * ld + a] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < m * m; e += nt) V[(e / m) * ld + e % m] = (e / m) == (e % m) ? 1.f : 0.f;
+  __syncthreads();
+
+  // cyclic Jacobi in FP32, round-robin pairs: round r pairs (r, m-1) and
+  // ((r + q) mod (m-1), (r - q) mod (m-1)) for q = 1 .. m/2 - 1.  The m/2
+  // rotations of a round are disjoint, so H <- J^T H J splits into 2 x 2
+  // blocks (pair a rows, pair b columns), each read and written by one thread
+  // (the block of pairs (b, a) is the transpose); V <- V J likewise by rows.
+  float fro = 0.f;
+  for (int e = tid; e < m * m; e += nt) fro += H[(e / m) * ld + e % m] * H[(e / m) * ld + e % m];
+  fro = block_sum(fro, red);
+  // this thread's 2 x 2 blocks (a <= b, row-major over the upper triangle of
+  // pair blocks), decoded once: (a << 16) | b, or -1
+  const int nblk = half * (half + 1) / 2;
+  constexpr int kBlk = ((MAXM / 2) * (MAXM / 2 + 1) / 2 + kEigThreads - 1) / kEigThreads;
+  int blk[kBlk];
+#pragma unroll
+  for (int u = 0; u < kBlk; ++u) {
+    const int e = tid + u * nt;
+    blk[u] = -1;
+    if (e < nblk) {
+      int a = 0, rem = e;
+      while (rem >= half - a) {
+        rem -= half - a;
+        ++a;
+      }
+      blk[u] = (a << 16) | (a + rem);
+    }
+  }
+  // V <- V J: a fixed pair per thread, rows strided
+  const int vgroups = nt / max(half, 1), vq = tid % max(half, 1), vi0 = tid / max(half, 1);
+  for (int sweep = 0; sweep < kMaxSweeps && m > 1; ++sweep) {
+    float off = 0.f;
+    for (int e = tid; e < m * m; e += nt) {
+      const int a = e / m, b = e % m;
+      if (a != b) off += H[a * ld + b] * H[a * ld + b];
+    }
+    off = block_sum(off, red);
+    if (off <= kOffTol * kOffTol * fro) break;
+    for (int r = 0; r < m - 1; ++r) {
+      for (int q = tid; q < half; q += nt) {
+        int p0, p1;
+        if (q == 0) {
+          p0 = r;
+          p1 = m - 1;
+        } else {
+          p0 = (r + q) % (m - 1);
+          p1 = (r - q + m - 1) % (m - 1);
+        }
+        const int p = min(p0, p1), qq = max(p0, p1);
+        const float hpq = H[p * ld + qq];
+        float c = 1.f, s = 0.f, t = 0.f;
+        if (fabsf(hpq) > 1e-30f) {
+          const float tau = (H[qq * ld + qq] - H[p * ld + p]) / (2.f * hpq);
+          t = fabsf(tau) > 1e18f ? 0.5f / tau : copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+          c = rsqrtf(fmaf(t, t, 1.f));
+          s = t * c;
+        }
+        pq[2 * q] = p;
+        pq[2 * q + 1] = qq;
+        cs[3 * q] = c;
+        cs[3 * q + 1] = s;
+        cs[3 * q + 2] = t;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < kBlk; ++u) {
+        if (blk[u] < 0) continue;
+        const int a = blk[u] >> 16, b = blk[u] & 0xffff;
+        const int pa = pq[2 * a], qa = pq[2 * a + 1], pb = pq[2 * b], qb = pq[2 * b + 1];
+        const float ca = cs[3 * a], sa = cs[3 * a + 1];
+        const float h00 = H[pa * ld + pb], h01 = H[pa * ld + qb], h10 = H[qa * ld + pb], h11 = H[qa * ld + qb];
+        if (a == b) {
+          const float ta = cs[3 * a + 2];
+          H[pa * ld + pa] = h00 - ta * h01;
+          H[qa * ld + qa] = h11 + ta * h01;
+          H[pa * ld + qa] = 0.f;
+          H[qa * ld + pa] = 0.f;
+        } else {
+          const float cb = cs[3 * b], sb = cs[3 * b + 1];
+          const float x00 = ca * h00 - sa * h10, x01 = ca * h01 - sa * h11;
+          const float x10 = sa * h00 + ca * h10, x11 = sa * h01 + ca * h11;
+          const float y00 = cb * x00 - sb * x01, y01 = sb * x00 + cb * x01;
+          const float y10 = cb * x10 - sb * x11, y11 = sb * x10 + cb * x11;
+          H[pa * ld + pb] = y00;
+          H[pa * ld + qb] = y01;
+          H[qa * ld + pb] = y10;
+          H[qa * ld + qb] = y11;
+          H[pb * ld + pa] = y00;
+          H[qb * ld + pa] = y01;
+          H[pb * ld + qa] = y10;
+          H[qb * ld + qa] = y11;
+        }
+      }
+      if (vi0 < vgroups) {
+        const int p = pq[2 * vq], qq = pq[2 * vq + 1];
+        const float c = cs[3 * vq], s = cs[3 * vq + 1];
+        for (int i = vi0; i < m; i += vgroups) {
+          const float vp = V[i * ld + p], vv = V[i * ld + qq];
+          V[i * ld + p] = c * vp - s * vv;
+          V[i * ld + qq] = s * vp + c * vv;
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // the eigenvectors to FP64, one padded row per vector (V64[a][j] = V[j][a]),
+  // over the space of H and V: rows a < m/2 land in H's space; the columns
+  // a >= m/2 of V are read into registers before their rows overwrite V's
+  double* V64 = reinterpret_cast<double*>(H);
+  for (int e = tid; e < half * m; e += nt) {
+    const int a = e / m, j = e % m;
+    V64[a * ld + j] = (double)V[j * ld + a];
+  }
+  constexpr int kHold = MAXM * MAXM / 2 / kEigThreads;
+  float hold[kHold];
+#pragma unroll
+  for (int u = 0; u < kHold; ++u) {
+    const int e = tid + u * nt;
+    hold[u] = e < half * m ? V[(e % m) * ld + half + e / m] : 0.f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < kHold; ++u) {
+    const int e = tid + u * nt;
+    if (e < half * m) V64[(half + e / m) * ld + e % m] = (double)hold[u];
+  }
+  __syncthreads();
+
+  // FP64 Rayleigh quotients of the FP32 eigenvectors on the FP64 factor:
+  // mu_a = (L v)^T Sigma (L v) / v^T v, second order in the eigenvector error;
+  // g = nt / m threads per vector (adjacent lanes), rows i dealt round-robin
+  {
+    const int g = min(8, max(1, nt / m));
+    const int a = tid / g, sub = tid % g;
+    double num = 0.0, den = 0.0;
+    if (a < m) {
+      const double* v = V64 + (size_t)a * ld;
+      for (int i = sub; i < m; i += g) {
+        double w = 0.0;
+        for (int j = 0; j <= i; ++j) w = fma(L[tri(i, j)], v[j], w);
+        num = fma((double)sig[i] * w, w, num);
+        den = fma(v[i], v[i], den);
+      }
+    }
+    for (int o = 1; o < g; o <<= 1) {
+      num += __shfl_xor_sync(0xffffffffu, num, o);
+      den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    if (a < m && sub == 0) mu[a] = den > 0.0 ? num / den : 0.0;
+  }
+  __syncthreads();
+
+  // the spectrum of exp(lambda W_hat): drop the rank deficiency, sort, merge the ones
+  if (tid == 0) {
+    int cnt = m;
+    if (jb.n < m) {  // drop the m - n eigenvalues of smallest modulus
+      sort_small(mu, m, [](double x) { return fabs(x); });
+      const int drop = m - (int)jb.n;
+      for (int i = 0; i < (int)jb.n; ++i) mu[i] = mu[i + drop];
+      cnt = (int)jb.n;
+    }
+    for (int i = 0; i < cnt; ++i) mu[i] = exp(jb.lambda * mu[i]);
+    sort_small(mu, cnt, [](double x) { return x; });
+    int below = 0, above = 0;
+    for (int i = 0; i < cnt; ++i) {
+      below += mu[i] < 1.0;
+      above += mu[i] > 1.0;
+    }
+    pq[0] = cnt;
+    pq[1] = below;
+    pq[2] = above;
+  }
+  __syncthreads();
+  const int cnt = pq[0], below = pq[1], above = pq[2];
+  const int64_t ones = jb.n > m ? jb.n - m : 0;
+  float* o = out + (size_t)blockIdx.x * k;
+  for (int j = tid; j < k; j += nt) {
+    double v;
+    if (!largest) {  // ascending: kappa < 1, then the ones (with any kappa == 1), then kappa > 1
+      if (j < below) v = mu[j];
+      else if ((int64_t)j < (int64_t)(cnt - above) + ones) v = 1.0;
+      else v = mu[(int64_t)j - ones];
+    } else {  // descending
+      if (j < above) v = mu[cnt - 1 - j];
+      else if ((int64_t)j < (int64_t)(cnt - below) + ones) v = 1.0;
+      else v = mu[cnt - 1 - ((int64_t)j - ones)];
+    }
+    o[j] = (float)v;
+  }
+}
+
+rfd_status launch_eigen(const EigJob* d_jobs, int count, int max_m, int k, int largest, float* d_out,
+                        cudaStream_t st) {
+  const size_t smem = eig_smem_bytes(max_m);
+  auto kern = max_m <= 64 ? kernel_eigen_kernel<64> : kernel_eigen_kernel<kEigMaxM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return fail(RFD_ECUDA, std::string("eigen attribute: ") + cudaGetErrorString(e));
+  kern<<<count, kEigThreads, smem, st>>>(d_jobs, k, largest, d_out);
+  count_launch();
+  e = cudaGetLastError();
+  return e == cudaSuccess ? RFD_OK : fail(RFD_ECUDA, std::string("eigen launch: ") + cudaGetErrorString(e));
+}
+
+rfd_status check_eigen_plan(const rfd_plan_s* pl, int k, int idx) {
+  const std::string who = idx < 0 ? std::string() : "cloud " + std::to_string(idx) + ": ";
+  if (pl->m > kEigMaxM) return fail(RFD_EINVAL, who + "m must be <= 128 for the kernel eigenvalues");
+  if ((int64_t)k > pl->n) return fail(RFD_EINVAL, who + "k must be <= N");
+  return RFD_OK;
+}
+
+EigJob job_of(const rfd_plan_s* pl) { return EigJob{pl->d_M, pl->d_oa, pl->p.lambda, pl->n, pl->m, 0}; }
+
+// runs the kernel on host-built jobs (a temporary device table on the stream)
+rfd_status run_jobs(const std::vector<EigJob>& jobs, int max_m, int k, int largest, float* d_out, cudaStream_t st) {
+  EigJob* d_jobs = nullptr;
+  const size_t bytes = jobs.size() * sizeof(EigJob);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_jobs), bytes, st);
+  if (e != cudaSuccess) return fail(RFD_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+  e = cudaMemcpyAsync(d_jobs, jobs.data(), bytes, cudaMemcpyHostToDevice, st);
+  rfd_status s = e == cudaSuccess ? launch_eigen(d_jobs, (int)jobs.size(), max_m, k, largest, d_out, st)
+                                  : fail(RFD_ECUDA, std::string("job upload: ") + cudaGetErrorString(e));
+  cudaFreeAsync(d_jobs, st);  // a pageable upload is staged before cudaMemcpyAsync returns
+  return s;
+}
+
+}  // namespace
+
+rfd_status batch_eigenvalues(rfd_plan_s* const* plans, int count, int k, int largest, float* d_out, cudaStream_t st,
+                             Timing* tm) {
+  std::vector<EigJob> jobs((size_t)count);
+  int max_m = 2;
+  for (int i = 0; i < count; ++i) {
+    jobs[i] = job_of(plans[i]);
+    max_m = std::max(max_m, plans[i]->m);
+  }
+  StepScope sc(tm, st, RFD_STEP_EIGEN);
+  return run_jobs(jobs, max_m, k, largest, d_out, st);
+}
+
+rfd_status check_eigen_args(rfd_plan_s* const* plans, int count, int k) {
+  if (k < 1) return fail(RFD_EINVAL, "k must be >= 1");
+  for (int i = 0; i < count; ++i) {
+    rfd_status s = check_eigen_plan(plans[i], k, count > 1 ? i : -1);
+    if (s != RFD_OK) return s;
+  }
+  return RFD_OK;
+}
+
+}  // namespace rfd
+
+using namespace rfd;
+
+extern "C" rfd_status rfd_eigenvalues(rfd_plan_t pl, int32_t k, int32_t largest, float* d_out) {
+  if (!pl || !d_out) return fail(RFD_EINVAL, "null plan or output");
+  if (largest != 0 && largest != 1) return fail(RFD_EINVAL, "largest must be 0 or 1");
+  if (!pl->have_G) return fail(RFD_EINVAL, "rfd_features (or rfd_gfi) must run before rfd_eigenvalues");
+  rfd_plan_s* one = pl;
+  rfd_status s = check_eigen_args(&one, 1, k);
+  if (s != RFD_OK) return s;
+  return batch_eigenvalues(&one, 1, k, largest, d_out, pl->stream, nullptr);
+}

@@ -65,6 +65,8 @@ struct TileSet {
 };
 
 enum Mode : int { kModeFeatures = 0, kModeIntegrate = 1, kModeGfi = 2 };
+// batch_run only: steps a2 and a3 of kModeFeatures (M, no step a4)
+constexpr int kModeGram = 3;
 
 // Host copies of one BF16 plan's batched-path descriptors (absolute device
 // pointers; tensor-map indices relative to the plan's own kMapsPerCloud maps,
@@ -169,6 +171,12 @@ size_t batch_device_bytes(BatchImpl* b);
 // device-side timeouts are reported by batch_check_error.
 rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* timing);
 cudaStream_t batch_stream(BatchImpl* b);
+// Kernel eigenvalues (rfd_eigen.cu): argument checks, and the k smallest /
+// largest eigenvalues of every plan's exp(lambda W_hat) from its resident M
+// into d_out (count x k), asynchronous on st.
+rfd_status check_eigen_args(rfd_plan_s* const* plans, int count, int k);
+rfd_status batch_eigenvalues(rfd_plan_s* const* plans, int count, int k, int largest, float* d_out, cudaStream_t st,
+                             Timing* tm);
 // Synchronises the batch's stream and reads (and clears) its device error word
 // and per-cloud finiteness flags: RFD_ETIMEDOUT if a bounded wait ran out,
 // RFD_ENUMERIC if some cloud's G is not finite (bad[k] = 1 for those clouds when

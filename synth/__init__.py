@@ -22,7 +22,7 @@ import numpy as np
 
 __all__ = [
     "rng_for", "unit_sphere", "torus", "ellipsoid_union", "gaussian_field",
-    "CloudSpec", "config_single", "batched_specs", "serving_trace", "make_cloud", "gw_problem",
+    "CloudSpec", "config_single", "batched_specs", "serving_trace", "make_cloud", "gw_problem", "eigen_specs",
 ]
 
 # stream ids keep the points, the field and the per-cloud parameters independent
@@ -236,3 +236,15 @@ def gw_problem(n1: int, n2: int, seed: int = 0):
     la, lb = rng.integers(0, 2, n1), rng.integers(0, 2, n2)
     M = (la[:, None] != lb[None, :]).astype(np.float64)
     return X, Y, T, p, q, Gt, M
+
+
+def eigen_specs(count: int = 1024, seed: int = 0, n: int = 2048, m: int = 64, eps: float = 0.1,
+                lam: float = -0.1) -> list[CloudSpec]:
+    """Shape-classification clouds (Sec. 3.3: 2048 points sampled per shape,
+    eps = 0.1, lambda = -0.1): sphere, torus or ellipsoid union in turn, random
+    scale U[0.5, 1] (spheres, tori), one feature seed per cloud; lambda is
+    the raw value (callers apply their units)."""
+    rng = rng_for(seed, _STREAM_PARAMS, 1)
+    kinds = ("sphere", "torus", "ellipsoids")
+    return [CloudSpec(kinds[i % 3], n, m, 1, eps, lam, seed * 100003 + i, scale=float(rng.uniform(0.5, 1.0)), sub=i)
+            for i in range(count)]
