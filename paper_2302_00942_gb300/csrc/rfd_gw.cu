@@ -91,6 +91,338 @@ __global__ void line_search_sums_kernel(const float* __restrict__ a1, const floa
   }
 }
 
+// ---- low-rank form (both clouds with m <= 32) --------------------------------
+// A cloud's structure matrix is C = I + Psi K Psi^T with Psi its FP32 features
+// (N x m) and K = diag(s sgn r) G diag(s) (m x m).  With U = Psi K:
+//   C^{(.)2} p:  v_i = p_i (1 + 2 U_i . Psi_i) + U_i^T S U_i,  S = Psi^T D_p Psi
+//   C T D^T   :  T + U_C P' + Q U_D^T,  P = Psi_C^T T, Q = T Psi_D,
+//                R = P Psi_D, P' = P + R U_D^T
+// (the same sums as Eq. sq and Algorithm tensor_prod, re-associated through
+// the factors), so the n1 x n2 matrices are read once for P and Q and once
+// for the output, and every other step is O(N m^2).
+
+constexpr int kTI = 32;    // rows of a projection tile
+constexpr int kTA = 64;    // rows of an assembly tile
+constexpr int kTJ = 256;   // columns of a tile (one per thread)
+constexpr int kTLd = kTJ + 8;  // smem row stride (8 banks between rows)
+constexpr int kRowGroups = 16;  // row groups of the projection grid
+
+// Pt[g][j][f] = sum_{i in group g} X[i][j] psc[i][f],  Qp[s][i][f] = sum_{j in strip s} X[i][j] psd[j][f]
+// Tile kTI x kTJ in shared memory.  P: a column per thread over the tile's
+// rows (accumulating over the group).  Q: a row per 8 threads, columns
+// dealt 8 apart, summed by shuffles.
+template <int MF>
+__global__ void __launch_bounds__(256) gw_project_kernel(const float* __restrict__ X, int64_t n1, int64_t n2,
+                                                         const float* __restrict__ psc, const float* __restrict__ psd,
+                                                         float* __restrict__ Pt_part, float* __restrict__ Q_part,
+                                                         int rows_per_group) {
+  constexpr int PLd = MF + 4;         // padded rows of psd: 8 consecutive rows hit distinct banks
+  extern __shared__ __align__(16) float sm[];
+  float* Ts = sm;                      // kTI x kTLd
+  float* pc = Ts + kTI * kTLd;         // kTI x MF
+  float* pd = pc + kTI * MF;           // kTJ x PLd
+  const int t = threadIdx.x;
+  const int64_t j0 = (int64_t)blockIdx.x * kTJ;
+  const int64_t ig0 = (int64_t)blockIdx.y * rows_per_group;
+  const int64_t ig1 = min(n1, ig0 + rows_per_group);
+  for (int e = t; e < kTJ * MF; e += 256) {
+    const int64_t j = j0 + e / MF;
+    pd[(e / MF) * PLd + e % MF] = j < n2 ? psd[j * MF + e % MF] : 0.f;
+  }
+  float accP[MF];
+#pragma unroll
+  for (int f = 0; f < MF; ++f) accP[f] = 0.f;
+  const int qr = t >> 3, qc = t & 7;  // Q: row qr of the tile, columns qc + 8k
+  // whole 16-byte column groups: rows start 16-byte aligned and a group never straddles n2
+  const bool vec = (n2 & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  for (int64_t i0 = ig0; i0 < ig1; i0 += kTI) {
+    __syncthreads();
+    if (vec) {  // 8 independent 16-byte loads per thread: rows t / 64 + 4u, columns 4 (t % 64)
+      const int c4 = (t & 63) * 4, r0 = t >> 6;
+      float4 v[kTI / 4];
+#pragma unroll
+      for (int u = 0; u < kTI / 4; ++u) {
+        const int64_t i = i0 + r0 + 4 * u, j = j0 + c4;
+        v[u] = (i < ig1 && j < n2) ? *reinterpret_cast<const float4*>(X + i * n2 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kTI / 4; ++u) *reinterpret_cast<float4*>(Ts + (r0 + 4 * u) * kTLd + c4) = v[u];
+    } else {
+#pragma unroll 8
+      for (int r = 0; r < kTI; ++r) {
+        const int64_t i = i0 + r, j = j0 + t;
+        Ts[r * kTLd + t] = (i < ig1 && j < n2) ? X[i * n2 + j] : 0.f;
+      }
+    }
+    for (int e = t; e < kTI * MF; e += 256) {
+      const int64_t i = i0 + e / MF;
+      pc[e] = i < ig1 ? psc[i * MF + e % MF] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int r = 0; r < kTI; ++r) {  // P: column t over the tile's rows
+      const float x = Ts[r * kTLd + t];
+      const float4* pr = reinterpret_cast<const float4*>(pc + r * MF);
+#pragma unroll
+      for (int f4 = 0; f4 < MF / 4; ++f4) {
+        const float4 w = pr[f4];
+        accP[4 * f4] = fmaf(x, w.x, accP[4 * f4]);
+        accP[4 * f4 + 1] = fmaf(x, w.y, accP[4 * f4 + 1]);
+        accP[4 * f4 + 2] = fmaf(x, w.z, accP[4 * f4 + 2]);
+        accP[4 * f4 + 3] = fmaf(x, w.w, accP[4 * f4 + 3]);
+      }
+    }
+    float accQ[MF];
+#pragma unroll
+    for (int f = 0; f < MF; ++f) accQ[f] = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < kTJ / 8; ++k) {  // Q: row qr over columns qc + 8k
+      const int c = qc + 8 * k;
+      const float x = Ts[qr * kTLd + c];
+      const float4* pr = reinterpret_cast<const float4*>(pd + c * PLd);
+#pragma unroll
+      for (int f4 = 0; f4 < MF / 4; ++f4) {
+        const float4 w = pr[f4];
+        accQ[4 * f4] = fmaf(x, w.x, accQ[4 * f4]);
+        accQ[4 * f4 + 1] = fmaf(x, w.y, accQ[4 * f4 + 1]);
+        accQ[4 * f4 + 2] = fmaf(x, w.z, accQ[4 * f4 + 2]);
+        accQ[4 * f4 + 3] = fmaf(x, w.w, accQ[4 * f4 + 3]);
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < MF; ++f) {
+      accQ[f] += __shfl_xor_sync(0xffffffffu, accQ[f], 1);
+      accQ[f] += __shfl_xor_sync(0xffffffffu, accQ[f], 2);
+      accQ[f] += __shfl_xor_sync(0xffffffffu, accQ[f], 4);
+    }
+    const int64_t i = i0 + qr;
+    if (i < ig1) {
+      float* q = Q_part + ((int64_t)blockIdx.x * n1 + i) * MF;
+#pragma unroll
+      for (int f = 0; f < MF / 4; ++f)
+        if (qc == (f & 7)) reinterpret_cast<float4*>(q)[f] = make_float4(accQ[4 * f], accQ[4 * f + 1], accQ[4 * f + 2], accQ[4 * f + 3]);
+    }
+  }
+  const int64_t j = j0 + t;
+  if (j < n2) {
+    float4* o = reinterpret_cast<float4*>(Pt_part + ((int64_t)blockIdx.y * n2 + j) * MF);
+#pragma unroll
+    for (int f4 = 0; f4 < MF / 4; ++f4)
+      o[f4] = make_float4(accP[4 * f4], accP[4 * f4 + 1], accP[4 * f4 + 2], accP[4 * f4 + 3]);
+  }
+}
+
+// out[e] = sum_s part[s * stride + e], e < count (fixed order)
+__global__ void sum_parts_kernel(const float* __restrict__ part, int parts, int64_t stride, int64_t count,
+                                 float* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  float s = 0.f;
+  for (int k = 0; k < parts; ++k) s += part[k * stride + e];
+  out[e] = s;
+}
+
+// point-major FP32 features: out[i][f] = psi[f][i] (f < m), 0 for m <= f < MF
+__global__ void features_point_major_kernel(const float* __restrict__ psi, int64_t ldpsi, int m, int64_t n, int mf,
+                                            float* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * mf) return;
+  const int64_t i = e / mf;
+  const int f = (int)(e % mf);
+  out[e] = f < m ? psi[(int64_t)f * ldpsi + i] : 0.f;
+}
+
+// K[f][g] = oa[f] G[f][g] ob[g] (zero padded to mf x mf)
+__global__ void lowrank_k_kernel(const double* __restrict__ G, const double* __restrict__ oa,
+                                 const double* __restrict__ ob, int m, int mf, float* __restrict__ K) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= mf * mf) return;
+  const int f = e / mf, g = e % mf;
+  K[e] = (f < m && g < m) ? (float)(oa[f] * G[(size_t)f * m + g] * ob[g]) : 0.f;
+}
+
+// out[i][:] = A[i][:] B (+ add[i][:]); B mf x mf (transposed when tB)
+__global__ void rowmat_kernel(const float* __restrict__ A, const float* __restrict__ B, int tB,
+                              const float* __restrict__ add, int64_t n, int mf, float* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * mf) return;
+  const int64_t i = e / mf;
+  const int f = (int)(e % mf);
+  float s = add ? add[e] : 0.f;
+  for (int g = 0; g < mf; ++g) s = fmaf(A[i * mf + g], tB ? B[f * mf + g] : B[g * mf + f], s);
+  out[e] = s;
+}
+
+// part[y][f][g] = sum_{i in chunk y} w_i A[i][f] B[i][g] (w = 1 when null); block (f, y);
+// FP32 over a thread's rows, FP64 across threads
+__global__ void weighted_gram_kernel(const float* __restrict__ A, const float* __restrict__ B,
+                                     const float* __restrict__ w, int64_t n, int mf, float* __restrict__ part) {
+  const int f = blockIdx.x;
+  const int64_t per = (n + gridDim.y - 1) / gridDim.y;
+  const int64_t r0 = (int64_t)blockIdx.y * per, r1 = min(n, r0 + per);
+  __shared__ double red[8][33];
+  float acc[32];
+  for (int g = 0; g < 32; ++g) acc[g] = 0.f;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const float a = A[i * mf + f] * (w ? w[i] : 1.f);
+    for (int g = 0; g < mf; ++g) acc[g] = fmaf(a, B[i * mf + g], acc[g]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int g = 0; g < mf; ++g) {
+    double v = acc[g];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][g] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < mf) {
+    double v = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v += red[k][threadIdx.x];
+    part[((size_t)blockIdx.y * mf + f) * mf + threadIdx.x] = (float)v;
+  }
+}
+
+// v_i = p_i (1 + 2 U_i . Psi_i) + U_i^T S U_i
+__global__ void hadamard_lowrank_kernel(const float* __restrict__ U, const float* __restrict__ Psi,
+                                        const float* __restrict__ S, const float* __restrict__ p, int64_t n, int mf,
+                                        float* __restrict__ v) {
+  __shared__ float Ss[32 * 32];
+  for (int e = threadIdx.x; e < mf * mf; e += blockDim.x) Ss[e] = S[e];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* u = U + i * mf;
+  float d = 0.f, q = 0.f;
+  for (int f = 0; f < mf; ++f) {
+    d = fmaf(u[f], Psi[i * mf + f], d);
+    float su = 0.f;
+    for (int g = 0; g < mf; ++g) su = fmaf(Ss[f * mf + g], u[g], su);
+    q = fmaf(u[f], su, q);
+  }
+  v[i] = p[i] * (1.f + 2.f * d) + q;
+}
+
+// L[i][j] = v1_i + v2_j - 2 (T_ij + Uc_i . Pp_j + Q_i . Ud_j); a column per thread
+template <int MF>
+__global__ void __launch_bounds__(256) gw_assemble_kernel(const float* __restrict__ T, const float* __restrict__ v1,
+                                                          const float* __restrict__ v2, const float* __restrict__ Uc,
+                                                          const float* __restrict__ Q, const float* __restrict__ Pp,
+                                                          const float* __restrict__ Ud, int64_t n1, int64_t n2,
+                                                          float* __restrict__ L) {
+  __shared__ __align__(16) float rowf[kTA][2 * MF];  // (Uc_i, Q_i)
+  const int t = threadIdx.x;
+  const int64_t j = (int64_t)blockIdx.x * kTJ + t, i0 = (int64_t)blockIdx.y * kTA;
+  for (int e = t; e < kTA * 2 * MF; e += 256) {
+    const int r = e / (2 * MF), k = e % (2 * MF);
+    const int64_t i = i0 + r;
+    rowf[r][k] = i < n1 ? (k < MF ? Uc[i * MF + k] : Q[i * MF + k - MF]) : 0.f;
+  }
+  float colf[2 * MF];  // (Pp_j, Ud_j)
+#pragma unroll
+  for (int k = 0; k < MF; ++k) {
+    colf[k] = j < n2 ? Pp[j * MF + k] : 0.f;
+    colf[MF + k] = j < n2 ? Ud[j * MF + k] : 0.f;
+  }
+  const float vj = j < n2 ? v2[j] : 0.f;
+  __syncthreads();
+  if (j >= n2) return;
+  const int rows = (int)(n1 - i0 < kTA ? n1 - i0 : kTA);
+#pragma unroll 8
+  for (int r = 0; r < rows; ++r) {
+    const int64_t i = i0 + r;
+    const float4* rf = reinterpret_cast<const float4*>(rowf[r]);
+    float s = T[i * n2 + j];
+#pragma unroll
+    for (int k4 = 0; k4 < MF / 2; ++k4) {
+      const float4 a = rf[k4];
+      s = fmaf(a.x, colf[4 * k4], s);
+      s = fmaf(a.y, colf[4 * k4 + 1], s);
+      s = fmaf(a.z, colf[4 * k4 + 2], s);
+      s = fmaf(a.w, colf[4 * k4 + 3], s);
+    }
+    L[i * n2 + j] = v1[i] + vj - 2.f * s;
+  }
+}
+
+// sum += sum_i A_i . (B_i Km)   (FP64)
+__global__ void rowdot_kernel(const float* __restrict__ A, const float* __restrict__ B, const float* __restrict__ Km,
+                              int64_t n, int mf, double* __restrict__ sum) {
+  __shared__ float Ks[32 * 32];
+  __shared__ double red[8];
+  for (int e = threadIdx.x; e < mf * mf; e += blockDim.x) Ks[e] = Km[e];
+  __syncthreads();
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int f = 0; f < mf; ++f) {
+      float bk = 0.f;
+      for (int g = 0; g < mf; ++g) bk = fmaf(B[i * mf + g], Ks[g * mf + f], bk);
+      acc = fma((double)A[i * mf + f], (double)bk, acc);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+    atomicAdd(sum, v);
+  }
+}
+
+// sums[0..3] += <dG, dG>, <dG, G>, <M, dG>, <v1 1^T + 1 v2^T, dG>  (FP64); rows
+// strided over blocks, columns over threads
+__global__ void gw_dots_kernel(const float* __restrict__ G, const float* __restrict__ dG, const float* __restrict__ M,
+                               const float* __restrict__ v1, const float* __restrict__ v2, int64_t n1, int64_t n2,
+                               double* __restrict__ sums) {
+  double s[4] = {0, 0, 0, 0};
+  const bool vec = (n2 & 3) == 0 && ((reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(dG) |
+                                       reinterpret_cast<uintptr_t>(M) | reinterpret_cast<uintptr_t>(v2)) & 15) == 0;
+  for (int64_t i = blockIdx.x; i < n1; i += gridDim.x) {  // FP32 within a row, FP64 across rows
+    const float vi = v1[i];
+    float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
+    if (vec) {
+      const float4* d4 = reinterpret_cast<const float4*>(dG + i * n2);
+      const float4* g4 = reinterpret_cast<const float4*>(G + i * n2);
+      const float4* m4 = reinterpret_cast<const float4*>(M + i * n2);
+      const float4* w4 = reinterpret_cast<const float4*>(v2);
+#pragma unroll 2
+      for (int64_t j = threadIdx.x; j < n2 / 4; j += blockDim.x) {
+        const float4 d = d4[j], g = g4[j], m = m4[j], w = w4[j];
+        r0 = fmaf(d.x, d.x, fmaf(d.y, d.y, fmaf(d.z, d.z, fmaf(d.w, d.w, r0))));
+        r1 = fmaf(d.x, g.x, fmaf(d.y, g.y, fmaf(d.z, g.z, fmaf(d.w, g.w, r1))));
+        r2 = fmaf(d.x, m.x, fmaf(d.y, m.y, fmaf(d.z, m.z, fmaf(d.w, m.w, r2))));
+        r3 = fmaf(d.x, vi + w.x, fmaf(d.y, vi + w.y, fmaf(d.z, vi + w.z, fmaf(d.w, vi + w.w, r3))));
+      }
+    } else {
+#pragma unroll 4
+      for (int64_t j = threadIdx.x; j < n2; j += blockDim.x) {
+        const int64_t e = i * n2 + j;
+        const float d = dG[e];
+        r0 = fmaf(d, d, r0);
+        r1 = fmaf(d, G[e], r1);
+        r2 = fmaf(d, M[e], r2);
+        r3 = fmaf(d, vi + v2[j], r3);
+      }
+    }
+    s[0] += r0;
+    s[1] += r1;
+    s[2] += r2;
+    s[3] += r3;
+  }
+  __shared__ double red[4][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < 4; ++k) {
+    double v = s[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[k][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double v = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+    atomicAdd(&sums[threadIdx.x], v);
+  }
+}
+
 rfd_status cuda_err(const char* what, cudaError_t e) { return fail(RFD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e)); }
 
 // Y = C X on the plan (column chunks of at most max_channels)
@@ -148,6 +480,240 @@ rfd_status check_pair(rfd_plan_t pc, rfd_plan_t pd) {
   return RFD_OK;
 }
 
+// ---- low-rank form: host side ---------------------------------------------------
+constexpr int kLowRankMaxM = 32;
+
+unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+constexpr int kGramChunks = 32;
+
+// out (mf x mf) = sum_i w_i A_i A_i^T-like reduction in kGramChunks row chunks; part: kGramChunks mf^2 floats
+void wgram(const float* A, const float* B, const float* w, int64_t n, int mf, float* part, float* out,
+           cudaStream_t st) {
+  weighted_gram_kernel<<<dim3(mf, kGramChunks), 256, 0, st>>>(A, B, w, n, mf, part);
+  sum_parts_kernel<<<blocks_for((int64_t)mf * mf, 256), 256, 0, st>>>(part, kGramChunks, (int64_t)mf * mf,
+                                                                      (int64_t)mf * mf, out);
+  count_launch(2);
+}
+
+// bump allocator over one stream-ordered block (64-float granules)
+struct Carve {
+  float* base = nullptr;
+  size_t used = 0;
+  float* take(size_t floats) {
+    float* p = base + used;
+    used += (floats + 63) & ~size_t(63);
+    return p;
+  }
+};
+
+struct LowRank {  // one cloud: Psi and U point-major (N x MF), K (MF x MF)
+  float *psi, *U, *K;
+};
+
+rfd_status launched_or(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RFD_OK : cuda_err(what, e);
+}
+
+rfd_status lowrank_prepare(rfd_plan_t pl, int mf, const LowRank& lr, float* tmp_fm, cudaStream_t st) {
+  const float* fm = static_cast<const float*>(pl->d_psi);
+  if (pl->bf16) {  // FP32 features from the plan's copy of its points
+    const cudaError_t e = launch_features(pl->d_xyz, pl->n, pl->n_pad, pl->d_omega_hi, pl->d_omega_lo, pl->h, false,
+                                          tmp_fm, st);
+    count_launch();
+    if (e != cudaSuccess) return cuda_err("features", e);
+    fm = tmp_fm;
+  }
+  const int64_t n = pl->n;
+  features_point_major_kernel<<<blocks_for(n * mf, 256), 256, 0, st>>>(fm, pl->n_pad, pl->m, n, mf, lr.psi);
+  lowrank_k_kernel<<<blocks_for((int64_t)mf * mf, 256), 256, 0, st>>>(pl->d_G, pl->d_oa, pl->d_ob, pl->m, mf, lr.K);
+  rowmat_kernel<<<blocks_for(n * mf, 256), 256, 0, st>>>(lr.psi, lr.K, 0, nullptr, n, mf, lr.U);
+  count_launch(3);
+  return launched_or("low-rank factors");
+}
+
+// v = C^{(.)2} p in the low-rank form; S: mf x mf scratch
+rfd_status lowrank_hadamard(rfd_plan_t pl, int mf, const LowRank& lr, const float* p, float* S, float* v,
+                            cudaStream_t st) {
+  wgram(lr.psi, lr.psi, p, pl->n, mf, S + mf * mf, S, st);
+  hadamard_lowrank_kernel<<<blocks_for(pl->n, 256), 256, 0, st>>>(lr.U, lr.psi, S, p, pl->n, mf, v);
+  count_launch();
+  return launched_or("hadamard square");
+}
+
+struct Proj {  // projections of one n1 x n2 matrix X: Pt = (Psi_C^T X)^T, Q = X Psi_D, Pp = P'^T
+  float *Pt, *Q, *Pp;
+};
+
+size_t project_parts_floats(int64_t n1, int64_t n2, int mf) {
+  const int64_t groups = std::min<int64_t>(kRowGroups, (n1 + kTI - 1) / kTI);
+  const int64_t strips = (n2 + kTJ - 1) / kTJ;
+  return (size_t)(groups * n2 * mf + 64) + (size_t)(strips * n1 * mf + 64);
+}
+
+template <int MF>
+rfd_status project_mf(const float* X, int64_t n1, int64_t n2, const LowRank& c, const LowRank& d, const Proj& pr,
+                      float* parts, float* R, cudaStream_t st) {
+  const int64_t tiles = (n1 + kTI - 1) / kTI;
+  const int groups = (int)std::min<int64_t>(kRowGroups, tiles);
+  const int rows_per_group = (int)(((tiles + groups - 1) / groups) * kTI);
+  const int strips = (int)((n2 + kTJ - 1) / kTJ);
+  float* Pt_part = parts;
+  float* Q_part = parts + (((size_t)groups * n2 * MF + 63) & ~size_t(63));
+  const size_t smem = (size_t)(kTI * kTLd + kTI * MF + kTJ * (MF + 4)) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(gw_project_kernel<MF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_err("projection attribute", e);
+  gw_project_kernel<MF><<<dim3(strips, groups), 256, smem, st>>>(X, n1, n2, c.psi, d.psi, Pt_part, Q_part,
+                                                                  rows_per_group);
+  sum_parts_kernel<<<blocks_for(n2 * MF, 256), 256, 0, st>>>(Pt_part, groups, n2 * MF, n2 * MF, pr.Pt);
+  sum_parts_kernel<<<blocks_for(n1 * MF, 256), 256, 0, st>>>(Q_part, strips, n1 * MF, n1 * MF, pr.Q);
+  wgram(pr.Pt, d.psi, nullptr, n2, MF, R + MF * MF, R, st);                                  // R = P Psi_D
+  rowmat_kernel<<<blocks_for(n2 * MF, 256), 256, 0, st>>>(d.U, R, 1, pr.Pt, n2, MF, pr.Pp);  // P'^T
+  count_launch(4);
+  return launched_or("projection");
+}
+
+rfd_status project(int mf, const float* X, int64_t n1, int64_t n2, const LowRank& c, const LowRank& d,
+                   const Proj& pr, float* parts, float* R, cudaStream_t st) {
+  return mf == 16 ? project_mf<16>(X, n1, n2, c, d, pr, parts, R, st)
+                  : project_mf<32>(X, n1, n2, c, d, pr, parts, R, st);
+}
+
+// everything both entry points need: factors of both clouds, v1, v2
+struct LowRankPair {
+  int mf = 16;
+  LowRank c{}, d{};
+  float *v1 = nullptr, *v2 = nullptr, *S = nullptr, *R = nullptr, *parts = nullptr;
+};
+
+size_t lowrank_floats(rfd_plan_t pc, rfd_plan_t pd, int mf, int nproj) {
+  const int64_t n1 = pc->n, n2 = pd->n;
+  const size_t fm = std::max((size_t)pc->m * pc->n_pad, (size_t)pd->m * pd->n_pad);
+  size_t f = fm + 64;
+  f += 2 * ((size_t)n1 * mf + 64) + 2 * ((size_t)n2 * mf + 64) + 2 * ((size_t)mf * mf + 64) +
+       2 * ((size_t)(1 + kGramChunks) * mf * mf + 64);
+  f += (size_t)n1 + (size_t)n2 + 128;
+  f += project_parts_floats(n1, n2, mf) + 64;
+  f += (size_t)nproj * ((size_t)n2 * mf * 2 + (size_t)n1 * mf + 192);
+  return f + 256;
+}
+
+rfd_status lowrank_setup(rfd_plan_t pc, rfd_plan_t pd, const float* p, const float* q, Carve& cv, LowRankPair& lp,
+                         cudaStream_t st) {
+  const int mf = lp.mf;
+  const int64_t n1 = pc->n, n2 = pd->n;
+  float* tmp_fm = cv.take(std::max((size_t)pc->m * pc->n_pad, (size_t)pd->m * pd->n_pad));
+  lp.c = LowRank{cv.take(n1 * mf), cv.take(n1 * mf), cv.take((size_t)mf * mf)};
+  lp.d = LowRank{cv.take(n2 * mf), cv.take(n2 * mf), cv.take((size_t)mf * mf)};
+  lp.S = cv.take((size_t)(1 + kGramChunks) * mf * mf);
+  lp.R = cv.take((size_t)(1 + kGramChunks) * mf * mf);
+  lp.v1 = cv.take(n1);
+  lp.v2 = cv.take(n2);
+  lp.parts = cv.take(project_parts_floats(n1, n2, mf));
+  rfd_status s = lowrank_prepare(pc, mf, lp.c, tmp_fm, st);
+  if (s == RFD_OK) s = lowrank_prepare(pd, mf, lp.d, tmp_fm, st);
+  if (s == RFD_OK) s = lowrank_hadamard(pc, mf, lp.c, p, lp.S, lp.v1, st);
+  if (s == RFD_OK) s = lowrank_hadamard(pd, mf, lp.d, q, lp.S, lp.v2, st);
+  return s;
+}
+
+Proj take_proj(Carve& cv, int64_t n1, int64_t n2, int mf) {
+  return Proj{cv.take(n2 * mf), cv.take(n1 * mf), cv.take(n2 * mf)};
+}
+
+bool lowrank_ok(rfd_plan_t pc, rfd_plan_t pd) { return pc->m <= kLowRankMaxM && pd->m <= kLowRankMaxM; }
+int lowrank_mf(rfd_plan_t pc, rfd_plan_t pd) { return std::max(pc->m, pd->m) <= 16 ? 16 : 32; }
+
+rfd_status tensor_product_lowrank(rfd_plan_t pc, rfd_plan_t pd, const float* T, const float* p, const float* q,
+                                  float* L) {
+  cudaStream_t st = pc->stream;
+  LowRankPair lp;
+  lp.mf = lowrank_mf(pc, pd);
+  const int64_t n1 = pc->n, n2 = pd->n;
+  Carve cv;
+  const size_t bytes = lowrank_floats(pc, pd, lp.mf, 1) * sizeof(float);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&cv.base), bytes, st);
+  if (e != cudaSuccess) return fail(RFD_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+  rfd_status s = lowrank_setup(pc, pd, p, q, cv, lp, st);
+  const Proj pr = take_proj(cv, n1, n2, lp.mf);
+  if (s == RFD_OK) s = project(lp.mf, T, n1, n2, lp.c, lp.d, pr, lp.parts, lp.R, st);
+  if (s == RFD_OK) {
+    const dim3 grid((unsigned)((n2 + kTJ - 1) / kTJ), (unsigned)((n1 + kTA - 1) / kTA));
+    if (lp.mf == 16)
+      gw_assemble_kernel<16><<<grid, 256, 0, st>>>(T, lp.v1, lp.v2, lp.c.U, pr.Q, pr.Pp, lp.d.U, n1, n2, L);
+    else
+      gw_assemble_kernel<32><<<grid, 256, 0, st>>>(T, lp.v1, lp.v2, lp.c.U, pr.Q, pr.Pp, lp.d.U, n1, n2, L);
+    count_launch();
+    s = launched_or("tensor product");
+  }
+  cudaFreeAsync(cv.base, st);
+  return s;
+}
+
+rfd_status line_search_lowrank(rfd_plan_t pc, rfd_plan_t pd, const float* G, const float* dG, const float* M,
+                               const float* p, const float* q, double h[5]) {
+  cudaStream_t st = pc->stream;
+  LowRankPair lp;
+  lp.mf = lowrank_mf(pc, pd);
+  const int64_t n1 = pc->n, n2 = pd->n;
+  Carve cv;
+  const size_t bytes = lowrank_floats(pc, pd, lp.mf, 2) * sizeof(float) + 32 * sizeof(double);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&cv.base), bytes, st);
+  if (e != cudaSuccess) return fail(RFD_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+  rfd_status s = lowrank_setup(pc, pd, p, q, cv, lp, st);
+  const Proj pdG = take_proj(cv, n1, n2, lp.mf), pG = take_proj(cv, n1, n2, lp.mf);
+  double* sums = reinterpret_cast<double*>(cv.take(2 * 16));
+  if (s == RFD_OK) s = project(lp.mf, dG, n1, n2, lp.c, lp.d, pdG, lp.parts, lp.R, st);
+  if (s == RFD_OK) s = project(lp.mf, G, n1, n2, lp.c, lp.d, pG, lp.parts, lp.R, st);
+  double hs[10] = {};
+  if (s == RFD_OK) {
+    e = cudaMemsetAsync(sums, 0, 10 * sizeof(double), st);
+    if (e == cudaSuccess) {
+      const int mf = lp.mf;
+      gw_dots_kernel<<<(unsigned)std::min<int64_t>(n1, 152 * 8), 256, 0, st>>>(G, dG, M, lp.v1, lp.v2, n1, n2, sums);
+      // <C X D^T, Y> = <X, Y> + sum_j Pp_X[j] . (Pt_Y[j] K_C) + sum_i Q_X[i] . (Q_Y[i] K_D)
+      const unsigned b2 = blocks_for(n2, 256) > 304 ? 304 : blocks_for(n2, 256);
+      const unsigned b1 = blocks_for(n1, 256) > 304 ? 304 : blocks_for(n1, 256);
+      rowdot_kernel<<<b2, 256, 0, st>>>(pdG.Pp, pdG.Pt, lp.c.K, n2, mf, sums + 4);
+      rowdot_kernel<<<b1, 256, 0, st>>>(pdG.Q, pdG.Q, lp.d.K, n1, mf, sums + 5);
+      rowdot_kernel<<<b2, 256, 0, st>>>(pdG.Pp, pG.Pt, lp.c.K, n2, mf, sums + 6);
+      rowdot_kernel<<<b1, 256, 0, st>>>(pdG.Q, pG.Q, lp.d.K, n1, mf, sums + 7);
+      rowdot_kernel<<<b2, 256, 0, st>>>(pG.Pp, pdG.Pt, lp.c.K, n2, mf, sums + 8);
+      rowdot_kernel<<<b1, 256, 0, st>>>(pG.Q, pdG.Q, lp.d.K, n1, mf, sums + 9);
+      count_launch(7);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_err("line search", e);
+  }
+  cudaFreeAsync(cv.base, st);
+  if (s != RFD_OK) return s;
+  h[0] = hs[0] + hs[4] + hs[5];  // <C dG D^T, dG>
+  h[1] = hs[1] + hs[6] + hs[7];  // <C dG D^T, G>
+  h[2] = hs[1] + hs[8] + hs[9];  // <C G D^T, dG>
+  h[3] = hs[2];                  // <M, dG>
+  h[4] = hs[3];                  // <c_CD, dG>
+  return RFD_OK;
+}
+
+// a, b and tau of Algorithm line_search from the inner products h = <C dG D^T, dG>,
+// <C dG D^T, G>, <C G D^T, dG>, <M, dG>, <c_CD, dG>
+rfd_status finish_line_search(double alpha, const double h[5], double* out3) {
+  const double a = -2.0 * alpha * h[0];
+  const double b = (1.0 - alpha) * h[3] + alpha * h[4] - 2.0 * alpha * (h[1] + h[2]);
+  double tau;
+  if (a > 0)
+    tau = std::min(1.0, std::max(0.0, -b / (2.0 * a)));
+  else
+    tau = (a + b < 0) ? 1.0 : 0.0;
+  out3[0] = tau;
+  out3[1] = a;
+  out3[2] = b;
+  return RFD_OK;
+}
+
 }  // namespace
 
 }  // namespace rfd
@@ -167,6 +733,7 @@ extern "C" rfd_status rfd_gw_tensor_product(rfd_plan_t pc, rfd_plan_t pd, const 
   rfd_status s = check_pair(pc, pd);
   if (s != RFD_OK) return s;
   if (!d_T || !d_p || !d_q || !d_L) return fail(RFD_EINVAL, "null argument");
+  if (lowrank_ok(pc, pd)) return tensor_product_lowrank(pc, pd, d_T, d_p, d_q, d_L);
   const int64_t n1 = pc->n, n2 = pd->n, nn = std::max(n1, n2);
   cudaStream_t st = pc->stream;
   float* work = nullptr;
@@ -198,6 +765,12 @@ extern "C" rfd_status rfd_gw_line_search(rfd_plan_t pc, rfd_plan_t pd, double al
   if (s != RFD_OK) return s;
   if (!d_G || !d_dG || !d_M || !d_p || !d_q || !out3) return fail(RFD_EINVAL, "null argument");
   if (!std::isfinite(alpha)) return fail(RFD_EINVAL, "alpha must be finite");
+  double h[5] = {0, 0, 0, 0, 0};
+  if (lowrank_ok(pc, pd)) {
+    s = line_search_lowrank(pc, pd, d_G, d_dG, d_M, d_p, d_q, h);
+    if (s != RFD_OK) return s;
+    return finish_line_search(alpha, h, out3);
+  }
   const int64_t n1 = pc->n, n2 = pd->n, nn = std::max(n1, n2);
   cudaStream_t st = pc->stream;
   float* work = nullptr;
@@ -215,7 +788,6 @@ extern "C" rfd_status rfd_gw_line_search(rfd_plan_t pc, rfd_plan_t pd, double al
   if (s == RFD_OK) s = hadamard_square(pd, d_q, v2, sq);
   if (s == RFD_OK) s = sandwich(pc, pd, d_dG, a1, sw);  // a1 = C dG D
   if (s == RFD_OK) s = sandwich(pc, pd, d_G, b1, sw);   // b1 = C G D
-  double h[5] = {0, 0, 0, 0, 0};
   if (s == RFD_OK) {
     e = cudaMemsetAsync(sums, 0, 5 * sizeof(double), st);
     if (e == cudaSuccess) {
@@ -229,15 +801,5 @@ extern "C" rfd_status rfd_gw_line_search(rfd_plan_t pc, rfd_plan_t pd, double al
   }
   cudaFreeAsync(work, st);
   if (s != RFD_OK) return s;
-  const double a = -2.0 * alpha * h[0];
-  const double b = (1.0 - alpha) * h[3] + alpha * h[4] - 2.0 * alpha * (h[1] + h[2]);
-  double tau;
-  if (a > 0)
-    tau = std::min(1.0, std::max(0.0, -b / (2.0 * a)));
-  else
-    tau = (a + b < 0) ? 1.0 : 0.0;
-  out3[0] = tau;
-  out3[1] = a;
-  out3[2] = b;
-  return RFD_OK;
+  return finish_line_search(alpha, h, out3);
 }
