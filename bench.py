@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the serving trace (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-executors", type=int, default=6, help="batches in flight at once (one stream each)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the reductions' default launch parameters (a fixed launch sequence for profiling)")
     ap.add_argument("--gw-n", type=int, default=8192, help="points per cloud of the GW workload (0: skip)")
@@ -421,7 +422,7 @@ def bench_serving(args, dev):
         spec = synth.CloudSpec(kind, n_max, 64, 1, 0.05, 0.1, 4242 + k, scale=0.5 + 1.5 * k / 15, sub=k)
         templates.append(torch.from_numpy(synth.make_cloud(spec)[0]).to(dev))
     F_pool = torch.randn(n_max * 32 + 4096, device=dev)
-    srv = rfd.Server(int(args.serve_budget_gb * (1 << 30)), max_batch=256, executors=2)
+    srv = rfd.Server(int(args.serve_budget_gb * (1 << 30)), max_batch=256, executors=args.serve_executors)
     cloud_of = {}
 
     def submit(i, spec, j):
@@ -487,6 +488,7 @@ def bench_serving(args, dev):
     units = sum(r["n"] * r["c"] for r in ok)
     return {"workload": f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds:.0f} s: N log-uniform "
                         "[500, 5e5], m in {64..512}, c in 1..32, lambda U[0.01,0.2] x m/N, eps=0.05, 30% reuse",
+            "executors": args.serve_executors,
             "requests": len(trace), "completed_ok": len(ok), "failed": len(results) - len(ok), "rejected": rejected,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_batch": float(np.mean([r["batch_size"] for r in ok])) if ok else 0.0,
