@@ -93,8 +93,13 @@ typedef struct {
  *                    paper's brute-force baseline, on the cube of RFD_KERNEL_CUBE):
  *                    tau(w) = sum_d g(w_d) prod_{e != d} sin(2 pi eps w_e) / (pi w_e) with
  *                    g(w) = int_{-eps}^{eps} |z| cos(2 pi w z) dz = 2 eps^2 (sin x / x + (cos x - 1) / x^2),
- *                    x = 2 pi eps w (eps^2 at w = 0). */
-typedef enum { RFD_KERNEL_CUBE = 0, RFD_KERNEL_BALL = 1, RFD_KERNEL_CUBE_L1 = 2 } rfd_kernel;
+ *                    x = 2 pi eps w (eps^2 at w = 0);
+ *   RFD_KERNEL_L1_BALL: f = 1[||z||_1 <= eps] (the L1 ball of Sec. 2.4, an octahedron; its transform
+ *                    does not factor over coordinates): the sum over the 8 simplices
+ *                    conv(0, +-eps e_1, +-eps e_2, +-eps e_3) of eps^3 times the divided difference
+ *                    of exp at 0, -2 pi i eps s_d w_d (d = 1..3), evaluated as its power series
+ *                    (value 4 eps^3 / 3, the volume, at w = 0). */
+typedef enum { RFD_KERNEL_CUBE = 0, RFD_KERNEL_BALL = 1, RFD_KERNEL_CUBE_L1 = 2, RFD_KERNEL_L1_BALL = 3 } rfd_kernel;
 
 typedef struct rfd_plan_s* rfd_plan_t;
 

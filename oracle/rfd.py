@@ -122,12 +122,31 @@ def tau(omega: np.ndarray, eps: float, kernel: str = "cube") -> np.ndarray:
 
     kernel="cube": f = 1[||z||_inf <= eps], the product of per-coordinate sincs,
     prod_d sin(2 pi eps w_d)/(pi w_d).
+    kernel="l1_ball": f = 1[||z||_1 <= eps], the octahedron (see below).
     kernel="ball": f = 1[||z||_2 <= eps] in R^3 (the Bessel case of Sec. 2.4):
     the transform of a radial function is radial, and for the ball it is
     (4/3) pi eps^3 * 3 j_1(x)/x with x = 2 pi eps |w| (j_1 from SciPy; the
     value at w = 0 is the ball's volume).
     """
     w = np.asarray(omega, dtype=np.float64)
+    if kernel == "l1_ball":
+        # f = 1[||z||_1 <= eps] (the L1 ball of Sec. 2.4, an octahedron): the union of
+        # the 8 simplices conv(0, s_1 eps e_1, s_2 eps e_2, s_3 eps e_3); over a simplex
+        # conv(0, v_1, v_2, v_3), int exp(u.z) dz = 3! vol * exp[0, u.v_1, u.v_2, u.v_3]
+        # (divided difference), here with u = -2 pi i w and vol = eps^3 / 6.  The
+        # divided difference of exp at nodes x_0..x_3 is the top-right entry of expm of
+        # the bidiagonal matrix with the nodes on the diagonal and ones above it (Opitz).
+        flat = w.reshape(-1, 3)
+        out = np.zeros(len(flat))
+        for i, wi in enumerate(flat):
+            total = 0.0
+            for s in range(8):
+                sg = np.array([1.0 if (s >> d) & 1 else -1.0 for d in range(3)])
+                nodes = np.concatenate([[0.0], -2j * np.pi * eps * sg * wi])
+                J = np.diag(nodes.astype(complex)) + np.diag(np.ones(3, dtype=complex), 1)
+                total += scipy.linalg.expm(J)[0, 3].real
+            out[i] = eps ** 3 * total
+        return out.reshape(w.shape[:-1])
     if kernel == "ball":
         x = 2.0 * np.pi * eps * np.linalg.norm(w, axis=-1)
         safe = np.where(x == 0.0, 1.0, x)

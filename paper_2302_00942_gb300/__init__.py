@@ -41,8 +41,9 @@ class rfd_params(ctypes.Structure):
                 ("freq_radius", ctypes.c_double), ("kernel", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
-RFD_KERNEL_CUBE, RFD_KERNEL_BALL, RFD_KERNEL_CUBE_L1 = 0, 1, 2  # rfd_kernel: the eps-NN threshold function
-KERNELS = {"cube": RFD_KERNEL_CUBE, "ball": RFD_KERNEL_BALL, "cube_l1": RFD_KERNEL_CUBE_L1}
+RFD_KERNEL_CUBE, RFD_KERNEL_BALL, RFD_KERNEL_CUBE_L1, RFD_KERNEL_L1_BALL = 0, 1, 2, 3  # rfd_kernel: the eps-NN threshold function
+KERNELS = {"cube": RFD_KERNEL_CUBE, "ball": RFD_KERNEL_BALL, "cube_l1": RFD_KERNEL_CUBE_L1,
+           "l1_ball": RFD_KERNEL_L1_BALL}
 
 
 RFD_FLAG_TIMING = 1

@@ -615,7 +615,8 @@ rfd_status plan_prepare(const rfd_params& p, cudaStream_t stream, rfd_plan_s** o
   if (p.flags & ~(RFD_FLAG_TIMING | RFD_FLAG_NATIVE_FP64 | RFD_FLAG_AUTOTUNE | RFD_FLAG_GRAPH))
     return fail(RFD_EINVAL, "unknown bits in flags");
   if (p.n > (int64_t)1 << 31) return fail(RFD_EINVAL, "n must be < 2^31");
-  if (p.kernel != RFD_KERNEL_CUBE && p.kernel != RFD_KERNEL_BALL && p.kernel != RFD_KERNEL_CUBE_L1)
+  if (p.kernel != RFD_KERNEL_CUBE && p.kernel != RFD_KERNEL_BALL && p.kernel != RFD_KERNEL_CUBE_L1 &&
+      p.kernel != RFD_KERNEL_L1_BALL)
     return fail(RFD_EINVAL, "unknown kernel");
   if (p.reserved_ != 0) return fail(RFD_EINVAL, "rfd_params.reserved_ must be 0");
   auto* pl = new (std::nothrow) rfd_plan_s();

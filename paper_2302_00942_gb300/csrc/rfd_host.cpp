@@ -23,7 +23,9 @@
 //
 // This file must be compiled without floating-point contraction
 // (-ffp-contract=off) so that R (2 u1 - 1) is two rounded operations.
+#include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <string>
 #include "rfd_internal.h"
@@ -84,6 +86,38 @@ double tau_ball(const double (&w)[3], double eps) {
   return 4.0 * kPi * (std::sin(x) - x * std::cos(x)) / (q * q * q);
 }
 
+// f = 1[||z||_1 <= eps]: the octahedron is the union of the 8 simplices
+// conv(0, s_1 eps e_1, s_2 eps e_2, s_3 eps e_3), s in {-1, 1}^3.  Over a simplex
+// conv(0, v_1, v_2, v_3), the integral of exp(u . z) is 3! vol times the
+// divided difference of exp at the nodes 0, u . v_1, u . v_2, u . v_3 (the
+// exponential-simplex integral); with a node at 0 that divided difference is
+// sum_k h_k(y_1, y_2, y_3) / (k + 3)!, h_k the complete homogeneous symmetric
+// polynomial of degree k, by the recurrence h_k(y_1..y_j) = h_k(y_1..y_{j-1}) +
+// y_j h_{k-1}(y_1..y_j).  Here u = -2 pi i w (the transform's 2 pi convention),
+// each simplex has volume eps^3 / 6, and the 8 terms sum to a real number.
+double tau_l1_ball(const double (&w)[3], double eps) {
+  double total = 0.0, ymax = 0.0;
+  for (int d = 0; d < 3; ++d) ymax = std::max(ymax, 2.0 * kPi * eps * std::fabs(w[d]));
+  for (int s = 0; s < 8; ++s) {
+    std::complex<double> y[3];
+    for (int d = 0; d < 3; ++d) y[d] = std::complex<double>(0.0, ((s >> d) & 1 ? 2.0 : -2.0) * kPi * eps * w[d]);
+    std::complex<double> h1 = 1.0, h2 = 1.0, h3 = 1.0;  // degree 0
+    double fact = 6.0;                                  // (k + 3)!
+    std::complex<double> sum = h3 / fact;
+    for (int k = 1; k < 400; ++k) {
+      h1 = y[0] * h1;
+      h2 = h1 + y[1] * h2;
+      h3 = h2 + y[2] * h3;
+      fact *= (double)(k + 3);
+      const std::complex<double> term = h3 / fact;
+      sum += term;
+      if (k > 2.0 * ymax + 8.0 && std::abs(term) < 1e-18 * (std::abs(sum) + 1e-300)) break;
+    }
+    total += sum.real();
+  }
+  return eps * eps * eps * total;
+}
+
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -99,7 +133,8 @@ double default_radius(double eps) { return 1.0 / eps; }
 rfd_status sample_frequencies_host(int m, double eps, uint64_t seed, double sigma,
                                    double radius, int kernel, double* omega, double* r) {
   if (m < 2 || (m & 1)) return fail(RFD_EINVAL, "m must be even and >= 2");
-  if (kernel != RFD_KERNEL_CUBE && kernel != RFD_KERNEL_BALL && kernel != RFD_KERNEL_CUBE_L1)
+  if (kernel != RFD_KERNEL_CUBE && kernel != RFD_KERNEL_BALL && kernel != RFD_KERNEL_CUBE_L1 &&
+      kernel != RFD_KERNEL_L1_BALL)
     return fail(RFD_EINVAL, "unknown kernel");
   if (!(eps > 0.0) || !std::isfinite(eps)) return fail(RFD_EINVAL, "eps must be finite and > 0");
   if (sigma == 0.0) sigma = default_sigma(eps);
@@ -136,6 +171,7 @@ rfd_status sample_frequencies_host(int m, double eps, uint64_t seed, double sigm
         p *= std::exp(-0.5 * a * a) / norm;
       }
       if (kernel == RFD_KERNEL_BALL) tau = tau_ball(w3, eps);
+      if (kernel == RFD_KERNEL_L1_BALL) tau = tau_l1_ball(w3, eps);
       if (kernel == RFD_KERNEL_CUBE_L1) {
         const double s0 = sinc_cube(w3[0], eps), s1 = sinc_cube(w3[1], eps), s2 = sinc_cube(w3[2], eps);
         tau = abs_cube(w3[0], eps) * s1 * s2 + s0 * abs_cube(w3[1], eps) * s2 + s0 * s1 * abs_cube(w3[2], eps);

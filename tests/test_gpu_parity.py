@@ -177,9 +177,9 @@ def test_torus_config(prec):
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("name", ["small", "torus"])
-@pytest.mark.parametrize("kernel", ["ball", "cube_l1"])
+@pytest.mark.parametrize("kernel", ["ball", "cube_l1", "l1_ball"])
 def test_kernel_variants_match_oracle(prec, name, kernel):
-    """Threshold-function variants (the L2 ball, the Bessel case of Sec. 2.4; the
+    """Threshold-function variants (the L2 ball, the Bessel case of Sec. 2.4; the L1 ball; the
     distance-weighted cube): only step a1's weights change; the whole path
     against the oracle with the same kernel."""
     spec, pts, F, lam = small_case(name)

@@ -58,7 +58,7 @@ def test_estimator_separates_ball_from_cube():
     assert means["cube"] > 0.7 and means["ball"] < 0.3, means
 
 
-@pytest.mark.parametrize("kernel", ["ball", "cube_l1"])
+@pytest.mark.parametrize("kernel", ["ball", "cube_l1", "l1_ball"])
 def test_host_sampler_draws_the_oracle_weights(kernel):
     rfd = pytest.importorskip("paper_2302_00942_gb300")
     for seed in (0, 5):
@@ -71,7 +71,7 @@ def test_host_sampler_draws_the_oracle_weights(kernel):
         np.testing.assert_array_equal(om_c, om)  # the draw does not depend on the kernel
 
 
-@pytest.mark.parametrize("kernel", ["ball", "cube_l1"])
+@pytest.mark.parametrize("kernel", ["ball", "cube_l1", "l1_ball"])
 def test_lowrank_oracle_equals_dense_exponential(kernel):
     rng = np.random.default_rng(3)
     pts = rng.uniform(0.0, 0.5, size=(300, 3))
@@ -108,3 +108,47 @@ def test_estimator_reproduces_the_weighted_cube():
     assert abs(mean_w([0.5 * EPS, 0.5 * EPS, 0.0]) - EPS) < 0.4 * EPS
     assert abs(mean_w([1.5 * EPS, 0.0, 0.0])) < 0.4 * EPS
     assert abs(mean_w([0.0, 0.0, 0.0])) < 0.4 * EPS
+
+
+# ---- the L1 ball (octahedron) -------------------------------------------------
+
+def test_tau_l1_ball_at_zero_is_the_volume():
+    assert oracle.tau(np.zeros((1, 3)), EPS, "l1_ball")[0] == pytest.approx(4.0 / 3.0 * EPS ** 3, rel=1e-13)
+
+
+@pytest.mark.parametrize("w", [3.0, -17.0, 0.4])
+def test_tau_l1_ball_on_an_axis(w):
+    """w = (w, 0, 0): the cross-section of the octahedron at z_1 is a square of
+    area 2 (eps - |z_1|)^2, so tau = int cos(2 pi w z) 2 (eps - |z|)^2 dz."""
+    f = lambda z: np.cos(2.0 * np.pi * w * z) * 2.0 * (EPS - abs(z)) ** 2
+    ref, _ = scipy.integrate.quad(f, -EPS, EPS, epsabs=0.0, epsrel=1e-13, limit=200, points=[0.0])
+    t = oracle.tau(np.array([[w, 0.0, 0.0]]), EPS, "l1_ball")[0]
+    assert abs(t - ref) <= 1e-11 * 4.0 / 3.0 * EPS ** 3
+
+
+@pytest.mark.parametrize("w", [[2.0, -3.0, 1.0], [7.0, 0.5, -11.0], [4.0, 4.0, 4.0], [-6.0, 6.0, 0.0]])
+def test_tau_l1_ball_matches_quadrature(w):
+    w = np.array(w)
+    f = lambda z2, z1, z0: np.cos(2.0 * np.pi * (w[0] * z0 + w[1] * z1 + w[2] * z2))
+    r1 = lambda z0: EPS - abs(z0)
+    r2 = lambda z0, z1: EPS - abs(z0) - abs(z1)
+    ref, _ = scipy.integrate.tplquad(f, -EPS, EPS, lambda z0: -r1(z0), r1, lambda z0, z1: -r2(z0, z1), r2,
+                                     epsabs=1e-14, epsrel=1e-10)
+    t = oracle.tau(w[None, :], EPS, "l1_ball")[0]
+    assert abs(t - ref) <= 1e-8 * 4.0 / 3.0 * EPS ** 3
+
+
+def test_estimator_separates_l1_ball_from_l2_ball():
+    """z = (0.6 eps, 0.6 eps, 0) lies in the L2 ball (||z||_2 = 0.85 eps) but not in
+    the L1 ball (||z||_1 = 1.2 eps); z = (0.3 eps, 0.3 eps, 0) lies in both."""
+    m, sigma, R = 4096, 1.0 / EPS, 3.0 / EPS
+    def mean_w(z, kernel):
+        vals = []
+        for s in range(16):
+            om = oracle.sample_frequencies(m, EPS, 100 + s, sigma, R)
+            r = oracle.weights(om, EPS, sigma, R, kernel)
+            vals.append((2.0 / m) * np.sum(r * np.cos(2.0 * np.pi * om @ np.asarray(z))))
+        return float(np.mean(vals))
+    out = [0.6 * EPS, 0.6 * EPS, 0.0]
+    assert mean_w(out, "l1_ball") < 0.3 and mean_w(out, "ball") > 0.7
+    assert mean_w([0.3 * EPS, 0.3 * EPS, 0.0], "l1_ball") > 0.7
