@@ -260,8 +260,11 @@ RFD_API rfd_status rfd_gw_line_search(rfd_plan_t plan_C, rfd_plan_t plan_D, doub
  * ascending) or the k largest (largest = 1, descending) of these N values to
  * d_out (k float32, device).  Needs the resident M of rfd_features / rfd_gfi;
  * 1 <= k <= N and m <= 128 (RFD_EINVAL otherwise).  Asynchronous on the
- * plan's stream; M is unchanged.  FP32 arithmetic from the FP64 M (Cholesky
- * of M diag(sgn r), then cyclic Jacobi on the symmetric m x m matrix). */
+ * plan's stream; M is unchanged.  Cholesky of M diag(sgn r), cyclic Jacobi
+ * in FP32 on the symmetric m x m matrix L^T diag(sgn r) L; for an FP32-plain
+ * plan the Cholesky factor is FP64 and each eigenvalue is the FP64 Rayleigh
+ * quotient of its eigenvector (~1e-10 relative), for a BF16 plan (M good to
+ * ~1e-4) FP32 throughout (~1e-6 of the largest |eigenvalue| of lambda M). */
 RFD_API rfd_status rfd_eigenvalues(rfd_plan_t plan, int32_t k, int32_t largest, float* d_out);
 
 /* One cold pass of the whole path (a2-a6) when F is known up front: the

@@ -15,14 +15,18 @@
 // N < m, the m - N eigenvalues of smallest modulus belong to the rank
 // deficiency and are dropped.
 //
-// One CTA per cloud, all in shared memory: the Cholesky factor in FP64, the
-// Jacobi iteration in FP32 with its rotations accumulated, and each
-// eigenvalue then taken as the FP64 Rayleigh quotient of its FP32 eigenvector
-// on the FP64 factor (error second order in the eigenvector's, so the FP32
-// rotations do not limit the eigenvalues).  No device-side waits.
+// One CTA per cloud, all in shared memory.  For an M from the FP32 plain form:
+// the Cholesky factor in FP64, the Jacobi iteration in FP32 with its rotations
+// accumulated, and each eigenvalue then taken as the FP64 Rayleigh quotient of
+// its FP32 eigenvector on the FP64 factor (error second order in the
+// eigenvector's, so the FP32 rotations do not limit the eigenvalues).  For an
+// M from the BF16 form (good to ~1e-4), FP32 throughout: the Jacobi diagonal
+// (~1e-6 of ||H||) is far inside that, and the slow FP64 pipe is not used.
+// No device-side waits.
 #include <cuda_runtime.h>
 #include <cmath>
 #include <string>
+#include <type_traits>
 #include <vector>
 #include "kernels.h"
 #include "rfd_internal.h"
@@ -32,7 +36,7 @@ namespace rfd {
 
 namespace {
 
-constexpr int kEigThreads = 256;
+constexpr int kEigThreads = 128;
 constexpr int kEigMaxM = 128;
 constexpr int kMaxSweeps = 20;
 // stop when off(H) <= kOffTol ||H||_F: the eigenvectors are then good to ~1e-5,
@@ -47,11 +51,13 @@ struct EigJob {
   int32_t m, pad_;
 };
 
-// shared memory: L (FP64, packed lower triangle), the Jacobi iterate H and the
-// accumulated rotations V (FP32, m x (m+1)), then small arrays
-size_t eig_smem_bytes(int m) {
+// shared memory: L (packed lower triangle; FP64 when refined, else FP32), the
+// eigenvalue array, the Jacobi iterate H and (refined) the accumulated
+// rotations V (FP32, m x (m+1)), then small arrays
+size_t eig_smem_bytes(int m, bool refine) {
   const size_t ld = (size_t)m + 1, tri = (size_t)m * (m + 1) / 2;
-  return tri * sizeof(double) + 2 * m * ld * sizeof(float) + (size_t)m * 2 * sizeof(double) +
+  const size_t lbytes = (tri * (refine ? sizeof(double) : sizeof(float)) + 15) & ~size_t(15);
+  return lbytes + (size_t)m * 2 * sizeof(double) + (refine ? 2 : 1) * m * ld * sizeof(float) +
          (size_t)(3 * m + 64) * sizeof(float) + (size_t)2 * m * sizeof(int);
 }
 
@@ -67,6 +73,8 @@ __device__ float block_sum(float v, float* red) {
 }
 
 __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // j <= i
+__device__ __forceinline__ double root(double x) { return sqrt(x); }
+__device__ __forceinline__ float root(float x) { return sqrtf(x); }
 
 // insertion sort of x[0, cnt) by key(x) ascending (one thread; cnt <= 128)
 template <typename Key>
@@ -82,17 +90,21 @@ __device__ void sort_small(double* x, int cnt, Key key) {
   }
 }
 
-template <int MAXM>
+// REFINE: FP64 Cholesky and FP64 Rayleigh quotients of the FP32 eigenvectors
+// (the FP32 plain form's M); otherwise FP32 throughout and the eigenvalues are
+// the Jacobi diagonal, ~1e-6 of ||H|| (the BF16 form's M is good to ~1e-4).
+template <int MAXM, bool REFINE>
 __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob* __restrict__ jobs, int k,
                                                                    int largest, float* __restrict__ out) {
+  using TL = typename std::conditional<REFINE, double, float>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const EigJob jb = jobs[blockIdx.x];
   const int m = jb.m, ld = m + 1, half = m / 2, tid = threadIdx.x, nt = blockDim.x;
-  double* L = reinterpret_cast<double*>(smem_raw);      // P, then its Cholesky factor (packed lower)
-  double* mu = L + (size_t)m * (m + 1) / 2;             // 2m: eigenvalues, kernel eigenvalues
+  TL* L = reinterpret_cast<TL*>(smem_raw);              // P, then its Cholesky factor (packed lower)
+  double* mu = reinterpret_cast<double*>(smem_raw + (((size_t)m * (m + 1) / 2 * sizeof(TL) + 15) & ~size_t(15)));
   float* H = reinterpret_cast<float*>(mu + 2 * m);      // L^T Sigma L, then the Jacobi iterate
-  float* V = H + m * ld;                                // accumulated rotations (columns: eigenvectors)
-  float* sig = V + m * ld;                              // Sigma
+  float* V = H + m * ld;                                // accumulated rotations (REFINE only)
+  float* sig = REFINE ? V + m * ld : V;                 // Sigma
   float* cs = sig + m;                                  // rotation (c, s, t) of each pair
   float* red = cs + 2 * m;                              // 64 floats of reduction scratch
   int* pq = reinterpret_cast<int*>(red + 64);           // (p, q) of each pair
@@ -103,20 +115,20 @@ __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob*
     const int i = e / m, j = e % m;
     if (j > i) continue;
     const double si = jb.oa[i] < 0.0 ? -1.0 : 1.0, sj = jb.oa[j] < 0.0 ? -1.0 : 1.0;
-    L[tri(i, j)] = 0.5 * (jb.M[(size_t)i * m + j] * sj + jb.M[(size_t)j * m + i] * si);
+    L[tri(i, j)] = (TL)(0.5 * (jb.M[(size_t)i * m + j] * sj + jb.M[(size_t)j * m + i] * si));
   }
   __syncthreads();
-  double dmax = 0.0;
-  for (int i = 0; i < m; ++i) dmax = fmax(dmax, L[tri(i, i)]);
-  const double tol = dmax * (double)m * 4e-16;
+  TL dmax = 0;
+  for (int i = 0; i < m; ++i) dmax = max(dmax, L[tri(i, i)]);
+  const TL tol = dmax * (TL)m * (TL)(REFINE ? 4e-16 : 2.4e-7);
 
-  // Cholesky P = L L^T (FP64), right-looking; a pivot <= tol drops its column
+  // Cholesky P = L L^T, right-looking; a pivot <= tol drops its column
   for (int j = 0; j < m; ++j) {
-    const double d = L[tri(j, j)];
-    const double piv = d > tol ? sqrt(d) : 0.0;
+    const TL d = L[tri(j, j)];
+    const TL piv = d > tol ? root(d) : (TL)0;
     __syncthreads();
     if (tid == 0) L[tri(j, j)] = piv;
-    const double inv = piv > 0.0 ? 1.0 / piv : 0.0;
+    const TL inv = piv > (TL)0 ? (TL)1 / piv : (TL)0;
     for (int i = j + 1 + tid; i < m; i += nt) L[tri(i, j)] *= inv;
     __syncthreads();
     const int t = m - j - 1;
@@ -127,24 +139,32 @@ __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob*
     __syncthreads();
   }
 
-  // H = L^T Sigma L in FP32 (it only seeds the FP32 iteration; the eigenvalues
-  // come from the FP64 factor below): an FP32 copy of L in V's space first
-  for (int e = tid; e < m * m; e += nt) {
-    const int i = e / m, j = e % m;
-    V[i * ld + j] = j <= i ? (float)L[tri(i, j)] : 0.f;
+  // H = L^T Sigma L in FP32 (refined: it only seeds the FP32 iteration, the
+  // eigenvalues come from the FP64 factor; an FP32 copy of L in V's space first)
+  const float* Lf = reinterpret_cast<const float*>(L);
+  if constexpr (REFINE) {
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = e / m, j = e % m;
+      V[i * ld + j] = j <= i ? (float)L[tri(i, j)] : 0.f;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   for (int e = tid; e < m * m; e += nt) {
     const int a = e / m, b = e % m;
     if (a > b) continue;
     float s = 0.f;
-    for (int i = b; i < m; ++i) s = fmaf(V[i * ld + a] * sig[i], V[i * ld + b], s);
+    if constexpr (REFINE)
+      for (int i = b; i < m; ++i) s = fmaf(V[i * ld + a] * sig[i], V[i * ld + b], s);
+    else
+      for (int i = b; i < m; ++i) s = fmaf(Lf[tri(i, a)] * sig[i], Lf[tri(i, b)], s);
     H[a * ld + b] = s;
     H[b * ld + a] = s;
   }
   __syncthreads();
-  for (int e = tid; e < m * m; e += nt) V[(e / m) * ld + e % m] = (e / m) == (e % m) ? 1.f : 0.f;
-  __syncthreads();
+  if constexpr (REFINE) {
+    for (int e = tid; e < m * m; e += nt) V[(e / m) * ld + e % m] = (e / m) == (e % m) ? 1.f : 0.f;
+    __syncthreads();
+  }
 
   // cyclic Jacobi in FP32, round-robin pairs: round r pairs (r, m-1) and
   // ((r + q) mod (m-1), (r - q) mod (m-1)) for q = 1 .. m/2 - 1.  The m/2
@@ -237,7 +257,7 @@ __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob*
           H[qb * ld + qa] = y11;
         }
       }
-      if (vi0 < vgroups) {
+      if (REFINE && vi0 < vgroups) {
         const int p = pq[2 * vq], qq = pq[2 * vq + 1];
         const float c = cs[3 * vq], s = cs[3 * vq + 1];
         for (int i = vi0; i < m; i += vgroups) {
@@ -250,6 +270,10 @@ __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob*
     }
   }
 
+  if constexpr (!REFINE) {
+    for (int a2 = tid; a2 < m; a2 += nt) mu[a2] = (double)H[a2 * ld + a2];
+    __syncthreads();
+  } else {
   // the eigenvectors to FP64, one padded row per vector (V64[a][j] = V[j][a]),
   // over the space of H and V: rows a < m/2 land in H's space; the columns
   // a >= m/2 of V are read into registers before their rows overwrite V's
@@ -297,6 +321,8 @@ __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob*
   }
   __syncthreads();
 
+  }
+
   // the spectrum of exp(lambda W_hat): drop the rank deficiency, sort, merge the ones
   if (tid == 0) {
     int cnt = m;
@@ -336,16 +362,26 @@ __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob*
   }
 }
 
-rfd_status launch_eigen(const EigJob* d_jobs, int count, int max_m, int k, int largest, float* d_out,
-                        cudaStream_t st) {
-  const size_t smem = eig_smem_bytes(max_m);
-  auto kern = max_m <= 64 ? kernel_eigen_kernel<64> : kernel_eigen_kernel<kEigMaxM>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int MAXM, bool REFINE>
+rfd_status launch_eigen_t(const EigJob* d_jobs, int count, int max_m, int k, int largest, float* d_out,
+                          cudaStream_t st) {
+  const size_t smem = eig_smem_bytes(max_m, REFINE);
+  cudaError_t e = cudaFuncSetAttribute(kernel_eigen_kernel<MAXM, REFINE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return fail(RFD_ECUDA, std::string("eigen attribute: ") + cudaGetErrorString(e));
-  kern<<<count, kEigThreads, smem, st>>>(d_jobs, k, largest, d_out);
+  kernel_eigen_kernel<MAXM, REFINE><<<count, kEigThreads, smem, st>>>(d_jobs, k, largest, d_out);
   count_launch();
   e = cudaGetLastError();
   return e == cudaSuccess ? RFD_OK : fail(RFD_ECUDA, std::string("eigen launch: ") + cudaGetErrorString(e));
+}
+
+rfd_status launch_eigen(const EigJob* d_jobs, int count, int max_m, int k, int largest, bool refine, float* d_out,
+                        cudaStream_t st) {
+  if (max_m <= 64)
+    return refine ? launch_eigen_t<64, true>(d_jobs, count, max_m, k, largest, d_out, st)
+                  : launch_eigen_t<64, false>(d_jobs, count, max_m, k, largest, d_out, st);
+  return refine ? launch_eigen_t<kEigMaxM, true>(d_jobs, count, max_m, k, largest, d_out, st)
+                : launch_eigen_t<kEigMaxM, false>(d_jobs, count, max_m, k, largest, d_out, st);
 }
 
 rfd_status check_eigen_plan(const rfd_plan_s* pl, int k, int idx) {
@@ -358,13 +394,14 @@ rfd_status check_eigen_plan(const rfd_plan_s* pl, int k, int idx) {
 EigJob job_of(const rfd_plan_s* pl) { return EigJob{pl->d_M, pl->d_oa, pl->p.lambda, pl->n, pl->m, 0}; }
 
 // runs the kernel on host-built jobs (a temporary device table on the stream)
-rfd_status run_jobs(const std::vector<EigJob>& jobs, int max_m, int k, int largest, float* d_out, cudaStream_t st) {
+rfd_status run_jobs(const std::vector<EigJob>& jobs, int max_m, int k, int largest, bool refine, float* d_out,
+                    cudaStream_t st) {
   EigJob* d_jobs = nullptr;
   const size_t bytes = jobs.size() * sizeof(EigJob);
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_jobs), bytes, st);
   if (e != cudaSuccess) return fail(RFD_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
   e = cudaMemcpyAsync(d_jobs, jobs.data(), bytes, cudaMemcpyHostToDevice, st);
-  rfd_status s = e == cudaSuccess ? launch_eigen(d_jobs, (int)jobs.size(), max_m, k, largest, d_out, st)
+  rfd_status s = e == cudaSuccess ? launch_eigen(d_jobs, (int)jobs.size(), max_m, k, largest, refine, d_out, st)
                                   : fail(RFD_ECUDA, std::string("job upload: ") + cudaGetErrorString(e));
   cudaFreeAsync(d_jobs, st);  // a pageable upload is staged before cudaMemcpyAsync returns
   return s;
@@ -376,12 +413,14 @@ rfd_status batch_eigenvalues(rfd_plan_s* const* plans, int count, int k, int lar
                              Timing* tm) {
   std::vector<EigJob> jobs((size_t)count);
   int max_m = 2;
+  bool refine = false;  // FP64 refinement when some cloud's M came from the FP32 plain form
   for (int i = 0; i < count; ++i) {
     jobs[i] = job_of(plans[i]);
     max_m = std::max(max_m, plans[i]->m);
+    refine = refine || !plans[i]->bf16;
   }
   StepScope sc(tm, st, RFD_STEP_EIGEN);
-  return run_jobs(jobs, max_m, k, largest, d_out, st);
+  return run_jobs(jobs, max_m, k, largest, refine, d_out, st);
 }
 
 rfd_status check_eigen_args(rfd_plan_s* const* plans, int count, int k) {
