@@ -260,7 +260,7 @@ __global__ void weighted_gram_kernel(const float* __restrict__ A, const float* _
   const int f = blockIdx.x;
   const int64_t per = (n + gridDim.y - 1) / gridDim.y;
   const int64_t r0 = (int64_t)blockIdx.y * per, r1 = min(n, r0 + per);
-  __shared__ double red[8][33];
+  __shared__ float red[8][33];
   float acc[32];
   for (int g = 0; g < 32; ++g) acc[g] = 0.f;
   for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
@@ -268,8 +268,8 @@ __global__ void weighted_gram_kernel(const float* __restrict__ A, const float* _
     for (int g = 0; g < mf; ++g) acc[g] = fmaf(a, B[i * mf + g], acc[g]);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int g = 0; g < mf; ++g) {
-    double v = acc[g];
+  for (int g = 0; g < mf; ++g) {  // FP32 within a warp (the FP64 pipe is slow), FP64 across warps
+    float v = acc[g];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) red[warp][g] = v;
   }
@@ -343,6 +343,81 @@ __global__ void __launch_bounds__(256) gw_assemble_kernel(const float* __restric
   }
 }
 
+// The same assembly, 16-byte I/O (n2 % 4 == 0, aligned T, L, v2): a CTA keeps
+// the (P'_j, Ud_j) of its 256 columns in shared memory, k-major, and walks
+// row tiles of 16; a thread takes 4 rows x 4 adjacent columns: it issues the
+// tile's T loads first, computes the rank-2 MF update (2 shared 16-byte loads
+// per 16 FMAs) while they are in flight, then writes L as float4.
+template <int MF>
+__global__ void __launch_bounds__(256) gw_assemble4_kernel(const float* __restrict__ T, const float* __restrict__ v1,
+                                                           const float* __restrict__ v2, const float* __restrict__ Uc,
+                                                           const float* __restrict__ Q, const float* __restrict__ Pp,
+                                                           const float* __restrict__ Ud, int64_t n1, int64_t n2,
+                                                           float* __restrict__ L, int rows_per_group) {
+  constexpr int K2 = 2 * MF, TR = 16;
+  extern __shared__ __align__(16) float sm[];
+  float* colS = sm;               // [K2][kTJ]
+  float* rowS = colS + K2 * kTJ;  // [K2][TR]
+  const int t = threadIdx.x, cg = t & 63, rg = t >> 6;
+  const int64_t j0 = (int64_t)blockIdx.x * kTJ;
+  for (int e = t; e < K2 * kTJ; e += 256) {
+    const int k = e / kTJ, c = e % kTJ;
+    const int64_t j = j0 + c;
+    colS[e] = j < n2 ? (k < MF ? Pp[j * MF + k] : Ud[j * MF + k - MF]) : 0.f;
+  }
+  const int64_t jc = j0 + 4 * cg;
+  const bool cols_ok = jc < n2;  // n2 % 4 == 0: all four or none
+  const float4 w2 = cols_ok ? *reinterpret_cast<const float4*>(v2 + jc) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const int64_t ig0 = (int64_t)blockIdx.y * rows_per_group, ig1 = min(n1, ig0 + rows_per_group);
+  for (int64_t i0 = ig0; i0 < ig1; i0 += TR) {
+    float4 tv[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t i = i0 + 4 * rg + r;
+      tv[r] = (cols_ok && i < ig1) ? *reinterpret_cast<const float4*>(T + i * n2 + jc) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    for (int e = t; e < K2 * TR; e += 256) {
+      const int k = e / TR, r = e % TR;
+      const int64_t i = i0 + r;
+      rowS[e] = i < ig1 ? (k < MF ? Uc[i * MF + k] : Q[i * MF + k - MF]) : 0.f;
+    }
+    __syncthreads();
+    float acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < K2; ++k) {
+      const float4 cv = *reinterpret_cast<const float4*>(colS + k * kTJ + 4 * cg);
+      const float4 ra = *reinterpret_cast<const float4*>(rowS + k * TR + 4 * rg);
+      const float rv[4] = {ra.x, ra.y, ra.z, ra.w};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        acc[r][0] = fmaf(rv[r], cv.x, acc[r][0]);
+        acc[r][1] = fmaf(rv[r], cv.y, acc[r][1]);
+        acc[r][2] = fmaf(rv[r], cv.z, acc[r][2]);
+        acc[r][3] = fmaf(rv[r], cv.w, acc[r][3]);
+      }
+    }
+    if (!cols_ok) continue;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t i = i0 + 4 * rg + r;
+      if (i < ig1) {
+        const float vi = v1[i];
+        float4 o;
+        o.x = vi + w2.x - 2.f * (tv[r].x + acc[r][0]);
+        o.y = vi + w2.y - 2.f * (tv[r].y + acc[r][1]);
+        o.z = vi + w2.z - 2.f * (tv[r].z + acc[r][2]);
+        o.w = vi + w2.w - 2.f * (tv[r].w + acc[r][3]);
+        *reinterpret_cast<float4*>(L + i * n2 + jc) = o;
+      }
+    }
+  }
+}
+
 // sum += sum_i A_i . (B_i Km)   (FP64)
 __global__ void rowdot_kernel(const float* __restrict__ A, const float* __restrict__ B, const float* __restrict__ Km,
                               int64_t n, int mf, double* __restrict__ sum) {
@@ -352,11 +427,13 @@ __global__ void rowdot_kernel(const float* __restrict__ A, const float* __restri
   __syncthreads();
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float row = 0.f;  // FP32 within a row, FP64 across rows
     for (int f = 0; f < mf; ++f) {
       float bk = 0.f;
       for (int g = 0; g < mf; ++g) bk = fmaf(B[i * mf + g], Ks[g * mf + f], bk);
-      acc = fma((double)A[i * mf + f], (double)bk, acc);
+      row = fmaf(A[i * mf + f], bk, row);
     }
+    acc += (double)row;
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -639,13 +716,35 @@ rfd_status tensor_product_lowrank(rfd_plan_t pc, rfd_plan_t pd, const float* T, 
   const Proj pr = take_proj(cv, n1, n2, lp.mf);
   if (s == RFD_OK) s = project(lp.mf, T, n1, n2, lp.c, lp.d, pr, lp.parts, lp.R, st);
   if (s == RFD_OK) {
-    const dim3 grid((unsigned)((n2 + kTJ - 1) / kTJ), (unsigned)((n1 + kTA - 1) / kTA));
-    if (lp.mf == 16)
-      gw_assemble_kernel<16><<<grid, 256, 0, st>>>(T, lp.v1, lp.v2, lp.c.U, pr.Q, pr.Pp, lp.d.U, n1, n2, L);
-    else
-      gw_assemble_kernel<32><<<grid, 256, 0, st>>>(T, lp.v1, lp.v2, lp.c.U, pr.Q, pr.Pp, lp.d.U, n1, n2, L);
+    const bool vec4 = (n2 & 3) == 0 && ((reinterpret_cast<uintptr_t>(T) | reinterpret_cast<uintptr_t>(L) |
+                                          reinterpret_cast<uintptr_t>(lp.v2)) & 15) == 0;
+    if (vec4) {
+      const int64_t tiles = (n1 + 15) / 16;
+      const int groups = (int)std::min<int64_t>(kRowGroups, tiles);
+      const int rows_per_group = (int)(((tiles + groups - 1) / groups) * 16);
+      const dim3 grid((unsigned)((n2 + kTJ - 1) / kTJ), (unsigned)groups);
+      const size_t smem = (size_t)2 * lp.mf * (kTJ + 16) * sizeof(float);
+      if (lp.mf == 16) {
+        e = cudaFuncSetAttribute(gw_assemble4_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+          gw_assemble4_kernel<16><<<grid, 256, smem, st>>>(T, lp.v1, lp.v2, lp.c.U, pr.Q, pr.Pp, lp.d.U, n1, n2, L,
+                                                           rows_per_group);
+      } else {
+        e = cudaFuncSetAttribute(gw_assemble4_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+          gw_assemble4_kernel<32><<<grid, 256, smem, st>>>(T, lp.v1, lp.v2, lp.c.U, pr.Q, pr.Pp, lp.d.U, n1, n2, L,
+                                                           rows_per_group);
+      }
+      if (e != cudaSuccess) s = cuda_err("assembly attribute", e);
+    } else {
+      const dim3 grid((unsigned)((n2 + kTJ - 1) / kTJ), (unsigned)((n1 + kTA - 1) / kTA));
+      if (lp.mf == 16)
+        gw_assemble_kernel<16><<<grid, 256, 0, st>>>(T, lp.v1, lp.v2, lp.c.U, pr.Q, pr.Pp, lp.d.U, n1, n2, L);
+      else
+        gw_assemble_kernel<32><<<grid, 256, 0, st>>>(T, lp.v1, lp.v2, lp.c.U, pr.Q, pr.Pp, lp.d.U, n1, n2, L);
+    }
     count_launch();
-    s = launched_or("tensor product");
+    if (s == RFD_OK) s = launched_or("tensor product");
   }
   cudaFreeAsync(cv.base, st);
   return s;

@@ -89,6 +89,20 @@ def test_tensor_product_and_line_search_match_oracle(prec, m, eps, lam):
         pd.close()
 
 
+@pytest.mark.parametrize("n1,n2", [(300, 203), (77, 1000)])
+def test_tensor_product_ragged_sizes(n1, n2):
+    """Column counts that are not a multiple of 4 take the scalar assembly;
+    row counts below one tile, and tiles cut by the row groups."""
+    pc, pd, ac, ad, (T, p, q, _, _) = _setup(rfd.RFD_FP32_PLAIN, 16, 0.3, -0.2, n1=n1, n2=n2)
+    try:
+        L = rfd.gw_tensor_product(pc, pd, _cuda(T), _cuda(p), _cuda(q))
+        pc.sync()
+        assert oracle.rel_frobenius(L.cpu().numpy(), oracle.gw_tensor_product(ac, ad, T, p, q)) <= 1e-4
+    finally:
+        pc.close()
+        pd.close()
+
+
 def test_gw_argument_checks():
     pc, pd, _, _, (T, p, q, _, _) = _setup(rfd.RFD_FP32_PLAIN, 16, 0.3, -0.2, n1=100, n2=80)
     other = torch.cuda.Stream(DEV)
