@@ -38,6 +38,7 @@ namespace {
 
 constexpr int kEigThreads = 128;
 constexpr int kEigMaxM = 128;
+static_assert(kEigThreads >= kEigMaxM, "the spectrum ranks take one thread per eigenvalue");
 constexpr int kMaxSweeps = 20;
 // stop when off(H) <= kOffTol ||H||_F: the eigenvectors are then good to ~1e-5,
 // and the FP64 Rayleigh quotients good to ~1e-10 relative (second order)
@@ -75,20 +76,6 @@ __device__ float block_sum(float v, float* red) {
 __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // j <= i
 __device__ __forceinline__ double root(double x) { return sqrt(x); }
 __device__ __forceinline__ float root(float x) { return sqrtf(x); }
-
-// insertion sort of x[0, cnt) by key(x) ascending (one thread; cnt <= 128)
-template <typename Key>
-__device__ void sort_small(double* x, int cnt, Key key) {
-  for (int i = 1; i < cnt; ++i) {
-    const double v = x[i];
-    int j = i - 1;
-    while (j >= 0 && key(x[j]) > key(v)) {
-      x[j + 1] = x[j];
-      --j;
-    }
-    x[j + 1] = v;
-  }
-}
 
 // REFINE: FP64 Cholesky and FP64 Rayleigh quotients of the FP32 eigenvectors
 // (the FP32 plain form's M); otherwise FP32 throughout and the eigenvalues are
@@ -323,28 +310,33 @@ __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob*
 
   }
 
-  // the spectrum of exp(lambda W_hat): drop the rank deficiency, sort, merge the ones
-  if (tid == 0) {
-    int cnt = m;
-    if (jb.n < m) {  // drop the m - n eigenvalues of smallest modulus
-      sort_small(mu, m, [](double x) { return fabs(x); });
-      const int drop = m - (int)jb.n;
-      for (int i = 0; i < (int)jb.n; ++i) mu[i] = mu[i + drop];
-      cnt = (int)jb.n;
+  // the spectrum of exp(lambda W_hat): drop the rank deficiency, sort, merge the
+  // ones -- all by ranks (thread i counts the entries before entry i), no serial step
+  const int drop = jb.n < m ? m - (int)jb.n : 0;  // the m - n of smallest modulus go (rank deficiency)
+  double kap = 0.0;
+  bool keep = false;
+  if (tid < m) {
+    const double x = mu[tid];
+    int r = 0;
+    for (int j = 0; j < m; ++j) {
+      const double y = fabs(mu[j]);
+      r += (y < fabs(x)) || (y == fabs(x) && j < tid);
     }
-    for (int i = 0; i < cnt; ++i) mu[i] = exp(jb.lambda * mu[i]);
-    sort_small(mu, cnt, [](double x) { return x; });
-    int below = 0, above = 0;
-    for (int i = 0; i < cnt; ++i) {
-      below += mu[i] < 1.0;
-      above += mu[i] > 1.0;
-    }
-    pq[0] = cnt;
-    pq[1] = below;
-    pq[2] = above;
+    keep = r >= drop;
+    kap = REFINE ? exp(jb.lambda * x) : (double)expf((float)(jb.lambda * x));
   }
   __syncthreads();
-  const int cnt = pq[0], below = pq[1], above = pq[2];
+  if (tid < m) mu[tid] = keep ? kap : INFINITY;  // dropped entries sort last and are never read
+  __syncthreads();
+  if (tid < m && keep) {
+    int r = 0;
+    for (int j = 0; j < m; ++j) r += (mu[j] < kap) || (mu[j] == kap && j < tid);
+    mu[m + r] = kap;
+  }
+  const int cnt = m - drop;
+  const int below = __syncthreads_count(tid < m && keep && kap < 1.0);
+  const int above = __syncthreads_count(tid < m && keep && kap > 1.0);
+  mu += m;  // the sorted kernel eigenvalues
   const int64_t ones = jb.n > m ? jb.n - m : 0;
   float* o = out + (size_t)blockIdx.x * k;
   for (int j = tid; j < k; j += nt) {
