@@ -29,6 +29,14 @@ RFD_API rfd_status rfd_debug_dgemm(int32_t method, int32_t M, int32_t N, int32_t
                                    int32_t lda, const double* B, int32_t ldb, double beta, double* C, int32_t ldc,
                                    void* cuda_stream);
 
+/* Step a4 of a BF16 plan alone, on a given m x m FP64 DEVICE matrix M (copied
+ * into the plan's M): the batched emulated evaluation of G = lambda phi1(lambda M)
+ * that rfd_features runs (Taylor degree 16 in Paterson-Stockmeyer form with
+ * scaling and squaring), leaving G resident for rfd_plan_export.  Synchronises
+ * the plan's stream; RFD_EINVAL for FP32 plans or plans on the native-FP64
+ * path, RFD_ENUMERIC if G is not finite. */
+RFD_API rfd_status rfd_debug_plan_phi1(rfd_plan_t plan, const double* d_M);
+
 /* Hold (paused = 1) or release (0) a server's executors: while held they
  * start no new batch (batches already running finish), so a test can make a
  * poll wait run out deterministically. */

@@ -1055,6 +1055,17 @@ rfd_status rfd_batch_stats_reset(rfd_batch_t b) {
 // on fails with RFD_ENOMEM (k = 0: the next one); k < 0 disables.
 void rfd_debug_fail_alloc_after(int32_t k) { g_fail_alloc_after = k; }
 
+rfd_status rfd_debug_plan_phi1(rfd_plan_t pl, const double* d_M) {
+  if (!pl || !d_M) return fail(RFD_EINVAL, "null plan or M");
+  if (!pl->bf16 || !pl->self) return fail(RFD_EINVAL, "the batched step a4 runs for BF16 plans");
+  RFD_CUDA(cudaMemcpyAsync(pl->d_M, d_M, (size_t)pl->m * pl->m * sizeof(double), cudaMemcpyDeviceToDevice,
+                           pl->stream));
+  rfd_status s = batch_phi1_only(pl->self);
+  if (s != RFD_OK) return s;
+  RFD_CUDA(cudaStreamSynchronize(pl->stream));
+  return check_device_error(pl);
+}
+
 rfd_status rfd_debug_dgemm(int32_t method, int32_t M, int32_t N, int32_t K, double alpha, const double* A, int32_t lda,
                            const double* B, int32_t ldb, double beta, double* C, int32_t ldc, void* cuda_stream) {
   if (M < 1 || N < 1 || K < 1 || !A || !B || !C || lda < K || ldb < N || ldc < N)

@@ -3,11 +3,11 @@
 // N and m); a single cloud runs as a batch of one.
 //
 // Step a4 runs on the FP64-accurate tensor-core GEMM for all clouds at once:
-// diagonal Pade of degree 5 on the block-triangular augmented matrix, the
-// denominator solved by the product (I + R)(I + R^2)...(I + R^16) (||R|| <
-// 0.14 for ||X||_1 <= theta_5, see rfd_phi1.cu), and per-cloud squarings s_c
-// chosen on the device from ||lambda M||_1 (clouds with s_c <= k skip squaring
-// step k).  The host waits once per call, for the largest s_c, which sets the
+// the degree-16 Taylor polynomial of phi1 at 2^-s_c lambda M, evaluated by
+// Paterson-Stockmeyer (X^2, X^3, X^4, then three Horner steps in X^4: six
+// products), and per-cloud squarings s_c chosen on the device from
+// ||lambda M||_1 so that ||2^-s_c lambda M||_1 <= theta_16 (clouds with
+// s_c <= k skip squaring step k).  The host waits once per call, for the largest s_c, which sets the
 // number of squaring launches.  Non-finite results and device-side timeouts
 // are recorded in sticky device words that batch_check_error reads.
 //
@@ -29,8 +29,10 @@ namespace rfd {
 
 namespace {
 
-constexpr double kTheta5 = 2.539398330063230e-1;  // Higham (2005), Table 2.3, degree 5
-constexpr int kSolveFactors = 5;                  // (0.135)^(2^5) / (1 - 0.135) < 2^-56
+// theta_16: the largest ||X||_1 with sum_{k > 16} ||X||_1^k / (k+1)! <= 2^-53, the tail
+// of the Taylor series of phi1 after degree 16 (0.97709 by bisection; rounded down)
+constexpr double kThetaT16 = 0.977;
+constexpr int kTaylorDegree = 16;
 constexpr int kMaxSquarings = 60;                 // beyond this exp(lambda M) overflows anyway
 // matrix slots of the phi1 evaluation (see kernels.h: slot k = work + k m^2)
 enum : int { sX = 0, sX2, sX4, sSp, sVp, sUp, sR, sR2, sF, sFb, sE, sT1, sT2 };
@@ -359,18 +361,39 @@ rfd_status phi1_select(BatchImpl* b, cudaStream_t st) {
   const double a[4] = {1.0, 0.0, 0.0, 0.0};
   BCK(launch_bcombine(b->d_phi, b->d_elem_prefix, n, b->elem_blocks, sX, src, a, 0.0, 1, -1, st));  // X = lambda M
   BCK(launch_bnorm1(b->d_phi, n, b->max_m, sX, b->d_norms, st));
-  BCK(launch_bselect(b->d_phi, n, b->d_norms, kTheta5, kMaxSquarings, b->d_sv, st));
+  BCK(launch_bselect(b->d_phi, n, b->d_norms, kThetaT16, kMaxSquarings, b->d_sv, st));
   BCK(cudaMemcpyAsync(b->h_sv, b->d_sv, (size_t)(n + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
   BCK(cudaMemcpyAsync(b->h_norms, b->d_norms, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
   return RFD_OK;
 }
 
-// Step a4, second part: diagonal Pade of degree 5 at 2^-s_c X, the product-form
-// solve, max_s masked squaring steps, G = lambda F, and the finiteness flags.
-// The combinations ride in the product epilogues (D = alpha A B + beta C +
-// diag I): R = I - Vp + X Sp, F_0 = (I + R) 2 Sp, F_j+1 = F_j + R^(2^j) F_j,
-// E = I + X F, F <- (E F + F) / 2; slots are swapped instead of copied.
-rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s) {
+// Step a4, second part: phi1 at X = 2^-s_c lambda M by its Taylor polynomial of
+// degree 16, sum_k X^k / (k+1)!, in Paterson-Stockmeyer form with blocks of 4:
+// with B_j = sum_{i<4} c_{4j+i} X^i (c_k = 1/(k+1)!),
+//   F = B_0 + X^4 (B_1 + X^4 (B_2 + X^4 (B_3 + c_16 X^4)))
+// -- three products for X^2, X^3, X^4 and three Horner products, whose
+// epilogues (D = alpha A B + beta C + diag I) add B_j (its X, X^2, X^3 part
+// from one element-wise combination, c_{4j} on the diagonal); then max_s masked
+// squaring steps, phi1(2Y) = (e^Y + I) phi1(Y) / 2 with e^Y = I + Y phi1(Y):
+// E = I + X F, F <- (E F + F) / 2, E <- E^2; G = lambda F, and the finiteness
+// flags.  Slots are swapped instead of copied.
+// Moduli of the first two Horner products (see phi1_core), from the batch's largest
+// scaled norm: {for j = 2, for j = 1}.  Part of the CUDA-graph key of the segment.
+void horner_moduli(const BatchImpl* b, int out[2]) {
+  double xmax = 0.0;  // largest ||2^-s_c lambda M||_1 over the batch (<= theta_16)
+  for (int c = 0; c < b->count; ++c)
+    if (std::isfinite(b->h_norms[c])) xmax = std::max(xmax, std::ldexp(b->h_norms[c], -std::max(b->h_sv[c], 0)));
+  xmax = std::min(xmax, kThetaT16);
+  const double x4 = xmax * xmax * xmax * xmax;
+  auto moduli_for = [&](double q) {
+    const int k = (int)std::ceil(53.0 + std::log2(std::max(q, 1e-300)));
+    return std::min(16, std::max(4, ozaki_moduli_for_bits(std::max(b->max_m, 1), k)));
+  };
+  out[0] = moduli_for(x4 * x4);
+  out[1] = moduli_for(x4);
+}
+
+rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s, const int horner_nmod[2]) {
   const int n = b->count;
   auto comb = [&](int dst, std::initializer_list<int> src, std::initializer_list<double> a, double diag, int kmode,
                   int mask) {
@@ -385,15 +408,10 @@ rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s) {
   // Moduli per product.  A product whose result enters F scaled by a factor Q with
   // max|Q| <= q only needs k = 53 - log2(1/q) bits of its operands for FP64 accuracy
   // relative to F (the emulation errs by ~2^-k K max|Q| max|F| per entry, like an FP64
-  // product's K u |Q||F|).  In the product-form solve Q = R^(2^j) with
-  // ||R||_1 <= p_5(theta_5) - 1 < 0.135 (so max|R^(2^j)| <= 0.135^(2^j)); the fewest
-  // moduli that give those bits for the batch's largest m are used.
+  // product's K u |Q||F|).  The first two Horner products enter F through one or two
+  // more factors X^4, max|X^4| <= ||X||_1^4 (the batch's largest scaled norm); the
+  // fewest moduli that give those bits for the batch's largest m are used.
   const int kfull = 16;
-  auto moduli_for = [&](double q) {
-    const int k = (int)std::ceil(53.0 + std::log2(q));
-    return std::min(kfull, ozaki_moduli_for_bits(std::max(b->max_m, 1), k));
-  };
-  constexpr double kRBound = 0.135;
   // the A / B residues hold the operands of the previous product (split with the same
   // number of moduli, hence the same integer width): split only what changed
   int last_a = kNoSlot, last_b = kNoSlot, last_na = 0, last_nb = 0;
@@ -411,30 +429,25 @@ rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s) {
     if (slot == last_a) last_a = kNoSlot;
     if (slot == last_b) last_b = kNoSlot;
   };
-  // diagonal Pade, degree 5: b_k = (10-k)! 5! / (10! k! (5-k)!) with b_0 = 1
-  double pb[6];
-  pb[0] = 1.0;
-  for (int k = 0; k < 5; ++k) pb[k + 1] = pb[k] * double(5 - k) / (double(10 - k) * double(k + 1));
+  double ck[kTaylorDegree + 1];  // c_k = 1 / (k + 1)!
+  ck[0] = 1.0;
+  for (int k = 1; k <= kTaylorDegree; ++k) ck[k] = ck[k - 1] / (double)(k + 1);
+  const int sX3 = sR;
   if (max_s > 0) BCK(comb(sX, {sX}, {1.0}, 0.0, 2, -1));  // X = 2^-s X
   BCK(gemm(sX, sX, kNoSlot, sX2, 1.0, 0.0, 0.0, -1, kfull));
   wrote(sX2);
+  BCK(gemm(sX2, sX, kNoSlot, sX3, 1.0, 0.0, 0.0, -1, kfull));
+  wrote(sX3);
   BCK(gemm(sX2, sX2, kNoSlot, sX4, 1.0, 0.0, 0.0, -1, kfull));
   wrote(sX4);
-  BCK(comb(sSp, {sX4, sX2}, {pb[5], pb[3]}, pb[1], 0, -1));
-  BCK(comb(sVp, {sX4, sX2}, {pb[4], pb[2]}, pb[0], 0, -1));
-  wrote(sSp);
-  wrote(sVp);
-  BCK(gemm(sX, sSp, sVp, sR, 1.0, -1.0, 1.0, -1, kfull));  // R = I - (Vp - Up), Up = X Sp
-  wrote(sR);
-  BCK(gemm(sR, sSp, sSp, sF, 2.0, 2.0, 0.0, -1, moduli_for(kRBound)));  // F = (I + R) 2 Sp
+  BCK(comb(sF, {sX, sX2, sX3, sX4}, {ck[13], ck[14], ck[15], ck[16]}, ck[12], 0, -1));  // B_3 + c_16 X^4
   wrote(sF);
-  int F = sF, Fb = sFb, R = sR, R2 = sR2;
-  for (int j = 1; j < kSolveFactors; ++j) {
-    const int nm = moduli_for(std::pow(kRBound, (double)(1 << j)));
-    BCK(gemm(R, R, kNoSlot, R2, 1.0, 0.0, 0.0, -1, nm));  // R^(2^j)
-    wrote(R2);
-    std::swap(R, R2);
-    BCK(gemm(R, F, F, Fb, 1.0, 1.0, 0.0, -1, nm));  // F <- F + R^(2^j) F
+  int F = sF, Fb = sFb;
+  for (int j = 2; j >= 0; --j) {
+    BCK(comb(sSp, {sX, sX2, sX3}, {ck[4 * j + 1], ck[4 * j + 2], ck[4 * j + 3]}, 0.0, 0, -1));
+    wrote(sSp);
+    const int nm = j == 2 ? horner_nmod[0] : (j == 1 ? horner_nmod[1] : kfull);  // X^4 factors still to come
+    BCK(gemm(sX4, F, sSp, Fb, 1.0, 1.0, ck[4 * j], -1, nm));  // F <- B_j + X^4 F
     wrote(Fb);
     std::swap(F, Fb);
   }
@@ -607,20 +620,51 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
     rfd_plan_s* pl = b->plans[k];
     const int s = b->h_sv[k];
     pl->stats.norm1 = b->h_norms[k];
-    pl->stats.pade_degree = 5;
+    pl->stats.pade_degree = kTaylorDegree;  // the Taylor degree on this path
     pl->stats.squarings = s;
     pl->stats.phi1_emulated = 1;
-    pl->stats.phi1_gemms = 3 + 2 * kSolveFactors - 1 + (s > 0 ? 2 * s : 0);
+    pl->stats.phi1_gemms = 6 + 2 * s;
   }
-  const int key_post[4] = {mode, max_s, with_apply ? cg : 0, with_apply ? apply_blocks : 0};
+  int hn[2];
+  horner_moduli(b, hn);
+  const int key_post[4] = {mode, max_s + 256 * (hn[0] * 32 + hn[1]), with_apply ? cg : 0,
+                           with_apply ? apply_blocks : 0};
   r = run_segment(b, key_post, graph, tm, [&](cudaStream_t s, Timing* t) -> rfd_status {
     {
       StepScope sc(t, s, RFD_STEP_PHI1);
-      rfd_status q = phi1_core(b, s, max_s);
+      rfd_status q = phi1_core(b, s, max_s, hn);
       if (q != RFD_OK) return q;
     }
     return with_apply ? small_apply(s, t) : RFD_OK;
   });
+  if (r != RFD_OK) return r;
+  for (rfd_plan_s* pl : b->plans) pl->have_G = true;
+  return RFD_OK;
+}
+
+// Step a4 alone on the plans' resident M (the batched, emulated path): what
+// batch_run does between the reductions and step a5, without CUDA graphs.
+rfd_status batch_phi1_only(BatchImpl* b) {
+  if (!b->phi_batched) return fail(RFD_EINVAL, "the batched step a4 is not in use for this batch");
+  cudaStream_t st = b->st;
+  const int n = b->count;
+  for (rfd_plan_s* pl : b->plans) pl->have_G = false;
+  rfd_status r = phi1_select(b, st);
+  if (r != RFD_OK) return r;
+  BCK(cudaEventRecord(b->ev_mid, st));
+  BCK(cudaEventSynchronize(b->ev_mid));
+  const int max_s = std::min(std::max(b->h_sv[n], 0), kMaxSquarings);
+  for (int k = 0; k < n; ++k) {
+    rfd_plan_s* pl = b->plans[k];
+    pl->stats.norm1 = b->h_norms[k];
+    pl->stats.pade_degree = kTaylorDegree;
+    pl->stats.squarings = b->h_sv[k];
+    pl->stats.phi1_emulated = 1;
+    pl->stats.phi1_gemms = 6 + 2 * b->h_sv[k];
+  }
+  int hn[2];
+  horner_moduli(b, hn);
+  r = phi1_core(b, st, max_s, hn);
   if (r != RFD_OK) return r;
   for (rfd_plan_s* pl : b->plans) pl->have_G = true;
   return RFD_OK;

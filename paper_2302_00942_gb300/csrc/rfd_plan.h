@@ -170,6 +170,8 @@ size_t batch_device_bytes(BatchImpl* b);
 // mode needs).  Updates each plan's stats and have_G.  Non-finite G and
 // device-side timeouts are reported by batch_check_error.
 rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* timing);
+// Step a4 alone (the batched emulated path) on the plans' resident M; synchronises.
+rfd_status batch_phi1_only(BatchImpl* b);
 cudaStream_t batch_stream(BatchImpl* b);
 // Kernel eigenvalues (rfd_eigen.cu): argument checks, and the k smallest /
 // largest eigenvalues of every plan's exp(lambda W_hat) from its resident M

@@ -249,3 +249,33 @@ def test_invalid_arguments_and_alloc_failure():
     p = rfd.Plan(spec.n, spec.m, spec.eps, lam, spec.seed, max_channels=3)
     p.close()
     assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
+
+
+@pytest.mark.parametrize("m,norm,lam", [(64, 0.5, 1.0), (256, 0.97, 1.0), (256, 3.0, -1.0), (1024, 0.5, 1.0),
+                                        (130, 40.0, 1.0), (96, 1e-6, 1.0)])
+def test_batched_phi1_matches_oracle(m, norm, lam):
+    """Step a4 as rfd_features runs it for BF16 plans (the batched, emulated path:
+    Taylor degree 16 in Paterson-Stockmeyer form, scaling and squaring above
+    ||X||_1 = 0.977), on a given M, against the oracle's expm-based phi1: FP64
+    accuracy, ~s u ||X|| after s squarings."""
+    rng = np.random.default_rng(m * 7 + int(norm * 100))
+    M = rng.standard_normal((m, m))
+    M *= norm / (abs(lam) * np.abs(M).sum(0).max())
+    plan = rfd.Plan(64, m, 0.1, lam, 1, precision=rfd.RFD_BF16_TC, stream=torch.cuda.current_stream(DEV))
+    try:
+        _check(rfd.lib.rfd_debug_plan_phi1(plan.handle, _cuda(M).data_ptr()), "rfd_debug_plan_phi1")
+        st = plan.stats()
+        _, _, G = plan.export()
+    finally:
+        plan.close()
+    ref = lam * oracle.phi1(lam * M)
+    err = oracle.rel_frobenius(G, ref)
+    print(m, norm, st["squarings"], st["phi1_gemms"], err)
+    assert abs(st["norm1"] - norm) <= 1e-9 * norm
+    assert st["pade_degree"] == 16 and st["phi1_gemms"] == 6 + 2 * st["squarings"]
+    assert err <= 1e-13 * max(1.0, norm)
+
+
+def _check(status, where):
+    if status != 0:
+        raise RuntimeError(f"{where}: {rfd.rfd_last_error()}")
