@@ -138,7 +138,8 @@ enum {
  * the plan launched since then.  rfd_plan_stats synchronises the stream. */
 typedef struct {
   double norm1;          /* ||lambda M||_1                                         */
-  int32_t pade_degree;   /* diagonal Pade degree q used for exp of the augmented matrix */
+  int32_t pade_degree;   /* degree of the approximant of step a4: Taylor degree (16) on the
+                            batched emulated path, diagonal Pade degree q on the native path */
   int32_t squarings;     /* scaling-and-squaring steps s                          */
   int32_t nonfinite;     /* 1 if G was not finite                                 */
   int32_t splits;        /* split-K pieces per tile (mean) of the reductions over N */
