@@ -158,25 +158,44 @@ __global__ void reduce_batched_kernel(const RedTile* __restrict__ tiles, const C
   }
 }
 
-// Z[f, ch] = oa[f] sum_g G[f, g] Y[g, ch]: block (32 channels x 8 g-slices) per row.
-__global__ void small_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
-                                     const CloudCall* __restrict__ calls) {
+// Z[f, ch] = oa[f] sum_g G[f, g] Y[g, ch]: a block of 256 threads per row f,
+// the threads over g, channels in groups of 8.  Products and the sums within
+// a thread and a warp in FP32 (this GPU's FP64 pipe is slow; Z is stored in
+// FP32 and enters out = F + Phi Z, an increment on F), the 8 warp sums in FP64.
+__global__ void __launch_bounds__(256) small_batched_kernel(const ApplyJob* __restrict__ jobs,
+                                                            const int* __restrict__ prefix, int count,
+                                                            const CloudCall* __restrict__ calls) {
+  constexpr int kCC = 8;
   const int j = find_job(prefix, count, blockIdx.x);
   const ApplyJob jb = jobs[j];
   const int f = blockIdx.x - prefix[j];
   const int c = calls[jb.cloud].c, m = jb.m;
-  __shared__ double red[8][32];
-  for (int ch0 = 0; ch0 < c; ch0 += 32) {
-    const int ch = ch0 + threadIdx.x;
-    double acc = 0.0;
-    if (ch < c)
-      for (int g = threadIdx.y; g < m; g += 8) acc = fma(jb.G[(size_t)f * m + g], jb.Y[(size_t)g * c + ch], acc);
-    red[threadIdx.y][threadIdx.x] = acc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ float red[8][kCC];
+  const double* grow = jb.G + (size_t)f * m;
+  for (int ch0 = 0; ch0 < c; ch0 += kCC) {
+    const int nc = min(kCC, c - ch0);
+    float acc[kCC];
+#pragma unroll
+    for (int q = 0; q < kCC; ++q) acc[q] = 0.f;
+    for (int g = threadIdx.x; g < m; g += 256) {
+      const float gv = (float)grow[g];
+      const double* yrow = jb.Y + (size_t)g * c + ch0;
+#pragma unroll
+      for (int q = 0; q < kCC; ++q)
+        if (q < nc) acc[q] = fmaf(gv, (float)yrow[q], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kCC; ++q) {
+      float v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][q] = v;
+    }
     __syncthreads();
-    if (threadIdx.y == 0 && ch < c) {
-      double s = 0.0;
-      for (int y = 0; y < 8; ++y) s += red[y][threadIdx.x];
-      jb.Z[(size_t)f * c + ch] = (float)(jb.oa[f] * s);
+    if (threadIdx.x < nc) {
+      double sum = 0.0;
+      for (int w = 0; w < 8; ++w) sum += (double)red[w][threadIdx.x];
+      jb.Z[(size_t)f * c + ch0 + threadIdx.x] = (float)(jb.oa[f] * sum);
     }
     __syncthreads();
   }
@@ -384,7 +403,7 @@ cudaError_t launch_reduce_batched(const RedTile* tiles, int num_tiles, const Clo
 cudaError_t launch_small_batched(const ApplyJob* jobs, const int* prefix, int count, int total_rows,
                                  const CloudCall* calls, cudaStream_t st) {
   if (total_rows <= 0) return cudaSuccess;
-  small_batched_kernel<<<total_rows, dim3(32, 8), 0, st>>>(jobs, prefix, count, calls);
+  small_batched_kernel<<<total_rows, 256, 0, st>>>(jobs, prefix, count, calls);
   return launched();
 }
 
