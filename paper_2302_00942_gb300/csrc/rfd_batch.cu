@@ -35,7 +35,7 @@ constexpr double kThetaT16 = 0.977;
 constexpr int kTaylorDegree = 16;
 constexpr int kMaxSquarings = 60;                 // beyond this exp(lambda M) overflows anyway
 // matrix slots of the phi1 evaluation (see kernels.h: slot k = work + k m^2)
-enum : int { sX = 0, sX2, sX4, sSp, sVp, sUp, sR, sR2, sF, sFb, sE, sT1, sT2 };
+enum : int { sX = 0, sX2, sX3, sX4, sB, sF, sFb, sE, sT1 };
 
 std::vector<int> prefix_of(const std::vector<int>& counts) {
   std::vector<int> p(counts.size() + 1, 0);
@@ -432,7 +432,6 @@ rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s, const int horner_
   double ck[kTaylorDegree + 1];  // c_k = 1 / (k + 1)!
   ck[0] = 1.0;
   for (int k = 1; k <= kTaylorDegree; ++k) ck[k] = ck[k - 1] / (double)(k + 1);
-  const int sX3 = sR;
   if (max_s > 0) BCK(comb(sX, {sX}, {1.0}, 0.0, 2, -1));  // X = 2^-s X
   BCK(gemm(sX, sX, kNoSlot, sX2, 1.0, 0.0, 0.0, -1, kfull));
   wrote(sX2);
@@ -444,10 +443,10 @@ rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s, const int horner_
   wrote(sF);
   int F = sF, Fb = sFb;
   for (int j = 2; j >= 0; --j) {
-    BCK(comb(sSp, {sX, sX2, sX3}, {ck[4 * j + 1], ck[4 * j + 2], ck[4 * j + 3]}, 0.0, 0, -1));
-    wrote(sSp);
+    BCK(comb(sB, {sX, sX2, sX3}, {ck[4 * j + 1], ck[4 * j + 2], ck[4 * j + 3]}, 0.0, 0, -1));  // B_j - c_4j I
+    wrote(sB);
     const int nm = j == 2 ? horner_nmod[0] : (j == 1 ? horner_nmod[1] : kfull);  // X^4 factors still to come
-    BCK(gemm(sX4, F, sSp, Fb, 1.0, 1.0, ck[4 * j], -1, nm));  // F <- B_j + X^4 F
+    BCK(gemm(sX4, F, sB, Fb, 1.0, 1.0, ck[4 * j], -1, nm));  // F <- B_j + X^4 F
     wrote(Fb);
     std::swap(F, Fb);
   }
