@@ -212,6 +212,16 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def arm_config(args, spec, n, m, c, lam, ws):
+    """The `config` object of the JSON line, the same for both arms."""
+    fbytes = 2 if args.precision == "bf16" else 4
+    return {"workload": f"{args.workload}: N={n} points ({spec.kind}), eps={spec.eps}, m={m}, c={c}, "
+                        f"lambda={spec.lam} x m/N = {lam:.4g}, seed={spec.seed}",
+            "l2": "inputs > L2: the step rewrites and rereads the feature matrix "
+                  f"({(m + 16) * n * fbytes / 1e9:.2f} GB)",
+            "parallelism": f"replicas x{ws}"}
+
+
 def reference_arm(args, spec, pts, F, lam):
     ns = min(args.cpu_sample, spec.n)
     c = F.shape[1]
@@ -225,7 +235,7 @@ def reference_arm(args, spec, pts, F, lam):
     return {"impl": "reference", "metric": METRIC, "value": val, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: N={ns} (sample of {spec.n}) m={spec.m} c={c}"},
+            "config": arm_config(args, spec, spec.n, spec.m, c, lam, args.gpus),
             "cpu_baseline": cb, "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -762,11 +772,7 @@ def main():
         "metric": METRIC, "value": whole_job_value(ws, n * c, ms_max), "unit": "points*ch/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": f"{args.workload}: N={n} points ({spec.kind}), eps={spec.eps}, m={m}, c={c}, "
-                               f"lambda={spec.lam} x m/N = {lam:.4g}, seed={spec.seed}",
-                   "l2": "inputs > L2: the step rewrites and rereads the feature matrix "
-                         f"({(m + 16) * n * (2 if prec else 4) / 1e9:.2f} GB)",
-                   "parallelism": f"replicas x{ws}"},
+        "config": arm_config(args, spec, n, m, c, lam, ws),
         "roofline": roof,
         "path_roofline": {"t_roofline_ms": t_roof * 1e3, "frac_of_step": t_roof * 1e3 / ms_max,
                           "bound": "tensor" if wm["gram_flops"] / peaks["bf16_tflops_sustained"] / 1e12 >
