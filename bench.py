@@ -172,7 +172,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work per step ("Roofline")
+# algorithmic work per step: tensor flops of the Gram and Phi^T F, HBM bytes of points, F and out
 # ---------------------------------------------------------------------------
 def work_model(n, m, c):
     gram_flops = n * m * (m + 1) + 2 * n * m * c          # symmetric Phi^T Phi + Phi^T F

@@ -1,5 +1,5 @@
 // Host-side helpers shared by the tcgen05 kernels: tensor-map encoding through
-// the driver entry point (no link-time dependency on libcuda) and the device check.
+// the CUDA driver API entry point (no link-time dependency on libcuda) and the device check.
 #include "tc_common.cuh"
 
 namespace rfd {
