@@ -152,3 +152,14 @@ def test_estimator_separates_l1_ball_from_l2_ball():
     out = [0.6 * EPS, 0.6 * EPS, 0.0]
     assert mean_w(out, "l1_ball") < 0.3 and mean_w(out, "ball") > 0.7
     assert mean_w([0.3 * EPS, 0.3 * EPS, 0.0], "l1_ball") > 0.7
+
+
+def test_host_l1_ball_weights_in_a_wide_band():
+    """The host evaluates the octahedron's divided differences by their power
+    series; with the frequency radius at 3/eps the nodes reach 6 pi, where the
+    series cancels most: still within 1e-9 of the largest weight."""
+    rfd = pytest.importorskip("paper_2302_00942_gb300")
+    sigma, R = 1.0 / EPS, 3.0 / EPS
+    om, r = rfd.rfd_sample_weights(512, EPS, 9, sigma, R, kernel="l1_ball")
+    ref = oracle.weights(oracle.sample_frequencies(512, EPS, 9, sigma, R), EPS, sigma, R, "l1_ball")
+    np.testing.assert_allclose(r, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
