@@ -97,8 +97,8 @@ typedef struct {
  *   RFD_KERNEL_L1_BALL: f = 1[||z||_1 <= eps] (the L1 ball of Sec. 2.4, an octahedron; its transform
  *                    does not factor over coordinates): the sum over the 8 simplices
  *                    conv(0, +-eps e_1, +-eps e_2, +-eps e_3) of eps^3 times the divided difference
- *                    of exp at 0, -2 pi i eps s_d w_d (d = 1..3), evaluated as its power series
- *                    (value 4 eps^3 / 3, the volume, at w = 0). */
+ *                    of exp at 0, -2 pi i eps s_d w_d (d = 1..3), the corner entry of exp of the
+ *                    bidiagonal matrix of those nodes (value 4 eps^3 / 3, the volume, at w = 0). */
 typedef enum { RFD_KERNEL_CUBE = 0, RFD_KERNEL_BALL = 1, RFD_KERNEL_CUBE_L1 = 2, RFD_KERNEL_L1_BALL = 3 } rfd_kernel;
 
 typedef struct rfd_plan_s* rfd_plan_t;

@@ -90,30 +90,60 @@ double tau_ball(const double (&w)[3], double eps) {
 // conv(0, s_1 eps e_1, s_2 eps e_2, s_3 eps e_3), s in {-1, 1}^3.  Over a simplex
 // conv(0, v_1, v_2, v_3), the integral of exp(u . z) is 3! vol times the
 // divided difference of exp at the nodes 0, u . v_1, u . v_2, u . v_3 (the
-// exponential-simplex integral); with a node at 0 that divided difference is
-// sum_k h_k(y_1, y_2, y_3) / (k + 3)!, h_k the complete homogeneous symmetric
-// polynomial of degree k, by the recurrence h_k(y_1..y_j) = h_k(y_1..y_{j-1}) +
-// y_j h_{k-1}(y_1..y_j).  Here u = -2 pi i w (the transform's 2 pi convention),
-// each simplex has volume eps^3 / 6, and the 8 terms sum to a real number.
-double tau_l1_ball(const double (&w)[3], double eps) {
-  double total = 0.0, ymax = 0.0;
-  for (int d = 0; d < 3; ++d) ymax = std::max(ymax, 2.0 * kPi * eps * std::fabs(w[d]));
-  for (int s = 0; s < 8; ++s) {
-    std::complex<double> y[3];
-    for (int d = 0; d < 3; ++d) y[d] = std::complex<double>(0.0, ((s >> d) & 1 ? 2.0 : -2.0) * kPi * eps * w[d]);
-    std::complex<double> h1 = 1.0, h2 = 1.0, h3 = 1.0;  // degree 0
-    double fact = 6.0;                                  // (k + 3)!
-    std::complex<double> sum = h3 / fact;
-    for (int k = 1; k < 400; ++k) {
-      h1 = y[0] * h1;
-      h2 = h1 + y[1] * h2;
-      h3 = h2 + y[2] * h3;
-      fact *= (double)(k + 3);
-      const std::complex<double> term = h3 / fact;
-      sum += term;
-      if (k > 2.0 * ymax + 8.0 && std::abs(term) < 1e-18 * (std::abs(sum) + 1e-300)) break;
+// exponential-simplex integral); here u = -2 pi i w (the transform's 2 pi
+// convention) and each simplex has volume eps^3 / 6, and the 8 terms sum to a
+// real number.  The divided difference of exp at y_0..y_3 is the top-right
+// entry of exp(J), J the upper bidiagonal matrix with y on the diagonal and
+// ones above it (Opitz 1964); exp(J) by scaling and squaring of its Taylor
+// polynomial (degree 18 at norm <= 1), which stays accurate where the power
+// series of the divided difference cancels (nodes of modulus up to tens).
+using cplx = std::complex<double>;
+struct Tri4 {
+  cplx a[4][4];  // upper triangular
+};
+Tri4 mul(const Tri4& x, const Tri4& y) {
+  Tri4 z{};
+  for (int i = 0; i < 4; ++i)
+    for (int j = i; j < 4; ++j) {
+      cplx t = 0.0;
+      for (int k = i; k <= j; ++k) t += x.a[i][k] * y.a[k][j];
+      z.a[i][j] = t;
     }
-    total += sum.real();
+  return z;
+}
+cplx divided_difference_exp(const cplx (&y)[4]) {
+  double nrm = 1.0;  // the superdiagonal
+  for (int i = 0; i < 4; ++i) nrm = std::max(nrm, std::abs(y[i]) + 1.0);
+  int s = 0;
+  while (nrm > 1.0) {
+    nrm *= 0.5;
+    ++s;
+  }
+  const double scale = std::ldexp(1.0, -s);
+  Tri4 A{};
+  for (int i = 0; i < 4; ++i) {
+    A.a[i][i] = y[i] * scale;
+    if (i < 3) A.a[i][i + 1] = scale;
+  }
+  Tri4 E{}, P{};
+  for (int i = 0; i < 4; ++i) E.a[i][i] = P.a[i][i] = 1.0;
+  for (int k = 1; k <= 18; ++k) {  // E = sum_k A^k / k!
+    P = mul(P, A);
+    for (int i = 0; i < 4; ++i)
+      for (int j = i; j < 4; ++j) P.a[i][j] /= (double)k;
+    for (int i = 0; i < 4; ++i)
+      for (int j = i; j < 4; ++j) E.a[i][j] += P.a[i][j];
+  }
+  for (int k = 0; k < s; ++k) E = mul(E, E);
+  return E.a[0][3];
+}
+double tau_l1_ball(const double (&w)[3], double eps) {
+  double total = 0.0;
+  for (int s = 0; s < 8; ++s) {
+    cplx y[4];
+    y[0] = 0.0;
+    for (int d = 0; d < 3; ++d) y[d + 1] = cplx(0.0, ((s >> d) & 1 ? 2.0 : -2.0) * kPi * eps * w[d]);
+    total += divided_difference_exp(y).real();
   }
   return eps * eps * eps * total;
 }

@@ -155,11 +155,12 @@ def test_estimator_separates_l1_ball_from_l2_ball():
 
 
 def test_host_l1_ball_weights_in_a_wide_band():
-    """The host evaluates the octahedron's divided differences by their power
-    series; with the frequency radius at 3/eps the nodes reach 6 pi, where the
-    series cancels most: still within 1e-9 of the largest weight."""
+    """The host evaluates the octahedron's divided differences by scaling and
+    squaring exp of the bidiagonal node matrix (a power series would cancel at
+    nodes of modulus ~6 pi, the frequency radius 3/eps): within 1e-13 of the
+    largest weight."""
     rfd = pytest.importorskip("paper_2302_00942_gb300")
     sigma, R = 1.0 / EPS, 3.0 / EPS
     om, r = rfd.rfd_sample_weights(512, EPS, 9, sigma, R, kernel="l1_ball")
     ref = oracle.weights(oracle.sample_frequencies(512, EPS, 9, sigma, R), EPS, sigma, R, "l1_ball")
-    np.testing.assert_allclose(r, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+    np.testing.assert_allclose(r, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
