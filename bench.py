@@ -205,6 +205,54 @@ def time_oracle(pts, F, eps, lam, m, seed, steps=1):
     return (time.perf_counter() - t0) / steps
 
 
+def time_oracle_stages(pts, F, eps, lam, m, seed):
+    """The oracle's steps timed one by one (ms), as the GPU's step breakdown is."""
+    import oracle
+    F64 = np.asarray(F, dtype=np.float64)
+    t = {}
+    t0 = time.perf_counter()
+    omega = oracle.sample_frequencies(m, eps, seed)
+    r = oracle.weights(omega, eps)
+    t["a1 frequencies and weights"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    A, B = oracle.factors(pts, omega, r)
+    t["a2 features"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    M = B.T @ A
+    Y = B.T @ F64
+    t["a3 reductions"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    G = lam * oracle.phi1(lam * M)
+    t["a4 phi1"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _ = F64 + A @ (G @ Y)
+    t["a5-a6 apply"] = time.perf_counter() - t0
+    return {k: round(v * 1e3, 3) for k, v in t.items()}
+
+
+def time_oracle_single_thread():
+    """The oracle on the small workload (N = 2048, m = 64, c = 3) with one BLAS /
+    OpenMP thread, in a child process (the thread count is fixed at import)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, time, oracle, synth\n"
+            "s = synth.config_single('small')\n"
+            "pts, F = synth.make_cloud(s)\n"
+            "lam = s.lam * s.m / s.n\n"
+            "oracle.rfd_gfi(pts, F, s.eps, lam, s.m, s.seed)\n"
+            "t0 = time.perf_counter()\n"
+            "for _ in range(5): oracle.rfd_gfi(pts, F, s.eps, lam, s.m, s.seed)\n"
+            "t = (time.perf_counter() - t0) / 5\n"
+            "print(json.dumps({'ms': t * 1e3, 'value': s.n * s.c / t}))\n")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, cwd=os.path.dirname(os.path.abspath(__file__)),
+                             capture_output=True, text=True, timeout=300)
+        d = json.loads(out.stdout.strip().splitlines()[-1])
+        return {"workload": "small: N=2048 (sphere), eps=0.1, m=64, c=3", "cores": 1, "ms_per_step": d["ms"],
+                "value": d["value"], "unit": "points*ch/s"}
+    except Exception as e:  # a missing measurement is reported, not fatal
+        return {"unavailable": str(e)[:200]}
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -809,7 +857,9 @@ def main():
         ns = min(args.cpu_sample, n)
         t = time_oracle(pts[:ns], F[:ns], spec.eps, lam, m, spec.seed)
         res["cpu_baseline"] = {"value": ns * c / t, "unit": "points*ch/s", "cores": cpu_cores(), "kind": "oracle",
-                               "sample": f"first {ns} of {n} points, same m, c, eps, lambda; whole path, FP64"}
+                               "sample": f"first {ns} of {n} points, same m, c, eps, lambda; whole path, FP64",
+                               "stages_ms": time_oracle_stages(pts[:ns], F[:ns], spec.eps, lam, m, spec.seed),
+                               "single_thread": time_oracle_single_thread()}
     if rank == 0:
         print(json.dumps(res))
     D.close()
