@@ -98,6 +98,26 @@ def test_null_handles_rejected():
     assert rfd.lib.rfd_debug_dgemm(1, 0, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, None) == rfd.RFD_EINVAL
 
 
+def test_null_handles_rejected_by_the_next_rows():
+    """The barycenter, GW, eigenvalue and debug entry points check their handles
+    and pointers before any device work (no GPU needed)."""
+    import ctypes
+    out3 = (ctypes.c_double * 3)()
+    alpha = (ctypes.c_double * 1)(1.0)
+    calls = {
+        "rfd_barycenter": lambda: rfd.lib.rfd_barycenter(None, None, 1, 1, alpha, None, 1, None),
+        "rfd_fm_apply": lambda: rfd.lib.rfd_fm_apply(None, None, 1, 1, None, 1),
+        "rfd_gw_tensor_product": lambda: rfd.lib.rfd_gw_tensor_product(None, None, None, None, None, None),
+        "rfd_gw_line_search": lambda: rfd.lib.rfd_gw_line_search(None, None, 0.5, None, None, None, None, None, out3),
+        "rfd_eigenvalues": lambda: rfd.lib.rfd_eigenvalues(None, 4, 0, None),
+        "rfd_batch_eigenvalues": lambda: rfd.lib.rfd_batch_eigenvalues(None, None, 4, 0, None),
+        "rfd_debug_plan_phi1": lambda: rfd.lib.rfd_debug_plan_phi1(None, None),
+    }
+    for name, call in calls.items():
+        assert call() == rfd.RFD_EINVAL, name
+        assert rfd.rfd_last_error(), name
+
+
 def test_phi1_gemm_count_matches_bench_model():
     import bench
     for q, s, m in [(3, 0, 8), (7, 0, 64), (9, 0, 10), (13, 0, 100), (13, 4, 32)]:
