@@ -232,15 +232,22 @@ RFD_API rfd_status rfd_barycenter(rfd_plan_t plan, const float* d_mu, int32_t k,
  *     rfd_integrate over column chunks of at most max_channels; asynchronous.
  *   rfd_gw_tensor_product: Algorithm tensor_prod with the square loss,
  *     d_L (n1 x n2) = (C^{(.)2} p) 1^T + 1 (D^{(.)2} q)^T - 2 C T D^T, with
- *     C^{(.)2} p = diag(C D_p C^T) from two actions of C (Eq. sq); d_T n1 x n2,
- *     d_p (n1), d_q (n2); asynchronous (temporaries of 2 max(n1,n2)^2 + 3 n1 n2
- *     floats from the stream-ordered allocator).
+ *     C^{(.)2} p = diag(C D_p C^T) (Eq. sq); d_T n1 x n2, d_p (n1), d_q (n2);
+ *     asynchronous.  When both clouds have m <= 32 the sums are taken through
+ *     the low-rank factors (C = I + Psi K Psi^T: the Hadamard squares in
+ *     O(N m^2), one pass over T for its two projections, one for L;
+ *     temporaries O((n1 + n2) m) plus 16 n2 m + n1 n2 m / 64 floats); otherwise
+ *     as four actions on n x n matrices (temporaries of 2 max(n1, n2)^2 +
+ *     3 n1 n2 floats).  Temporaries come from the stream-ordered allocator
+ *     (RFD_ENOMEM if it fails).
  *   rfd_gw_line_search: Algorithm line_search, the optimal step of a
  *     conditional-gradient (F)GW iteration for the transport G, direction dG,
  *     feature cost M (all n1 x n2) and trade-off alpha: with c_CD = steps 1-2 of
  *     tensor_prod, a1 = C dG D, b1 = C G D, a = -2 alpha <a1, dG>,
  *     b = <(1 - alpha) M + alpha c_CD, dG> - 2 alpha (<a1, G> + <b1, dG>);
  *     tau = clamp(-b / 2a, 0, 1) if a > 0, else 1 if a + b < 0, else 0.
+ *     The inner products are accumulated in FP64 (the low-rank form for
+ *     m <= 32 as in rfd_gw_tensor_product, reading G, dG and M once more).
  *     out3 (host, 3 doubles) = {tau, a, b}; waits for the stream. */
 RFD_API rfd_status rfd_fm_apply(rfd_plan_t plan, const float* d_X, int64_t ncols, int64_t ldX, float* d_Y,
                                 int64_t ldY);
