@@ -236,7 +236,8 @@ RFD_API rfd_status rfd_barycenter(rfd_plan_t plan, const float* d_mu, int32_t k,
  *     asynchronous.  When both clouds have m <= 32 the sums are taken through
  *     the low-rank factors (C = I + Psi K Psi^T: the Hadamard squares in
  *     O(N m^2), one pass over T for its two projections, one for L;
- *     temporaries O((n1 + n2) m) plus 16 n2 m + n1 n2 m / 64 floats); otherwise
+ *     temporaries O((n1 + n2) mf) plus 16 n2 mf + n1 n2 mf / 256 floats, mf = 16
+ *     or 32 the padded m); otherwise
  *     as four actions on n x n matrices (temporaries of 2 max(n1, n2)^2 +
  *     3 n1 n2 floats).  Temporaries come from the stream-ordered allocator
  *     (RFD_ENOMEM if it fails).
