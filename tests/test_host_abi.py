@@ -124,3 +124,15 @@ def test_phi1_gemm_count_matches_bench_model():
         gem = {3: 1, 5: 2, 7: 3, 9: 4, 13: 5}[q] + 1 + (2 * s - 1 if s else 0)
         nrhs = 2 * m if s else m
         assert bench.phi1_flops(m, q, s) == pytest.approx(gem * 2 * m ** 3 + 2 / 3 * m ** 3 + 2 * m * m * nrhs)
+
+
+def test_bench_work_model_at_the_headline():
+    """The algorithmic work the roofline is computed from, at N = 1e6, m = 1024,
+    c = 3: T = N m (m + 1) + 4 N m c flops (symmetric Gram, Phi^T F, Phi Z) and
+    12 N (1 + c) HBM bytes (points, F read twice, out)."""
+    import bench
+    w = bench.work_model(1_000_000, 1024, 3)
+    assert w["gram_flops"] + w["apply_flops"] == 1_000_000 * 1024 * 1025 + 4 * 1_000_000 * 1024 * 3
+    assert abs((w["gram_flops"] + w["apply_flops"]) - 1.062e12) < 0.001e12
+    assert w["hbm_bytes"] == 48_000_000
+    assert w["sincos"] == 1_024_000_000
