@@ -37,6 +37,25 @@ RFD_API rfd_status rfd_debug_dgemm(int32_t method, int32_t M, int32_t N, int32_t
  * path, RFD_ENUMERIC if G is not finite. */
 RFD_API rfd_status rfd_debug_plan_phi1(rfd_plan_t plan, const double* d_M);
 
+/* Set the point-axis phase length of a BF16 plan's tensor-core reductions:
+ * the reductions run as one launch per phase of phase_blocks 64-point blocks,
+ * each later phase adding to the split-K lanes' partials (step a3).  A short
+ * phase makes a modest cloud take the multi-phase accumulation that the large
+ * workload takes.  Plans without RFD_FLAG_GRAPH and RFD_FLAG_AUTOTUNE only
+ * (RFD_EINVAL otherwise, for FP32 plans, or for phase_blocks < 1).  Host only. */
+RFD_API rfd_status rfd_debug_plan_set_phase(rfd_plan_t plan, int32_t phase_blocks);
+
+/* The bounded device-side wait on its own.  Every wait of the library's
+ * kernels on an mbarrier gives up after a %globaltimer limit, records a code
+ * in a device error word, frees its TMEM and returns, and the host reports
+ * RFD_ETIMEDOUT instead of hanging.  This hook launches, on the plan's stream,
+ * one CTA that allocates TMEM and waits on an mbarrier that nothing ever
+ * arrives on, with a limit of limit_us microseconds (1 .. 10^6), recording
+ * into the plan's own error word: the next rfd_sync(plan) returns
+ * RFD_ETIMEDOUT (and clears the word), and the plan stays usable.  No copy is
+ * issued and nothing faults.  Asynchronous; RFD_ENOTSUP off sm_103. */
+RFD_API rfd_status rfd_debug_plan_wait_timeout(rfd_plan_t plan, int32_t limit_us);
+
 /* Hold (paused = 1) or release (0) a server's executors: while held they
  * start no new batch (batches already running finish), so a test can make a
  * poll wait run out deterministically. */

@@ -134,6 +134,8 @@ def _load():
         "rfd_debug_fail_alloc_after": (None, [I32]),
         "rfd_debug_dgemm": (I32, [I32, I32, I32, I32, D, P, I32, P, I32, D, P, I32, P]),
         "rfd_debug_plan_phi1": (I32, [P, P]),
+        "rfd_debug_plan_set_phase": (I32, [P, I32]),
+        "rfd_debug_plan_wait_timeout": (I32, [P, I32]),
         "rfd_batch_create": (I32, [ctypes.POINTER(P), I32, I32, P, ctypes.POINTER(P)]),
         "rfd_batch_destroy": (I32, [P]),
         "rfd_batch_features": (I32, [P, ctypes.POINTER(rfd_batch_item)]),
@@ -162,7 +164,8 @@ lib = _load()
 HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_sample_weights", "rfd_barycenter", "rfd_fm_apply",
                   "rfd_gw_tensor_product", "rfd_gw_line_search", "rfd_eigenvalues", "rfd_batch_eigenvalues", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
                   "rfd_gfi", "rfd_phi1", "rfd_phi1_noalloc", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
-                  "rfd_version", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "rfd_debug_plan_phi1", "rfd_batch_create",
+                  "rfd_version", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "rfd_debug_plan_phi1", "rfd_debug_plan_set_phase",
+                  "rfd_debug_plan_wait_timeout", "rfd_batch_create",
                   "rfd_batch_destroy", "rfd_batch_features", "rfd_batch_integrate", "rfd_batch_gfi",
                   "rfd_batch_sync", "rfd_batch_stats", "rfd_batch_stats_reset", "rfd_server_create",
                   "rfd_server_destroy", "rfd_submit", "rfd_poll", "rfd_server_stats_get", "rfd_debug_server_pause")

@@ -131,37 +131,40 @@ fill_batched_kernel(const FillJob* __restrict__ jobs, const int* __restrict__ pr
   for (int row = jb.fsplit ? 2 * c : c; row < jb.cpad; ++row) psi[psi_index(p, r0 + row, ra)] = zero;
 }
 
-// One thread per tile element; lanes summed in order (deterministic) in FP64.
+// One thread per tile element; lanes summed in order (deterministic),
+// compensated FP32; column scales applied in FP32, results stored in FP64
+// (step a4's input).
 __global__ void reduce_batched_kernel(const RedTile* __restrict__ tiles, const CloudCall* __restrict__ calls) {
   const RedTile t = tiles[blockIdx.y];
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = e / kTcBNMax, col = e % kTcBNMax;
   if (r >= t.ni || col >= t.nj) return;
   const float* p = t.part + (int64_t)r * t.ld + t.col_off + col;
-  double s = 0.0;
-  for (int u = 0; u < t.count; ++u) s += (double)p[(int64_t)u * t.slot_elems];
+  Fp32Sum acc;
+  for (int u = 0; u < t.count; ++u) acc.add(p[(int64_t)u * t.slot_elems]);
   const int f = t.i0 + r;
   if (t.kind == kTileGram) {
     const int g = t.j0 + col;
     if (f > g) return;  // the mirrored entry (g, f) is covered as (row g, column f)
-    t.M[(size_t)f * t.m + g] = t.ob[f] * s * t.oa[g];
-    if (f != g) t.M[(size_t)g * t.m + f] = t.ob[g] * s * t.oa[f];
+    const float s = acc.value();
+    t.M[(size_t)f * t.m + g] = (double)((float)t.ob[f] * s * (float)t.oa[g]);
+    if (f != g) t.M[(size_t)g * t.m + f] = (double)((float)t.ob[g] * s * (float)t.oa[f]);
   } else {
     const int c = calls[t.cloud].c;
     if (col < c) {
       if (t.fsplit) {  // add the lo column of the same channel
         const float* q = t.part + (int64_t)r * t.ld + t.col_off + c + col;
-        for (int u = 0; u < t.count; ++u) s += (double)q[(int64_t)u * t.slot_elems];
+        for (int u = 0; u < t.count; ++u) acc.add(q[(int64_t)u * t.slot_elems]);
       }
-      t.Y[(size_t)f * c + col] = t.ob[f] * s;
+      t.Y[(size_t)f * c + col] = (double)((float)t.ob[f] * acc.value());
     }
   }
 }
 
 // Z[f, ch] = oa[f] sum_g G[f, g] Y[g, ch]: a block of 256 threads per row f,
-// the threads over g, channels in groups of 8.  Products and the sums within
-// a thread and a warp in FP32 (this GPU's FP64 pipe is slow; Z is stored in
-// FP32 and enters out = F + Phi Z, an increment on F), the 8 warp sums in FP64.
+// the threads over g, channels in groups of 8.  FP32 products; each thread's
+// terms, the warp sums and the 8 warps' sums are compensated FP32 sums (Z is
+// stored in FP32 and enters out = F + Phi Z, an increment on F).
 __global__ void __launch_bounds__(256) small_batched_kernel(const ApplyJob* __restrict__ jobs,
                                                             const int* __restrict__ prefix, int count,
                                                             const CloudCall* __restrict__ calls) {
@@ -171,31 +174,40 @@ __global__ void __launch_bounds__(256) small_batched_kernel(const ApplyJob* __re
   const int f = blockIdx.x - prefix[j];
   const int c = calls[jb.cloud].c, m = jb.m;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ float red[8][kCC];
+  __shared__ float red[8][kCC][2];
   const double* grow = jb.G + (size_t)f * m;
   for (int ch0 = 0; ch0 < c; ch0 += kCC) {
     const int nc = min(kCC, c - ch0);
-    float acc[kCC];
-#pragma unroll
-    for (int q = 0; q < kCC; ++q) acc[q] = 0.f;
+    Fp32Sum acc[kCC];
     for (int g = threadIdx.x; g < m; g += 256) {
       const float gv = (float)grow[g];
       const double* yrow = jb.Y + (size_t)g * c + ch0;
 #pragma unroll
       for (int q = 0; q < kCC; ++q)
-        if (q < nc) acc[q] = fmaf(gv, (float)yrow[q], acc[q]);
+        if (q < nc) acc[q].add(gv * (float)yrow[q]);
     }
 #pragma unroll
     for (int q = 0; q < kCC; ++q) {
-      float v = acc[q];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red[warp][q] = v;
+      // warp sum of the (sum, compensation) pairs: each butterfly step adds a pair as two terms
+      Fp32Sum v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) {
+        const float os = __shfl_xor_sync(0xffffffffu, v.s, o), oc = __shfl_xor_sync(0xffffffffu, v.c, o);
+        v.add(os);
+        v.c += oc;
+      }
+      if (lane == 0) {
+        red[warp][q][0] = v.s;
+        red[warp][q][1] = v.c;
+      }
     }
     __syncthreads();
     if (threadIdx.x < nc) {
-      double sum = 0.0;
-      for (int w = 0; w < 8; ++w) sum += (double)red[w][threadIdx.x];
-      jb.Z[(size_t)f * c + ch0 + threadIdx.x] = (float)(jb.oa[f] * sum);
+      Fp32Sum tot;
+      for (int w = 0; w < 8; ++w) {
+        tot.add(red[w][threadIdx.x][0]);
+        tot.add(red[w][threadIdx.x][1]);
+      }
+      jb.Z[(size_t)f * c + ch0 + threadIdx.x] = (float)jb.oa[f] * tot.value();
     }
     __syncthreads();
   }

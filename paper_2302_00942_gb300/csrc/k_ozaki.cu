@@ -254,42 +254,7 @@ struct Smem {
   uint32_t tmem_base;
 };
 
-// cluster-scope helpers (2-CTA clusters that share the B rows of a tile pair)
-__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, int32_t z,
-                                               uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
-      "%3, %4}], [%5], %6;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar), "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-      "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_index() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_count() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// One work item of the residue GEMM: rows m0 + 128 rank .. + 127 (rank: the
-// CTA's place in its cluster) of the A residues against rows n0 .. n0 + nb of
+// One work item of the residue GEMM: rows m0 .. m0 + 127 of the A residues against rows n0 .. n0 + nb of
 // the B^T residues, for the moduli g0 .. g0 + G - 1 in turn, over kp of K;
 // residues of the products into res planes [16][mp][np] (bytes in [0, p)).
 struct Item {
@@ -297,18 +262,16 @@ struct Item {
   const CUtensorMap* mb;
   uint8_t* res;
   int kp, mp, np, m0, n0, nb, g0, G;
-  bool skip;  // the cloud skips this product (every CTA of a cluster sees the same)
+  bool skip;  // the cloud skips this product
 };
 
-// The residue GEMM, persistent: cluster c takes items c, c + clusters, ...  A
+// The residue GEMM, persistent: CTA c takes items c, c + gridDim.x, ...  A
 // unit is one modulus over one segment of at most 1024 of K (the FP32
 // exactness bound); units alternate between two TMEM buffers of 256 columns,
-// so the epilogue drains one unit while the MMAs of the next run.  With CL = 2
-// the two CTAs of a cluster take the two 128-row halves of a 256-row tile: each
-// loads its own A rows and half of the B boxes, multicast to both, and each
-// MMA commit frees the stage in both CTAs (a stage is refilled only when both
-// have consumed it).  Stages (64 of K of one modulus) follow the units in order.
-template <int CL, typename ItemFn>
+// so the epilogue drains one unit while the MMAs of the next run.  Each CTA
+// loads its own A rows and every B box of its item; stages (64 of K of one
+// modulus) follow the units in order.
+template <typename ItemFn>
 __device__ __forceinline__ void residue_gemm_core(ItemFn item_of, int num_items, const crt::Constants& cc,
                                                   int stages, int stage_bytes, int* err) {
   extern __shared__ uint8_t smem_raw[];
@@ -316,15 +279,12 @@ __device__ __forceinline__ void residue_gemm_core(ItemFn item_of, int num_items,
   const uint32_t base = (raw_addr + 1023u) & ~1023u;
   Smem* sm = reinterpret_cast<Smem*>(smem_raw + (base - raw_addr) + stages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rank = CL > 1 ? (int)cluster_rank() : 0;
-  const int cid = CL > 1 ? (int)cluster_index() : (int)blockIdx.x;
-  const int ncl = CL > 1 ? (int)cluster_count() : (int)gridDim.x;
-  constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
+  const int cid = (int)blockIdx.x, ncl = (int)gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(smem_u32(&sm->full[s]), 1);
-      mbar_init(smem_u32(&sm->empty[s]), CL);  // one release from the MMA of every CTA of the cluster
+      mbar_init(smem_u32(&sm->empty[s]), 1);
     }
     for (int q = 0; q < 2; ++q) {
       mbar_init(smem_u32(&sm->acc_full[q]), 1);
@@ -336,7 +296,6 @@ __device__ __forceinline__ void residue_gemm_core(ItemFn item_of, int num_items,
   fence_before();
   __syncthreads();
   fence_after();
-  if (CL > 1) cluster_sync_all();  // the peer's barriers exist before any multicast or remote release
   const uint32_t tmem = sm->tmem_base;
 
   if (warp == 0) {
@@ -348,7 +307,7 @@ __device__ __forceinline__ void residue_gemm_core(ItemFn item_of, int num_items,
         const Item I = item_of(it);
         if (I.skip) continue;
         const int nchunks = I.kp / kBK, nseg = (nchunks + kChunksPerSeg - 1) / kChunksPerSeg;
-        const uint32_t tx = (uint32_t)(kBM + I.nb) * kBK * 2;  // own A rows + every B box (own and multicast)
+        const uint32_t tx = (uint32_t)(kBM + I.nb) * kBK * 2;  // A rows + every B box
         for (int u = 0; u < I.G * nseg && ok; ++u) {
           const int g = I.g0 + u / nseg, seg = u % nseg;
           const int c1 = min(nchunks, (seg + 1) * kChunksPerSeg);
@@ -361,18 +320,14 @@ __device__ __forceinline__ void residue_gemm_core(ItemFn item_of, int num_items,
             const uint32_t full = smem_u32(&sm->full[s]);
             mbar_arrive_expect_tx(full, tx);
             const uint32_t sa = base + s * stage_bytes, sb = sa + kABytes;
-            tma_load_3d(sa, I.ma, c * kBK, I.m0 + kBM * rank, g, full);
-            for (int q = rank; q < I.nb / kBBox; q += CL) {
-              if (CL > 1)
-                tma_load_3d_mc(sb + q * kBBoxBytes, I.mb, c * kBK, I.n0 + q * kBBox, g, full, kMask);
-              else
-                tma_load_3d(sb + q * kBBoxBytes, I.mb, c * kBK, I.n0 + q * kBBox, g, full);
-            }
+            tma_load_3d(sa, I.ma, c * kBK, I.m0, g, full);
+            for (int q = 0; q < I.nb / kBBox; ++q)
+              tma_load_3d(sb + q * kBBoxBytes, I.mb, c * kBK, I.n0 + q * kBBox, g, full);
           }
         }
       }
-      // every stage this CTA filled has been released by every CTA of the cluster: no copy
-      // into, or release of, this CTA's shared memory is still in flight when it exits
+      // every stage this CTA filled has been released by its MMAs: no copy into this
+      // CTA's shared memory is still in flight when it exits
       for (int t = (i > stages ? i - stages : 0); t < i; ++t)
         mbar_wait(smem_u32(&sm->empty[t % stages]), (uint32_t)(t / stages) & 1u, err, 12);
     }
@@ -406,10 +361,7 @@ __device__ __forceinline__ void residue_gemm_core(ItemFn item_of, int num_items,
             for (int kk = 0; kk < kBK / 16; ++kk)
               mma_bf16(tmem + (uint32_t)(q * 256), sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
                        (c > c0 || kk > 0) ? 1u : 0u);
-            if (CL > 1)
-              mma_commit_mc(smem_u32(&sm->empty[s]), kMask);  // frees the stage in every CTA of the cluster
-            else
-              mma_commit(smem_u32(&sm->empty[s]));
+            mma_commit(smem_u32(&sm->empty[s]));  // frees the stage when these MMAs finish
           }
           if (ok) mma_commit(smem_u32(&sm->acc_full[q]));  // the unit's sums are complete
         }
@@ -426,8 +378,7 @@ __device__ __forceinline__ void residue_gemm_core(ItemFn item_of, int num_items,
       if (I.skip) continue;
       const int nchunks = I.kp / kBK, nseg = (nchunks + kChunksPerSeg - 1) / kChunksPerSeg;
       const size_t plane = (size_t)I.mp * I.np;
-      const int row0 = I.m0 + kBM * rank;
-      const bool rows_ok = row0 < I.mp;  // a cluster's second half may lie past the padded rows
+      const int row0 = I.m0;
       for (int u = 0; u < I.G * nseg; ++u, ++ug) {
         const int g = I.g0 + u / nseg, seg = u % nseg, q = ug & 1;
         if (!mbar_wait(smem_u32(&sm->acc_full[q]), (uint32_t)(ug >> 1) & 1u, err, 15)) {
@@ -441,7 +392,6 @@ __device__ __forceinline__ void residue_gemm_core(ItemFn item_of, int num_items,
           const int c0 = cq * 32;
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(q * 256 + c0), v);
-          if (!rows_ok) continue;
           uint8_t* dst = I.res + g * plane + (size_t)row * I.np + I.n0 + c0;
           uint32_t old[8] = {0, 0, 0, 0, 0, 0, 0, 0};
           if (seg > 0) {
@@ -481,7 +431,6 @@ __device__ __forceinline__ void residue_gemm_core(ItemFn item_of, int num_items,
   __syncthreads();
   fence_after();
   if (warp == 1) tmem_dealloc(tmem, 512);
-  if (CL > 1) cluster_sync_all();  // no CTA leaves while its peer may still address it
 }
 
 __device__ __forceinline__ bool pow2_of(double alpha, int* k, bool* neg) {
@@ -602,13 +551,12 @@ __global__ void bsplit_kernel(const PhiCloud* __restrict__ pcs, const int* __res
     bsplit_cols_block(pcs, strip_prefix, count, b_slot, nmod, mask_k, blockIdx.x - row_blocks);
 }
 
-template <int CL>
 __global__ void __launch_bounds__(kThreads, 1)
 bresidue_gemm_kernel(const CUtensorMap* __restrict__ maps, const OzTile* __restrict__ tiles, int num_tiles,
                      const PhiCloud* __restrict__ pcs, const __grid_constant__ crt::Constants cc, int stages,
                      int stage_bytes, int mask_k, int* err) {
   const int nmod = cc.nmod;
-  // item a = (tile a / nmod, modulus a mod nmod): the moduli in use only, spread over the clusters
+  // item a = (tile a / nmod, modulus a mod nmod): the moduli in use only, spread over the CTAs
   auto item_of = [&](int it) {
     const OzTile t = tiles[it / nmod];
     const PhiCloud& pc = pcs[t.cloud];
@@ -627,7 +575,7 @@ bresidue_gemm_kernel(const CUtensorMap* __restrict__ maps, const OzTile* __restr
     I.skip = mask_k >= 0 && pc.s <= mask_k;
     return I;
   };
-  residue_gemm_core<CL>(item_of, num_tiles * nmod, cc, stages, stage_bytes, err);
+  residue_gemm_core(item_of, num_tiles * nmod, cc, stages, stage_bytes, err);
 }
 
 // D = alpha A B + beta C + diag I, one thread per 4 consecutive entries of a
@@ -673,13 +621,12 @@ __global__ void split_cols_kernel(const double* __restrict__ B, int ld, int K, i
   split_cols(B, ld, K, N, K_pad, N_pad, sh0, kNumMod, res, exps, part, blockIdx.x * 32, blockIdx.y);
 }
 
-// items (row tile of 128 CL, column tile of 256, modulus), one modulus each
-template <int CL>
+// items (row tile of 128, column tile of 256, modulus), one modulus each
 __global__ void __launch_bounds__(kThreads, 1)
 residue_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                     const __grid_constant__ crt::Constants cc, int K_pad, int mp, int np, uint8_t* res, int stages,
                     int stage_bytes, int* err) {
-  const int ntn = (np + kBNMax - 1) / kBNMax, ntm = (mp + kBM * CL - 1) / (kBM * CL);
+  const int ntn = (np + kBNMax - 1) / kBNMax, ntm = (mp + kBM - 1) / kBM;
   auto item_of = [&](int it) {
     Item I;
     I.ma = &map_a;
@@ -692,12 +639,12 @@ residue_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_cons
     I.G = 1;
     const int t = it / kNumMod;
     I.n0 = (t % ntn) * kBNMax;
-    I.m0 = (t / ntn) * kBM * CL;
+    I.m0 = (t / ntn) * kBM;
     I.nb = min(kBNMax, np - I.n0);
     I.skip = false;
     return I;
   };
-  residue_gemm_core<CL>(item_of, ntn * ntm * kNumMod, cc, stages, stage_bytes, err);
+  residue_gemm_core(item_of, ntn * ntm * kNumMod, cc, stages, stage_bytes, err);
 }
 
 __global__ void combine_product_kernel(const __grid_constant__ crt::Constants cc, const uint8_t* __restrict__ res,
@@ -721,15 +668,15 @@ bool make_ozaki_maps(void* map_a_host, void* map_b_host, const void* sa, const v
 
 namespace {
 
-// Co-resident CTAs of the residue GEMM (1 per SM, shared memory bound) and
-// co-resident 2-CTA clusters; the persistent grids use these counts.
+// Co-resident CTAs of the residue GEMM (1 per SM, shared memory bound); the
+// persistent grids use this count.
 struct GemmSlots {
   cudaError_t status;
-  int ctas, clusters2;
+  int ctas;
 };
 const GemmSlots& gemm_slots() {
   static const GemmSlots g = [] {  // once per process (thread-safe initialisation)
-    GemmSlots r{cudaSuccess, 0, 0};
+    GemmSlots r{cudaSuccess, 0};
     constants();
     int dev = 0;
     r.status = cudaGetDevice(&dev);
@@ -738,25 +685,8 @@ const GemmSlots& gemm_slots() {
       if (r.status == cudaSuccess)
         r.status = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     };
-    attr(bresidue_gemm_kernel<1>);
-    attr(bresidue_gemm_kernel<2>);
-    attr(residue_gemm_kernel<1>);
-    attr(residue_gemm_kernel<2>);
-    if (r.status == cudaSuccess) {
-      cudaLaunchConfig_t cfg = {};
-      cudaLaunchAttribute la[1];
-      la[0].id = cudaLaunchAttributeClusterDimension;
-      la[0].val.clusterDim.x = 2;
-      la[0].val.clusterDim.y = 1;
-      la[0].val.clusterDim.z = 1;
-      cfg.gridDim = dim3(2 * r.ctas);
-      cfg.blockDim = dim3(kThreads);
-      cfg.dynamicSmemBytes = kSmemLimit;
-      cfg.attrs = la;
-      cfg.numAttrs = 1;
-      r.status = cudaOccupancyMaxActiveClusters(&r.clusters2, bresidue_gemm_kernel<2>, &cfg);
-      if (r.status == cudaSuccess && r.clusters2 < 1) r.status = cudaErrorInvalidConfiguration;
-    }
+    attr(bresidue_gemm_kernel);
+    attr(residue_gemm_kernel);
     return r;
   }();
   return g;
@@ -768,43 +698,27 @@ int stages_for(int stage_bytes) {
   return s < 2 ? 0 : (s > kMaxStages ? kMaxStages : s);
 }
 
-// A persistent launch with clusters of CL CTAs: grid = CL x (co-resident clusters, at most one per item).
-template <int CL, typename Kern, typename... Args>
+// A persistent launch: one CTA per SM, at most one per item.
+template <typename Kern, typename... Args>
 cudaError_t launch_persistent(Kern kern, int items, int smem, cudaStream_t st, Args... args) {
   const GemmSlots& g = gemm_slots();
   if (g.status != cudaSuccess) return g.status;
-  const int clusters = std::max(1, std::min(items, CL > 1 ? g.clusters2 : g.ctas));
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute la[1];
-  la[0].id = cudaLaunchAttributeClusterDimension;
-  la[0].val.clusterDim.x = CL;
-  la[0].val.clusterDim.y = 1;
-  la[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(CL * clusters);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cfg.attrs = la;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, args...);
+  const int ctas = std::max(1, std::min(items, g.ctas));
+  kern<<<ctas, kThreads, smem, st>>>(args...);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t bgemm_prepare() { return gemm_slots().status; }
 
-void ozaki_batch_tiles(const std::vector<int>& ms, int sms, std::vector<OzTile>* out, int* stage_bytes,
-                       int* cluster) {
+void ozaki_batch_tiles(const std::vector<int>& ms, int sms, std::vector<OzTile>* out, int* stage_bytes) {
   (void)sms;
   out->clear();
-  // 2-CTA clusters (tile pairs sharing B) when every cloud has at least two 128-row tiles
-  int CL = 2;
-  for (int m : ms)
-    if (ozaki_layout(m, m, m).mp < 2 * kBM) CL = 1;
   int nb_max = kBBox;
   for (int k = 0; k < (int)ms.size(); ++k) {
     const OzLayout L = ozaki_layout(ms[k], ms[k], ms[k]);
-    for (int m0 = 0; m0 < L.mp; m0 += CL * kBM)
+    for (int m0 = 0; m0 < L.mp; m0 += kBM)
       for (int n0 = 0; n0 < L.np; n0 += kBNMax) {
         const int nb = std::min(kBNMax, L.np - n0);
         nb_max = std::max(nb_max, nb);
@@ -815,22 +729,18 @@ void ozaki_batch_tiles(const std::vector<int>& ms, int sms, std::vector<OzTile>*
   std::stable_sort(out->begin(), out->end(),
                    [](const OzTile& a, const OzTile& b) { return (int64_t)a.nb * a.kp > (int64_t)b.nb * b.kp; });
   *stage_bytes = kABytes + nb_max * kBK * 2;
-  *cluster = CL;
 }
 
 namespace {
 // grid-stride launch of the batched residue GEMM over its items
 cudaError_t launch_bresidue(const void* maps_dev, const OzTile* tiles, int num_tiles, const PhiCloud* pc,
-                            int stage_bytes, int cluster, int nmod, int mask_k, int* err, cudaStream_t st) {
+                            int stage_bytes, int nmod, int mask_k, int* err, cudaStream_t st) {
   const int stages = stages_for(stage_bytes);
   if (stages == 0) return cudaErrorInvalidValue;
   const int smem = stages * stage_bytes + kSmemExtra;
   const auto* maps = static_cast<const CUtensorMap*>(maps_dev);
-  if (cluster == 2)
-    return launch_persistent<2>(bresidue_gemm_kernel<2>, num_tiles * nmod, smem, st, maps, tiles, num_tiles, pc,
-                                constants(nmod), stages, stage_bytes, mask_k, err);
-  return launch_persistent<1>(bresidue_gemm_kernel<1>, num_tiles * nmod, smem, st, maps, tiles, num_tiles, pc,
-                              constants(nmod), stages, stage_bytes, mask_k, err);
+  return launch_persistent(bresidue_gemm_kernel, num_tiles * nmod, smem, st, maps, tiles, num_tiles, pc,
+                           constants(nmod), stages, stage_bytes, mask_k, err);
 }
 }  // namespace
 
@@ -855,7 +765,7 @@ void launch_bcombine_product(int nmod, int blocks, cudaStream_t st, Args... args
 
 cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* rexp_prefix,
                          int rexp_blocks, const int* strip_prefix,
-                         int col_strips, const OzTile* tiles, int num_tiles, int stage_bytes, int cluster,
+                         int col_strips, const OzTile* tiles, int num_tiles, int stage_bytes,
                          const int* group_prefix, int group_blocks, int nmod,
                          const void* maps_dev, int a_slot, int b_slot, int c_slot, int d_slot, double alpha,
                          double beta, double diag, int mask_k, bool split_a, bool split_b, int* err, cudaStream_t st) {
@@ -869,7 +779,7 @@ cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a,
     bsplit_kernel<<<rsb + cb, 256, 0, st>>>(pc, row_prefix_a, strip_prefix, count, a_slot, b_slot, nmod, mask_k, rsb);
     count_launch(2);
   }
-  const cudaError_t e = launch_bresidue(maps_dev, tiles, num_tiles, pc, stage_bytes, cluster, nmod, mask_k, err, st);
+  const cudaError_t e = launch_bresidue(maps_dev, tiles, num_tiles, pc, stage_bytes, nmod, mask_k, err, st);
   if (e != cudaSuccess) return e;
   count_launch();
   launch_bcombine_product(nmod, group_blocks, st, pc, group_prefix, count, constants(nmod), c_slot, d_slot, alpha,
@@ -937,13 +847,8 @@ cudaError_t dgemm_ozaki(int M, int N, int K, double alpha, const double* A, int 
   {
     const int stage_bytes = kABytes + kBNMax * kBK * 2, stages = stages_for(stage_bytes);
     const int smem = stages * stage_bytes + kSmemExtra, ntn = (np + kBNMax - 1) / kBNMax;
-    cudaError_t e;
-    if (mp >= 2 * kBM)
-      e = launch_persistent<2>(residue_gemm_kernel<2>, ntn * ((mp + 2 * kBM - 1) / (2 * kBM)) * kNumMod, smem, st, ma,
-                               mb, constants(), kp, mp, np, res, stages, stage_bytes, err);
-    else
-      e = launch_persistent<1>(residue_gemm_kernel<1>, ntn * (mp / kBM) * kNumMod, smem, st, ma, mb, constants(), kp,
-                               mp, np, res, stages, stage_bytes, err);
+    const cudaError_t e = launch_persistent(residue_gemm_kernel, ntn * (mp / kBM) * kNumMod, smem, st, ma, mb,
+                                            constants(), kp, mp, np, res, stages, stage_bytes, err);
     if (e != cudaSuccess) return e;
     count_launch();
   }

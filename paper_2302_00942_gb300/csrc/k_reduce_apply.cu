@@ -10,7 +10,9 @@ namespace rfd {
 namespace {
 
 // One thread per tile element; partials of one tile are summed in split order
-// (deterministic for a given N, m and channel count) in FP64.
+// (deterministic for a given N, m and channel count), compensated FP32; the
+// column scales are applied in FP32 and the result stored in FP64 (step a4's
+// input).
 __global__ void reduce_kernel(const GramTile* __restrict__ tiles, const float* __restrict__ partials,
                               int64_t slot_elems, const double* __restrict__ oa,
                               const double* __restrict__ ob, int m, int c, double* __restrict__ M,
@@ -19,37 +21,42 @@ __global__ void reduce_kernel(const GramTile* __restrict__ tiles, const float* _
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = e / tile_cols, col = e % tile_cols;
   if (r >= t.ni || col >= t.nj) return;
-  double s = 0.0;
+  Fp32Sum acc;
   for (int u = 0; u < t.unit_count; ++u)
-    s += (double)partials[(int64_t)(t.unit_first + u) * slot_elems + (int64_t)r * t.ld + t.col_off + col];
+    acc.add(partials[(int64_t)(t.unit_first + u) * slot_elems + (int64_t)r * t.ld + t.col_off + col]);
+  const float s = acc.value();
   const int f = t.i0 + r;
   if (t.kind == kTileGram) {
     const int g = t.j0 + col;
     if (f > g) return;  // the mirrored entry (g, f) is covered as (row g, column f)
-    M[(size_t)f * m + g] = ob[f] * s * oa[g];
-    if (f != g) M[(size_t)g * m + f] = ob[g] * s * oa[f];
+    M[(size_t)f * m + g] = (double)((float)ob[f] * s * (float)oa[g]);
+    if (f != g) M[(size_t)g * m + f] = (double)((float)ob[g] * s * (float)oa[f]);
   } else {
-    if (col < c) Y[(size_t)f * c + col] = ob[f] * s;
+    if (col < c) Y[(size_t)f * c + col] = (double)((float)ob[f] * s);
   }
 }
 
-// Z[f, ch] = oa[f] * sum_g G[f, g] Y[g, ch], FP64, stored FP32.
-// Block (32 channels x 8 g-slices) per row f.
+// Z[f, ch] = oa[f] * sum_g G[f, g] Y[g, ch]: FP32 products, compensated FP32
+// sums, stored FP32.  Block (32 channels x 8 g-slices) per row f.
 __global__ void small_product_kernel(const double* __restrict__ G, const double* __restrict__ Y,
                                      const double* __restrict__ oa, int m, int c, float* __restrict__ Z) {
   const int f = blockIdx.x;
-  __shared__ double red[8][32];
+  __shared__ float red[8][32][2];
   for (int ch0 = 0; ch0 < c; ch0 += 32) {
     const int ch = ch0 + threadIdx.x;
-    double acc = 0.0;
+    Fp32Sum acc;
     if (ch < c)
-      for (int g = threadIdx.y; g < m; g += 8) acc = fma(G[(size_t)f * m + g], Y[(size_t)g * c + ch], acc);
-    red[threadIdx.y][threadIdx.x] = acc;
+      for (int g = threadIdx.y; g < m; g += 8) acc.add((float)G[(size_t)f * m + g] * (float)Y[(size_t)g * c + ch]);
+    red[threadIdx.y][threadIdx.x][0] = acc.s;
+    red[threadIdx.y][threadIdx.x][1] = acc.c;
     __syncthreads();
     if (threadIdx.y == 0 && ch < c) {
-      double s = 0.0;
-      for (int y = 0; y < 8; ++y) s += red[y][threadIdx.x];
-      Z[(size_t)f * c + ch] = (float)(oa[f] * s);
+      Fp32Sum tot;
+      for (int y = 0; y < 8; ++y) {
+        tot.add(red[y][threadIdx.x][0]);
+        tot.add(red[y][threadIdx.x][1]);
+      }
+      Z[(size_t)f * c + ch] = (float)oa[f] * tot.value();
     }
     __syncthreads();
   }

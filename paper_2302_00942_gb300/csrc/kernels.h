@@ -16,6 +16,20 @@ inline cudaError_t launched(long long k = 1) {
   return cudaGetLastError();
 }
 
+// Compensated FP32 summation (Knuth's TwoSum per term, the lost low parts kept
+// in a second FP32 word): the split-K partials and the small products are
+// summed this way, so no FP64 arithmetic runs outside step a4.
+struct Fp32Sum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ float value() const { return s + c; }
+};
+
 // One output tile of the reductions over N (step a3).  Rows i0.. of the
 // feature matrix Psi form the M side (features f), rows j0.. the N side
 // (features g, or field channels when kind == kTileField).
@@ -76,14 +90,15 @@ constexpr int kTcLd = 512;
 // part of a diagonal tile below the diagonal), N = nj_mma - skip1 (+ cpad).
 // maps[map + 0/1/2/5]: the cloud's A (box 128 rows), B (64 rows), F (cpad rows)
 // and B (16 rows) maps; b_rows: rows of the B map (m).  slot: the logical tile
-// index of half 0 in the plan's partial buffer (half 1: slot + 1).
+// index of half 0 (half 1: slot + 1); out / out1 point at this lane's partials.
 struct TcUnit {
   float* out;   // half 0 partial: 128 rows x kTcLd floats
   float* out1;  // half 1 partial, or null when the unit has one half
   int32_t map;
   int32_t i0, j0, nj_mma, has_f, cpad;
   int32_t lane, nlanes, kb_total, a_rows, b_rows;
-  int32_t slot, skip1, pad_;
+  int32_t slot, skip1;
+  int32_t work;  // the tile's cost per 64-point block (SM clocks; sets its share of the lanes)
 };
 // Encodes the three tensor maps of a cloud's bf16 feature matrix Psi
 // ([rows_alloc][n_pad], rows 0..m-1 features, m..m+cpad-1 field) into maps[0..2].
@@ -97,9 +112,14 @@ constexpr int kGramPhaseBlocks = 4096;  // default phase length
 cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_units, int a_boxes, int max_kb,
                            int phase_blocks, int* err, cudaStream_t st);
 bool tc_gram_supported();
+// One CTA that allocates TMEM, waits on an mbarrier nothing arrives on for
+// limit_ns, records its code in *err, frees the TMEM and returns: the bounded
+// wait's unwind path on its own (a test hook).
+cudaError_t launch_wait_probe(unsigned long long limit_ns, int* err, cudaStream_t st);
 
-// Sum the split-K partials of every tile in a fixed order (Kahan) and apply
-// the column scales: M = diag(ob) K diag(oa) (both triangles), Y = diag(ob) Y'.
+// Sum the split-K partials of every tile in a fixed order (compensated FP32)
+// and apply the column scales in FP32: M = diag(ob) K diag(oa) (both
+// triangles), Y = diag(ob) Y', stored as FP64 for step a4.
 // Partials of tile t, split s live at partials + (t.unit_first + s) * slot_elems.
 cudaError_t launch_reduce(const GramTile* tiles, int num_tiles, const float* partials, int64_t slot_elems,
                           const double* oa, const double* ob, int m, int c, double* M, double* Y,
@@ -233,7 +253,7 @@ struct PhiCloud {
   int32_t s, pad_;        // squarings (set per call)
   int8_t kbits_n[16];     // bits of the scaled integers with the first n moduli: ozaki_kbits(m, n), n = 1..16
 };
-// One tile of the residue GEMM: rows m0 .. (128 per CTA of a cluster), columns
+// One tile of the residue GEMM: rows m0 .. m0 + 127, columns
 // n0 .. n0 + nb of one cloud's product (kp: the padded K, for ordering the tiles
 // by cost); a launch with nmod moduli has the work items (tile, modulus g < nmod).
 struct OzTile {
@@ -241,11 +261,8 @@ struct OzTile {
 };
 // The residue-GEMM tiles of a batch of m x m products (cloud k of size ms[k]),
 // longest first: one per (row tile, column tile of <= 256).
-// *cluster = 2 when every cloud has two or more 128-row tiles: the two CTAs of
-// a cluster take the halves of a 256-row tile and share its B rows by
-// multicast; else 1 (128-row tiles).  *stage_bytes: the pipeline stage size.
-void ozaki_batch_tiles(const std::vector<int>& ms, int sms, std::vector<OzTile>* out, int* stage_bytes,
-                       int* cluster);
+// *stage_bytes: the pipeline stage size.
+void ozaki_batch_tiles(const std::vector<int>& ms, int sms, std::vector<OzTile>* out, int* stage_bytes);
 
 cudaError_t launch_features_batched(const FeatJob* jobs, const int* prefix, int count, int total_blocks,
                                     const CloudCall* calls, cudaStream_t st);
@@ -284,7 +301,7 @@ cudaError_t launch_bfinite(const PhiCloud* pc, const int* prefix, int count, int
 // clouds).
 cudaError_t launch_bgemm(const PhiCloud* pc, int count, const int* row_prefix_a, int rows_a, const int* rexp_prefix,
                          int rexp_blocks, const int* strip_prefix,
-                         int col_strips, const OzTile* tiles, int num_tiles, int stage_bytes, int cluster,
+                         int col_strips, const OzTile* tiles, int num_tiles, int stage_bytes,
                          const int* group_prefix, int group_blocks, int nmod,
                          const void* maps_dev, int a_slot, int b_slot, int c_slot, int d_slot, double alpha,
                          double beta, double diag, int mask_k, bool split_a, bool split_b, int* err, cudaStream_t st);

@@ -229,25 +229,66 @@ int gram_halves(const std::vector<GramCT>& ct) {
   return h;
 }
 
-// Lanes of the point axis per compute tile: the tiles' CTAs fill lanes_pct % of the SMs.
-int gram_lanes(int64_t kb_total, int sms, int lanes_pct, int tiles) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>(kb_total, (int64_t)sms * lanes_pct / 100 / std::max(tiles, 1)));
+// Cost of one 64-point block for a compute tile's CTA, in SM clocks: the
+// larger of its MMA time (2 clocks per MMA column per 128-row half at the
+// BF16 rate) and the time its TMA loads take to arrive (~2.6 clocks per
+// 128-byte row of A and B, the L2 -> SM rate measured for this kernel).
+int gram_tile_cost(const GramCT& c, int cpad) {
+  const int n0 = c.nj_mma + (c.f ? cpad : 0);
+  const int n1 = c.ni1 > 0 ? n0 - c.skip1 : 0;
+  const int a_rows = c.ni1 > 0 ? 2 * kTcBM : kTcBM;
+  return std::max(2 * (n0 + n1), (26 * (a_rows + n0)) / 10);
+}
+
+// Lanes of the point axis per compute tile.  The tiles' CTAs fill lanes_pct %
+// of the SMs (at least one lane each, at most one per 64-point block), and the
+// lanes go to the tiles in proportion to their cost (greedily to the tile with
+// the most work per lane), so that every CTA has about the same work and the
+// tiles' lanes sweep the point axis at the same pace (their slabs of Psi are
+// then shared in L2).
+std::vector<int> gram_tile_lanes(const std::vector<GramCT>& ct, int cpad, int64_t kb_total, int sms, int lanes_pct) {
+  const int T = (int)ct.size();
+  std::vector<int> L(T, 1);
+  if (T == 0) return L;
+  std::vector<double> w(T);
+  for (int t = 0; t < T; ++t) w[t] = (double)gram_tile_cost(ct[t], cpad);
+  int budget = std::max(T, sms * lanes_pct / 100) - T;
+  while (budget-- > 0) {
+    int best = -1;
+    for (int t = 0; t < T; ++t)
+      if (L[t] < kb_total && (best < 0 || w[t] / L[t] > w[best] / L[best])) best = t;
+    if (best < 0) break;
+    ++L[best];
+  }
+  return L;
 }
 
 constexpr int kTuneLanesMax = 200;  // the largest lanes_pct the autotuner tries
+
+// split-K lanes per compute tile, rounded mean over the tiles (0 without units)
+int mean_lanes(const std::vector<TcUnit>& units) {
+  int tiles = 0;
+  for (const TcUnit& u : units) tiles += u.lane == 0 ? 1 : 0;
+  return tiles ? (int)((units.size() + tiles / 2) / tiles) : 0;
+}
 
 int tc_partial_slots(int m, int cpad, int64_t n_pad, int sms, int lanes_pct) {
   int slots = 1;
   for (int mode = 0; mode < 3; ++mode) {
     const std::vector<GramCT> ct = gram_tiles(m, cpad, mode);
-    slots = std::max(slots, gram_halves(ct) * gram_lanes(n_pad / kTcBK, sms, lanes_pct, (int)ct.size()));
+    const std::vector<int> L = gram_tile_lanes(ct, cpad, n_pad / kTcBK, sms, lanes_pct);
+    int sum = 0;
+    for (size_t t = 0; t < ct.size(); ++t) sum += (ct[t].ni1 > 0 ? 2 : 1) * L[t];
+    slots = std::max(slots, sum);
   }
   return slots;
 }
 
-// Each compute tile gets L lanes of the point axis, L = SMs / tiles, so a lone
-// cloud fills the GPU in one wave.  Partial slot of half h (logical tile s) in
-// lane l: s * L + l.
+// Each compute tile t gets L_t lanes of the point axis (gram_tile_lanes), so a
+// lone cloud fills the GPU in one wave (lanes_pct 100).  The partial slots of
+// the logical 128-row halves follow each other: half s (of tile t) takes L_t
+// consecutive slots, one per lane.  TcUnit.slot is the logical half index of
+// half 0, TcUnit.work the tile's cost (a batch rescales the lanes with it).
 rfd_status build_desc(rfd_plan_s* pl) {
   PlanDesc& d = pl->desc;
   for (int mode = 0; mode < 3; ++mode) {
@@ -260,15 +301,17 @@ rfd_status build_desc(rfd_plan_s* pl) {
   for (int mode = 0; mode < 3; ++mode) {
     const std::vector<GramCT> ct = gram_tiles(m, pl->cpad, mode);
     const int T = (int)ct.size();
-    const int L = gram_lanes(kb_total, pl->sms, pl->tune.lanes_pct, T);
+    const std::vector<int> Ls = gram_tile_lanes(ct, pl->cpad, kb_total, pl->sms, pl->tune.lanes_pct);
     int slot = 0;
+    int64_t base = 0;  // first partial slot of the current logical half
     for (int t = 0; t < T; ++t) {
       const GramCT& c = ct[t];
       const bool two = c.ni1 > 0;
+      const int L = Ls[t];
       for (int l = 0; l < L; ++l) {
         TcUnit u{};
-        u.out = pl->d_part + (int64_t)(slot * L + l) * pl->slot_elems;
-        u.out1 = two ? pl->d_part + (int64_t)((slot + 1) * L + l) * pl->slot_elems : nullptr;
+        u.out = pl->d_part + (base + l) * pl->slot_elems;
+        u.out1 = two ? pl->d_part + (base + L + l) * pl->slot_elems : nullptr;
         u.map = 0;
         u.i0 = c.i0;
         u.j0 = c.j0;
@@ -282,9 +325,10 @@ rfd_status build_desc(rfd_plan_s* pl) {
         u.b_rows = m;
         u.slot = slot;
         u.skip1 = c.skip1;
+        u.work = gram_tile_cost(c, pl->cpad);
         d.units[mode].push_back(u);
       }
-      // reduce tiles: .count holds the logical tile (slot) index until a batch assigns lanes
+      // reduce tiles: .count holds the logical half index until a batch assigns lanes
       for (int h = 0; h < (two ? 2 : 1); ++h) {
         RedTile r{};
         r.M = pl->d_M;
@@ -315,7 +359,9 @@ rfd_status build_desc(rfd_plan_s* pl) {
         }
       }
       slot += two ? 2 : 1;
+      base += (two ? 2 : 1) * (int64_t)L;
     }
+    if (base > pl->part_slots) return fail(RFD_ECUDA, "internal: Gram partial slots exceed their allocation");
   }
   auto* psi = static_cast<__nv_bfloat16_raw*>(pl->d_psi);
   d.feat = FeatJob{pl->n, pl->n_pad, pl->d_omega_hi, psi, pl->d_xyz, pl->h, (int)((pl->n_pad + 511) / 512), 0,
@@ -463,7 +509,7 @@ rfd_status rebuild_self(rfd_plan_s* pl) {
   RFD_CUDA(cudaStreamSynchronize(pl->stream));
   batch_free(pl->self);
   pl->self = nb;
-  pl->stats.splits = pl->desc.units[kModeGfi].empty() ? 0 : pl->desc.units[kModeGfi][0].nlanes;
+  pl->stats.splits = mean_lanes(pl->desc.units[kModeGfi]);
   return RFD_OK;
 }
 
@@ -738,7 +784,7 @@ rfd_status plan_materialize(rfd_plan_s* pl, MemSource* mem, bool self_batch, boo
       rfd_plan_s* self = pl;
       if ((st2 = batch_build(&self, 1, st, mem, self_options(pl), pl->tune, &pl->self)) != RFD_OK) return bail(st2);
     }
-    pl->stats.splits = pl->desc.units[kModeGfi].empty() ? 0 : pl->desc.units[kModeGfi][0].nlanes;
+    pl->stats.splits = mean_lanes(pl->desc.units[kModeGfi]);
   } else {
     pl->stats.splits = pl->both.units.empty() ? 0 : (int)(pl->both.units.size() / pl->both.tiles.size());
   }
@@ -1064,6 +1110,27 @@ rfd_status rfd_debug_plan_phi1(rfd_plan_t pl, const double* d_M) {
   if (s != RFD_OK) return s;
   RFD_CUDA(cudaStreamSynchronize(pl->stream));
   return check_device_error(pl);
+}
+
+rfd_status rfd_debug_plan_set_phase(rfd_plan_t pl, int32_t phase_blocks) {
+  if (!pl) return fail(RFD_EINVAL, "null plan");
+  if (!pl->bf16 || !pl->self) return fail(RFD_EINVAL, "the phase length belongs to the tensor-core reductions");
+  if (pl->p.flags & (RFD_FLAG_GRAPH | RFD_FLAG_AUTOTUNE))
+    return fail(RFD_EINVAL, "not for plans with RFD_FLAG_GRAPH or RFD_FLAG_AUTOTUNE");
+  if (phase_blocks < 1) return fail(RFD_EINVAL, "phase_blocks must be >= 1");
+  pl->tune.phase_blocks = phase_blocks;
+  batch_set_phase(pl->self, phase_blocks);
+  return RFD_OK;
+}
+
+rfd_status rfd_debug_plan_wait_timeout(rfd_plan_t pl, int32_t limit_us) {
+  if (!pl) return fail(RFD_EINVAL, "null plan");
+  if (limit_us < 1 || limit_us > 1000000) return fail(RFD_EINVAL, "limit_us must be in [1, 1000000]");
+  if (!tc_gram_supported()) return fail(RFD_ENOTSUP, "the probe uses tcgen05 (sm_103 only)");
+  int* err = pl->bf16 ? batch_error_word(pl->self) : pl->d_ints;
+  cudaStream_t st = pl->bf16 ? batch_stream(pl->self) : pl->stream;
+  RFD_CUDA(launch_wait_probe((unsigned long long)limit_us * 1000ull, err, st));
+  return RFD_OK;
 }
 
 rfd_status rfd_debug_dgemm(int32_t method, int32_t M, int32_t N, int32_t K, double alpha, const double* A, int32_t lda,

@@ -95,7 +95,6 @@ struct BatchImpl {
   int col_strips = 0;
   OzTile* d_oz = nullptr;
   int oz_stage_bytes = 0;  // pipeline stage of the residue GEMM
-  int oz_cluster = 1;      // CTAs per cluster of the residue GEMM
   int n_oz = 0;
   int max_m = 0, max_cpad = 16, max_kb = 0;
   int a_boxes = 1;  // 2 when some Gram unit has a second 128-row half
@@ -158,11 +157,12 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
     return fail(s, msg);
   };
   const int sms = plans[0]->sms;
-  // --- Gram lanes: each cloud's lanes share the batch's CTAs in proportion to its work
-  double work = 0.0;
+  // --- Gram lanes: every tile's lanes share the batch's CTAs in proportion to its cost
+  double work = 0.0;  // SM clocks of all tiles over all their 64-point blocks
   for (int k = 0; k < count; ++k)
-    work += (double)plans[k]->desc.units[kModeGfi].size() * (double)(plans[k]->n_pad / kTcBK);
-  const double target = (count == 1) ? 1e300 : std::max(1.0, work / (tune.waves * (double)sms));  // k-blocks per CTA
+    for (const TcUnit& u : plans[k]->desc.units[kModeGfi])
+      if (u.lane == 0) work += (double)u.work * (double)(plans[k]->n_pad / kTcBK);
+  const double target = (count == 1) ? 1e300 : std::max(1.0, work / (tune.waves * (double)sms));  // clocks per CTA
   std::vector<TcUnit> units[3];
   std::vector<RedTile> red[3];
   std::vector<unsigned char> maps((size_t)count * kMapsPerCloud * kTensorMapBytes);
@@ -182,29 +182,42 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
     std::memcpy(maps.data() + (size_t)k * kMapsPerCloud * kTensorMapBytes, d.maps, sizeof(d.maps));
     const int64_t kb = pl->n_pad / kTcBK;
     for (int mode = 0; mode < 3; ++mode) {
-      // the plan's own units use nlanes = L_plan; the batch may use fewer lanes
+      // the plan's own units give each tile L_plan lanes; a batch may give it fewer
       const std::vector<TcUnit>& pu = d.units[mode];
       if (pu.empty()) continue;
-      const int L_plan = pu[0].nlanes;
-      const int T = (int)pu.size() / L_plan;
-      int L = L_plan;
-      if (count > 1) L = (int)std::max<int64_t>(1, std::min<int64_t>(L_plan, (int64_t)std::ceil(kb / target)));
-      for (int t = 0; t < T; ++t)
+      std::vector<int64_t> half_base;  // first partial slot of each logical half
+      std::vector<int> half_lanes;
+      int64_t base = 0;
+      for (size_t i = 0; i < pu.size(); i += pu[i].nlanes) {
+        const TcUnit& u0 = pu[i];
+        const int L_plan = u0.nlanes;
+        int L = L_plan;
+        if (count > 1)
+          L = (int)std::max<int64_t>(1, std::min<int64_t>(L_plan, (int64_t)std::ceil((double)kb * u0.work / target)));
+        const int halves = u0.out1 ? 2 : 1;
+        half_base.resize(u0.slot + halves);
+        half_lanes.resize(u0.slot + halves);
+        for (int h = 0; h < halves; ++h) {
+          half_base[u0.slot + h] = base + (int64_t)h * L;
+          half_lanes[u0.slot + h] = L;
+        }
         for (int l = 0; l < L; ++l) {
-          TcUnit u = pu[(size_t)t * L_plan];
+          TcUnit u = u0;
           u.lane = l;
           u.nlanes = L;
           u.map += k * kMapsPerCloud;
-          u.out = pl->d_part + (int64_t)(u.slot * L + l) * pl->slot_elems;
-          if (u.out1) u.out1 = pl->d_part + (int64_t)((u.slot + 1) * L + l) * pl->slot_elems;
+          u.out = pl->d_part + (base + l) * pl->slot_elems;
+          if (u.out1) u.out1 = pl->d_part + (base + L + l) * pl->slot_elems;
           if (u.out1) b->a_boxes = 2;
           units[mode].push_back(u);
         }
+        base += (int64_t)halves * L;
+      }
       for (RedTile r : d.red[mode]) {
-        // red tiles of the plan are per logical tile (its slot index stored in .count): remap to lanes
-        const int t = r.count;
-        r.part = pl->d_part + (int64_t)t * L * pl->slot_elems;
-        r.count = L;
+        // red tiles of the plan name their logical half in .count: point them at its lanes' partials
+        const int s = r.count;
+        r.part = pl->d_part + half_base[s] * pl->slot_elems;
+        r.count = half_lanes[s];
         r.cloud = k;
         red[mode].push_back(r);
       }
@@ -247,7 +260,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   {
     std::vector<int> ms;
     for (int k = 0; k < count; ++k) ms.push_back(plans[k]->m);
-    ozaki_batch_tiles(ms, sms, &oz, &b->oz_stage_bytes, &b->oz_cluster);
+    ozaki_batch_tiles(ms, sms, &oz, &b->oz_stage_bytes);
   }
   b->n_oz = (int)oz.size();
   // --- one device block: the tables, then the per-call words
@@ -421,7 +434,7 @@ rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s, const int horner_
     last_b = bb;
     last_na = last_nb = nmod;
     return launch_bgemm(b->d_phi, n, b->d_rowa_prefix, b->rows_a, b->d_rexp_prefix, b->rexp_blocks, b->d_strip_prefix, b->col_strips, b->d_oz,
-                        b->n_oz, b->oz_stage_bytes, b->oz_cluster, b->d_grp_prefix, b->grp_blocks, nmod, b->d_maps, a,
+                        b->n_oz, b->oz_stage_bytes, b->d_grp_prefix, b->grp_blocks, nmod, b->d_maps, a,
                         bb, c, d, alpha, beta, diag, mask, sa, sb, b->d_err, st);
   };
   // a slot that is written no longer matches its residues
@@ -746,6 +759,8 @@ rfd_status batch_time_gram(BatchImpl* b, int mode, int reps, float* ms) {
   *ms = t / (float)reps;
   return RFD_OK;
 }
+
+int* batch_error_word(BatchImpl* b) { return b->d_err; }
 
 rfd_status batch_check_error(BatchImpl* b, int* bad) {
   const int n = b->count;

@@ -173,6 +173,7 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tim
 // Step a4 alone (the batched emulated path) on the plans' resident M; synchronises.
 rfd_status batch_phi1_only(BatchImpl* b);
 cudaStream_t batch_stream(BatchImpl* b);
+int* batch_error_word(BatchImpl* b);  // the sticky device word that batch_check_error reads
 // Kernel eigenvalues (rfd_eigen.cu): argument checks, and the k smallest /
 // largest eigenvalues of every plan's exp(lambda W_hat) from its resident M
 // into d_out (count x k), asynchronous on st.

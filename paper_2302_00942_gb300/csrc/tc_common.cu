@@ -1,6 +1,8 @@
 // Host-side helpers shared by the tcgen05 kernels: tensor-map encoding through
-// the CUDA driver API entry point (no link-time dependency on libcuda) and the device check.
+// the CUDA driver API entry point (no link-time dependency on libcuda) and the
+// device check; and the probe of the kernels' bounded-wait unwind path.
 #include "tc_common.cuh"
+#include "kernels.h"
 
 namespace rfd {
 namespace tc {
@@ -65,4 +67,41 @@ bool sm103_available() {
 }
 
 }  // namespace tc
+
+namespace {
+
+constexpr int kWaitProbeCode = 21;
+
+// The unwind path of the tcgen05 kernels on its own: warp 1 allocates TMEM as
+// the Gram and residue-GEMM kernels do, thread 0 waits on an mbarrier that no
+// thread and no copy ever arrives on, with the caller's limit; when the wait
+// runs out it records kWaitProbeCode in *err (unless an earlier code is
+// there), and the CTA frees its TMEM and returns.  No TMA copy is issued, so
+// there is nothing in flight to drain.
+__global__ void __launch_bounds__(64, 1) wait_probe_kernel(unsigned long long limit_ns, int* err) {
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(tc::smem_u32(&bar), 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) tc::tmem_alloc(tc::smem_u32(&tmem_base), 32);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (threadIdx.x == 0) tc::mbar_wait(tc::smem_u32(&bar), 0u, err, kWaitProbeCode, limit_ns);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 1) tc::tmem_dealloc(tmem_base, 32);
+}
+
+}  // namespace
+
+cudaError_t launch_wait_probe(unsigned long long limit_ns, int* err, cudaStream_t st) {
+  wait_probe_kernel<<<1, 64, 0, st>>>(limit_ns, err);
+  return launched();
+}
+
 }  // namespace rfd

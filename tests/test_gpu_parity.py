@@ -1,14 +1,16 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle.
 
-Tolerances (relative Frobenius error over the whole N x c output):
-  FP32 plain form   <= 1e-5
-  BF16 tensor-core  <= 1e-3
+Every whole-path check asserts, on the same seeded inputs (parity_checks):
+  the whole output   FP32 plain <= 1e-5, BF16 tensor core <= 1e-3 (relative Frobenius);
+  the increment      out - F against ref - F: FP32 <= 1e-4, BF16 <= 2e-2;
+  every row          max_i ||out_i - ref_i|| <= the increment bound x max_i ||ref_i - F_i||.
 Step a4 alone (FP64 on both sides): <= 1e-12.
 """
 import numpy as np
 import pytest
 
 import oracle
+import parity_checks as pc
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -64,9 +66,8 @@ def test_small_config_matches_oracle(prec):
     spec, pts, F, lam = small_case()
     ref, parts = oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, return_parts=True)
     out, stats, (om, r, G) = gpu_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, prec)
-    err = oracle.rel_frobenius(out, ref)
-    print(f"precision {prec}: rel err {err:.3e}, inc {oracle.rel_frobenius(F, ref):.3e}, stats {stats}")
-    assert err <= TOL[prec]
+    print(f"stats {stats}")
+    pc.assert_matches(out, ref, F, prec, label="small")
     np.testing.assert_array_equal(om, parts["omega"])
     np.testing.assert_allclose(r, parts["r"], rtol=1e-13)
     # G from the device-side M against the oracle's G: limited by the reductions' precision
@@ -114,9 +115,8 @@ def test_ragged_and_degenerate_shapes(prec, n, m, c, ld):
     lam = 0.1 * m / max(n, m)
     ref = oracle.rfd_gfi(pts, F, eps, lam, m, seed)
     out, stats, _ = gpu_gfi(pts, F, eps, lam, m, seed, prec, ld=ld)
-    err = oracle.rel_frobenius(out, ref)
-    print(n, m, c, prec, err, stats)
-    assert err <= TOL[prec]
+    print(stats)
+    pc.assert_matches(out, ref, F, prec, label=f"N={n} m={m} c={c} ld={ld}")
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -133,7 +133,7 @@ def test_negative_lambda(prec):
     spec, pts, F, lam = small_case()
     ref = oracle.rfd_gfi(pts, F, spec.eps, -lam, spec.m, spec.seed)
     out, _, _ = gpu_gfi(pts, F, spec.eps, -lam, spec.m, spec.seed, prec)
-    assert oracle.rel_frobenius(out, ref) <= TOL[prec]
+    pc.assert_matches(out, ref, F, prec, label="negative lambda")
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -143,7 +143,8 @@ def test_warm_path_equals_cold_and_inplace(prec):
     warm, _, _ = gpu_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, prec, api="split", max_channels=8)
     inpl, _, _ = gpu_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, prec, inplace=True)
     ref = oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed)
-    assert oracle.rel_frobenius(warm, ref) <= TOL[prec]
+    pc.assert_matches(warm, ref, F, prec, label="warm")
+    pc.assert_matches(cold, ref, F, prec, label="cold")
     np.testing.assert_array_equal(inpl, cold)
 
 
@@ -160,7 +161,7 @@ def test_resident_plan_reuse_new_fields(prec):
             out = plan.integrate(_cuda(Fk))
             plan.sync()
             ref = oracle.rfd_gfi(pts, Fk, spec.eps, lam, spec.m, spec.seed)
-            assert oracle.rel_frobenius(out.cpu().numpy(), ref) <= TOL[prec]
+            pc.assert_matches(out.cpu().numpy(), ref, Fk, prec, label=f"resident c={c}")
     finally:
         plan.close()
 
@@ -170,9 +171,23 @@ def test_torus_config(prec):
     spec, pts, F, lam = small_case("torus")
     ref = oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed)
     out, stats, _ = gpu_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, prec)
-    err = oracle.rel_frobenius(out, ref)
-    print(f"torus N={spec.n} m={spec.m} c={spec.c} prec={prec} err={err:.3e} stats={stats}")
-    assert err <= TOL[prec]
+    print(f"torus N={spec.n} m={spec.m} c={spec.c} stats={stats}")
+    pc.assert_matches(out, ref, F, prec, label="torus")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name,factor", [("small", 2.5), ("torus", 6.0)])
+def test_large_relative_increment(prec, name, factor):
+    """A longer diffusion time, where the integrated part is a large share of the
+    output (relative increment 0.36 on the small workload, 0.44 on the torus):
+    the whole-output bounds of both forms still hold, so they do not rest on a
+    small increment."""
+    spec, pts, F, lam = small_case(name)
+    lam *= factor
+    ref = oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed)
+    out, _, _ = gpu_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, prec)
+    e = pc.assert_matches(out, ref, F, prec, label=f"{name} x{factor}")
+    assert e["relative_increment"] >= 0.3
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -185,9 +200,7 @@ def test_kernel_variants_match_oracle(prec, name, kernel):
     spec, pts, F, lam = small_case(name)
     ref, parts = oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, return_parts=True, kernel=kernel)
     out, stats, (om, r, G) = gpu_gfi(pts, F, spec.eps, lam, spec.m, spec.seed, prec, kernel=kernel)
-    err = oracle.rel_frobenius(out, ref)
-    print(f"{kernel} {name} precision {prec}: rel err {err:.3e}, inc {oracle.rel_frobenius(F, ref):.3e}")
-    assert err <= TOL[prec]
+    pc.assert_matches(out, ref, F, prec, label=f"{kernel} {name}")
     np.testing.assert_array_equal(om, parts["omega"])
     np.testing.assert_allclose(r, parts["r"], rtol=0, atol=1e-13 * np.abs(parts["r"]).max())
 
@@ -217,7 +230,7 @@ def test_plan_graph_replay_is_bitwise_identical():
     for a, b in zip(outs[False], outs[True]):
         np.testing.assert_array_equal(a, b)
     ref = oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed)
-    assert oracle.rel_frobenius(outs[True][2], ref) <= TOL[rfd.RFD_BF16_TC]
+    pc.assert_matches(outs[True][2], ref, F, rfd.RFD_BF16_TC, label="graph replay")
 
 
 def test_invalid_arguments_and_alloc_failure():
@@ -236,7 +249,8 @@ def test_invalid_arguments_and_alloc_failure():
         # the plan stays usable after failed calls
         out = plan.gfi(_cuda(pts), Ft)
         plan.sync()
-        assert oracle.rel_frobenius(out.cpu().numpy(), oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed)) <= 1e-3
+        pc.assert_matches(out.cpu().numpy(), oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed), F,
+                          rfd.RFD_BF16_TC, label="after failed calls")
     finally:
         plan.close()
     for k in (0, 1, 2):  # the plan chunk, its batch tables, their pinned staging
@@ -279,3 +293,31 @@ def test_batched_phi1_matches_oracle(m, norm, lam):
 def _check(status, where):
     if status != 0:
         raise RuntimeError(f"{where}: {rfd.rfd_last_error()}")
+
+
+@pytest.mark.parametrize("phase_blocks", [64, 300, 1])
+def test_multi_phase_point_axis_matches_oracle(phase_blocks):
+    """The tensor-core reductions walk the point axis in phases (one launch each,
+    later phases adding into the split-K lanes' FP32 partials, Sec. 2.4's
+    reduction over N).  The large workload takes several phases; here a short
+    phase makes the torus cloud (1563 blocks of 64 points) take 25, 6 and 1563
+    of them, and the result must match the oracle and the one-phase result."""
+    spec, pts, F, lam = small_case("torus")
+    ref = oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed)
+    P, Ft = _cuda(pts), _cuda(F)
+    outs = []
+    for ph in (phase_blocks, 1 << 20):
+        plan = rfd.Plan(spec.n, spec.m, spec.eps, lam, spec.seed, max_channels=F.shape[1],
+                        precision=rfd.RFD_BF16_TC, stream=torch.cuda.current_stream(DEV))
+        try:
+            _check(rfd.lib.rfd_debug_plan_set_phase(plan.handle, ph), "rfd_debug_plan_set_phase")
+            o = plan.gfi(P, Ft)
+            plan.sync()
+            assert plan.stats()["tune_phase_blocks"] == ph
+            outs.append(o.cpu().numpy())
+        finally:
+            plan.close()
+    pc.assert_matches(outs[0], ref, F, rfd.RFD_BF16_TC, label=f"{phase_blocks}-block phases")
+    # against the single-phase run: the same products, summed in another order (FP32)
+    pc.assert_matches(outs[0], outs[1], F, rfd.RFD_BF16_TC, label="phases vs one phase", tol_out=1e-5,
+                      tol_inc=2e-3, tol_row=2e-3)

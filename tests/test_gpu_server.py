@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
+import parity_checks as pc
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -14,7 +15,7 @@ torch = pytest.importorskip("torch")
 import paper_2302_00942_gb300 as rfd  # noqa: E402
 
 DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
-TOL = 1e-3
+BF16 = 1  # RFD_BF16_TC: every comparison asserts the output, increment and per-row bounds of parity_checks
 WAIT_US = 60_000_000
 
 
@@ -66,12 +67,10 @@ def test_server_mix_equals_alone_and_oracle():
         assert max(sizes) > 1, "the burst was not batched"
         for k, s in enumerate(specs):
             mixed = outs[k].cpu().numpy()
-            assert oracle.rel_frobenius(mixed, alone[k]) <= TOL
+            pc.assert_matches(mixed, alone[k], clouds[k][1], BF16, label=f"request {k} mixed vs alone")
             if k < 4:
                 ref = oracle.rfd_gfi(clouds[k][0], clouds[k][1], s.eps, _lam(s), s.m, s.seed)
-                err = oracle.rel_frobenius(mixed, ref)
-                print(f"request {k}: N={s.n} m={s.m} c={s.c} err vs oracle {err:.2e}")
-                assert err <= TOL
+                pc.assert_matches(mixed, ref, clouds[k][1], BF16, label=f"request {k}: N={s.n} m={s.m} c={s.c}")
         st = srv.stats()
         assert st["completed"] == 24 and st["batches"] >= 13 and st["kernel_launches"] > 0
     finally:
@@ -94,7 +93,7 @@ def test_server_resident_cloud_reused_with_new_field():
         res2 = _wait(srv, srv.submit(F2d, out2, cloud=cid))
         assert res2["status"] == rfd.RFD_OK and res2["reused"] == 1 and res2["cloud"] == cid
         ref = oracle.rfd_gfi(pts, F2, s.eps, _lam(s), s.m, s.seed)
-        assert oracle.rel_frobenius(out2.cpu().numpy(), ref) <= TOL
+        pc.assert_matches(out2.cpu().numpy(), ref, F2, BF16, label="reused cloud")
         # more channels than the cloud was kept for: the request fails, the cloud stays usable
         F3 = torch.zeros((s.n, 17), device=DEV)
         res3 = _wait(srv, srv.submit(F3, torch.empty_like(F3), cloud=cid))
@@ -158,6 +157,6 @@ def test_server_evicts_idle_clouds_and_rebuilds_from_points():
         res = _wait(srv, _submit(srv, specs[0], dev[0][0], F0, out, cloud=ids[0]))
         assert res["status"] == rfd.RFD_OK and res["reused"] == 0
         ref = oracle.rfd_gfi(clouds[0][0], clouds[0][1], specs[0].eps, _lam(specs[0]), specs[0].m, specs[0].seed)
-        assert oracle.rel_frobenius(out.cpu().numpy(), ref) <= TOL
+        pc.assert_matches(out.cpu().numpy(), ref, clouds[0][1], BF16, label="rebuilt cloud")
     finally:
         srv.close()
