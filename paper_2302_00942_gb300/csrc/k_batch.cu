@@ -132,7 +132,7 @@ fill_batched_kernel(const FillJob* __restrict__ jobs, const int* __restrict__ pr
 }
 
 // One thread per tile element; lanes summed in order (deterministic),
-// compensated FP32; column scales applied in FP32, results stored in FP64
+// compensated FP32; the compensated sum scaled by the column scales in FP64
 // (step a4's input).
 __global__ void reduce_batched_kernel(const RedTile* __restrict__ tiles, const CloudCall* __restrict__ calls) {
   const RedTile t = tiles[blockIdx.y];
@@ -146,9 +146,11 @@ __global__ void reduce_batched_kernel(const RedTile* __restrict__ tiles, const C
   if (t.kind == kTileGram) {
     const int g = t.j0 + col;
     if (f > g) return;  // the mirrored entry (g, f) is covered as (row g, column f)
-    const float s = acc.value();
-    t.M[(size_t)f * t.m + g] = (double)((float)t.ob[f] * s * (float)t.oa[g]);
-    if (f != g) t.M[(size_t)g * t.m + f] = (double)((float)t.ob[g] * s * (float)t.oa[f]);
+    // M = diag(s) K diag(s sgn r) with the commutative product s_f s_g, so that
+    // M diag(sgn r) is exactly symmetric
+    const double v = acc.wide() * (t.ob[f] * t.ob[g]);
+    t.M[(size_t)f * t.m + g] = t.oa[g] < 0.0 ? -v : v;
+    if (f != g) t.M[(size_t)g * t.m + f] = t.oa[f] < 0.0 ? -v : v;
   } else {
     const int c = calls[t.cloud].c;
     if (col < c) {
@@ -156,7 +158,7 @@ __global__ void reduce_batched_kernel(const RedTile* __restrict__ tiles, const C
         const float* q = t.part + (int64_t)r * t.ld + t.col_off + c + col;
         for (int u = 0; u < t.count; ++u) acc.add(q[(int64_t)u * t.slot_elems]);
       }
-      t.Y[(size_t)f * c + col] = (double)((float)t.ob[f] * acc.value());
+      t.Y[(size_t)f * c + col] = t.ob[f] * acc.wide();
     }
   }
 }

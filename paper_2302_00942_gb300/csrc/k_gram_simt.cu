@@ -6,12 +6,17 @@
 //   C[f, g] = sum_{n in [k0, k1)} Psi[i0 + f][n] * Psi[j0 + g][n].
 // Psi is feature-major (n contiguous), so every row of a tile is a contiguous
 // run of points: 16-point slabs are read with float4 loads and transposed
-// into shared memory.
+// into shared memory.  Each thread holds an 8 x 8 outer-product tile in
+// registers; the next slab's loads are issued before the current slab's
+// FMAs, so the global-memory latency hides behind 16 x 64 FMAs per thread.
 //
-// Accuracy: per-thread FP32 accumulators are folded every 256 points into a
-// Kahan-compensated (sum, carry) pair, so the rounding error of a partial is
-// ~sqrt(16) ulps of the partial instead of growing with N; the split-K
-// partials are summed in a fixed order, compensated, by the reduce kernel.
+// Accuracy: every 256 points each accumulator is folded into a running FP32
+// sum by an exact TwoSum (Knuth), and the rounding error of that addition
+// becomes the accumulator's starting value for the next 256 points: the
+// compensated (Kahan-type) sum without a third register array, so the
+// rounding error of a partial is ~sqrt(16) ulps of the partial instead of
+// growing with N; the split-K partials are summed in a fixed order,
+// compensated, by the reduce kernel.
 #include <cuda_runtime.h>
 #include "kernels.h"
 
@@ -32,35 +37,45 @@ gram_simt_kernel(const float* __restrict__ psi, int64_t n_pad, const GramUnit* _
   __shared__ __align__(16) float Bs[kK][kT + 4];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 
-  float acc[8][8], sum[8][8], carry[8][8];
+  float acc[8][8], sum[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) { acc[i][j] = 0.f; sum[i][j] = 0.f; carry[i][j] = 0.f; }
+    for (int j = 0; j < 8; ++j) { acc[i][j] = 0.f; sum[i][j] = 0.f; }
 
   // loader mapping: 128 rows x 4 float4 per slab and operand -> 2 float4 per thread
   const int lrow = threadIdx.x >> 2;       // 0..63
   const int lq = threadIdx.x & 3;          // which float4 of the 16-point slab
-  const float* arow0 = psi + (size_t)(u.i0 + lrow) * n_pad;
-  const float* arow1 = psi + (size_t)(u.i0 + lrow + 64) * n_pad;
-  const float* brow0 = psi + (size_t)(u.j0 + lrow) * n_pad;
-  const float* brow1 = psi + (size_t)(u.j0 + lrow + 64) * n_pad;
+  const float* arow0 = psi + (size_t)(u.i0 + lrow) * n_pad + lq * 4;
+  const float* arow1 = psi + (size_t)(u.i0 + lrow + 64) * n_pad + lq * 4;
+  const float* brow0 = psi + (size_t)(u.j0 + lrow) * n_pad + lq * 4;
+  const float* brow1 = psi + (size_t)(u.j0 + lrow + 64) * n_pad + lq * 4;
   // The plan allocates Psi with whole 128-row blocks past every tile start, so
   // these rows always exist; rows beyond a tile's valid range only feed
   // output rows/columns that the reduce ignores.
 
+  float4 va0, va1, vb0, vb1;  // the next slab, loaded one slab ahead
+  if (u.k0 < u.k1) {
+    va0 = __ldg(reinterpret_cast<const float4*>(arow0 + u.k0));
+    va1 = __ldg(reinterpret_cast<const float4*>(arow1 + u.k0));
+    vb0 = __ldg(reinterpret_cast<const float4*>(brow0 + u.k0));
+    vb1 = __ldg(reinterpret_cast<const float4*>(brow1 + u.k0));
+  }
   int slab = 0;
   for (int64_t k = u.k0; k < u.k1; k += kK, ++slab) {
-    const float4 va0 = *reinterpret_cast<const float4*>(arow0 + k + lq * 4);
-    const float4 va1 = *reinterpret_cast<const float4*>(arow1 + k + lq * 4);
-    const float4 vb0 = *reinterpret_cast<const float4*>(brow0 + k + lq * 4);
-    const float4 vb1 = *reinterpret_cast<const float4*>(brow1 + k + lq * 4);
-    __syncthreads();
+    __syncthreads();  // every thread is done reading the previous slab
     As[lq * 4 + 0][lrow] = va0.x; As[lq * 4 + 1][lrow] = va0.y; As[lq * 4 + 2][lrow] = va0.z; As[lq * 4 + 3][lrow] = va0.w;
     As[lq * 4 + 0][lrow + 64] = va1.x; As[lq * 4 + 1][lrow + 64] = va1.y; As[lq * 4 + 2][lrow + 64] = va1.z; As[lq * 4 + 3][lrow + 64] = va1.w;
     Bs[lq * 4 + 0][lrow] = vb0.x; Bs[lq * 4 + 1][lrow] = vb0.y; Bs[lq * 4 + 2][lrow] = vb0.z; Bs[lq * 4 + 3][lrow] = vb0.w;
     Bs[lq * 4 + 0][lrow + 64] = vb1.x; Bs[lq * 4 + 1][lrow + 64] = vb1.y; Bs[lq * 4 + 2][lrow + 64] = vb1.z; Bs[lq * 4 + 3][lrow + 64] = vb1.w;
     __syncthreads();
+    const int64_t kn = k + kK;
+    if (kn < u.k1) {  // in flight during this slab's FMAs
+      va0 = __ldg(reinterpret_cast<const float4*>(arow0 + kn));
+      va1 = __ldg(reinterpret_cast<const float4*>(arow1 + kn));
+      vb0 = __ldg(reinterpret_cast<const float4*>(brow0 + kn));
+      vb1 = __ldg(reinterpret_cast<const float4*>(brow1 + kn));
+    }
 #pragma unroll
     for (int kk = 0; kk < kK; ++kk) {
       const float4 a_lo = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
@@ -78,12 +93,11 @@ gram_simt_kernel(const float* __restrict__ psi, int64_t n_pad, const GramUnit* _
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float y = acc[i][j] - carry[i][j];
-          const float t = sum[i][j] + y;
-          carry[i][j] = (t - sum[i][j]) - y;
+        for (int j = 0; j < 8; ++j) {  // sum + acc = t + e exactly; e carries on in acc
+          const float t = sum[i][j] + acc[i][j];
+          const float bp = t - sum[i][j];
+          acc[i][j] = (sum[i][j] - (t - bp)) + (acc[i][j] - bp);
           sum[i][j] = t;
-          acc[i][j] = 0.f;
         }
     }
   }
@@ -93,10 +107,7 @@ gram_simt_kernel(const float* __restrict__ psi, int64_t n_pad, const GramUnit* _
     const int r = (i < 4) ? (ty * 4 + i) : (64 + ty * 4 + i - 4);
     float v[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float y = acc[i][j] - carry[i][j];
-      v[j] = sum[i][j] + y;
-    }
+    for (int j = 0; j < 8; ++j) v[j] = sum[i][j] + acc[i][j];
     *reinterpret_cast<float4*>(out + (size_t)r * kT + tx * 4) = make_float4(v[0], v[1], v[2], v[3]);
     *reinterpret_cast<float4*>(out + (size_t)r * kT + 64 + tx * 4) = make_float4(v[4], v[5], v[6], v[7]);
   }

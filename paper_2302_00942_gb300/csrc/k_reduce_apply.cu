@@ -11,8 +11,7 @@ namespace {
 
 // One thread per tile element; partials of one tile are summed in split order
 // (deterministic for a given N, m and channel count), compensated FP32; the
-// column scales are applied in FP32 and the result stored in FP64 (step a4's
-// input).
+// compensated sum is scaled by the column scales in FP64 (step a4's input).
 __global__ void reduce_kernel(const GramTile* __restrict__ tiles, const float* __restrict__ partials,
                               int64_t slot_elems, const double* __restrict__ oa,
                               const double* __restrict__ ob, int m, int c, double* __restrict__ M,
@@ -24,15 +23,18 @@ __global__ void reduce_kernel(const GramTile* __restrict__ tiles, const float* _
   Fp32Sum acc;
   for (int u = 0; u < t.unit_count; ++u)
     acc.add(partials[(int64_t)(t.unit_first + u) * slot_elems + (int64_t)r * t.ld + t.col_off + col]);
-  const float s = acc.value();
+  const double s = acc.wide();
   const int f = t.i0 + r;
   if (t.kind == kTileGram) {
     const int g = t.j0 + col;
     if (f > g) return;  // the mirrored entry (g, f) is covered as (row g, column f)
-    M[(size_t)f * m + g] = (double)((float)ob[f] * s * (float)oa[g]);
-    if (f != g) M[(size_t)g * m + f] = (double)((float)ob[g] * s * (float)oa[f]);
+    // M = diag(s) K diag(s sgn r) with the commutative product s_f s_g, so that
+    // M diag(sgn r) is exactly symmetric
+    const double v = s * (ob[f] * ob[g]);
+    M[(size_t)f * m + g] = oa[g] < 0.0 ? -v : v;
+    if (f != g) M[(size_t)g * m + f] = oa[f] < 0.0 ? -v : v;
   } else {
-    if (col < c) Y[(size_t)f * c + col] = (double)((float)ob[f] * s);
+    if (col < c) Y[(size_t)f * c + col] = ob[f] * s;
   }
 }
 

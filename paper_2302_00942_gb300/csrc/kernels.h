@@ -18,7 +18,8 @@ inline cudaError_t launched(long long k = 1) {
 
 // Compensated FP32 summation (Knuth's TwoSum per term, the lost low parts kept
 // in a second FP32 word): the split-K partials and the small products are
-// summed this way, so no FP64 arithmetic runs outside step a4.
+// summed this way.  wide() keeps both words (the compensated sum carries more
+// bits than one FP32 word holds) for the reduction's final column scaling.
 struct Fp32Sum {
   float s = 0.f, c = 0.f;
   __device__ __forceinline__ void add(float x) {
@@ -28,6 +29,7 @@ struct Fp32Sum {
     s = t;
   }
   __device__ __forceinline__ float value() const { return s + c; }
+  __device__ __forceinline__ double wide() const { return (double)s + (double)c; }
 };
 
 // One output tile of the reductions over N (step a3).  Rows i0.. of the
@@ -118,8 +120,10 @@ bool tc_gram_supported();
 cudaError_t launch_wait_probe(unsigned long long limit_ns, int* err, cudaStream_t st);
 
 // Sum the split-K partials of every tile in a fixed order (compensated FP32)
-// and apply the column scales in FP32: M = diag(ob) K diag(oa) (both
-// triangles), Y = diag(ob) Y', stored as FP64 for step a4.
+// and apply the column scales: M = diag(ob) K diag(oa) (both triangles),
+// Y = diag(ob) Y', stored as FP64 for step a4 (the scaling is the only FP64
+// arithmetic of step a3: three multiplies per entry, with the commutative
+// product ob_f ob_g so that M diag(sgn r) is exactly symmetric).
 // Partials of tile t, split s live at partials + (t.unit_first + s) * slot_elems.
 cudaError_t launch_reduce(const GramTile* tiles, int num_tiles, const float* partials, int64_t slot_elems,
                           const double* oa, const double* ob, int m, int c, double* M, double* Y,

@@ -252,6 +252,7 @@ void executor(rfd_server_s* s, int idx) {
     std::vector<uint64_t> fresh_t, reuse_t;
     const Clock::time_point now = Clock::now();
     bool mem_blocked = false;
+    bool finished_here = false;  // requests refused during admission: their pollers are woken below
     for (auto it = s->queue.begin(); it != s->queue.end() && (int)(fresh.size() + reuse.size()) < s->cfg.max_batch;) {
       const uint64_t t = *it;
       Req& q = s->reqs[t];
@@ -263,6 +264,7 @@ void executor(rfd_server_s* s, int idx) {
           if (ps != RFD_OK) {
             q.t_start = now;
             finish(s, q, ps, now, 0);
+            finished_here = true;
             it = s->queue.erase(it);
             continue;
           }
@@ -278,6 +280,7 @@ void executor(rfd_server_s* s, int idx) {
         if (!cl->plan->have_G || q.r.c > cl->plan->p.max_channels || (q.r.n && q.r.n != cl->plan->n)) {
           q.t_start = now;
           finish(s, q, cl->plan->have_G ? RFD_EINVAL : RFD_ENUMERIC, now, 0);
+          finished_here = true;
           it = s->queue.erase(it);
           continue;
         }
@@ -305,6 +308,7 @@ void executor(rfd_server_s* s, int idx) {
       fresh_t.push_back(t);
       it = s->queue.erase(it);
     }
+    if (finished_here) s->cv_done.notify_all();
     if (fresh.empty() && reuse.empty()) {
       // everything queued waits for memory or a busy cloud: sleep until something finishes
       s->cv_work.wait(lk);

@@ -3,6 +3,8 @@ a mixed stream of requests equal the same requests run alone (within the BF16
 tolerance) and the FP64 oracle; resident clouds are reused; admission, poll
 timeouts and eviction behave as the header states.  Every failure is made on
 the host (a paused scheduler, a full queue, a budget too small)."""
+import time
+
 import numpy as np
 import pytest
 
@@ -96,8 +98,10 @@ def test_server_resident_cloud_reused_with_new_field():
         pc.assert_matches(out2.cpu().numpy(), ref, F2, BF16, label="reused cloud")
         # more channels than the cloud was kept for: the request fails, the cloud stays usable
         F3 = torch.zeros((s.n, 17), device=DEV)
+        t0 = time.monotonic()
         res3 = _wait(srv, srv.submit(F3, torch.empty_like(F3), cloud=cid))
         assert res3["status"] == rfd.RFD_EINVAL
+        assert time.monotonic() - t0 < 5.0   # a request refused at admission wakes its poller at once
         res4 = _wait(srv, srv.submit(F2d, out2, cloud=cid))
         assert res4["status"] == rfd.RFD_OK
         assert srv.stats()["reused"] == 2
