@@ -869,7 +869,8 @@ def main():
         "barycenter": {"what": f"entropic Wasserstein barycenter of {bary_k} bump distributions on the same cloud "
                                "(App. C): 2 GFI of k columns + 2 element-wise kernels per pass, resident plan",
                        "passes": bary_passes, "ms_per_pass": bary_ms},
-        "autotune": {"lanes_pct": st["tune_lanes_pct"], "phase_blocks": st["tune_phase_blocks"], "tuned": st["tuned"]},
+        "autotune": {"lanes_pct": st["tune_lanes_pct"], "phase_blocks": st["tune_phase_blocks"], "tuned": st["tuned"],
+                     "gram_form": "CTA pairs (2-SM MMA)" if st.get("tune_pair_gram") else "one SM per tile"},
         "warm": {"value": whole_job_value(ws, n * c, warm_ms), "unit": "points*ch/s", "ms_per_step": warm_ms,
                  "what": "rfd_integrate: a new field on the resident features and G (steps a3(Y) to a6)",
                  "step_ms": {k: round(v, 4) for k, v in wst["step_ms"].items() if v}},

@@ -113,7 +113,8 @@ typedef struct rfd_plan_s* rfd_plan_t;
                                    are then not recorded; ignored by FP32 plain plans) */
 #define RFD_FLAG_AUTOTUNE 8     /* BF16 plans and batches: after the first features pass, time the
                                    tensor-core reductions for a few split-K lane counts (plans) or
-                                   wave targets (batches) and point-axis phase lengths on the
+                                   wave targets (batches), point-axis phase lengths and (a plan with
+                                   m >= 512) the one-SM or CTA-pair form of the Gram on the
                                    cloud's own features, and keep the fastest (cached per bucket:
                                    m, point count and field width for plans; cloud count and work
                                    for batches).  That first call returns after the tuning. */
@@ -152,6 +153,8 @@ typedef struct {
   int32_t tune_waves;        /*   split-K lanes (% of SMs per tile), waves a batch plans for, */
   int32_t tune_phase_blocks; /*   point-axis phase length (64-point blocks)                  */
   int32_t tuned;             /* 1 once the autotuner has chosen them                        */
+  int32_t tune_pair_gram;    /* 1: the reductions run on CTA pairs (2-SM MMAs; a lone BF16  */
+                             /*    cloud with m >= 512, chosen by the autotuner)           */
 } rfd_stats;
 
 /* ---------------------------------------------------------------------------

@@ -37,6 +37,15 @@ RFD_API rfd_status rfd_debug_dgemm(int32_t method, int32_t M, int32_t N, int32_t
  * path, RFD_ENUMERIC if G is not finite. */
 RFD_API rfd_status rfd_debug_plan_phi1(rfd_plan_t plan, const double* d_M);
 
+/* The form of the Gram reductions that plans created from now on start with
+ * (process-wide): enable = 1 puts a BF16 plan with m >= 512 (m a multiple of
+ * 16, at most 64 field channels) on CTA pairs (tcgen05.mma.cta_group::2, half
+ * of B loaded by each SM of the pair); enable = 0 (the default) on the one-SM
+ * kernel.  The autotuner (RFD_FLAG_AUTOTUNE) times both and may change it.
+ * A test compares the two forms on the same inputs with it.  Not thread-safe
+ * against concurrent plan creation; tests only. */
+RFD_API void rfd_debug_gram_pairs(int32_t enable);
+
 /* Set the point-axis phase length of a BF16 plan's tensor-core reductions:
  * the reductions run as one launch per phase of phase_blocks 64-point blocks,
  * each later phase adding to the split-K lanes' partials (step a3).  A short

@@ -47,14 +47,24 @@ constexpr int kFeatFreq = 32;
 // j0 + 4 t + g (t = 0..7), so each store instruction writes rows
 // j0 + 4t .. j0 + 4t + 3 of the block -- 4 adjacent rows of 128 bytes, one
 // contiguous 512-byte span -- with 16-byte stores.
+// blk_n > 0: a single cloud (job 0), only its 512-point blocks blk0 .. blk0 + blk_n - 1
+// (the grid is blk_n x frequency groups); blk_n = 0: every block of every job.
 __global__ void __launch_bounds__(kFeatThreads)
 features_batched_kernel(const FeatJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
-                        const CloudCall* __restrict__ calls) {
-  const int j = find_job(prefix, count, blockIdx.x);
+                        const CloudCall* __restrict__ calls, int blk0, int blk_n) {
+  int j = 0, bxi, byi;
+  if (blk_n > 0) {
+    bxi = blk0 + (int)(blockIdx.x % blk_n);
+    byi = (int)(blockIdx.x / blk_n);
+  } else {
+    j = find_job(prefix, count, blockIdx.x);
+    const int local = blockIdx.x - prefix[j];
+    bxi = local % jobs[j].bx;
+    byi = local / jobs[j].bx;
+  }
   const FeatJob jb = jobs[j];
-  const int local = blockIdx.x - prefix[j];
-  const int bxi = local % jb.bx, byi = local / jb.bx;
   const float* __restrict__ pts = calls[jb.cloud].pts;
+  if (!pts) return;  // a call table without this cloud's points: nothing to read
   __shared__ float w_s[kFeatFreq][3];
   const int j0 = byi * kFeatFreq;
   const int jn = min(kFeatFreq, jb.h - j0);
@@ -396,7 +406,15 @@ __global__ void bfinite_kernel(const PhiCloud* __restrict__ pcs, const int* __re
 cudaError_t launch_features_batched(const FeatJob* jobs, const int* prefix, int count, int total_blocks,
                                     const CloudCall* calls, cudaStream_t st) {
   if (total_blocks <= 0) return cudaSuccess;
-  features_batched_kernel<<<total_blocks, kFeatThreads, 0, st>>>(jobs, prefix, count, calls);
+  features_batched_kernel<<<total_blocks, kFeatThreads, 0, st>>>(jobs, prefix, count, calls, 0, 0);
+  return launched();
+}
+
+cudaError_t launch_features_range(const FeatJob* jobs, const CloudCall* calls, int h, int blk0, int blk_n,
+                                  cudaStream_t st) {
+  if (blk_n <= 0) return cudaSuccess;
+  const int groups = (h + kFeatFreq - 1) / kFeatFreq;
+  features_batched_kernel<<<blk_n * groups, kFeatThreads, 0, st>>>(jobs, nullptr, 1, calls, blk0, blk_n);
   return launched();
 }
 

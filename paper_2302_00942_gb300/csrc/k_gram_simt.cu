@@ -13,10 +13,12 @@
 // Accuracy: every 256 points each accumulator is folded into a running FP32
 // sum by an exact TwoSum (Knuth), and the rounding error of that addition
 // becomes the accumulator's starting value for the next 256 points: the
-// compensated (Kahan-type) sum without a third register array, so the
-// rounding error of a partial is ~sqrt(16) ulps of the partial instead of
-// growing with N; the split-K partials are summed in a fixed order,
-// compensated, by the reduce kernel.
+// compensated (Kahan-type) sum without a carry array, so the rounding error
+// of a partial is ~sqrt(16) ulps of the partial instead of growing with N;
+// the split-K partials are summed in a fixed order, compensated, by the
+// reduce kernel.  The running sums live in shared memory ([entry][thread],
+// 64 KB, conflict-free), so a thread holds only its 64 accumulators and the
+// operands: ~100 registers, two CTAs (16 warps) per SM to hide latency.
 #include <cuda_runtime.h>
 #include "kernels.h"
 
@@ -28,20 +30,25 @@ constexpr int kT = kSimtTile;   // 128
 constexpr int kK = kSimtK;      // 16 points per slab
 constexpr int kThreads = 256;   // 16 x 16 threads, 8 x 8 outputs each
 constexpr int kFold = 16;       // slabs per Kahan fold (256 points)
+constexpr int kSumBytes = 64 * kThreads * 4;  // running sums: 64 entries per thread
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
 gram_simt_kernel(const float* __restrict__ psi, int64_t n_pad, const GramUnit* __restrict__ units,
                  float* __restrict__ partials) {
   const GramUnit u = units[blockIdx.x];
   __shared__ __align__(16) float As[kK][kT + 4];
   __shared__ __align__(16) float Bs[kK][kT + 4];
+  extern __shared__ float sum_s[];  // [64][kThreads]: entry (i, j) of thread t at (8 i + j) kThreads + t
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 
-  float acc[8][8], sum[8][8];
+  float acc[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) { acc[i][j] = 0.f; sum[i][j] = 0.f; }
+    for (int j = 0; j < 8; ++j) {
+      acc[i][j] = 0.f;
+      sum_s[(8 * i + j) * kThreads + threadIdx.x] = 0.f;
+    }
 
   // loader mapping: 128 rows x 4 float4 per slab and operand -> 2 float4 per thread
   const int lrow = threadIdx.x >> 2;       // 0..63
@@ -94,10 +101,12 @@ gram_simt_kernel(const float* __restrict__ psi, int64_t n_pad, const GramUnit* _
       for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {  // sum + acc = t + e exactly; e carries on in acc
-          const float t = sum[i][j] + acc[i][j];
-          const float bp = t - sum[i][j];
-          acc[i][j] = (sum[i][j] - (t - bp)) + (acc[i][j] - bp);
-          sum[i][j] = t;
+          float& sm = sum_s[(8 * i + j) * kThreads + threadIdx.x];
+          const float sv = sm;
+          const float t = sv + acc[i][j];
+          const float bp = t - sv;
+          acc[i][j] = (sv - (t - bp)) + (acc[i][j] - bp);
+          sm = t;
         }
     }
   }
@@ -107,7 +116,7 @@ gram_simt_kernel(const float* __restrict__ psi, int64_t n_pad, const GramUnit* _
     const int r = (i < 4) ? (ty * 4 + i) : (64 + ty * 4 + i - 4);
     float v[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = sum[i][j] + acc[i][j];
+    for (int j = 0; j < 8; ++j) v[j] = sum_s[(8 * i + j) * kThreads + threadIdx.x] + acc[i][j];
     *reinterpret_cast<float4*>(out + (size_t)r * kT + tx * 4) = make_float4(v[0], v[1], v[2], v[3]);
     *reinterpret_cast<float4*>(out + (size_t)r * kT + 64 + tx * 4) = make_float4(v[4], v[5], v[6], v[7]);
   }
@@ -118,7 +127,10 @@ gram_simt_kernel(const float* __restrict__ psi, int64_t n_pad, const GramUnit* _
 cudaError_t launch_gram_simt(const float* psi, int64_t n_pad, const GramUnit* units, int num_units,
                              float* partials, cudaStream_t st) {
   if (num_units <= 0) return cudaSuccess;
-  gram_simt_kernel<<<num_units, kThreads, 0, st>>>(psi, n_pad, units, partials);
+  static const cudaError_t attr =  // once per process (thread-safe initialisation)
+      cudaFuncSetAttribute(gram_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSumBytes);
+  if (attr != cudaSuccess) return attr;
+  gram_simt_kernel<<<num_units, kThreads, kSumBytes, st>>>(psi, n_pad, units, partials);
   return launched();
 }
 

@@ -230,8 +230,8 @@ gram_tc_kernel(const CUtensorMap* __restrict__ maps, const TcUnit* __restrict__ 
 
 bool tc_gram_supported() { return tc::sm103_available(); }
 
-bool make_gram_maps(void* maps_host3, void* map_b16, const void* psi, int64_t n_pad, int m, int cpad,
-                    int rows_alloc) {
+bool make_gram_maps(void* maps_host3, void* map_b16, void* maps_pair2, const void* psi, int64_t n_pad, int m,
+                    int cpad, int rows_alloc) {
   auto* maps = static_cast<CUtensorMap*>(maps_host3);
   const uint32_t a_rows = (uint32_t)(m < kTcBM ? m : kTcBM);
   const uint32_t b_rows = (uint32_t)(m < 64 ? m : 64);
@@ -241,7 +241,10 @@ bool make_gram_maps(void* maps_host3, void* map_b16, const void* psi, int64_t n_
   return make_map_bf16_blocked(&maps[0], p, (uint64_t)m, ra, nb, a_rows) &&
          make_map_bf16_blocked(&maps[1], p, (uint64_t)m, ra, nb, b_rows) &&
          make_map_bf16_blocked(&maps[2], p + (size_t)m * 64, (uint64_t)cpad, ra, nb, (uint32_t)cpad) &&
-         make_map_bf16_blocked(static_cast<CUtensorMap*>(map_b16), p, (uint64_t)m, ra, nb, b16_rows);
+         make_map_bf16_blocked(static_cast<CUtensorMap*>(map_b16), p, (uint64_t)m, ra, nb, b16_rows) &&
+         make_map_bf16_blocked(static_cast<CUtensorMap*>(maps_pair2), p, (uint64_t)m, ra, nb, m < 8 ? m : 8) &&
+         make_map_bf16_blocked(static_cast<CUtensorMap*>(maps_pair2) + 1, p + (size_t)m * 64, (uint64_t)cpad, ra, nb,
+                               (uint32_t)(cpad / 2));
 }
 
 cudaError_t gram_tc_prepare() {
@@ -250,10 +253,10 @@ cudaError_t gram_tc_prepare() {
   return attr;
 }
 
-cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_units, int a_boxes, int max_kb,
-                           int phase_blocks, int* err, cudaStream_t st) {
+cudaError_t launch_gram_tc_phase(const void* maps_dev, const TcUnit* units, int num_units, int a_boxes, int kb0,
+                                 int phase_blocks, int* err, cudaStream_t st) {
   if (num_units <= 0) return cudaSuccess;
-  if (a_boxes < 1 || a_boxes > 2) return cudaErrorInvalidValue;
+  if (a_boxes < 1 || a_boxes > 2 || phase_blocks < 1) return cudaErrorInvalidValue;
   const int b_off = a_boxes * kABytes;
   const int stage_bytes = b_off + kBBytes;  // multiples of 1024 (the 128-byte swizzle's atom)
   int stages = (kSmemLimit - kSmemExtra) / stage_bytes;
@@ -262,14 +265,21 @@ cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_un
   const int smem = stages * stage_bytes + kSmemExtra;
   const cudaError_t attr = gram_tc_prepare();
   if (attr != cudaSuccess) return attr;
+  gram_tc_kernel<<<num_units, kThreads, smem, st>>>(static_cast<const CUtensorMap*>(maps_dev), units, stages,
+                                                    stage_bytes, b_off, kb0, phase_blocks, err);
+  return launched();
+}
+
+cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_units, int a_boxes, int max_kb,
+                           int phase_blocks, int* err, cudaStream_t st) {
+  if (num_units <= 0) return cudaSuccess;
   // the point axis in phases of phase_blocks 64-point blocks, one launch each, so that the
   // lanes of a tile restart in step (and the slab they share stays in L2) every phase
   if (phase_blocks < 1) phase_blocks = kGramPhaseBlocks;
   const int phases = max_kb > 0 ? (max_kb + phase_blocks - 1) / phase_blocks : 1;
   for (int ph = 0; ph < phases; ++ph) {
-    gram_tc_kernel<<<num_units, kThreads, smem, st>>>(static_cast<const CUtensorMap*>(maps_dev), units, stages,
-                                                      stage_bytes, b_off, ph * phase_blocks, phase_blocks, err);
-    const cudaError_t e = launched();
+    const cudaError_t e = launch_gram_tc_phase(maps_dev, units, num_units, a_boxes, ph * phase_blocks, phase_blocks,
+                                               err, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

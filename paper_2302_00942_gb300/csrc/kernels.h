@@ -102,17 +102,48 @@ struct TcUnit {
   int32_t slot, skip1;
   int32_t work;  // the tile's cost per 64-point block (SM clocks; sets its share of the lanes)
 };
+// One CTA pair of the 2-SM reductions (k_gram_pair.cu, m >= 512, m % 16 == 0):
+// feature rows r0 .. r0 + 511 (S0 = r0.., S1 = r0 + 256..) against the nc
+// columns c0 .. c0 + nc - 1 (nc a multiple of 16, <= 256), and, on the first
+// column tile of the row block (c0 = r0, no S1 x B part), the cpad field rows
+// (has_f).  CTA rank k of the pair holds the logical halves S0 + 128 k and
+// S1 + 128 k: out0[k] / out1[k] are this lane's partials of them (out1 null
+// when the pair tile has no S1 part).  g2: the S1 x B MMA; a1: S1 rows are
+// loaded (g2 or the field with S1 rows); m: rows of the cloud (loads of rows
+// >= m are skipped).  maps[map + 0/1/5/6/7]: A (128-row box), B (64-, 16-,
+// 8-row boxes), the field rows (box cpad / 2 rows).
+struct PairUnit {
+  float* out0[2];
+  float* out1[2];
+  int32_t map, r0, c0, nc, cpad, m;
+  int32_t g2, has_f, a1;
+  int32_t lane, nlanes, kb_total;
+  int32_t work, pad_;
+};
+// Stage size of the pair kernel for the largest column tile and field width of a launch.
+int gram_pair_stage_bytes(int max_nc, int max_cpad);
+// One phase of the pair reductions: grid 2 x num_units in clusters of two.
+cudaError_t launch_gram_pair_phase(const void* maps_dev, const PairUnit* units, int num_units, int stage_bytes,
+                                   int kb0, int phase_blocks, int* err, cudaStream_t st);
+cudaError_t gram_pair_prepare();
+// CTA pairs of the pair kernel that fit on the GPU at once (0 if unknown).
+int gram_pair_max_clusters();
 // Encodes the three tensor maps of a cloud's bf16 feature matrix Psi
 // ([rows_alloc][n_pad], rows 0..m-1 features, m..m+cpad-1 field) into maps[0..2].
 // maps_host3[0..2]: A (box min(128, m) rows), B (box min(64, m) rows), F rows (box cpad rows);
-// map_b16: B with a box of min(16, m) rows.
-bool make_gram_maps(void* maps_host3, void* map_b16, const void* psi, int64_t n_pad, int m, int cpad, int rows_alloc);
+// map_b16: B with a box of min(16, m) rows; maps_pair2[0..1] (the pair kernel's): B with a
+// box of min(8, m) rows, and the F rows with a box of cpad / 2 rows.
+bool make_gram_maps(void* maps_host3, void* map_b16, void* maps_pair2, const void* psi, int64_t n_pad, int m,
+                    int cpad, int rows_alloc);
 // One launch per phase of phase_blocks 64-point blocks (max_kb: the largest
 // point-block count of the units' clouds); later phases add to the partials.
 constexpr int kGramPhaseBlocks = 4096;  // default phase length
 // a_boxes: 2 when some unit has a second half (stages hold two A boxes), else 1.
 cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_units, int a_boxes, int max_kb,
                            int phase_blocks, int* err, cudaStream_t st);
+// One phase alone: the 64-point blocks [kb0, kb0 + phase_blocks) (kb0 > 0 adds to the partials).
+cudaError_t launch_gram_tc_phase(const void* maps_dev, const TcUnit* units, int num_units, int a_boxes, int kb0,
+                                 int phase_blocks, int* err, cudaStream_t st);
 bool tc_gram_supported();
 // One CTA that allocates TMEM, waits on an mbarrier nothing arrives on for
 // limit_ns, records its code in *err, frees the TMEM and returns: the bounded
@@ -270,6 +301,10 @@ void ozaki_batch_tiles(const std::vector<int>& ms, int sms, std::vector<OzTile>*
 
 cudaError_t launch_features_batched(const FeatJob* jobs, const int* prefix, int count, int total_blocks,
                                     const CloudCall* calls, cudaStream_t st);
+// Step a2 for one cloud (job 0 of jobs), its 512-point blocks blk0 .. blk0 + blk_n - 1 only
+// (the features of one phase of the point axis; h: the cloud's frequencies).
+cudaError_t launch_features_range(const FeatJob* jobs, const CloudCall* calls, int h, int blk0, int blk_n,
+                                  cudaStream_t st);
 cudaError_t launch_fill_batched(const FillJob* jobs, const int* prefix, int count, int total_blocks,
                                 const CloudCall* calls, cudaStream_t st);
 cudaError_t launch_reduce_batched(const RedTile* tiles, int num_tiles, const CloudCall* calls, cudaStream_t st);

@@ -7,6 +7,7 @@
 // plans run the SIMT reductions and the native-FP64 step a4.
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -118,14 +119,20 @@ void plan_free(rfd_plan_s* pl) {
 // Depends only on (N, m, channel capacity, SM count).
 void schedule_simt(TileSet& ts, int64_t n_pad, int target_units, const std::vector<double>& cost) {
   const int64_t ksteps = n_pad / kSimtK;
-  double total = 0;
-  for (double c : cost) total += c;
   int slot = 0;
-  std::vector<int> splits(ts.tiles.size());
-  for (size_t t = 0; t < ts.tiles.size(); ++t) {
-    int64_t s = (int64_t)std::llround(cost[t] / total * target_units);
-    s = std::max<int64_t>(1, std::min<int64_t>(s, ksteps));
-    splits[t] = (int)s;
+  // one piece per tile, then the rest of the target one at a time to the tile with the most
+  // cost per piece: the pieces never exceed the target (one wave), and their costs even out
+  const int T = (int)ts.tiles.size();
+  std::vector<int> splits(T, 1);
+  for (int left = target_units - T; left > 0; --left) {
+    int best = -1;
+    for (int t = 0; t < T; ++t)
+      if (splits[t] < ksteps && (best < 0 || cost[t] / splits[t] > cost[best] / splits[best])) best = t;
+    if (best < 0) break;
+    ++splits[best];
+  }
+  for (int t = 0; t < T; ++t) {
+    const int s = splits[t];
     ts.tiles[t].unit_first = slot;
     ts.tiles[t].unit_count = (int)s;
     ts.tiles[t].ld = kSimtTile;
@@ -165,7 +172,7 @@ void build_tiles_simt(rfd_plan_s* pl, bool with_gram, bool with_field, TileSet& 
                                   kTileField, 0, 0, 0, 0, 0});
       cost.push_back(1.0);
     }
-  schedule_simt(ts, pl->n_pad, 2 * pl->sms, cost);
+  schedule_simt(ts, pl->n_pad, 2 * pl->sms, cost);  // one wave: two CTAs per SM
 }
 
 // ---- BF16 tensor-core form: the plan's batched-path descriptors -------------
@@ -265,6 +272,156 @@ std::vector<int> gram_tile_lanes(const std::vector<GramCT>& ct, int cpad, int64_
 
 constexpr int kTuneLanesMax = 200;  // the largest lanes_pct the autotuner tries
 
+// ---- the 2-SM (CTA pair) form of the Gram modes, m >= 512 ----------------------
+// Pair tiles: for each block of 512 feature rows r0.. (S0 = r0.., S1 = r0 + 256..),
+// the column tiles c0 = r0, r0 + 256, ... of at most 256 columns; S1 x B where
+// some column lies right of S1's first row (g2); the field on the first column
+// tile (c0 = r0, whose S1 part lies below the diagonal).
+struct PairCT {
+  int r0, c0, nc;
+  bool g2, f, a1;
+};
+std::atomic<int> g_gram_pairs{1};  // test hook: 0 keeps every plan on the one-SM Gram kernel
+bool pair_eligible(const rfd_plan_s* pl) {
+  return g_gram_pairs.load() && pl->bf16 && pl->m >= 512 && pl->m % 16 == 0 && pl->cpad <= 128 &&
+         tc_gram_supported();
+}
+std::vector<PairCT> pair_tiles(int m, int mode) {
+  std::vector<PairCT> ct;
+  if (mode == kModeIntegrate) return ct;
+  for (int r0 = 0; r0 < m; r0 += 4 * kTcBM) {
+    const bool s1 = r0 + 2 * kTcBM < m;
+    for (int c0 = r0; c0 < m; c0 += kTcBNMax) {
+      PairCT t{r0, c0, std::min(kTcBNMax, m - c0), false, false, false};
+      t.g2 = s1 && c0 + t.nc > r0 + 2 * kTcBM;
+      t.f = mode != kModeFeatures && c0 == r0;
+      t.a1 = t.g2 || (t.f && s1);
+      ct.push_back(t);
+    }
+  }
+  return ct;
+}
+// per-block cost of a pair tile (SM clocks, as gram_tile_cost): the larger of the MMA
+// columns of the pair's M = 256 MMAs (2 clocks each) and the 128-byte rows one CTA loads
+// (~2.6 clocks each).  Measured: weighting by the MMA columns alone gives the diagonal
+// tiles (half the MMAs, about the same loads) too few lanes, and they finish last.
+int pair_tile_cost(const PairCT& t, int cpad) {
+  const int mma_cols = t.nc * (t.g2 ? 2 : 1) + (t.f ? cpad * (t.a1 ? 2 : 1) : 0);
+  const int rows = kTcBM * (t.a1 ? 2 : 1) + t.nc / 2 + (t.f ? cpad / 2 : 0);
+  return std::max(2 * mma_cols, (26 * rows) / 10);
+}
+// lanes per pair tile: lanes_pct % of the SM pairs, by cost (greedy, as gram_tile_lanes)
+std::vector<int> pair_tile_lanes(const std::vector<PairCT>& ct, int cpad, int64_t kb_total, int sms, int lanes_pct) {
+  const int T = (int)ct.size();
+  std::vector<int> L(T, 1);
+  std::vector<double> w(T);
+  for (int t = 0; t < T; ++t) w[t] = (double)pair_tile_cost(ct[t], cpad);
+  // a wave is the co-resident pairs (clusters need both SMs in one GPU processing cluster,
+  // so fewer than sms / 2 may fit at once)
+  const int fit = gram_pair_max_clusters();
+  const int wave = fit > 0 ? std::min(sms / 2, fit) : sms / 2;
+  int budget = std::max(T, wave * lanes_pct / 100) - T;
+  while (budget-- > 0) {
+    int best = -1;
+    for (int t = 0; t < T; ++t)
+      if (L[t] < kb_total && (best < 0 || w[t] / L[t] > w[best] / L[best])) best = t;
+    if (best < 0) break;
+    ++L[best];
+  }
+  return L;
+}
+int pair_partial_slots(int m, int64_t n_pad, int cpad, int sms, int lanes_pct) {
+  int slots = 0;
+  for (int mode = 0; mode < 3; ++mode) {
+    const std::vector<PairCT> ct = pair_tiles(m, mode);
+    const std::vector<int> L = pair_tile_lanes(ct, cpad, n_pad / kTcBK, sms, lanes_pct);
+    int sum = 0;
+    for (size_t t = 0; t < ct.size(); ++t) sum += (ct[t].a1 ? 4 : 2) * L[t];
+    slots = std::max(slots, sum);
+  }
+  return slots;
+}
+
+// The pair units and reduce tiles of the Gram modes (partial slots: each logical 128-row
+// half of a pair tile takes L_t consecutive slots, one per lane).
+rfd_status build_pair_desc(rfd_plan_s* pl) {
+  PlanDesc& d = pl->desc;
+  const int m = pl->m, cpad = pl->cpad;
+  const int64_t kb_total = pl->n_pad / kTcBK;
+  int max_nc = 16;
+  for (int mode = 0; mode < 3; ++mode) {
+    d.pair_units[mode].clear();
+    d.pair_red[mode].clear();
+    if (!pair_eligible(pl)) continue;
+    const std::vector<PairCT> ct = pair_tiles(m, mode);
+    const std::vector<int> Ls = pair_tile_lanes(ct, cpad, kb_total, pl->sms, pl->tune.lanes_pct);
+    int64_t base = 0;
+    for (size_t t = 0; t < ct.size(); ++t) {
+      const PairCT& c = ct[t];
+      const int L = Ls[t];
+      max_nc = std::max(max_nc, c.nc);
+      auto slot = [&](int half, int l) { return pl->d_part + (base + (int64_t)half * L + l) * pl->slot_elems; };
+      for (int l = 0; l < L; ++l) {
+        PairUnit u{};
+        u.out0[0] = slot(0, l);
+        u.out0[1] = slot(1, l);
+        u.out1[0] = c.a1 ? slot(2, l) : nullptr;
+        u.out1[1] = c.a1 ? slot(3, l) : nullptr;
+        u.map = 0;
+        u.r0 = c.r0;
+        u.c0 = c.c0;
+        u.nc = c.nc;
+        u.cpad = cpad;
+        u.m = m;
+        u.g2 = c.g2 ? 1 : 0;
+        u.has_f = c.f ? 1 : 0;
+        u.a1 = c.a1 ? 1 : 0;
+        u.lane = l;
+        u.nlanes = L;
+        u.kb_total = (int)kb_total;
+        u.work = pair_tile_cost(c, cpad);
+        d.pair_units[mode].push_back(u);
+      }
+      for (int half = 0; half < (c.a1 ? 4 : 2); ++half) {
+        const int row0 = c.r0 + (half < 2 ? 0 : 2 * kTcBM) + kTcBM * (half & 1);
+        if (row0 >= m) continue;
+        RedTile r{};
+        r.part = slot(half, 0);
+        r.M = pl->d_M;
+        r.Y = pl->d_Y;
+        r.oa = pl->d_oa;
+        r.ob = pl->d_ob;
+        r.slot_elems = pl->slot_elems;
+        r.i0 = row0;
+        r.ni = std::min(kTcBM, m - row0);
+        r.count = L;
+        r.ld = kTcLd;
+        r.m = m;
+        r.cloud = 0;
+        if (half < 2 || c.g2) {
+          r.j0 = c.c0;
+          r.nj = c.nc;
+          r.kind = kTileGram;
+          r.col_off = 0;
+          d.pair_red[mode].push_back(r);
+        }
+        if (c.f) {
+          r.j0 = m;
+          r.nj = cpad;
+          r.fsplit = pl->fsplit ? 1 : 0;
+          r.kind = kTileField;
+          r.col_off = kTcBNMax;
+          d.pair_red[mode].push_back(r);
+        }
+      }
+      base += (int64_t)(c.a1 ? 4 : 2) * L;
+    }
+    if (base > pl->part_slots) return fail(RFD_ECUDA, "internal: pair partial slots exceed their allocation");
+  }
+  d.pair_stage_bytes = gram_pair_stage_bytes(max_nc, cpad);
+  return RFD_OK;
+}
+
 // split-K lanes per compute tile, rounded mean over the tiles (0 without units)
 int mean_lanes(const std::vector<TcUnit>& units) {
   int tiles = 0;
@@ -363,6 +520,7 @@ rfd_status build_desc(rfd_plan_s* pl) {
     }
     if (base > pl->part_slots) return fail(RFD_ECUDA, "internal: Gram partial slots exceed their allocation");
   }
+  if (rfd_status ps = build_pair_desc(pl); ps != RFD_OK) return ps;
   auto* psi = static_cast<__nv_bfloat16_raw*>(pl->d_psi);
   d.feat = FeatJob{pl->n, pl->n_pad, pl->d_omega_hi, psi, pl->d_xyz, pl->h, (int)((pl->n_pad + 511) / 512), 0,
                    pl->rows_alloc};
@@ -397,7 +555,7 @@ rfd_status build_desc(rfd_plan_s* pl) {
   pc.scale = 1.0;
   pc.map_a = 3;
   pc.map_b = 4;
-  if (!make_gram_maps(d.maps[0], d.maps[5], pl->d_psi, pl->n_pad, m, pl->cpad, pl->rows_alloc))
+  if (!make_gram_maps(d.maps[0], d.maps[5], d.maps[6], pl->d_psi, pl->n_pad, m, pl->cpad, pl->rows_alloc))
     return fail(RFD_ECUDA, "tensor-map encoding of the feature matrix failed");
   if (!make_ozaki_maps(d.maps[3], d.maps[4], pc.sa, pc.sb, pc.mpa, pc.mpb, pc.kp))
     return fail(RFD_ECUDA, "tensor-map encoding of the FP64-emulation residues failed");
@@ -484,14 +642,17 @@ struct CallScope {
 // Picks the launch parameters of the tensor-core reductions by timing them on
 // the cloud's own features after its first features pass: split-K lanes of a
 // lone cloud (50 / 100 / 200 % of SMs per tile) or the waves a batch plans
-// for (2 / 4 / 8), times the phase length of the point axis (2048 / 4096 /
-// 8192 blocks of 64 points).  Choices are kept per bucket -- (m, log2 of the
+// for (2 / 4 / 8), times the phase length of the point axis (1024 / 2048 /
+// 4096 / 8192 blocks of 64 points; for a lone cloud with several phases the
+// features run beside the Gram, phase by phase, and are timed with it), and
+// for a lone cloud with m >= 512 both forms of the Gram (one SM per tile, or
+// CTA pairs).  Choices are kept per bucket -- (m, log2 of the
 // point blocks, field width) for plans, (clouds, log2 of the work) for batches
 // -- and reused without timing by later plans / batches of the same bucket.
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, GramTuning> g_plan_tune;
 std::map<std::pair<int, int>, GramTuning> g_batch_tune;
-constexpr int kTunePhases[3] = {2048, 4096, 8192};
+constexpr int kTunePhases[4] = {1024, 2048, 4096, 8192};
 
 int ilog2(double x) { return x < 1.0 ? 0 : (int)std::floor(std::log2(x)); }
 
@@ -513,7 +674,7 @@ rfd_status rebuild_self(rfd_plan_s* pl) {
   return RFD_OK;
 }
 
-rfd_status tune_plan(rfd_plan_s* pl, int mode) {
+rfd_status tune_plan(rfd_plan_s* pl, int mode, const CloudCall* cc) {
   const auto key = std::make_tuple(pl->m, ilog2((double)(pl->n_pad / kTcBK)), pl->cpad);
   pl->tuned = true;
   {
@@ -527,28 +688,30 @@ rfd_status tune_plan(rfd_plan_s* pl, int mode) {
   RFD_CUDA(cudaStreamSynchronize(pl->stream));  // the features of the first pass are in place
   float best = 1e30f;
   GramTuning best_t = pl->tune;
-  for (int lp : {50, 100, kTuneLanesMax}) {
-    pl->tune.lanes_pct = lp;
-    rfd_status s = build_desc(pl);
-    BatchImpl* tb = nullptr;
-    rfd_plan_s* self = pl;
-    if (s == RFD_OK) s = batch_build(&self, 1, pl->stream, cuda_mem(), 0, pl->tune, &tb);
-    if (s != RFD_OK) return s;
-    for (int ph : kTunePhases) {
-      batch_set_phase(tb, ph);
-      float ms = 0.f;
-      s = batch_time_gram(tb, mode, 2, &ms);
-      if (s != RFD_OK) break;
-      if (ms < best) {
-        best = ms;
-        best_t = pl->tune;
-        best_t.phase_blocks = ph;
+  for (int form = 0; form < (pair_eligible(pl) ? 2 : 1); ++form)
+    for (int lp : {50, 100, kTuneLanesMax}) {
+      pl->tune.lanes_pct = lp;
+      pl->tune.pairs = form;
+      rfd_status s = build_desc(pl);
+      BatchImpl* tb = nullptr;
+      rfd_plan_s* self = pl;
+      if (s == RFD_OK) s = batch_build(&self, 1, pl->stream, cuda_mem(), 0, pl->tune, &tb);
+      if (s != RFD_OK) return s;
+      for (int ph : kTunePhases) {
+        batch_set_phase(tb, ph);
+        float ms = 0.f;
+        s = batch_time_gram(tb, mode, 2, &ms, cc);
+        if (s != RFD_OK) break;
+        if (ms < best) {
+          best = ms;
+          best_t = pl->tune;
+          best_t.phase_blocks = ph;
+        }
       }
+      cudaStreamSynchronize(pl->stream);
+      batch_free(tb);
+      if (s != RFD_OK) return s;
     }
-    cudaStreamSynchronize(pl->stream);
-    batch_free(tb);
-    if (s != RFD_OK) return s;
-  }
   pl->tune = best_t;
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
@@ -563,7 +726,7 @@ rfd_status run_plan(rfd_plan_s* pl, int mode, const float* pts, const float* F, 
   if (pl->bf16) {
     CloudCall cc{pts, F, out, ldF, ldOut, c, 0};
     rfd_status s = batch_run(pl->self, mode, &cc, &pl->timing);
-    if (s == RFD_OK && pl->autotune && !pl->tuned && mode != kModeIntegrate) s = tune_plan(pl, mode);
+    if (s == RFD_OK && pl->autotune && !pl->tuned && mode != kModeIntegrate) s = tune_plan(pl, mode, &cc);
     return s;
   }
   cudaStream_t st = pl->stream;
@@ -718,7 +881,11 @@ rfd_status plan_prepare(const rfd_params& p, cudaStream_t stream, rfd_plan_s** o
     build_tiles_simt(pl, true, true, pl->both);
   }
   pl->autotune = pl->bf16 && (p.flags & RFD_FLAG_AUTOTUNE);
-  pl->part_slots = pl->bf16 ? tc_partial_slots(pl->m, pl->cpad, pl->n_pad, pl->sms, pl->autotune ? kTuneLanesMax : 100)
+  pl->part_slots = pl->bf16 ? std::max(tc_partial_slots(pl->m, pl->cpad, pl->n_pad, pl->sms,
+                                                         pl->autotune ? kTuneLanesMax : 100),
+                                        pair_eligible(pl) ? pair_partial_slots(pl->m, pl->n_pad, pl->cpad, pl->sms,
+                                                                               pl->autotune ? kTuneLanesMax : 100)
+                                                          : 0)
                             : std::max({pl->gram_only.slots, pl->field_only.slots, pl->both.slots});
   pl->slot_elems = pl->bf16 ? (int64_t)kTcBM * kTcLd : (int64_t)kSimtTile * kSimtTile;
   pl->rows_alloc = (int)std::max<int64_t>(round_up(p.m, 128), p.m + round_up(pl->cpad, 128));
@@ -916,6 +1083,7 @@ rfd_status rfd_plan_stats(rfd_plan_t pl, rfd_stats* out) {
   out->tune_lanes_pct = pl->tune.lanes_pct;
   out->tune_waves = pl->tune.waves;
   out->tune_phase_blocks = pl->tune.phase_blocks;
+  out->tune_pair_gram = pl->tune.pairs;
   out->tuned = pl->tuned ? 1 : 0;
   return RFD_OK;
 }
@@ -972,7 +1140,7 @@ rfd_status rfd_batch_destroy(rfd_batch_t b) {
 }
 
 // Batch autotuning (see tune_plan): waves x phase length, timed on the batch's own features.
-static rfd_status tune_batch(rfd_batch_t b, int mode) {
+static rfd_status tune_batch(rfd_batch_t b, int mode, const CloudCall* calls) {
   b->tuned = true;
   double work = 0.0;
   for (rfd_plan_s* pl : b->plans) work += (double)pl->desc.units[kModeGfi].size() * (double)(pl->n_pad / kTcBK);
@@ -999,7 +1167,7 @@ static rfd_status tune_batch(rfd_batch_t b, int mode) {
       for (int ph : kTunePhases) {
         batch_set_phase(tb, ph);
         float ms = 0.f;
-        s = batch_time_gram(tb, mode, 2, &ms);
+        s = batch_time_gram(tb, mode, 2, &ms, calls);
         if (s != RFD_OK) break;
         if (ms < best) {
           best = ms;
@@ -1043,7 +1211,7 @@ static rfd_status batch_call(rfd_batch_t b, int mode, const rfd_batch_item* item
   }
   CallScope call(&b->timing, b->stream);
   rfd_status s = batch_run(b->impl, mode, calls.data(), &b->timing);
-  if (s == RFD_OK && b->autotune && !b->tuned && mode != kModeIntegrate) s = tune_batch(b, mode);
+  if (s == RFD_OK && b->autotune && !b->tuned && mode != kModeIntegrate) s = tune_batch(b, mode, calls.data());
   return s;
 }
 
@@ -1111,6 +1279,8 @@ rfd_status rfd_debug_plan_phi1(rfd_plan_t pl, const double* d_M) {
   RFD_CUDA(cudaStreamSynchronize(pl->stream));
   return check_device_error(pl);
 }
+
+void rfd_debug_gram_pairs(int32_t enable) { g_gram_pairs.store(enable ? 1 : 0); }
 
 rfd_status rfd_debug_plan_set_phase(rfd_plan_t pl, int32_t phase_blocks) {
   if (!pl) return fail(RFD_EINVAL, "null plan");

@@ -70,6 +70,9 @@ struct BatchImpl {
   void* d_maps = nullptr;
   TcUnit* d_units[3] = {};
   int n_units[3] = {};
+  PairUnit* d_pair[3] = {};  // a lone cloud with m >= 512: the 2-SM form of the Gram modes
+  int n_pair[3] = {};
+  int pair_stage_bytes = 0;
   RedTile* d_red[3] = {};
   int n_red[3] = {};
   FeatJob* d_feat = nullptr;
@@ -116,6 +119,11 @@ struct BatchImpl {
   int* h_sv = nullptr;
   int* h_flags = nullptr;  // followed by the error word
   cudaEvent_t ev_mid = nullptr;
+  // features beside the Gram (a lone cloud with several point-axis phases): a side
+  // stream runs the features of phase p + 1 while the main stream runs the Gram of phase p
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_phase;  // features of phase p done
   // CUDA graphs (kBatchGraphs)
   cudaStream_t cap = nullptr;  // capture-only stream (the caller's stream may be the legacy one)
   struct Graph {
@@ -136,6 +144,9 @@ void batch_free(BatchImpl* b) {
   for (int i = 0; i < BatchImpl::kStageRing; ++i)
     if (b->stage_done[i]) cudaEventDestroy(b->stage_done[i]);
   if (b->ev_mid) cudaEventDestroy(b->ev_mid);
+  for (cudaEvent_t e : b->ev_phase) cudaEventDestroy(e);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->side) cudaStreamDestroy(b->side);
   if (b->dblob) b->mem->dev_free(b->dblob);
   if (b->hblob) b->mem->pinned_free(b->hblob);
   delete b;
@@ -164,6 +175,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
       if (u.lane == 0) work += (double)u.work * (double)(plans[k]->n_pad / kTcBK);
   const double target = (count == 1) ? 1e300 : std::max(1.0, work / (tune.waves * (double)sms));  // clocks per CTA
   std::vector<TcUnit> units[3];
+  std::vector<PairUnit> pairs[3];
   std::vector<RedTile> red[3];
   std::vector<unsigned char> maps((size_t)count * kMapsPerCloud * kTensorMapBytes);
   std::vector<FeatJob> feat;
@@ -182,6 +194,12 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
     std::memcpy(maps.data() + (size_t)k * kMapsPerCloud * kTensorMapBytes, d.maps, sizeof(d.maps));
     const int64_t kb = pl->n_pad / kTcBK;
     for (int mode = 0; mode < 3; ++mode) {
+      if (count == 1 && tune.pairs && !d.pair_units[mode].empty()) {  // a lone cloud: the plan's pair units
+        pairs[mode] = d.pair_units[mode];
+        red[mode] = d.pair_red[mode];
+        b->pair_stage_bytes = d.pair_stage_bytes;
+        continue;
+      }
       // the plan's own units give each tile L_plan lanes; a batch may give it fewer
       const std::vector<TcUnit>& pu = d.units[mode];
       if (pu.empty()) continue;
@@ -277,11 +295,13 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   };
   auto vtable = [&](const auto& v) { return table(v.data(), v.size() * sizeof(v[0])); };
   const size_t o_maps = vtable(maps);
-  size_t o_units[3], o_red[3];
+  size_t o_units[3], o_pair[3], o_red[3];
   for (int mode = 0; mode < 3; ++mode) {
     o_units[mode] = vtable(units[mode]);
+    o_pair[mode] = vtable(pairs[mode]);
     o_red[mode] = vtable(red[mode]);
     b->n_units[mode] = (int)units[mode].size();
+    b->n_pair[mode] = (int)pairs[mode].size();
     b->n_red[mode] = (int)red[mode].size();
   }
   const size_t o_feat = vtable(feat), o_feat_pre = vtable(pre_feat), o_fill = vtable(fill),
@@ -311,6 +331,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   b->d_maps = D + o_maps;
   for (int mode = 0; mode < 3; ++mode) {
     b->d_units[mode] = reinterpret_cast<TcUnit*>(D + o_units[mode]);
+    b->d_pair[mode] = reinterpret_cast<PairUnit*>(D + o_pair[mode]);
     b->d_red[mode] = reinterpret_cast<RedTile*>(D + o_red[mode]);
   }
   b->d_feat = reinterpret_cast<FeatJob*>(D + o_feat);
@@ -343,8 +364,13 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   for (int i = 0; i < BatchImpl::kStageRing && e == cudaSuccess; ++i)
     e = cudaEventCreateWithFlags(&b->stage_done[i], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_mid, cudaEventDisableTiming);
+  if (e == cudaSuccess && count == 1) {
+    e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  }
   if (e == cudaSuccess && (options & kBatchGraphs)) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = gram_tc_prepare();
+  if (e == cudaSuccess && b->n_pair[0] + b->n_pair[1] + b->n_pair[2] > 0) e = gram_pair_prepare();
   if (e == cudaSuccess) e = bgemm_prepare();
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -533,6 +559,69 @@ rfd_status run_segment(BatchImpl* b, const int (&key)[4], bool graph, Timing* tm
 
 }  // namespace
 
+// One phase of the reductions over N of `mode`: the 2-SM pair kernel when the batch
+// has pair units for the mode, else the one-SM kernel.
+cudaError_t gram_phase(BatchImpl* b, int mode, int kb0, cudaStream_t s) {
+  if (b->n_pair[mode] > 0)
+    return launch_gram_pair_phase(b->d_maps, b->d_pair[mode], b->n_pair[mode], b->pair_stage_bytes, kb0,
+                                  b->phase_blocks, b->d_err, s);
+  return launch_gram_tc_phase(b->d_maps, b->d_units[mode], b->n_units[mode], b->a_boxes, kb0, b->phase_blocks,
+                              b->d_err, s);
+}
+// All phases of the reductions over N of `mode`, one launch each.
+cudaError_t gram_all(BatchImpl* b, int mode, cudaStream_t s) {
+  const int phases = b->max_kb > 0 ? (b->max_kb + b->phase_blocks - 1) / b->phase_blocks : 1;
+  for (int p = 0; p < phases; ++p) {
+    const cudaError_t e = gram_phase(b, mode, p * b->phase_blocks, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Features beside the Gram: a lone cloud whose point axis takes several Gram
+// phases (of a multiple of 8 blocks, so that the 512-point blocks of the
+// features kernel fall in one phase) runs its features phase by phase on the
+// side stream; the Gram of phase p waits for the features of phase p only, so
+// the features of phase p + 1 (MUFU and HBM writes) overlap the Gram of phase
+// p (tensor cores and L2 reads).
+int gram_phases(const BatchImpl* b) {
+  return b->max_kb > 0 ? (b->max_kb + b->phase_blocks - 1) / b->phase_blocks : 1;
+}
+bool pipelines(const BatchImpl* b) { return b->side && gram_phases(b) >= 2 && b->phase_blocks % 8 == 0; }
+
+// The features, phase by phase, on the side stream (forked from s); ev_phase[p]
+// marks phase p done.  The last event is recorded after the step's timing scope.
+rfd_status pipelined_features(BatchImpl* b, cudaStream_t s, Timing* t) {
+  const int phases = gram_phases(b);
+  while ((int)b->ev_phase.size() < phases) {
+    cudaEvent_t e = nullptr;
+    BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    b->ev_phase.push_back(e);
+  }
+  const rfd_plan_s* pl = b->plans[0];
+  const int bx = pl->desc.feat.bx, per = b->phase_blocks / 8;  // 512-point blocks per phase
+  BCK(cudaEventRecord(b->ev_fork, s));
+  BCK(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+  {
+    StepScope sc(t, b->side, RFD_STEP_FEATURES);
+    for (int p = 0; p < phases; ++p) {
+      BCK(launch_features_range(b->d_feat, b->d_calls, pl->h, p * per, std::min(per, bx - p * per), b->side));
+      if (p + 1 < phases) BCK(cudaEventRecord(b->ev_phase[p], b->side));
+    }
+  }
+  BCK(cudaEventRecord(b->ev_phase[phases - 1], b->side));
+  return RFD_OK;
+}
+
+// The Gram phases on s, each after the features of its phase (pipelined_features first).
+rfd_status pipelined_gram(BatchImpl* b, int mode, cudaStream_t s) {
+  for (int p = 0; p < gram_phases(b); ++p) {
+    BCK(cudaStreamWaitEvent(s, b->ev_phase[p], 0));
+    BCK(gram_phase(b, mode, p * b->phase_blocks, s));
+  }
+  return RFD_OK;
+}
+
 rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm) {
   cudaStream_t st = b->st;
   const bool gram_only = mode == kModeGram;
@@ -564,7 +653,22 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   const bool with_apply = mode != kModeFeatures;
   const bool graph = (b->options & kBatchGraphs) && (!with_phi || b->phi_batched);
 
+  const bool pipelined = with_feat && pipelines(b);
   auto reductions = [&](cudaStream_t s, Timing* t) -> rfd_status {
+    if (pipelined) {
+      if (rfd_status q = pipelined_features(b, s, t); q != RFD_OK) return q;
+      if (with_apply) {
+        StepScope sc(t, s, RFD_STEP_FIELD);
+        BCK(launch_fill_batched(b->d_fill, b->d_fill_prefix, n, b->fill_blocks, b->d_calls, s));
+      }
+      {
+        StepScope sc(t, s, RFD_STEP_GRAM);
+        if (rfd_status q = pipelined_gram(b, mode, s); q != RFD_OK) return q;
+      }
+      StepScope sc(t, s, RFD_STEP_REDUCE);
+      BCK(launch_reduce_batched(b->d_red[mode], b->n_red[mode], b->d_calls, s));
+      return RFD_OK;
+    }
     if (with_feat) {
       StepScope sc(t, s, RFD_STEP_FEATURES);
       BCK(launch_features_batched(b->d_feat, b->d_feat_prefix, n, b->feat_blocks, b->d_calls, s));
@@ -575,8 +679,7 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
     }
     {
       StepScope sc(t, s, RFD_STEP_GRAM);
-      BCK(launch_gram_tc(b->d_maps, b->d_units[mode], b->n_units[mode], b->a_boxes, b->max_kb, b->phase_blocks,
-                         b->d_err, s));
+      BCK(gram_all(b, mode, s));
     }
     StepScope sc(t, s, RFD_STEP_REDUCE);
     BCK(launch_reduce_batched(b->d_red[mode], b->n_red[mode], b->d_calls, s));
@@ -738,13 +841,28 @@ void Timing::reset(cudaStream_t st) {
 
 void batch_set_phase(BatchImpl* b, int phase_blocks) { b->phase_blocks = phase_blocks; }
 
-rfd_status batch_time_gram(BatchImpl* b, int mode, int reps, float* ms) {
+rfd_status batch_time_gram(BatchImpl* b, int mode, int reps, float* ms, const CloudCall* calls) {
+  // the call table of this batch: the features beside the Gram read the callers' points
+  {
+    const int slot = b->stage_next;
+    b->stage_next = (slot + 1) % BatchImpl::kStageRing;
+    BCK(cudaEventSynchronize(b->stage_done[slot]));
+    std::memcpy(b->h_stage[slot], calls, (size_t)b->count * sizeof(CloudCall));
+    BCK(cudaMemcpyAsync(b->d_calls, b->h_stage[slot], (size_t)b->count * sizeof(CloudCall), cudaMemcpyHostToDevice,
+                        b->st));
+    BCK(cudaEventRecord(b->stage_done[slot], b->st));
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
-  auto launch = [&] {
-    return launch_gram_tc(b->d_maps, b->d_units[mode], b->n_units[mode], b->a_boxes, b->max_kb, b->phase_blocks,
-                          b->d_err, b->st);
+  // with features beside the Gram, time both together (the phase length trades the first
+  // phase's exposed features against the launches of more phases)
+  const bool pipe = mode != kModeIntegrate && pipelines(b);
+  auto launch = [&]() -> cudaError_t {
+    if (!pipe) return gram_all(b, mode, b->st);
+    if (pipelined_features(b, b->st, nullptr) != RFD_OK || pipelined_gram(b, mode, b->st) != RFD_OK)
+      return cudaErrorLaunchFailure;
+    return cudaSuccess;
   };
   cudaError_t e = launch();  // warm-up
   if (e == cudaSuccess) e = cudaEventRecord(e0, b->st);

@@ -12,7 +12,9 @@ namespace rfd {
 
 constexpr int kRing = 64;
 constexpr int kTensorMapBytes = 128;
-constexpr int kMapsPerCloud = 6;  // Gram A / B (64-row box) / F maps, Ozaki slice maps A / B, Gram B (16-row box)
+// Gram A / B (64-row box) / F maps, Ozaki slice maps A / B, Gram B (16-row box), and the
+// pair kernel's B (8-row box) and F (half-width box) maps
+constexpr int kMapsPerCloud = 8;
 
 // CUDA-event timing of the path's steps (RFD_FLAG_TIMING): a ring of per-call
 // event sets, folded into per-step sums when the stream is synchronised.
@@ -74,6 +76,11 @@ constexpr int kModeGram = 3;
 struct PlanDesc {
   std::vector<TcUnit> units[3];    // indexed by Mode
   std::vector<RedTile> red[3];
+  // the 2-SM form of the Gram modes (features, gfi) for m >= 512: pair units and their
+  // reduce tiles (partials final for the plan's own lanes; used by the plan's batch of one)
+  std::vector<PairUnit> pair_units[3];
+  std::vector<RedTile> pair_red[3];
+  int pair_stage_bytes = 0;
   FeatJob feat{};
   FillJob fill{};
   ApplyJob apply{};
@@ -100,11 +107,13 @@ enum : int { kBatchGraphs = 1 };  // replay the batch's launches from CUDA graph
 
 // Launch parameters of the tensor-core reductions that the autotuner varies:
 // the split-K lanes of a lone cloud (percent of SMs / tiles), the waves of CTAs
-// a batch plans for, and the phase length of the point axis.
+// a batch plans for, the phase length of the point axis, and (a lone cloud
+// with m >= 512) the one-SM or the CTA-pair form of the Gram.
 struct GramTuning {
   int lanes_pct = 100;
   int waves = 4;
   int phase_blocks = kGramPhaseBlocks;
+  int pairs = 0;  // a lone cloud with m >= 512: the Gram modes on CTA pairs (k_gram_pair.cu)
 };
 
 }  // namespace rfd
@@ -186,8 +195,10 @@ rfd_status batch_eigenvalues(rfd_plan_s* const* plans, int count, int k, int lar
 // bad is given).
 rfd_status batch_check_error(BatchImpl* b, int* bad = nullptr);
 // Times the Gram launches of one batched call of `mode` (the features must be
-// in place): mean ms over `reps` launches after one warm-up.
-rfd_status batch_time_gram(BatchImpl* b, int mode, int reps, float* ms);
+// in place; for a lone cloud whose features run beside the Gram, those too,
+// from the points of calls, one CloudCall per plan): mean ms over `reps`
+// launches after one warm-up.
+rfd_status batch_time_gram(BatchImpl* b, int mode, int reps, float* ms, const CloudCall* calls);
 void batch_set_phase(BatchImpl* b, int phase_blocks);
 
 }  // namespace rfd
