@@ -285,6 +285,26 @@ RFD_API rfd_status rfd_eigenvalues(rfd_plan_t plan, int32_t k, int32_t largest, 
 RFD_API rfd_status rfd_gfi(rfd_plan_t plan, const float* d_points, const float* d_F, int32_t c,
                    int64_t ldF, float* d_out, int64_t ldOut);
 
+/* Keep a BF16 plan resident at a fraction of its memory (inference on a resident
+ * cloud, Sec. 2.4: "linear in N, quadratic in m").  After rfd_features or
+ * rfd_gfi, the plan's feature matrix Phi (2 (m + field rows) N bytes), its
+ * split-K partials and its FP64 phi1 workspace are released; it keeps its copy
+ * of the points, the frequencies and column scales, M and G, and a small
+ * partial buffer (at most 16 MB).  Later rfd_integrate calls recompute the
+ * features from the points in FP32 for both B^T F and the apply (the BF16
+ * rounding of Phi in B^T F is then gone: results agree with the full plan's
+ * within the BF16 form's tolerance and with the FP64 oracle more closely).
+ * rfd_features / rfd_gfi on a compact plan return RFD_EINVAL (create a new
+ * plan); rfd_integrate, rfd_barycenter, rfd_fm_apply, the GW calls and
+ * rfd_eigenvalues work as before.  Allocates the compact chunk before
+ * releasing the full one (RFD_ENOMEM leaves the plan unchanged); synchronises
+ * the plan's stream.  RFD_EINVAL for FP32 plain plans or before G exists;
+ * a compact plan stays compact (a second call does nothing). */
+RFD_API rfd_status rfd_plan_compact(rfd_plan_t plan);
+
+/* Device bytes the plan holds now (its chunk: the full or the compact form). */
+RFD_API rfd_status rfd_plan_device_bytes(rfd_plan_t plan, int64_t* bytes_out);
+
 /* Step a4 alone: G = lambda phi1(lambda M) for an m x m FP64 matrix M
  * (Sec. 2.4: [exp(lambda M) - I] M^{-1}, evaluated without the inverse),
  * by the same scaling-and-squaring Pade evaluation rfd_features uses.
@@ -388,9 +408,10 @@ RFD_API rfd_status rfd_batch_eigenvalues(rfd_batch_t batch, const rfd_batch_item
  * tensor-core batched path.  Several batches are in flight at once on
  * separate streams, so requests that arrive while others run are started as
  * soon as an executor and memory free up.  A request that names a resident
- * cloud reuses its features Phi and its G (only steps a3(Y)-a6 run); clouds
- * submitted with keep = 1 stay resident until memory is needed (least
- * recently used first) or the server is destroyed.
+ * cloud reuses its G (only steps a3(Y)-a6 run); clouds submitted with keep = 1
+ * stay resident, in the compact form of rfd_plan_compact (points, frequencies,
+ * M, G), until memory is needed (least recently used first) or the server is
+ * destroyed.
  * --------------------------------------------------------------------------- */
 typedef struct rfd_server_s* rfd_server_t;
 
@@ -412,15 +433,17 @@ typedef struct {
   int32_t c;             /* 1 <= c <= 256                                               */
   double eps, lambda;    /* as rfd_params                                               */
   uint64_t seed;
-  uint64_t cloud;        /* 0, or an id returned by an earlier request: reuse that cloud */
-  int32_t keep;          /* 1: keep this request's cloud resident, its id in rfd_result */
+  uint64_t cloud;        /* 0, or a resident cloud to reuse: its id is the ticket of the
+                            request that kept it (keep = 1), which may still be pending:
+                            this request then waits for it                             */
+  int32_t keep;          /* 1: keep this request's cloud resident (id = this ticket)   */
   int32_t max_channels;  /* channel capacity of a kept cloud for later requests (0: c)  */
 } rfd_request;
 
 typedef struct {
   int32_t status;        /* the request's own outcome (an rfd_status)                   */
   int32_t reused;        /* 1 if a resident cloud's Phi and G were reused              */
-  uint64_t cloud;        /* id of the resident cloud (keep = 1 or reuse), else 0       */
+  uint64_t cloud;        /* id of the resident cloud (keep = 1: this ticket; reuse), else 0 */
   double queue_ms;       /* rfd_submit -> its batch's launch                            */
   double latency_ms;     /* rfd_submit -> the server saw its batch complete            */
   int32_t batch_size;    /* requests in the batch that ran it                          */

@@ -129,6 +129,8 @@ def _load():
         "rfd_plan_export": (I32, [P, DP, DP, DP]),
         "rfd_plan_stats": (I32, [P, ctypes.POINTER(rfd_stats)]),
         "rfd_plan_stats_reset": (I32, [P]),
+        "rfd_plan_compact": (I32, [P]),
+        "rfd_plan_device_bytes": (I32, [P, ctypes.POINTER(I64)]),
         "rfd_last_error": (ctypes.c_char_p, []),
         "rfd_version": (ctypes.c_char_p, []),
         "rfd_debug_fail_alloc_after": (None, [I32]),
@@ -164,7 +166,8 @@ lib = _load()
 # Every function include/rfd.h and include/rfd_testing.h declare (checked against the headers by a test).
 HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_sample_weights", "rfd_barycenter", "rfd_fm_apply",
                   "rfd_gw_tensor_product", "rfd_gw_line_search", "rfd_eigenvalues", "rfd_batch_eigenvalues", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
-                  "rfd_gfi", "rfd_phi1", "rfd_phi1_noalloc", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_last_error",
+                  "rfd_gfi", "rfd_phi1", "rfd_phi1_noalloc", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_plan_compact",
+                  "rfd_plan_device_bytes", "rfd_last_error",
                   "rfd_version", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "rfd_debug_plan_phi1", "rfd_debug_plan_set_phase",
                   "rfd_debug_plan_wait_timeout", "rfd_debug_gram_pairs", "rfd_batch_create",
                   "rfd_batch_destroy", "rfd_batch_features", "rfd_batch_integrate", "rfd_batch_gfi",
@@ -388,6 +391,15 @@ class Plan:
 
     def stats_reset(self):
         rfd_plan_stats_reset(self.handle)
+
+    def compact(self):
+        """Release Phi, the partials and the phi1 workspace (rfd_plan_compact)."""
+        _check(lib.rfd_plan_compact(self.handle), "rfd_plan_compact")
+
+    def device_bytes(self) -> int:
+        v = ctypes.c_int64(0)
+        _check(lib.rfd_plan_device_bytes(self.handle, ctypes.byref(v)), "rfd_plan_device_bytes")
+        return v.value
 
     def close(self):
         if self.handle:

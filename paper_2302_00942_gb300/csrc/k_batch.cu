@@ -311,6 +311,71 @@ apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ 
       }
 }
 
+// Y' partials from the points (compact plans, see FieldPtsJob): a thread per
+// frequency f (256 per block), one chunk of points and CG channels per block.
+// The points and the block's F columns pass through shared memory 128 points
+// at a time (every thread reads the same point: broadcasts); Phi(n, f) is the
+// apply's FP32 feature (angle reduced in cycles, MUFU sin / cos).
+template <int CG>
+__global__ void __launch_bounds__(256)
+fieldpts_batched_kernel(const FieldPtsJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
+                        const CloudCall* __restrict__ calls) {
+  constexpr int kTile = 128;
+  __shared__ float xs[kTile][3];
+  __shared__ float fs[kTile][CG];
+  const int j = find_job(prefix, count, blockIdx.x);
+  const FieldPtsJob jb = jobs[j];
+  const CloudCall cc = calls[jb.cloud];
+  const int fgroups = (jb.h + 255) / 256;
+  const int local = blockIdx.x - prefix[j];
+  const int chunk = local % jb.chunks, rest = local / jb.chunks;
+  const int fg = rest % fgroups, cgi = rest / fgroups;
+  const int f = fg * 256 + threadIdx.x;
+  const bool fvalid = f < jb.h;
+  const int ch0 = cgi * CG, cg = min(CG, cc.c - ch0);
+  float w0 = 0.f, w1 = 0.f, w2 = 0.f;
+  if (fvalid) {
+    w0 = jb.omega_hi[(size_t)f * 3];
+    w1 = jb.omega_hi[(size_t)f * 3 + 1];
+    w2 = jb.omega_hi[(size_t)f * 3 + 2];
+  }
+  float acc_c[CG], acc_s[CG];
+#pragma unroll
+  for (int q = 0; q < CG; ++q) acc_c[q] = acc_s[q] = 0.f;
+  const float two_pi = 6.283185307179586f;
+  const int64_t p_begin = (int64_t)chunk * jb.pts, p_end = min(jb.n, p_begin + jb.pts);
+  for (int64_t p0 = p_begin; p0 < p_end; p0 += kTile) {
+    const int np = (int)min((int64_t)kTile, p_end - p0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < np * 3; i += blockDim.x) xs[i / 3][i % 3] = jb.xyz[p0 * 3 + i];
+    for (int i = threadIdx.x; i < np * CG; i += blockDim.x) {
+      const int pp = i / CG, q = i % CG;
+      fs[pp][q] = q < cg ? cc.F[(p0 + pp) * cc.ldF + ch0 + q] : 0.f;
+    }
+    __syncthreads();
+    if (fvalid)
+      for (int pp = 0; pp < np; ++pp) {
+        const float t = fmaf(w0, xs[pp][0], fmaf(w1, xs[pp][1], w2 * xs[pp][2]));
+        const float ang = two_pi * (t - round_int(t));
+        const float cs = __cosf(ang), sn = __sinf(ang);
+#pragma unroll
+        for (int q = 0; q < CG; ++q) {
+          acc_c[q] = fmaf(cs, fs[pp][q], acc_c[q]);
+          acc_s[q] = fmaf(sn, fs[pp][q], acc_s[q]);
+        }
+      }
+  }
+  if (!fvalid) return;
+  float* pc = jb.part + ((size_t)chunk * jb.m + f) * jb.ld + ch0;
+  float* ps = jb.part + ((size_t)chunk * jb.m + jb.h + f) * jb.ld + ch0;
+#pragma unroll
+  for (int q = 0; q < CG; ++q)
+    if (q < cg) {
+      pc[q] = acc_c[q];
+      ps[q] = acc_s[q];
+    }
+}
+
 __device__ __forceinline__ const double* slot_ptr(const PhiCloud& pc, int slot) {
   return slot == kSlotM ? pc.M : (slot == kSlotG ? pc.G : pc.work + (size_t)slot * pc.m * pc.m);
 }
@@ -448,6 +513,20 @@ cudaError_t launch_apply_batched(const ApplyJob* jobs, const int* prefix, int co
     case 8: apply_batched_kernel<8><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
     case 16: apply_batched_kernel<16><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
     case 32: apply_batched_kernel<32><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return launched();
+}
+
+cudaError_t launch_fieldpts_batched(const FieldPtsJob* jobs, const int* prefix, int count, int total_blocks, int cg,
+                                    const CloudCall* calls, cudaStream_t st) {
+  if (total_blocks <= 0) return cudaSuccess;
+  switch (cg) {
+    case 3: fieldpts_batched_kernel<3><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
+    case 4: fieldpts_batched_kernel<4><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
+    case 8: fieldpts_batched_kernel<8><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
+    case 16: fieldpts_batched_kernel<16><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
+    case 32: fieldpts_batched_kernel<32><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
     default: return cudaErrorInvalidValue;
   }
   return launched();

@@ -244,6 +244,17 @@ struct FillJob {
   int32_t cpad, bx, cloud, fsplit;  // bx: 256-point blocks
   int32_t row0, rows_alloc;         // F rows start at row0 (= m) of the blocked buffer
 };
+// Y' = Phi^T F from the points, for a compact plan (no feature matrix): per
+// chunk of `pts` points, part[chunk][f][ch] = sum_n Phi(n, f) F[n, ch] with
+// Phi recomputed in FP32 exactly as the apply does (rows f < h cos, h + f sin);
+// part is [chunks][m][ld] floats, summed over the chunks by the reduce kernel.
+struct FieldPtsJob {
+  const float* xyz;       // the plan's copy of the points (N x 3)
+  const float* omega_hi;  // h x 3
+  float* part;
+  int64_t n, pts;
+  int32_t h, m, chunks, ld, cloud, pad_;
+};
 // One output tile of the split-K reduction (absolute pointers).
 struct RedTile {
   const float* part;    // partial of lane 0; lane l at part + l * slot_elems
@@ -308,6 +319,14 @@ cudaError_t launch_features_range(const FeatJob* jobs, const CloudCall* calls, i
 cudaError_t launch_fill_batched(const FillJob* jobs, const int* prefix, int count, int total_blocks,
                                 const CloudCall* calls, cudaStream_t st);
 cudaError_t launch_reduce_batched(const RedTile* tiles, int num_tiles, const CloudCall* calls, cudaStream_t st);
+// Y' partials of compact plans from their points: cg channels per block (3, 4, 8, 16 or 32);
+// prefix over chunks x ceil(h / 256) x ceil(c / cg) blocks per cloud.
+cudaError_t launch_fieldpts_batched(const FieldPtsJob* jobs, const int* prefix, int count, int total_blocks, int cg,
+                                    const CloudCall* calls, cudaStream_t st);
+// blocks of one cloud's fieldpts launch for c channels, cg per block
+inline int fieldpts_blocks(const FieldPtsJob& j, int c, int cg) {
+  return j.chunks * ((j.h + 255) / 256) * ((c + cg - 1) / cg);
+}
 // Z = diag(oa) G Y per cloud (one block per matrix row: prefix over m)
 cudaError_t launch_small_batched(const ApplyJob* jobs, const int* prefix, int count, int total_rows,
                                  const CloudCall* calls, cudaStream_t st);

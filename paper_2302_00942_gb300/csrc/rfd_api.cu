@@ -807,7 +807,146 @@ void plan_carve(rfd_plan_s* pl, PlanCarve& c) {
     }
 }
 
+// Chunks of the points-based Phi^T F of a compact plan: at most 64 chunks of at least 4096
+// points, and partials of at most 16 MB ([chunks][m][ld] floats, ld = channels padded to 4).
+void fieldpts_shape(const rfd_plan_s* pl, int* chunks, int64_t* pts, int* ld) {
+  *ld = (int)round_up(pl->p.max_channels, 4);
+  const int64_t cap = std::max<int64_t>(1, (16ll << 20) / ((int64_t)pl->m * *ld * 4));
+  int64_t ch = std::min<int64_t>({64, cap, std::max<int64_t>(1, (pl->n + 4095) / 4096)});
+  *pts = (pl->n + ch - 1) / ch;
+  *chunks = (int)((pl->n + *pts - 1) / *pts);
+}
+
+void plan_carve_compact(rfd_plan_s* pl, PlanCarve& c) {
+  const int m = pl->m;
+  int chunks, ld;
+  int64_t pts;
+  fieldpts_shape(pl, &chunks, &pts, &ld);
+  c.add(&pl->d_omega_hi, (size_t)pl->h * 3);
+  c.add(&pl->d_omega_lo, (size_t)pl->h * 3);
+  c.add(&pl->d_oa, (size_t)m);
+  c.add(&pl->d_ob, (size_t)m);
+  c.add(&pl->d_xyz, (size_t)pl->n * 3);
+  c.add(&pl->d_M, (size_t)m * m);
+  c.add(&pl->d_Y, (size_t)m * pl->p.max_channels);
+  c.add(&pl->d_G, (size_t)m * m);
+  c.add(&pl->d_Z, (size_t)m * pl->p.max_channels);
+  c.add(&pl->d_ints, 4);
+  c.add(&pl->d_scalar, 2);
+  c.add(&pl->d_fpart, (size_t)chunks * m * ld);
+}
+
+// The compact plan's descriptors: the points-based Phi^T F, its reduce tiles (one per 128
+// feature rows, summing the chunks), and the apply (as the full plan's).
+void build_compact_desc(rfd_plan_s* pl) {
+  PlanDesc& d = pl->desc;
+  for (int mode = 0; mode < 3; ++mode) {
+    d.units[mode].clear();
+    d.red[mode].clear();
+    d.pair_units[mode].clear();
+    d.pair_red[mode].clear();
+  }
+  int chunks, ld;
+  int64_t pts;
+  fieldpts_shape(pl, &chunks, &pts, &ld);
+  d.fpts = FieldPtsJob{pl->d_xyz, pl->d_omega_hi, pl->d_fpart, pl->n, pts, pl->h, pl->m, chunks, ld, 0, 0};
+  d.red_pts.clear();
+  for (int i0 = 0; i0 < pl->m; i0 += kTcBM) {
+    RedTile r{};
+    r.part = pl->d_fpart + (size_t)i0 * ld;
+    r.M = pl->d_M;
+    r.Y = pl->d_Y;
+    r.oa = pl->d_oa;
+    r.ob = pl->d_ob;
+    r.slot_elems = (int64_t)pl->m * ld;
+    r.i0 = i0;
+    r.ni = std::min(kTcBM, pl->m - i0);
+    r.j0 = pl->m;
+    r.nj = ld;
+    r.kind = kTileField;
+    r.count = chunks;
+    r.ld = ld;
+    r.col_off = 0;
+    r.m = pl->m;
+    r.cloud = 0;
+    r.fsplit = 0;
+    d.red_pts.push_back(r);
+  }
+  d.apply = ApplyJob{pl->d_xyz, pl->d_omega_hi, pl->d_omega_lo, pl->d_G, pl->d_Y, pl->d_oa, pl->d_Z,
+                     pl->n,     pl->n_pad,      pl->m, 0, (int)((pl->n + 511) / 512), 0};
+}
+
 }  // namespace
+
+size_t plan_compact_bytes(const rfd_plan_s* pl) {
+  rfd_plan_s tmp;  // the carve only reads the sizes
+  tmp.p = pl->p;
+  tmp.m = pl->m;
+  tmp.h = pl->h;
+  tmp.n = pl->n;
+  PlanCarve c;
+  plan_carve_compact(&tmp, c);
+  return c.total;
+}
+
+rfd_status plan_compact(rfd_plan_s* pl, bool self_batch) {
+  if (!pl->bf16) return fail(RFD_EINVAL, "only BF16 tensor-core plans have a compact form");
+  if (pl->compact) return RFD_OK;
+  if (!pl->have_G) return fail(RFD_EINVAL, "rfd_features (or rfd_gfi) must run before the plan is compacted");
+  RFD_CUDA(cudaStreamSynchronize(pl->stream));
+  // the buffers that stay, and where they are now
+  struct Keep {
+    void** field;
+    void* old;
+    size_t bytes;
+  };
+  const int m = pl->m;
+  std::vector<Keep> keep = {
+      {reinterpret_cast<void**>(&pl->d_omega_hi), pl->d_omega_hi, (size_t)pl->h * 3 * 4},
+      {reinterpret_cast<void**>(&pl->d_omega_lo), pl->d_omega_lo, (size_t)pl->h * 3 * 4},
+      {reinterpret_cast<void**>(&pl->d_oa), pl->d_oa, (size_t)m * 8},
+      {reinterpret_cast<void**>(&pl->d_ob), pl->d_ob, (size_t)m * 8},
+      {reinterpret_cast<void**>(&pl->d_xyz), pl->d_xyz, (size_t)pl->n * 12},
+      {reinterpret_cast<void**>(&pl->d_M), pl->d_M, (size_t)m * m * 8},
+      {reinterpret_cast<void**>(&pl->d_Y), pl->d_Y, (size_t)m * pl->p.max_channels * 8},
+      {reinterpret_cast<void**>(&pl->d_G), pl->d_G, (size_t)m * m * 8},
+      {reinterpret_cast<void**>(&pl->d_Z), pl->d_Z, (size_t)m * pl->p.max_channels * 4},
+      {reinterpret_cast<void**>(&pl->d_ints), pl->d_ints, 4 * 4},
+      {reinterpret_cast<void**>(&pl->d_scalar), pl->d_scalar, 2 * 8}};
+  const size_t bytes = plan_compact_bytes(pl);
+  void* chunk = pl->mem->dev(bytes);
+  if (!chunk) return fail(RFD_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes (compact plan) failed");
+  PlanCarve c;
+  plan_carve_compact(pl, c);  // points the plan's fields into the new chunk
+  c.assign(chunk);
+  cudaError_t e = cudaSuccess;
+  for (const Keep& k : keep)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(*k.field, k.old, k.bytes, cudaMemcpyDeviceToDevice, pl->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
+  if (e != cudaSuccess) {  // back to the full chunk, which still holds everything
+    for (const Keep& k : keep) *k.field = k.old;
+    pl->mem->dev_free(chunk);
+    return cuda_fail("plan compaction", e);
+  }
+  if (pl->self) batch_free(pl->self);
+  pl->self = nullptr;
+  pl->mem->dev_free(pl->chunk);
+  pl->chunk = chunk;
+  pl->chunk_bytes = bytes;
+  pl->d_psi = nullptr;
+  pl->d_part = nullptr;
+  pl->d_work = nullptr;
+  pl->d_ipiv = nullptr;
+  pl->compact = true;
+  build_compact_desc(pl);
+  if (self_batch) {
+    rfd_plan_s* self = pl;
+    rfd_status s = batch_build(&self, 1, pl->stream, pl->mem, 0, pl->tune, &pl->self);
+    if (s != RFD_OK) return s;
+    RFD_CUDA(cudaStreamSynchronize(pl->stream));
+  }
+  return RFD_OK;
+}
 
 MemSource* cuda_mem() {
   static CudaMem m;
@@ -995,6 +1134,7 @@ rfd_status rfd_plan_destroy(rfd_plan_t plan) {
 
 rfd_status rfd_features(rfd_plan_t pl, const float* d_points) {
   if (!pl || !d_points) return fail(RFD_EINVAL, "null plan or points");
+  if (pl->compact) return fail(RFD_EINVAL, "a compact plan has no feature matrix: create a new plan");
   return run_plan(pl, kModeFeatures, d_points, nullptr, 1, 1, nullptr, 1);
 }
 
@@ -1009,9 +1149,21 @@ rfd_status rfd_integrate(rfd_plan_t pl, const float* d_F, int32_t c, int64_t ldF
 rfd_status rfd_gfi(rfd_plan_t pl, const float* d_points, const float* d_F, int32_t c, int64_t ldF, float* d_out,
                    int64_t ldOut) {
   if (!pl || !d_points) return fail(RFD_EINVAL, "null plan or points");
+  if (pl->compact) return fail(RFD_EINVAL, "a compact plan has no feature matrix: create a new plan");
   rfd_status s = check_field_args(pl, d_F, c, ldF, d_out, ldOut);
   if (s != RFD_OK) return s;
   return run_plan(pl, kModeGfi, d_points, d_F, c, ldF, d_out, ldOut);
+}
+
+rfd_status rfd_plan_compact(rfd_plan_t pl) {
+  if (!pl) return fail(RFD_EINVAL, "null plan");
+  return plan_compact(pl, true);
+}
+
+rfd_status rfd_plan_device_bytes(rfd_plan_t pl, int64_t* out) {
+  if (!pl || !out) return fail(RFD_EINVAL, "null plan or output");
+  *out = (int64_t)pl->chunk_bytes;
+  return RFD_OK;
 }
 
 rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double* d_G, int32_t flags, void* cuda_stream,

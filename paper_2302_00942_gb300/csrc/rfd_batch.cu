@@ -70,6 +70,9 @@ struct BatchImpl {
   void* d_maps = nullptr;
   TcUnit* d_units[3] = {};
   int n_units[3] = {};
+  bool compact = false;      // every plan compact: integrate computes Phi^T F from the points
+  FieldPtsJob* d_fpts = nullptr;
+  std::vector<FieldPtsJob> fpts_h;  // host copies (block counts per call)
   PairUnit* d_pair[3] = {};  // a lone cloud with m >= 512: the 2-SM form of the Gram modes
   int n_pair[3] = {};
   int pair_stage_bytes = 0;
@@ -179,6 +182,16 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   std::vector<RedTile> red[3];
   std::vector<unsigned char> maps((size_t)count * kMapsPerCloud * kTensorMapBytes);
   std::vector<FeatJob> feat;
+  std::vector<FieldPtsJob> fpts;
+  int n_compact = 0;
+  for (int k = 0; k < count; ++k) n_compact += plans[k]->compact ? 1 : 0;
+  if (n_compact && n_compact != count) return bail(RFD_EINVAL, "a batch cannot mix compact and full plans");
+  b->compact = n_compact == count;
+  if (b->compact)
+    for (int k = 0; k < count; ++k) {
+      b->fpts_h.push_back(plans[k]->desc.fpts);
+      b->fpts_h.back().cloud = k;
+    }
   std::vector<FillJob> fill;
   std::vector<ApplyJob> apply;
   std::vector<PhiCloud> phi;
@@ -193,7 +206,16 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
     if (!ozaki_supported(pl->m) || (pl->p.flags & RFD_FLAG_NATIVE_FP64)) b->phi_batched = false;
     std::memcpy(maps.data() + (size_t)k * kMapsPerCloud * kTensorMapBytes, d.maps, sizeof(d.maps));
     const int64_t kb = pl->n_pad / kTcBK;
-    for (int mode = 0; mode < 3; ++mode) {
+    if (b->compact) {  // integrate from the points only
+      FieldPtsJob fj = d.fpts;
+      fj.cloud = k;
+      fpts.push_back(fj);
+      for (RedTile r : d.red_pts) {
+        r.cloud = k;
+        red[kModeIntegrate].push_back(r);
+      }
+    }
+    for (int mode = 0; mode < 3 && !b->compact; ++mode) {
       if (count == 1 && tune.pairs && !d.pair_units[mode].empty()) {  // a lone cloud: the plan's pair units
         pairs[mode] = d.pair_units[mode];
         red[mode] = d.pair_red[mode];
@@ -307,9 +329,10 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   const size_t o_feat = vtable(feat), o_feat_pre = vtable(pre_feat), o_fill = vtable(fill),
                o_fill_pre = vtable(pre_fill), o_apply = vtable(apply), o_small_pre = vtable(pre_small),
                o_phi = vtable(phi), o_elem_pre = vtable(pre_elem), o_grp_pre = vtable(pre_grp), o_rexp_pre = vtable(pre_rexp), o_rowa_pre = vtable(pre_rowa),
-               o_strip_pre = vtable(pre_strip), o_oz = vtable(oz);
+               o_strip_pre = vtable(pre_strip), o_oz = vtable(oz), o_fpts = vtable(fpts);
   const size_t table_bytes = L.total;
-  b->stage_bytes = (size_t)count * sizeof(CloudCall) + (size_t)(count + 1) * sizeof(int);
+  // per call: the CloudCalls, then the apply-block prefix and the points-based Phi^T F prefix
+  b->stage_bytes = (size_t)count * sizeof(CloudCall) + 2 * (size_t)(count + 1) * sizeof(int);
   const size_t o_calls = L.add(b->stage_bytes);
   const size_t o_norms = L.add((size_t)count * sizeof(double));
   const size_t o_sv = L.add((size_t)(count + 1) * sizeof(int));
@@ -332,6 +355,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   for (int mode = 0; mode < 3; ++mode) {
     b->d_units[mode] = reinterpret_cast<TcUnit*>(D + o_units[mode]);
     b->d_pair[mode] = reinterpret_cast<PairUnit*>(D + o_pair[mode]);
+    b->d_fpts = reinterpret_cast<FieldPtsJob*>(D + o_fpts);
     b->d_red[mode] = reinterpret_cast<RedTile*>(D + o_red[mode]);
   }
   b->d_feat = reinterpret_cast<FeatJob*>(D + o_feat);
@@ -647,6 +671,14 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   const int apply_blocks = hp[n];
   const int* d_apply_prefix = reinterpret_cast<const int*>(reinterpret_cast<unsigned char*>(b->d_calls) +
                                                            (size_t)n * sizeof(CloudCall));
+  // compact plans: the blocks of the points-based Phi^T F (they depend on c too)
+  int* hq = hp + (n + 1);
+  hq[0] = 0;
+  for (int k = 0; k < n; ++k) hq[k + 1] = hq[k] + (b->compact ? fieldpts_blocks(b->fpts_h[k], calls[k].c, cg) : 0);
+  const int fpts_blocks = hq[n];
+  const int* d_fpts_prefix = d_apply_prefix + (n + 1);
+  if (b->compact && mode != kModeIntegrate)
+    return fail(RFD_EINVAL, "a compact plan has no feature matrix: only integration runs on it");
   BCK(cudaMemcpyAsync(b->d_calls, stage, b->stage_bytes, cudaMemcpyHostToDevice, st));
   BCK(cudaEventRecord(b->stage_done[slot], st));
   const bool with_feat = mode != kModeIntegrate, with_phi = with_feat && !gram_only;
@@ -655,6 +687,15 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
 
   const bool pipelined = with_feat && pipelines(b);
   auto reductions = [&](cudaStream_t s, Timing* t) -> rfd_status {
+    if (b->compact) {  // Phi^T F from the points, summed over the chunks by the reduce kernel
+      {
+        StepScope sc(t, s, RFD_STEP_FIELD);
+        BCK(launch_fieldpts_batched(b->d_fpts, d_fpts_prefix, n, fpts_blocks, cg, b->d_calls, s));
+      }
+      StepScope sc(t, s, RFD_STEP_REDUCE);
+      BCK(launch_reduce_batched(b->d_red[mode], b->n_red[mode], b->d_calls, s));
+      return RFD_OK;
+    }
     if (pipelined) {
       if (rfd_status q = pipelined_features(b, s, t); q != RFD_OK) return q;
       if (with_apply) {
@@ -701,7 +742,7 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
     return run_segment(b, key, graph, tm, reductions);
   }
   if (!with_phi) {
-    const int key[4] = {mode, -1, cg, apply_blocks};
+    const int key[4] = {mode, b->compact ? -4 - fpts_blocks : -1, cg, apply_blocks};
     return run_segment(b, key, graph, tm, [&](cudaStream_t s, Timing* t) -> rfd_status {
       rfd_status r = reductions(s, t);
       return r == RFD_OK ? small_apply(s, t) : r;

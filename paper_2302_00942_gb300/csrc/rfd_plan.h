@@ -81,6 +81,9 @@ struct PlanDesc {
   std::vector<PairUnit> pair_units[3];
   std::vector<RedTile> pair_red[3];
   int pair_stage_bytes = 0;
+  // a compact plan (rfd_plan_compact): Phi^T F from the points, into d_fpart
+  FieldPtsJob fpts{};
+  std::vector<RedTile> red_pts;
   FeatJob feat{};
   FillJob fill{};
   ApplyJob apply{};
@@ -149,6 +152,10 @@ struct rfd_plan_s {
   rfd::PlanDesc desc;                         // BF16 tensor-core form
   rfd::BatchImpl* self = nullptr;             // the plan as a batch of one (BF16 form)
   bool have_G = false;
+  // compact (rfd_plan_compact): Psi, the split-K partials and the phi1 workspace are released;
+  // rfd_integrate recomputes the features from d_xyz (FieldPtsJob) into d_fpart
+  bool compact = false;
+  float* d_fpart = nullptr;
   rfd_stats stats{};
   std::vector<void*> allocs;       // temporary owners only (rfd_phi1, debug GEMM)
   rfd::MemSource* mem = nullptr;   // source of the plan's single device chunk
@@ -167,6 +174,11 @@ namespace rfd {
 rfd_status plan_prepare(const rfd_params& p, cudaStream_t st, rfd_plan_s** out);
 size_t plan_device_bytes(rfd_plan_s* pl);
 rfd_status plan_materialize(rfd_plan_s* pl, MemSource* mem, bool self_batch, bool sync_init);
+// Shrinks a BF16 plan with G to its compact form (a new chunk from the plan's memory
+// source, the old one released; synchronises the plan's stream).  On failure the plan
+// is unchanged.  self_batch: rebuild the plan's batch of one for the compact form.
+rfd_status plan_compact(rfd_plan_s* pl, bool self_batch);
+size_t plan_compact_bytes(const rfd_plan_s* pl);
 void plan_destroy(rfd_plan_s* pl);  // frees without synchronising (the caller has)
 
 // Builds / frees the device tables of a batch over the given BF16 plans (one

@@ -16,6 +16,14 @@
 // clouds (steps a3(Y)-a6), runs them, and waits for them on its stream.  The
 // other executors keep admitting and launching meanwhile, so batches of
 // requests that arrived while others run overlap on the device.
+//
+// Residency: a cloud kept for later requests (keep = 1) is compacted after its
+// first pass to its points, frequencies, M and G (plan_compact: the feature
+// matrix, partials and phi1 workspace go back to the pool), so the budget holds
+// ~50x more resident clouds; a request on it recomputes the features from the
+// points (FP32) for B^T F and the apply.  A cloud's id is the ticket of the
+// request that keeps it, so a request may name a cloud whose keeping request
+// has not finished yet: it waits in the queue behind it.
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <chrono>
@@ -158,7 +166,7 @@ struct rfd_server_s {
   std::unordered_map<uint64_t, Req> reqs;
   std::unordered_map<uint64_t, std::unique_ptr<Cloud>> clouds;
   std::list<uint64_t> lru;  // idle resident clouds, least recently used first
-  uint64_t next_ticket = 1, next_cloud = 1;
+  uint64_t next_ticket = 1;
   int64_t outstanding = 0;
   bool stop = false, paused = false;
   rfd_server_stats st{};
@@ -240,6 +248,13 @@ void run_group(rfd_server_s* s, std::vector<Req*>& group, int mode, cudaStream_t
   batch_free(b);
 }
 
+// A request with keep = 1 that has not finished: its ticket names the cloud it will
+// leave resident, so requests that reuse that cloud wait behind it.  Lock held.
+bool root_pending(rfd_server_s* s, uint64_t ticket) {
+  auto it = s->reqs.find(ticket);
+  return it != s->reqs.end() && it->second.r.keep && !it->second.done;
+}
+
 void executor(rfd_server_s* s, int idx) {
   cudaSetDevice(s->device);
   cudaStream_t stream = s->streams[idx];
@@ -256,6 +271,10 @@ void executor(rfd_server_s* s, int idx) {
     for (auto it = s->queue.begin(); it != s->queue.end() && (int)(fresh.size() + reuse.size()) < s->cfg.max_batch;) {
       const uint64_t t = *it;
       Req& q = s->reqs[t];
+      if (q.r.cloud && !q.plan && !s->clouds.count(q.r.cloud) && root_pending(s, q.r.cloud)) {
+        ++it;  // its cloud is still being made by the request that keeps it
+        continue;
+      }
       if (q.r.cloud && !q.plan) {
         auto c = s->clouds.find(q.r.cloud);
         if (c == s->clouds.end()) {  // evicted since rfd_submit: rebuild it from the points, if given
@@ -340,6 +359,10 @@ void executor(rfd_server_s* s, int idx) {
     for (size_t i = 0; i < ready.size(); ++i) fs[ready_idx[i]] = rstat[i];
     run_group(s, reuse, kModeIntegrate, stream, rs.data());
     const Clock::time_point t_done = Clock::now();
+    // clouds that stay resident keep only their compact form (points, frequencies, M, G):
+    // later requests on them recompute the features from the points
+    for (size_t k = 0; k < fresh.size(); ++k)
+      if (fresh[k]->plan && fs[k] == RFD_OK && fresh[k]->r.keep) plan_compact(fresh[k]->plan, false);
     const long long launches = t_kernel_launches - l0;
     lk.lock();
     s->st.kernel_launches += launches;
@@ -348,7 +371,7 @@ void executor(rfd_server_s* s, int idx) {
       Req& q = *fresh[k];
       if (q.plan && fs[k] == RFD_OK && q.r.keep) {
         auto cl = std::make_unique<Cloud>();
-        cl->id = s->next_cloud++;
+        cl->id = fresh_t[k];  // the ticket of the request that keeps it
         cl->plan = q.plan;
         q.res.cloud = cl->id;
         s->lru.push_back(cl->id);
@@ -462,7 +485,7 @@ rfd_status rfd_submit(rfd_server_t s, const rfd_request* req, uint64_t* ticket) 
       ++s->st.rejected;
       return fail(RFD_EBUSY, "admission refused: " + std::to_string(s->outstanding) + " requests outstanding");
     }
-    resident = r.cloud && s->clouds.count(r.cloud);
+    resident = r.cloud && (s->clouds.count(r.cloud) || root_pending(s, r.cloud));
   }
   rfd_plan_s* pl = nullptr;
   if (!resident) {

@@ -140,10 +140,48 @@ def test_server_admission_and_poll_timeouts():
         srv.close()
 
 
+def test_server_chained_reuse_waits_for_its_root():
+    """A request may name the cloud of a keep = 1 request that has not finished
+    (a cloud's id is the ticket of the request that keeps it): it waits behind
+    it, runs on the compact resident cloud, and matches the oracle."""
+    s = _specs(1, seed=13)[0]
+    (pts, F), = [synth.make_cloud(s)]
+    P, Fd = torch.from_numpy(pts).to(DEV), torch.from_numpy(F).to(DEV)
+    fields = [synth.gaussian_field(s.n, 8, 300 + k) for k in range(3)]
+    srv = rfd.Server(2 << 30, executors=3)
+    try:
+        srv.pause(True)   # everything is queued before any of it runs
+        root_out = torch.empty_like(Fd)
+        root = _submit(srv, s, P, Fd, root_out, keep=True, max_channels=8)
+        outs, tickets = [], []
+        for Fk in fields:
+            Fk_d = torch.from_numpy(Fk).to(DEV)
+            o = torch.empty_like(Fk_d)
+            tickets.append(srv.submit(Fk_d, o, cloud=root))   # no points: the root's cloud
+            outs.append(o)
+        srv.pause(False)
+        res = _wait(srv, root)
+        assert res["status"] == rfd.RFD_OK and res["cloud"] == root
+        for t, o, Fk in zip(tickets, outs, fields):
+            r = _wait(srv, t)
+            assert r["status"] == rfd.RFD_OK and r["reused"] == 1 and r["cloud"] == root
+            ref = oracle.rfd_gfi(pts, Fk, s.eps, _lam(s), s.m, s.seed)
+            pc.assert_matches(o.cpu().numpy(), ref, Fk, BF16, label="chained reuse")
+        # a request that names a finished request which kept nothing is refused at once
+        t2 = _submit(srv, s, P, Fd, torch.empty_like(Fd))
+        _wait(srv, t2)
+        st, _ = srv.try_submit(Fd, torch.empty_like(Fd), cloud=t2)
+        assert st == rfd.RFD_EINVAL
+    finally:
+        srv.close()
+
+
 def test_server_evicts_idle_clouds_and_rebuilds_from_points():
-    specs = synth.batched_specs(count=10, seed=9, n_lo=1500, n_hi=2000, ms=(64,), c=3)
+    # resident clouds are compact (points, M, G: 2 m^2 doubles dominate at m = 1024), so 20
+    # clouds of m = 1024 overflow a 512 MB plan pool that also has to hold one full plan
+    specs = synth.batched_specs(count=20, seed=9, n_lo=1500, n_hi=2000, ms=(1024,), c=3)
     clouds, dev = _upload(specs)
-    srv = rfd.Server(128 << 20, executors=2)   # room for a few small clouds beside the table pools
+    srv = rfd.Server((64 + 512) << 20, executors=2)
     try:
         ids = []
         for s, (P, F) in zip(specs, dev):
