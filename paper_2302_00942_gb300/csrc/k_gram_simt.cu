@@ -122,7 +122,81 @@ gram_simt_kernel(const float* __restrict__ psi, int64_t n_pad, const GramUnit* _
   }
 }
 
+// A field tile of at most 16 columns (Y' = Phi^T F for up to 16 channel rows):
+// 128 feature rows x 16 columns, each thread 8 rows x 1 column, so that a few
+// channels do not cost a whole 128 x 128 tile.  Same slabs, the same
+// compensated folding (in registers: 8 sums per thread), and the same partial
+// layout (row stride 128) as the square kernel.
+__global__ void __launch_bounds__(kThreads)
+gram_simt_narrow_kernel(const float* __restrict__ psi, int64_t n_pad, const GramUnit* __restrict__ units,
+                        float* __restrict__ partials) {
+  constexpr int kN = kSimtNarrow;
+  const GramUnit u = units[blockIdx.x];
+  __shared__ __align__(16) float As[kK][kT + 4];
+  __shared__ __align__(16) float Bs[kK][kN + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // column tx, rows 8 ty .. 8 ty + 7
+  float acc[8], sum[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = sum[i] = 0.f;
+  const int lrow = threadIdx.x >> 2, lq = threadIdx.x & 3;  // A: rows lrow and lrow + 64, float4 lq
+  const float* arow0 = psi + (size_t)(u.i0 + lrow) * n_pad + lq * 4;
+  const float* arow1 = psi + (size_t)(u.i0 + lrow + 64) * n_pad + lq * 4;
+  const bool bload = threadIdx.x < kN * 4;                   // B: 16 rows x 4 float4
+  const float* brow = psi + (size_t)(u.j0 + (threadIdx.x >> 2)) * n_pad + lq * 4;
+  float4 va0, va1, vb = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (u.k0 < u.k1) {
+    va0 = __ldg(reinterpret_cast<const float4*>(arow0 + u.k0));
+    va1 = __ldg(reinterpret_cast<const float4*>(arow1 + u.k0));
+    if (bload) vb = __ldg(reinterpret_cast<const float4*>(brow + u.k0));
+  }
+  int slab = 0;
+  for (int64_t k = u.k0; k < u.k1; k += kK, ++slab) {
+    __syncthreads();
+    As[lq * 4 + 0][lrow] = va0.x; As[lq * 4 + 1][lrow] = va0.y; As[lq * 4 + 2][lrow] = va0.z; As[lq * 4 + 3][lrow] = va0.w;
+    As[lq * 4 + 0][lrow + 64] = va1.x; As[lq * 4 + 1][lrow + 64] = va1.y; As[lq * 4 + 2][lrow + 64] = va1.z; As[lq * 4 + 3][lrow + 64] = va1.w;
+    if (bload) {
+      const int br = threadIdx.x >> 2;
+      Bs[lq * 4 + 0][br] = vb.x; Bs[lq * 4 + 1][br] = vb.y; Bs[lq * 4 + 2][br] = vb.z; Bs[lq * 4 + 3][br] = vb.w;
+    }
+    __syncthreads();
+    const int64_t kn = k + kK;
+    if (kn < u.k1) {
+      va0 = __ldg(reinterpret_cast<const float4*>(arow0 + kn));
+      va1 = __ldg(reinterpret_cast<const float4*>(arow1 + kn));
+      if (bload) vb = __ldg(reinterpret_cast<const float4*>(brow + kn));
+    }
+#pragma unroll
+    for (int kk = 0; kk < kK; ++kk) {
+      const float4 a_lo = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
+      const float4 a_hi = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
+      const float b = Bs[kk][tx];
+      const float a[8] = {a_lo.x, a_lo.y, a_lo.z, a_lo.w, a_hi.x, a_hi.y, a_hi.z, a_hi.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i) acc[i] = fmaf(a[i], b, acc[i]);
+    }
+    if ((slab + 1) % kFold == 0) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {  // sum + acc = t + e exactly; e carries on in acc
+        const float t = sum[i] + acc[i];
+        const float bp = t - sum[i];
+        acc[i] = (sum[i] - (t - bp)) + (acc[i] - bp);
+        sum[i] = t;
+      }
+    }
+  }
+  float* out = partials + u.out;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) out[(size_t)(ty * 8 + i) * kT + tx] = sum[i] + acc[i];
+}
+
 }  // namespace
+
+cudaError_t launch_gram_simt_narrow(const float* psi, int64_t n_pad, const GramUnit* units, int num_units,
+                                    float* partials, cudaStream_t st) {
+  if (num_units <= 0) return cudaSuccess;
+  gram_simt_narrow_kernel<<<num_units, kThreads, 0, st>>>(psi, n_pad, units, partials);
+  return launched();
+}
 
 cudaError_t launch_gram_simt(const float* psi, int64_t n_pad, const GramUnit* units, int num_units,
                              float* partials, cudaStream_t st) {

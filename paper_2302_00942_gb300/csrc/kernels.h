@@ -75,6 +75,10 @@ constexpr int kSimtTile = 128;
 constexpr int kSimtK = 16;
 cudaError_t launch_gram_simt(const float* psi, int64_t n_pad, const GramUnit* units, int num_units,
                              float* partials, cudaStream_t st);
+// Field tiles of at most kSimtNarrow columns: 128 x 16 tiles (same partial layout).
+constexpr int kSimtNarrow = 16;
+cudaError_t launch_gram_simt_narrow(const float* psi, int64_t n_pad, const GramUnit* units, int num_units,
+                                    float* partials, cudaStream_t st);
 
 // BF16 tensor-core form (tcgen05 + TMA): one CTA per (tile pair, lane).  A
 // logical tile is 128 rows x (Gram columns + field columns <= 256); partial

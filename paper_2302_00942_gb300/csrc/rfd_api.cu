@@ -117,44 +117,63 @@ void plan_free(rfd_plan_s* pl) {
 // Each tile gets point-range pieces in proportion to its cost; pieces are
 // ordered split-major so concurrently running CTAs read the same point range.
 // Depends only on (N, m, channel capacity, SM count).
-void schedule_simt(TileSet& ts, int64_t n_pad, int target_units, const std::vector<double>& cost) {
-  const int64_t ksteps = n_pad / kSimtK;
-  int slot = 0;
-  // one piece per tile, then the rest of the target one at a time to the tile with the most
-  // cost per piece: the pieces never exceed the target (one wave), and their costs even out
+// The tiles of one launch (narrow == the narrow-kernel field tiles, or the rest) get
+// point-range pieces in proportion to their cost: one piece per tile, then the rest of
+// the target one at a time to the tile with the most cost per piece, so the pieces never
+// exceed the target (one wave) and their costs even out.
+void split_simt(const TileSet& ts, const std::vector<double>& cost, const std::vector<bool>& narrow, bool which,
+                int64_t ksteps, int target_units, std::vector<int>& splits) {
   const int T = (int)ts.tiles.size();
-  std::vector<int> splits(T, 1);
-  for (int left = target_units - T; left > 0; --left) {
+  int n = 0;
+  for (int t = 0; t < T; ++t) n += narrow[t] == which ? 1 : 0;
+  for (int left = target_units - n; left > 0; --left) {
     int best = -1;
     for (int t = 0; t < T; ++t)
-      if (splits[t] < ksteps && (best < 0 || cost[t] / splits[t] > cost[best] / splits[best])) best = t;
+      if (narrow[t] == which && splits[t] < ksteps && (best < 0 || cost[t] / splits[t] > cost[best] / splits[best]))
+        best = t;
     if (best < 0) break;
     ++splits[best];
   }
+}
+
+// FP32 plain form: split-K schedule of the square tiles (target_units pieces, one wave)
+// and, in a launch of their own, the narrow field tiles (target_narrow pieces); pieces
+// are ordered split-major within each launch so that concurrently running CTAs read the
+// same point range.  Depends only on (N, m, channel capacity, SM count).
+void schedule_simt(TileSet& ts, int64_t n_pad, int target_units, int target_narrow, const std::vector<double>& cost,
+                   const std::vector<bool>& narrow) {
+  const int64_t ksteps = n_pad / kSimtK;
+  const int T = (int)ts.tiles.size();
+  std::vector<int> splits(T, 1);
+  split_simt(ts, cost, narrow, false, ksteps, target_units, splits);
+  split_simt(ts, cost, narrow, true, ksteps, target_narrow, splits);
+  int slot = 0;
   for (int t = 0; t < T; ++t) {
-    const int s = splits[t];
     ts.tiles[t].unit_first = slot;
-    ts.tiles[t].unit_count = (int)s;
+    ts.tiles[t].unit_count = splits[t];
     ts.tiles[t].ld = kSimtTile;
-    slot += (int)s;
+    slot += splits[t];
   }
   ts.slots = slot;
-  const int smax = ts.tiles.empty() ? 0 : *std::max_element(splits.begin(), splits.end());
-  for (int s = 0; s < smax; ++s)
-    for (size_t t = 0; t < ts.tiles.size(); ++t) {
-      if (s >= splits[t]) continue;
-      const GramTile& T = ts.tiles[t];
-      GramUnit u{};
-      u.tile = (int)t;
-      u.kind = T.kind;
-      u.i0 = T.i0;
-      u.j0 = T.j0;
-      const int64_t a = ksteps * s / splits[t], b = ksteps * (s + 1) / splits[t];
-      u.k0 = a * kSimtK;
-      u.k1 = b * kSimtK;
-      u.out = (int64_t)(T.unit_first + s) * kSimtTile * kSimtTile;
-      ts.units.push_back(u);
-    }
+  ts.n_narrow = 0;
+  const int smax = T ? *std::max_element(splits.begin(), splits.end()) : 0;
+  for (bool which : {false, true})
+    for (int s = 0; s < smax; ++s)
+      for (int t = 0; t < T; ++t) {
+        if (narrow[t] != which || s >= splits[t]) continue;
+        const GramTile& Tt = ts.tiles[t];
+        GramUnit u{};
+        u.tile = t;
+        u.kind = Tt.kind;
+        u.i0 = Tt.i0;
+        u.j0 = Tt.j0;
+        const int64_t a = ksteps * s / splits[t], b = ksteps * (s + 1) / splits[t];
+        u.k0 = a * kSimtK;
+        u.k1 = b * kSimtK;
+        u.out = (int64_t)(Tt.unit_first + s) * kSimtTile * kSimtTile;
+        ts.units.push_back(u);
+        if (which) ++ts.n_narrow;
+      }
 }
 
 void build_tiles_simt(rfd_plan_s* pl, bool with_gram, bool with_field, TileSet& ts) {
@@ -166,13 +185,16 @@ void build_tiles_simt(rfd_plan_s* pl, bool with_gram, bool with_field, TileSet& 
           GramTile{i0, j0, std::min(kSimtTile, m - i0), std::min(kSimtTile, m - j0), kTileGram, 0, 0, 0, 0, 0});
       cost.push_back(1.0);
     }
+  std::vector<bool> narrow(cost.size(), false);
   for (int i0 = 0; i0 < m && with_field; i0 += kSimtTile)
     for (int c0 = 0; c0 < pl->cpad; c0 += kSimtTile) {
-      ts.tiles.push_back(GramTile{i0, m + c0, std::min(kSimtTile, m - i0), std::min(kSimtTile, pl->cpad - c0),
-                                  kTileField, 0, 0, 0, 0, 0});
+      const int nj = std::min(kSimtTile, pl->cpad - c0);
+      ts.tiles.push_back(GramTile{i0, m + c0, std::min(kSimtTile, m - i0), nj, kTileField, 0, 0, 0, 0, 0});
       cost.push_back(1.0);
+      narrow.push_back(nj <= kSimtNarrow);  // 128 x 16 tiles in a launch of their own
     }
-  schedule_simt(ts, pl->n_pad, 2 * pl->sms, cost);  // one wave: two CTAs per SM
+  // one wave each: two square-kernel CTAs per SM, four narrow-kernel CTAs per SM
+  schedule_simt(ts, pl->n_pad, 2 * pl->sms, 4 * pl->sms, cost, narrow);
 }
 
 // ---- BF16 tensor-core form: the plan's batched-path descriptors -------------
@@ -281,10 +303,9 @@ struct PairCT {
   int r0, c0, nc;
   bool g2, f, a1;
 };
-std::atomic<int> g_gram_pairs{1};  // test hook: 0 keeps every plan on the one-SM Gram kernel
+std::atomic<int> g_gram_pairs{0};  // test hook: the Gram form new plans start with (1: CTA pairs)
 bool pair_eligible(const rfd_plan_s* pl) {
-  return g_gram_pairs.load() && pl->bf16 && pl->m >= 512 && pl->m % 16 == 0 && pl->cpad <= 128 &&
-         tc_gram_supported();
+  return pl->bf16 && pl->m >= 512 && pl->m % 16 == 0 && pl->cpad <= 128 && tc_gram_supported();
 }
 std::vector<PairCT> pair_tiles(int m, int mode) {
   std::vector<PairCT> ct;
@@ -567,8 +588,10 @@ rfd_status run_reductions_simt(rfd_plan_s* pl, const TileSet& ts, int c) {
   cudaStream_t st = pl->stream;
   {
     StepScope t(&pl->timing, st, RFD_STEP_GRAM);
-    RFD_CUDA(launch_gram_simt(static_cast<const float*>(pl->d_psi), pl->n_pad, ts.d_units, (int)ts.units.size(),
-                              pl->d_part, st));
+    const int nfull = (int)ts.units.size() - ts.n_narrow;
+    RFD_CUDA(launch_gram_simt(static_cast<const float*>(pl->d_psi), pl->n_pad, ts.d_units, nfull, pl->d_part, st));
+    RFD_CUDA(launch_gram_simt_narrow(static_cast<const float*>(pl->d_psi), pl->n_pad, ts.d_units + nfull,
+                                     ts.n_narrow, pl->d_part, st));
   }
   StepScope t(&pl->timing, st, RFD_STEP_REDUCE);
   RFD_CUDA(launch_reduce(ts.d_tiles, (int)ts.tiles.size(), pl->d_part, pl->slot_elems, pl->d_oa, pl->d_ob, pl->m, c,
@@ -1020,6 +1043,7 @@ rfd_status plan_prepare(const rfd_params& p, cudaStream_t stream, rfd_plan_s** o
     build_tiles_simt(pl, true, true, pl->both);
   }
   pl->autotune = pl->bf16 && (p.flags & RFD_FLAG_AUTOTUNE);
+  pl->tune.pairs = g_gram_pairs.load() && pair_eligible(pl) ? 1 : 0;
   pl->part_slots = pl->bf16 ? std::max(tc_partial_slots(pl->m, pl->cpad, pl->n_pad, pl->sms,
                                                          pl->autotune ? kTuneLanesMax : 100),
                                         pair_eligible(pl) ? pair_partial_slots(pl->m, pl->n_pad, pl->cpad, pl->sms,

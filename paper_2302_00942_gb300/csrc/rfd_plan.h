@@ -64,6 +64,7 @@ struct TileSet {
   GramTile* d_tiles = nullptr;
   GramUnit* d_units = nullptr;
   int slots = 0;
+  int n_narrow = 0;  // the last n_narrow units are field tiles of <= kSimtNarrow columns (narrow kernel)
 };
 
 enum Mode : int { kModeFeatures = 0, kModeIntegrate = 1, kModeGfi = 2 };

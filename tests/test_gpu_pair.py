@@ -49,7 +49,8 @@ def test_pair_gram_matches_oracle_and_one_sm_form(m, c, n, phase):
     lam = 0.1 * m / n
     ref = oracle.rfd_gfi(pts, F, eps, lam, m, seed)
     out2, warm2, st = _run(pts, F, eps, lam, m, seed, True, phase)
-    out1, warm1, _ = _run(pts, F, eps, lam, m, seed, False, phase)
+    out1, warm1, st1 = _run(pts, F, eps, lam, m, seed, False, phase)
+    assert st["tune_pair_gram"] == 1 and st1["tune_pair_gram"] == 0   # each run took the form it names
     pc.assert_matches(out2, ref, F, BF16, label=f"pairs m={m} c={c} N={n} phase={phase}")
     pc.assert_matches(warm2, ref, F, BF16, label="pairs, then the warm path")
     pc.assert_matches(out1, ref, F, BF16, label="one-SM form")
