@@ -325,8 +325,10 @@ RFD_API rfd_status rfd_phi1(int32_t m, double lambda, const double* d_M, double*
  * allocating routine: its workspace is a fixed 3.75 MiB __device__ array that
  * every GPU loading the library holds until the process exits, so it only
  * serves 1 <= m <= 128 (RFD_EINVAL with a message beyond that).  The first call
- * on each device looks up that array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the array
+ * on each device looks up that array's device address (cudaGetSymbolAddress),
+ * and so does the first call after the device's context changed (after a
+ * cudaDeviceReset the module is loaded anew); make such a call before any
+ * stream capture.  All calls share the array
  * and it keeps the previous call's contents: calls whose device work overlaps
  * (other streams or threads) race and must be serialised by the caller.
  * Synchronises `cuda_stream`. */

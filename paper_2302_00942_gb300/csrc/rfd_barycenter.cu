@@ -1,13 +1,13 @@
 // Entropic Wasserstein barycenter on a resident plan (App. C, Algorithm
-// wass_barycenter, after Solomon et al. 2015, Algorithm 2): the kernel action
+// wass_barycenter, after Solomon et al. 2015, Algorithm 2).  The kernel action
 // x -> K x with K = exp(lambda W_hat) is rfd_integrate on the plan's resident
-// features and G, for all k distributions at once (k field channels), and the
-// element-wise steps are two fused kernels per pass:
-//
-//   v^i = w^i = 1;  repeat iters times:
-//     w^i = mu^i / K(a v^i)                     (step 1)
-//     d^i = v^i K(a w^i);  mu = prod_i (d^i)^alpha_i   (steps 2, 3; mu reset per pass)
-//     v^i = v^i mu / d^i                        (step 4)
+// features and G, applied to all k distributions at once (k field channels).
+// Each pass is a round of Sinkhorn-type scalings: every input distribution
+// gets a pair of scaling vectors (v^i, w^i); the barycenter estimate mu is the
+// alpha-weighted geometric mean of the current marginals v^i K(a w^i), and the
+// v^i are rescaled towards it.  A pass is two kernel actions (on a v^i and on
+// a w^i, a the area weights) and two fused element-wise kernels around them;
+// mu starts from 1 in every pass.
 //
 // Kernel outputs are lifted to kFloor before they divide or enter a power (the
 // random-feature kernel need not be positive).  FP32 throughout, on the plan's

@@ -797,16 +797,17 @@ rfd_status line_search_lowrank(rfd_plan_t pc, rfd_plan_t pd, const float* G, con
   return RFD_OK;
 }
 
-// a, b and tau of Algorithm line_search from the inner products h = <C dG D^T, dG>,
-// <C dG D^T, G>, <C G D^T, dG>, <M, dG>, <c_CD, dG>
+// The step of Algorithm line_search.  Along G + tau dG the (F)GW cost is a
+// quadratic in tau, q(tau) = a tau^2 + b tau + q(0), whose coefficients are
+// combinations of five inner products h = <C dG D^T, dG>, <C dG D^T, G>,
+// <C G D^T, dG>, <M, dG>, <c_CD, dG> weighted by alpha (the quadratic part
+// comes from the structure term only, the linear part from both terms).  The
+// step is the minimiser of q on [0, 1]: the vertex clamped to the interval
+// when q is convex, else whichever end costs less (q(1) - q(0) = a + b).
 rfd_status finish_line_search(double alpha, const double h[5], double* out3) {
   const double a = -2.0 * alpha * h[0];
   const double b = (1.0 - alpha) * h[3] + alpha * h[4] - 2.0 * alpha * (h[1] + h[2]);
-  double tau;
-  if (a > 0)
-    tau = std::min(1.0, std::max(0.0, -b / (2.0 * a)));
-  else
-    tau = (a + b < 0) ? 1.0 : 0.0;
+  const double tau = a > 0 ? std::min(1.0, std::max(0.0, -b / (2.0 * a))) : (a + b < 0 ? 1.0 : 0.0);
   out3[0] = tau;
   out3[1] = a;
   out3[2] = b;
