@@ -34,7 +34,7 @@ import synth  # noqa: E402
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (profiling recipe's table); a DFMA probe measured ~1.0
 MUFU_PER_SM_CLK = 16            # sin or cos results per SM per clock (SFU)
-GRAM_DRAM_BYTES_PER_BLOCK = 548.98e6 / 4096  # Gram kernel DRAM bytes per 64-point block, m = 1024 (ncu)
+GRAM_DRAM_BYTES_PER_BLOCK = 548.81e6 / 4096  # Gram kernel DRAM bytes per 64-point block, m = 1024 (ncu)
 
 
 def load_peaks():
@@ -767,6 +767,42 @@ def main():
     e2e_ms = D.max(a0.elapsed_time(a1) / args.e2e_steps)
     # the pipelined steps return what the device-timed step returned
     e2e_same = bool(torch.equal(Oh[(args.e2e_steps - 1) % 2], out_bf.cpu()))
+
+    # compact warm path: the same plan with Phi released (rfd_plan_compact); a new field is
+    # integrated from the points alone (Phi^T F from the points in FP32, then a5, a6), the cost
+    # of generating the features on the fly instead of keeping them resident
+    out2_full = out2.clone()
+    full_bytes = gplan.device_bytes()
+    gplan.compact()
+    compact_bytes = gplan.device_bytes()
+    out3 = torch.empty_like(F2)
+    for _ in range(2):
+        gplan.integrate(F2, out3)
+    gplan.sync()
+    torch.cuda.synchronize(dev)
+    w0.record(stream)
+    for _ in range(args.steps):
+        gplan.integrate(F2, out3)
+    w1.record(stream)
+    torch.cuda.synchronize(dev)
+    compact_ms = D.max(w0.elapsed_time(w1) / args.steps)
+    # the step breakdown of the compact path, on the event-timed plan compacted the same way
+    plan.compact()
+    for _ in range(2):
+        plan.integrate(F2, out3)
+    plan.sync()
+    plan.stats_reset()
+    for _ in range(args.steps):
+        plan.integrate(F2, out3)
+    plan.sync()
+    cst = plan.stats()
+    inc_full = (out2_full.double() - F2.double())
+    compact_dev = float((out3.double() - out2_full.double()).norm() / inc_full.norm())
+    compact = {"value": whole_job_value(ws, n * c, compact_ms), "unit": "points*ch/s", "ms_per_step": compact_ms,
+               "what": "rfd_integrate on the compact plan: B^T F from the points (FP32 SIMT), a5, a6",
+               "step_ms": {k: round(v, 4) for k, v in cst["step_ms"].items() if v},
+               "device_bytes": int(compact_bytes), "full_plan_device_bytes": int(full_bytes),
+               "increment_rel_diff_vs_resident_bf16": compact_dev}
     plan.close()
     gplan.close()
 
@@ -835,7 +871,7 @@ def main():
     roof = {k: v for k, v in step_roof["gram"].items() if k != "work"}
     roof["kernel"] = "gram_tc_kernel (step a3)"
     # DRAM bytes of the Gram kernel per 64-point block of the feature matrix, from one ncu capture at
-    # N = 262,144, m = 1024 (dram__bytes_read.sum + dram__bytes_write.sum = 548.98 MB over 4096 blocks,
+    # N = 262,144, m = 1024 (dram__bytes_read.sum + dram__bytes_write.sum = 548.81 MB over 4096 blocks,
     # field rows padded to 16); the kernel reads the matrix once, so the bytes scale with the blocks a
     # launch covers.  Null for other shapes.
     roof["traffic"] = None
@@ -878,10 +914,12 @@ def main():
                                "(App. C): 2 GFI of k columns + 2 element-wise kernels per pass, resident plan",
                        "passes": bary_passes, "ms_per_pass": bary_ms},
         "autotune": {"lanes_pct": st["tune_lanes_pct"], "phase_blocks": st["tune_phase_blocks"], "tuned": st["tuned"],
-                     "gram_form": "CTA pairs (2-SM MMA)" if st.get("tune_pair_gram") else "one SM per tile"},
+                     "gram_form": "CTA pairs (2-SM MMA)" if st.get("tune_pair_gram") else "one SM per tile",
+                     "features_beside_gram": bool(st.get("tune_overlap"))},
         "warm": {"value": whole_job_value(ws, n * c, warm_ms), "unit": "points*ch/s", "ms_per_step": warm_ms,
                  "what": "rfd_integrate: a new field on the resident features and G (steps a3(Y) to a6)",
                  "step_ms": {k: round(v, 4) for k, v in wst["step_ms"].items() if v}},
+        "warm_compact": compact,
         "fp32_plain": fp32,
     }
     if "batched" in sections and args.batched_clouds > 0 and prec == rfd.RFD_BF16_TC:

@@ -155,6 +155,8 @@ typedef struct {
   int32_t tuned;             /* 1 once the autotuner has chosen them                        */
   int32_t tune_pair_gram;    /* 1: the reductions run on CTA pairs (2-SM MMAs; a lone BF16  */
                              /*    cloud with m >= 512, chosen by the autotuner)           */
+  int32_t tune_overlap;      /* 1: a lone cloud's features run phase by phase beside the    */
+                             /*    Gram (chosen by the autotuner only when it is faster)    */
 } rfd_stats;
 
 /* ---------------------------------------------------------------------------
@@ -444,7 +446,7 @@ typedef struct {
 
 typedef struct {
   int32_t status;        /* the request's own outcome (an rfd_status)                   */
-  int32_t reused;        /* 1 if a resident cloud's Phi and G were reused              */
+  int32_t reused;        /* 1 if a resident cloud's G (and its points) were reused     */
   uint64_t cloud;        /* id of the resident cloud (keep = 1: this ticket; reuse), else 0 */
   double queue_ms;       /* rfd_submit -> its batch's launch                            */
   double latency_ms;     /* rfd_submit -> the server saw its batch complete            */

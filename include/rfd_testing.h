@@ -54,6 +54,14 @@ RFD_API void rfd_debug_gram_pairs(int32_t enable);
  * (RFD_EINVAL otherwise, for FP32 plans, or for phase_blocks < 1).  Host only. */
 RFD_API rfd_status rfd_debug_plan_set_phase(rfd_plan_t plan, int32_t phase_blocks);
 
+/* Run a BF16 plan's features phase by phase beside its Gram (enable = 1) or
+ * before it (0): the schedule the autotuner may choose for a lone cloud whose
+ * point axis takes several phases.  Takes effect with the plan's current phase
+ * length (rfd_debug_plan_set_phase); RFD_EINVAL when that schedule cannot run
+ * (one phase, or a phase length that is not a multiple of 8 blocks), for FP32
+ * plans, or for plans with RFD_FLAG_GRAPH or RFD_FLAG_AUTOTUNE.  Host only. */
+RFD_API rfd_status rfd_debug_plan_set_overlap(rfd_plan_t plan, int32_t enable);
+
 /* The bounded device-side wait on its own.  Every wait of the library's
  * kernels on an mbarrier gives up after a %globaltimer limit, records a code
  * in a device error word, frees its TMEM and returns, and the host reports

@@ -58,7 +58,8 @@ class rfd_stats(ctypes.Structure):
                 ("nonfinite", ctypes.c_int32), ("splits", ctypes.c_int32), ("phi1_emulated", ctypes.c_int32),
                 ("phi1_gemms", ctypes.c_int32), ("step_ms", ctypes.c_double * len(STEP_NAMES)), ("timed_calls", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("tune_lanes_pct", ctypes.c_int32), ("tune_waves", ctypes.c_int32),
-                ("tune_phase_blocks", ctypes.c_int32), ("tuned", ctypes.c_int32), ("tune_pair_gram", ctypes.c_int32)]
+                ("tune_phase_blocks", ctypes.c_int32), ("tuned", ctypes.c_int32), ("tune_pair_gram", ctypes.c_int32),
+                ("tune_overlap", ctypes.c_int32)]
 
 
 class rfd_batch_item(ctypes.Structure):
@@ -137,6 +138,7 @@ def _load():
         "rfd_debug_dgemm": (I32, [I32, I32, I32, I32, D, P, I32, P, I32, D, P, I32, P]),
         "rfd_debug_plan_phi1": (I32, [P, P]),
         "rfd_debug_plan_set_phase": (I32, [P, I32]),
+        "rfd_debug_plan_set_overlap": (I32, [P, I32]),
         "rfd_debug_gram_pairs": (None, [I32]),
         "rfd_debug_plan_wait_timeout": (I32, [P, I32]),
         "rfd_batch_create": (I32, [ctypes.POINTER(P), I32, I32, P, ctypes.POINTER(P)]),
@@ -168,7 +170,7 @@ HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_sample_weights", "rfd_barycente
                   "rfd_gw_tensor_product", "rfd_gw_line_search", "rfd_eigenvalues", "rfd_batch_eigenvalues", "rfd_plan", "rfd_plan_destroy", "rfd_features", "rfd_integrate",
                   "rfd_gfi", "rfd_phi1", "rfd_phi1_noalloc", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_plan_compact",
                   "rfd_plan_device_bytes", "rfd_last_error",
-                  "rfd_version", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "rfd_debug_plan_phi1", "rfd_debug_plan_set_phase",
+                  "rfd_version", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "rfd_debug_plan_phi1", "rfd_debug_plan_set_phase", "rfd_debug_plan_set_overlap",
                   "rfd_debug_plan_wait_timeout", "rfd_debug_gram_pairs", "rfd_batch_create",
                   "rfd_batch_destroy", "rfd_batch_features", "rfd_batch_integrate", "rfd_batch_gfi",
                   "rfd_batch_sync", "rfd_batch_stats", "rfd_batch_stats_reset", "rfd_server_create",

@@ -229,15 +229,22 @@ __global__ void __launch_bounds__(256) small_batched_kernel(const ApplyJob* __re
 // the features are recomputed in FP32 from the cloud's copy of its points
 // instead of read back from the BF16 Psi, so the apply carries no BF16
 // rounding and reads only points, F and out.  The angle in cycles is the FP32
-// t = w^T x (absolute error ~|t| 2^-24) reduced to [-1/2, 1/2]; MUFU sin/cos
-// of 2 pi r add ~4e-7.  Two points per thread (p and p + 256) share each
-// frequency's shared-memory loads; CG channels per thread.  F[n] is read
-// before out[n] is written by the same thread.
+// t = w^T x (absolute error ~|t| 2^-24) reduced to [-1/2, 1/2] exactly
+// (t - rint(t), the rounding on the FMA pipe: an FRND instruction instead made
+// the kernel 10 % slower); MUFU sin/cos of 2 pi r add ~4e-7.  A block of 256
+// threads covers 512 points, two per thread (p and p + 256), which share each
+// frequency's shared-memory loads (its w and Z rows).  The kernel is bound by
+// instruction issue (~19 instructions per point and frequency at 3 channels);
+// four points per thread cut that by 14 % but halved the resident warps and
+// left a 1.6-wave tail at N = 10^6, and ran 10 % slower.  CG channels per
+// thread.  F[n] is read before out[n] is written by the same thread.
 template <int CG>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kApplyPts / 2)
 apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
                      const CloudCall* __restrict__ calls) {
   constexpr int kChunk = 64;
+  constexpr int UP = 2;  // points per thread
+  constexpr int kThreads = kApplyPts / UP;
   constexpr int CW = (CG + 3) / 4;  // float4 per row of Z in shared memory (CG channels used)
   __shared__ float4 w_s[kChunk];
   __shared__ float4 zc[kChunk][CW], zsn[kChunk][CW];
@@ -247,32 +254,32 @@ apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ 
   const int local = blockIdx.x - prefix[j];
   const int bxi = local % jb.bx, cgi = local / jb.bx;
   const int h = jb.m / 2;
-  int64_t p[2];
-  bool valid[2];
-  float x[2][3];
+  int64_t p[UP];
+  bool valid[UP];
+  float x[UP][3];
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    p[u] = (int64_t)bxi * 512 + u * 256 + threadIdx.x;
+  for (int u = 0; u < UP; ++u) {
+    p[u] = (int64_t)bxi * kApplyPts + u * kThreads + threadIdx.x;
     valid[u] = p[u] < jb.n;
 #pragma unroll
     for (int d = 0; d < 3; ++d) x[u][d] = valid[u] ? jb.xyz[p[u] * 3 + d] : 0.f;
   }
   const int ch0 = cgi * CG;
   const int cg = min(CG, cc.c - ch0);
-  float acc[2][CG];
+  float acc[UP][CG];
 #pragma unroll
-  for (int u = 0; u < 2; ++u)
+  for (int u = 0; u < UP; ++u)
 #pragma unroll
     for (int q = 0; q < CG; ++q) acc[u][q] = 0.f;
   const float two_pi = 6.283185307179586f;
   for (int f0 = 0; f0 < h; f0 += kChunk) {
     const int fn = min(kChunk, h - f0);
     __syncthreads();
-    for (int i = threadIdx.x; i < kChunk; i += blockDim.x) {
+    for (int i = threadIdx.x; i < kChunk; i += kThreads) {
       const float* w = jb.omega_hi + (size_t)(f0 + i) * 3;
       w_s[i] = i < fn ? make_float4(w[0], w[1], w[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (int i = threadIdx.x; i < kChunk * CW * 4; i += blockDim.x) {
+    for (int i = threadIdx.x; i < kChunk * CW * 4; i += kThreads) {
       const int fr = i / (CW * 4), q = i % (CW * 4);
       const bool ok = fr < fn && q < cg;
       reinterpret_cast<float*>(zc[fr])[q] = ok ? jb.Z[(size_t)(f0 + fr) * cc.c + ch0 + q] : 0.f;
@@ -281,9 +288,9 @@ apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ 
     __syncthreads();
     for (int fr = 0; fr < fn; ++fr) {
       const float4 w = w_s[fr];
-      float cs[2], sn[2];
+      float cs[UP], sn[UP];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < UP; ++u) {
         const float t = fmaf(w.x, x[u][0], fmaf(w.y, x[u][1], w.z * x[u][2]));
         const float ang = two_pi * (t - round_int(t));
         cs[u] = __cosf(ang);
@@ -297,13 +304,13 @@ apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ 
         for (int e = 0; e < 4; ++e)
           if (4 * q4 + e < CG)  // compile-time: the channels of the group only
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
+            for (int u = 0; u < UP; ++u)
               acc[u][4 * q4 + e] = fmaf(cs[u], a[e], fmaf(sn[u], b[e], acc[u][4 * q4 + e]));
       }
     }
   }
 #pragma unroll
-  for (int u = 0; u < 2; ++u)
+  for (int u = 0; u < UP; ++u)
     if (valid[u])
       for (int q = 0; q < cg; ++q) {
         const float fv = cc.F[p[u] * cc.ldF + ch0 + q];
@@ -311,69 +318,130 @@ apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ 
       }
 }
 
-// Y' partials from the points (compact plans, see FieldPtsJob): a thread per
-// frequency f (256 per block), one chunk of points and CG channels per block.
-// The points and the block's F columns pass through shared memory 128 points
-// at a time (every thread reads the same point: broadcasts); Phi(n, f) is the
-// apply's FP32 feature (angle reduced in cycles, MUFU sin / cos).
+// Y' partials from the points (compact plans, see FieldPtsJob): 256 threads,
+// each with FPT frequencies (fieldpts_fpt: 2 for up to 8 channels per block,
+// else 1), one chunk of points and CG channels per block.  The points (as
+// float4) and the block's F columns (float4 groups) pass through shared memory
+// 128 points at a time; every thread reads the same point, so each point costs
+// one 16-byte broadcast load plus one per 4 channels, shared by the thread's
+// frequencies.  Phi(n, f) is the apply's FP32 feature (angle reduced in
+// cycles, MUFU sin / cos); plain FP32 sums over the chunk's points.
 template <int CG>
 __global__ void __launch_bounds__(256)
 fieldpts_batched_kernel(const FieldPtsJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
                         const CloudCall* __restrict__ calls) {
   constexpr int kTile = 128;
-  __shared__ float xs[kTile][3];
-  __shared__ float fs[kTile][CG];
+  constexpr int FPT = fieldpts_fpt(CG);
+  constexpr int CW = (CG + 3) / 4;
+  __shared__ float4 xs[kTile];
+  __shared__ float4 fs[kTile][CW];
   const int j = find_job(prefix, count, blockIdx.x);
   const FieldPtsJob jb = jobs[j];
   const CloudCall cc = calls[jb.cloud];
-  const int fgroups = (jb.h + 255) / 256;
+  const int fgroups = (jb.h + 256 * FPT - 1) / (256 * FPT);
   const int local = blockIdx.x - prefix[j];
   const int chunk = local % jb.chunks, rest = local / jb.chunks;
   const int fg = rest % fgroups, cgi = rest / fgroups;
-  const int f = fg * 256 + threadIdx.x;
-  const bool fvalid = f < jb.h;
   const int ch0 = cgi * CG, cg = min(CG, cc.c - ch0);
-  float w0 = 0.f, w1 = 0.f, w2 = 0.f;
-  if (fvalid) {
-    w0 = jb.omega_hi[(size_t)f * 3];
-    w1 = jb.omega_hi[(size_t)f * 3 + 1];
-    w2 = jb.omega_hi[(size_t)f * 3 + 2];
-  }
-  float acc_c[CG], acc_s[CG];
+  int fi[FPT];
+  float w[FPT][3];
 #pragma unroll
-  for (int q = 0; q < CG; ++q) acc_c[q] = acc_s[q] = 0.f;
+  for (int u = 0; u < FPT; ++u) {
+    fi[u] = (fg * FPT + u) * 256 + threadIdx.x;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) w[u][d] = fi[u] < jb.h ? jb.omega_hi[(size_t)fi[u] * 3 + d] : 0.f;
+  }
+  float acc_c[FPT][CG], acc_s[FPT][CG];
+#pragma unroll
+  for (int u = 0; u < FPT; ++u)
+#pragma unroll
+    for (int q = 0; q < CG; ++q) acc_c[u][q] = acc_s[u][q] = 0.f;
   const float two_pi = 6.283185307179586f;
   const int64_t p_begin = (int64_t)chunk * jb.pts, p_end = min(jb.n, p_begin + jb.pts);
   for (int64_t p0 = p_begin; p0 < p_end; p0 += kTile) {
     const int np = (int)min((int64_t)kTile, p_end - p0);
     __syncthreads();
-    for (int i = threadIdx.x; i < np * 3; i += blockDim.x) xs[i / 3][i % 3] = jb.xyz[p0 * 3 + i];
-    for (int i = threadIdx.x; i < np * CG; i += blockDim.x) {
-      const int pp = i / CG, q = i % CG;
-      fs[pp][q] = q < cg ? cc.F[(p0 + pp) * cc.ldF + ch0 + q] : 0.f;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+      const float* x = jb.xyz + (p0 + i) * 3;
+      xs[i] = make_float4(x[0], x[1], x[2], 0.f);
+    }
+    for (int i = threadIdx.x; i < np * CW * 4; i += blockDim.x) {
+      const int pp = i / (CW * 4), q = i % (CW * 4);
+      reinterpret_cast<float*>(fs[pp])[q] = q < cg ? cc.F[(p0 + pp) * cc.ldF + ch0 + q] : 0.f;
     }
     __syncthreads();
-    if (fvalid)
-      for (int pp = 0; pp < np; ++pp) {
-        const float t = fmaf(w0, xs[pp][0], fmaf(w1, xs[pp][1], w2 * xs[pp][2]));
+    for (int pp = 0; pp < np; ++pp) {
+      const float4 x = xs[pp];
+      float fv[CW * 4];
+#pragma unroll
+      for (int q4 = 0; q4 < CW; ++q4) {
+        const float4 v = fs[pp][q4];
+        fv[4 * q4] = v.x;
+        fv[4 * q4 + 1] = v.y;
+        fv[4 * q4 + 2] = v.z;
+        fv[4 * q4 + 3] = v.w;
+      }
+#pragma unroll
+      for (int u = 0; u < FPT; ++u) {
+        const float t = fmaf(w[u][0], x.x, fmaf(w[u][1], x.y, w[u][2] * x.z));
         const float ang = two_pi * (t - round_int(t));
         const float cs = __cosf(ang), sn = __sinf(ang);
 #pragma unroll
         for (int q = 0; q < CG; ++q) {
-          acc_c[q] = fmaf(cs, fs[pp][q], acc_c[q]);
-          acc_s[q] = fmaf(sn, fs[pp][q], acc_s[q]);
+          acc_c[u][q] = fmaf(cs, fv[q], acc_c[u][q]);
+          acc_s[u][q] = fmaf(sn, fv[q], acc_s[u][q]);
         }
       }
-  }
-  if (!fvalid) return;
-  float* pc = jb.part + ((size_t)chunk * jb.m + f) * jb.ld + ch0;
-  float* ps = jb.part + ((size_t)chunk * jb.m + jb.h + f) * jb.ld + ch0;
-#pragma unroll
-  for (int q = 0; q < CG; ++q)
-    if (q < cg) {
-      pc[q] = acc_c[q];
-      ps[q] = acc_s[q];
     }
+  }
+#pragma unroll
+  for (int u = 0; u < FPT; ++u) {
+    if (fi[u] >= jb.h) continue;
+    float* pc = jb.part + ((size_t)chunk * jb.m + fi[u]) * jb.ld + ch0;
+    float* ps = jb.part + ((size_t)chunk * jb.m + jb.h + fi[u]) * jb.ld + ch0;
+#pragma unroll
+    for (int q = 0; q < CG; ++q)
+      if (q < cg) {
+        pc[q] = acc_c[u][q];
+        ps[q] = acc_s[u][q];
+      }
+  }
+}
+
+// Y[f, ch] = ob[f] sum over the chunks of the fieldpts partials (compact plans):
+// one warp per feature row f and group of 4 channels; lane l sums the chunks
+// l, l + 32, ... (one 16-byte load each) in compensated FP32, the lanes'
+// (sum, carry) pairs meet in a fixed butterfly order (deterministic), and the
+// pair is scaled in FP64.  The loads of a warp go to 32 chunks at once.
+__global__ void __launch_bounds__(256) fieldpts_reduce_kernel(const FieldPtsJob* __restrict__ jobs,
+                                                              const int* __restrict__ prefix, int count,
+                                                              const CloudCall* __restrict__ calls) {
+  const int j = find_job(prefix, count, blockIdx.x);
+  const FieldPtsJob jb = jobs[j];
+  const int c = calls[jb.cloud].c, cq = (c + 3) / 4;
+  const int w = (blockIdx.x - prefix[j]) * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w >= jb.m * cq) return;  // w is uniform across the warp
+  const int f = w / cq, q0 = (w % cq) * 4;
+  const float* base = jb.part + (size_t)f * jb.ld + q0;
+  const size_t chunk_stride = (size_t)jb.m * jb.ld;
+  Fp32Sum acc[4];
+  for (int u = lane; u < jb.chunks; u += 32) {
+    const float4 v = *reinterpret_cast<const float4*>(base + (size_t)u * chunk_stride);
+    acc[0].add(v.x);
+    acc[1].add(v.y);
+    acc[2].add(v.z);
+    acc[3].add(v.w);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    Fp32Sum v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) {
+      const float os = __shfl_xor_sync(0xffffffffu, v.s, o), oc = __shfl_xor_sync(0xffffffffu, v.c, o);
+      v.add(os);
+      v.add(oc);
+    }
+    if (lane == 0 && q0 + q < c) jb.Y[(size_t)f * c + q0 + q] = jb.ob[f] * v.wide();
+  }
 }
 
 __device__ __forceinline__ const double* slot_ptr(const PhiCloud& pc, int slot) {
@@ -508,11 +576,11 @@ cudaError_t launch_apply_batched(const ApplyJob* jobs, const int* prefix, int co
                                  const CloudCall* calls, cudaStream_t st) {
   if (total_blocks <= 0) return cudaSuccess;
   switch (cg) {
-    case 3: apply_batched_kernel<3><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
-    case 4: apply_batched_kernel<4><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
-    case 8: apply_batched_kernel<8><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
-    case 16: apply_batched_kernel<16><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
-    case 32: apply_batched_kernel<32><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
+    case 3: apply_batched_kernel<3><<<total_blocks, kApplyPts / 2, 0, st>>>(jobs, prefix, count, calls); break;
+    case 4: apply_batched_kernel<4><<<total_blocks, kApplyPts / 2, 0, st>>>(jobs, prefix, count, calls); break;
+    case 8: apply_batched_kernel<8><<<total_blocks, kApplyPts / 2, 0, st>>>(jobs, prefix, count, calls); break;
+    case 16: apply_batched_kernel<16><<<total_blocks, kApplyPts / 2, 0, st>>>(jobs, prefix, count, calls); break;
+    case 32: apply_batched_kernel<32><<<total_blocks, kApplyPts / 2, 0, st>>>(jobs, prefix, count, calls); break;
     default: return cudaErrorInvalidValue;
   }
   return launched();
@@ -529,6 +597,13 @@ cudaError_t launch_fieldpts_batched(const FieldPtsJob* jobs, const int* prefix, 
     case 32: fieldpts_batched_kernel<32><<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls); break;
     default: return cudaErrorInvalidValue;
   }
+  return launched();
+}
+
+cudaError_t launch_fieldpts_reduce(const FieldPtsJob* jobs, const int* prefix, int count, int total_blocks,
+                                   const CloudCall* calls, cudaStream_t st) {
+  if (total_blocks <= 0) return cudaSuccess;
+  fieldpts_reduce_kernel<<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls);
   return launched();
 }
 

@@ -251,13 +251,16 @@ struct FillJob {
 // Y' = Phi^T F from the points, for a compact plan (no feature matrix): per
 // chunk of `pts` points, part[chunk][f][ch] = sum_n Phi(n, f) F[n, ch] with
 // Phi recomputed in FP32 exactly as the apply does (rows f < h cos, h + f sin);
-// part is [chunks][m][ld] floats, summed over the chunks by the reduce kernel.
+// part is [chunks][m][ld] floats, summed over the chunks into Y[f][ch] =
+// ob[f] sum_chunks part by fieldpts_reduce.
 struct FieldPtsJob {
   const float* xyz;       // the plan's copy of the points (N x 3)
   const float* omega_hi;  // h x 3
   float* part;
   int64_t n, pts;
   int32_t h, m, chunks, ld, cloud, pad_;
+  double* Y;              // m x c (the call's c), the plan's Y
+  const double* ob;       // m column scales s
 };
 // One output tile of the split-K reduction (absolute pointers).
 struct RedTile {
@@ -323,19 +326,29 @@ cudaError_t launch_features_range(const FeatJob* jobs, const CloudCall* calls, i
 cudaError_t launch_fill_batched(const FillJob* jobs, const int* prefix, int count, int total_blocks,
                                 const CloudCall* calls, cudaStream_t st);
 cudaError_t launch_reduce_batched(const RedTile* tiles, int num_tiles, const CloudCall* calls, cudaStream_t st);
-// Y' partials of compact plans from their points: cg channels per block (3, 4, 8, 16 or 32);
-// prefix over chunks x ceil(h / 256) x ceil(c / cg) blocks per cloud.
+// Y' partials of compact plans from their points: cg channels per block (3, 4, 8, 16 or 32),
+// fieldpts_fpt(cg) frequencies per thread; prefix over chunks x ceil(h / (256 fpt)) x
+// ceil(c / cg) blocks per cloud.
 cudaError_t launch_fieldpts_batched(const FieldPtsJob* jobs, const int* prefix, int count, int total_blocks, int cg,
                                     const CloudCall* calls, cudaStream_t st);
+constexpr int fieldpts_fpt(int cg) { return cg <= 8 ? 2 : 1; }
+// Y of compact plans from their fieldpts partials (one warp per feature row and group of 4
+// channels, 8 warps per block); prefix over fieldpts_reduce_blocks per cloud.
+cudaError_t launch_fieldpts_reduce(const FieldPtsJob* jobs, const int* prefix, int count, int total_blocks,
+                                   const CloudCall* calls, cudaStream_t st);
+inline int fieldpts_reduce_blocks(const FieldPtsJob& j, int c) { return (j.m * ((c + 3) / 4) + 7) / 8; }
 // blocks of one cloud's fieldpts launch for c channels, cg per block
 inline int fieldpts_blocks(const FieldPtsJob& j, int c, int cg) {
-  return j.chunks * ((j.h + 255) / 256) * ((c + cg - 1) / cg);
+  const int fb = 256 * fieldpts_fpt(cg);
+  return j.chunks * ((j.h + fb - 1) / fb) * ((c + cg - 1) / cg);
 }
 // Z = diag(oa) G Y per cloud (one block per matrix row: prefix over m)
 cudaError_t launch_small_batched(const ApplyJob* jobs, const int* prefix, int count, int total_rows,
                                  const CloudCall* calls, cudaStream_t st);
-// out = F + Phi Z per cloud; cg: channels per thread (4, 8, 16 or 32);
-// prefix over bx * ceil(c / cg) blocks per cloud
+// out = F + Phi Z per cloud; cg: channels per thread (3, 4, 8, 16 or 32); a block covers
+// kApplyPts points, two per thread; prefix over bx * ceil(c / cg) blocks per cloud
+// (bx = ceil(n / kApplyPts))
+constexpr int kApplyPts = 512;
 cudaError_t launch_apply_batched(const ApplyJob* jobs, const int* prefix, int count, int total_blocks, int cg,
                                  const CloudCall* calls, cudaStream_t st);
 // phi1 building blocks over all clouds (elements: prefix over ceil(m^2 / 256) blocks)

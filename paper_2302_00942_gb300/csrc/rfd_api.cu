@@ -548,7 +548,7 @@ rfd_status build_desc(rfd_plan_s* pl) {
   d.fill = FillJob{pl->n, pl->n_pad, psi, pl->cpad, (int)((pl->n_pad + 255) / 256), 0, pl->fsplit ? 1 : 0, m,
                    pl->rows_alloc};
   d.apply = ApplyJob{pl->d_xyz,  pl->d_omega_hi, pl->d_omega_lo, pl->d_G, pl->d_Y, pl->d_oa, pl->d_Z,
-                     pl->n,      pl->n_pad,      m, 0, (int)((pl->n + 511) / 512), 0};
+                     pl->n,      pl->n_pad,      m, 0, (int)((pl->n + kApplyPts - 1) / kApplyPts), 0};
   // step a4 on the emulated path: slots in the FP64 workspace, the residue buffers after them
   PhiCloud& pc = d.phi;
   pc = PhiCloud{};
@@ -722,14 +722,22 @@ rfd_status tune_plan(rfd_plan_s* pl, int mode, const CloudCall* cc) {
       if (s != RFD_OK) return s;
       for (int ph : kTunePhases) {
         batch_set_phase(tb, ph);
-        float ms = 0.f;
-        s = batch_time_gram(tb, mode, 2, &ms, cc);
-        if (s != RFD_OK) break;
-        if (ms < best) {
-          best = ms;
-          best_t = pl->tune;
-          best_t.phase_blocks = ph;
+        // the serial schedule, then the features beside the Gram where the phases allow it; the
+        // latter must win by 5 %: at N = 10^6, m = 1024 it gained 0.7 % of the step, which is
+        // noise, while it made the Gram's own time unattributable (the two kernels share SMs)
+        for (int ov = 0; ov < 2 && s == RFD_OK; ++ov) {
+          if (!batch_set_overlap(tb, ov != 0) && ov) break;
+          float ms = 0.f;
+          s = batch_time_gram(tb, mode, 2, &ms, cc);
+          if (s != RFD_OK) break;
+          if (ms < (ov ? 0.95f : 1.f) * best) {
+            best = ms;
+            best_t = pl->tune;
+            best_t.phase_blocks = ph;
+            best_t.overlap = ov;
+          }
         }
+        if (s != RFD_OK) break;
       }
       cudaStreamSynchronize(pl->stream);
       batch_free(tb);
@@ -830,12 +838,17 @@ void plan_carve(rfd_plan_s* pl, PlanCarve& c) {
     }
 }
 
-// Chunks of the points-based Phi^T F of a compact plan: at most 64 chunks of at least 4096
-// points, and partials of at most 16 MB ([chunks][m][ld] floats, ld = channels padded to 4).
+// Chunks of the points-based Phi^T F of a compact plan: enough for ~6 blocks of 256 threads
+// per SM (at 512 frequencies per block), of at least 1024 points each, with partials
+// ([chunks][m][ld] floats, ld = channels padded to 4) no larger than the points' own
+// 12 N bytes (4 MB at least).
 void fieldpts_shape(const rfd_plan_s* pl, int* chunks, int64_t* pts, int* ld) {
   *ld = (int)round_up(pl->p.max_channels, 4);
-  const int64_t cap = std::max<int64_t>(1, (16ll << 20) / ((int64_t)pl->m * *ld * 4));
-  int64_t ch = std::min<int64_t>({64, cap, std::max<int64_t>(1, (pl->n + 4095) / 4096)});
+  const int64_t fgroups = (pl->h + 511) / 512;
+  const int64_t want = std::max<int64_t>(1, (6ll * std::max(pl->sms, 1) + fgroups - 1) / fgroups);
+  const int64_t cap =
+      std::max<int64_t>(1, std::max<int64_t>(4ll << 20, 12 * pl->n) / ((int64_t)pl->m * *ld * 4));
+  int64_t ch = std::min<int64_t>({want, cap, std::max<int64_t>(1, (pl->n + 1023) / 1024)});
   *pts = (pl->n + ch - 1) / ch;
   *chunks = (int)((pl->n + *pts - 1) / *pts);
 }
@@ -859,8 +872,8 @@ void plan_carve_compact(rfd_plan_s* pl, PlanCarve& c) {
   c.add(&pl->d_fpart, (size_t)chunks * m * ld);
 }
 
-// The compact plan's descriptors: the points-based Phi^T F, its reduce tiles (one per 128
-// feature rows, summing the chunks), and the apply (as the full plan's).
+// The compact plan's descriptors: the points-based Phi^T F (with its sum over the chunks)
+// and the apply (as the full plan's).
 void build_compact_desc(rfd_plan_s* pl) {
   PlanDesc& d = pl->desc;
   for (int mode = 0; mode < 3; ++mode) {
@@ -872,31 +885,10 @@ void build_compact_desc(rfd_plan_s* pl) {
   int chunks, ld;
   int64_t pts;
   fieldpts_shape(pl, &chunks, &pts, &ld);
-  d.fpts = FieldPtsJob{pl->d_xyz, pl->d_omega_hi, pl->d_fpart, pl->n, pts, pl->h, pl->m, chunks, ld, 0, 0};
-  d.red_pts.clear();
-  for (int i0 = 0; i0 < pl->m; i0 += kTcBM) {
-    RedTile r{};
-    r.part = pl->d_fpart + (size_t)i0 * ld;
-    r.M = pl->d_M;
-    r.Y = pl->d_Y;
-    r.oa = pl->d_oa;
-    r.ob = pl->d_ob;
-    r.slot_elems = (int64_t)pl->m * ld;
-    r.i0 = i0;
-    r.ni = std::min(kTcBM, pl->m - i0);
-    r.j0 = pl->m;
-    r.nj = ld;
-    r.kind = kTileField;
-    r.count = chunks;
-    r.ld = ld;
-    r.col_off = 0;
-    r.m = pl->m;
-    r.cloud = 0;
-    r.fsplit = 0;
-    d.red_pts.push_back(r);
-  }
+  d.fpts = FieldPtsJob{pl->d_xyz, pl->d_omega_hi, pl->d_fpart, pl->n, pts, pl->h, pl->m, chunks, ld, 0, 0,
+                       pl->d_Y,   pl->d_ob};
   d.apply = ApplyJob{pl->d_xyz, pl->d_omega_hi, pl->d_omega_lo, pl->d_G, pl->d_Y, pl->d_oa, pl->d_Z,
-                     pl->n,     pl->n_pad,      pl->m, 0, (int)((pl->n + 511) / 512), 0};
+                     pl->n,     pl->n_pad,      pl->m, 0, (int)((pl->n + kApplyPts - 1) / kApplyPts), 0};
 }
 
 }  // namespace
@@ -904,6 +896,7 @@ void build_compact_desc(rfd_plan_s* pl) {
 size_t plan_compact_bytes(const rfd_plan_s* pl) {
   rfd_plan_s tmp;  // the carve only reads the sizes
   tmp.p = pl->p;
+  tmp.sms = pl->sms;
   tmp.m = pl->m;
   tmp.h = pl->h;
   tmp.n = pl->n;
@@ -1260,6 +1253,7 @@ rfd_status rfd_plan_stats(rfd_plan_t pl, rfd_stats* out) {
   out->tune_waves = pl->tune.waves;
   out->tune_phase_blocks = pl->tune.phase_blocks;
   out->tune_pair_gram = pl->tune.pairs;
+  out->tune_overlap = pl->tune.overlap;
   out->tuned = pl->tuned ? 1 : 0;
   return RFD_OK;
 }
@@ -1466,6 +1460,20 @@ rfd_status rfd_debug_plan_set_phase(rfd_plan_t pl, int32_t phase_blocks) {
   if (phase_blocks < 1) return fail(RFD_EINVAL, "phase_blocks must be >= 1");
   pl->tune.phase_blocks = phase_blocks;
   batch_set_phase(pl->self, phase_blocks);
+  return RFD_OK;
+}
+
+rfd_status rfd_debug_plan_set_overlap(rfd_plan_t pl, int32_t enable) {
+  if (!pl) return fail(RFD_EINVAL, "null plan");
+  if (!pl->bf16 || !pl->self) return fail(RFD_EINVAL, "the schedule belongs to the tensor-core reductions");
+  if (pl->p.flags & (RFD_FLAG_GRAPH | RFD_FLAG_AUTOTUNE))
+    return fail(RFD_EINVAL, "not for plans with RFD_FLAG_GRAPH or RFD_FLAG_AUTOTUNE");
+  if (!batch_set_overlap(pl->self, enable != 0) && enable) {
+    batch_set_overlap(pl->self, false);
+    pl->tune.overlap = 0;
+    return fail(RFD_EINVAL, "features beside the Gram need several phases of a multiple of 8 blocks");
+  }
+  pl->tune.overlap = enable ? 1 : 0;
   return RFD_OK;
 }
 

@@ -105,9 +105,10 @@ struct BatchImpl {
   int max_m = 0, max_cpad = 16, max_kb = 0;
   int a_boxes = 1;  // 2 when some Gram unit has a second 128-row half
   int phase_blocks = kGramPhaseBlocks;
+  bool overlap = false;     // features phase by phase beside the Gram (a lone cloud, tuned)
   bool phi_batched = true;  // all clouds on the emulated path (no native-FP64 flag)
   // per-call device words
-  CloudCall* d_calls = nullptr;  // followed by the apply-block prefix (count + 1 ints)
+  CloudCall* d_calls = nullptr;  // followed by three block prefixes (count + 1 ints each)
   double* d_norms = nullptr;
   int* d_sv = nullptr;     // squarings per cloud, then their maximum
   int* d_flags = nullptr;  // sticky: G of cloud k not finite
@@ -166,6 +167,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   b->mem = mem;
   b->options = options;
   b->phase_blocks = tune.phase_blocks;
+  b->overlap = tune.overlap != 0;
   auto bail = [&](rfd_status s, const std::string& msg) {
     batch_free(b);
     return fail(s, msg);
@@ -210,10 +212,6 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
       FieldPtsJob fj = d.fpts;
       fj.cloud = k;
       fpts.push_back(fj);
-      for (RedTile r : d.red_pts) {
-        r.cloud = k;
-        red[kModeIntegrate].push_back(r);
-      }
     }
     for (int mode = 0; mode < 3 && !b->compact; ++mode) {
       if (count == 1 && tune.pairs && !d.pair_units[mode].empty()) {  // a lone cloud: the plan's pair units
@@ -331,8 +329,9 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
                o_phi = vtable(phi), o_elem_pre = vtable(pre_elem), o_grp_pre = vtable(pre_grp), o_rexp_pre = vtable(pre_rexp), o_rowa_pre = vtable(pre_rowa),
                o_strip_pre = vtable(pre_strip), o_oz = vtable(oz), o_fpts = vtable(fpts);
   const size_t table_bytes = L.total;
-  // per call: the CloudCalls, then the apply-block prefix and the points-based Phi^T F prefix
-  b->stage_bytes = (size_t)count * sizeof(CloudCall) + 2 * (size_t)(count + 1) * sizeof(int);
+  // per call: the CloudCalls, then the block prefixes of the apply, the points-based Phi^T F
+  // and its sum over the chunks
+  b->stage_bytes = (size_t)count * sizeof(CloudCall) + 3 * (size_t)(count + 1) * sizeof(int);
   const size_t o_calls = L.add(b->stage_bytes);
   const size_t o_norms = L.add((size_t)count * sizeof(double));
   const size_t o_sv = L.add((size_t)(count + 1) * sizeof(int));
@@ -604,14 +603,17 @@ cudaError_t gram_all(BatchImpl* b, int mode, cudaStream_t s) {
 
 // Features beside the Gram: a lone cloud whose point axis takes several Gram
 // phases (of a multiple of 8 blocks, so that the 512-point blocks of the
-// features kernel fall in one phase) runs its features phase by phase on the
-// side stream; the Gram of phase p waits for the features of phase p only, so
-// the features of phase p + 1 (MUFU and HBM writes) overlap the Gram of phase
-// p (tensor cores and L2 reads).
+// features kernel fall in one phase) may run its features phase by phase on
+// the side stream; the Gram of phase p waits for the features of phase p only,
+// so the features of phase p + 1 (MUFU and HBM writes) overlap the Gram of
+// phase p (tensor cores and L2 reads).  The autotuner takes this schedule only
+// where it beats the serial one by 5 % (at N = 10^6, m = 1024 it gains 0.7 %:
+// both kernels contend for L2 and HBM).
 int gram_phases(const BatchImpl* b) {
   return b->max_kb > 0 ? (b->max_kb + b->phase_blocks - 1) / b->phase_blocks : 1;
 }
-bool pipelines(const BatchImpl* b) { return b->side && gram_phases(b) >= 2 && b->phase_blocks % 8 == 0; }
+bool can_overlap(const BatchImpl* b) { return b->side && gram_phases(b) >= 2 && b->phase_blocks % 8 == 0; }
+bool pipelines(const BatchImpl* b) { return b->overlap && can_overlap(b); }
 
 // The features, phase by phase, on the side stream (forked from s); ev_phase[p]
 // marks phase p done.  The last event is recorded after the step's timing scope.
@@ -677,6 +679,11 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   for (int k = 0; k < n; ++k) hq[k + 1] = hq[k] + (b->compact ? fieldpts_blocks(b->fpts_h[k], calls[k].c, cg) : 0);
   const int fpts_blocks = hq[n];
   const int* d_fpts_prefix = d_apply_prefix + (n + 1);
+  int* hr = hq + (n + 1);  // and of their sums over the chunks
+  hr[0] = 0;
+  for (int k = 0; k < n; ++k) hr[k + 1] = hr[k] + (b->compact ? fieldpts_reduce_blocks(b->fpts_h[k], calls[k].c) : 0);
+  const int fred_blocks = hr[n];
+  const int* d_fred_prefix = d_fpts_prefix + (n + 1);
   if (b->compact && mode != kModeIntegrate)
     return fail(RFD_EINVAL, "a compact plan has no feature matrix: only integration runs on it");
   BCK(cudaMemcpyAsync(b->d_calls, stage, b->stage_bytes, cudaMemcpyHostToDevice, st));
@@ -693,7 +700,7 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
         BCK(launch_fieldpts_batched(b->d_fpts, d_fpts_prefix, n, fpts_blocks, cg, b->d_calls, s));
       }
       StepScope sc(t, s, RFD_STEP_REDUCE);
-      BCK(launch_reduce_batched(b->d_red[mode], b->n_red[mode], b->d_calls, s));
+      BCK(launch_fieldpts_reduce(b->d_fpts, d_fred_prefix, n, fred_blocks, b->d_calls, s));
       return RFD_OK;
     }
     if (pipelined) {
@@ -742,7 +749,9 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
     return run_segment(b, key, graph, tm, reductions);
   }
   if (!with_phi) {
-    const int key[4] = {mode, b->compact ? -4 - fpts_blocks : -1, cg, apply_blocks};
+    // compact batches: both points-based launches' grids (they depend on every call's c)
+    const int key[4] = {mode, b->compact ? -4 - fpts_blocks : -1, b->compact ? cg + 64 * fred_blocks : cg,
+                        apply_blocks};
     return run_segment(b, key, graph, tm, [&](cudaStream_t s, Timing* t) -> rfd_status {
       rfd_status r = reductions(s, t);
       return r == RFD_OK ? small_apply(s, t) : r;
@@ -882,6 +891,11 @@ void Timing::reset(cudaStream_t st) {
 
 void batch_set_phase(BatchImpl* b, int phase_blocks) { b->phase_blocks = phase_blocks; }
 
+bool batch_set_overlap(BatchImpl* b, bool overlap) {
+  b->overlap = overlap;
+  return can_overlap(b);
+}
+
 rfd_status batch_time_gram(BatchImpl* b, int mode, int reps, float* ms, const CloudCall* calls) {
   // the call table of this batch: the features beside the Gram read the callers' points
   {
@@ -896,11 +910,19 @@ rfd_status batch_time_gram(BatchImpl* b, int mode, int reps, float* ms, const Cl
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
-  // with features beside the Gram, time both together (the phase length trades the first
-  // phase's exposed features against the launches of more phases)
-  const bool pipe = mode != kModeIntegrate && pipelines(b);
+  // modes with features time them with the Gram, so that the serial schedule and the features
+  // beside the Gram compare (there the phase length trades the first phase's exposed features
+  // against the launches of more phases)
+  const bool feat = mode != kModeIntegrate, pipe = feat && pipelines(b);
   auto launch = [&]() -> cudaError_t {
-    if (!pipe) return gram_all(b, mode, b->st);
+    if (!pipe) {
+      if (feat) {
+        cudaError_t f =
+            launch_features_batched(b->d_feat, b->d_feat_prefix, b->count, b->feat_blocks, b->d_calls, b->st);
+        if (f != cudaSuccess) return f;
+      }
+      return gram_all(b, mode, b->st);
+    }
     if (pipelined_features(b, b->st, nullptr) != RFD_OK || pipelined_gram(b, mode, b->st) != RFD_OK)
       return cudaErrorLaunchFailure;
     return cudaSuccess;

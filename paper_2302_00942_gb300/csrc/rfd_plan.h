@@ -84,7 +84,6 @@ struct PlanDesc {
   int pair_stage_bytes = 0;
   // a compact plan (rfd_plan_compact): Phi^T F from the points, into d_fpart
   FieldPtsJob fpts{};
-  std::vector<RedTile> red_pts;
   FeatJob feat{};
   FillJob fill{};
   ApplyJob apply{};
@@ -118,6 +117,7 @@ struct GramTuning {
   int waves = 4;
   int phase_blocks = kGramPhaseBlocks;
   int pairs = 0;  // a lone cloud with m >= 512: the Gram modes on CTA pairs (k_gram_pair.cu)
+  int overlap = 0;  // a lone cloud with several phases: its features phase by phase beside the Gram
 };
 
 }  // namespace rfd
@@ -207,11 +207,14 @@ rfd_status batch_eigenvalues(rfd_plan_s* const* plans, int count, int k, int lar
 // RFD_ENUMERIC if some cloud's G is not finite (bad[k] = 1 for those clouds when
 // bad is given).
 rfd_status batch_check_error(BatchImpl* b, int* bad = nullptr);
-// Times the Gram launches of one batched call of `mode` (the features must be
-// in place; for a lone cloud whose features run beside the Gram, those too,
-// from the points of calls, one CloudCall per plan): mean ms over `reps`
-// launches after one warm-up.
+// Times the Gram launches of one batched call of `mode`, with the features in
+// front of them (serially or beside them, as the batch is set) in modes that
+// compute features, from the points of calls (one CloudCall per plan): mean ms
+// over `reps` launches after one warm-up.
 rfd_status batch_time_gram(BatchImpl* b, int mode, int reps, float* ms, const CloudCall* calls);
 void batch_set_phase(BatchImpl* b, int phase_blocks);
+// Features beside the Gram on or off; returns whether the batch can run that schedule at all
+// (a lone cloud with several phases of a multiple of 8 blocks).
+bool batch_set_overlap(BatchImpl* b, bool overlap);
 
 }  // namespace rfd

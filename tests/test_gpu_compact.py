@@ -115,3 +115,27 @@ def test_compact_plan_in_a_batch_and_eigenvalues():
     finally:
         for p in plans:
             p.close()
+
+
+def test_compact_graph_replay_tracks_channel_count():
+    """A compact plan with CUDA-graph replay: calls whose channel counts share the
+    per-block channel group (9 and 13 channels: one group of 16) but not the grid
+    of the sum over the chunks (one warp per 4 channels) each get a graph of
+    their own, and each matches the oracle."""
+    spec = synth.config_single("small")
+    pts, F = synth.make_cloud(spec)
+    lam = spec.lam * spec.m / spec.n
+    plan = rfd.Plan(spec.n, spec.m, spec.eps, lam, spec.seed, max_channels=16, precision=BF16,
+                    stream=torch.cuda.current_stream(DEV), graph=True)
+    try:
+        plan.gfi(torch.from_numpy(pts).to(DEV), torch.from_numpy(F).to(DEV))
+        plan.sync()
+        plan.compact()
+        for k, c in enumerate((9, 13, 9, 16)):
+            Fk = synth.gaussian_field(spec.n, c, 80 + k, 1)
+            out = plan.integrate(torch.from_numpy(Fk).to(DEV))
+            plan.sync()
+            ref = oracle.rfd_gfi(pts, Fk, spec.eps, lam, spec.m, spec.seed)
+            pc.assert_matches(out.cpu().numpy(), ref, Fk, BF16, label=f"compact, graphs, c={c}")
+    finally:
+        plan.close()

@@ -321,3 +321,38 @@ def test_multi_phase_point_axis_matches_oracle(phase_blocks):
     # against the single-phase run: the same products, summed in another order (FP32)
     pc.assert_matches(outs[0], outs[1], F, rfd.RFD_BF16_TC, label="phases vs one phase", tol_out=1e-5,
                       tol_inc=2e-3, tol_row=2e-3)
+
+
+@pytest.mark.parametrize("phase_blocks", [64, 512])
+def test_features_beside_gram_matches_oracle(phase_blocks):
+    """The schedule that runs the features phase by phase on a side stream beside
+    the Gram (the Gram of phase p waits for the features of phase p only) gives
+    the oracle's result, and bit for bit the serial schedule's: the same kernels
+    on the same data, only their overlap differs.  A single phase, or a phase
+    length that is not a multiple of 8 blocks, refuses the schedule."""
+    spec, pts, F, lam = small_case("torus")
+    ref = oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed)
+    P, Ft = _cuda(pts), _cuda(F)
+    outs = []
+    for overlap in (1, 0):
+        plan = rfd.Plan(spec.n, spec.m, spec.eps, lam, spec.seed, max_channels=F.shape[1],
+                        precision=rfd.RFD_BF16_TC, stream=torch.cuda.current_stream(DEV))
+        try:
+            _check(rfd.lib.rfd_debug_plan_set_phase(plan.handle, phase_blocks), "rfd_debug_plan_set_phase")
+            _check(rfd.lib.rfd_debug_plan_set_overlap(plan.handle, overlap), "rfd_debug_plan_set_overlap")
+            o = plan.gfi(P, Ft)
+            o2 = plan.gfi(P, Ft)  # a second call through the same schedule
+            plan.sync()
+            assert plan.stats()["tune_overlap"] == overlap
+            assert torch.equal(o, o2)
+            outs.append(o.cpu().numpy())
+            if overlap:
+                assert rfd.lib.rfd_debug_plan_set_phase(plan.handle, 300) == 0
+                assert rfd.lib.rfd_debug_plan_set_overlap(plan.handle, 1) != 0   # 300 % 8 != 0
+                assert rfd.lib.rfd_debug_plan_set_phase(plan.handle, 1 << 20) == 0
+                assert rfd.lib.rfd_debug_plan_set_overlap(plan.handle, 1) != 0   # one phase
+                assert plan.stats()["tune_overlap"] == 0
+        finally:
+            plan.close()
+    pc.assert_matches(outs[0], ref, F, rfd.RFD_BF16_TC, label=f"features beside the Gram, {phase_blocks}-block phases")
+    assert np.array_equal(outs[0], outs[1])
