@@ -439,23 +439,49 @@ rfd_status phi1_select(BatchImpl* b, cudaStream_t st) {
 // squaring steps, phi1(2Y) = (e^Y + I) phi1(Y) / 2 with e^Y = I + Y phi1(Y):
 // E = I + X F, F <- (E F + F) / 2, E <- E^2; G = lambda F, and the finiteness
 // flags.  Slots are swapped instead of copied.
-// Moduli of the first two Horner products (see phi1_core), from the batch's largest
-// scaled norm: {for j = 2, for j = 1}.  Part of the CUDA-graph key of the segment.
-void horner_moduli(const BatchImpl* b, int out[2]) {
-  double xmax = 0.0;  // largest ||2^-s_c lambda M||_1 over the batch (<= theta_16)
+// Moduli per product of the Taylor evaluation (see phi1_core), from the batch's
+// largest scaled norm x = max ||2^-s lambda M||_1 <= theta_16 and largest m:
+// {X^2, X^3 and X^4 (one count: they share operands), Horner j = 2, 1, 0}.
+// An emulated product P = A B with k-bit operand integers errs by at most
+// 2^(1-k) K max|A| max|B| per entry; a native FP64 product by ~K u max|A|
+// max|B|.  If P's error reaches F = phi1(X) multiplied by at most S, and F's
+// largest entry is at least 1/2 (its diagonal is >= phi1(-x) >= 0.6), then
+// k = 55 + log2(max|A| max|B| S / (1/2)) bits keep P's share of F's error at
+// half a native product's worst case or less.  Entry bounds (|M| is symmetric,
+// so its row and column norms agree): |(X^i)_ab| <= x^i; the Horner partial
+// sums F_j = B_j + X^4 F_(j+1) have entries <= f_j = sum_(k >= 4j) c_k x^(k-4j).
+//   X^p (p = 2, 3, 4):  max|A| max|B| = x^p, S = sum_(k >= p) k c_k x^(k-p)
+//     (X^p occurs at most k times in the evaluation of X^k);
+//   Horner j (X^4 F_(j+1) + B_j):  x^4 f_(j+1), S = x^(4j) (the factors X^4 to come).
+// The Horner products take far fewer moduli than the powers: their operands
+// F_(j+1) are small (f_3 ~ c_12 = 1/13!).  The counts enter the CUDA-graph key.
+void product_moduli(const BatchImpl* b, int out[4]) {
+  double x = 0.0;
   for (int c = 0; c < b->count; ++c)
-    if (std::isfinite(b->h_norms[c])) xmax = std::max(xmax, std::ldexp(b->h_norms[c], -std::max(b->h_sv[c], 0)));
-  xmax = std::min(xmax, kThetaT16);
-  const double x4 = xmax * xmax * xmax * xmax;
-  auto moduli_for = [&](double q) {
-    const int k = (int)std::ceil(53.0 + std::log2(std::max(q, 1e-300)));
+    if (std::isfinite(b->h_norms[c])) x = std::max(x, std::ldexp(b->h_norms[c], -std::max(b->h_sv[c], 0)));
+  x = std::min(x, kThetaT16);
+  double ck[kTaylorDegree + 1];
+  ck[0] = 1.0;
+  for (int k = 1; k <= kTaylorDegree; ++k) ck[k] = ck[k - 1] / (double)(k + 1);
+  auto moduli_for = [&](double scale) {  // scale = max|A| max|B| S
+    const int k = (int)std::ceil(55.0 + std::log2(std::max(scale / 0.5, 1e-300)));
     return std::min(16, std::max(4, ozaki_moduli_for_bits(std::max(b->max_m, 1), k)));
   };
-  out[0] = moduli_for(x4 * x4);
-  out[1] = moduli_for(x4);
+  int powers = 4;
+  for (int p = 2; p <= 4; ++p) {
+    double S = 0.0;
+    for (int k = p; k <= kTaylorDegree; ++k) S += k * ck[k] * std::pow(x, k - p);
+    powers = std::max(powers, moduli_for(std::pow(x, p) * S));
+  }
+  out[0] = powers;
+  for (int j = 2; j >= 0; --j) {
+    double f = 0.0;  // f_(j+1)
+    for (int k = 4 * (j + 1); k <= kTaylorDegree; ++k) f += ck[k] * std::pow(x, k - 4 * (j + 1));
+    out[3 - j] = moduli_for(std::pow(x, 4) * f * std::pow(x, 4 * j));
+  }
 }
 
-rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s, const int horner_nmod[2]) {
+rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s, const int nmod[4]) {
   const int n = b->count;
   auto comb = [&](int dst, std::initializer_list<int> src, std::initializer_list<double> a, double diag, int kmode,
                   int mask) {
@@ -467,12 +493,7 @@ rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s, const int horner_
     for (double v : a) a4[i++] = v;
     return launch_bcombine(b->d_phi, b->d_elem_prefix, n, b->elem_blocks, dst, s4, a4, diag, kmode, mask, st);
   };
-  // Moduli per product.  A product whose result enters F scaled by a factor Q with
-  // max|Q| <= q only needs k = 53 - log2(1/q) bits of its operands for FP64 accuracy
-  // relative to F (the emulation errs by ~2^-k K max|Q| max|F| per entry, like an FP64
-  // product's K u |Q||F|).  The first two Horner products enter F through one or two
-  // more factors X^4, max|X^4| <= ||X||_1^4 (the batch's largest scaled norm); the
-  // fewest moduli that give those bits for the batch's largest m are used.
+  // moduli per product (product_moduli); the squaring steps take all 16
   const int kfull = 16;
   // the A / B residues hold the operands of the previous product (split with the same
   // number of moduli, hence the same integer width): split only what changed
@@ -495,11 +516,11 @@ rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s, const int horner_
   ck[0] = 1.0;
   for (int k = 1; k <= kTaylorDegree; ++k) ck[k] = ck[k - 1] / (double)(k + 1);
   if (max_s > 0) BCK(comb(sX, {sX}, {1.0}, 0.0, 2, -1));  // X = 2^-s X
-  BCK(gemm(sX, sX, kNoSlot, sX2, 1.0, 0.0, 0.0, -1, kfull));
+  BCK(gemm(sX, sX, kNoSlot, sX2, 1.0, 0.0, 0.0, -1, nmod[0]));
   wrote(sX2);
-  BCK(gemm(sX2, sX, kNoSlot, sX3, 1.0, 0.0, 0.0, -1, kfull));
+  BCK(gemm(sX2, sX, kNoSlot, sX3, 1.0, 0.0, 0.0, -1, nmod[0]));
   wrote(sX3);
-  BCK(gemm(sX2, sX2, kNoSlot, sX4, 1.0, 0.0, 0.0, -1, kfull));
+  BCK(gemm(sX2, sX2, kNoSlot, sX4, 1.0, 0.0, 0.0, -1, nmod[0]));
   wrote(sX4);
   BCK(comb(sF, {sX, sX2, sX3, sX4}, {ck[13], ck[14], ck[15], ck[16]}, ck[12], 0, -1));  // B_3 + c_16 X^4
   wrote(sF);
@@ -507,7 +528,7 @@ rfd_status phi1_core(BatchImpl* b, cudaStream_t st, int max_s, const int horner_
   for (int j = 2; j >= 0; --j) {
     BCK(comb(sB, {sX, sX2, sX3}, {ck[4 * j + 1], ck[4 * j + 2], ck[4 * j + 3]}, 0.0, 0, -1));  // B_j - c_4j I
     wrote(sB);
-    const int nm = j == 2 ? horner_nmod[0] : (j == 1 ? horner_nmod[1] : kfull);  // X^4 factors still to come
+    const int nm = nmod[3 - j];
     BCK(gemm(sX4, F, sB, Fb, 1.0, 1.0, ck[4 * j], -1, nm));  // F <- B_j + X^4 F
     wrote(Fb);
     std::swap(F, Fb);
@@ -790,10 +811,10 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
     pl->stats.phi1_emulated = 1;
     pl->stats.phi1_gemms = 6 + 2 * s;
   }
-  int hn[2];
-  horner_moduli(b, hn);
-  const int key_post[4] = {mode, max_s + 256 * (hn[0] * 32 + hn[1]), with_apply ? cg : 0,
-                           with_apply ? apply_blocks : 0};
+  int hn[4];
+  product_moduli(b, hn);
+  const int key_post[4] = {mode, max_s + 64 * ((hn[0] - 1) | (hn[1] - 1) << 4 | (hn[2] - 1) << 8 | (hn[3] - 1) << 12),
+                           with_apply ? cg : 0, with_apply ? apply_blocks : 0};
   r = run_segment(b, key_post, graph, tm, [&](cudaStream_t s, Timing* t) -> rfd_status {
     {
       StepScope sc(t, s, RFD_STEP_PHI1);
@@ -827,8 +848,8 @@ rfd_status batch_phi1_only(BatchImpl* b) {
     pl->stats.phi1_emulated = 1;
     pl->stats.phi1_gemms = 6 + 2 * b->h_sv[k];
   }
-  int hn[2];
-  horner_moduli(b, hn);
+  int hn[4];
+  product_moduli(b, hn);
   r = phi1_core(b, st, max_s, hn);
   if (r != RFD_OK) return r;
   for (rfd_plan_s* pl : b->plans) pl->have_G = true;
