@@ -156,7 +156,7 @@ typedef struct {
   int32_t tune_pair_gram;    /* 1: the reductions run on CTA pairs (2-SM MMAs; a lone BF16  */
                              /*    cloud with m >= 512, chosen by the autotuner)           */
   int32_t tune_overlap;      /* 1: a lone cloud's features run phase by phase beside the    */
-                             /*    Gram (chosen by the autotuner only when it is faster)    */
+                             /*    Gram (a test hook selects it; the autotuner does not)    */
 } rfd_stats;
 
 /* ---------------------------------------------------------------------------

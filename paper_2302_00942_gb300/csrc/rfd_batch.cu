@@ -627,9 +627,9 @@ cudaError_t gram_all(BatchImpl* b, int mode, cudaStream_t s) {
 // features kernel fall in one phase) may run its features phase by phase on
 // the side stream; the Gram of phase p waits for the features of phase p only,
 // so the features of phase p + 1 (MUFU and HBM writes) overlap the Gram of
-// phase p (tensor cores and L2 reads).  The autotuner takes this schedule only
-// where it beats the serial one by 5 % (at N = 10^6, m = 1024 it gains 0.7 %:
-// both kernels contend for L2 and HBM).
+// phase p (tensor cores and L2 reads).  The autotuner does not choose it (at
+// N = 10^6, m = 1024 it gains 1.5 - 2 % of the step, and the Gram's own time
+// is no longer measurable); rfd_debug_plan_set_overlap selects it.
 int gram_phases(const BatchImpl* b) {
   return b->max_kb > 0 ? (b->max_kb + b->phase_blocks - 1) / b->phase_blocks : 1;
 }
@@ -661,9 +661,12 @@ rfd_status pipelined_features(BatchImpl* b, cudaStream_t s, Timing* t) {
 }
 
 // The Gram phases on s, each after the features of its phase (pipelined_features first).
-rfd_status pipelined_gram(BatchImpl* b, int mode, cudaStream_t s) {
+// The step's timing scope opens after the wait for the first phase's features, so that
+// it spans the Gram launches (and any later wait between them), not the features ahead.
+rfd_status pipelined_gram(BatchImpl* b, int mode, cudaStream_t s, Timing* t) {
   for (int p = 0; p < gram_phases(b); ++p) {
     BCK(cudaStreamWaitEvent(s, b->ev_phase[p], 0));
+    StepScope sc(t, s, RFD_STEP_GRAM);
     BCK(gram_phase(b, mode, p * b->phase_blocks, s));
   }
   return RFD_OK;
@@ -730,10 +733,7 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
         StepScope sc(t, s, RFD_STEP_FIELD);
         BCK(launch_fill_batched(b->d_fill, b->d_fill_prefix, n, b->fill_blocks, b->d_calls, s));
       }
-      {
-        StepScope sc(t, s, RFD_STEP_GRAM);
-        if (rfd_status q = pipelined_gram(b, mode, s); q != RFD_OK) return q;
-      }
+      if (rfd_status q = pipelined_gram(b, mode, s, t); q != RFD_OK) return q;
       StepScope sc(t, s, RFD_STEP_REDUCE);
       BCK(launch_reduce_batched(b->d_red[mode], b->n_red[mode], b->d_calls, s));
       return RFD_OK;
@@ -944,7 +944,7 @@ rfd_status batch_time_gram(BatchImpl* b, int mode, int reps, float* ms, const Cl
       }
       return gram_all(b, mode, b->st);
     }
-    if (pipelined_features(b, b->st, nullptr) != RFD_OK || pipelined_gram(b, mode, b->st) != RFD_OK)
+    if (pipelined_features(b, b->st, nullptr) != RFD_OK || pipelined_gram(b, mode, b->st, nullptr) != RFD_OK)
       return cudaErrorLaunchFailure;
     return cudaSuccess;
   };

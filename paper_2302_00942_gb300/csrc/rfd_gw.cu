@@ -102,56 +102,87 @@ __global__ void line_search_sums_kernel(const float* __restrict__ a1, const floa
 // for the output, and every other step is O(N m^2).
 
 constexpr int kTI = 32;    // rows of a projection tile
-constexpr int kTA = 64;    // rows of an assembly tile
+constexpr int kTA = 64;    // rows of an assembly tile (scalar form)
 constexpr int kTJ = 256;   // columns of a tile (one per thread)
-constexpr int kTLd = kTJ + 8;  // smem row stride (8 banks between rows)
-constexpr int kRowGroups = 16;  // row groups of the projection grid
+constexpr int kPLd = kTJ + 1;  // smem row stride of a projection tile: rows and columns both conflict-free
+
+// The row groups of the projection and assembly grids: about four CTAs per SM
+// in all (two resident per SM, two waves), at least one tile per group.
+int row_groups(int64_t n1, int64_t n2, int tile_rows) {
+  static const int sms = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      v = 148;
+    return v > 0 ? v : 148;
+  }();
+  const int64_t strips = (n2 + kTJ - 1) / kTJ, tiles = (n1 + tile_rows - 1) / tile_rows;
+  const int64_t want = (4ll * sms + strips - 1) / strips;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, tiles));
+}
 
 // Pt[g][j][f] = sum_{i in group g} X[i][j] psc[i][f],  Qp[s][i][f] = sum_{j in strip s} X[i][j] psd[j][f]
-// Tile kTI x kTJ in shared memory.  P: a column per thread over the tile's
-// rows (accumulating over the group).  Q: a row per 8 threads, columns
-// dealt 8 apart, summed by shuffles.
+// in one pass over X.  A CTA takes a strip of kTJ columns and a group of rows
+// in tiles of kTI rows staged in shared memory (row stride kTJ + 1: conflict-
+// free along rows and down columns); with 16-byte loads the next tile's loads
+// are issued into registers before the current tile is computed, so they are
+// in flight during its FMAs.
+//   P: thread t owns column t, MF sums over the group's rows (per row one
+//      shared load of X and MF / 4 broadcast 16-byte loads of psc).
+//   Q: warp w owns the tile's kTI rows (lane = row) over the columns
+//      32 w .. 32 w + 31 (per column one shared load of X, MF / 4 broadcast
+//      loads of psd); the 8 warps' partial sums meet in shared memory.
 template <int MF>
-__global__ void __launch_bounds__(256) gw_project_kernel(const float* __restrict__ X, int64_t n1, int64_t n2,
-                                                         const float* __restrict__ psc, const float* __restrict__ psd,
-                                                         float* __restrict__ Pt_part, float* __restrict__ Q_part,
-                                                         int rows_per_group) {
-  constexpr int PLd = MF + 4;         // padded rows of psd: 8 consecutive rows hit distinct banks
+__global__ void __launch_bounds__(256, 2) gw_project_kernel(const float* __restrict__ X, int64_t n1, int64_t n2,
+                                                            const float* __restrict__ psc,
+                                                            const float* __restrict__ psd,
+                                                            float* __restrict__ Pt_part, float* __restrict__ Q_part,
+                                                            int rows_per_group) {
+  static_assert(kTI == 32 && kTJ == 256, "lane = tile row, 8 warps x 32 columns");
+  constexpr int RLd = MF + 1;  // row stride of the Q reduction buffer
   extern __shared__ __align__(16) float sm[];
-  float* Ts = sm;                      // kTI x kTLd
-  float* pc = Ts + kTI * kTLd;         // kTI x MF
-  float* pd = pc + kTI * MF;           // kTJ x PLd
-  const int t = threadIdx.x;
+  float* Ts = sm;                   // kTI x kPLd
+  float* pc = Ts + kTI * kPLd;      // kTI x MF  (kTI * kPLd is a multiple of 4: 16-byte aligned)
+  float* pd = pc + kTI * MF;        // kTJ x MF
+  float* red = pd + kTJ * MF;       // 8 x kTI x RLd
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int64_t j0 = (int64_t)blockIdx.x * kTJ;
   const int64_t ig0 = (int64_t)blockIdx.y * rows_per_group;
   const int64_t ig1 = min(n1, ig0 + rows_per_group);
   for (int e = t; e < kTJ * MF; e += 256) {
     const int64_t j = j0 + e / MF;
-    pd[(e / MF) * PLd + e % MF] = j < n2 ? psd[j * MF + e % MF] : 0.f;
+    pd[e] = j < n2 ? psd[j * MF + e % MF] : 0.f;
   }
   float accP[MF];
 #pragma unroll
   for (int f = 0; f < MF; ++f) accP[f] = 0.f;
-  const int qr = t >> 3, qc = t & 7;  // Q: row qr of the tile, columns qc + 8k
   // whole 16-byte column groups: rows start 16-byte aligned and a group never straddles n2
   const bool vec = (n2 & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  const int c4 = (t & 63) * 4, r0 = t >> 6;  // vec: rows r0 + 4u, columns c4 .. c4 + 3
+  float4 v[kTI / 4];
+  auto fetch = [&](int64_t i0) {
+#pragma unroll
+    for (int u = 0; u < kTI / 4; ++u) {
+      const int64_t i = i0 + r0 + 4 * u, j = j0 + c4;
+      v[u] = (i < ig1 && j < n2) ? *reinterpret_cast<const float4*>(X + i * n2 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  if (vec && ig0 < ig1) fetch(ig0);
   for (int64_t i0 = ig0; i0 < ig1; i0 += kTI) {
-    __syncthreads();
-    if (vec) {  // 8 independent 16-byte loads per thread: rows t / 64 + 4u, columns 4 (t % 64)
-      const int c4 = (t & 63) * 4, r0 = t >> 6;
-      float4 v[kTI / 4];
+    __syncthreads();  // the previous tile and its reduction buffer are consumed
+    if (vec) {
 #pragma unroll
       for (int u = 0; u < kTI / 4; ++u) {
-        const int64_t i = i0 + r0 + 4 * u, j = j0 + c4;
-        v[u] = (i < ig1 && j < n2) ? *reinterpret_cast<const float4*>(X + i * n2 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float* d = Ts + (r0 + 4 * u) * kPLd + c4;
+        d[0] = v[u].x;
+        d[1] = v[u].y;
+        d[2] = v[u].z;
+        d[3] = v[u].w;
       }
-#pragma unroll
-      for (int u = 0; u < kTI / 4; ++u) *reinterpret_cast<float4*>(Ts + (r0 + 4 * u) * kTLd + c4) = v[u];
     } else {
 #pragma unroll 8
       for (int r = 0; r < kTI; ++r) {
         const int64_t i = i0 + r, j = j0 + t;
-        Ts[r * kTLd + t] = (i < ig1 && j < n2) ? X[i * n2 + j] : 0.f;
+        Ts[r * kPLd + t] = (i < ig1 && j < n2) ? X[i * n2 + j] : 0.f;
       }
     }
     for (int e = t; e < kTI * MF; e += 256) {
@@ -159,9 +190,10 @@ __global__ void __launch_bounds__(256) gw_project_kernel(const float* __restrict
       pc[e] = i < ig1 ? psc[i * MF + e % MF] : 0.f;
     }
     __syncthreads();
-#pragma unroll 8
+    if (vec && i0 + kTI < ig1) fetch(i0 + kTI);  // the next tile's loads fly during this tile's FMAs
+#pragma unroll 4
     for (int r = 0; r < kTI; ++r) {  // P: column t over the tile's rows
-      const float x = Ts[r * kTLd + t];
+      const float x = Ts[r * kPLd + t];
       const float4* pr = reinterpret_cast<const float4*>(pc + r * MF);
 #pragma unroll
       for (int f4 = 0; f4 < MF / 4; ++f4) {
@@ -175,11 +207,11 @@ __global__ void __launch_bounds__(256) gw_project_kernel(const float* __restrict
     float accQ[MF];
 #pragma unroll
     for (int f = 0; f < MF; ++f) accQ[f] = 0.f;
-#pragma unroll 8
-    for (int k = 0; k < kTJ / 8; ++k) {  // Q: row qr over columns qc + 8k
-      const int c = qc + 8 * k;
-      const float x = Ts[qr * kTLd + c];
-      const float4* pr = reinterpret_cast<const float4*>(pd + c * PLd);
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {  // Q: row `lane` over the warp's 32 columns
+      const int c = warp * 32 + k;
+      const float x = Ts[lane * kPLd + c];
+      const float4* pr = reinterpret_cast<const float4*>(pd + c * MF);
 #pragma unroll
       for (int f4 = 0; f4 < MF / 4; ++f4) {
         const float4 w = pr[f4];
@@ -189,18 +221,17 @@ __global__ void __launch_bounds__(256) gw_project_kernel(const float* __restrict
         accQ[4 * f4 + 3] = fmaf(x, w.w, accQ[4 * f4 + 3]);
       }
     }
+    float* rw = red + (warp * kTI + lane) * RLd;
 #pragma unroll
-    for (int f = 0; f < MF; ++f) {
-      accQ[f] += __shfl_xor_sync(0xffffffffu, accQ[f], 1);
-      accQ[f] += __shfl_xor_sync(0xffffffffu, accQ[f], 2);
-      accQ[f] += __shfl_xor_sync(0xffffffffu, accQ[f], 4);
-    }
-    const int64_t i = i0 + qr;
-    if (i < ig1) {
-      float* q = Q_part + ((int64_t)blockIdx.x * n1 + i) * MF;
+    for (int f = 0; f < MF; ++f) rw[f] = accQ[f];
+    __syncthreads();
+    for (int e = t; e < kTI * MF; e += 256) {  // the warps' sums, in warp order
+      const int r = e / MF, f = e % MF;
+      float q = 0.f;
 #pragma unroll
-      for (int f = 0; f < MF / 4; ++f)
-        if (qc == (f & 7)) reinterpret_cast<float4*>(q)[f] = make_float4(accQ[4 * f], accQ[4 * f + 1], accQ[4 * f + 2], accQ[4 * f + 3]);
+      for (int w = 0; w < 8; ++w) q += red[(w * kTI + r) * RLd + f];
+      const int64_t i = i0 + r;
+      if (i < ig1) Q_part[((int64_t)blockIdx.x * n1 + i) * MF + f] = q;
     }
   }
   const int64_t j = j0 + t;
@@ -345,19 +376,23 @@ __global__ void __launch_bounds__(256) gw_assemble_kernel(const float* __restric
 
 // The same assembly, 16-byte I/O (n2 % 4 == 0, aligned T, L, v2): a CTA keeps
 // the (P'_j, Ud_j) of its 256 columns in shared memory, k-major, and walks
-// row tiles of 16; a thread takes 4 rows x 4 adjacent columns: it issues the
-// tile's T loads first, computes the rank-2 MF update (2 shared 16-byte loads
-// per 16 FMAs) while they are in flight, then writes L as float4.
+// row tiles of 16; a thread takes 4 rows x 4 adjacent columns (2 shared
+// 16-byte loads per 16 FMAs).  The next tile's T and row factors (Uc_i, Q_i)
+// are loaded into registers while the current tile is computed; the row
+// factors pass through two shared buffers in turn, so one barrier per tile
+// suffices.
 template <int MF>
-__global__ void __launch_bounds__(256) gw_assemble4_kernel(const float* __restrict__ T, const float* __restrict__ v1,
-                                                           const float* __restrict__ v2, const float* __restrict__ Uc,
-                                                           const float* __restrict__ Q, const float* __restrict__ Pp,
-                                                           const float* __restrict__ Ud, int64_t n1, int64_t n2,
-                                                           float* __restrict__ L, int rows_per_group) {
+__global__ void __launch_bounds__(256, 2) gw_assemble4_kernel(const float* __restrict__ T, const float* __restrict__ v1,
+                                                              const float* __restrict__ v2, const float* __restrict__ Uc,
+                                                              const float* __restrict__ Q, const float* __restrict__ Pp,
+                                                              const float* __restrict__ Ud, int64_t n1, int64_t n2,
+                                                              float* __restrict__ L, int rows_per_group) {
   constexpr int K2 = 2 * MF, TR = 16;
+  constexpr int RF = K2 * TR / 256;  // row-factor values a thread loads per tile
+  static_assert(RF * 256 == K2 * TR, "whole row-factor tiles");
   extern __shared__ __align__(16) float sm[];
   float* colS = sm;               // [K2][kTJ]
-  float* rowS = colS + K2 * kTJ;  // [K2][TR]
+  float* rowS = colS + K2 * kTJ;  // two buffers of [K2][TR]
   const int t = threadIdx.x, cg = t & 63, rg = t >> 6;
   const int64_t j0 = (int64_t)blockIdx.x * kTJ;
   for (int e = t; e < K2 * kTJ; e += 256) {
@@ -369,20 +404,32 @@ __global__ void __launch_bounds__(256) gw_assemble4_kernel(const float* __restri
   const bool cols_ok = jc < n2;  // n2 % 4 == 0: all four or none
   const float4 w2 = cols_ok ? *reinterpret_cast<const float4*>(v2 + jc) : make_float4(0.f, 0.f, 0.f, 0.f);
   const int64_t ig0 = (int64_t)blockIdx.y * rows_per_group, ig1 = min(n1, ig0 + rows_per_group);
-  for (int64_t i0 = ig0; i0 < ig1; i0 += TR) {
-    float4 tv[4];
+  float4 tv[4];
+  float rf[RF];
+  auto fetch = [&](int64_t i0) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int64_t i = i0 + 4 * rg + r;
       tv[r] = (cols_ok && i < ig1) ? *reinterpret_cast<const float4*>(T + i * n2 + jc) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    __syncthreads();
-    for (int e = t; e < K2 * TR; e += 256) {
-      const int k = e / TR, r = e % TR;
-      const int64_t i = i0 + r;
-      rowS[e] = i < ig1 ? (k < MF ? Uc[i * MF + k] : Q[i * MF + k - MF]) : 0.f;
+#pragma unroll
+    for (int q = 0; q < RF; ++q) {
+      const int e = t + 256 * q, k = e / TR;
+      const int64_t i = i0 + e % TR;
+      rf[q] = i < ig1 ? (k < MF ? Uc[i * MF + k] : Q[i * MF + k - MF]) : 0.f;
     }
-    __syncthreads();
+  };
+  if (ig0 < ig1) fetch(ig0);
+  int buf = 0;
+  for (int64_t i0 = ig0; i0 < ig1; i0 += TR, buf ^= 1) {
+    float* rs = rowS + buf * K2 * TR;
+#pragma unroll
+    for (int q = 0; q < RF; ++q) rs[t + 256 * q] = rf[q];
+    float4 cur[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) cur[r] = tv[r];
+    __syncthreads();  // this tile's row factors (and, the first time, colS) are in place
+    if (i0 + TR < ig1) fetch(i0 + TR);
     float acc[4][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -391,7 +438,7 @@ __global__ void __launch_bounds__(256) gw_assemble4_kernel(const float* __restri
 #pragma unroll 8
     for (int k = 0; k < K2; ++k) {
       const float4 cv = *reinterpret_cast<const float4*>(colS + k * kTJ + 4 * cg);
-      const float4 ra = *reinterpret_cast<const float4*>(rowS + k * TR + 4 * rg);
+      const float4 ra = *reinterpret_cast<const float4*>(rs + k * TR + 4 * rg);
       const float rv[4] = {ra.x, ra.y, ra.z, ra.w};
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
@@ -408,10 +455,10 @@ __global__ void __launch_bounds__(256) gw_assemble4_kernel(const float* __restri
       if (i < ig1) {
         const float vi = v1[i];
         float4 o;
-        o.x = vi + w2.x - 2.f * (tv[r].x + acc[r][0]);
-        o.y = vi + w2.y - 2.f * (tv[r].y + acc[r][1]);
-        o.z = vi + w2.z - 2.f * (tv[r].z + acc[r][2]);
-        o.w = vi + w2.w - 2.f * (tv[r].w + acc[r][3]);
+        o.x = vi + w2.x - 2.f * (cur[r].x + acc[r][0]);
+        o.y = vi + w2.y - 2.f * (cur[r].y + acc[r][1]);
+        o.z = vi + w2.z - 2.f * (cur[r].z + acc[r][2]);
+        o.w = vi + w2.w - 2.f * (cur[r].w + acc[r][3]);
         *reinterpret_cast<float4*>(L + i * n2 + jc) = o;
       }
     }
@@ -624,7 +671,7 @@ struct Proj {  // projections of one n1 x n2 matrix X: Pt = (Psi_C^T X)^T, Q = X
 };
 
 size_t project_parts_floats(int64_t n1, int64_t n2, int mf) {
-  const int64_t groups = std::min<int64_t>(kRowGroups, (n1 + kTI - 1) / kTI);
+  const int64_t groups = row_groups(n1, n2, kTI);
   const int64_t strips = (n2 + kTJ - 1) / kTJ;
   return (size_t)(groups * n2 * mf + 64) + (size_t)(strips * n1 * mf + 64);
 }
@@ -633,12 +680,12 @@ template <int MF>
 rfd_status project_mf(const float* X, int64_t n1, int64_t n2, const LowRank& c, const LowRank& d, const Proj& pr,
                       float* parts, float* R, cudaStream_t st) {
   const int64_t tiles = (n1 + kTI - 1) / kTI;
-  const int groups = (int)std::min<int64_t>(kRowGroups, tiles);
+  const int groups = row_groups(n1, n2, kTI);
   const int rows_per_group = (int)(((tiles + groups - 1) / groups) * kTI);
   const int strips = (int)((n2 + kTJ - 1) / kTJ);
   float* Pt_part = parts;
   float* Q_part = parts + (((size_t)groups * n2 * MF + 63) & ~size_t(63));
-  const size_t smem = (size_t)(kTI * kTLd + kTI * MF + kTJ * (MF + 4)) * sizeof(float);
+  const size_t smem = (size_t)(kTI * kPLd + kTI * MF + kTJ * MF + 8 * kTI * (MF + 1)) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(gw_project_kernel<MF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_err("projection attribute", e);
   gw_project_kernel<MF><<<dim3(strips, groups), 256, smem, st>>>(X, n1, n2, c.psi, d.psi, Pt_part, Q_part,
@@ -720,10 +767,10 @@ rfd_status tensor_product_lowrank(rfd_plan_t pc, rfd_plan_t pd, const float* T, 
                                           reinterpret_cast<uintptr_t>(lp.v2)) & 15) == 0;
     if (vec4) {
       const int64_t tiles = (n1 + 15) / 16;
-      const int groups = (int)std::min<int64_t>(kRowGroups, tiles);
+      const int groups = row_groups(n1, n2, 16);
       const int rows_per_group = (int)(((tiles + groups - 1) / groups) * 16);
       const dim3 grid((unsigned)((n2 + kTJ - 1) / kTJ), (unsigned)groups);
-      const size_t smem = (size_t)2 * lp.mf * (kTJ + 16) * sizeof(float);
+      const size_t smem = (size_t)2 * lp.mf * (kTJ + 2 * 16) * sizeof(float);
       if (lp.mf == 16) {
         e = cudaFuncSetAttribute(gw_assemble4_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
