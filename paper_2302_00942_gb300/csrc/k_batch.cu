@@ -151,7 +151,16 @@ __global__ void reduce_batched_kernel(const RedTile* __restrict__ tiles, const C
   if (r >= t.ni || col >= t.nj) return;
   const float* p = t.part + (int64_t)r * t.ld + t.col_off + col;
   Fp32Sum acc;
-  for (int u = 0; u < t.count; ++u) acc.add(p[(int64_t)u * t.slot_elems]);
+  int u = 0;
+  for (; u + 4 <= t.count; u += 4) {  // four loads in flight, summed in lane order
+    const float a0 = p[(int64_t)u * t.slot_elems], a1 = p[(int64_t)(u + 1) * t.slot_elems];
+    const float a2 = p[(int64_t)(u + 2) * t.slot_elems], a3 = p[(int64_t)(u + 3) * t.slot_elems];
+    acc.add(a0);
+    acc.add(a1);
+    acc.add(a2);
+    acc.add(a3);
+  }
+  for (; u < t.count; ++u) acc.add(p[(int64_t)u * t.slot_elems]);
   const int f = t.i0 + r;
   if (t.kind == kTileGram) {
     const int g = t.j0 + col;
@@ -200,6 +209,7 @@ __global__ void __launch_bounds__(256) small_batched_kernel(const ApplyJob* __re
     }
 #pragma unroll
     for (int q = 0; q < kCC; ++q) {
+      if (q >= nc) break;  // the group's channels only (nc is uniform across the block)
       // warp sum of the (sum, compensation) pairs: each butterfly step adds a pair as two terms
       Fp32Sum v = acc[q];
       for (int o = 16; o > 0; o >>= 1) {
