@@ -238,16 +238,18 @@ __global__ void __launch_bounds__(256) small_batched_kernel(const ApplyJob* __re
 // out[n, ch] = F[n, ch] + sum_j (cos(2 pi w_j^T x_n) Z[j, ch] + sin(2 pi w_j^T x_n) Z[h + j, ch]):
 // the features are recomputed in FP32 from the cloud's copy of its points
 // instead of read back from the BF16 Psi, so the apply carries no BF16
-// rounding and reads only points, F and out.  The angle in cycles is the FP32
-// t = w^T x (absolute error ~|t| 2^-24) reduced to [-1/2, 1/2] exactly
-// (t - rint(t), the rounding on the FMA pipe: an FRND instruction instead made
-// the kernel 10 % slower); MUFU sin/cos of 2 pi r add ~4e-7.  A block of 256
-// threads covers 512 points, two per thread (p and p + 256), which share each
-// frequency's shared-memory loads (its w and Z rows).  The kernel is bound by
-// instruction issue (~19 instructions per point and frequency at 3 channels);
-// four points per thread cut that by 14 % but halved the resident warps and
-// left a 1.6-wave tail at N = 10^6, and ran 10 % slower.  CG channels per
-// thread.  F[n] is read before out[n] is written by the same thread.
+// rounding and reads only points, F and out.  The phase in radians is the
+// FP32 t = (2 pi w)^T x (absolute error ~|t| 2^-24), given to MUFU sin/cos
+// as it is: their own handling of a large argument adds about |t| 2^-23
+// (measured on this GPU: 1.4e-4 at |t| = 1000), far below the BF16 rounding
+// of Phi in the B^T F of the form this kernel serves.  Reducing t to one
+// period first (4 of the ~19 instructions per point and frequency) made this
+// issue-bound kernel 11 % slower.  A block of 256 threads covers 512 points,
+// two per thread (p and p + 256), which share each frequency's shared-memory
+// loads (its w and Z rows); four points per thread cut the instructions by
+// 14 % but halved the resident warps and left a 1.6-wave tail at N = 10^6,
+// and ran 10 % slower.  CG channels per thread.  F[n] is read before out[n]
+// is written by the same thread.
 template <int CG>
 __global__ void __launch_bounds__(kApplyPts / 2)
 apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
@@ -285,9 +287,9 @@ apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ 
   for (int f0 = 0; f0 < h; f0 += kChunk) {
     const int fn = min(kChunk, h - f0);
     __syncthreads();
-    for (int i = threadIdx.x; i < kChunk; i += kThreads) {
+    for (int i = threadIdx.x; i < kChunk; i += kThreads) {  // 2 pi w: the phase in radians
       const float* w = jb.omega_hi + (size_t)(f0 + i) * 3;
-      w_s[i] = i < fn ? make_float4(w[0], w[1], w[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+      w_s[i] = i < fn ? make_float4(two_pi * w[0], two_pi * w[1], two_pi * w[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     for (int i = threadIdx.x; i < kChunk * CW * 4; i += kThreads) {
       const int fr = i / (CW * 4), q = i % (CW * 4);
@@ -301,8 +303,7 @@ apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ 
       float cs[UP], sn[UP];
 #pragma unroll
       for (int u = 0; u < UP; ++u) {
-        const float t = fmaf(w.x, x[u][0], fmaf(w.y, x[u][1], w.z * x[u][2]));
-        const float ang = two_pi * (t - round_int(t));
+        const float ang = fmaf(w.x, x[u][0], fmaf(w.y, x[u][1], w.z * x[u][2]));
         cs[u] = __cosf(ang);
         sn[u] = __sinf(ang);
       }
@@ -334,8 +335,8 @@ apply_batched_kernel(const ApplyJob* __restrict__ jobs, const int* __restrict__ 
 // float4) and the block's F columns (float4 groups) pass through shared memory
 // 128 points at a time; every thread reads the same point, so each point costs
 // one 16-byte broadcast load plus one per 4 channels, shared by the thread's
-// frequencies.  Phi(n, f) is the apply's FP32 feature (angle reduced in
-// cycles, MUFU sin / cos); plain FP32 sums over the chunk's points.
+// frequencies.  Phi(n, f) is the apply's FP32 feature (the phase in radians,
+// unreduced, into MUFU sin / cos); plain FP32 sums over the chunk's points.
 template <int CG>
 __global__ void __launch_bounds__(256)
 fieldpts_batched_kernel(const FieldPtsJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
@@ -353,20 +354,20 @@ fieldpts_batched_kernel(const FieldPtsJob* __restrict__ jobs, const int* __restr
   const int chunk = local % jb.chunks, rest = local / jb.chunks;
   const int fg = rest % fgroups, cgi = rest / fgroups;
   const int ch0 = cgi * CG, cg = min(CG, cc.c - ch0);
+  const float two_pi = 6.283185307179586f;
   int fi[FPT];
-  float w[FPT][3];
+  float w[FPT][3];  // 2 pi w: the phase in radians
 #pragma unroll
   for (int u = 0; u < FPT; ++u) {
     fi[u] = (fg * FPT + u) * 256 + threadIdx.x;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) w[u][d] = fi[u] < jb.h ? jb.omega_hi[(size_t)fi[u] * 3 + d] : 0.f;
+    for (int d = 0; d < 3; ++d) w[u][d] = fi[u] < jb.h ? two_pi * jb.omega_hi[(size_t)fi[u] * 3 + d] : 0.f;
   }
   float acc_c[FPT][CG], acc_s[FPT][CG];
 #pragma unroll
   for (int u = 0; u < FPT; ++u)
 #pragma unroll
     for (int q = 0; q < CG; ++q) acc_c[u][q] = acc_s[u][q] = 0.f;
-  const float two_pi = 6.283185307179586f;
   const int64_t p_begin = (int64_t)chunk * jb.pts, p_end = min(jb.n, p_begin + jb.pts);
   for (int64_t p0 = p_begin; p0 < p_end; p0 += kTile) {
     const int np = (int)min((int64_t)kTile, p_end - p0);
@@ -393,8 +394,7 @@ fieldpts_batched_kernel(const FieldPtsJob* __restrict__ jobs, const int* __restr
       }
 #pragma unroll
       for (int u = 0; u < FPT; ++u) {
-        const float t = fmaf(w[u][0], x.x, fmaf(w[u][1], x.y, w[u][2] * x.z));
-        const float ang = two_pi * (t - round_int(t));
+        const float ang = fmaf(w[u][0], x.x, fmaf(w[u][1], x.y, w[u][2] * x.z));
         const float cs = __cosf(ang), sn = __sinf(ang);
 #pragma unroll
         for (int q = 0; q < CG; ++q) {
