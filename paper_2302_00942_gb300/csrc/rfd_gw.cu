@@ -243,6 +243,127 @@ __global__ void __launch_bounds__(256, 2) gw_project_kernel(const float* __restr
   }
 }
 
+// The same projections for MF = 16 with register tiles, so that a 16-byte
+// shared load feeds 16 FMAs where the kernel above spends 9 wavefronts per
+// warp on 16: the tile is stored with a row stride of kTJ + 4 floats (16-byte
+// aligned rows, conflict-free 16-byte stores and loads along rows), and
+//   P: thread (fq = t % 4, jq = t / 4) owns 4 features x 4 adjacent columns
+//      (per row: one 16-byte load of X, one of psc, 16 FMAs);
+//   Q: warp rq owns rows 4 rq .. 4 rq + 3; lane (ks = lane % 8, fq = lane / 8)
+//      owns 4 features and the column quads ks, ks + 8, ... (per quad: four
+//      16-byte loads of X rows, four of psd held transposed, 64 FMAs); the 8
+//      column slices meet by shuffles, in a fixed order.
+// The next tile's loads are issued into registers before the current tile is
+// computed.  X with 16-byte rows only (n2 % 4 == 0, 16-byte aligned).
+__global__ void __launch_bounds__(256, 2) gw_project16_kernel(const float* __restrict__ X, int64_t n1, int64_t n2,
+                                                             const float* __restrict__ psc,
+                                                             const float* __restrict__ psd,
+                                                             float* __restrict__ Pt_part, float* __restrict__ Q_part,
+                                                             int rows_per_group) {
+  constexpr int MF = 16, TLd = kTJ + 4;
+  static_assert(kTI == 32 && kTJ == 256, "8 warps x 4 rows, 64 column quads");
+  extern __shared__ __align__(16) float sm[];
+  float* Ts = sm;                // kTI x TLd
+  float* pc = Ts + kTI * TLd;    // kTI x MF
+  float* pdT = pc + kTI * MF;    // MF x kTJ: psd transposed, so that a column quad of one feature is 16 bytes
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t j0 = (int64_t)blockIdx.x * kTJ;
+  const int64_t ig0 = (int64_t)blockIdx.y * rows_per_group;
+  const int64_t ig1 = min(n1, ig0 + rows_per_group);
+  for (int e = t; e < kTJ * MF; e += 256) {
+    const int64_t j = j0 + e / MF;
+    pdT[(e % MF) * kTJ + e / MF] = j < n2 ? psd[j * MF + e % MF] : 0.f;
+  }
+  const int pfq = t & 3, pjq = t >> 2;             // P: features 4 pfq.., columns 4 pjq..
+  const int ks = lane & 7, qfq = lane >> 3;        // Q: column quads ks + 8 k, features 4 qfq..
+  float accP[4][4];                                // [feature][column]
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) accP[a][b] = 0.f;
+  const int c4 = (t & 63) * 4, r0 = t >> 6;        // loads: rows r0 + 4u, columns c4 .. c4 + 3
+  float4 v[kTI / 4];
+  auto fetch = [&](int64_t i0) {
+#pragma unroll
+    for (int u = 0; u < kTI / 4; ++u) {
+      const int64_t i = i0 + r0 + 4 * u, j = j0 + c4;
+      v[u] = (i < ig1 && j < n2) ? *reinterpret_cast<const float4*>(X + i * n2 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  if (ig0 < ig1) fetch(ig0);
+  for (int64_t i0 = ig0; i0 < ig1; i0 += kTI) {
+    __syncthreads();  // the previous tile is consumed
+#pragma unroll
+    for (int u = 0; u < kTI / 4; ++u) *reinterpret_cast<float4*>(Ts + (r0 + 4 * u) * TLd + c4) = v[u];
+    for (int e = t; e < kTI * MF; e += 256) {
+      const int64_t i = i0 + e / MF;
+      pc[e] = i < ig1 ? psc[i * MF + e % MF] : 0.f;
+    }
+    __syncthreads();
+    if (i0 + kTI < ig1) fetch(i0 + kTI);  // the next tile's loads fly during this tile's FMAs
+#pragma unroll 4
+    for (int r = 0; r < kTI; ++r) {  // P
+      const float4 x = *reinterpret_cast<const float4*>(Ts + r * TLd + 4 * pjq);
+      const float4 w = *reinterpret_cast<const float4*>(pc + r * MF + 4 * pfq);
+      const float xs[4] = {x.x, x.y, x.z, x.w}, ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) accP[a][b] = fmaf(ws[a], xs[b], accP[a][b]);
+    }
+    float accQ[4][4];  // [row][feature]
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) accQ[a][b] = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < kTJ / 32; ++k) {  // Q: column quad cq of this lane's slice
+      const int cq = ks + 8 * k;
+      float xr[4][4], wc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const float4 x = *reinterpret_cast<const float4*>(Ts + (4 * warp + a) * TLd + 4 * cq);
+        xr[a][0] = x.x; xr[a][1] = x.y; xr[a][2] = x.z; xr[a][3] = x.w;
+        const float4 w = *reinterpret_cast<const float4*>(pdT + (4 * qfq + a) * kTJ + 4 * cq);  // feature 4 qfq + a
+        wc[0][a] = w.x; wc[1][a] = w.y; wc[2][a] = w.z; wc[3][a] = w.w;
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)        // row
+#pragma unroll
+        for (int c = 0; c < 4; ++c)      // column of the quad
+#pragma unroll
+          for (int b = 0; b < 4; ++b)    // feature
+            accQ[a][b] = fmaf(xr[a][c], wc[c][b], accQ[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {  // the 8 column slices, in a fixed butterfly order
+        float q = accQ[a][b];
+        q += __shfl_xor_sync(0xffffffffu, q, 1);
+        q += __shfl_xor_sync(0xffffffffu, q, 2);
+        q += __shfl_xor_sync(0xffffffffu, q, 4);
+        accQ[a][b] = q;
+      }
+    if (ks == 0) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int64_t i = i0 + 4 * warp + a;
+        if (i < ig1)
+          *reinterpret_cast<float4*>(Q_part + ((int64_t)blockIdx.x * n1 + i) * MF + 4 * qfq) =
+              make_float4(accQ[a][0], accQ[a][1], accQ[a][2], accQ[a][3]);
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int64_t j = j0 + 4 * pjq + b;
+    if (j < n2)
+      *reinterpret_cast<float4*>(Pt_part + ((int64_t)blockIdx.y * n2 + j) * MF + 4 * pfq) =
+          make_float4(accP[0][b], accP[1][b], accP[2][b], accP[3][b]);
+  }
+}
+
 // out[e] = sum_s part[s * stride + e], e < count (fixed order)
 __global__ void sum_parts_kernel(const float* __restrict__ part, int parts, int64_t stride, int64_t count,
                                  float* __restrict__ out) {
@@ -685,11 +806,21 @@ rfd_status project_mf(const float* X, int64_t n1, int64_t n2, const LowRank& c, 
   const int strips = (int)((n2 + kTJ - 1) / kTJ);
   float* Pt_part = parts;
   float* Q_part = parts + (((size_t)groups * n2 * MF + 63) & ~size_t(63));
-  const size_t smem = (size_t)(kTI * kPLd + kTI * MF + kTJ * MF + 8 * kTI * (MF + 1)) * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(gw_project_kernel<MF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_err("projection attribute", e);
-  gw_project_kernel<MF><<<dim3(strips, groups), 256, smem, st>>>(X, n1, n2, c.psi, d.psi, Pt_part, Q_part,
-                                                                  rows_per_group);
+  const bool vec16 = MF == 16 && (n2 & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  cudaError_t e = cudaSuccess;
+  if (vec16) {  // register tiles (16-byte rows of X)
+    const size_t smem = (size_t)(kTI * (kTJ + 4) + kTI * MF + kTJ * MF) * sizeof(float);
+    e = cudaFuncSetAttribute(gw_project16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_err("projection attribute", e);
+    gw_project16_kernel<<<dim3(strips, groups), 256, smem, st>>>(X, n1, n2, c.psi, d.psi, Pt_part, Q_part,
+                                                                 rows_per_group);
+  } else {
+    const size_t smem = (size_t)(kTI * kPLd + kTI * MF + kTJ * MF + 8 * kTI * (MF + 1)) * sizeof(float);
+    e = cudaFuncSetAttribute(gw_project_kernel<MF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_err("projection attribute", e);
+    gw_project_kernel<MF><<<dim3(strips, groups), 256, smem, st>>>(X, n1, n2, c.psi, d.psi, Pt_part, Q_part,
+                                                                    rows_per_group);
+  }
   sum_parts_kernel<<<blocks_for(n2 * MF, 256), 256, 0, st>>>(Pt_part, groups, n2 * MF, n2 * MF, pr.Pt);
   sum_parts_kernel<<<blocks_for(n1 * MF, 256), 256, 0, st>>>(Q_part, strips, n1 * MF, n1 * MF, pr.Q);
   wgram(pr.Pt, d.psi, nullptr, n2, MF, R + MF * MF, R, st);                                  // R = P Psi_D
