@@ -915,7 +915,8 @@ def main():
                        "passes": bary_passes, "ms_per_pass": bary_ms},
         "autotune": {"lanes_pct": st["tune_lanes_pct"], "phase_blocks": st["tune_phase_blocks"], "tuned": st["tuned"],
                      "gram_form": "CTA pairs (2-SM MMA)" if st.get("tune_pair_gram") else "one SM per tile",
-                     "features_beside_gram": bool(st.get("tune_overlap"))},
+                     "features_beside_gram": bool(st.get("tune_overlap")),
+                     "form_ms": {"one_sm": round(st["tune_form_ms"][0], 4), "cta_pairs": round(st["tune_form_ms"][1], 4)}},
         "warm": {"value": whole_job_value(ws, n * c, warm_ms), "unit": "points*ch/s", "ms_per_step": warm_ms,
                  "what": "rfd_integrate: a new field on the resident features and G (steps a3(Y) to a6)",
                  "step_ms": {k: round(v, 4) for k, v in wst["step_ms"].items() if v}},

@@ -157,6 +157,8 @@ typedef struct {
                              /*    cloud with m >= 512, chosen by the autotuner)           */
   int32_t tune_overlap;      /* 1: a lone cloud's features run phase by phase beside the    */
                              /*    Gram (a test hook selects it; the autotuner does not)    */
+  double tune_form_ms[2];    /* the autotuner's best time (ms) of features + reductions with */
+                             /*    one SM per tile [0] and CTA pairs [1] (0: not timed)     */
 } rfd_stats;
 
 /* ---------------------------------------------------------------------------

@@ -59,7 +59,7 @@ class rfd_stats(ctypes.Structure):
                 ("phi1_gemms", ctypes.c_int32), ("step_ms", ctypes.c_double * len(STEP_NAMES)), ("timed_calls", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("tune_lanes_pct", ctypes.c_int32), ("tune_waves", ctypes.c_int32),
                 ("tune_phase_blocks", ctypes.c_int32), ("tuned", ctypes.c_int32), ("tune_pair_gram", ctypes.c_int32),
-                ("tune_overlap", ctypes.c_int32)]
+                ("tune_overlap", ctypes.c_int32), ("tune_form_ms", ctypes.c_double * 2)]
 
 
 class rfd_batch_item(ctypes.Structure):
@@ -93,8 +93,9 @@ class rfd_server_stats(ctypes.Structure):
 
 
 def _stats_dict(s: "rfd_stats") -> dict:
-    d = {k: getattr(s, k) for k, _ in rfd_stats._fields_ if k != "step_ms"}
+    d = {k: getattr(s, k) for k, _ in rfd_stats._fields_ if k not in ("step_ms", "tune_form_ms")}
     d["step_ms"] = dict(zip(STEP_NAMES, list(s.step_ms)))
+    d["tune_form_ms"] = list(s.tune_form_ms)
     return d
 
 

@@ -96,7 +96,7 @@ __device__ __forceinline__ void store_cols(float* out, const float* v, bool accu
 
 __global__ void __launch_bounds__(kThreads, 1)
 gram_pair_kernel(const CUtensorMap* __restrict__ maps, const PairUnit* __restrict__ units, int stages,
-                 int stage_bytes, int kb0, int kb_len, int* err) {
+                 int stage_bytes, int kb0, int kb_len, int* err, unsigned long long* prof) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
   const uint32_t base = (raw_addr + 1023u) & ~1023u;  // the same offset in both CTAs of the pair
@@ -142,6 +142,7 @@ gram_pair_kernel(const CUtensorMap* __restrict__ maps, const PairUnit* __restric
   cluster_sync();  // both CTAs' barriers exist and the pair's TMEM is allocated before any remote arrival
   fence_after();
   const uint32_t tmem = sm->tmem_base;
+  const unsigned long long t_start = (prof && threadIdx.x == 0) ? globaltimer() : 0ull;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -252,6 +253,10 @@ gram_pair_kernel(const CUtensorMap* __restrict__ maps, const PairUnit* __restric
   __syncthreads();
   cluster_sync();  // both CTAs are done with TMEM and with each other's barriers
   fence_after();
+  if (prof && threadIdx.x == 0) {
+    prof[2 * blockIdx.x] = t_start;
+    prof[2 * blockIdx.x + 1] = globaltimer();
+  }
   if (warp == 1) tmem_dealloc_pair(tmem, kTmemCols);
 }
 
@@ -297,7 +302,8 @@ int gram_pair_stage_bytes(int max_nc, int max_cpad) {
 }
 
 cudaError_t launch_gram_pair_phase(const void* maps_dev, const PairUnit* units, int num_units, int stage_bytes,
-                                   int kb0, int phase_blocks, int* err, cudaStream_t st) {
+                                   int kb0, int phase_blocks, int* err, cudaStream_t st,
+                                   unsigned long long* prof) {
   if (num_units <= 0) return cudaSuccess;
   if (phase_blocks < 1 || stage_bytes % 1024) return cudaErrorInvalidValue;
   int stages = (kSmemLimit - kSmemExtra) / stage_bytes;
@@ -318,7 +324,7 @@ cudaError_t launch_gram_pair_phase(const void* maps_dev, const PairUnit* units, 
   cfg.attrs = la;
   cfg.numAttrs = 1;
   const cudaError_t e = cudaLaunchKernelEx(&cfg, gram_pair_kernel, static_cast<const CUtensorMap*>(maps_dev), units,
-                                           stages, stage_bytes, kb0, phase_blocks, err);
+                                           stages, stage_bytes, kb0, phase_blocks, err, prof);
   if (e != cudaSuccess) return e;
   return launched();
 }

@@ -91,7 +91,7 @@ __device__ __forceinline__ void store_cols(float* out, const float* v, bool accu
 
 __global__ void __launch_bounds__(kThreads, 1)
 gram_tc_kernel(const CUtensorMap* __restrict__ maps, const TcUnit* __restrict__ units, int stages, int stage_bytes,
-               int b_off, int kb0, int kb_len, int* err) {
+               int b_off, int kb0, int kb_len, int* err, unsigned long long* prof) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
   const uint32_t base = (raw_addr + 1023u) & ~1023u;
@@ -123,6 +123,7 @@ gram_tc_kernel(const CUtensorMap* __restrict__ maps, const TcUnit* __restrict__ 
   __syncthreads();
   fence_after();
   const uint32_t tmem = sm->tmem_base;
+  const unsigned long long t_start = (prof && threadIdx.x == 0) ? globaltimer() : 0ull;
   // B rows: 64-row boxes while they fit (m >= 64), then 16-row boxes (min(16, m) rows each)
   const int b64 = (u.b_rows >= 64) ? u.nj_mma / 64 : 0;
   const int b16_rows = u.b_rows < 16 ? u.b_rows : 16;
@@ -223,6 +224,10 @@ gram_tc_kernel(const CUtensorMap* __restrict__ maps, const TcUnit* __restrict__ 
   fence_before();
   __syncthreads();
   fence_after();
+  if (prof && threadIdx.x == 0) {
+    prof[2 * blockIdx.x] = t_start;
+    prof[2 * blockIdx.x + 1] = globaltimer();
+  }
   if (warp == 1) tmem_dealloc(tmem, kTmemCols);
 }
 
@@ -254,7 +259,7 @@ cudaError_t gram_tc_prepare() {
 }
 
 cudaError_t launch_gram_tc_phase(const void* maps_dev, const TcUnit* units, int num_units, int a_boxes, int kb0,
-                                 int phase_blocks, int* err, cudaStream_t st) {
+                                 int phase_blocks, int* err, cudaStream_t st, unsigned long long* prof) {
   if (num_units <= 0) return cudaSuccess;
   if (a_boxes < 1 || a_boxes > 2 || phase_blocks < 1) return cudaErrorInvalidValue;
   const int b_off = a_boxes * kABytes;
@@ -266,7 +271,7 @@ cudaError_t launch_gram_tc_phase(const void* maps_dev, const TcUnit* units, int 
   const cudaError_t attr = gram_tc_prepare();
   if (attr != cudaSuccess) return attr;
   gram_tc_kernel<<<num_units, kThreads, smem, st>>>(static_cast<const CUtensorMap*>(maps_dev), units, stages,
-                                                    stage_bytes, b_off, kb0, phase_blocks, err);
+                                                    stage_bytes, b_off, kb0, phase_blocks, err, prof);
   return launched();
 }
 

@@ -127,8 +127,11 @@ struct PairUnit {
 // Stage size of the pair kernel for the largest column tile and field width of a launch.
 int gram_pair_stage_bytes(int max_nc, int max_cpad);
 // One phase of the pair reductions: grid 2 x num_units in clusters of two.
+// prof (optional, 2 x 2 num_units words): each CTA's %globaltimer at the start of its pipeline
+// and at its end, for the autotuner's measure of every tile's pace.
 cudaError_t launch_gram_pair_phase(const void* maps_dev, const PairUnit* units, int num_units, int stage_bytes,
-                                   int kb0, int phase_blocks, int* err, cudaStream_t st);
+                                   int kb0, int phase_blocks, int* err, cudaStream_t st,
+                                   unsigned long long* prof = nullptr);
 cudaError_t gram_pair_prepare();
 // CTA pairs of the pair kernel that fit on the GPU at once (0 if unknown).
 int gram_pair_max_clusters();
@@ -146,8 +149,10 @@ constexpr int kGramPhaseBlocks = 4096;  // default phase length
 cudaError_t launch_gram_tc(const void* maps_dev, const TcUnit* units, int num_units, int a_boxes, int max_kb,
                            int phase_blocks, int* err, cudaStream_t st);
 // One phase alone: the 64-point blocks [kb0, kb0 + phase_blocks) (kb0 > 0 adds to the partials).
+// prof: as launch_gram_pair_phase's (2 x num_units words)
 cudaError_t launch_gram_tc_phase(const void* maps_dev, const TcUnit* units, int num_units, int a_boxes, int kb0,
-                                 int phase_blocks, int* err, cudaStream_t st);
+                                 int phase_blocks, int* err, cudaStream_t st,
+                                 unsigned long long* prof = nullptr);
 bool tc_gram_supported();
 // One CTA that allocates TMEM, waits on an mbarrier nothing arrives on for
 // limit_ns, records its code in *err, frees the TMEM and returns: the bounded

@@ -275,12 +275,15 @@ int gram_tile_cost(const GramCT& c, int cpad) {
 // the most work per lane), so that every CTA has about the same work and the
 // tiles' lanes sweep the point axis at the same pace (their slabs of Psi are
 // then shared in L2).
-std::vector<int> gram_tile_lanes(const std::vector<GramCT>& ct, int cpad, int64_t kb_total, int sms, int lanes_pct) {
+// meas: the tiles' measured per-block costs (any unit), in place of the model.
+std::vector<int> gram_tile_lanes(const std::vector<GramCT>& ct, int cpad, int64_t kb_total, int sms, int lanes_pct,
+                                 const std::vector<double>* meas = nullptr) {
   const int T = (int)ct.size();
   std::vector<int> L(T, 1);
   if (T == 0) return L;
   std::vector<double> w(T);
-  for (int t = 0; t < T; ++t) w[t] = (double)gram_tile_cost(ct[t], cpad);
+  for (int t = 0; t < T; ++t)
+    w[t] = (meas && (int)meas->size() == T) ? (*meas)[t] : (double)gram_tile_cost(ct[t], cpad);
   int budget = std::max(T, sms * lanes_pct / 100) - T;
   while (budget-- > 0) {
     int best = -1;
@@ -332,11 +335,13 @@ int pair_tile_cost(const PairCT& t, int cpad) {
   return std::max(2 * mma_cols, (26 * rows) / 10);
 }
 // lanes per pair tile: lanes_pct % of the SM pairs, by cost (greedy, as gram_tile_lanes)
-std::vector<int> pair_tile_lanes(const std::vector<PairCT>& ct, int cpad, int64_t kb_total, int sms, int lanes_pct) {
+std::vector<int> pair_tile_lanes(const std::vector<PairCT>& ct, int cpad, int64_t kb_total, int sms, int lanes_pct,
+                                 const std::vector<double>* meas = nullptr) {
   const int T = (int)ct.size();
   std::vector<int> L(T, 1);
   std::vector<double> w(T);
-  for (int t = 0; t < T; ++t) w[t] = (double)pair_tile_cost(ct[t], cpad);
+  for (int t = 0; t < T; ++t)
+    w[t] = (meas && (int)meas->size() == T) ? (*meas)[t] : (double)pair_tile_cost(ct[t], cpad);
   // a wave is the co-resident pairs (clusters need both SMs in one GPU processing cluster,
   // so fewer than sms / 2 may fit at once)
   const int fit = gram_pair_max_clusters();
@@ -375,7 +380,12 @@ rfd_status build_pair_desc(rfd_plan_s* pl) {
     d.pair_red[mode].clear();
     if (!pair_eligible(pl)) continue;
     const std::vector<PairCT> ct = pair_tiles(m, mode);
-    const std::vector<int> Ls = pair_tile_lanes(ct, cpad, kb_total, pl->sms, pl->tune.lanes_pct);
+    std::vector<int> Ls = pair_tile_lanes(ct, cpad, kb_total, pl->sms, pl->tune.lanes_pct, &pl->tile_cost[1][mode]);
+    {  // measured lanes whose partial slots would not fit the allocation: the model's
+      int64_t need = 0;
+      for (size_t t = 0; t < ct.size(); ++t) need += (int64_t)(ct[t].a1 ? 4 : 2) * Ls[t];
+      if (need > pl->part_slots) Ls = pair_tile_lanes(ct, cpad, kb_total, pl->sms, pl->tune.lanes_pct);
+    }
     int64_t base = 0;
     for (size_t t = 0; t < ct.size(); ++t) {
       const PairCT& c = ct[t];
@@ -479,7 +489,12 @@ rfd_status build_desc(rfd_plan_s* pl) {
   for (int mode = 0; mode < 3; ++mode) {
     const std::vector<GramCT> ct = gram_tiles(m, pl->cpad, mode);
     const int T = (int)ct.size();
-    const std::vector<int> Ls = gram_tile_lanes(ct, pl->cpad, kb_total, pl->sms, pl->tune.lanes_pct);
+    std::vector<int> Ls = gram_tile_lanes(ct, pl->cpad, kb_total, pl->sms, pl->tune.lanes_pct, &pl->tile_cost[0][mode]);
+    {  // measured lanes whose partial slots would not fit the allocation: the model's
+      int64_t need = 0;
+      for (int t = 0; t < T; ++t) need += (int64_t)(ct[t].ni1 > 0 ? 2 : 1) * Ls[t];
+      if (need > pl->part_slots) Ls = gram_tile_lanes(ct, pl->cpad, kb_total, pl->sms, pl->tune.lanes_pct);
+    }
     int slot = 0;
     int64_t base = 0;  // first partial slot of the current logical half
     for (int t = 0; t < T; ++t) {
@@ -673,7 +688,12 @@ struct CallScope {
 // point blocks, field width) for plans, (clouds, log2 of the work) for batches
 // -- and reused without timing by later plans / batches of the same bucket.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, GramTuning> g_plan_tune;
+struct PlanTuneEntry {
+  GramTuning t;
+  std::vector<double> cost[2][3];  // the measured tile costs (rfd_plan_s::tile_cost)
+  double form_ms[2] = {0.0, 0.0};
+};
+std::map<std::tuple<int, int, int>, PlanTuneEntry> g_plan_tune;
 std::map<std::pair<int, int>, GramTuning> g_batch_tune;
 constexpr int kTunePhases[5] = {1024, 2048, 4096, 8192, 16384};
 
@@ -697,6 +717,75 @@ rfd_status rebuild_self(rfd_plan_s* pl) {
   return RFD_OK;
 }
 
+// Measures every compute tile's cost per 64-point block (ns for one lane) in one launch over
+// the whole point axis with the plan's current lanes of form `form` (0: one SM per tile, 1: CTA
+// pairs), into pl->tile_cost[form][mode].  The units of a tile are consecutive, lane 0 first.
+rfd_status measure_tile_costs(rfd_plan_s* pl, int form, int mode, const CloudCall* cc) {
+  pl->tune.pairs = form;
+  rfd_status s = build_desc(pl);
+  BatchImpl* tb = nullptr;
+  rfd_plan_s* self = pl;
+  if (s == RFD_OK) s = batch_build(&self, 1, pl->stream, cuda_mem(), 0, pl->tune, &tb);
+  if (s != RFD_OK) return s;
+  const int64_t kb_total = pl->n_pad / kTcBK;
+  const int n_units = form ? (int)pl->desc.pair_units[mode].size() : (int)pl->desc.units[mode].size();
+  const int ctas = form ? 2 * n_units : n_units;
+  std::vector<unsigned long long> h(2 * (size_t)ctas, 0ull);
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (ctas > 0) {
+    e = cudaMalloc(reinterpret_cast<void**>(&d), h.size() * sizeof(unsigned long long));
+    if (e == cudaSuccess) {
+      batch_set_phase(tb, (int)std::min<int64_t>(kb_total, 1 << 30));
+      batch_set_profile(tb, d);
+      float ms = 0.f;
+      s = batch_time_gram(tb, mode, 1, &ms, cc);
+      batch_set_profile(tb, nullptr);
+      if (s == RFD_OK) e = cudaMemcpy(h.data(), d, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+      cudaFree(d);
+    }
+  }
+  cudaStreamSynchronize(pl->stream);
+  batch_free(tb);
+  if (s != RFD_OK) return s;
+  if (e != cudaSuccess) return cuda_fail("tile timing", e);
+  std::vector<double> cost;
+  double sum = 0.0;
+  int nl = 0;
+  for (int i = 0; i < n_units; ++i) {
+    int lane, nlanes;
+    unsigned long long t0, t1;
+    if (form) {
+      const PairUnit& u = pl->desc.pair_units[mode][i];
+      lane = u.lane;
+      nlanes = u.nlanes;
+      t0 = std::min(h[4 * i], h[4 * i + 2]);
+      t1 = std::max(h[4 * i + 1], h[4 * i + 3]);
+    } else {
+      const TcUnit& u = pl->desc.units[mode][i];
+      lane = u.lane;
+      nlanes = u.nlanes;
+      t0 = h[2 * i];
+      t1 = h[2 * i + 1];
+    }
+    if (lane == 0 && i > 0) {  // the previous tile is complete
+      cost.push_back(nl > 0 ? sum / nl : -1.0);
+      sum = 0.0;
+      nl = 0;
+    }
+    const int64_t blocks = nlanes > 0 ? (kb_total - lane + nlanes - 1) / nlanes : 0;
+    if (blocks > 0 && t1 > t0) {
+      sum += (double)(t1 - t0) / (double)blocks;
+      ++nl;
+    }
+  }
+  if (n_units > 0) cost.push_back(nl > 0 ? sum / nl : -1.0);
+  bool all = true;
+  for (double c : cost) all = all && c > 0.0;
+  pl->tile_cost[form][mode] = all ? cost : std::vector<double>();  // a tile without a measure: the model
+  return RFD_OK;
+}
+
 rfd_status tune_plan(rfd_plan_s* pl, int mode, const CloudCall* cc) {
   const auto key = std::make_tuple(pl->m, ilog2((double)(pl->n_pad / kTcBK)), pl->cpad);
   pl->tuned = true;
@@ -704,14 +793,27 @@ rfd_status tune_plan(rfd_plan_s* pl, int mode, const CloudCall* cc) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_plan_tune.find(key);
     if (it != g_plan_tune.end()) {
-      pl->tune = it->second;
+      pl->tune = it->second.t;
+      for (int f = 0; f < 2; ++f) {
+        for (int md = 0; md < 3; ++md) pl->tile_cost[f][md] = it->second.cost[f][md];
+        pl->tune_form_ms[f] = it->second.form_ms[f];
+      }
       return rebuild_self(pl);
     }
   }
   RFD_CUDA(cudaStreamSynchronize(pl->stream));  // the features of the first pass are in place
   float best = 1e30f;
   GramTuning best_t = pl->tune;
-  for (int form = 0; form < (pair_eligible(pl) ? 2 : 1); ++form)
+  for (int form = 0; form < (pair_eligible(pl) ? 2 : 1); ++form) {
+    // the tiles' lanes from their measured pace: two rounds (measure with the model's lanes,
+    // then with the measured ones), so that every tile sweeps the point axis at one pace and
+    // the slabs of Psi the tiles share are read from HBM once
+    pl->tune.pairs = form;
+    pl->tune.lanes_pct = 100;
+    pl->tile_cost[form][mode].clear();
+    pl->tune_form_ms[form] = 0.0;
+    for (int round = 0; round < 2; ++round)
+      if (rfd_status s = measure_tile_costs(pl, form, mode, cc); s != RFD_OK) return s;
     for (int lp : {50, 100, kTuneLanesMax}) {
       pl->tune.lanes_pct = lp;
       pl->tune.pairs = form;
@@ -730,6 +832,7 @@ rfd_status tune_plan(rfd_plan_s* pl, int mode, const CloudCall* cc) {
         float ms = 0.f;
         s = batch_time_gram(tb, mode, 3, &ms, cc);
         if (s != RFD_OK) break;
+        if (pl->tune_form_ms[form] == 0.0 || ms < pl->tune_form_ms[form]) pl->tune_form_ms[form] = ms;
         if (ms < best) {
           best = ms;
           best_t = pl->tune;
@@ -741,10 +844,16 @@ rfd_status tune_plan(rfd_plan_s* pl, int mode, const CloudCall* cc) {
       batch_free(tb);
       if (s != RFD_OK) return s;
     }
+  }
   pl->tune = best_t;
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
-    g_plan_tune[key] = best_t;
+    PlanTuneEntry& en = g_plan_tune[key];
+    en.t = best_t;
+    for (int f = 0; f < 2; ++f) {
+      for (int md = 0; md < 3; ++md) en.cost[f][md] = pl->tile_cost[f][md];
+      en.form_ms[f] = pl->tune_form_ms[f];
+    }
   }
   return rebuild_self(pl);
 }
@@ -1252,6 +1361,7 @@ rfd_status rfd_plan_stats(rfd_plan_t pl, rfd_stats* out) {
   out->tune_phase_blocks = pl->tune.phase_blocks;
   out->tune_pair_gram = pl->tune.pairs;
   out->tune_overlap = pl->tune.overlap;
+  for (int f = 0; f < 2; ++f) out->tune_form_ms[f] = pl->tune_form_ms[f];
   out->tuned = pl->tuned ? 1 : 0;
   return RFD_OK;
 }

@@ -106,6 +106,7 @@ struct BatchImpl {
   int a_boxes = 1;  // 2 when some Gram unit has a second 128-row half
   int phase_blocks = kGramPhaseBlocks;
   bool overlap = false;     // features phase by phase beside the Gram (a lone cloud, tuned)
+  unsigned long long* prof = nullptr;  // the autotuner's per-CTA times of the Gram launches (or null)
   bool phi_batched = true;  // all clouds on the emulated path (no native-FP64 flag)
   // per-call device words
   CloudCall* d_calls = nullptr;  // followed by three block prefixes (count + 1 ints each)
@@ -608,9 +609,9 @@ rfd_status run_segment(BatchImpl* b, const int (&key)[4], bool graph, Timing* tm
 cudaError_t gram_phase(BatchImpl* b, int mode, int kb0, cudaStream_t s) {
   if (b->n_pair[mode] > 0)
     return launch_gram_pair_phase(b->d_maps, b->d_pair[mode], b->n_pair[mode], b->pair_stage_bytes, kb0,
-                                  b->phase_blocks, b->d_err, s);
+                                  b->phase_blocks, b->d_err, s, b->prof);
   return launch_gram_tc_phase(b->d_maps, b->d_units[mode], b->n_units[mode], b->a_boxes, kb0, b->phase_blocks,
-                              b->d_err, s);
+                              b->d_err, s, b->prof);
 }
 // All phases of the reductions over N of `mode`, one launch each.
 cudaError_t gram_all(BatchImpl* b, int mode, cudaStream_t s) {
@@ -911,6 +912,8 @@ void Timing::reset(cudaStream_t st) {
 }
 
 void batch_set_phase(BatchImpl* b, int phase_blocks) { b->phase_blocks = phase_blocks; }
+
+void batch_set_profile(BatchImpl* b, unsigned long long* prof) { b->prof = prof; }
 
 bool batch_set_overlap(BatchImpl* b, bool overlap) {
   b->overlap = overlap;

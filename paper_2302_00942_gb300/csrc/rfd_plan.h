@@ -161,6 +161,10 @@ struct rfd_plan_s {
   std::vector<void*> allocs;       // temporary owners only (rfd_phi1, debug GEMM)
   rfd::MemSource* mem = nullptr;   // source of the plan's single device chunk
   rfd::GramTuning tune;            // tensor-core reduction launch parameters
+  // per-block cost of each compute tile, measured by the autotuner ([form: one SM, CTA pairs][mode];
+  // empty: the cost model), so that every tile's lanes sweep the point axis at one pace
+  std::vector<double> tile_cost[2][3];
+  double tune_form_ms[2] = {0.0, 0.0};  // the autotuner's best time of each form
   bool autotune = false, tuned = false;
   void* chunk = nullptr;
   size_t chunk_bytes = 0;
@@ -216,5 +220,8 @@ void batch_set_phase(BatchImpl* b, int phase_blocks);
 // Features beside the Gram on or off; returns whether the batch can run that schedule at all
 // (a lone cloud with several phases of a multiple of 8 blocks).
 bool batch_set_overlap(BatchImpl* b, bool overlap);
+// Gram launches record each CTA's start and end (%globaltimer) into prof (2 words per CTA;
+// null: off).  The autotuner's measure of the tiles' pace.
+void batch_set_profile(BatchImpl* b, unsigned long long* prof);
 
 }  // namespace rfd
