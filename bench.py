@@ -802,7 +802,7 @@ def main():
                "what": "rfd_integrate on the compact plan: B^T F from the points (FP32 SIMT), a5, a6",
                "step_ms": {k: round(v, 4) for k, v in cst["step_ms"].items() if v},
                "device_bytes": int(compact_bytes), "full_plan_device_bytes": int(full_bytes),
-               "increment_rel_diff_vs_resident_bf16": compact_dev}
+               "increment_rel_diff_vs_resident": compact_dev}
     plan.close()
     gplan.close()
 
@@ -918,7 +918,7 @@ def main():
                      "features_beside_gram": bool(st.get("tune_overlap")),
                      "form_ms": {"one_sm": round(st["tune_form_ms"][0], 4), "cta_pairs": round(st["tune_form_ms"][1], 4)}},
         "warm": {"value": whole_job_value(ws, n * c, warm_ms), "unit": "points*ch/s", "ms_per_step": warm_ms,
-                 "what": "rfd_integrate: a new field on the resident features and G (steps a3(Y) to a6)",
+                 "what": "rfd_integrate: a new field on the resident plan (steps a3(Y) to a6; with c <= 4 B^T F comes from the points in FP32, with more channels from a pass over the resident BF16 Psi)",
                  "step_ms": {k: round(v, 4) for k, v in wst["step_ms"].items() if v}},
         "warm_compact": compact,
         "fp32_plain": fp32,

@@ -24,6 +24,8 @@
 namespace rfd {
 const char* last_error_cstr();
 thread_local long long t_kernel_launches = 0;
+// the points-based Phi^T F of a full BF16 plan, with the Gram partials as its scratch
+void set_points_field_job(rfd_plan_s* pl);
 }  // namespace rfd
 
 using namespace rfd;
@@ -557,6 +559,7 @@ rfd_status build_desc(rfd_plan_s* pl) {
     if (base > pl->part_slots) return fail(RFD_ECUDA, "internal: Gram partial slots exceed their allocation");
   }
   if (rfd_status ps = build_pair_desc(pl); ps != RFD_OK) return ps;
+  set_points_field_job(pl);
   auto* psi = static_cast<__nv_bfloat16_raw*>(pl->d_psi);
   d.feat = FeatJob{pl->n, pl->n_pad, pl->d_omega_hi, psi, pl->d_xyz, pl->h, (int)((pl->n_pad + 511) / 512), 0,
                    pl->rows_alloc};
@@ -948,13 +951,14 @@ void plan_carve(rfd_plan_s* pl, PlanCarve& c) {
 // Chunks of the points-based Phi^T F of a compact plan: enough for ~6 blocks of 256 threads
 // per SM (at 512 frequencies per block), of at least 1024 points each, with partials
 // ([chunks][m][ld] floats, ld = channels padded to 4) no larger than the points' own
-// 12 N bytes (4 MB at least).
-void fieldpts_shape(const rfd_plan_s* pl, int* chunks, int64_t* pts, int* ld) {
+// 12 N bytes (4 MB at least) and, where given, no larger than max_floats.
+void fieldpts_shape(const rfd_plan_s* pl, int* chunks, int64_t* pts, int* ld, int64_t max_floats = 0) {
   *ld = (int)round_up(pl->p.max_channels, 4);
   const int64_t fgroups = (pl->h + 511) / 512;
   const int64_t want = std::max<int64_t>(1, (6ll * std::max(pl->sms, 1) + fgroups - 1) / fgroups);
-  const int64_t cap =
-      std::max<int64_t>(1, std::max<int64_t>(4ll << 20, 12 * pl->n) / ((int64_t)pl->m * *ld * 4));
+  int64_t cap = std::max<int64_t>(4ll << 20, 12 * pl->n) / ((int64_t)pl->m * *ld * 4);
+  if (max_floats > 0) cap = std::min<int64_t>(cap, max_floats / ((int64_t)pl->m * *ld));
+  cap = std::max<int64_t>(1, cap);
   int64_t ch = std::min<int64_t>({want, cap, std::max<int64_t>(1, (pl->n + 1023) / 1024)});
   *pts = (pl->n + ch - 1) / ch;
   *chunks = (int)((pl->n + *pts - 1) / *pts);
@@ -999,6 +1003,17 @@ void build_compact_desc(rfd_plan_s* pl) {
 }
 
 }  // namespace
+
+void set_points_field_job(rfd_plan_s* pl) {
+  if (pl->compact) return;  // a compact plan's job (build_compact_desc) stays
+  pl->desc.fpts = FieldPtsJob{};
+  if (!pl->bf16 || !pl->d_part || pl->part_slots < 1) return;
+  int chunks, ld;
+  int64_t pts;
+  fieldpts_shape(pl, &chunks, &pts, &ld, (int64_t)pl->part_slots * pl->slot_elems);
+  pl->desc.fpts = FieldPtsJob{pl->d_xyz, pl->d_omega_hi, pl->d_part, pl->n, pts, pl->h, pl->m, chunks, ld, 0, 0,
+                              pl->d_Y,   pl->d_ob};
+}
 
 size_t plan_compact_bytes(const rfd_plan_s* pl) {
   rfd_plan_s tmp;  // the carve only reads the sizes

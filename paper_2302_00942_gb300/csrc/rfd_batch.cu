@@ -34,6 +34,7 @@ namespace {
 constexpr double kThetaT16 = 0.977;
 constexpr int kTaylorDegree = 16;
 constexpr int kMaxSquarings = 60;                 // beyond this exp(lambda M) overflows anyway
+constexpr int kPtsMaxChannels = 4;  // integrate calls of full plans up to this c take Phi^T F from the points
 // matrix slots of the phi1 evaluation (see kernels.h: slot k = work + k m^2)
 enum : int { sX = 0, sX2, sX3, sX4, sB, sF, sFb, sE, sT1 };
 
@@ -71,6 +72,7 @@ struct BatchImpl {
   TcUnit* d_units[3] = {};
   int n_units[3] = {};
   bool compact = false;      // every plan compact: integrate computes Phi^T F from the points
+  bool pts_ok = false;       // every plan has a points-based Phi^T F (compact, or a full BF16 plan)
   FieldPtsJob* d_fpts = nullptr;
   std::vector<FieldPtsJob> fpts_h;  // host copies (block counts per call)
   PairUnit* d_pair[3] = {};  // a lone cloud with m >= 512: the 2-SM form of the Gram modes
@@ -190,7 +192,9 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   for (int k = 0; k < count; ++k) n_compact += plans[k]->compact ? 1 : 0;
   if (n_compact && n_compact != count) return bail(RFD_EINVAL, "a batch cannot mix compact and full plans");
   b->compact = n_compact == count;
-  if (b->compact)
+  b->pts_ok = true;
+  for (int k = 0; k < count; ++k) b->pts_ok = b->pts_ok && plans[k]->desc.fpts.part != nullptr;
+  if (b->pts_ok)
     for (int k = 0; k < count; ++k) {
       b->fpts_h.push_back(plans[k]->desc.fpts);
       b->fpts_h.back().cloud = k;
@@ -209,7 +213,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
     if (!ozaki_supported(pl->m) || (pl->p.flags & RFD_FLAG_NATIVE_FP64)) b->phi_batched = false;
     std::memcpy(maps.data() + (size_t)k * kMapsPerCloud * kTensorMapBytes, d.maps, sizeof(d.maps));
     const int64_t kb = pl->n_pad / kTcBK;
-    if (b->compact) {  // integrate from the points only
+    if (b->pts_ok) {  // integrate from the points (always for compact plans)
       FieldPtsJob fj = d.fpts;
       fj.cloud = k;
       fpts.push_back(fj);
@@ -698,15 +702,19 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   const int apply_blocks = hp[n];
   const int* d_apply_prefix = reinterpret_cast<const int*>(reinterpret_cast<unsigned char*>(b->d_calls) +
                                                            (size_t)n * sizeof(CloudCall));
-  // compact plans: the blocks of the points-based Phi^T F (they depend on c too)
+  // Phi^T F from the points: always for compact plans; for full plans in integration calls of
+  // few channels, where it is faster than a pass over Psi (its cost grows with c, the pass's
+  // hardly) and carries no BF16 rounding
+  const bool pts = b->compact || (mode == kModeIntegrate && b->pts_ok && max_c <= kPtsMaxChannels);
+  // the blocks of the points-based Phi^T F (they depend on c too)
   int* hq = hp + (n + 1);
   hq[0] = 0;
-  for (int k = 0; k < n; ++k) hq[k + 1] = hq[k] + (b->compact ? fieldpts_blocks(b->fpts_h[k], calls[k].c, cg) : 0);
+  for (int k = 0; k < n; ++k) hq[k + 1] = hq[k] + (pts ? fieldpts_blocks(b->fpts_h[k], calls[k].c, cg) : 0);
   const int fpts_blocks = hq[n];
   const int* d_fpts_prefix = d_apply_prefix + (n + 1);
   int* hr = hq + (n + 1);  // and of their sums over the chunks
   hr[0] = 0;
-  for (int k = 0; k < n; ++k) hr[k + 1] = hr[k] + (b->compact ? fieldpts_reduce_blocks(b->fpts_h[k], calls[k].c) : 0);
+  for (int k = 0; k < n; ++k) hr[k + 1] = hr[k] + (pts ? fieldpts_reduce_blocks(b->fpts_h[k], calls[k].c) : 0);
   const int fred_blocks = hr[n];
   const int* d_fred_prefix = d_fpts_prefix + (n + 1);
   if (b->compact && mode != kModeIntegrate)
@@ -719,7 +727,7 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
 
   const bool pipelined = with_feat && pipelines(b);
   auto reductions = [&](cudaStream_t s, Timing* t) -> rfd_status {
-    if (b->compact) {  // Phi^T F from the points, summed over the chunks by the reduce kernel
+    if (pts) {  // Phi^T F from the points, summed over the chunks by the reduce kernel
       {
         StepScope sc(t, s, RFD_STEP_FIELD);
         BCK(launch_fieldpts_batched(b->d_fpts, d_fpts_prefix, n, fpts_blocks, cg, b->d_calls, s));
@@ -771,9 +779,8 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
     return run_segment(b, key, graph, tm, reductions);
   }
   if (!with_phi) {
-    // compact batches: both points-based launches' grids (they depend on every call's c)
-    const int key[4] = {mode, b->compact ? -4 - fpts_blocks : -1, b->compact ? cg + 64 * fred_blocks : cg,
-                        apply_blocks};
+    // the points-based path: both of its launches' grids (they depend on every call's c)
+    const int key[4] = {mode, pts ? -4 - fpts_blocks : -1, pts ? cg + 64 * fred_blocks : cg, apply_blocks};
     return run_segment(b, key, graph, tm, [&](cudaStream_t s, Timing* t) -> rfd_status {
       rfd_status r = reductions(s, t);
       return r == RFD_OK ? small_apply(s, t) : r;

@@ -148,6 +148,30 @@ def test_warm_path_equals_cold_and_inplace(prec):
     np.testing.assert_array_equal(inpl, cold)
 
 
+def test_warm_integrate_of_few_channels_has_no_bf16_rounding():
+    """A full BF16 plan integrates a field of few channels (c <= 4) with B^T F
+    from the points in FP32, the compact plans' path, so its increment error
+    drops well below the cold pass's, whose B^T F rides on the BF16 Psi; with
+    more channels it passes over Psi, within the BF16 bounds."""
+    spec, pts, F, lam = small_case("torus")
+    plan = rfd.Plan(spec.n, spec.m, spec.eps, lam, spec.seed, max_channels=16, precision=rfd.RFD_BF16_TC,
+                    stream=torch.cuda.current_stream(DEV))
+    try:
+        F3 = np.ascontiguousarray(F[:, :3])
+        cold = plan.gfi(_cuda(pts), _cuda(F3))
+        warm = plan.integrate(_cuda(F3))
+        wide = plan.integrate(_cuda(F))
+        plan.sync()
+        ref3 = oracle.rfd_gfi(pts, F3, spec.eps, lam, spec.m, spec.seed)
+        ref = oracle.rfd_gfi(pts, F, spec.eps, lam, spec.m, spec.seed)
+        e_cold = pc.assert_matches(cold.cpu().numpy(), ref3, F3, rfd.RFD_BF16_TC, label="cold, c=3")
+        e_warm = pc.assert_matches(warm.cpu().numpy(), ref3, F3, rfd.RFD_BF16_TC, label="warm, c=3")
+        pc.assert_matches(wide.cpu().numpy(), ref, F, rfd.RFD_BF16_TC, label=f"warm, c={F.shape[1]}")
+        assert e_warm["inc"] < 0.2 * e_cold["inc"], (e_warm, e_cold)
+    finally:
+        plan.close()
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_resident_plan_reuse_new_fields(prec):
     """One plan, resident Phi and G, several fields of different widths (Sec. 2.4 inference)."""
