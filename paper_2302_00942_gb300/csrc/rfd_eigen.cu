@@ -73,9 +73,116 @@ __device__ float block_sum(float v, float* red) {
   return s;
 }
 
+// e / d and e % d for 0 <= e < 2^14, 1 <= d <= 2^7 by a multiply-high with ceil(2^32 / d):
+// the error e (ceil(2^32/d) - 2^32/d) / 2^32 < 2^-18 stays below the gap 1/d to the next
+// integer, so the quotient is exact (the loops below index flat m x m or t x t ranges).
+struct FastDiv {
+  uint32_t d, magic;
+  __device__ explicit FastDiv(int dd) : d((uint32_t)dd), magic(dd > 1 ? 0xFFFFFFFFu / (uint32_t)dd + 1u : 0u) {}
+  __device__ int quo(int e) const { return d > 1 ? (int)__umulhi((uint32_t)e, magic) : e; }
+};
 __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // j <= i
 __device__ __forceinline__ double root(double x) { return sqrt(x); }
 __device__ __forceinline__ float root(float x) { return sqrtf(x); }
+
+// All m eigenvalues of the symmetric H (m x m, row stride ld, FP32; overwritten)
+// into mu[0..m): Householder reduction to tridiagonal form (m - 2 reflections,
+// each a matrix-vector product and a rank-2 update over the CTA, 5 barriers),
+// then bisection on Sturm counts, one thread per eigenvalue with no barrier.
+// Backward stable in FP32: the eigenvalues carry an error of ~m 2^-24 ||H||.
+// Scratch: vs, ps (m floats each), dg, e2 (m floats each), red (block_sum's).
+__device__ void eig_tridiag_bisect(float* H, int ld, int m, double* mu, float* vs, float* ps, float* dg,
+                                   float* e2, float* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int k = 0; k + 2 < m; ++k) {
+    const int n = m - k - 1;  // the column below the diagonal: rows k + 1 .. m - 1
+    float ss = 0.f;
+    for (int i = tid; i < n; i += nt) {
+      const float x = H[(k + 1 + i) * ld + k];
+      ss = fmaf(x, x, ss);
+    }
+    ss = block_sum(ss, red);  // the whole CTA has it
+    const float x0 = H[(k + 1) * ld + k];
+    const float tail = ss - x0 * x0;  // below the subdiagonal
+    const bool reflect = tail > 1e-30f * ss;
+    float alpha = x0;
+    if (reflect) {
+      alpha = x0 > 0.f ? -sqrtf(ss) : sqrtf(ss);
+      const float beta = 1.f / (ss - alpha * x0);  // 2 / ||v||^2, v = x - alpha e1
+      for (int i = tid; i < n; i += nt) vs[i] = H[(k + 1 + i) * ld + k] - (i == 0 ? alpha : 0.f);
+      __syncthreads();
+      for (int i = tid; i < n; i += nt) {  // p = beta H' v, H' the trailing block
+        const float* row = H + (k + 1 + i) * ld + (k + 1);
+        float acc = 0.f;
+        for (int j = 0; j < n; ++j) acc = fmaf(row[j], vs[j], acc);
+        ps[i] = beta * acc;
+      }
+      __syncthreads();
+      float vp = 0.f;
+      for (int i = tid; i < n; i += nt) vp = fmaf(vs[i], ps[i], vp);
+      const float kk = 0.5f * beta * block_sum(vp, red);
+      for (int i = tid; i < n; i += nt) ps[i] = fmaf(-kk, vs[i], ps[i]);  // w = p - (beta v^T p / 2) v
+      __syncthreads();
+      const FastDiv divn(n);
+      for (int e = tid; e < n * n; e += nt) {  // H' -= v w^T + w v^T
+        const int i = divn.quo(e), j = e - i * n;
+        float* h = H + (k + 1 + i) * ld + (k + 1 + j);
+        *h = fmaf(-vs[i], ps[j], fmaf(-ps[i], vs[j], *h));
+      }
+    }
+    if (tid == 0) {
+      dg[k] = H[k * ld + k];  // untouched by this step's update
+      e2[k] = alpha * alpha;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (m >= 2) {
+      dg[m - 2] = H[(m - 2) * ld + m - 2];
+      const float e = H[(m - 1) * ld + m - 2];
+      e2[m - 2] = e * e;
+    }
+    dg[m - 1] = H[(m - 1) * ld + m - 1];
+    // Gershgorin bounds of the tridiagonal matrix, in red[0], red[1]
+    float lo = 3.0e38f, hi = -3.0e38f;
+    for (int i = 0; i < m; ++i) {
+      const float r = (i > 0 ? sqrtf(e2[i - 1]) : 0.f) + (i + 1 < m ? sqrtf(e2[i]) : 0.f);
+      lo = fminf(lo, dg[i] - r);
+      hi = fmaxf(hi, dg[i] + r);
+    }
+    const float w = fmaxf(fabsf(lo), fabsf(hi));
+    red[0] = lo - 1e-6f * w - 1e-30f;
+    red[1] = hi + 1e-6f * w + 1e-30f;
+  }
+  __syncthreads();
+  const float lo0 = red[0], hi0 = red[1];
+  const float tnorm = fmaxf(fabsf(lo0), fabsf(hi0));
+  const float pivmin = 1e-30f * fmaxf(1.f, tnorm);
+  // an interval of 2^-24 ||T|| is below the reduction's own error (~m 2^-24 ||H||)
+  const float tol = 5.96e-8f * tnorm;
+  for (int i = tid; i < m; i += nt) {  // the (i + 1)-th smallest eigenvalue
+    float a = lo0, b = hi0;
+    for (int it = 0; it < 64 && b - a > tol; ++it) {
+      const float x = 0.5f * (a + b);
+      if (!(x > a && x < b)) break;  // no representable midpoint left
+      int cnt = 0;                   // eigenvalues below x (Sturm sequence of T - x I)
+      float q = dg[0] - x;
+      if (fabsf(q) < pivmin) q = -pivmin;
+      cnt += q < 0.f;
+      for (int j = 1; j < m; ++j) {
+        q = (dg[j] - x) - __fdividef(e2[j - 1], q);  // |q| >= pivmin, far below 2^126
+        if (fabsf(q) < pivmin) q = -pivmin;
+        cnt += q < 0.f;
+      }
+      if (cnt > i)
+        b = x;
+      else
+        a = x;
+    }
+    mu[i] = 0.5 * ((double)a + (double)b);
+  }
+  __syncthreads();
+}
 
 // REFINE: FP64 Cholesky and FP64 Rayleigh quotients of the FP32 eigenvectors
 // (the FP32 plain form's M); otherwise FP32 throughout and the eigenvalues are
@@ -98,8 +205,9 @@ __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob*
 
   // P = M Sigma, symmetrised (M Sigma is symmetric up to rounding), FP64
   for (int i = tid; i < m; i += nt) sig[i] = jb.oa[i] < 0.0 ? -1.f : 1.f;
+  const FastDiv divm(m);
   for (int e = tid; e < m * m; e += nt) {
-    const int i = e / m, j = e % m;
+    const int i = divm.quo(e), j = e - i * m;
     if (j > i) continue;
     const double si = jb.oa[i] < 0.0 ? -1.0 : 1.0, sj = jb.oa[j] < 0.0 ? -1.0 : 1.0;
     L[tri(i, j)] = (TL)(0.5 * (jb.M[(size_t)i * m + j] * sj + jb.M[(size_t)j * m + i] * si));
@@ -119,8 +227,9 @@ __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob*
     for (int i = j + 1 + tid; i < m; i += nt) L[tri(i, j)] *= inv;
     __syncthreads();
     const int t = m - j - 1;
+    const FastDiv divt(t > 0 ? t : 1);
     for (int e = tid; e < t * t; e += nt) {
-      const int i = j + 1 + e / t, l = j + 1 + e % t;
+      const int q = divt.quo(e), i = j + 1 + q, l = j + 1 + (e - q * t);
       if (l <= i) L[tri(i, l)] -= L[tri(i, j)] * L[tri(l, j)];
     }
     __syncthreads();
@@ -131,13 +240,13 @@ __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob*
   const float* Lf = reinterpret_cast<const float*>(L);
   if constexpr (REFINE) {
     for (int e = tid; e < m * m; e += nt) {
-      const int i = e / m, j = e % m;
+      const int i = divm.quo(e), j = e - i * m;
       V[i * ld + j] = j <= i ? (float)L[tri(i, j)] : 0.f;
     }
     __syncthreads();
   }
   for (int e = tid; e < m * m; e += nt) {
-    const int a = e / m, b = e % m;
+    const int a = divm.quo(e), b = e - a * m;
     if (a > b) continue;
     float s = 0.f;
     if constexpr (REFINE)
@@ -148,6 +257,9 @@ __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob*
     H[b * ld + a] = s;
   }
   __syncthreads();
+  if constexpr (!REFINE) {  // eigenvalues only: tridiagonal form and bisection
+    eig_tridiag_bisect(H, ld, m, mu, cs, cs + m, reinterpret_cast<float*>(pq), reinterpret_cast<float*>(pq) + m, red);
+  } else {
   if constexpr (REFINE) {
     for (int e = tid; e < m * m; e += nt) V[(e / m) * ld + e % m] = (e / m) == (e % m) ? 1.f : 0.f;
     __syncthreads();
@@ -184,7 +296,7 @@ __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob*
   for (int sweep = 0; sweep < kMaxSweeps && m > 1; ++sweep) {
     float off = 0.f;
     for (int e = tid; e < m * m; e += nt) {
-      const int a = e / m, b = e % m;
+      const int a = divm.quo(e), b = e - a * m;
       if (a != b) off += H[a * ld + b] * H[a * ld + b];
     }
     off = block_sum(off, red);
@@ -257,10 +369,7 @@ __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob*
     }
   }
 
-  if constexpr (!REFINE) {
-    for (int a2 = tid; a2 < m; a2 += nt) mu[a2] = (double)H[a2 * ld + a2];
-    __syncthreads();
-  } else {
+  {
   // the eigenvectors to FP64, one padded row per vector (V64[a][j] = V[j][a]),
   // over the space of H and V: rows a < m/2 land in H's space; the columns
   // a >= m/2 of V are read into registers before their rows overwrite V's
@@ -309,6 +418,7 @@ __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob*
   __syncthreads();
 
   }
+  }  // REFINE
 
   // the spectrum of exp(lambda W_hat): drop the rank deficiency, sort, merge the
   // ones -- all by ranks (thread i counts the entries before entry i), no serial step
