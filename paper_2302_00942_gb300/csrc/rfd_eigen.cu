@@ -87,30 +87,39 @@ __device__ __forceinline__ float root(float x) { return sqrtf(x); }
 
 // All m eigenvalues of the symmetric H (m x m, row stride ld, FP32; overwritten)
 // into mu[0..m): Householder reduction to tridiagonal form (m - 2 reflections,
-// each a matrix-vector product and a rank-2 update over the CTA, 5 barriers),
+// each a matrix-vector product and a rank-2 update over the CTA),
 // then bisection on Sturm counts, one thread per eigenvalue with no barrier.
-// Backward stable in FP32: the eigenvalues carry an error of ~m 2^-24 ||H||.
-// Scratch: vs, ps (m floats each), dg, e2 (m floats each), red (block_sum's).
+// Each reflection's norm, v and w come from one warp (shuffle sums), so a
+// reflection takes four CTA barriers.  Backward stable in FP32: the
+// eigenvalues carry an error of ~m 2^-24 ||H||.
+// Scratch: vs, ps (m floats each), dg, e2 (m floats each), red (>= 2 floats).
 __device__ void eig_tridiag_bisect(float* H, int ld, int m, double* mu, float* vs, float* ps, float* dg,
                                    float* e2, float* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
   for (int k = 0; k + 2 < m; ++k) {
     const int n = m - k - 1;  // the column below the diagonal: rows k + 1 .. m - 1
-    float ss = 0.f;
-    for (int i = tid; i < n; i += nt) {
-      const float x = H[(k + 1 + i) * ld + k];
-      ss = fmaf(x, x, ss);
+    if (warp == 0) {  // the reflection: norm, alpha, beta and v, by one warp (no block reduction)
+      float ss = 0.f;
+      for (int i = lane; i < n; i += 32) {
+        const float x = H[(k + 1 + i) * ld + k];
+        ss = fmaf(x, x, ss);
+      }
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      const float x0 = H[(k + 1) * ld + k];
+      const bool reflect = ss - x0 * x0 > 1e-30f * ss;  // anything below the subdiagonal
+      const float alpha = reflect ? (x0 > 0.f ? -sqrtf(ss) : sqrtf(ss)) : x0;
+      if (reflect)
+        for (int i = lane; i < n; i += 32) vs[i] = H[(k + 1 + i) * ld + k] - (i == 0 ? alpha : 0.f);
+      if (lane == 0) {
+        red[0] = reflect ? 1.f / (ss - alpha * x0) : 0.f;  // beta = 2 / ||v||^2, v = x - alpha e1
+        dg[k] = H[k * ld + k];                              // final since the previous step
+        e2[k] = alpha * alpha;
+      }
     }
-    ss = block_sum(ss, red);  // the whole CTA has it
-    const float x0 = H[(k + 1) * ld + k];
-    const float tail = ss - x0 * x0;  // below the subdiagonal
-    const bool reflect = tail > 1e-30f * ss;
-    float alpha = x0;
-    if (reflect) {
-      alpha = x0 > 0.f ? -sqrtf(ss) : sqrtf(ss);
-      const float beta = 1.f / (ss - alpha * x0);  // 2 / ||v||^2, v = x - alpha e1
-      for (int i = tid; i < n; i += nt) vs[i] = H[(k + 1 + i) * ld + k] - (i == 0 ? alpha : 0.f);
-      __syncthreads();
+    __syncthreads();
+    const float beta = red[0];
+    if (beta != 0.f) {
       for (int i = tid; i < n; i += nt) {  // p = beta H' v, H' the trailing block
         const float* row = H + (k + 1 + i) * ld + (k + 1);
         float acc = 0.f;
@@ -118,10 +127,13 @@ __device__ void eig_tridiag_bisect(float* H, int ld, int m, double* mu, float* v
         ps[i] = beta * acc;
       }
       __syncthreads();
-      float vp = 0.f;
-      for (int i = tid; i < n; i += nt) vp = fmaf(vs[i], ps[i], vp);
-      const float kk = 0.5f * beta * block_sum(vp, red);
-      for (int i = tid; i < n; i += nt) ps[i] = fmaf(-kk, vs[i], ps[i]);  // w = p - (beta v^T p / 2) v
+      if (warp == 0) {  // w = p - (beta v^T p / 2) v
+        float vp = 0.f;
+        for (int i = lane; i < n; i += 32) vp = fmaf(vs[i], ps[i], vp);
+        for (int o = 16; o > 0; o >>= 1) vp += __shfl_xor_sync(0xffffffffu, vp, o);
+        const float kk = 0.5f * beta * vp;
+        for (int i = lane; i < n; i += 32) ps[i] = fmaf(-kk, vs[i], ps[i]);
+      }
       __syncthreads();
       const FastDiv divn(n);
       for (int e = tid; e < n * n; e += nt) {  // H' -= v w^T + w v^T
@@ -130,11 +142,7 @@ __device__ void eig_tridiag_bisect(float* H, int ld, int m, double* mu, float* v
         *h = fmaf(-vs[i], ps[j], fmaf(-ps[i], vs[j], *h));
       }
     }
-    if (tid == 0) {
-      dg[k] = H[k * ld + k];  // untouched by this step's update
-      e2[k] = alpha * alpha;
-    }
-    __syncthreads();
+    __syncthreads();  // the update is complete; red[0] and vs may be rewritten
   }
   if (tid == 0) {
     if (m >= 2) {
@@ -252,7 +260,8 @@ __global__ void __launch_bounds__(kEigThreads) kernel_eigen_kernel(const EigJob*
     if constexpr (REFINE)
       for (int i = b; i < m; ++i) s = fmaf(V[i * ld + a] * sig[i], V[i * ld + b], s);
     else
-      for (int i = b; i < m; ++i) s = fmaf(Lf[tri(i, a)] * sig[i], Lf[tri(i, b)], s);
+      for (int i = b, ia = tri(b, a), ib = tri(b, b); i < m; ia += i + 1, ib += i + 1, ++i)
+        s = fmaf(Lf[ia] * sig[i], Lf[ib], s);
     H[a * ld + b] = s;
     H[b * ld + a] = s;
   }
