@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--precision", choices=["bf16", "fp32"], default="bf16")
     ap.add_argument("--fp32-steps", type=int, default=2, help="timed steps of the FP32 plain form (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--c64-steps", type=int, default=20, help="timed steps of the c = 64 line (0: skip)")
     ap.add_argument("--cpu-sample", type=int, default=65536, help="points in the CPU-oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true",
@@ -255,25 +256,31 @@ def time_oracle_stages(pts, F, eps, lam, m, seed):
     return {k: round(v * 1e3, 3) for k, v in t.items()}
 
 
-def time_oracle_single_thread():
-    """The oracle on the small workload (N = 2048, m = 64, c = 3) with one BLAS /
-    OpenMP thread, in a child process (the thread count is fixed at import)."""
+def time_oracle_single_thread(name="small", sample=None, reps=5):
+    """The oracle on a workload (by default the small one: N = 2048, m = 64, c = 3),
+    or on its first `sample` points, with one BLAS / OpenMP thread, in a child
+    process (the thread count is fixed at import)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import json, time, oracle, synth\n"
-            "s = synth.config_single('small')\n"
+            f"s = synth.config_single({name!r})\n"
             "pts, F = synth.make_cloud(s)\n"
+            f"k = {sample or 0} or s.n\n"
+            "pts, F = pts[:k], F[:k]\n"
             "lam = s.lam * s.m / s.n\n"
             "oracle.rfd_gfi(pts, F, s.eps, lam, s.m, s.seed)\n"
             "t0 = time.perf_counter()\n"
-            "for _ in range(5): oracle.rfd_gfi(pts, F, s.eps, lam, s.m, s.seed)\n"
-            "t = (time.perf_counter() - t0) / 5\n"
-            "print(json.dumps({'ms': t * 1e3, 'value': s.n * s.c / t}))\n")
+            f"for _ in range({reps}): oracle.rfd_gfi(pts, F, s.eps, lam, s.m, s.seed)\n"
+            f"t = (time.perf_counter() - t0) / {reps}\n"
+            "print(json.dumps({'ms': t * 1e3, 'value': k * F.shape[1] / t, 'n': s.n, 'm': s.m, 'c': F.shape[1],"
+            " 'eps': s.eps}))\n")
     try:
         out = subprocess.run([sys.executable, "-c", code], env=env, cwd=os.path.dirname(os.path.abspath(__file__)),
                              capture_output=True, text=True, timeout=300)
         d = json.loads(out.stdout.strip().splitlines()[-1])
-        return {"workload": "small: N=2048 (sphere), eps=0.1, m=64, c=3", "cores": 1, "ms_per_step": d["ms"],
-                "value": d["value"], "unit": "points*ch/s"}
+        what = f"{name}: N={d['n']}, eps={d['eps']}, m={d['m']}, c={d['c']}"
+        if sample:
+            what += f"; the first {sample} points (lambda kept at the full cloud's lambda m/N)"
+        return {"workload": what, "cores": 1, "ms_per_step": d["ms"], "value": d["value"], "unit": "points*ch/s"}
     except Exception as e:  # a missing measurement is reported, not fatal
         return {"unavailable": str(e)[:200]}
 
@@ -806,6 +813,38 @@ def main():
     plan.close()
     gplan.close()
 
+    # the same cloud with 64 channels (the large workload's second field width): its own
+    # autotuned, graph-replayed plan, timed the same way
+    c64 = None
+    if prec == rfd.RFD_BF16_TC and c != 64 and args.c64_steps > 0:
+        F64 = torch.from_numpy(synth.gaussian_field(n, 64, spec.seed + 2)).to(dev)
+        o64 = torch.empty_like(F64)
+        p64 = rfd.Plan(n, m, spec.eps, lam, spec.seed, max_channels=64, precision=prec, stream=stream,
+                       autotune=tune, graph=True)
+        for _ in range(max(args.warmup, 3)):
+            p64.gfi(P, F64, o64)
+        p64.sync()
+        torch.cuda.synchronize(dev)
+        D.barrier()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(args.c64_steps):
+            p64.gfi(P, F64, o64)
+        q1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = D.max(q0.elapsed_time(q1) / args.c64_steps)
+        wm64, (pk, _) = work_model(n, m, 64), load_peaks()
+        t64 = max(wm64["hbm_bytes"] / (pk["hbm_gbs"] * 1e9),
+                  (wm64["gram_flops"] + wm64["apply_flops"]) / (pk["bf16_tflops"] * 1e12))
+        s64 = p64.stats()
+        c64 = {"value": whole_job_value(ws, n * 64, ms64), "unit": "points*ch/s", "ms_per_step": ms64,
+               "what": "rfd_gfi with c = 64 on the same cloud (own plan, CUDA graphs, autotuned)",
+               "path_roofline": {"t_roofline_ms": t64 * 1e3, "frac_of_step": t64 * 1e3 / ms64},
+               "autotune": {"lanes_pct": s64["tune_lanes_pct"], "phase_blocks": s64["tune_phase_blocks"],
+                            "gram_form": "CTA pairs (2-SM MMA)" if s64["tune_pair_gram"] else "one SM per tile"}}
+        p64.close()
+        del F64, o64
+
     # FP32 plain form on the same inputs (the form the BF16 path must beat), and the BF16 form's
     # deviation from it (the FP32 form matches the FP64 oracle to <= 1e-5 in the parity tests)
     fp32 = None
@@ -884,6 +923,8 @@ def main():
     roof["peak_source"] = (f"{peak_src} (burst bf16: the kernel runs at full SM clock inside a ~2 ms step; "
                            f"the sustained figure is for seconds-long loops under the power cap)")
     roof["scope"] = "the dominant kernel alone; the whole step's fraction is path_roofline.frac_of_step"
+    # the same time against the paper-literal work of a general B^T A (2 N m^2) and B^T F
+    roof["frac_paper_literal"] = (2.0 * n * m * m + 2.0 * n * m * c) / (steps["gram"] * 1e-3) / 1e12 / peaks["bf16_tflops"]
     roof["dominant_step"] = dom
     # whole-path roofline: slower of HBM bytes at peak bandwidth and tensor flops at peak
     t_roof = max(wm["hbm_bytes"] / (peaks["hbm_gbs"] * 1e9),
@@ -899,7 +940,11 @@ def main():
                           "bound": "tensor" if wm["gram_flops"] / peaks["bf16_tflops"] / 1e12 >
                           wm["hbm_bytes"] / peaks["hbm_gbs"] / 1e9 else "hbm",
                           "peak": "measured burst bf16 and copy bandwidth",
-                          "target_frac": 0.60, "target_met": t_roof * 1e3 / ms_max >= 0.60},
+                          "target_frac": 0.60, "target_met": t_roof * 1e3 / ms_max >= 0.60,
+                          # against the paper-literal tensor work (a general B^T A: 2 N m^2, plus 4 N m c)
+                          "frac_of_step_paper_literal": max(wm["hbm_bytes"] / (peaks["hbm_gbs"] * 1e9),
+                                                            (2.0 * n * m * m + 4.0 * n * m * c) /
+                                                            (peaks["bf16_tflops"] * 1e12)) * 1e3 / ms_max},
         "step_ms": {k: round(v, 4) for k, v in steps.items()},
         "step_roofline": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
                           for k, v in step_roof.items()},
@@ -922,6 +967,7 @@ def main():
                  "step_ms": {k: round(v, 4) for k, v in wst["step_ms"].items() if v}},
         "warm_compact": compact,
         "fp32_plain": fp32,
+        "headline_c64": c64,
     }
     if "batched" in sections and args.batched_clouds > 0 and prec == rfd.RFD_BF16_TC:
         res["batched"] = bench_batched(args, dev, stream, D)
@@ -946,7 +992,8 @@ def main():
         res["cpu_baseline"] = {"value": ns * c / t, "unit": "points*ch/s", "cores": cpu_cores(), "kind": "oracle",
                                "sample": f"first {ns} of {n} points, same m, c, eps, lambda; whole path, FP64",
                                "stages_ms": time_oracle_stages(pts[:ns], F[:ns], spec.eps, lam, m, spec.seed),
-                               "single_thread": time_oracle_single_thread()}
+                               "single_thread": time_oracle_single_thread(),
+                               "single_thread_torus": time_oracle_single_thread("torus", None, 1)}
     if rank == 0:
         print(json.dumps(res))
     D.close()
