@@ -140,6 +140,7 @@ def _load():
         "rfd_debug_plan_phi1": (I32, [P, P]),
         "rfd_debug_plan_set_phase": (I32, [P, I32]),
         "rfd_debug_plan_set_overlap": (I32, [P, I32]),
+        "rfd_debug_plan_set_apply_tc": (I32, [P, I32]),
         "rfd_debug_gram_pairs": (None, [I32]),
         "rfd_debug_plan_wait_timeout": (I32, [P, I32]),
         "rfd_batch_create": (I32, [ctypes.POINTER(P), I32, I32, P, ctypes.POINTER(P)]),
@@ -172,6 +173,7 @@ HEADER_SYMBOLS = ("rfd_sample_frequencies", "rfd_sample_weights", "rfd_barycente
                   "rfd_gfi", "rfd_phi1", "rfd_phi1_noalloc", "rfd_sync", "rfd_plan_export", "rfd_plan_stats", "rfd_plan_stats_reset", "rfd_plan_compact",
                   "rfd_plan_device_bytes", "rfd_last_error",
                   "rfd_version", "rfd_debug_fail_alloc_after", "rfd_debug_dgemm", "rfd_debug_plan_phi1", "rfd_debug_plan_set_phase", "rfd_debug_plan_set_overlap",
+                  "rfd_debug_plan_set_apply_tc",
                   "rfd_debug_plan_wait_timeout", "rfd_debug_gram_pairs", "rfd_batch_create",
                   "rfd_batch_destroy", "rfd_batch_features", "rfd_batch_integrate", "rfd_batch_gfi",
                   "rfd_batch_sync", "rfd_batch_stats", "rfd_batch_stats_reset", "rfd_server_create",

@@ -24,7 +24,7 @@ LIB = os.path.join(HERE, "librfd_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["tc_common.cu", "k_features.cu", "k_gram_simt.cu", "k_gram_tc.cu", "k_gram_pair.cu", "k_reduce_apply.cu", "k_fp64.cu",
-              "k_ozaki.cu", "k_batch.cu", "rfd_batch.cu",
+              "k_ozaki.cu", "k_batch.cu", "k_apply_tc.cu", "rfd_batch.cu",
               "rfd_phi1.cu", "rfd_api.cu", "rfd_noalloc.cu", "rfd_server.cu", "rfd_barycenter.cu",
               "rfd_gw.cu", "rfd_eigen.cu"]
 CPP_SOURCES = ["rfd_host.cpp"]

@@ -109,9 +109,9 @@ features_batched_kernel(const FeatJob* __restrict__ jobs, const int* __restrict_
   }
 }
 
-// F^T rows of the feature buffer: one point per thread, every row of the
-// point written by it (coalesced along the points); points >= N and rows
-// beyond the channels get zeros.
+// F^T rows of the feature buffer, for fields of up to 8 channels: one point
+// per thread, every row of the point written by it (coalesced along the
+// points); points >= N and rows beyond the channels get zeros.
 __global__ void __launch_bounds__(256)
 fill_batched_kernel(const FillJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
                     const CloudCall* __restrict__ calls) {
@@ -133,6 +133,46 @@ fill_batched_kernel(const FillJob* __restrict__ jobs, const int* __restrict__ pr
   }
   const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
   for (int row = jb.fsplit ? 2 * c : c; row < jb.cpad; ++row) psi[psi_index(p, r0 + row, ra)] = zero;
+}
+
+// The same for wider fields: a block per 64-point block of Psi and group of 32
+// channels; each warp takes 8 points, each lane one channel: 8 loads of F (a
+// warp's loads are 128 contiguous bytes when ldF = c), then the 8 points' hi
+// and lo parts as one 16-byte store each into the channel's rows.  The first
+// channel group's block also zeroes the rows beyond the channels.
+__global__ void __launch_bounds__(256)
+fill_wide_batched_kernel(const FillJob* __restrict__ jobs, const int* __restrict__ prefix, int count,
+                         const CloudCall* __restrict__ calls) {
+  const int j = find_job(prefix, count, blockIdx.x);
+  const FillJob jb = jobs[j];
+  const CloudCall cc = calls[jb.cloud];
+  const int local = blockIdx.x - prefix[j];
+  const int pb = local % jb.bxw, cgi = local / jb.bxw;
+  const int c = cc.c, r0 = jb.row0, ra = jb.rows_alloc;
+  const int lane = threadIdx.x & 31;
+  const int64_t p0 = (int64_t)pb * 64 + (threadIdx.x >> 5) * 8;
+  auto* psi = reinterpret_cast<uint4*>(jb.psi);  // 8 points of row r: psi_index(p0, r, ra) / 8
+  const int ch = cgi * 32 + lane;
+  if (ch < c) {
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = (p0 + e < jb.n) ? cc.F[(p0 + e) * cc.ldF + ch] : 0.f;
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+      const float2 hf = __bfloat1622float2(h);
+      const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+      hi[e] = *reinterpret_cast<const uint32_t*>(&h);
+      lo[e] = *reinterpret_cast<const uint32_t*>(&l);
+    }
+    psi[psi_index(p0, r0 + ch, ra) / 8] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    // row c + ch: the lo part of channel ch (fsplit)
+    if (jb.fsplit) psi[psi_index(p0, r0 + c + ch, ra) / 8] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
+  if (cgi == 0)
+    for (int rr = (jb.fsplit ? 2 * c : c) + lane; rr < jb.cpad; rr += 32)
+      psi[psi_index(p0, r0 + rr, ra) / 8] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // One thread per tile element; lanes summed in order (deterministic),
@@ -226,6 +266,65 @@ __global__ void __launch_bounds__(256) small_batched_kernel(const ApplyJob* __re
       jb.Z[(size_t)f * c + ch0 + threadIdx.x] = (float)jb.oa[f] * tot.value();
     }
     __syncthreads();
+  }
+}
+
+// Z for wide fields (more than 16 channels): a block per 8 rows f and 64
+// channels; each thread one channel, all 8 rows (8 independent sums) and a
+// quarter of g.  G's rows pass through shared memory (as FP32) 512 columns at
+// a time, Y is read along the channels.  Each thread's terms are compensated
+// FP32 sums in g order, and the four quarters' (sum, compensation) pairs are
+// added in quarter order (Z is stored in FP32).  Blocks of channels >= c
+// return at once (the prefix counts the plan's max_channels).
+__global__ void __launch_bounds__(256) small_wide_batched_kernel(const ApplyJob* __restrict__ jobs,
+                                                                 const int* __restrict__ prefix, int count,
+                                                                 const CloudCall* __restrict__ calls) {
+  constexpr int kG = 512;
+  const int j = find_job(prefix, count, blockIdx.x);
+  const ApplyJob jb = jobs[j];
+  const int c = calls[jb.cloud].c, m = jb.m;
+  const int local = blockIdx.x - prefix[j];
+  const int nrb = (m + 7) / 8;
+  const int f0 = (local % nrb) * 8, ch0 = (local / nrb) * 64;
+  if (ch0 >= c) return;
+  const int cl = threadIdx.x & 63, qt = threadIdx.x >> 6, ch = ch0 + cl;
+  __shared__ float gs[8][kG];
+  __shared__ float red[4][8][64][2];
+  Fp32Sum a[8];
+  for (int g0 = 0; g0 < m; g0 += kG) {
+    const int gn = min(kG, m - g0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 8 * kG; i += 256) {
+      const int r = i / kG, gi = i % kG;
+      gs[r][gi] = (f0 + r < m && gi < gn) ? (float)jb.G[(size_t)(f0 + r) * m + g0 + gi] : 0.f;
+    }
+    __syncthreads();
+    const int qn = (gn + 3) / 4, gb = qt * qn, ge = min(gn, gb + qn);
+    if (ch < c)
+      for (int gi = gb; gi < ge; ++gi) {
+        const float y = (float)jb.Y[(size_t)(g0 + gi) * c + ch];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) a[r].add(gs[r][gi] * y);
+      }
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    red[qt][r][cl][0] = a[r].s;
+    red[qt][r][cl][1] = a[r].c;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int r = qt * 2 + k, f = f0 + r;
+    if (ch < c && f < m) {
+      Fp32Sum tot;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        tot.add(red[q][r][cl][0]);
+        tot.add(red[q][r][cl][1]);
+      }
+      jb.Z[(size_t)f * c + ch] = (float)jb.oa[f] * tot.value();
+    }
   }
 }
 
@@ -562,6 +661,13 @@ cudaError_t launch_fill_batched(const FillJob* jobs, const int* prefix, int coun
   return launched();
 }
 
+cudaError_t launch_fill_wide_batched(const FillJob* jobs, const int* prefix, int count, int total_blocks,
+                                     const CloudCall* calls, cudaStream_t st) {
+  if (total_blocks <= 0) return cudaSuccess;
+  fill_wide_batched_kernel<<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls);
+  return launched();
+}
+
 cudaError_t launch_reduce_batched(const RedTile* tiles, int num_tiles, const CloudCall* calls, cudaStream_t st) {
   if (num_tiles <= 0) return cudaSuccess;
   dim3 grid((unsigned)((kTcBM * kTcBNMax + 255) / 256), (unsigned)num_tiles);
@@ -573,6 +679,13 @@ cudaError_t launch_small_batched(const ApplyJob* jobs, const int* prefix, int co
                                  const CloudCall* calls, cudaStream_t st) {
   if (total_rows <= 0) return cudaSuccess;
   small_batched_kernel<<<total_rows, 256, 0, st>>>(jobs, prefix, count, calls);
+  return launched();
+}
+
+cudaError_t launch_small_wide_batched(const ApplyJob* jobs, const int* prefix, int count, int total_blocks,
+                                      const CloudCall* calls, cudaStream_t st) {
+  if (total_blocks <= 0) return cudaSuccess;
+  small_wide_batched_kernel<<<total_blocks, 256, 0, st>>>(jobs, prefix, count, calls);
   return launched();
 }
 

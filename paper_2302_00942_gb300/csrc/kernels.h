@@ -250,8 +250,9 @@ struct FeatJob {
 struct FillJob {
   int64_t n, n_pad;
   __nv_bfloat16_raw* psi;
-  int32_t cpad, bx, cloud, fsplit;  // bx: 256-point blocks
+  int32_t cpad, bx, cloud, fsplit;  // bx: 256-point blocks (fill_batched)
   int32_t row0, rows_alloc;         // F rows start at row0 (= m) of the blocked buffer
+  int32_t bxw, cgw;                 // fill_wide_batched: 64-point blocks x channel groups of 32
 };
 // Y' = Phi^T F from the points, for a compact plan (no feature matrix): per
 // chunk of `pts` points, part[chunk][f][ch] = sum_n Phi(n, f) F[n, ch] with
@@ -330,6 +331,9 @@ cudaError_t launch_features_range(const FeatJob* jobs, const CloudCall* calls, i
                                   cudaStream_t st);
 cudaError_t launch_fill_batched(const FillJob* jobs, const int* prefix, int count, int total_blocks,
                                 const CloudCall* calls, cudaStream_t st);
+// the same for calls whose largest c is above 8 (prefix over bxw * cgw blocks per cloud)
+cudaError_t launch_fill_wide_batched(const FillJob* jobs, const int* prefix, int count, int total_blocks,
+                                     const CloudCall* calls, cudaStream_t st);
 cudaError_t launch_reduce_batched(const RedTile* tiles, int num_tiles, const CloudCall* calls, cudaStream_t st);
 // Y' partials of compact plans from their points: cg channels per block (3, 4, 8, 16 or 32),
 // fieldpts_fpt(cg) frequencies per thread; prefix over chunks x ceil(h / (256 fpt)) x
@@ -350,12 +354,45 @@ inline int fieldpts_blocks(const FieldPtsJob& j, int c, int cg) {
 // Z = diag(oa) G Y per cloud (one block per matrix row: prefix over m)
 cudaError_t launch_small_batched(const ApplyJob* jobs, const int* prefix, int count, int total_rows,
                                  const CloudCall* calls, cudaStream_t st);
+// the same for calls whose largest c is above 16: blocks of 8 rows x 64 channels, prefix over
+// small_wide_blocks per cloud
+cudaError_t launch_small_wide_batched(const ApplyJob* jobs, const int* prefix, int count, int total_blocks,
+                                      const CloudCall* calls, cudaStream_t st);
+inline int small_wide_blocks(int m, int max_channels) { return (m + 7) / 8 * ((max_channels + 63) / 64); }
 // out = F + Phi Z per cloud; cg: channels per thread (3, 4, 8, 16 or 32); a block covers
 // kApplyPts points, two per thread; prefix over bx * ceil(c / cg) blocks per cloud
 // (bx = ceil(n / kApplyPts))
 constexpr int kApplyPts = 512;
 cudaError_t launch_apply_batched(const ApplyJob* jobs, const int* prefix, int count, int total_blocks, int cg,
                                  const CloudCall* calls, cudaStream_t st);
+// Step a6 on the tensor cores (k_apply_tc.cu), for 1 <= c <= kApplyTcMaxC channels:
+// per cloud, 2 pi w as float4 (zero past h) and Z split into BF16 hi / lo parts,
+// laid out per chunk of 64 features as the MMA's B operand (apply_prep, from
+// the FP32 Z of step a5); the apply then recomputes Phi per 256-point tile.
+struct ApplyTcJob {
+  const float* xyz;       // the plan's copy of the points (N x 3)
+  const float* omega_hi;  // h x 3
+  const float* Z;         // m x c FP32 (the call's c), step a5's output
+  float4* w2pi;           // 32 kchunks frequencies
+  uint8_t* zimg;          // kchunks x 2 cp rows x 128 B (cp = apply_tc_cpad(c))
+  int64_t n;
+  int32_t h, kchunks, cloud, tiles;  // kchunks = ceil(h / 32), tiles = ceil(n / 256)
+};
+constexpr int kApplyTcMaxC = 64;
+constexpr int kApplyTcMinC = 4;  // the batch takes this form when its largest c is above this
+__host__ __device__ constexpr int apply_tc_cpad(int c) { return (c + 15) / 16 * 16; }
+inline size_t apply_tc_zimg_bytes(int h, int max_c) {
+  const int c = max_c < kApplyTcMaxC ? max_c : kApplyTcMaxC;
+  return (size_t)((h + 31) / 32) * 2 * apply_tc_cpad(c) * 128;
+}
+inline int apply_prep_blocks(const ApplyTcJob& j, int c) { return (j.kchunks * 2 * apply_tc_cpad(c) * 8 + 255) / 256; }
+bool apply_tc_supported();
+cudaError_t apply_tc_prepare();
+cudaError_t launch_apply_prep(const ApplyTcJob* jobs, const int* prefix, int count, int total_blocks,
+                              const CloudCall* calls, cudaStream_t st);
+// grid: persistent CTAs (at most one per SM) over total_tiles = tile_prefix[count]
+cudaError_t launch_apply_tc(const ApplyTcJob* jobs, const int* tile_prefix, int count, int total_tiles, int grid,
+                            const CloudCall* calls, int* err, cudaStream_t st);
 // phi1 building blocks over all clouds (elements: prefix over ceil(m^2 / 256) blocks)
 // D = k (a0 X0 + a1 X1 + a2 X2 + a3 X3 + diag I), k = 1, lambda or scale (kmode 0/1/2);
 // clouds with s <= mask_k are skipped (mask_k < 0: none).

@@ -474,6 +474,12 @@ int tc_partial_slots(int m, int cpad, int64_t n_pad, int sms, int lanes_pct) {
   return slots;
 }
 
+// The tensor-core apply's job of a BF16 plan (k_apply_tc.cu)
+ApplyTcJob apply_tc_job(const rfd_plan_s* pl) {
+  return ApplyTcJob{pl->d_xyz, pl->d_omega_hi, pl->d_Z, pl->d_w2pi, pl->d_zimg, pl->n, pl->h, (pl->h + 31) / 32, 0,
+                    (int)((pl->n + 255) / 256)};
+}
+
 // Each compute tile t gets L_t lanes of the point axis (gram_tile_lanes), so a
 // lone cloud fills the GPU in one wave (lanes_pct 100).  The partial slots of
 // the logical 128-row halves follow each other: half s (of tile t) takes L_t
@@ -564,9 +570,10 @@ rfd_status build_desc(rfd_plan_s* pl) {
   d.feat = FeatJob{pl->n, pl->n_pad, pl->d_omega_hi, psi, pl->d_xyz, pl->h, (int)((pl->n_pad + 511) / 512), 0,
                    pl->rows_alloc};
   d.fill = FillJob{pl->n, pl->n_pad, psi, pl->cpad, (int)((pl->n_pad + 255) / 256), 0, pl->fsplit ? 1 : 0, m,
-                   pl->rows_alloc};
+                   pl->rows_alloc, (int)(pl->n_pad / 64), (pl->p.max_channels + 31) / 32};
   d.apply = ApplyJob{pl->d_xyz,  pl->d_omega_hi, pl->d_omega_lo, pl->d_G, pl->d_Y, pl->d_oa, pl->d_Z,
                      pl->n,      pl->n_pad,      m, 0, (int)((pl->n + kApplyPts - 1) / kApplyPts), 0};
+  d.apply_tc = apply_tc_job(pl);
   // step a4 on the emulated path: slots in the FP64 workspace, the residue buffers after them
   PhiCloud& pc = d.phi;
   pc = PhiCloud{};
@@ -937,6 +944,10 @@ void plan_carve(rfd_plan_s* pl, PlanCarve& c) {
   c.add(&pl->d_Y, (size_t)m * pl->p.max_channels);
   c.add(&pl->d_G, (size_t)m * m);
   c.add(&pl->d_Z, (size_t)m * pl->p.max_channels);
+  if (pl->bf16) {
+    c.add(&pl->d_w2pi, (size_t)32 * ((pl->h + 31) / 32));
+    c.bytes(reinterpret_cast<void**>(&pl->d_zimg), apply_tc_zimg_bytes(pl->h, pl->p.max_channels));
+  }
   c.add(&pl->d_work, phi1_workspace_doubles(m));
   c.add(&pl->d_ipiv, (size_t)m);
   c.add(&pl->d_ints, 4);
@@ -978,6 +989,8 @@ void plan_carve_compact(rfd_plan_s* pl, PlanCarve& c) {
   c.add(&pl->d_Y, (size_t)m * pl->p.max_channels);
   c.add(&pl->d_G, (size_t)m * m);
   c.add(&pl->d_Z, (size_t)m * pl->p.max_channels);
+  c.add(&pl->d_w2pi, (size_t)32 * ((pl->h + 31) / 32));
+  c.bytes(reinterpret_cast<void**>(&pl->d_zimg), apply_tc_zimg_bytes(pl->h, pl->p.max_channels));
   c.add(&pl->d_ints, 4);
   c.add(&pl->d_scalar, 2);
   c.add(&pl->d_fpart, (size_t)chunks * m * ld);
@@ -1000,6 +1013,7 @@ void build_compact_desc(rfd_plan_s* pl) {
                        pl->d_Y,   pl->d_ob};
   d.apply = ApplyJob{pl->d_xyz, pl->d_omega_hi, pl->d_omega_lo, pl->d_G, pl->d_Y, pl->d_oa, pl->d_Z,
                      pl->n,     pl->n_pad,      pl->m, 0, (int)((pl->n + kApplyPts - 1) / kApplyPts), 0};
+  d.apply_tc = apply_tc_job(pl);
 }
 
 }  // namespace
@@ -1597,6 +1611,14 @@ rfd_status rfd_debug_plan_set_overlap(rfd_plan_t pl, int32_t enable) {
     return fail(RFD_EINVAL, "features beside the Gram need several phases of a multiple of 8 blocks");
   }
   pl->tune.overlap = enable ? 1 : 0;
+  return RFD_OK;
+}
+
+rfd_status rfd_debug_plan_set_apply_tc(rfd_plan_t pl, int32_t enable) {
+  if (!pl) return fail(RFD_EINVAL, "null plan");
+  if (!pl->bf16 || !pl->self) return fail(RFD_EINVAL, "the tensor-core apply belongs to the BF16 form");
+  if (pl->p.flags & RFD_FLAG_GRAPH) return fail(RFD_EINVAL, "not for plans with RFD_FLAG_GRAPH");
+  if (!batch_set_apply_tc(pl->self, enable != 0) && enable) return fail(RFD_ENOTSUP, "the tensor-core apply needs sm_103");
   return RFD_OK;
 }
 

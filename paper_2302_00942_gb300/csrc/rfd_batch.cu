@@ -86,10 +86,23 @@ struct BatchImpl {
   FillJob* d_fill = nullptr;
   int* d_fill_prefix = nullptr;
   int fill_blocks = 0;
+  int* d_fillw_prefix = nullptr;  // the wide form (fields of more than 8 channels)
+  int fillw_blocks = 0;
   ApplyJob* d_apply = nullptr;
   std::vector<int> apply_bx;
+  // the tensor-core apply (k_apply_tc.cu): jobs, their 256-point tiles, and whether every
+  // plan has its buffers (apply_tc_ok) and the form is not switched off (apply_tc_on)
+  ApplyTcJob* d_apply_tc = nullptr;
+  std::vector<ApplyTcJob> apply_tc_h;
+  int* d_tile_prefix = nullptr;
+  int apply_tiles = 0;
+  int max_channels = 0;  // the smallest max_channels of the plans (their Z images' capacity)
+  bool apply_tc_ok = false, apply_tc_on = true;
+  int sms = 0;
   int* d_small_prefix = nullptr;
   int small_rows = 0;
+  int* d_wide_prefix = nullptr;  // step a5 for wide fields (small_wide_blocks per cloud)
+  int wide_blocks = 0;
   PhiCloud* d_phi = nullptr;
   int* d_elem_prefix = nullptr;
   int elem_blocks = 0;
@@ -111,7 +124,7 @@ struct BatchImpl {
   unsigned long long* prof = nullptr;  // the autotuner's per-CTA times of the Gram launches (or null)
   bool phi_batched = true;  // all clouds on the emulated path (no native-FP64 flag)
   // per-call device words
-  CloudCall* d_calls = nullptr;  // followed by three block prefixes (count + 1 ints each)
+  CloudCall* d_calls = nullptr;  // followed by four block prefixes (count + 1 ints each)
   double* d_norms = nullptr;
   int* d_sv = nullptr;     // squarings per cloud, then their maximum
   int* d_flags = nullptr;  // sticky: G of cloud k not finite
@@ -201,6 +214,10 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
     }
   std::vector<FillJob> fill;
   std::vector<ApplyJob> apply;
+  std::vector<int> tiles_n, wide_n, fillw_n;
+  b->apply_tc_ok = apply_tc_supported();
+  b->max_channels = plans[0]->p.max_channels;
+  b->sms = sms;
   std::vector<PhiCloud> phi;
   std::vector<int> feat_n, fill_n, small_n, elem_n, grp_n, rowa_n, rexp_n, strip_n;
   std::vector<OzTile> oz;
@@ -273,11 +290,19 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
     fl.cloud = k;
     fill.push_back(fl);
     fill_n.push_back(fl.bx);
+    fillw_n.push_back(fl.bxw * fl.cgw);
     ApplyJob aj = d.apply;
     aj.cloud = k;
     apply.push_back(aj);
     b->apply_bx.push_back(aj.bx);
+    ApplyTcJob tj = d.apply_tc;
+    tj.cloud = k;
+    b->apply_tc_h.push_back(tj);
+    tiles_n.push_back(tj.tiles);
+    b->apply_tc_ok = b->apply_tc_ok && tj.zimg != nullptr && tj.w2pi != nullptr;
+    b->max_channels = std::min(b->max_channels, pl->p.max_channels);
     small_n.push_back(pl->m);
+    wide_n.push_back(small_wide_blocks(pl->m, pl->p.max_channels));
     PhiCloud pc = d.phi;
     pc.map_a += k * kMapsPerCloud;
     pc.map_b += k * kMapsPerCloud;
@@ -290,6 +315,10 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
     rexp_n.push_back(ozaki_row_exponent_blocks(pl->m));
     strip_n.push_back(ozaki_col_split_blocks(pl->m));
   }
+  const std::vector<int> pre_tiles = prefix_of(tiles_n), pre_wide = prefix_of(wide_n), pre_fillw = prefix_of(fillw_n);
+  b->fillw_blocks = pre_fillw.back();
+  b->apply_tiles = pre_tiles.back();
+  b->wide_blocks = pre_wide.back();
   const std::vector<int> pre_feat = prefix_of(feat_n), pre_fill = prefix_of(fill_n), pre_small = prefix_of(small_n),
                          pre_elem = prefix_of(elem_n), pre_grp = prefix_of(grp_n), pre_rexp = prefix_of(rexp_n), pre_rowa = prefix_of(rowa_n), pre_strip = prefix_of(strip_n);
   b->feat_blocks = pre_feat.back();
@@ -332,11 +361,13 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   const size_t o_feat = vtable(feat), o_feat_pre = vtable(pre_feat), o_fill = vtable(fill),
                o_fill_pre = vtable(pre_fill), o_apply = vtable(apply), o_small_pre = vtable(pre_small),
                o_phi = vtable(phi), o_elem_pre = vtable(pre_elem), o_grp_pre = vtable(pre_grp), o_rexp_pre = vtable(pre_rexp), o_rowa_pre = vtable(pre_rowa),
-               o_strip_pre = vtable(pre_strip), o_oz = vtable(oz), o_fpts = vtable(fpts);
+               o_strip_pre = vtable(pre_strip), o_oz = vtable(oz), o_fpts = vtable(fpts),
+               o_apply_tc = vtable(b->apply_tc_h), o_tile_pre = vtable(pre_tiles), o_wide_pre = vtable(pre_wide),
+               o_fillw_pre = vtable(pre_fillw);
   const size_t table_bytes = L.total;
-  // per call: the CloudCalls, then the block prefixes of the apply, the points-based Phi^T F
-  // and its sum over the chunks
-  b->stage_bytes = (size_t)count * sizeof(CloudCall) + 3 * (size_t)(count + 1) * sizeof(int);
+  // per call: the CloudCalls, then the block prefixes of the apply, the points-based Phi^T F,
+  // its sum over the chunks and the tensor-core apply's Z images
+  b->stage_bytes = (size_t)count * sizeof(CloudCall) + 4 * (size_t)(count + 1) * sizeof(int);
   const size_t o_calls = L.add(b->stage_bytes);
   const size_t o_norms = L.add((size_t)count * sizeof(double));
   const size_t o_sv = L.add((size_t)(count + 1) * sizeof(int));
@@ -367,6 +398,10 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   b->d_fill = reinterpret_cast<FillJob*>(D + o_fill);
   b->d_fill_prefix = reinterpret_cast<int*>(D + o_fill_pre);
   b->d_apply = reinterpret_cast<ApplyJob*>(D + o_apply);
+  b->d_apply_tc = reinterpret_cast<ApplyTcJob*>(D + o_apply_tc);
+  b->d_tile_prefix = reinterpret_cast<int*>(D + o_tile_pre);
+  b->d_wide_prefix = reinterpret_cast<int*>(D + o_wide_pre);
+  b->d_fillw_prefix = reinterpret_cast<int*>(D + o_fillw_pre);
   b->d_small_prefix = reinterpret_cast<int*>(D + o_small_pre);
   b->d_phi = reinterpret_cast<PhiCloud*>(D + o_phi);
   b->d_elem_prefix = reinterpret_cast<int*>(D + o_elem_pre);
@@ -400,6 +435,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   if (e == cudaSuccess) e = gram_tc_prepare();
   if (e == cudaSuccess && b->n_pair[0] + b->n_pair[1] + b->n_pair[2] > 0) e = gram_pair_prepare();
   if (e == cudaSuccess) e = bgemm_prepare();
+  if (e == cudaSuccess && b->apply_tc_ok) e = apply_tc_prepare();
   if (e != cudaSuccess) {
     cudaGetLastError();
     return bail(RFD_ECUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
@@ -686,6 +722,10 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   int max_c = 1;
   for (int k = 0; k < n; ++k) max_c = std::max(max_c, calls[k].c);
   const int cg = max_c <= 3 ? 3 : (max_c <= 4 ? 4 : (max_c <= 8 ? 8 : (max_c <= 16 ? 16 : 32)));
+  // the apply on the tensor cores from 5 channels on (the SIMT kernel's FMAs grow with c, the
+  // tensor-core form's per-point work hardly), up to the Z images' capacity
+  const bool use_tc = mode != kModeFeatures && b->apply_tc_ok && b->apply_tc_on && max_c > kApplyTcMinC &&
+                      max_c <= std::min(kApplyTcMaxC, b->max_channels);
   // a pinned staging buffer whose previous upload has been consumed
   const int slot = b->stage_next;
   b->stage_next = (slot + 1) % BatchImpl::kStageRing;
@@ -696,7 +736,7 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   hp[0] = 0;
   for (int k = 0; k < n; ++k) {
     hc[k] = calls[k];
-    const int nb = (mode == kModeFeatures) ? 0 : b->apply_bx[k] * ((calls[k].c + cg - 1) / cg);
+    const int nb = (mode == kModeFeatures || use_tc) ? 0 : b->apply_bx[k] * ((calls[k].c + cg - 1) / cg);
     hp[k + 1] = hp[k] + nb;
   }
   const int apply_blocks = hp[n];
@@ -717,6 +757,11 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   for (int k = 0; k < n; ++k) hr[k + 1] = hr[k] + (pts ? fieldpts_reduce_blocks(b->fpts_h[k], calls[k].c) : 0);
   const int fred_blocks = hr[n];
   const int* d_fred_prefix = d_fpts_prefix + (n + 1);
+  int* hz = hr + (n + 1);  // and of the tensor-core apply's Z images
+  hz[0] = 0;
+  for (int k = 0; k < n; ++k) hz[k + 1] = hz[k] + (use_tc ? apply_prep_blocks(b->apply_tc_h[k], calls[k].c) : 0);
+  const int prep_blocks = hz[n];
+  const int* d_prep_prefix = d_fred_prefix + (n + 1);
   if (b->compact && mode != kModeIntegrate)
     return fail(RFD_EINVAL, "a compact plan has no feature matrix: only integration runs on it");
   BCK(cudaMemcpyAsync(b->d_calls, stage, b->stage_bytes, cudaMemcpyHostToDevice, st));
@@ -726,6 +771,12 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   const bool graph = (b->options & kBatchGraphs) && (!with_phi || b->phi_batched);
 
   const bool pipelined = with_feat && pipelines(b);
+  // F's rows of Psi: one point per thread up to 8 channels, else 8 points x 32 channels per warp
+  const bool wide_fill = max_c > 8;
+  auto fill = [&](cudaStream_t s) -> cudaError_t {
+    return wide_fill ? launch_fill_wide_batched(b->d_fill, b->d_fillw_prefix, n, b->fillw_blocks, b->d_calls, s)
+                     : launch_fill_batched(b->d_fill, b->d_fill_prefix, n, b->fill_blocks, b->d_calls, s);
+  };
   auto reductions = [&](cudaStream_t s, Timing* t) -> rfd_status {
     if (pts) {  // Phi^T F from the points, summed over the chunks by the reduce kernel
       {
@@ -740,7 +791,7 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
       if (rfd_status q = pipelined_features(b, s, t); q != RFD_OK) return q;
       if (with_apply) {
         StepScope sc(t, s, RFD_STEP_FIELD);
-        BCK(launch_fill_batched(b->d_fill, b->d_fill_prefix, n, b->fill_blocks, b->d_calls, s));
+        BCK(fill(s));
       }
       if (rfd_status q = pipelined_gram(b, mode, s, t); q != RFD_OK) return q;
       StepScope sc(t, s, RFD_STEP_REDUCE);
@@ -753,7 +804,7 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
     }
     if (with_apply) {
       StepScope sc(t, s, RFD_STEP_FIELD);
-      BCK(launch_fill_batched(b->d_fill, b->d_fill_prefix, n, b->fill_blocks, b->d_calls, s));
+      BCK(fill(s));
     }
     {
       StepScope sc(t, s, RFD_STEP_GRAM);
@@ -766,12 +817,31 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   auto small_apply = [&](cudaStream_t s, Timing* t) -> rfd_status {
     {
       StepScope sc(t, s, RFD_STEP_SMALL);
-      BCK(launch_small_batched(b->d_apply, b->d_small_prefix, n, b->small_rows, b->d_calls, s));
+      if (max_c > 16)
+        BCK(launch_small_wide_batched(b->d_apply, b->d_wide_prefix, n, b->wide_blocks, b->d_calls, s));
+      else
+        BCK(launch_small_batched(b->d_apply, b->d_small_prefix, n, b->small_rows, b->d_calls, s));
+    }
+    if (use_tc) {
+      {
+        StepScope sc(t, s, RFD_STEP_SMALL);
+        BCK(launch_apply_prep(b->d_apply_tc, d_prep_prefix, n, prep_blocks, b->d_calls, s));
+      }
+      StepScope sc(t, s, RFD_STEP_APPLY);
+      BCK(launch_apply_tc(b->d_apply_tc, b->d_tile_prefix, n, b->apply_tiles, std::min(b->apply_tiles, b->sms),
+                          b->d_calls, b->d_err, s));
+      return RFD_OK;
     }
     StepScope sc(t, s, RFD_STEP_APPLY);
     BCK(launch_apply_batched(b->d_apply, d_apply_prefix, n, apply_blocks, cg, b->d_calls, s));
     return RFD_OK;
   };
+  // the apply's part of the graph keys: the SIMT kernel's channel group and grid, or the
+  // tensor-core form's Z-image grid (its own grid is fixed per batch)
+  // (a tensor-core apply: 100, + 1 with the wide fill, + 2 with the wide form of step a5;
+  // the SIMT apply's channel group implies both: 16 and 32 above 8 channels, 32 above 16)
+  const int akey_cg = use_tc ? 100 + (wide_fill ? 1 : 0) + (max_c > 16 ? 2 : 0) : cg;
+  const int akey_blocks = use_tc ? -1 - prep_blocks : apply_blocks;
 
   if (gram_only) {  // steps a2-a3: M only, and G no longer matches the points
     for (rfd_plan_s* pl : b->plans) pl->have_G = false;
@@ -780,7 +850,7 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   }
   if (!with_phi) {
     // the points-based path: both of its launches' grids (they depend on every call's c)
-    const int key[4] = {mode, pts ? -4 - fpts_blocks : -1, pts ? cg + 64 * fred_blocks : cg, apply_blocks};
+    const int key[4] = {mode, pts ? -4 - fpts_blocks : -1, pts ? akey_cg + 64 * fred_blocks : akey_cg, akey_blocks};
     return run_segment(b, key, graph, tm, [&](cudaStream_t s, Timing* t) -> rfd_status {
       rfd_status r = reductions(s, t);
       return r == RFD_OK ? small_apply(s, t) : r;
@@ -799,7 +869,7 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
     return with_apply ? small_apply(st, tm) : RFD_OK;
   }
   // reductions, then the first part of a4; the host learns the largest s_c
-  const int key_pre[4] = {mode, -2, 0, 0};
+  const int key_pre[4] = {mode, -2, with_apply && wide_fill ? 1 : 0, 0};
   rfd_status r = run_segment(b, key_pre, graph, tm, [&](cudaStream_t s, Timing* t) -> rfd_status {
     rfd_status q = reductions(s, t);
     if (q != RFD_OK) return q;
@@ -822,7 +892,7 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   int hn[4];
   product_moduli(b, hn);
   const int key_post[4] = {mode, max_s + 64 * ((hn[0] - 1) | (hn[1] - 1) << 4 | (hn[2] - 1) << 8 | (hn[3] - 1) << 12),
-                           with_apply ? cg : 0, with_apply ? apply_blocks : 0};
+                           with_apply ? akey_cg : 0, with_apply ? akey_blocks : 0};
   r = run_segment(b, key_post, graph, tm, [&](cudaStream_t s, Timing* t) -> rfd_status {
     {
       StepScope sc(t, s, RFD_STEP_PHI1);
@@ -973,6 +1043,11 @@ rfd_status batch_time_gram(BatchImpl* b, int mode, int reps, float* ms, const Cl
 }
 
 int* batch_error_word(BatchImpl* b) { return b->d_err; }
+
+bool batch_set_apply_tc(BatchImpl* b, bool on) {
+  b->apply_tc_on = on;
+  return b->apply_tc_ok;
+}
 
 rfd_status batch_check_error(BatchImpl* b, int* bad) {
   const int n = b->count;

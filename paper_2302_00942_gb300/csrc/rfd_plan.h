@@ -87,6 +87,7 @@ struct PlanDesc {
   FeatJob feat{};
   FillJob fill{};
   ApplyJob apply{};
+  ApplyTcJob apply_tc{};  // the tensor-core apply (w2pi / zimg null: the plan has none)
   PhiCloud phi{};
   unsigned char maps[kMapsPerCloud][kTensorMapBytes];
 };
@@ -145,6 +146,8 @@ struct rfd_plan_s {
   double* d_Y = nullptr;
   double* d_G = nullptr;
   float* d_Z = nullptr;
+  float4* d_w2pi = nullptr;    // BF16 form: the tensor-core apply's 2 pi w and Z images
+  uint8_t* d_zimg = nullptr;
   double* d_work = nullptr;
   int* d_ipiv = nullptr;
   int* d_ints = nullptr;  // [0] error word, [1] LU info, [2] finite flag
@@ -211,6 +214,9 @@ rfd_status batch_eigenvalues(rfd_plan_s* const* plans, int count, int k, int lar
 // RFD_ENUMERIC if some cloud's G is not finite (bad[k] = 1 for those clouds when
 // bad is given).
 rfd_status batch_check_error(BatchImpl* b, int* bad = nullptr);
+// The apply (step a6) on the tensor cores where every call's c allows (1: the default)
+// or always on the SIMT kernel (0); returns whether the batch has the tensor-core form.
+bool batch_set_apply_tc(BatchImpl* b, bool on);
 // Times the Gram launches of one batched call of `mode`, with the features in
 // front of them (serially or beside them, as the batch is set) in modes that
 // compute features, from the points of calls (one CloudCall per plan): mean ms

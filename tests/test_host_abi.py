@@ -114,6 +114,7 @@ def test_null_handles_rejected_by_the_next_rows():
         "rfd_debug_plan_phi1": lambda: rfd.lib.rfd_debug_plan_phi1(None, None),
         "rfd_debug_plan_set_phase": lambda: rfd.lib.rfd_debug_plan_set_phase(None, 64),
         "rfd_debug_plan_set_overlap": lambda: rfd.lib.rfd_debug_plan_set_overlap(None, 1),
+        "rfd_debug_plan_set_apply_tc": lambda: rfd.lib.rfd_debug_plan_set_apply_tc(None, 1),
         "rfd_debug_plan_wait_timeout": lambda: rfd.lib.rfd_debug_plan_wait_timeout(None, 1000),
     }
     for name, call in calls.items():
