@@ -1,34 +1,46 @@
 // Step a6, out = F + Phi Z (Sec. 2.4: the apply A (G (B^T F)) of the low-rank
 // factors, "linear in N"), on the 5th-generation tensor cores for fields of
-// 5..64 channels.  Phi is not read back from the BF16 feature matrix: producer
-// warps recompute each point's features in FP32 (the SIMT apply's phase and
-// MUFU sin/cos, bit for bit), split each value v into BF16 hi = bf16(v) and
-// lo = bf16(v - hi), and write both into shared memory in the MMA's operand
-// layout; Z is split the same way.  Per 16 features one MMA forms
-//   D[:, 0:2cp]  += Phi_hi [Z_hi | Z_lo]      (N = 2 cp)
-// and a second adds Phi_lo Z_hi into the Z_lo columns D[:, cp:2cp], so that
-// D[:, ch] + D[:, cp + ch] = (Phi Z)[:, ch] up to the dropped Phi_lo Z_lo and
-// the 16-bit splits: a relative error of about 2^-16 per term, against 2^-8 for
-// one BF16 product.  The FP32 accumulators stay in TMEM for all of K.
+// up to 64 channels.  Phi is not read back from the BF16 feature matrix:
+// producer warps recompute each point's features in FP32 (the SIMT apply's
+// phase and MUFU sin/cos, bit for bit) and split each value v into BF16
+// hi = bf16(v) and lo = bf16(v - hi); Z is split the same way (apply_prep).
+// The MMAs form the transpose, D = Z^T Phi^T: M = 128 rows of Z's image, N =
+// the 256 points of a tile, so that one MMA per 16 features and product
+// covers the whole tile (each MMA costs ~100 cycles to issue, and one of
+// N = 256 keeps the tensor pipe busy for about as long).  In shared memory
+// Z's image of a chunk is cp rows of Z_hi^T then cp rows of Z_lo^T (cp =
+// channels rounded up to 16), right after cp rows of zeros; two 128-row
+// windows of it are the A operands:
+//   rows [2cp - 128, 2cp) of the image:  D += [.. | Z_hi | Z_lo]^T Phi_hi
+//   rows [cp - 128, cp) of the image:    D += [.. | 0    | Z_hi]^T Phi_lo
+// so that TMEM lane 128 - cp + ch accumulates Z_lo Phi_hi + Z_hi Phi_lo and
+// lane 128 - 2cp + ch accumulates Z_hi Phi_hi for channel ch, and their sum is
+// (Phi Z)[:, ch] up to the dropped Phi_lo Z_lo and the 16-bit splits: a
+// relative error of about 2^-16 per term, against 2^-8 for one BF16 product.
+// (The lanes below 128 - 2cp read whatever lies before the zeros and are never
+// used.)  The FP32 accumulators stay in TMEM for all of K.
 //
-// A tile is 256 points (two M = 128 halves); K runs over chunks of 64
-// features, the cos then the sin of 32 frequencies (Z's rows are permuted to
-// match by apply_prep).  Two producer threads share a point, one for each half
-// of the chunk's frequencies, and each writes four 16-byte pieces of the
-// point's 128-byte row in each operand.  The CTAs are persistent, one per SM,
-// walking the tiles of all clouds of the batch.
+// A tile is 256 points; K runs over chunks of 64 features, the cos then the
+// sin of 32 frequencies (Z's rows are permuted to match by apply_prep).  A
+// producer thread takes two points (rows r and r + 128 of the tile) and a
+// quarter of the chunk's frequencies, so each broadcast load of w serves two
+// points, and writes two 16-byte pieces of each point's 128-byte row of
+// Phi_hi and of Phi_lo (the shared-memory port, not the arithmetic, sets this
+// kernel's pace: Phi's stores and the MMAs' operand reads share it).  The CTAs are persistent, one per SM, walking
+// the tiles of all clouds of the batch.
 //
-// Warp roles: warps 0..15 produce the A operand, warp 16 allocates TMEM and
-// issues the MMAs (one lane), warp 17 copies each chunk's Z image and its 32
-// frequencies 2 pi w into shared memory with the bulk copy engine (one lane;
-// the producers read w there, a broadcast, instead of through the L1 cache
-// that the epilogue's stream of F evicts), warps 18..21 drain the
-// accumulators (TMEM lane quarter warp % 4) and write out = F + D.  Two A
-// stages, four B stages and two accumulator buffers (2 x 256 TMEM columns)
-// let the epilogue of one tile run beside the MMAs of the next.  Every
-// mbarrier wait is bounded by a %globaltimer limit; a wait that runs out
-// records a code in *err and the role stops, waiting (again bounded) for its
-// own copies and MMAs before the CTA frees its TMEM and exits.
+// Warp roles: warps 0..15 produce Phi, warp 16 allocates TMEM and issues the
+// MMAs (one lane), warp 17 copies each chunk's Z image and its 32 frequencies
+// 2 pi w into shared memory with the bulk copy engine (one lane; the
+// producers read w there, a broadcast), warps 18..21 drain the accumulators:
+// 32 points at a time, each warp moves its TMEM lane quarter to shared memory,
+// and the four warps then write out = F + D_x + D_y with lanes along the
+// channels (coalesced rows of out).  Two Phi stages, three Z stages and two
+// accumulator buffers (2 x 256 TMEM columns) let the epilogue of one tile run
+// beside the MMAs of the next.  Every mbarrier wait is bounded by a
+// %globaltimer limit; a wait that runs out records a code in *err and the
+// role stops, waiting (again bounded) for its own copies and MMAs before the
+// CTA frees its TMEM and exits.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -41,16 +53,25 @@ namespace {
 
 using namespace tc;
 
-constexpr int kAtHalf = 128 * 128;            // one M = 128 half of one split: 128 rows x 128 B
-constexpr int kAtAStage = 4 * kAtHalf;        // hi (half 0, half 1), then lo (half 0, half 1)
-constexpr int kAtZBytes = 128 * 128;          // the Z image: 2 cp <= 128 rows of 128 B
-constexpr int kAtBStage = kAtZBytes + 1024;   // then the chunk's 32 frequencies 2 pi w (512 B)
-constexpr int kAtAStages = 2, kAtBStages = 4;
-constexpr int kAtProducers = 512;             // two per point: frequencies 0..15 / 16..31 of each chunk
-constexpr int kMmaWarp = kAtProducers / 32, kLoadWarp = kMmaWarp + 1;
+constexpr int kAtPhi = 256 * 128;             // one split of Phi: 256 point rows x 128 B
+constexpr int kAtAStage = 2 * kAtPhi;         // Phi_hi, then Phi_lo
+constexpr int kAtAStages = 2;
+constexpr int kAtZeros = 64 * 128;            // zero rows before each Z image (cp <= 64 of them are read)
+constexpr int kAtZData = 128 * 128;           // the Z image: 2 cp <= 128 rows of 128 B
+constexpr int kAtBStage = kAtZeros + kAtZData;
+constexpr int kAtBStages = 3;
+constexpr int kAtEPitch = 33;                 // epilogue exchange: 128 lanes x 32 points, padded
+constexpr int kAtProducers = 512;             // two points x 8 of each chunk's 32 frequencies per thread
+constexpr int kMmaWarp = kAtProducers / 32, kLoadWarp = kMmaWarp + 1, kEpiWarp0 = kLoadWarp + 1;
 constexpr int kAtThreads = kAtProducers + 32 + 32 + 128;
-constexpr uint32_t kAtTmemCols = 512;  // buffer b at columns [256 b, 256 b + 256): half h at + 128 h
-constexpr int kAtSmem = 1024 + kAtAStages * kAtAStage + kAtBStages * kAtBStage + 256;
+constexpr uint32_t kAtTmemCols = 512;  // accumulator buffer b at columns [256 b, 256 b + 256)
+// layout after the 1024-aligned base: Phi stages, Z stages (zeros then image), the chunks' 2 pi w,
+// the epilogue exchange, the barriers
+constexpr int kAtOffB = kAtAStages * kAtAStage;
+constexpr int kAtOffW = kAtOffB + kAtBStages * kAtBStage;
+constexpr int kAtOffE = kAtOffW + kAtBStages * 512;
+constexpr int kAtOffBar = kAtOffE + 128 * kAtEPitch * 4;
+constexpr int kAtSmem = 1024 + kAtOffBar + 256;
 
 struct AtSmem {
   uint64_t afull[kAtAStages], aempty[kAtAStages];
@@ -81,6 +102,32 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
+// the four epilogue warps: barrier 1, and the AND of a predicate over them (so that they
+// leave the tile loop together and never strand one another at the barrier)
+__device__ __forceinline__ float4 ld_shared_f4(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ bool epi_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred p, 1, 128, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane (warp-collective)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
 // (a, b) -> BF16 pairs hi = (bf16(a), bf16(b)) and lo = (bf16(a - hi.x), bf16(b - hi.y)),
 // the first value in the low half (the lower address)
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
@@ -90,14 +137,6 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
   hi = *reinterpret_cast<const uint32_t*>(&h);
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
-// 16 consecutive FP32 columns of this thread's TMEM lane, without waiting
-__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
 
 __global__ void __launch_bounds__(kAtThreads, 1)
 apply_tc_kernel(const ApplyTcJob* __restrict__ jobs, const int* __restrict__ prefix, int count, int total_tiles,
@@ -105,9 +144,10 @@ apply_tc_kernel(const ApplyTcJob* __restrict__ jobs, const int* __restrict__ pre
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
   const uint32_t base = (raw_addr + 1023u) & ~1023u;
-  const uint32_t sA = base, sB = base + kAtAStages * kAtAStage;
-  AtSmem* sm = reinterpret_cast<AtSmem*>(smem_raw + (base - raw_addr) + kAtAStages * kAtAStage +
-                                         kAtBStages * kAtBStage);
+  uint8_t* gbase = smem_raw + (base - raw_addr);
+  const uint32_t sA = base, sB = base + kAtOffB;
+  AtSmem* sm = reinterpret_cast<AtSmem*>(gbase + kAtOffBar);
+  float* E = reinterpret_cast<float*>(gbase + kAtOffE);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kAtAStages; ++s) {
@@ -125,6 +165,12 @@ apply_tc_kernel(const ApplyTcJob* __restrict__ jobs, const int* __restrict__ pre
     mbar_init(smem_u32(&sm->done), 1);
     fence_mbar_init();
   }
+  // the zero rows before each Z image (never written again)
+  for (int i = threadIdx.x; i < kAtBStages * (kAtZeros / 16); i += kAtThreads) {
+    const int s = i / (kAtZeros / 16), q = i % (kAtZeros / 16);
+    st_shared_v4(sB + s * kAtBStage + q * 16, 0u, 0u, 0u, 0u);
+  }
+  fence_proxy_async();  // before the MMAs read them
   if (warp == kMmaWarp) tmem_alloc(smem_u32(&sm->tmem_base), kAtTmemCols);
   fence_before();
   __syncthreads();
@@ -132,47 +178,55 @@ apply_tc_kernel(const ApplyTcJob* __restrict__ jobs, const int* __restrict__ pre
   const uint32_t tmem = sm->tmem_base;
 
   if (warp < kMmaWarp) {
-    // ---------------- A producers: two threads per point ----------------
-    const int pt = threadIdx.x & 255, fh = threadIdx.x >> 8;  // point of the tile, half of the chunk's frequencies
-    const int half = pt >> 7, r = pt & 127, r7 = r & 7;
+    // ---------------- Phi producers: two points and 8 frequencies per thread ----------------
+    const int pr = threadIdx.x & 127, fq = threadIdx.x >> 7;  // points pr and pr + 128; frequencies 8 fq .. + 7
+    const int r7 = pr & 7;                                     // (pr + 128) mod 8 as well
+    const uint32_t oc = (uint32_t)((fq ^ r7) << 4), os = (uint32_t)(((4 + fq) ^ r7) << 4);
     int it = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
       const int j = find_job_at(prefix, count, t);
-      const int64_t p = (int64_t)(t - prefix[j]) * 256 + pt;
+      const int64_t pa = (int64_t)(t - prefix[j]) * 256 + pr, pb = pa + 128;
       const int64_t n = jobs[j].n;
       const float* __restrict__ xyz = jobs[j].xyz;
       const int kchunks = jobs[j].kchunks;
-      const float x0 = p < n ? xyz[p * 3] : 0.f, x1 = p < n ? xyz[p * 3 + 1] : 0.f, x2 = p < n ? xyz[p * 3 + 2] : 0.f;
+      float xa[3], xb[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        xa[d] = pa < n ? xyz[pa * 3 + d] : 0.f;
+        xb[d] = pb < n ? xyz[pb * 3 + d] : 0.f;
+      }
       for (int kc = 0; kc < kchunks; ++kc, ++it) {
-        const int s = it & 1, u = it >> 1, bs = it & 3;
+        const int s = it & 1, u = it >> 1, bs = it % kAtBStages;
         if ((u > 0 && !mbar_wait(smem_u32(&sm->aempty[s]), (uint32_t)(u - 1) & 1u, err, 21)) ||
-            !mbar_wait(smem_u32(&sm->bfull[bs]), (uint32_t)(it >> 2) & 1u, err, 29)) {
+            !mbar_wait(smem_u32(&sm->bfull[bs]), (uint32_t)(it / kAtBStages) & 1u, err, 29)) {
           ok = false;
           break;
         }
-        const uint32_t rowhi = sA + s * kAtAStage + half * kAtHalf + r * 128;
-        const uint32_t rowlo = rowhi + 2 * kAtHalf;
-        // the chunk's 2 pi w, copied in beside its Z image
-        const float4* wk = reinterpret_cast<const float4*>(smem_raw + (sB - raw_addr) + bs * kAtBStage + kAtZBytes);
+        // the chunk's 2 pi w, copied in beside its Z image: one broadcast 16-byte load per frequency
+        const uint32_t wk = base + kAtOffW + bs * 512 + fq * 8 * 16;
+        uint32_t cha[4], cla[4], sha[4], sla[4], chb[4], clb[4], shb[4], slb[4];
 #pragma unroll
-        for (int gg = 0; gg < 2; ++gg) {  // frequencies 8 g .. 8 g + 7: pieces g (cos) and 4 + g (sin)
-          const int g = 2 * fh + gg;
-          uint32_t ch[4], cl[4], sh[4], sl[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float4 wa = wk[8 * g + 2 * e], wb = wk[8 * g + 2 * e + 1];
-            const float ta = fmaf(wa.x, x0, fmaf(wa.y, x1, wa.z * x2));
-            const float tb = fmaf(wb.x, x0, fmaf(wb.y, x1, wb.z * x2));
-            split2(__cosf(ta), __cosf(tb), ch[e], cl[e]);
-            split2(__sinf(ta), __sinf(tb), sh[e], sl[e]);
-          }
-          const uint32_t oc = (uint32_t)((g ^ r7) << 4), os = (uint32_t)(((4 + g) ^ r7) << 4);
-          st_shared_v4(rowhi + oc, ch[0], ch[1], ch[2], ch[3]);
-          st_shared_v4(rowhi + os, sh[0], sh[1], sh[2], sh[3]);
-          st_shared_v4(rowlo + oc, cl[0], cl[1], cl[2], cl[3]);
-          st_shared_v4(rowlo + os, sl[0], sl[1], sl[2], sl[3]);
+        for (int e = 0; e < 4; ++e) {
+          const float4 wa = ld_shared_f4(wk + (2 * e) * 16), wb = ld_shared_f4(wk + (2 * e + 1) * 16);
+          const float t0 = fmaf(wa.x, xa[0], fmaf(wa.y, xa[1], wa.z * xa[2]));
+          const float t1 = fmaf(wb.x, xa[0], fmaf(wb.y, xa[1], wb.z * xa[2]));
+          const float t2 = fmaf(wa.x, xb[0], fmaf(wa.y, xb[1], wa.z * xb[2]));
+          const float t3 = fmaf(wb.x, xb[0], fmaf(wb.y, xb[1], wb.z * xb[2]));
+          split2(__cosf(t0), __cosf(t1), cha[e], cla[e]);
+          split2(__sinf(t0), __sinf(t1), sha[e], sla[e]);
+          split2(__cosf(t2), __cosf(t3), chb[e], clb[e]);
+          split2(__sinf(t2), __sinf(t3), shb[e], slb[e]);
         }
+        const uint32_t ra = sA + s * kAtAStage + pr * 128, rb = ra + 128 * 128;  // rows pr, pr + 128 of Phi_hi
+        st_shared_v4(ra + oc, cha[0], cha[1], cha[2], cha[3]);
+        st_shared_v4(ra + os, sha[0], sha[1], sha[2], sha[3]);
+        st_shared_v4(ra + kAtPhi + oc, cla[0], cla[1], cla[2], cla[3]);
+        st_shared_v4(ra + kAtPhi + os, sla[0], sla[1], sla[2], sla[3]);
+        st_shared_v4(rb + oc, chb[0], chb[1], chb[2], chb[3]);
+        st_shared_v4(rb + os, shb[0], shb[1], shb[2], shb[3]);
+        st_shared_v4(rb + kAtPhi + oc, clb[0], clb[1], clb[2], clb[3]);
+        st_shared_v4(rb + kAtPhi + os, slb[0], slb[1], slb[2], slb[3]);
         fence_proxy_async();  // the generic-proxy stores, before the MMAs read them
         mbar_arrive(smem_u32(&sm->afull[s]));
       }
@@ -182,33 +236,30 @@ apply_tc_kernel(const ApplyTcJob* __restrict__ jobs, const int* __restrict__ pre
     if (lane == 0) {
       int it = 0, tc = 0;
       bool ok = true;
+      const uint32_t idesc = idesc_bf16(128, 256);
       for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x, ++tc) {
         const int j = find_job_at(prefix, count, t);
         const int kchunks = jobs[j].kchunks;
         const int cp = apply_tc_cpad(calls[jobs[j].cloud].c);
-        const uint32_t id_hi = idesc_bf16(128, 2 * cp), id_lo = idesc_bf16(128, cp);
         const int buf = tc & 1, ub = tc >> 1;
         if (ub > 0 && !mbar_wait(smem_u32(&sm->acce[buf]), (uint32_t)(ub - 1) & 1u, err, 22)) break;
         fence_after();
-        const uint32_t d0 = tmem + (uint32_t)(buf * 256);
+        const uint32_t d = tmem + (uint32_t)(buf * 256);
         for (int kc = 0; kc < kchunks; ++kc, ++it) {
-          const int s = it & 1, bs = it & 3;
+          const int s = it & 1, bs = it % kAtBStages;
           if (!mbar_wait(smem_u32(&sm->afull[s]), (uint32_t)(it >> 1) & 1u, err, 23) ||
-              !mbar_wait(smem_u32(&sm->bfull[bs]), (uint32_t)(it >> 2) & 1u, err, 24)) {
+              !mbar_wait(smem_u32(&sm->bfull[bs]), (uint32_t)(it / kAtBStages) & 1u, err, 24)) {
             ok = false;
             break;
           }
           fence_after();
-          const uint32_t a = sA + s * kAtAStage, b = sB + bs * kAtBStage;
+          const uint32_t phi = sA + s * kAtAStage;
+          const uint32_t zimg = sB + bs * kAtBStage + kAtZeros;  // the image's row 0
+          const uint32_t a1 = zimg - (uint32_t)((128 - 2 * cp) * 128), a2 = zimg - (uint32_t)((128 - cp) * 128);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const uint32_t d = d0 + (uint32_t)(h * 128);
-              const uint64_t bd = sdesc_sw128(b + kk * 32);
-              mma_bf16(d, sdesc_sw128(a + h * kAtHalf + kk * 32), bd, id_hi, (kc > 0 || kk > 0) ? 1u : 0u);
-              mma_bf16(d + (uint32_t)cp, sdesc_sw128(a + (2 + h) * kAtHalf + kk * 32), bd, id_lo, 1u);
-            }
+            mma_bf16(d, sdesc_sw128(a1 + kk * 32), sdesc_sw128(phi + kk * 32), idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+            mma_bf16(d, sdesc_sw128(a2 + kk * 32), sdesc_sw128(phi + kAtPhi + kk * 32), idesc, 1u);
           }
           mma_commit(smem_u32(&sm->aempty[s]));  // frees the stages when these MMAs finish
           mma_commit(smem_u32(&sm->bempty[bs]));
@@ -221,7 +272,7 @@ apply_tc_kernel(const ApplyTcJob* __restrict__ jobs, const int* __restrict__ pre
     }
     __syncwarp();
   } else if (warp == kLoadWarp) {
-    // ---------------- Z images: bulk copies ----------------
+    // ---------------- Z images and 2 pi w: bulk copies ----------------
     if (lane == 0) {
       int it = 0;
       bool ok = true;
@@ -232,75 +283,72 @@ apply_tc_kernel(const ApplyTcJob* __restrict__ jobs, const int* __restrict__ pre
         const float4* w2 = jobs[j].w2pi;
         const uint32_t zbytes = (uint32_t)(2 * apply_tc_cpad(calls[jobs[j].cloud].c) * 128);
         for (int kc = 0; kc < kchunks; ++kc, ++it) {
-          const int bs = it & 3, bu = it >> 2;
+          const int bs = it % kAtBStages, bu = it / kAtBStages;
           if (bu > 0 && !mbar_wait(smem_u32(&sm->bempty[bs]), (uint32_t)(bu - 1) & 1u, err, 26)) {
             ok = false;
             break;
           }
           const uint32_t full = smem_u32(&sm->bfull[bs]);
           mbar_arrive_expect_tx(full, zbytes + 512u);
-          bulk_load(sB + bs * kAtBStage, zimg + (size_t)kc * zbytes, zbytes, full);
-          bulk_load(sB + bs * kAtBStage + kAtZBytes, w2 + kc * 32, 512u, full);
+          bulk_load(sB + bs * kAtBStage + kAtZeros, zimg + (size_t)kc * zbytes, zbytes, full);
+          bulk_load(base + kAtOffW + bs * 512, w2 + kc * 32, 512u, full);
         }
       }
       // drain: our copies into the last stages must land before the CTA exits
       for (int q = (it > kAtBStages ? it - kAtBStages : 0); q < it; ++q)
-        mbar_wait(smem_u32(&sm->bfull[q & 3]), (uint32_t)(q >> 2) & 1u, err, 27);
+        mbar_wait(smem_u32(&sm->bfull[q % kAtBStages]), (uint32_t)(q / kAtBStages) & 1u, err, 27);
     }
     __syncwarp();
   } else {
-    // ---------------- epilogue: out = F + D_hi + D_lo ----------------
-    const int quarter = warp & 3;  // TMEM lanes 32 quarter .. + 31
-    const int r = quarter * 32 + lane;
+    // ---------------- epilogue: out = F + D_x + D_y ----------------
+    const int quarter = warp & 3;                 // TMEM lanes 32 quarter .. + 31
+    const int et = threadIdx.x - kEpiWarp0 * 32;  // 0..127
+    const int ch = et & 63, pofs = et >> 6;       // output channel, point parity
     int tc = 0;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++tc) {
       const int j = find_job_at(prefix, count, t);
       const int64_t n = jobs[j].n;
       const CloudCall cc = calls[jobs[j].cloud];
       const int c = cc.c, cp = apply_tc_cpad(c);
+      const int lx = 128 - cp + ch, ly = 128 - 2 * cp + ch;  // the TMEM lanes of channel ch
       const int buf = tc & 1;
-      if (!mbar_wait(smem_u32(&sm->accf[buf]), (uint32_t)(tc >> 1) & 1u, err, 28)) break;
+      if (!epi_all(mbar_wait(smem_u32(&sm->accf[buf]), (uint32_t)(tc >> 1) & 1u, err, 28))) break;
       fence_after();
-      const bool vec = ((cc.ldF | cc.ldOut) & 3) == 0 &&
-                       ((reinterpret_cast<uintptr_t>(cc.F) | reinterpret_cast<uintptr_t>(cc.out)) & 15) == 0;
+      const int64_t p0 = (int64_t)(t - prefix[j]) * 256;
+      // F of the next 32 points is loaded right after the current ones are written, so the
+      // loads are in flight through the next TMEM read and barrier (and all of a thread's
+      // loads of a point come before its store: out may be F itself)
+      float f[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int64_t p = p0 + 2 * k + pofs;
+        f[k] = (ch < c && p < n) ? cc.F[p * cc.ldF + ch] : 0.f;
+      }
 #pragma unroll 1
-      for (int h = 0; h < 2; ++h) {
-        const int64_t p = (int64_t)(t - prefix[j]) * 256 + h * 128 + r;
-        const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 256 + h * 128);
-#pragma unroll 1
-        for (int c0 = 0; c0 < cp; c0 += 16) {
-          uint32_t hi[16], lo[16];
-          tmem_ld16_nowait(ta + (uint32_t)c0, hi);
-          tmem_ld16_nowait(ta + (uint32_t)(cp + c0), lo);
-          tmem_wait_ld();
-          if (p < n) {
-            const float* f = cc.F + p * cc.ldF + c0;
-            float* o = cc.out + p * cc.ldOut + c0;
-            if (vec && c0 + 16 <= c) {
-              float4 fv[4];
+      for (int col0 = 0; col0 < 256; col0 += 32) {  // 32 points of the tile
+        float* er = E + (quarter * 32 + lane) * kAtEPitch;
 #pragma unroll
-              for (int q = 0; q < 4; ++q) fv[q] = reinterpret_cast<const float4*>(f)[q];
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t v[16];
+          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 256 + col0 + 16 * hh), v);
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                float4 v = fv[q];
-                v.x += __uint_as_float(hi[4 * q]) + __uint_as_float(lo[4 * q]);
-                v.y += __uint_as_float(hi[4 * q + 1]) + __uint_as_float(lo[4 * q + 1]);
-                v.z += __uint_as_float(hi[4 * q + 2]) + __uint_as_float(lo[4 * q + 2]);
-                v.w += __uint_as_float(hi[4 * q + 3]) + __uint_as_float(lo[4 * q + 3]);
-                reinterpret_cast<float4*>(o)[q] = v;
-              }
-            } else {
-              const int nq = min(16, c - c0);
-              float fv[16];
+          for (int q = 0; q < 16; ++q) er[16 * hh + q] = __uint_as_float(v[q]);
+        }
+        epi_sync();
+        if (ch < c) {
 #pragma unroll
-              for (int q = 0; q < 16; ++q)
-                if (q < nq) fv[q] = f[q];
+          for (int k = 0; k < 16; ++k) {
+            const int q = 2 * k + pofs;
+            const int64_t p = p0 + col0 + q;
+            if (p < n) cc.out[p * cc.ldOut + ch] = f[k] + (E[lx * kAtEPitch + q] + E[ly * kAtEPitch + q]);
+          }
 #pragma unroll
-              for (int q = 0; q < 16; ++q)
-                if (q < nq) o[q] = fv[q] + (__uint_as_float(hi[q]) + __uint_as_float(lo[q]));
-            }
+          for (int k = 0; k < 16; ++k) {
+            const int64_t p = p0 + col0 + 32 + 2 * k + pofs;
+            f[k] = (col0 + 32 < 256 && p < n) ? cc.F[p * cc.ldF + ch] : 0.f;
           }
         }
+        epi_sync();
       }
       fence_before();
       mbar_arrive(smem_u32(&sm->acce[buf]));
@@ -312,9 +360,9 @@ apply_tc_kernel(const ApplyTcJob* __restrict__ jobs, const int* __restrict__ pre
   if (warp == kMmaWarp) tmem_dealloc(tmem, kAtTmemCols);
 }
 
-// Z (m x c FP32, rows f < h the cos features, h + f the sin ones) as the MMA's
-// B operand: per chunk kc of 64 features, 2 cp rows of 128 B (rows ch < cp the
-// hi parts of channel ch, rows cp + ch the lo parts), each row eight 16-byte
+// Z (m x c FP32, rows f < h the cos features, h + f the sin ones) as rows of
+// the MMA's A operand (Z^T, K-major): per chunk kc of 64 features, 2 cp rows of
+// 128 B (rows ch < cp the hi parts of channel ch, rows cp + ch the lo parts), each row eight 16-byte
 // pieces -- piece q holds features 8 q .. 8 q + 7 of the chunk (q < 4: the cos
 // of frequencies 32 kc + 8 q + e; q >= 4: their sin) -- stored at position
 // q ^ (row mod 8), the 128-byte swizzle; and 2 pi w per frequency, zero past h.
