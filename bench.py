@@ -843,6 +843,25 @@ def main():
                "autotune": {"lanes_pct": s64["tune_lanes_pct"], "phase_blocks": s64["tune_phase_blocks"],
                             "gram_form": "CTA pairs (2-SM MMA)" if s64["tune_pair_gram"] else "one SM per tile"}}
         p64.close()
+        # its step breakdown (direct launches, CUDA-event timing; same tuning, from the cache), and
+        # the apply (step a6) in both forms: tensor cores (BF16 hi/lo splits) and FP32 SIMT
+        t64p = rfd.Plan(n, m, spec.eps, lam, spec.seed, max_channels=64, precision=prec, stream=stream,
+                        autotune=tune, timing=True)
+        apply_ms = {}
+        for form, flag in (("tensor_core", 1), ("simt_fp32", 0)):
+            assert rfd.lib.rfd_debug_plan_set_apply_tc(t64p.handle, flag) == 0, rfd.rfd_last_error()
+            for _ in range(2):
+                t64p.gfi(P, F64, o64)
+            t64p.sync()
+            t64p.stats_reset()
+            t64p.gfi(P, F64, o64)
+            t64p.sync()
+            sm64 = t64p.stats()["step_ms"]
+            if flag:
+                c64["step_ms"] = {k: round(v, 4) for k, v in sm64.items() if v}
+            apply_ms[form] = round(sm64["apply"], 4)
+        c64["apply_ms"] = apply_ms
+        t64p.close()
         del F64, o64
 
     # FP32 plain form on the same inputs (the form the BF16 path must beat), and the BF16 form's
