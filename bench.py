@@ -848,7 +848,7 @@ def main():
         t64p = rfd.Plan(n, m, spec.eps, lam, spec.seed, max_channels=64, precision=prec, stream=stream,
                         autotune=tune, timing=True)
         apply_ms = {}
-        for form, flag in (("tensor_core", 1), ("simt_fp32", 0)):
+        for form, flag in (("tensor_core", 2), ("simt_fp32", 0)):
             assert rfd.lib.rfd_debug_plan_set_apply_tc(t64p.handle, flag) == 0, rfd.rfd_last_error()
             for _ in range(2):
                 t64p.gfi(P, F64, o64)
@@ -903,7 +903,10 @@ def main():
     ngemm = st.get("phi1_gemms", 0) if st.get("phi1_emulated") else 0
     pf = ngemm * 2.0 * m ** 3 if ngemm else phi1_flops(m, st["pade_degree"], st["squarings"])
     phi1_tc_flops = ngemm * 16 * 2.0 * m ** 3
-    groups = -(-c // (4 if c <= 4 else 8 if c <= 8 else 16 if c <= 16 else 32))
+    # the apply's sin/cos count: the SIMT kernel recomputes Phi per channel group; the tensor-core
+    # form (BF16 form, 5..64 channels) once per point and frequency
+    tc_apply = prec == rfd.RFD_BF16_TC and (16 < c <= 64 or (8 < c <= 64 and m >= 512))
+    groups = 1 if tc_apply else -(-c // (4 if c <= 4 else 8 if c <= 8 else 16 if c <= 16 else 32))
     step_roof = {
         "gram": {"bound": "tensor", "achieved": wm["gram_flops"] / (steps["gram"] * 1e-3) / 1e12,
                  "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
@@ -921,7 +924,9 @@ def main():
                      "peak": mufu_peak / 1e9, "unit": "Gsincos/s", "work": "N m sin/cos values (MUFU)"},
         "apply": {"bound": "alu", "achieved": wm["sincos"] * groups / (steps["apply"] * 1e-3) / 1e9,
                   "peak": mufu_peak / 1e9, "unit": "Gsincos/s",
-                  "work": f"N m sin/cos values recomputed per channel group ({groups}); reads points, F; writes out"},
+                  "work": ("N m sin/cos values (Phi recomputed once in FP32, its BF16 hi/lo parts times Z's "
+                           "on the tensor cores); reads points, F; writes out") if tc_apply else
+                          f"N m sin/cos values recomputed per channel group ({groups}); reads points, F; writes out"},
     }
     for v in step_roof.values():
         v["frac"] = v["achieved"] / v["peak"]

@@ -62,13 +62,15 @@ RFD_API rfd_status rfd_debug_plan_set_phase(rfd_plan_t plan, int32_t phase_block
  * plans, or for plans with RFD_FLAG_GRAPH or RFD_FLAG_AUTOTUNE.  Host only. */
 RFD_API rfd_status rfd_debug_plan_set_overlap(rfd_plan_t plan, int32_t enable);
 
-/* Step a6 of a BF16 plan on the tensor cores (enable = 1, the default) or on
- * the SIMT kernel (0).  With 1 the plan takes the tensor-core form in calls of
- * 5 <= c <= min(64, max_channels) channels: Phi recomputed in FP32 and split
+/* Which form step a6 of a BF16 plan takes (Sec. 2.4, the apply of the low-rank
+ * factors).  enable = 0: the FP32 SIMT kernel in every call.  1 (the default):
+ * the tensor-core form where it is the faster -- calls of 17..64 channels, or
+ * 9..16 channels when m >= 512 -- else the SIMT kernel.  2: the tensor-core form
+ * in every call of c <= min(64, max_channels): Phi recomputed in FP32 and split
  * into BF16 hi and lo parts, out = F + Phi_hi Z_hi + Phi_hi Z_lo + Phi_lo Z_hi
- * with FP32 accumulation (Sec. 2.4, the apply of the low-rank factors); with 0
- * every call takes the FP32 SIMT kernel.  RFD_EINVAL for FP32 plans or plans
- * with RFD_FLAG_GRAPH, RFD_ENOTSUP (enable = 1) off sm_103.  Host only. */
+ * with FP32 accumulation.  RFD_EINVAL for FP32 plans, plans with
+ * RFD_FLAG_GRAPH or another value; RFD_ENOTSUP (enable = 2) off sm_103.
+ * Host only. */
 RFD_API rfd_status rfd_debug_plan_set_apply_tc(rfd_plan_t plan, int32_t enable);
 
 /* The bounded device-side wait on its own.  Every wait of the library's

@@ -119,15 +119,6 @@ __device__ __forceinline__ bool epi_all(bool v) {
       : "memory");
   return r != 0;
 }
-// 16 consecutive FP32 columns of this thread's TMEM lane (warp-collective)
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 // (a, b) -> BF16 pairs hi = (bf16(a), bf16(b)) and lo = (bf16(a - hi.x), bf16(b - hi.y)),
 // the first value in the low half (the lower address)
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
@@ -312,27 +303,33 @@ apply_tc_kernel(const ApplyTcJob* __restrict__ jobs, const int* __restrict__ pre
       const int c = cc.c, cp = apply_tc_cpad(c);
       const int lx = 128 - cp + ch, ly = 128 - 2 * cp + ch;  // the TMEM lanes of channel ch
       const int buf = tc & 1;
-      if (!epi_all(mbar_wait(smem_u32(&sm->accf[buf]), (uint32_t)(tc >> 1) & 1u, err, 28))) break;
-      fence_after();
       const int64_t p0 = (int64_t)(t - prefix[j]) * 256;
-      // F of the next 32 points is loaded right after the current ones are written, so the
-      // loads are in flight through the next TMEM read and barrier (and all of a thread's
-      // loads of a point come before its store: out may be F itself)
-      float f[16];
+      // F of 32 points is loaded one round ahead of its use -- the first round's before the
+      // wait for the accumulators -- so its latency overlaps the wait, the TMEM reads and the
+      // barriers (a thread's loads of a point precede its store: out may be F itself)
+      float f[16], fn[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const int64_t p = p0 + 2 * k + pofs;
         f[k] = (ch < c && p < n) ? cc.F[p * cc.ldF + ch] : 0.f;
       }
+      if (!epi_all(mbar_wait(smem_u32(&sm->accf[buf]), (uint32_t)(tc >> 1) & 1u, err, 28))) break;
+      fence_after();
 #pragma unroll 1
       for (int col0 = 0; col0 < 256; col0 += 32) {  // 32 points of the tile
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int64_t p = p0 + col0 + 32 + 2 * k + pofs;
+          fn[k] = (ch < c && col0 + 32 < 256 && p < n) ? cc.F[p * cc.ldF + ch] : 0.f;
+        }
         float* er = E + (quarter * 32 + lane) * kAtEPitch;
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          uint32_t v[16];
-          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 256 + col0 + 16 * hh), v);
+        for (int hh = 0; hh < 4; ++hh) {
+          uint32_t v[8];
+          tmem_ld8_nowait(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 256 + col0 + 8 * hh), v);
+          tmem_wait_ld();
 #pragma unroll
-          for (int q = 0; q < 16; ++q) er[16 * hh + q] = __uint_as_float(v[q]);
+          for (int q = 0; q < 8; ++q) er[8 * hh + q] = __uint_as_float(v[q]);
         }
         epi_sync();
         if (ch < c) {
@@ -342,13 +339,10 @@ apply_tc_kernel(const ApplyTcJob* __restrict__ jobs, const int* __restrict__ pre
             const int64_t p = p0 + col0 + q;
             if (p < n) cc.out[p * cc.ldOut + ch] = f[k] + (E[lx * kAtEPitch + q] + E[ly * kAtEPitch + q]);
           }
-#pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int64_t p = p0 + col0 + 32 + 2 * k + pofs;
-            f[k] = (col0 + 32 < 256 && p < n) ? cc.F[p * cc.ldF + ch] : 0.f;
-          }
         }
         epi_sync();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) f[k] = fn[k];
       }
       fence_before();
       mbar_arrive(smem_u32(&sm->acce[buf]));

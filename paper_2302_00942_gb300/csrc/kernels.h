@@ -379,7 +379,6 @@ struct ApplyTcJob {
   int32_t h, kchunks, cloud, tiles;  // kchunks = ceil(h / 32), tiles = ceil(n / 256)
 };
 constexpr int kApplyTcMaxC = 64;
-constexpr int kApplyTcMinC = 4;  // the batch takes this form when its largest c is above this
 __host__ __device__ constexpr int apply_tc_cpad(int c) { return (c + 15) / 16 * 16; }
 inline size_t apply_tc_zimg_bytes(int h, int max_c) {
   const int c = max_c < kApplyTcMaxC ? max_c : kApplyTcMaxC;

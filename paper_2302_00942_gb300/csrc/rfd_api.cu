@@ -1618,7 +1618,8 @@ rfd_status rfd_debug_plan_set_apply_tc(rfd_plan_t pl, int32_t enable) {
   if (!pl) return fail(RFD_EINVAL, "null plan");
   if (!pl->bf16 || !pl->self) return fail(RFD_EINVAL, "the tensor-core apply belongs to the BF16 form");
   if (pl->p.flags & RFD_FLAG_GRAPH) return fail(RFD_EINVAL, "not for plans with RFD_FLAG_GRAPH");
-  if (!batch_set_apply_tc(pl->self, enable != 0) && enable) return fail(RFD_ENOTSUP, "the tensor-core apply needs sm_103");
+  if (enable < 0 || enable > 2) return fail(RFD_EINVAL, "enable must be 0, 1 or 2");
+  if (!batch_set_apply_tc(pl->self, enable) && enable == 2) return fail(RFD_ENOTSUP, "the tensor-core apply needs sm_103");
   return RFD_OK;
 }
 

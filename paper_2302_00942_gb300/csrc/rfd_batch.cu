@@ -90,14 +90,16 @@ struct BatchImpl {
   int fillw_blocks = 0;
   ApplyJob* d_apply = nullptr;
   std::vector<int> apply_bx;
-  // the tensor-core apply (k_apply_tc.cu): jobs, their 256-point tiles, and whether every
-  // plan has its buffers (apply_tc_ok) and the form is not switched off (apply_tc_on)
+  // the tensor-core apply (k_apply_tc.cu): jobs, their 256-point tiles, whether every plan
+  // has its buffers (apply_tc_ok), and when the form is taken (apply_tc_mode)
   ApplyTcJob* d_apply_tc = nullptr;
   std::vector<ApplyTcJob> apply_tc_h;
   int* d_tile_prefix = nullptr;
   int apply_tiles = 0;
   int max_channels = 0;  // the smallest max_channels of the plans (their Z images' capacity)
-  bool apply_tc_ok = false, apply_tc_on = true;
+  int min_m = 0;         // the smallest m of the plans
+  bool apply_tc_ok = false;
+  int apply_tc_mode = 1;  // 0: SIMT always, 1: by the channel count and m, 2: tensor cores where they can
   int sms = 0;
   int* d_small_prefix = nullptr;
   int small_rows = 0;
@@ -301,6 +303,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
     tiles_n.push_back(tj.tiles);
     b->apply_tc_ok = b->apply_tc_ok && tj.zimg != nullptr && tj.w2pi != nullptr;
     b->max_channels = std::min(b->max_channels, pl->p.max_channels);
+    b->min_m = (k == 0) ? pl->m : std::min(b->min_m, pl->m);
     small_n.push_back(pl->m);
     wide_n.push_back(small_wide_blocks(pl->m, pl->p.max_channels));
     PhiCloud pc = d.phi;
@@ -722,10 +725,13 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   int max_c = 1;
   for (int k = 0; k < n; ++k) max_c = std::max(max_c, calls[k].c);
   const int cg = max_c <= 3 ? 3 : (max_c <= 4 ? 4 : (max_c <= 8 ? 8 : (max_c <= 16 ? 16 : 32)));
-  // the apply on the tensor cores from 5 channels on (the SIMT kernel's FMAs grow with c, the
-  // tensor-core form's per-point work hardly), up to the Z images' capacity
-  const bool use_tc = mode != kModeFeatures && b->apply_tc_ok && b->apply_tc_on && max_c > kApplyTcMinC &&
-                      max_c <= std::min(kApplyTcMaxC, b->max_channels);
+  // the apply on the tensor cores where it is the faster form: the SIMT kernel's FMAs grow with
+  // c, the tensor-core form's time hardly (it has a fixed cost per 256-point tile instead), so
+  // above 16 channels always, from 9 channels on when every cloud has m >= 512 (measured on
+  // GB300 at N = 10^5 and 10^6, m = 128 .. 1024); up to the Z images' capacity
+  const bool tc_fits = mode != kModeFeatures && b->apply_tc_ok && max_c <= std::min(kApplyTcMaxC, b->max_channels);
+  const bool use_tc = tc_fits && (b->apply_tc_mode == 2 ||
+                                  (b->apply_tc_mode == 1 && (max_c > 16 || (max_c > 8 && b->min_m >= 512))));
   // a pinned staging buffer whose previous upload has been consumed
   const int slot = b->stage_next;
   b->stage_next = (slot + 1) % BatchImpl::kStageRing;
@@ -1044,8 +1050,8 @@ rfd_status batch_time_gram(BatchImpl* b, int mode, int reps, float* ms, const Cl
 
 int* batch_error_word(BatchImpl* b) { return b->d_err; }
 
-bool batch_set_apply_tc(BatchImpl* b, bool on) {
-  b->apply_tc_on = on;
+bool batch_set_apply_tc(BatchImpl* b, int mode) {
+  b->apply_tc_mode = mode;
   return b->apply_tc_ok;
 }
 

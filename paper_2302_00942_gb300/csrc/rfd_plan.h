@@ -214,9 +214,10 @@ rfd_status batch_eigenvalues(rfd_plan_s* const* plans, int count, int k, int lar
 // RFD_ENUMERIC if some cloud's G is not finite (bad[k] = 1 for those clouds when
 // bad is given).
 rfd_status batch_check_error(BatchImpl* b, int* bad = nullptr);
-// The apply (step a6) on the tensor cores where every call's c allows (1: the default)
-// or always on the SIMT kernel (0); returns whether the batch has the tensor-core form.
-bool batch_set_apply_tc(BatchImpl* b, bool on);
+// The apply (step a6): 0 always on the SIMT kernel, 1 (the default) on the tensor cores where
+// that form is the faster (by the calls' largest c and the clouds' m), 2 on the tensor cores
+// wherever the calls' c fits; returns whether the batch has the tensor-core form.
+bool batch_set_apply_tc(BatchImpl* b, int mode);
 // Times the Gram launches of one batched call of `mode`, with the features in
 // front of them (serially or beside them, as the batch is set) in modes that
 // compute features, from the points of calls (one CloudCall per plan): mean ms

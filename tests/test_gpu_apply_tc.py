@@ -1,6 +1,7 @@
-"""Step a6, out = F + Phi Z, on the tensor cores (the BF16 form's apply for 5..64
-channels) against the FP32 SIMT apply of the same plan and against the CPU FP64
-oracle.
+"""Step a6, out = F + Phi Z, on the tensor cores (the BF16 form's apply for up to
+64 channels, forced here; by default the batch takes it above 16 channels, or
+above 8 when m >= 512) against the FP32 SIMT apply of the same plan and against
+the CPU FP64 oracle.
 
 The tensor-core form recomputes Phi in FP32 exactly as the SIMT kernel does,
 splits Phi and Z into BF16 hi and lo parts and sums Phi_hi Z_hi + Phi_hi Z_lo +
@@ -46,7 +47,7 @@ def _gfi(pts, F, eps, lam, m, seed, ld, tc, *, inplace=False):
     out = Ft if inplace else torch.full((n, ld), float("nan"), device=DEV)
     plan = rfd.Plan(n, m, eps, lam, seed, max_channels=c, precision=BF16, stream=torch.cuda.current_stream(DEV))
     try:
-        assert rfd.lib.rfd_debug_plan_set_apply_tc(plan.handle, 1 if tc else 0) == 0, rfd.rfd_last_error()
+        assert rfd.lib.rfd_debug_plan_set_apply_tc(plan.handle, 2 if tc else 0) == 0, rfd.rfd_last_error()
         rfd.rfd_gfi(plan.handle, P, Ft, c, ld, out, ld)
         plan.sync()
         launches = plan.stats()["kernel_launches"]
@@ -87,7 +88,8 @@ def test_tensor_core_apply_matches_simt_and_oracle(n, m, c, ld):
 
 def test_tensor_core_apply_on_compact_plan_and_batch():
     """A compact plan's warm integration (Phi^T F from the points) with 24 channels,
-    and a batch whose clouds take 1, 9 and 64 channels in one tensor-core launch."""
+    and a batch whose clouds take 1, 9 and 64 channels in one tensor-core launch
+    (the default choice: the largest c is above 16)."""
     specs = synth.batched_specs(count=3, seed=31, n_lo=900, n_hi=9000, ms=(64, 128, 256), c=8)
     for s, c in zip(specs, (1, 9, 64)):
         s.c = c
