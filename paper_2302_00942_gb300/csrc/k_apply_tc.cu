@@ -398,13 +398,308 @@ __global__ void __launch_bounds__(256) apply_prep_kernel(const ApplyTcJob* __res
   *dst = make_uint4(packed[0], packed[1], packed[2], packed[3]);
 }
 
+// Y' = Phi^T F from the points on the tensor cores (compact plans, fields of
+// more than 16 channels, or more than 8 with m >= 512): the apply's machinery
+// with K running over the points instead of the features.  A work item is one
+// chunk of the cloud's points (the FieldPtsJob's chunks) and one tile of 128
+// frequencies (256 features: their cos, then their sin); per step of 64 points
+//   D += [.. | F_hi | F_lo]^T Phi_hi^T  and  D += [.. | 0 | F_hi]^T Phi_lo^T
+// (M = 128 rows of F's image, N = the 256 features, K = 16 points per MMA), so
+// that TMEM lane 128 - cp + ch gathers F_lo Phi_hi + F_hi Phi_lo and lane
+// 128 - 2cp + ch gathers F_hi Phi_hi.  The producers write both operands each
+// step: Phi^T (a thread per frequency and 16 points: the phase and MUFU sin/cos
+// of the SIMT fieldpts kernel, split into BF16 hi / lo) and F's image (a thread
+// per channel and 8 points, F split the same way; zero for points >= N).  The
+// points of each step come in by bulk copy (a ring of four).  The epilogue
+// writes the item's FP32 partial part[chunk][f][ch] = lane x + lane y, which
+// fieldpts_reduce sums over the chunks as it does the SIMT kernel's.
+constexpr int kFtPhi = 256 * 128;           // Phi^T split: 256 feature rows x 64 points (128 B)
+constexpr int kFtZeros = 64 * 128;          // zero rows before F's image
+constexpr int kFtImg = 128 * 128;           // F's image: 2 cp <= 128 channel rows x 64 points
+constexpr int kFtStage = 2 * kFtPhi + kFtZeros + kFtImg;
+constexpr int kFtStages = 2;
+constexpr int kFtXSlots = 4;                // points ring: 64 points x 12 B each
+constexpr int kFtOffX = kFtStages * kFtStage;
+constexpr int kFtOffE = kFtOffX + kFtXSlots * 768;
+constexpr int kFtOffBar = kFtOffE + 128 * kAtEPitch * 4;
+constexpr int kFtSmem = 1024 + kFtOffBar + 256;
+
+struct FtSmem {
+  uint64_t afull[kFtStages], aempty[kFtStages];
+  uint64_t xfull[kFtXSlots], xempty[kFtXSlots];
+  uint64_t accf[2], acce[2];
+  uint64_t done;
+  uint32_t tmem_base;
+};
+
+// the item's chunk and frequency tile, and its points [p_begin, p_end)
+struct FtItem {
+  int j, chunk, ft, steps;
+  int64_t p_begin, p_end;
+};
+__device__ __forceinline__ FtItem ft_item(const FieldPtsJob* __restrict__ jobs, const int* __restrict__ prefix,
+                                          int count, int t) {
+  FtItem r;
+  r.j = find_job_at(prefix, count, t);
+  const FieldPtsJob& jb = jobs[r.j];
+  const int ftiles = (jb.h + 127) / 128;
+  const int local = t - prefix[r.j];
+  r.chunk = local / ftiles;
+  r.ft = local % ftiles;
+  r.p_begin = (int64_t)r.chunk * jb.pts;
+  r.p_end = min(jb.n, r.p_begin + jb.pts);
+  r.steps = r.p_end > r.p_begin ? (int)((r.p_end - r.p_begin + 63) / 64) : 0;
+  return r;
+}
+
+__global__ void __launch_bounds__(kAtThreads, 1)
+fieldpts_tc_kernel(const FieldPtsJob* __restrict__ jobs, const int* __restrict__ prefix, int count, int total_items,
+                   const CloudCall* __restrict__ calls, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw_addr = smem_u32(smem_raw);
+  const uint32_t base = (raw_addr + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw_addr);
+  FtSmem* sm = reinterpret_cast<FtSmem*>(gbase + kFtOffBar);
+  float* E = reinterpret_cast<float*>(gbase + kFtOffE);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kFtStages; ++s) {
+      mbar_init(smem_u32(&sm->afull[s]), kAtProducers);
+      mbar_init(smem_u32(&sm->aempty[s]), 1);
+    }
+    for (int s = 0; s < kFtXSlots; ++s) {
+      mbar_init(smem_u32(&sm->xfull[s]), 1);
+      mbar_init(smem_u32(&sm->xempty[s]), kAtProducers);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&sm->accf[b]), 1);
+      mbar_init(smem_u32(&sm->acce[b]), 128);
+    }
+    mbar_init(smem_u32(&sm->done), 1);
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < kFtStages * (kFtZeros / 16); i += kAtThreads) {
+    const int s = i / (kFtZeros / 16), q = i % (kFtZeros / 16);
+    st_shared_v4(base + s * kFtStage + 2 * kFtPhi + q * 16, 0u, 0u, 0u, 0u);
+  }
+  fence_proxy_async();
+  if (warp == kMmaWarp) tmem_alloc(smem_u32(&sm->tmem_base), kAtTmemCols);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = sm->tmem_base;
+
+  if (warp < kMmaWarp) {
+    // ---------------- producers: Phi^T (a frequency x 16 points) and F's image (a channel x 8 points) ----
+    const int fj = threadIdx.x & 127, pq = threadIdx.x >> 7;  // frequency of the tile, 16-point quarter
+    const int fch = threadIdx.x & 63, pg = threadIdx.x >> 6;  // channel, 8-point group
+    const int r7 = fj & 7, c7 = fch & 7;
+    const float two_pi = 6.283185307179586f;
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < total_items && ok; t += gridDim.x) {
+      const FtItem im = ft_item(jobs, prefix, count, t);
+      const FieldPtsJob& jb = jobs[im.j];
+      const CloudCall cc = calls[jb.cloud];
+      const int c = cc.c, cp = apply_tc_cpad(c);
+      const int fidx = im.ft * 128 + fj;
+      float w[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) w[d] = fidx < jb.h ? two_pi * jb.omega_hi[(size_t)fidx * 3 + d] : 0.f;
+      // F of the first step (then of the next, loaded one step ahead)
+      float fv[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int64_t p = im.p_begin + pg * 8 + e;
+        fv[e] = (fch < c && p < im.p_end) ? cc.F[p * cc.ldF + fch] : 0.f;
+      }
+      for (int k = 0; k < im.steps; ++k, ++it) {
+        const int s = it & 1, u = it >> 1, xs = it % kFtXSlots;
+        const int64_t p0 = im.p_begin + (int64_t)k * 64;
+        const int np = (int)min((int64_t)64, im.p_end - p0);
+        if ((u > 0 && !mbar_wait(smem_u32(&sm->aempty[s]), (uint32_t)(u - 1) & 1u, err, 31)) ||
+            !mbar_wait(smem_u32(&sm->xfull[xs]), (uint32_t)(it / kFtXSlots) & 1u, err, 32)) {
+          ok = false;
+          break;
+        }
+        const uint32_t st0 = base + s * kFtStage;
+        // Phi^T rows fj (cos) and 128 + fj (sin): pieces 2 pq and 2 pq + 1 (points 16 pq ..)
+        const float* xsm = reinterpret_cast<const float*>(gbase + kFtOffX + xs * 768);
+        uint32_t chv[8], clv[8], shv[8], slv[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int pa = pq * 16 + 2 * e, pb = pa + 1;
+          const float ax = pa < np ? xsm[pa * 3] : 0.f, ay = pa < np ? xsm[pa * 3 + 1] : 0.f,
+                      az = pa < np ? xsm[pa * 3 + 2] : 0.f;
+          const float bx = pb < np ? xsm[pb * 3] : 0.f, by = pb < np ? xsm[pb * 3 + 1] : 0.f,
+                      bz = pb < np ? xsm[pb * 3 + 2] : 0.f;
+          const float ta = fmaf(w[0], ax, fmaf(w[1], ay, w[2] * az));
+          const float tb = fmaf(w[0], bx, fmaf(w[1], by, w[2] * bz));
+          split2(__cosf(ta), __cosf(tb), chv[e], clv[e]);
+          split2(__sinf(ta), __sinf(tb), shv[e], slv[e]);
+        }
+        mbar_arrive(smem_u32(&sm->xempty[xs]));  // done with this step's points
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const uint32_t off = (uint32_t)(((2 * pq + h2) ^ r7) << 4);
+          const uint32_t rc = st0 + fj * 128 + off, rs = st0 + (128 + fj) * 128 + off;
+          st_shared_v4(rc, chv[4 * h2], chv[4 * h2 + 1], chv[4 * h2 + 2], chv[4 * h2 + 3]);
+          st_shared_v4(rs, shv[4 * h2], shv[4 * h2 + 1], shv[4 * h2 + 2], shv[4 * h2 + 3]);
+          st_shared_v4(rc + kFtPhi, clv[4 * h2], clv[4 * h2 + 1], clv[4 * h2 + 2], clv[4 * h2 + 3]);
+          st_shared_v4(rs + kFtPhi, slv[4 * h2], slv[4 * h2 + 1], slv[4 * h2 + 2], slv[4 * h2 + 3]);
+        }
+        // F's image: rows fch (hi) and cp + fch (lo), piece pg (points 8 pg ..)
+        if (fch < cp) {
+          uint32_t hv[4], lv[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) split2(fv[2 * e], fv[2 * e + 1], hv[e], lv[e]);
+          const uint32_t img = st0 + 2 * kFtPhi + kFtZeros;
+          st_shared_v4(img + fch * 128 + (uint32_t)((pg ^ c7) << 4), hv[0], hv[1], hv[2], hv[3]);
+          const int rl = cp + fch;
+          st_shared_v4(img + rl * 128 + (uint32_t)((pg ^ (rl & 7)) << 4), lv[0], lv[1], lv[2], lv[3]);
+        }
+        // the next step's F
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int64_t p = p0 + 64 + pg * 8 + e;
+          fv[e] = (fch < c && p < im.p_end) ? cc.F[p * cc.ldF + fch] : 0.f;
+        }
+        fence_proxy_async();
+        mbar_arrive(smem_u32(&sm->afull[s]));
+      }
+    }
+  } else if (warp == kMmaWarp) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int it = 0, tc = 0;
+      bool ok = true;
+      const uint32_t idesc = idesc_bf16(128, 256);
+      for (int t = blockIdx.x; t < total_items && ok; t += gridDim.x, ++tc) {
+        const FtItem im = ft_item(jobs, prefix, count, t);
+        const int cp = apply_tc_cpad(calls[jobs[im.j].cloud].c);
+        const int buf = tc & 1, ub = tc >> 1;
+        if (ub > 0 && !mbar_wait(smem_u32(&sm->acce[buf]), (uint32_t)(ub - 1) & 1u, err, 33)) break;
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * 256);
+        for (int k = 0; k < im.steps; ++k, ++it) {
+          const int s = it & 1;
+          if (!mbar_wait(smem_u32(&sm->afull[s]), (uint32_t)(it >> 1) & 1u, err, 34)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t st0 = base + s * kFtStage, img = st0 + 2 * kFtPhi + kFtZeros;
+          const uint32_t a1 = img - (uint32_t)((128 - 2 * cp) * 128), a2 = img - (uint32_t)((128 - cp) * 128);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            mma_bf16(d, sdesc_sw128(a1 + kk * 32), sdesc_sw128(st0 + kk * 32), idesc, (k > 0 || kk > 0) ? 1u : 0u);
+            mma_bf16(d, sdesc_sw128(a2 + kk * 32), sdesc_sw128(st0 + kFtPhi + kk * 32), idesc, 1u);
+          }
+          mma_commit(smem_u32(&sm->aempty[s]));
+        }
+        if (ok) mma_commit(smem_u32(&sm->accf[buf]));
+      }
+      mma_commit(smem_u32(&sm->done));
+      mbar_wait(smem_u32(&sm->done), 0u, err, 35);
+    }
+    __syncwarp();
+  } else if (warp == kLoadWarp) {
+    // ---------------- the points of each step: bulk copies ----------------
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total_items && ok; t += gridDim.x) {
+        const FtItem im = ft_item(jobs, prefix, count, t);
+        const float* xyz = jobs[im.j].xyz;
+        for (int k = 0; k < im.steps; ++k, ++it) {
+          const int xs = it % kFtXSlots, xu = it / kFtXSlots;
+          if (xu > 0 && !mbar_wait(smem_u32(&sm->xempty[xs]), (uint32_t)(xu - 1) & 1u, err, 36)) {
+            ok = false;
+            break;
+          }
+          const int64_t p0 = im.p_begin + (int64_t)k * 64;
+          const int np = (int)min((int64_t)64, im.p_end - p0);
+          // np x 12 bytes, rounded up to 16: within the points' allocation (rounded up to 256 B)
+          const uint32_t bytes = (uint32_t)((np * 12 + 15) & ~15);
+          const uint32_t full = smem_u32(&sm->xfull[xs]);
+          mbar_arrive_expect_tx(full, bytes);
+          bulk_load(base + kFtOffX + xs * 768, xyz + p0 * 3, bytes, full);
+        }
+      }
+      for (int q = (it > kFtXSlots ? it - kFtXSlots : 0); q < it; ++q)
+        mbar_wait(smem_u32(&sm->xfull[q % kFtXSlots]), (uint32_t)(q / kFtXSlots) & 1u, err, 37);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: part[chunk][f][ch] = D_x + D_y ----------------
+    const int quarter = warp & 3;
+    const int et = threadIdx.x - kEpiWarp0 * 32;
+    const int ch = et & 63, pofs = et >> 6;
+    int tc = 0;
+    for (int t = blockIdx.x; t < total_items; t += gridDim.x, ++tc) {
+      const FtItem im = ft_item(jobs, prefix, count, t);
+      const FieldPtsJob& jb = jobs[im.j];
+      const int c = calls[jb.cloud].c, cp = apply_tc_cpad(c);
+      const int lx = 128 - cp + ch, ly = 128 - 2 * cp + ch;
+      const int buf = tc & 1;
+      if (!epi_all(mbar_wait(smem_u32(&sm->accf[buf]), (uint32_t)(tc >> 1) & 1u, err, 38))) break;
+      fence_after();
+      float* part = jb.part + (size_t)im.chunk * jb.m * jb.ld;
+#pragma unroll 1
+      for (int col0 = 0; col0 < 256; col0 += 32) {
+        float* er = E + (quarter * 32 + lane) * kAtEPitch;
+#pragma unroll
+        for (int hh = 0; hh < 4; ++hh) {
+          uint32_t v[8];
+          tmem_ld8_nowait(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 256 + col0 + 8 * hh), v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int q = 0; q < 8; ++q) er[8 * hh + q] = __uint_as_float(v[q]);
+        }
+        epi_sync();
+        if (ch < c) {
+#pragma unroll 4
+          for (int k = 0; k < 16; ++k) {
+            const int col = col0 + 2 * k + pofs;  // feature column of the tile
+            const int fr = im.ft * 128 + (col & 127);
+            if (fr < jb.h) {
+              const int f = (col < 128 ? 0 : jb.h) + fr;
+              part[(size_t)f * jb.ld + ch] =
+                  im.steps ? E[lx * kAtEPitch + 2 * k + pofs] + E[ly * kAtEPitch + 2 * k + pofs] : 0.f;
+            }
+          }
+        }
+        epi_sync();
+      }
+      fence_before();
+      mbar_arrive(smem_u32(&sm->acce[buf]));
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == kMmaWarp) tmem_dealloc(tmem, kAtTmemCols);
+}
+
 }  // namespace
 
 bool apply_tc_supported() { return tc::sm103_available(); }
 
 cudaError_t apply_tc_prepare() {
-  static cudaError_t once = cudaFuncSetAttribute(apply_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kAtSmem);
+  static cudaError_t once = [] {
+    cudaError_t e = cudaFuncSetAttribute(apply_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kAtSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fieldpts_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFtSmem);
+    return e;
+  }();
   return once;
+}
+
+cudaError_t launch_fieldpts_tc(const FieldPtsJob* jobs, const int* item_prefix, int count, int total_items, int grid,
+                               const CloudCall* calls, int* err, cudaStream_t st) {
+  if (total_items <= 0) return cudaSuccess;
+  fieldpts_tc_kernel<<<grid, kAtThreads, kFtSmem, st>>>(jobs, item_prefix, count, total_items, calls, err);
+  return launched();
 }
 
 cudaError_t launch_apply_prep(const ApplyTcJob* jobs, const int* prefix, int count, int total_blocks,

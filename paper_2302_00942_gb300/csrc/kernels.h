@@ -386,6 +386,13 @@ inline size_t apply_tc_zimg_bytes(int h, int max_c) {
 }
 inline int apply_prep_blocks(const ApplyTcJob& j, int c) { return (j.kchunks * 2 * apply_tc_cpad(c) * 8 + 255) / 256; }
 bool apply_tc_supported();
+// Y' of compact plans from their points on the tensor cores (k_apply_tc.cu): work items of one
+// chunk of points (jobs[k].pts a multiple of 64) and one tile of 128 frequencies, item_prefix over
+// chunks * ceil(h / 128) per cloud; persistent CTAs (at most one per SM).  The partials are laid
+// out as the SIMT kernel's (launch_fieldpts_reduce sums them).
+cudaError_t launch_fieldpts_tc(const FieldPtsJob* jobs, const int* item_prefix, int count, int total_items, int grid,
+                               const CloudCall* calls, int* err, cudaStream_t st);
+inline int fieldpts_tc_items(const FieldPtsJob& j) { return j.chunks * ((j.h + 127) / 128); }
 cudaError_t apply_tc_prepare();
 cudaError_t launch_apply_prep(const ApplyTcJob* jobs, const int* prefix, int count, int total_blocks,
                               const CloudCall* calls, cudaStream_t st);

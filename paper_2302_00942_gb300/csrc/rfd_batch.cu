@@ -75,6 +75,11 @@ struct BatchImpl {
   bool pts_ok = false;       // every plan has a points-based Phi^T F (compact, or a full BF16 plan)
   FieldPtsJob* d_fpts = nullptr;
   std::vector<FieldPtsJob> fpts_h;  // host copies (block counts per call)
+  // the same on the tensor cores (wide fields): chunks of a multiple of 64 points, as many as
+  // fill the GPU with their 128-frequency tiles, and the work items' prefix
+  FieldPtsJob* d_fpts_tc = nullptr;
+  int* d_item_prefix = nullptr;
+  int fpts_items = 0;
   PairUnit* d_pair[3] = {};  // a lone cloud with m >= 512: the 2-SM form of the Gram modes
   int n_pair[3] = {};
   int pair_stage_bytes = 0;
@@ -216,7 +221,8 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
     }
   std::vector<FillJob> fill;
   std::vector<ApplyJob> apply;
-  std::vector<int> tiles_n, wide_n, fillw_n;
+  std::vector<int> tiles_n, wide_n, fillw_n, items_n;
+  std::vector<FieldPtsJob> fpts_tc;
   b->apply_tc_ok = apply_tc_supported();
   b->max_channels = plans[0]->p.max_channels;
   b->sms = sms;
@@ -236,6 +242,18 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
       FieldPtsJob fj = d.fpts;
       fj.cloud = k;
       fpts.push_back(fj);
+      // the tensor-core form: chunks of a multiple of 64 points, no more than the partials hold;
+      // a lone cloud takes as many as fill whole waves of SMs with its frequency tiles
+      const int ftiles = (fj.h + 127) / 128;
+      int want = fj.chunks;
+      if (count == 1 && fj.chunks * ftiles > sms)
+        want = std::max(1, (std::max(1, fj.chunks * ftiles / sms) * sms) / ftiles);
+      want = std::min(want, fj.chunks);
+      FieldPtsJob tj = fj;
+      tj.pts = std::max<int64_t>(64, (fj.n + want - 1) / want + 63) / 64 * 64;
+      tj.chunks = (int)((fj.n + tj.pts - 1) / tj.pts);
+      fpts_tc.push_back(tj);
+      items_n.push_back(fieldpts_tc_items(tj));
     }
     for (int mode = 0; mode < 3 && !b->compact; ++mode) {
       if (count == 1 && tune.pairs && !d.pair_units[mode].empty()) {  // a lone cloud: the plan's pair units
@@ -318,7 +336,9 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
     rexp_n.push_back(ozaki_row_exponent_blocks(pl->m));
     strip_n.push_back(ozaki_col_split_blocks(pl->m));
   }
-  const std::vector<int> pre_tiles = prefix_of(tiles_n), pre_wide = prefix_of(wide_n), pre_fillw = prefix_of(fillw_n);
+  const std::vector<int> pre_tiles = prefix_of(tiles_n), pre_wide = prefix_of(wide_n), pre_fillw = prefix_of(fillw_n),
+                         pre_items = prefix_of(items_n);
+  b->fpts_items = pre_items.back();
   b->fillw_blocks = pre_fillw.back();
   b->apply_tiles = pre_tiles.back();
   b->wide_blocks = pre_wide.back();
@@ -366,7 +386,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
                o_phi = vtable(phi), o_elem_pre = vtable(pre_elem), o_grp_pre = vtable(pre_grp), o_rexp_pre = vtable(pre_rexp), o_rowa_pre = vtable(pre_rowa),
                o_strip_pre = vtable(pre_strip), o_oz = vtable(oz), o_fpts = vtable(fpts),
                o_apply_tc = vtable(b->apply_tc_h), o_tile_pre = vtable(pre_tiles), o_wide_pre = vtable(pre_wide),
-               o_fillw_pre = vtable(pre_fillw);
+               o_fillw_pre = vtable(pre_fillw), o_fpts_tc = vtable(fpts_tc), o_items_pre = vtable(pre_items);
   const size_t table_bytes = L.total;
   // per call: the CloudCalls, then the block prefixes of the apply, the points-based Phi^T F,
   // its sum over the chunks and the tensor-core apply's Z images
@@ -405,6 +425,8 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
   b->d_tile_prefix = reinterpret_cast<int*>(D + o_tile_pre);
   b->d_wide_prefix = reinterpret_cast<int*>(D + o_wide_pre);
   b->d_fillw_prefix = reinterpret_cast<int*>(D + o_fillw_pre);
+  b->d_fpts_tc = reinterpret_cast<FieldPtsJob*>(D + o_fpts_tc);
+  b->d_item_prefix = reinterpret_cast<int*>(D + o_items_pre);
   b->d_small_prefix = reinterpret_cast<int*>(D + o_small_pre);
   b->d_phi = reinterpret_cast<PhiCloud*>(D + o_phi);
   b->d_elem_prefix = reinterpret_cast<int*>(D + o_elem_pre);
@@ -729,9 +751,10 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   // c, the tensor-core form's time hardly (it has a fixed cost per 256-point tile instead), so
   // above 16 channels always, from 9 channels on when every cloud has m >= 512 (measured on
   // GB300 at N = 10^5 and 10^6, m = 128 .. 1024); up to the Z images' capacity
-  const bool tc_fits = mode != kModeFeatures && b->apply_tc_ok && max_c <= std::min(kApplyTcMaxC, b->max_channels);
-  const bool use_tc = tc_fits && (b->apply_tc_mode == 2 ||
-                                  (b->apply_tc_mode == 1 && (max_c > 16 || (max_c > 8 && b->min_m >= 512))));
+  const bool tc_rule = b->apply_tc_ok && max_c <= std::min(kApplyTcMaxC, b->max_channels) &&
+                       (b->apply_tc_mode == 2 ||
+                        (b->apply_tc_mode == 1 && (max_c > 16 || (max_c > 8 && b->min_m >= 512))));
+  const bool use_tc = mode != kModeFeatures && tc_rule;
   // a pinned staging buffer whose previous upload has been consumed
   const int slot = b->stage_next;
   b->stage_next = (slot + 1) % BatchImpl::kStageRing;
@@ -752,10 +775,13 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   // few channels, where it is faster than a pass over Psi (its cost grows with c, the pass's
   // hardly) and carries no BF16 rounding
   const bool pts = b->compact || (mode == kModeIntegrate && b->pts_ok && max_c <= kPtsMaxChannels);
+  // the same on the tensor cores where the apply takes them (the two share the rule)
+  const bool use_tcf = pts && tc_rule;
   // the blocks of the points-based Phi^T F (they depend on c too)
   int* hq = hp + (n + 1);
   hq[0] = 0;
-  for (int k = 0; k < n; ++k) hq[k + 1] = hq[k] + (pts ? fieldpts_blocks(b->fpts_h[k], calls[k].c, cg) : 0);
+  for (int k = 0; k < n; ++k)
+    hq[k + 1] = hq[k] + (pts && !use_tcf ? fieldpts_blocks(b->fpts_h[k], calls[k].c, cg) : 0);
   const int fpts_blocks = hq[n];
   const int* d_fpts_prefix = d_apply_prefix + (n + 1);
   int* hr = hq + (n + 1);  // and of their sums over the chunks
@@ -785,12 +811,17 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   };
   auto reductions = [&](cudaStream_t s, Timing* t) -> rfd_status {
     if (pts) {  // Phi^T F from the points, summed over the chunks by the reduce kernel
+      const FieldPtsJob* fj = use_tcf ? b->d_fpts_tc : b->d_fpts;
       {
         StepScope sc(t, s, RFD_STEP_FIELD);
-        BCK(launch_fieldpts_batched(b->d_fpts, d_fpts_prefix, n, fpts_blocks, cg, b->d_calls, s));
+        if (use_tcf)
+          BCK(launch_fieldpts_tc(fj, b->d_item_prefix, n, b->fpts_items, std::min(b->fpts_items, b->sms), b->d_calls,
+                                 b->d_err, s));
+        else
+          BCK(launch_fieldpts_batched(fj, d_fpts_prefix, n, fpts_blocks, cg, b->d_calls, s));
       }
       StepScope sc(t, s, RFD_STEP_REDUCE);
-      BCK(launch_fieldpts_reduce(b->d_fpts, d_fred_prefix, n, fred_blocks, b->d_calls, s));
+      BCK(launch_fieldpts_reduce(fj, d_fred_prefix, n, fred_blocks, b->d_calls, s));
       return RFD_OK;
     }
     if (pipelined) {
@@ -856,7 +887,8 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   }
   if (!with_phi) {
     // the points-based path: both of its launches' grids (they depend on every call's c)
-    const int key[4] = {mode, pts ? -4 - fpts_blocks : -1, pts ? akey_cg + 64 * fred_blocks : akey_cg, akey_blocks};
+    const int key[4] = {mode, pts ? (use_tcf ? -(1 << 24) - b->fpts_items : -4 - fpts_blocks) : -1,
+                        pts ? akey_cg + 64 * fred_blocks : akey_cg, akey_blocks};
     return run_segment(b, key, graph, tm, [&](cudaStream_t s, Timing* t) -> rfd_status {
       rfd_status r = reductions(s, t);
       return r == RFD_OK ? small_apply(s, t) : r;

@@ -117,3 +117,46 @@ def test_tensor_core_apply_on_compact_plan_and_batch():
     finally:
         for p in plans:
             p.close()
+
+
+@pytest.mark.parametrize("n,m,c,ld", [(3001, 130, 9, 9), (5000, 514, 17, 20), (2047, 256, 40, 40),
+                                      (777, 1024, 64, 67)])
+def test_tensor_core_field_from_points_matches_simt(n, m, c, ld):
+    """A compact plan's B^T F from the points on the tensor cores (Phi^T and F split
+    into BF16 hi / lo parts, K over the points) against the SIMT kernel of the same
+    plan and against the oracle: point counts that are not multiples of 64 (a
+    partial last step of a chunk), frequency tiles of 128 that the cloud's h fills
+    only in part (m = 130, 514), leading dimensions above c."""
+    rng = synth.rng_for(29, c, n)
+    pts = synth.unit_sphere(n, rng)
+    F = synth.gaussian_field(n, c, 29, n)
+    eps, seed = 0.1, 7
+    lam = 0.1 * m / max(n, m)
+    ref = oracle.rfd_gfi(pts, F, eps, lam, m, seed)
+    Fp = np.zeros((n, ld), np.float32)
+    Fp[:, :c] = F
+    P, Ft = _cuda(pts), _cuda(Fp)
+    outs = {}
+    for mode in (2, 0):
+        plan = rfd.Plan(n, m, eps, lam, seed, max_channels=c, precision=BF16, stream=torch.cuda.current_stream(DEV))
+        try:
+            plan.features(P)
+            plan.compact()
+            assert rfd.lib.rfd_debug_plan_set_apply_tc(plan.handle, mode) == 0, rfd.rfd_last_error()
+            out = torch.full((n, ld), float("nan"), device=DEV)
+            rfd.rfd_integrate(plan.handle, Ft, c, ld, out, ld)
+            plan.sync()
+        finally:
+            plan.close()
+        res = out.cpu().numpy()
+        if ld > c:
+            assert np.isnan(res[:, c:]).all(), "columns beyond c were written"
+        outs[mode] = res[:, :c]
+    e = pc.assert_matches(outs[2], ref, F, BF16, label=f"tensor-core B^T F N={n} m={m} c={c} ld={ld}")
+    inc = outs[0].astype(np.float64) - F
+    d = outs[2].astype(np.float64) - outs[0]
+    rel = np.linalg.norm(d) / np.linalg.norm(inc)
+    worst = np.abs(d).max() / np.abs(inc).max()
+    print(f"N={n} m={m} c={c}: vs oracle {e}, vs SIMT: frobenius {rel:.3e}, worst element {worst:.3e}")
+    assert rel <= 2e-4, rel
+    assert worst <= 2e-3, worst
