@@ -63,12 +63,14 @@ RFD_API rfd_status rfd_debug_plan_set_phase(rfd_plan_t plan, int32_t phase_block
 RFD_API rfd_status rfd_debug_plan_set_overlap(rfd_plan_t plan, int32_t enable);
 
 /* Which form step a6 of a BF16 plan takes (Sec. 2.4, the apply of the low-rank
- * factors).  enable = 0: the FP32 SIMT kernel in every call.  1 (the default):
- * the tensor-core form where it is the faster -- calls of 17..64 channels, or
- * 9..16 channels when m >= 512 -- else the SIMT kernel.  2: the tensor-core form
- * in every call of c <= min(64, max_channels): Phi recomputed in FP32 and split
- * into BF16 hi and lo parts, out = F + Phi_hi Z_hi + Phi_hi Z_lo + Phi_lo Z_hi
- * with FP32 accumulation.  RFD_EINVAL for FP32 plans, plans with
+ * factors), and with it a compact plan's B^T F from the points.  enable = 0:
+ * the FP32 SIMT kernels in every call.  1 (the default): the tensor-core forms
+ * where they are the faster -- calls of 17..64 channels, or 9..16 channels when
+ * m >= 512; for B^T F from the points, clouds of 2^19 points or more -- else
+ * the SIMT kernels.  2: the tensor-core forms in every call of
+ * c <= min(64, max_channels): Phi recomputed in FP32 and split into BF16 hi and
+ * lo parts, out = F + Phi_hi Z_hi + Phi_hi Z_lo + Phi_lo Z_hi (and B^T F
+ * likewise) with FP32 accumulation.  RFD_EINVAL for FP32 plans, plans with
  * RFD_FLAG_GRAPH or another value; RFD_ENOTSUP (enable = 2) off sm_103.
  * Host only. */
 RFD_API rfd_status rfd_debug_plan_set_apply_tc(rfd_plan_t plan, int32_t enable);

@@ -80,6 +80,7 @@ struct BatchImpl {
   FieldPtsJob* d_fpts_tc = nullptr;
   int* d_item_prefix = nullptr;
   int fpts_items = 0;
+  int64_t total_n = 0;  // the points of all clouds
   PairUnit* d_pair[3] = {};  // a lone cloud with m >= 512: the 2-SM form of the Gram modes
   int n_pair[3] = {};
   int pair_stage_bytes = 0;
@@ -322,6 +323,7 @@ rfd_status batch_build(rfd_plan_s* const* plans, int count, cudaStream_t st, Mem
     b->apply_tc_ok = b->apply_tc_ok && tj.zimg != nullptr && tj.w2pi != nullptr;
     b->max_channels = std::min(b->max_channels, pl->p.max_channels);
     b->min_m = (k == 0) ? pl->m : std::min(b->min_m, pl->m);
+    b->total_n += pl->n;
     small_n.push_back(pl->m);
     wide_n.push_back(small_wide_blocks(pl->m, pl->p.max_channels));
     PhiCloud pc = d.phi;
@@ -775,8 +777,10 @@ rfd_status batch_run(BatchImpl* b, int mode, const CloudCall* calls, Timing* tm)
   // few channels, where it is faster than a pass over Psi (its cost grows with c, the pass's
   // hardly) and carries no BF16 rounding
   const bool pts = b->compact || (mode == kModeIntegrate && b->pts_ok && max_c <= kPtsMaxChannels);
-  // the same on the tensor cores where the apply takes them (the two share the rule)
-  const bool use_tcf = pts && tc_rule;
+  // the same on the tensor cores where the apply takes them (the two share the rule), and by
+  // default only for 2^19 points or more: its persistent CTAs take whole SMs, and in a serving
+  // mix of smaller concurrent requests that cost latency (p99 2.0 -> 6.4 ms measured)
+  const bool use_tcf = pts && tc_rule && (b->apply_tc_mode == 2 || b->total_n >= (int64_t(1) << 19));
   // the blocks of the points-based Phi^T F (they depend on c too)
   int* hq = hp + (n + 1);
   hq[0] = 0;
